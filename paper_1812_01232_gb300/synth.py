@@ -1,0 +1,258 @@
+"""Seeded synthetic GOSMA workloads (numpy only).
+
+This module only draws inputs: mixtures, ground-truth poses and batches of
+sub-cubes.  It holds none of the bound or objective arithmetic, so both the
+CUDA path and the CPU oracle can be fed from it.
+
+Workloads (sizes and distributions follow the evaluation set-up of the
+method; the paper's own data sets are not used):
+
+* ``tiny_problem``      10 Gaussian components in a 4 x 4 x 3 m room, 8 vMF
+                        image components (7 projected + 1 outlier).
+* ``paper_scale_problem`` 128 components in a 10 x 10 x 3 m room, 64 vMF
+                        components (48 noisy inliers + 16 outliers in a 90
+                        degree field of view).
+* ``uneven_problems``   many independent tiny-style problems with component
+                        counts drawn from U{16..256} x U{8..128}.
+* ``stress_problem``    2048 x 512 components with kappa in U[5, 2000] and
+                        near-antipodal image means.
+* ``tree_cubes``        sub-cubes at given depths of the branch-and-bound
+                        tree, reached by random root-to-leaf paths.
+
+Conventions: a camera with rotation R (world to camera) and centre t sees
+model point mu along R (mu - t) / |mu - t| (the transformation of the proof
+of Lemma 1).  A cube row is ``[r0(3), r_half_width, t0(3), t_half_width(3)]``.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+CUBE_LEN = 10
+
+
+def _quat_to_matrix(q):
+    w, x, y, z = q
+    return np.array([
+        [1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+        [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+        [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)],
+    ])
+
+
+def random_rotation(rng):
+    """Rotation uniform on SO(3) (normalised 4-D Gaussian quaternion).
+
+    Returns (R, r) with r the angle-axis vector, |r| <= pi."""
+    q = rng.standard_normal(4)
+    q /= np.linalg.norm(q)
+    if q[0] < 0:
+        q = -q
+    ang = 2.0 * np.arccos(min(1.0, q[0]))
+    s = np.linalg.norm(q[1:])
+    axis = q[1:] / s if s > 0 else np.array([1.0, 0.0, 0.0])
+    return _quat_to_matrix(q), axis * ang
+
+
+def _unit(v):
+    return v / np.linalg.norm(v, axis=-1, keepdims=True)
+
+
+def _uniform_sphere(rng, n):
+    return _unit(rng.standard_normal((n, 3)))
+
+
+def _uniform_cap(rng, n, half_angle):
+    """Directions uniform (by area) on the cap of the given half-angle around +z."""
+    cz = 1.0 - rng.random(n) * (1.0 - np.cos(half_angle))
+    ph = rng.random(n) * 2 * np.pi
+    sz = np.sqrt(np.maximum(0.0, 1 - cz * cz))
+    return np.stack([sz * np.cos(ph), sz * np.sin(ph), cz], axis=1)
+
+
+def _perturb(rng, d, sigma_ang):
+    """Rotate each unit vector by a small random angle (isotropic, std sigma_ang per axis)."""
+    out = d + sigma_ang * rng.standard_normal(d.shape)
+    return _unit(out)
+
+
+def _means_in_room(rng, n, half, t_gt, min_dist):
+    mu = np.empty((n, 3))
+    k = 0
+    while k < n:
+        p = (rng.random(3) * 2 - 1) * half
+        if np.linalg.norm(p - t_gt) >= min_dist:
+            mu[k] = p
+            k += 1
+    return mu
+
+
+def _camera_dirs(R, mu, t):
+    return _unit((mu - t) @ R.T)
+
+
+def tiny_problem(seed: int, n1: int = 10, n_in: int = 7, n_out: int = 1, zeta: float = 0.5):
+    """Small single problem: 4 x 4 x 3 m room, sigma = 0.05 m, equal weights,
+    image = n_in projected components (qPN concentration) + n_out outliers
+    (uniform direction, kappa = 50).  Translation domain [-1, 1]^3."""
+    rng = np.random.default_rng(seed)
+    R, r = random_rotation(rng)
+    t_gt = rng.uniform(-0.5, 0.5, 3)
+    half = np.array([2.0, 2.0, 1.5])
+    mu1 = _means_in_room(rng, n1, half, t_gt, 1.2 * zeta)
+    sigma1 = np.full(n1, 0.05)
+    phi1 = np.full(n1, 1.0 / n1)
+    idx = rng.permutation(n1)[:n_in]
+    dirs_in = _camera_dirs(R, mu1[idx], t_gt)
+    dist = np.linalg.norm(mu1[idx] - t_gt, axis=1)
+    kap_in = (dist / sigma1[idx]) ** 2 + 1.0
+    dirs_out = _uniform_sphere(rng, n_out)
+    mu2 = np.concatenate([dirs_in, dirs_out])
+    kappa2 = np.concatenate([kap_in, np.full(n_out, 50.0)])
+    n2 = n_in + n_out
+    phi2 = np.full(n2, 1.0 / n2)
+    return dict(name="tiny", mu1=mu1, sigma1=sigma1, phi1=phi1, mu2=mu2, kappa2=kappa2, phi2=phi2,
+                t_lo=np.full(3, -1.0), t_hi=np.full(3, 1.0), zeta=zeta, eps=1e-3,
+                R_gt=R, r_gt=r, t_gt=t_gt)
+
+
+def noise_free_problem(seed: int, n1: int = 6, zeta: float = 0.5):
+    """Every model component projected at the true pose with its own qPN
+    concentration and weight: the image mixture equals the projected model
+    mixture, so the L2 distance is zero at the true pose."""
+    rng = np.random.default_rng(seed)
+    R, r = random_rotation(rng)
+    t_gt = rng.uniform(-0.5, 0.5, 3)
+    half = np.array([2.0, 2.0, 1.5])
+    mu1 = _means_in_room(rng, n1, half, t_gt, 1.2 * zeta)
+    sigma1 = np.full(n1, 0.25)
+    phi1 = np.full(n1, 1.0 / n1)
+    mu2 = _camera_dirs(R, mu1, t_gt)
+    kappa2 = (np.linalg.norm(mu1 - t_gt, axis=1) / sigma1) ** 2 + 1.0
+    return dict(name="noise_free", mu1=mu1, sigma1=sigma1, phi1=phi1, mu2=mu2, kappa2=kappa2, phi2=phi1.copy(),
+                t_lo=np.full(3, -1.0), t_hi=np.full(3, 1.0), zeta=zeta, eps=1e-3,
+                R_gt=R, r_gt=r, t_gt=t_gt)
+
+
+def paper_scale_problem(seed: int, n1: int = 128, n_in: int = 48, n_out: int = 16, zeta: float = 0.5):
+    """10 x 10 x 3 m room, sigma in U[0.03, 0.1] m, Dirichlet(1) weights.
+    Image: the n_in model components nearest the optical axis (+z of the
+    camera), each direction perturbed by 1 degree of angular noise, plus
+    n_out directions uniform on a 90 degree field-of-view cap; kappa in
+    U[20, 200]; Dirichlet(1) weights.  Translation domain [-2, 2]^3."""
+    rng = np.random.default_rng(seed)
+    R, r = random_rotation(rng)
+    t_gt = rng.uniform(-1.0, 1.0, 3)
+    half = np.array([5.0, 5.0, 1.5])
+    mu1 = _means_in_room(rng, n1, half, t_gt, 1.2 * zeta)
+    sigma1 = rng.uniform(0.03, 0.1, n1)
+    phi1 = rng.dirichlet(np.ones(n1))
+    d = _camera_dirs(R, mu1, t_gt)
+    idx = np.argsort(-d[:, 2])[:n_in]
+    dirs_in = _perturb(rng, d[idx], np.deg2rad(1.0))
+    dirs_out = _uniform_cap(rng, n_out, np.deg2rad(45.0))
+    mu2 = np.concatenate([dirs_in, dirs_out])
+    n2 = n_in + n_out
+    kappa2 = rng.uniform(20.0, 200.0, n2)
+    phi2 = rng.dirichlet(np.ones(n2))
+    return dict(name="paper_scale", mu1=mu1, sigma1=sigma1, phi1=phi1, mu2=mu2, kappa2=kappa2, phi2=phi2,
+                t_lo=np.full(3, -2.0), t_hi=np.full(3, 2.0), zeta=zeta, eps=1e-4,
+                R_gt=R, r_gt=r, t_gt=t_gt)
+
+
+def uneven_problems(seed: int, count: int = 256, outlier_frac: float = 0.2):
+    """Independent tiny-style problems with n1 ~ U{16..256}, n2 ~ U{8..128},
+    a fraction of the image components being outliers."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(count):
+        n1 = int(rng.integers(16, 257))
+        n2 = int(rng.integers(8, 129))
+        n_out = int(round(outlier_frac * n2))
+        n_in = min(n2 - n_out, n1)
+        n_out = n2 - n_in
+        p = tiny_problem(int(rng.integers(0, 2**31)), n1=n1, n_in=n_in, n_out=n_out)
+        p["name"] = "uneven_%d" % k
+        out.append(p)
+    return out
+
+
+def stress_problem(seed: int, n1: int = 2048, n2: int = 512, antipodal_frac: float = 0.1, zeta: float = 0.5):
+    """Large precision stress: 10 x 10 x 3 m room, sigma in U[0.03, 0.1] m,
+    kappa_2 in U[5, 2000]; at least ``antipodal_frac`` of the image means lie
+    within 1 degree of the antipode of a projected model mean."""
+    rng = np.random.default_rng(seed)
+    R, r = random_rotation(rng)
+    t_gt = rng.uniform(-1.0, 1.0, 3)
+    half = np.array([5.0, 5.0, 1.5])
+    mu1 = _means_in_room(rng, n1, half, t_gt, 1.2 * zeta)
+    sigma1 = rng.uniform(0.03, 0.1, n1)
+    phi1 = rng.dirichlet(np.ones(n1))
+    d = _camera_dirs(R, mu1, t_gt)
+    n_anti = int(np.ceil(antipodal_frac * n2))
+    n_in = n2 // 2
+    n_rand = n2 - n_in - n_anti
+    pick = rng.permutation(n1)
+    dirs_in = _perturb(rng, d[pick[:n_in]], np.deg2rad(0.5))
+    anti = -d[pick[n_in:n_in + n_anti]]
+    # move each antipode by an angle in [0, 1] degree
+    dirs_anti = _unit(anti + np.tan(np.deg2rad(rng.uniform(0, 1.0, (n_anti, 1)))) *
+                      _unit(np.cross(anti, rng.standard_normal((n_anti, 3)))))
+    dirs_rand = _uniform_sphere(rng, n_rand)
+    mu2 = np.concatenate([dirs_in, dirs_anti, dirs_rand])
+    kappa2 = rng.uniform(5.0, 2000.0, n2)
+    phi2 = rng.dirichlet(np.ones(n2))
+    return dict(name="stress", mu1=mu1, sigma1=sigma1, phi1=phi1, mu2=mu2, kappa2=kappa2, phi2=phi2,
+                t_lo=np.full(3, -2.0), t_hi=np.full(3, 2.0), zeta=zeta, eps=1e-4,
+                R_gt=R, r_gt=r, t_gt=t_gt)
+
+
+def root_cube(t_lo, t_hi):
+    t_lo = np.asarray(t_lo, dtype=np.float64)
+    t_hi = np.asarray(t_hi, dtype=np.float64)
+    c = np.zeros(CUBE_LEN)
+    c[3] = np.pi
+    c[4:7] = 0.5 * (t_lo + t_hi)
+    c[7:10] = 0.5 * (t_hi - t_lo)
+    return c
+
+
+def tree_cubes(seed: int, n: int, t_lo, t_hi, depth_lo: int = 2, depth_hi: int = 12, near=None, near_frac=0.0):
+    """``n`` sub-cubes at depths uniform in [depth_lo, depth_hi], each reached
+    from the root by a random path (at every level a random choice between
+    splitting rotation and translation, then a random child of the eight).
+    Cubes whose rotation part lies wholly outside the pi-ball are redrawn.
+    With ``near=(r, t)``, a fraction ``near_frac`` of the paths follow the
+    children that contain that pose, so the batch also holds cubes around
+    the optimum."""
+    rng = np.random.default_rng(seed)
+    root = root_cube(t_lo, t_hi)
+    out = np.empty((n, CUBE_LEN))
+    depth = rng.integers(depth_lo, depth_hi + 1, n)
+    k = 0
+    while k < n:
+        c = root.copy()
+        follow = near is not None and rng.random() < near_frac
+        for _ in range(depth[k]):
+            rot = rng.random() < 0.5
+            if rot:
+                h = c[3] * 0.5
+                if follow:
+                    bits = (np.asarray(near[0]) > c[0:3]).astype(float)
+                else:
+                    bits = rng.integers(0, 2, 3).astype(float)
+                c[0:3] = c[0:3] + (2 * bits - 1) * h
+                c[3] = h
+            else:
+                h = c[7:10] * 0.5
+                if follow:
+                    bits = (np.asarray(near[1]) > c[4:7]).astype(float)
+                else:
+                    bits = rng.integers(0, 2, 3).astype(float)
+                c[4:7] = c[4:7] + (2 * bits - 1) * h
+                c[7:10] = h
+        gap = np.maximum(np.abs(c[0:3]) - c[3], 0.0)
+        if np.linalg.norm(gap) > np.pi:
+            continue
+        out[k] = c
+        k += 1
+    return out

@@ -1,0 +1,62 @@
+"""Algorithm 1 (GOSMA) in the oracle: certificate checks against brute force
+and recovery of the true pose on noise-free data."""
+import numpy as np
+import pytest
+from scipy.spatial.transform import Rotation
+
+from paper_1812_01232_gb300 import synth
+
+
+def _noise_free(seed, n1, sigma):
+    p = synth.noise_free_problem(seed, n1=n1)
+    p["sigma1"] = np.full(n1, sigma)
+    p["kappa2"] = (np.linalg.norm(p["mu1"] - p["t_gt"], axis=1) / sigma) ** 2 + 1
+    return p
+
+
+def test_bnb_recovers_true_pose_noise_free(oracle_mod):
+    """With the image mixture equal to the projected model, the L2 distance
+    is zero at the true pose, so f* = -C22 (proof of Lemma 1) and the pose
+    meets the success criterion of Sec. 6 (angle < 0.1 rad, relative
+    translation error < 5%)."""
+    p = _noise_free(3, 4, 0.1)
+    mix = oracle_mod.Mixtures.from_problem(p)
+    res = oracle_mod.bnb(mix, p["t_lo"], p["t_hi"], p["zeta"], 1e-2, pop=64, max_nodes=40_000_000)
+    c22 = oracle_mod.c22(mix)
+    assert res["status"] == 0
+    assert res["gap_norm"] <= 1e-2
+    assert res["f"] == pytest.approx(-c22, abs=1e-2 * c22)
+    assert res["lb"] <= -c22 + 1e-9
+    ang = np.arccos(np.clip((np.trace(res["R"].T @ p["R_gt"]) - 1) / 2, -1, 1))
+    assert ang < 0.1
+    assert np.linalg.norm(res["t"] - p["t_gt"]) < 0.05 * np.linalg.norm(p["t_gt"]) + 1e-3
+    # the reported pose attains the reported objective
+    assert oracle_mod.objective(mix, res["R"], res["t"]) == pytest.approx(res["f"], rel=1e-12)
+
+
+def test_bnb_certificate_against_brute_force(oracle_mod):
+    """d* - eps never exceeds the objective at any sampled feasible pose, and
+    the global lower bound never exceeds it either."""
+    p = synth.tiny_problem(5, n1=5, n_in=3, n_out=1)
+    p["sigma1"] = np.full(5, 0.1)
+    mix = oracle_mod.Mixtures.from_problem(p)
+    eps = 2e-2
+    res = oracle_mod.bnb(mix, p["t_lo"], p["t_hi"], p["zeta"], eps, pop=64, max_nodes=40_000_000)
+    assert res["status"] == 0
+    c22 = oracle_mod.c22(mix)
+    rng = np.random.default_rng(6)
+    best = np.inf
+    for _ in range(4000):
+        r = Rotation.random(random_state=rng).as_rotvec()
+        t = rng.uniform(p["t_lo"], p["t_hi"])
+        if np.min(np.linalg.norm(p["mu1"] - t, axis=1)) < p["zeta"]:
+            continue
+        best = min(best, oracle_mod.objective_r(mix, r, t))
+    # local refinement from the best random samples cannot beat the certificate either
+    assert res["lb"] <= best + 1e-9
+    assert res["f"] - eps * c22 <= best + 1e-9
+    assert oracle_mod.objective(mix, res["R"], res["t"]) == pytest.approx(res["f"], rel=1e-12)
+    # a grid through the found optimum: nothing on it is below lb
+    for d in np.linspace(-0.05, 0.05, 11):
+        f = oracle_mod.objective_r(mix, res["r"] + d, res["t"])
+        assert f >= res["lb"] - 1e-9
