@@ -1,0 +1,150 @@
+/*
+ * libgosma: C ABI of the GB300 (sm_103a) implementation of the GOSMA
+ * branch-and-bound hot path (Campbell et al., "The Alignment of the
+ * Spheres: Globally-Optimal Spherical Mixture Alignment for Camera Pose
+ * Estimation").
+ *
+ * Conventions shared by every entry point
+ *   - Plain pointers and sizes only.  Unless an argument says "device",
+ *     pointers are host pointers; the library copies what it needs and the
+ *     caller keeps ownership of every buffer it passes.
+ *   - All floating-point inputs and outputs are IEEE double.
+ *   - Return value: GOSMA_OK (0) or a negative GOSMA_E* code.  No C++
+ *     exception crosses the ABI.  gosma_last_error() gives a message for the
+ *     last failing call on a context.
+ *   - A context is bound to one device and one CUDA stream; calls on one
+ *     context must not run concurrently from several host threads.
+ *   - Vectors are row-major: an array of n 3-vectors is n x 3 doubles.
+ *   - Camera model (proof of Lemma 1): a camera with rotation R (world to
+ *     camera) and centre t sees model point mu along R (mu - t)/|mu - t|.
+ *     Rotations are angle-axis vectors r, R = R_r by Rodrigues' formula
+ *     (Sec. 4.1).
+ */
+#ifndef GOSMA_H
+#define GOSMA_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GOSMA_OK 0
+#define GOSMA_EINVAL (-1)     /* invalid argument (sizes, weights, concentrations, ...) */
+#define GOSMA_ENOMEM (-2)     /* device or host allocation failed */
+#define GOSMA_ECUDA (-3)      /* a CUDA runtime call failed */
+#define GOSMA_ETIMEOUT (-4)   /* a bounded device wait ran out */
+#define GOSMA_ENOTREADY (-5)  /* mixtures or domain not set yet */
+
+/* Result status of gosma_bnb_solve (gosma_result.status). */
+#define GOSMA_OPTIMAL 0      /* d* - global lower bound <= eps (Algorithm 1 stopping rule) */
+#define GOSMA_NODE_LIMIT 1   /* stopped at opts.max_nodes */
+#define GOSMA_TIME_LIMIT 2   /* stopped at opts.max_seconds */
+#define GOSMA_QUEUE_FULL 3   /* the device queue reached its capacity */
+
+typedef struct gosma_ctx gosma_ctx;
+
+/* A 6-orthotope C_r x C_t (Sec. 4.1): rotation cube with centre r0 and
+ * half-width r_hw, translation cuboid with centre t0 and half-widths t_hw.
+ * 80 bytes, the layout of 10 consecutive doubles. */
+typedef struct {
+    double r0[3];
+    double r_hw;
+    double t0[3];
+    double t_hw[3];
+} gosma_cube;
+
+/* Per-cube bound record written by gosma_eval_bounds_detail (8 doubles). */
+typedef struct {
+    double lb;        /* Theorem 1 lower bound, = self_lb - 2 cross_ub          */
+    double ub;        /* Theorem 1 upper bound f(R_r0, t0), +inf if t0 infeasible */
+    double self_lb;   /* sum over i,j of the self-pair lower bounds             */
+    double cross_ub;  /* sum over i,j of the cross-pair upper bounds            */
+    double self_c;    /* self sum of f at the centre                            */
+    double cross_c;   /* cross sum of f at the centre                           */
+    double psi_r;     /* rotation uncertainty angle (Lemma 2)                   */
+    double psi_t_max; /* max over model means of the translation angle (Lemma 3) */
+} gosma_bound;
+
+typedef struct {
+    double eps;          /* tolerance on the normalised L2 distance f/C22 + 1 (Sec. 6 uses 0.1) */
+    int pop;             /* hypercubes removed from the queue per iteration (Algorithm 1); each gives 8 children */
+    long long max_nodes; /* stop after this many evaluated sub-cubes (<= 0: no limit) */
+    double max_seconds;  /* wall-clock limit (<= 0: no limit) */
+    int use_sma;         /* run local refinement (SMA, Sec. 5) when a sub-cube improves d* */
+    int sma_max_iter;    /* L-BFGS iterations per SMA call (<= 0: 100) */
+    long long queue_capacity; /* device queue capacity in cubes (<= 0: library default) */
+} gosma_opts;
+
+typedef struct {
+    double R[9], r[3], t[3]; /* best pose (r canonical: |r| <= pi) */
+    double objective;        /* d*: f at the best pose (FP64)      */
+    double objective_norm;   /* d* divided by C22, plus 1          */
+    double lower_bound;      /* global lower bound at termination   */
+    double gap_norm;         /* (d* - lower_bound) / C22            */
+    double c22;              /* C22 = 2 pi * integral of p2^2       */
+    long long nodes;         /* sub-cubes evaluated                 */
+    long long iterations;    /* Algorithm 1 loop iterations          */
+    long long sma_calls;
+    long long queue_peak;
+    double seconds;
+    int status;              /* GOSMA_OPTIMAL, GOSMA_NODE_LIMIT, ... */
+} gosma_result;
+
+/* Create a context on CUDA device `device`, issuing all work on `stream`
+ * (a cudaStream_t; NULL means the legacy default stream).  The context owns
+ * every device buffer it allocates.  Returns GOSMA_ECUDA when the device
+ * cannot be used (no GPU, or a device that is not sm_103). */
+int gosma_create(int device, void *stream, gosma_ctx **out);
+
+/* Release the context and all its device memory.  NULL is accepted. */
+void gosma_destroy(gosma_ctx *ctx);
+
+/* Message for the last error on ctx ("" if none).  Valid until the next call. */
+const char *gosma_last_error(const gosma_ctx *ctx);
+
+/* Set the GMM theta_1 = {mu1 (n1 x 3), sigma1 (standard deviations), phi1}
+ * and the vMFMM theta_2 = {mu2 (n2 x 3, unit vectors), kappa2, phi2}
+ * (Sec. 4, Eq. GMM, Eq. vMFMM).  Deep-copies the arrays.  GOSMA_EINVAL when
+ * n < 1, sigma <= 0, kappa <= 0, a weight < 0, |sum(phi) - 1| > 1e-9 or
+ * ||mu2_j| - 1| > 1e-6. */
+int gosma_set_mixtures(gosma_ctx *ctx, int n1, const double *mu1, const double *sigma1, const double *phi1, int n2,
+                       const double *mu2, const double *kappa2, const double *phi2);
+
+/* Translation domain Omega_t: the cuboid [t_lo, t_hi] minus the points
+ * within zeta of any model mean (Sec. 4.1).  zeta >= 0, t_lo < t_hi. */
+int gosma_set_domain(gosma_ctx *ctx, const double t_lo[3], const double t_hi[3], double zeta);
+
+/* Theorem 1 bounds for n cubes: lb[k] <= min of f over the feasible part of
+ * cube k, ub[k] = f at its centre (+inf when the centre is within zeta of a
+ * mean).  Cubes with no feasible pose (rotation part outside the pi-ball,
+ * translation part within zeta of one mean) get lb = ub = +inf.
+ * Pair terms are computed in FP32 (log domain) with a rounding slack that
+ * keeps lb at or below the exact-arithmetic bound; per-cube sums are FP64.
+ * on_device = 0: cubes, lb, ub are host pointers (copied in and out).
+ * on_device = 1: they are device pointers on the context's device; the call
+ * is then asynchronous on the context's stream.  n = 0 is a no-op. */
+int gosma_eval_bounds(gosma_ctx *ctx, const gosma_cube *cubes, int n, double *lb, double *ub, int on_device);
+
+/* Same bounds, with the full per-cube record (gosma_bound, 8 doubles). */
+int gosma_eval_bounds_detail(gosma_ctx *ctx, const gosma_cube *cubes, int n, gosma_bound *out, int on_device);
+
+/* f(R_r, t) of Lemma 1 in FP64 on the device (host pointers). */
+int gosma_eval_objective(gosma_ctx *ctx, const double r[3], const double t[3], double *f);
+
+/* f and its gradient with respect to (r, t) in FP64 on the device, for
+ * `count` poses x (count x 6: r then t, host pointers). */
+int gosma_eval_objective_grad(gosma_ctx *ctx, int count, const double *x, double *f, double *grad);
+
+/* Algorithm 1 (GOSMA) on the device: branch, bound, prune and select run in
+ * device kernels; d* is always an FP64 evaluation of f.  opts may be NULL
+ * (eps = 0.1, pop = 1024, no limits, SMA on). */
+int gosma_bnb_solve(gosma_ctx *ctx, const gosma_opts *opts, gosma_result *out);
+
+/* Diagnostics: measured maximum relative error of the device's approximate
+ * ex2, lg2, rcp, rsqrt and sqrt against FP64 over dense samples (5 values,
+ * in that order), and the error bounds the bound kernel's slack assumes. */
+int gosma_selftest_approx(gosma_ctx *ctx, double measured[5], double assumed[5]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GOSMA_H */

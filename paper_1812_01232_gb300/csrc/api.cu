@@ -1,0 +1,282 @@
+// C ABI entry points of libgosma (declared in include/gosma.h): context,
+// mixtures, domain, bounds and objective.  Branch-and-bound is in bnb.cu.
+#include <math.h>
+#include <string.h>
+
+#include <new>
+
+#include "gosma_internal.cuh"
+
+namespace gosma {
+
+int fail(gosma_ctx *ctx, int code, const std::string &msg) {
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+int cuda_fail(gosma_ctx *ctx, cudaError_t e, const char *what) {
+    return fail(ctx, GOSMA_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+int ensure_stage(gosma_ctx *ctx, size_t bytes) {
+    if (bytes <= ctx->stage_bytes) return GOSMA_OK;
+    if (ctx->d_stage) cudaFree(ctx->d_stage);
+    ctx->d_stage = nullptr;
+    ctx->stage_bytes = 0;
+    cudaError_t e = cudaMalloc(&ctx->d_stage, bytes);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(stage)");
+    ctx->stage_bytes = bytes;
+    return GOSMA_OK;
+}
+
+int ensure_pinned(gosma_ctx *ctx, size_t bytes) {
+    if (bytes <= ctx->pinned_bytes) return GOSMA_OK;
+    if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+    ctx->h_pinned = nullptr;
+    ctx->pinned_bytes = 0;
+    cudaError_t e = cudaMallocHost(&ctx->h_pinned, bytes);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMallocHost(stage)");
+    ctx->pinned_bytes = bytes;
+    return GOSMA_OK;
+}
+
+int setup_constants(gosma_ctx *ctx, float *P2, float *inv_sig2, float *lphi1, double *c22_out);
+int selftest_approx(gosma_ctx *ctx, double measured[5], double assumed[5]);
+
+__global__ void split_bounds(const gosma_bound *__restrict__ in, int n, double *lb, double *ub) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) {
+        if (lb) lb[k] = in[k].lb;
+        if (ub) ub[k] = in[k].ub;
+    }
+}
+
+}  // namespace gosma
+
+using namespace gosma;
+
+extern "C" {
+
+int gosma_create(int device, void *stream, gosma_ctx **out) {
+    if (!out) return GOSMA_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return GOSMA_ECUDA;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return GOSMA_ECUDA;
+    if (prop.major != 10 || prop.minor != 3) return GOSMA_ECUDA;  // built for sm_103a only
+    if (cudaSetDevice(device) != cudaSuccess) return GOSMA_ECUDA;
+    gosma_ctx *c = new (std::nothrow) gosma_ctx();
+    if (!c) return GOSMA_ENOMEM;
+    c->device = device;
+    c->stream = (cudaStream_t)stream;
+    c->sm_count = prop.multiProcessorCount;
+    *out = c;
+    return GOSMA_OK;
+}
+
+void gosma_destroy(gosma_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    bnb_release(ctx);
+    if (ctx->d_mix) cudaFree(ctx->d_mix);
+    if (ctx->d_stage) cudaFree(ctx->d_stage);
+    if (ctx->d_obj) cudaFree(ctx->d_obj);
+    if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+    delete ctx;
+}
+
+const char *gosma_last_error(const gosma_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int gosma_set_mixtures(gosma_ctx *ctx, int n1, const double *mu1, const double *sigma1, const double *phi1, int n2,
+                       const double *mu2, const double *kappa2, const double *phi2) {
+    if (!ctx) return GOSMA_EINVAL;
+    ctx->err.clear();
+    if (n1 < 1 || n2 < 1 || !mu1 || !sigma1 || !phi1 || !mu2 || !kappa2 || !phi2)
+        return fail(ctx, GOSMA_EINVAL, "set_mixtures: empty mixture or null pointer");
+    if (bounds_smem_bytes(n1, n2) > 200 * 1024)
+        return fail(ctx, GOSMA_EINVAL, "set_mixtures: 11*n1 + 5*n2 floats exceed the 200 KB shared-memory budget");
+    double s1 = 0, s2 = 0;
+    for (int i = 0; i < n1; ++i) {
+        if (!(sigma1[i] > 0) || !(phi1[i] >= 0) || !isfinite(mu1[3 * i]) || !isfinite(mu1[3 * i + 1]) ||
+            !isfinite(mu1[3 * i + 2]) || !isfinite(sigma1[i]))
+            return fail(ctx, GOSMA_EINVAL, "set_mixtures: sigma1 must be > 0, phi1 >= 0, means finite");
+        s1 += phi1[i];
+    }
+    for (int j = 0; j < n2; ++j) {
+        double nn = sqrt(mu2[3 * j] * mu2[3 * j] + mu2[3 * j + 1] * mu2[3 * j + 1] + mu2[3 * j + 2] * mu2[3 * j + 2]);
+        if (!(kappa2[j] > 0) || !isfinite(kappa2[j]) || !(phi2[j] >= 0) || !(fabs(nn - 1.0) <= 1e-6))
+            return fail(ctx, GOSMA_EINVAL, "set_mixtures: kappa2 must be > 0, phi2 >= 0, |mu2_j| = 1");
+        s2 += phi2[j];
+    }
+    if (fabs(s1 - 1.0) > 1e-9 || fabs(s2 - 1.0) > 1e-9)
+        return fail(ctx, GOSMA_EINVAL, "set_mixtures: mixture weights must sum to 1");
+    cudaSetDevice(ctx->device);
+    size_t nd = 3 * (size_t)n1 + 2 * n1 + 3 * (size_t)n2 + 2 * n2;
+    size_t nf = 2 * (size_t)n1 + 2 * (size_t)n2;
+    size_t bytes = nd * sizeof(double) + nf * sizeof(float) + 256;
+    void *d = nullptr;
+    cudaError_t e = cudaMalloc(&d, bytes);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(mixtures)");
+    double *pd = (double *)d;
+    double *dmu1 = pd, *dsig = pd + 3 * n1, *dphi1 = dsig + n1, *dmu2 = dphi1 + n1, *dk2 = dmu2 + 3 * n2,
+           *dphi2 = dk2 + n2;
+    float *pf = (float *)(dphi2 + n2);
+    float *inv_sig2 = pf, *lphi1 = pf + n1, *k2f = lphi1 + n1, *P2 = k2f + n2;
+    std::vector<float> hk2(n2);
+    for (int j = 0; j < n2; ++j) hk2[j] = (float)kappa2[j];
+    struct {
+        void *dst;
+        const void *src;
+        size_t n;
+    } cp[] = {{dmu1, mu1, 3 * (size_t)n1 * 8}, {dsig, sigma1, (size_t)n1 * 8}, {dphi1, phi1, (size_t)n1 * 8},
+              {dmu2, mu2, 3 * (size_t)n2 * 8}, {dk2, kappa2, (size_t)n2 * 8},  {dphi2, phi2, (size_t)n2 * 8},
+              {k2f, hk2.data(), (size_t)n2 * 4}};
+    for (auto &c : cp) {
+        e = cudaMemcpyAsync(c.dst, c.src, c.n, cudaMemcpyHostToDevice, ctx->stream);
+        if (e != cudaSuccess) {
+            cudaFree(d);
+            return cuda_fail(ctx, e, "copy mixtures");
+        }
+    }
+    MixDev mx;
+    mx.n1 = n1;
+    mx.n2 = n2;
+    mx.mu1 = dmu1;
+    mx.inv_sig2 = inv_sig2;
+    mx.lphi1 = lphi1;
+    mx.sigma1d = dsig;
+    mx.phi1d = dphi1;
+    mx.mu2 = dmu2;
+    mx.kappa2 = k2f;
+    mx.P2 = P2;
+    mx.kappa2d = dk2;
+    mx.phi2d = dphi2;
+    mx.zeta = ctx->zeta;
+    void *old = ctx->d_mix;
+    MixDev old_mix = ctx->mix;
+    int old_n1 = ctx->n1, old_n2 = ctx->n2;
+    ctx->mix = mx;
+    ctx->n1 = n1;
+    ctx->n2 = n2;
+    double c22 = 0;
+    int rc = setup_constants(ctx, P2, inv_sig2, lphi1, &c22);
+    if (rc) {
+        cudaFree(d);
+        ctx->mix = old_mix;
+        ctx->n1 = old_n1;
+        ctx->n2 = old_n2;
+        return rc;
+    }
+    if (old) cudaFree(old);
+    ctx->d_mix = d;
+    ctx->c22 = c22;
+    ctx->h_mu1.assign(mu1, mu1 + 3 * (size_t)n1);
+    ctx->h_sigma1.assign(sigma1, sigma1 + n1);
+    ctx->h_phi1.assign(phi1, phi1 + n1);
+    ctx->h_mu2.assign(mu2, mu2 + 3 * (size_t)n2);
+    ctx->h_kappa2.assign(kappa2, kappa2 + n2);
+    ctx->h_phi2.assign(phi2, phi2 + n2);
+    ctx->have_mix = true;
+    return GOSMA_OK;
+}
+
+int gosma_set_domain(gosma_ctx *ctx, const double t_lo[3], const double t_hi[3], double zeta) {
+    if (!ctx) return GOSMA_EINVAL;
+    ctx->err.clear();
+    if (!t_lo || !t_hi || !(zeta >= 0) || !isfinite(zeta)) return fail(ctx, GOSMA_EINVAL, "set_domain: bad arguments");
+    for (int k = 0; k < 3; ++k)
+        if (!(t_lo[k] < t_hi[k]) || !isfinite(t_lo[k]) || !isfinite(t_hi[k]))
+            return fail(ctx, GOSMA_EINVAL, "set_domain: need t_lo < t_hi");
+    for (int k = 0; k < 3; ++k) {
+        ctx->t_lo[k] = t_lo[k];
+        ctx->t_hi[k] = t_hi[k];
+    }
+    ctx->zeta = zeta;
+    ctx->mix.zeta = zeta;
+    ctx->have_dom = true;
+    return GOSMA_OK;
+}
+
+static int eval_common(gosma_ctx *ctx, const gosma_cube *cubes, int n, gosma_bound *detail, double *lb, double *ub,
+                       int on_device) {
+    if (!ctx) return GOSMA_EINVAL;
+    ctx->err.clear();
+    if (!ctx->have_mix || !ctx->have_dom) return fail(ctx, GOSMA_ENOTREADY, "eval_bounds: set mixtures and domain first");
+    if (n < 0 || (n > 0 && !cubes)) return fail(ctx, GOSMA_EINVAL, "eval_bounds: bad cube array");
+    if (n == 0) return GOSMA_OK;
+    cudaSetDevice(ctx->device);
+    size_t bc = sizeof(gosma_cube) * (size_t)n, bo = sizeof(gosma_bound) * (size_t)n;
+    cudaError_t e;
+    int rc;
+    if (on_device) {
+        gosma_bound *dout = detail;
+        if (!dout) {
+            rc = ensure_stage(ctx, bo);
+            if (rc) return rc;
+            dout = (gosma_bound *)ctx->d_stage;
+        }
+        rc = launch_bounds(ctx, cubes, n, dout);
+        if (rc) return rc;
+        if (!detail) {
+            split_bounds<<<(n + 255) / 256, 256, 0, ctx->stream>>>(dout, n, lb, ub);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "launch(split)");
+        }
+        return GOSMA_OK;
+    }
+    rc = ensure_stage(ctx, bc + bo);
+    if (rc) return rc;
+    rc = ensure_pinned(ctx, bc > bo ? bc : bo);
+    if (rc) return rc;
+    gosma_cube *dc = (gosma_cube *)ctx->d_stage;
+    gosma_bound *dout = (gosma_bound *)((char *)ctx->d_stage + bc);
+    memcpy(ctx->h_pinned, cubes, bc);
+    e = cudaMemcpyAsync(dc, ctx->h_pinned, bc, cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "copy cubes");
+    rc = launch_bounds(ctx, dc, n, dout);
+    if (rc) return rc;
+    e = cudaMemcpyAsync(ctx->h_pinned, dout, bo, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "copy bounds");
+    e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "sync(bounds)");
+    const gosma_bound *hb = (const gosma_bound *)ctx->h_pinned;
+    if (detail) memcpy(detail, hb, bo);
+    for (int k = 0; k < n; ++k) {
+        if (lb) lb[k] = hb[k].lb;
+        if (ub) ub[k] = hb[k].ub;
+    }
+    return GOSMA_OK;
+}
+
+int gosma_eval_bounds(gosma_ctx *ctx, const gosma_cube *cubes, int n, double *lb, double *ub, int on_device) {
+    return eval_common(ctx, cubes, n, nullptr, lb, ub, on_device);
+}
+
+int gosma_eval_bounds_detail(gosma_ctx *ctx, const gosma_cube *cubes, int n, gosma_bound *out, int on_device) {
+    if (!out && n > 0) return fail(ctx, GOSMA_EINVAL, "eval_bounds_detail: null output");
+    return eval_common(ctx, cubes, n, out, nullptr, nullptr, on_device);
+}
+
+int gosma_eval_objective_grad(gosma_ctx *ctx, int count, const double *x, double *f, double *grad) {
+    if (!ctx) return GOSMA_EINVAL;
+    ctx->err.clear();
+    if (!ctx->have_mix) return fail(ctx, GOSMA_ENOTREADY, "eval_objective: set mixtures first");
+    if (count < 0 || (count > 0 && !x)) return fail(ctx, GOSMA_EINVAL, "eval_objective: bad poses");
+    cudaSetDevice(ctx->device);
+    return objective_grad_device(ctx, count, x, f, grad);
+}
+
+int gosma_eval_objective(gosma_ctx *ctx, const double r[3], const double t[3], double *f) {
+    if (!r || !t || !f) return fail(ctx, GOSMA_EINVAL, "eval_objective: null pointer");
+    double x[6] = {r[0], r[1], r[2], t[0], t[1], t[2]};
+    return gosma_eval_objective_grad(ctx, 1, x, f, nullptr);
+}
+
+int gosma_selftest_approx(gosma_ctx *ctx, double measured[5], double assumed[5]) {
+    if (!ctx || !measured || !assumed) return GOSMA_EINVAL;
+    cudaSetDevice(ctx->device);
+    return selftest_approx(ctx, measured, assumed);
+}
+
+}  // extern "C"

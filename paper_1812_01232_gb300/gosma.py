@@ -1,0 +1,224 @@
+"""Python binding of libgosma (include/gosma.h): argument marshalling only.
+
+Every step of the branch-and-bound path runs in the CUDA library; this
+module converts numpy arrays or torch tensors to pointers and sizes and
+turns error codes into exceptions.  There is no fallback: if the library
+is missing or no sm_103 device is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgosma.so")
+
+GOSMA_OK = 0
+ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "ENOTREADY"}
+STATUS = {0: "optimal", 1: "node_limit", 2: "time_limit", 3: "queue_full"}
+
+D = C.POINTER(C.c_double)
+
+
+class Cube(C.Structure):
+    _fields_ = [("r0", C.c_double * 3), ("r_hw", C.c_double), ("t0", C.c_double * 3), ("t_hw", C.c_double * 3)]
+
+
+class Bound(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("lb", "ub", "self_lb", "cross_ub", "self_c", "cross_c", "psi_r", "psi_t_max")]
+
+
+class Opts(C.Structure):
+    _fields_ = [("eps", C.c_double), ("pop", C.c_int), ("max_nodes", C.c_longlong), ("max_seconds", C.c_double),
+                ("use_sma", C.c_int), ("sma_max_iter", C.c_int), ("queue_capacity", C.c_longlong)]
+
+
+class Result(C.Structure):
+    _fields_ = [("R", C.c_double * 9), ("r", C.c_double * 3), ("t", C.c_double * 3), ("objective", C.c_double),
+                ("objective_norm", C.c_double), ("lower_bound", C.c_double), ("gap_norm", C.c_double),
+                ("c22", C.c_double), ("nodes", C.c_longlong), ("iterations", C.c_longlong),
+                ("sma_calls", C.c_longlong), ("queue_peak", C.c_longlong), ("seconds", C.c_double),
+                ("status", C.c_int)]
+
+
+# exported symbols and their signatures (restype, argtypes); the header is the authority
+SIGNATURES = {
+    "gosma_create": (C.c_int, [C.c_int, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "gosma_destroy": (None, [C.c_void_p]),
+    "gosma_last_error": (C.c_char_p, [C.c_void_p]),
+    "gosma_set_mixtures": (C.c_int, [C.c_void_p, C.c_int, D, D, D, C.c_int, D, D, D]),
+    "gosma_set_domain": (C.c_int, [C.c_void_p, D, D, C.c_double]),
+    "gosma_eval_bounds": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int]),
+    "gosma_eval_bounds_detail": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int]),
+    "gosma_eval_objective": (C.c_int, [C.c_void_p, D, D, D]),
+    "gosma_eval_objective_grad": (C.c_int, [C.c_void_p, C.c_int, D, D, D]),
+    "gosma_bnb_solve": (C.c_int, [C.c_void_p, C.POINTER(Opts), C.POINTER(Result)]),
+    "gosma_selftest_approx": (C.c_int, [C.c_void_p, D, D]),
+}
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libgosma.so and declare its signatures.  Raises if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError("libgosma.so is not built (run __graft_entry__.build()); there is no fallback path")
+        L = C.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class GosmaError(RuntimeError):
+    pass
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    return a.reshape(shape) if shape is not None else a
+
+
+def _p(a):
+    return a.ctypes.data_as(D)
+
+
+def _is_torch_cuda(x):
+    return type(x).__module__.startswith("torch") and getattr(x, "is_cuda", False)
+
+
+class Gosma:
+    """One libgosma context on one CUDA device and stream."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self.L = load_library()
+        if stream is None:
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    stream = torch.cuda.current_stream(device).cuda_stream
+            except Exception:
+                stream = None
+        elif hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        self._stream = stream or 0
+        h = C.c_void_p()
+        rc = self.L.gosma_create(int(device), C.c_void_p(self._stream), C.byref(h))
+        if rc != GOSMA_OK:
+            raise GosmaError("gosma_create failed (%s): no usable sm_103 device" % ERRORS.get(rc, rc))
+        self.h = h
+        self.device = device
+        self.n1 = self.n2 = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.gosma_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc, what):
+        if rc != GOSMA_OK:
+            msg = self.L.gosma_last_error(self.h)
+            raise GosmaError("%s failed (%s): %s" % (what, ERRORS.get(rc, rc), msg.decode() if msg else ""))
+
+    # ---------------------------------------------------------------- set-up
+    def set_mixtures(self, mu1, sigma1, phi1, mu2, kappa2, phi2):
+        mu1, sigma1, phi1 = _f64(mu1, (-1, 3)), _f64(sigma1, (-1,)), _f64(phi1, (-1,))
+        mu2, kappa2, phi2 = _f64(mu2, (-1, 3)), _f64(kappa2, (-1,)), _f64(phi2, (-1,))
+        self._check(self.L.gosma_set_mixtures(self.h, len(sigma1), _p(mu1), _p(sigma1), _p(phi1), len(kappa2),
+                                              _p(mu2), _p(kappa2), _p(phi2)), "set_mixtures")
+        self.n1, self.n2 = len(sigma1), len(kappa2)
+
+    def set_domain(self, t_lo, t_hi, zeta):
+        lo, hi = _f64(t_lo, (3,)), _f64(t_hi, (3,))
+        self._check(self.L.gosma_set_domain(self.h, _p(lo), _p(hi), float(zeta)), "set_domain")
+
+    def set_problem(self, prob):
+        self.set_mixtures(prob["mu1"], prob["sigma1"], prob["phi1"], prob["mu2"], prob["kappa2"], prob["phi2"])
+        self.set_domain(prob["t_lo"], prob["t_hi"], prob["zeta"])
+
+    # ---------------------------------------------------------------- bounds
+    def eval_bounds(self, cubes, lb=None, ub=None):
+        """Theorem 1 bounds.  cubes: (n, 10) float64 numpy array (host path) or
+        a CUDA torch tensor (device path, asynchronous on the context stream)."""
+        if _is_torch_cuda(cubes):
+            import torch
+            n = cubes.shape[0]
+            assert cubes.dtype == torch.float64 and cubes.is_contiguous() and cubes.shape[1] == 10
+            if lb is None:
+                lb = torch.empty(n, dtype=torch.float64, device=cubes.device)
+            if ub is None:
+                ub = torch.empty(n, dtype=torch.float64, device=cubes.device)
+            self._check(self.L.gosma_eval_bounds(self.h, C.c_void_p(cubes.data_ptr()), n, C.c_void_p(lb.data_ptr()),
+                                                 C.c_void_p(ub.data_ptr()), 1), "eval_bounds")
+            return lb, ub
+        cubes = _f64(cubes, (-1, 10))
+        n = cubes.shape[0]
+        lb = np.empty(n)
+        ub = np.empty(n)
+        self._check(self.L.gosma_eval_bounds(self.h, cubes.ctypes.data, n, lb.ctypes.data, ub.ctypes.data, 0),
+                    "eval_bounds")
+        return lb, ub
+
+    def eval_bounds_detail(self, cubes, out=None):
+        """Full per-cube records, (n, 8): lb, ub, self_lb, cross_ub, self_c, cross_c, psi_r, psi_t_max."""
+        if _is_torch_cuda(cubes):
+            import torch
+            n = cubes.shape[0]
+            if out is None:
+                out = torch.empty((n, 8), dtype=torch.float64, device=cubes.device)
+            self._check(self.L.gosma_eval_bounds_detail(self.h, C.c_void_p(cubes.data_ptr()), n,
+                                                        C.c_void_p(out.data_ptr()), 1), "eval_bounds_detail")
+            return out
+        cubes = _f64(cubes, (-1, 10))
+        n = cubes.shape[0]
+        out = np.empty((n, 8))
+        self._check(self.L.gosma_eval_bounds_detail(self.h, cubes.ctypes.data, n, out.ctypes.data, 0),
+                    "eval_bounds_detail")
+        return out
+
+    # ---------------------------------------------------------------- objective
+    def eval_objective(self, r, t):
+        r, t = _f64(r, (3,)), _f64(t, (3,))
+        f = C.c_double()
+        self._check(self.L.gosma_eval_objective(self.h, _p(r), _p(t), C.byref(f)), "eval_objective")
+        return f.value
+
+    def eval_objective_grad(self, x):
+        x = _f64(x, (-1, 6))
+        n = x.shape[0]
+        f = np.empty(n)
+        g = np.empty((n, 6))
+        self._check(self.L.gosma_eval_objective_grad(self.h, n, _p(x), _p(f), _p(g)), "eval_objective_grad")
+        return f, g
+
+    # ---------------------------------------------------------------- branch-and-bound
+    def bnb_solve(self, eps=0.1, pop=1024, max_nodes=0, max_seconds=0.0, use_sma=True, sma_max_iter=100,
+                  queue_capacity=0):
+        o = Opts(float(eps), int(pop), int(max_nodes), float(max_seconds), int(bool(use_sma)), int(sma_max_iter),
+                 int(queue_capacity))
+        r = Result()
+        self._check(self.L.gosma_bnb_solve(self.h, C.byref(o), C.byref(r)), "bnb_solve")
+        return {
+            "f": r.objective, "f_norm": r.objective_norm, "lb": r.lower_bound, "gap_norm": r.gap_norm,
+            "c22": r.c22, "R": np.array(r.R[:]).reshape(3, 3), "r": np.array(r.r[:]), "t": np.array(r.t[:]),
+            "nodes": r.nodes, "iterations": r.iterations, "sma_calls": r.sma_calls, "queue_peak": r.queue_peak,
+            "seconds": r.seconds, "status": r.status, "status_name": STATUS.get(r.status, str(r.status)),
+        }
+
+    def selftest_approx(self):
+        m = np.zeros(5)
+        a = np.zeros(5)
+        self._check(self.L.gosma_selftest_approx(self.h, _p(m), _p(a)), "selftest_approx")
+        return m, a

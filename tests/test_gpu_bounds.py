@@ -1,0 +1,158 @@
+"""GPU parity of the bound kernel (Theorem 1) against the FP64 oracle.
+
+Tolerances (written here, derived from the FP32 error model):
+* lower bound: never above the oracle's (up to 1e-13 of the term scale, the
+  oracle's own FP64 summation) and within 1e-5 of the term scale
+  S = self_lb + 2 cross_ub;
+* upper bound (f at the centre): within 1e-5 of S_c = self_c + 2 cross_c;
+* feasibility decisions: identical.
+"""
+import numpy as np
+import pytest
+
+from paper_1812_01232_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+LB_TOL = 1e-5
+UB_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1812_01232_gb300 import build
+    build.build()
+    from paper_1812_01232_gb300.gosma import Gosma
+    c = Gosma(0)
+    yield c
+    c.close()
+
+
+def compare(got, ref, tag=""):
+    fin = np.isfinite(ref[:, 0])
+    assert np.array_equal(fin, np.isfinite(got[:, 0])), tag + " feasibility"
+    cf = np.isfinite(ref[:, 1])
+    assert np.array_equal(cf, np.isfinite(got[:, 1])), tag + " centre feasibility"
+    S = ref[fin, 2] + 2 * ref[fin, 3]
+    d = got[fin, 0] - ref[fin, 0]
+    assert np.all(d <= 1e-13 * S), tag + " lb above oracle by %g" % (d / S).max()
+    lb_err = np.abs(d) / S
+    assert lb_err.max() <= LB_TOL, tag + " lb rel err %g" % lb_err.max()
+    Sc = ref[cf, 4] + 2 * ref[cf, 5]
+    ub_err = np.abs(got[cf, 1] - ref[cf, 1]) / Sc
+    if cf.any():
+        assert ub_err.max() <= UB_TOL, tag + " ub rel err %g" % ub_err.max()
+    assert np.allclose(got[:, 6], ref[:, 6], rtol=1e-6)
+    # psi_t as used (after the pi/2 reading) agrees to FP32 accuracy
+    assert np.allclose(got[:, 7], ref[:, 7], rtol=2e-3, atol=2e-5)
+    return lb_err.max() if fin.any() else 0.0, ub_err.max() if cf.any() else 0.0
+
+
+def test_approx_instruction_accuracy(ctx):
+    measured, assumed = ctx.selftest_approx()
+    assert np.all(measured <= assumed), (measured, assumed)
+
+
+@pytest.mark.parametrize("seed", [1000, 1001, 1002])
+def test_tiny_parity(ctx, oracle_mod, seed):
+    prob = synth.tiny_problem(seed)
+    ctx.set_problem(prob)
+    cubes = synth.tree_cubes(seed + 1, 1024, prob["t_lo"], prob["t_hi"], 0, 16, near=(prob["r_gt"], prob["t_gt"]),
+                             near_frac=0.5)
+    got = ctx.eval_bounds_detail(cubes)
+    ref = oracle_mod.bounds(oracle_mod.Mixtures.from_problem(prob), cubes, prob["zeta"])
+    compare(got, ref, "tiny")
+
+
+def test_host_and_device_paths_agree(ctx):
+    import torch
+    prob = synth.tiny_problem(7)
+    ctx.set_problem(prob)
+    cubes = synth.tree_cubes(8, 333, prob["t_lo"], prob["t_hi"], 1, 12)
+    lb_h, ub_h = ctx.eval_bounds(cubes)
+    dc = torch.tensor(cubes, device="cuda")
+    lb_d, ub_d = ctx.eval_bounds(dc)
+    torch.cuda.synchronize()
+    assert np.array_equal(lb_h, lb_d.cpu().numpy(), equal_nan=True)
+    assert np.array_equal(ub_h, ub_d.cpu().numpy(), equal_nan=True)
+    det = ctx.eval_bounds_detail(cubes)
+    assert np.array_equal(det[:, 0], lb_h) and np.array_equal(det[:, 1], ub_h)
+
+
+@pytest.mark.parametrize("n1,n2", [(1, 1), (2, 3), (33, 17), (65, 129), (100, 7), (257, 40)])
+def test_ragged_sizes(ctx, oracle_mod, n1, n2):
+    rng = np.random.default_rng(n1 * 1000 + n2)
+    n_in = min(n1, max(1, n2 - 1))
+    prob = synth.tiny_problem(int(rng.integers(1 << 30)), n1=n1, n_in=n_in, n_out=n2 - n_in)
+    ctx.set_problem(prob)
+    cubes = synth.tree_cubes(int(rng.integers(1 << 30)), 97, prob["t_lo"], prob["t_hi"], 1, 14,
+                             near=(prob["r_gt"], prob["t_gt"]), near_frac=0.5)
+    got = ctx.eval_bounds_detail(cubes)
+    ref = oracle_mod.bounds(oracle_mod.Mixtures.from_problem(prob), cubes, prob["zeta"])
+    compare(got, ref, "%dx%d" % (n1, n2))
+
+
+def test_edge_cases(ctx, oracle_mod):
+    prob = synth.tiny_problem(11)
+    ctx.set_problem(prob)
+    lb, ub = ctx.eval_bounds(np.zeros((0, 10)))
+    assert lb.shape == (0,)
+    mu = prob["mu1"][0]
+    cubes = np.array([
+        np.concatenate([[0, 0, 0, 0.1], mu, [0.05, 0.05, 0.05]]),         # cuboid inside a zeta-ball
+        np.concatenate([[3.0, 3.0, 3.0, 0.2], [0, 0, 0], [0.1] * 3]),      # rotation outside the pi-ball
+        np.concatenate([[0, 0, 0, np.pi], [0, 0, 0], [1, 1, 1]]),          # the root
+        np.concatenate([prob["r_gt"], [1e-7], prob["t_gt"], [1e-7] * 3]),  # a tiny cube at the optimum
+        np.concatenate([[0.1, 0.2, 0.3, 0.05], mu + 0.3, [0.4] * 3]),      # centre infeasible, cube feasible
+    ])
+    got = ctx.eval_bounds_detail(cubes)
+    ref = oracle_mod.bounds(oracle_mod.Mixtures.from_problem(prob), cubes, prob["zeta"])
+    compare(got, ref, "edge")
+    assert np.isinf(got[0, 0]) and np.isinf(got[1, 0])
+    assert np.isfinite(got[3, 0]) and got[3, 1] - got[3, 0] < 1e-4 * (got[3, 2] + 2 * got[3, 3])
+
+
+def test_invalid_mixtures_rejected(ctx):
+    from paper_1812_01232_gb300.gosma import GosmaError
+    prob = synth.tiny_problem(12)
+    bad = dict(prob)
+    bad["phi1"] = prob["phi1"] * 2
+    with pytest.raises(GosmaError):
+        ctx.set_problem(bad)
+    bad = dict(prob)
+    bad["sigma1"] = -prob["sigma1"]
+    with pytest.raises(GosmaError):
+        ctx.set_problem(bad)
+    bad = dict(prob)
+    bad["mu2"] = prob["mu2"] * 1.01
+    with pytest.raises(GosmaError):
+        ctx.set_problem(bad)
+
+
+def test_objective_and_gradient_fp64(ctx, oracle_mod):
+    prob = synth.paper_scale_problem(2000)
+    ctx.set_problem(prob)
+    mix = oracle_mod.Mixtures.from_problem(prob)
+    rng = np.random.default_rng(3)
+    X = np.concatenate([prob["r_gt"] + rng.normal(0, 0.05, (8, 3)), prob["t_gt"] + rng.normal(0, 0.05, (8, 3))], 1)
+    f, g = ctx.eval_objective_grad(X)
+    for k in range(8):
+        fr, gr = oracle_mod.objective_grad(mix, X[k])
+        assert f[k] == pytest.approx(fr, rel=1e-11, abs=1e-12)
+        assert np.allclose(g[k], gr, rtol=1e-9, atol=1e-9 * np.abs(gr).max())
+
+
+def test_paper_scale_parity_full_batch(ctx, oracle_mod):
+    """128 x 64 components, the full 65,536-cube batch in the benchmark's
+    launch configuration; the oracle checks a sample of the cubes."""
+    prob = synth.paper_scale_problem(2000)
+    ctx.set_problem(prob)
+    cubes = synth.tree_cubes(2001, 65536, prob["t_lo"], prob["t_hi"], 2, 12, near=(prob["r_gt"], prob["t_gt"]),
+                             near_frac=0.3)
+    got = ctx.eval_bounds_detail(cubes)
+    idx = np.random.default_rng(5).choice(len(cubes), 96, replace=False)
+    ref = oracle_mod.bounds(oracle_mod.Mixtures.from_problem(prob), cubes[idx], prob["zeta"])
+    compare(got[idx], ref, "paper-scale")
+    # every cube: lb <= ub where both finite, and ub equals the FP64 objective at the centre for a few
+    both = np.isfinite(got[:, 0]) & np.isfinite(got[:, 1])
+    assert np.all(got[both, 0] <= got[both, 1])
