@@ -40,7 +40,7 @@ int ensure_pinned(gosma_ctx *ctx, size_t bytes) {
     return GOSMA_OK;
 }
 
-int setup_constants(gosma_ctx *ctx, float *P2, float *inv_sig2, float *lphi1, double *c22_out);
+int setup_constants(gosma_ctx *ctx, float *Q2, float *inv_sig2, float *phi1f, double *c22_out);
 int selftest_approx(gosma_ctx *ctx, double measured[5], double assumed[5]);
 
 __global__ void split_bounds(const gosma_bound *__restrict__ in, int n, double *lb, double *ub) {
@@ -95,7 +95,7 @@ int gosma_set_mixtures(gosma_ctx *ctx, int n1, const double *mu1, const double *
     if (n1 < 1 || n2 < 1 || !mu1 || !sigma1 || !phi1 || !mu2 || !kappa2 || !phi2)
         return fail(ctx, GOSMA_EINVAL, "set_mixtures: empty mixture or null pointer");
     if (bounds_smem_bytes(n1, n2) > 200 * 1024)
-        return fail(ctx, GOSMA_EINVAL, "set_mixtures: 11*n1 + 5*n2 floats exceed the 200 KB shared-memory budget");
+        return fail(ctx, GOSMA_EINVAL, "set_mixtures: 13*n1 + 8*n2 floats exceed the 200 KB shared-memory budget");
     double s1 = 0, s2 = 0;
     for (int i = 0; i < n1; ++i) {
         if (!(sigma1[i] > 0) || !(phi1[i] >= 0) || !isfinite(mu1[3 * i]) || !isfinite(mu1[3 * i + 1]) ||
@@ -122,7 +122,7 @@ int gosma_set_mixtures(gosma_ctx *ctx, int n1, const double *mu1, const double *
     double *dmu1 = pd, *dsig = pd + 3 * n1, *dphi1 = dsig + n1, *dmu2 = dphi1 + n1, *dk2 = dmu2 + 3 * n2,
            *dphi2 = dk2 + n2;
     float *pf = (float *)(dphi2 + n2);
-    float *inv_sig2 = pf, *lphi1 = pf + n1, *k2f = lphi1 + n1, *P2 = k2f + n2;
+    float *inv_sig2 = pf, *phi1f = pf + n1, *k2f = phi1f + n1, *Q2 = k2f + n2;
     std::vector<float> hk2(n2);
     for (int j = 0; j < n2; ++j) hk2[j] = (float)kappa2[j];
     struct {
@@ -144,12 +144,12 @@ int gosma_set_mixtures(gosma_ctx *ctx, int n1, const double *mu1, const double *
     mx.n2 = n2;
     mx.mu1 = dmu1;
     mx.inv_sig2 = inv_sig2;
-    mx.lphi1 = lphi1;
+    mx.phi1f = phi1f;
     mx.sigma1d = dsig;
     mx.phi1d = dphi1;
     mx.mu2 = dmu2;
     mx.kappa2 = k2f;
-    mx.P2 = P2;
+    mx.Q2 = Q2;
     mx.kappa2d = dk2;
     mx.phi2d = dphi2;
     mx.zeta = ctx->zeta;
@@ -160,7 +160,7 @@ int gosma_set_mixtures(gosma_ctx *ctx, int n1, const double *mu1, const double *
     ctx->n1 = n1;
     ctx->n2 = n2;
     double c22 = 0;
-    int rc = setup_constants(ctx, P2, inv_sig2, lphi1, &c22);
+    int rc = setup_constants(ctx, Q2, inv_sig2, phi1f, &c22);
     if (rc) {
         cudaFree(d);
         ctx->mix = old_mix;

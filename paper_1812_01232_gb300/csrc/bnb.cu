@@ -1,9 +1,930 @@
-// placeholder, replaced below
-#include "gosma_internal.cuh"
+// GOSMA branch-and-bound (Algorithm 1) with the queue in device memory.
+//
+// Queue: an array of 64-byte nodes (integer cell coordinates of the
+// rotation cube and the translation cuboid, the node's lower bound and the
+// cached self-term sums of its cuboid) plus one 32-bit orderable key per
+// node (the lower bound rounded down to FP32).  Removed nodes get the key
+// DEAD and stay until a compaction.
+//
+// One iteration, all on the context's stream:
+//   1. select   three histogram passes over the keys find the P-th smallest
+//               key T; nodes with key < T and the first (in index order)
+//               nodes with key == T are the popped set (deterministic);
+//   2. extract  per-block counts, one scan, one scatter: popped nodes are
+//               copied to the parent buffer and their keys set to DEAD;
+//   3. bound    every parent gives eight children (rotation or translation
+//               split, whichever has the larger uncertainty angle); each
+//               child is bounded by the per-cube core; a child of a
+//               rotation split reuses its parent's self sums;
+//   4. append   children with lb < d* go to the queue tail (block scan, in
+//               child order); the smallest child upper bound and its child
+//               are recorded;
+//   5. min      the smallest live key, the global lower bound of the next
+//               iteration.
+// The host reads a 64-byte status per iteration, refines the incumbent in
+// FP64 (exact objective at the centre, then SMA) when a child's upper bound
+// beats d*, and stops when d* - lower bound <= eps * C22.
+#include <math.h>
+#include <stddef.h>
+#include <string.h>
+
+#include <chrono>
+#include <vector>
+
+#include "bounds_core.cuh"
+
 namespace gosma {
-void bnb_release(gosma_ctx *ctx) { (void)ctx; }
+
+struct Node {
+    double lb;
+    double self_lb, self_c;  // self sums of the translation cuboid (valid when flags & 1)
+    uint32_t r[3], t[3];     // cell coordinates at levels lr, lt
+    uint16_t lr, lt;
+    float psit;              // max_i psi_t over the cuboid
+    uint32_t flags;
+    uint32_t pad;
+};
+static_assert(sizeof(Node) == 64, "node layout");
+
+struct Domain {
+    double t_lo[3], t_hi[3];
+};
+
+constexpr uint32_t DEAD = 0xFFFFFFFFu;
+constexpr int MAX_LEVEL = 30;
+constexpr int SEL_BLOCK = 256;
+constexpr int SEL_ITEMS = 8;  // keys per thread in the scan kernels
+constexpr int SEL_TILE = SEL_BLOCK * SEL_ITEMS;
+
+struct Status {
+    unsigned long long tail;      // slots used in the queue
+    unsigned long long new_tail;
+    unsigned long long appended;  // children that survived this iteration
+    unsigned long long best_key;  // order of the smallest child upper bound below d*
+    unsigned int best_child_u;    // smallest child index attaining it
+    unsigned int minkey;          // smallest live key (orderable)
+    int best_child;               // child with the smallest upper bound (-1: none)
+    int pad;
+    double best_ub;
+    Node best_node;
+    // selection results
+    unsigned int sel_bin[3];
+    unsigned int sel_need[3];
+};
+
+__host__ __device__ inline uint32_t order_key(float f) {
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
-extern "C" int gosma_bnb_solve(gosma_ctx *ctx, const gosma_opts *opts, gosma_result *out) {
-    (void)opts; (void)out;
-    return gosma::fail(ctx, GOSMA_ENOTREADY, "not built");
+__host__ __device__ inline float key_value(uint32_t k) {
+    uint32_t u = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
+}
+
+__host__ __device__ inline double psi_r_level(int lr) {
+    double p = sqrt(3.0) * ldexp(M_PI, -lr);
+    return p < M_PI ? p : M_PI;
+}
+
+__host__ __device__ inline void decode(const Node &n, const Domain &d, CubeGeom &g) {
+    double rh = ldexp(M_PI, -(int)n.lr);
+    g.rhw = rh;
+    for (int k = 0; k < 3; ++k) {
+        g.r0[k] = -M_PI + (2.0 * n.r[k] + 1.0) * rh;
+        double th = ldexp(d.t_hi[k] - d.t_lo[k], -(int)n.lt - 1);
+        g.thw[k] = th;
+        g.t0[k] = d.t_lo[k] + (2.0 * n.t[k] + 1.0) * th;
+    }
+}
+
+// Child k of a parent (Sec. 4.1: the split halves the rotation cube or the
+// translation cuboid, whichever has the greater angular uncertainty).
+__host__ __device__ inline bool split_rotation(const Node &p) {
+    if (p.lr >= MAX_LEVEL) return false;
+    if (p.lt >= MAX_LEVEL) return true;
+    return psi_r_level(p.lr) >= (double)p.psit;
+}
+
+__host__ __device__ inline Node child_of(const Node &p, int k, bool rot) {
+    Node c = p;
+    if (rot) {
+        c.lr = p.lr + 1;
+        for (int a = 0; a < 3; ++a) c.r[a] = 2u * p.r[a] + ((k >> a) & 1u);
+    } else {
+        c.lt = p.lt + 1;
+        for (int a = 0; a < 3; ++a) c.t[a] = 2u * p.t[a] + ((k >> a) & 1u);
+        c.flags &= ~1u;  // the cuboid changed: self sums must be recomputed
+    }
+    return c;
+}
+
+// ---------------------------------------------------------------- 1. select
+__global__ void sel_hist(const uint32_t *__restrict__ keys, unsigned long long n, int pass, const Status *st,
+                         unsigned int *__restrict__ hist) {
+    __shared__ unsigned int h[2048];
+    for (int b = threadIdx.x; b < 2048; b += blockDim.x) h[b] = 0;
+    __syncthreads();
+    uint32_t b1 = pass >= 1 ? st->sel_bin[0] : 0, b2 = pass >= 2 ? st->sel_bin[1] : 0;
+    uint32_t pre = (b1 << 11) | b2;
+    for (unsigned long long q = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+         q += (unsigned long long)gridDim.x * blockDim.x) {
+        uint32_t k = keys[q];
+        if (k == DEAD) continue;
+        if (pass == 0) atomicAdd(&h[k >> 21], 1u);
+        else if (pass == 1) {
+            if ((k >> 21) == b1) atomicAdd(&h[(k >> 10) & 0x7ffu], 1u);
+        } else if ((k >> 10) == pre) atomicAdd(&h[k & 0x3ffu], 1u);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < 2048; b += blockDim.x)
+        if (h[b]) atomicAdd(&hist[b], h[b]);
+}
+
+// Find the bin holding the need-th smallest key (1-based) of this pass.
+__global__ void sel_find(unsigned int *__restrict__ hist, int pass, Status *st, unsigned int need0) {
+    __shared__ unsigned int part[1024];
+    const int t = threadIdx.x;  // 1024 threads, 2 bins each
+    unsigned int need = pass == 0 ? need0 : st->sel_need[pass - 1];
+    unsigned int a = hist[2 * t], b = hist[2 * t + 1];
+    part[t] = a + b;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        unsigned int v = t >= o ? part[t - o] : 0u;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    unsigned int before = t ? part[t - 1] : 0u;
+    if (before < need && need <= before + a) {
+        st->sel_bin[pass] = 2 * t;
+        st->sel_need[pass] = need - before;
+    } else if (before + a < need && need <= before + a + b) {
+        st->sel_bin[pass] = 2 * t + 1;
+        st->sel_need[pass] = need - before - a;
+    }
+    __syncthreads();
+    hist[2 * t] = 0;  // ready for the next pass
+    hist[2 * t + 1] = 0;
+}
+
+// ---------------------------------------------------------------- 2. extract
+__device__ inline uint32_t sel_threshold(const Status *st) {
+    return (st->sel_bin[0] << 21) | (st->sel_bin[1] << 10) | st->sel_bin[2];
+}
+
+// Block-wide exclusive scan of one int per thread (SEL_BLOCK threads).
+__device__ inline int block_excl_scan(int v, int *sh, int &total) {
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int s = lane < SEL_BLOCK / 32 ? sh[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < SEL_BLOCK / 32) sh[lane] = s;
+    }
+    __syncthreads();
+    int base = w ? sh[w - 1] : 0;
+    total = sh[SEL_BLOCK / 32 - 1];
+    __syncthreads();
+    return base + x - v;
+}
+
+// Per tile: number of keys below T and equal to T.
+__global__ void ext_count(const uint32_t *__restrict__ keys, unsigned long long n, const Status *st,
+                          int2 *__restrict__ cnt) {
+    __shared__ int sh[32];
+    uint32_t T = sel_threshold(st);
+    unsigned long long base = (unsigned long long)blockIdx.x * SEL_TILE + threadIdx.x * SEL_ITEMS;
+    int lt = 0, eq = 0;
+    for (int k = 0; k < SEL_ITEMS; ++k) {
+        unsigned long long q = base + k;
+        if (q < n) {
+            uint32_t key = keys[q];
+            lt += key != DEAD && key < T;
+            eq += key != DEAD && key == T;
+        }
+    }
+    int tot_lt, tot_eq;
+    block_excl_scan(lt, sh, tot_lt);
+    block_excl_scan(eq, sh, tot_eq);
+    if (threadIdx.x == 0) cnt[blockIdx.x] = make_int2(tot_lt, tot_eq);
+}
+
+// One block: per tile, how many of its ties are popped and where its popped
+// nodes start in the parent buffer.
+__global__ void ext_scan(const int2 *__restrict__ cnt, int ntile, const Status *st, int2 *__restrict__ off) {
+    __shared__ int sh[32];
+    __shared__ int carry_eq, carry_pop;
+    if (threadIdx.x == 0) {
+        carry_eq = 0;
+        carry_pop = 0;
+    }
+    __syncthreads();
+    const int ties = (int)st->sel_need[2];
+    for (int b0 = 0; b0 < ntile; b0 += SEL_BLOCK) {
+        int b = b0 + threadIdx.x;
+        int2 c = b < ntile ? cnt[b] : make_int2(0, 0);
+        int tot;
+        int eq_before = carry_eq + block_excl_scan(c.y, sh, tot);
+        int take = min(max(ties - eq_before, 0), c.y);
+        int pop = c.x + take;
+        int tot_pop;
+        int pop_before = carry_pop + block_excl_scan(pop, sh, tot_pop);
+        if (b < ntile) off[b] = make_int2(pop_before, take);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            carry_eq += tot;
+            carry_pop += tot_pop;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void ext_scatter(uint32_t *__restrict__ keys, const Node *__restrict__ q, unsigned long long n,
+                            const Status *st, const int2 *__restrict__ off, Node *__restrict__ parents) {
+    __shared__ int sh[32];
+    uint32_t T = sel_threshold(st);
+    unsigned long long base = (unsigned long long)blockIdx.x * SEL_TILE + threadIdx.x * SEL_ITEMS;
+    int2 o = off[blockIdx.x];
+    uint32_t kk[SEL_ITEMS];
+    int eq = 0;
+    for (int k = 0; k < SEL_ITEMS; ++k) {
+        unsigned long long qq = base + k;
+        kk[k] = qq < n ? keys[qq] : DEAD;
+        eq += kk[k] != DEAD && kk[k] == T;
+    }
+    int tot;
+    int eq_rank = block_excl_scan(eq, sh, tot);
+    int pop = 0;
+    bool popped[SEL_ITEMS];
+    for (int k = 0; k < SEL_ITEMS; ++k) {
+        bool p = false;
+        if (kk[k] != DEAD) {
+            if (kk[k] < T) p = true;
+            else if (kk[k] == T) p = eq_rank++ < o.y;
+        }
+        popped[k] = p;
+        pop += p;
+    }
+    int pos = o.x + block_excl_scan(pop, sh, tot);
+    for (int k = 0; k < SEL_ITEMS; ++k)
+        if (popped[k]) {
+            parents[pos++] = q[base + k];
+            keys[base + k] = DEAD;
+        }
+}
+
+// ---------------------------------------------------------------- 3. bound
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+    bound_children(MixDev mx, Domain dom, const Node *__restrict__ parents, int np, Node *__restrict__ kids,
+                   double *__restrict__ kid_ub) {
+    extern __shared__ float smem_f[];
+    __shared__ CubeShared cs;
+    __shared__ CubeSums sums;
+    SmemArrays sm = carve(smem_f, mx.n1, mx.n2);
+    const double inf = __longlong_as_double(0x7ff0000000000000LL);
+    for (int c = blockIdx.x; c < 8 * np; c += gridDim.x) {
+        const Node p = parents[c >> 3];
+        bool rot = split_rotation(p);
+        Node ch = child_of(p, c & 7, rot);
+        CubeGeom g;
+        decode(ch, dom, g);
+        bool need_self = !(ch.flags & 1u);
+        cube_bounds<BLOCK>(mx, g, need_self, cs, sm, sums);
+        if (threadIdx.x == 0) {
+            double sl = need_self ? sums.self_lb : p.self_lb;
+            double sc = need_self ? sums.self_c : p.self_c;
+            double lb, ub;
+            if (!sums.feasible) {
+                lb = ub = inf;
+            } else {
+                double S = sl + 2.0 * sums.cross_ub;
+                lb = sl - 2.0 * sums.cross_ub - 1e-12 * S;
+                ub = sums.centre_feasible ? sc - 2.0 * sums.cross_c : inf;
+            }
+            ch.lb = lb;
+            ch.self_lb = sl;
+            ch.self_c = sc;
+            ch.psit = sums.psi_t_max;
+            ch.flags |= 1u;
+            kids[c] = ch;
+            kid_ub[c] = ub;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- 4. append
+__device__ inline unsigned long long dbl_order(double d) {
+    unsigned long long u = (unsigned long long)__double_as_longlong(d);
+    return (u & 0x8000000000000000ULL) ? ~u : (u | 0x8000000000000000ULL);
+}
+
+// Per tile of children: how many survive (lb < d*), and the smallest upper
+// bound below d* (exact 64-bit order).
+__global__ void app_count(const Node *__restrict__ kids, const double *__restrict__ kid_ub, int nk,
+                          const double *__restrict__ dstar, int2 *__restrict__ cnt, Status *st) {
+    __shared__ int sh[32];
+    const double ds = *dstar;
+    int base = blockIdx.x * SEL_TILE + threadIdx.x * SEL_ITEMS;
+    int alive = 0;
+    unsigned long long best = ~0ULL;
+    for (int k = 0; k < SEL_ITEMS; ++k) {
+        int c = base + k;
+        if (c < nk) {
+            alive += kids[c].lb < ds;
+            double ub = kid_ub[c];
+            if (ub < ds) best = min(best, dbl_order(ub));
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_down_sync(0xffffffffu, best, o));
+    if ((threadIdx.x & 31) == 0 && best != ~0ULL) atomicMin(&st->best_key, best);
+    int tot;
+    block_excl_scan(alive, sh, tot);
+    if (threadIdx.x == 0) cnt[blockIdx.x] = make_int2(tot, 0);
+}
+
+// One block: offsets of each tile's survivors after the queue tail.
+__global__ void app_scan(const int2 *__restrict__ cnt, int ntile, int2 *__restrict__ off, Status *st,
+                         unsigned long long cap) {
+    __shared__ int sh[32];
+    __shared__ long long carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < ntile; b0 += SEL_BLOCK) {
+        int b = b0 + threadIdx.x;
+        int v = b < ntile ? cnt[b].x : 0;
+        int tot;
+        int ex = block_excl_scan(v, sh, tot);
+        if (b < ntile) off[b] = make_int2((int)(carry + ex), 0);
+        __syncthreads();
+        if (threadIdx.x == 0) carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        unsigned long long tail = st->tail;
+        unsigned long long fit = tail + carry <= cap ? carry : cap - tail;
+        st->appended = carry;
+        st->new_tail = tail + fit;
+    }
+}
+
+__global__ void app_scatter(const Node *__restrict__ kids, const double *__restrict__ kid_ub, int nk,
+                            const double *__restrict__ dstar, const int2 *__restrict__ off, Node *__restrict__ q,
+                            uint32_t *__restrict__ keys, unsigned long long cap, Status *st) {
+    __shared__ int sh[32];
+    const double ds = *dstar;
+    const unsigned long long tail = st->tail, bk = st->best_key;
+    int base = blockIdx.x * SEL_TILE + threadIdx.x * SEL_ITEMS;
+    bool alive[SEL_ITEMS];
+    int cnt = 0;
+    for (int k = 0; k < SEL_ITEMS; ++k) {
+        int c = base + k;
+        alive[k] = c < nk && kids[c].lb < ds;
+        cnt += alive[k];
+        if (c < nk && bk != ~0ULL && dbl_order(kid_ub[c]) == bk) atomicMin(&st->best_child_u, (unsigned)c);
+    }
+    int tot;
+    unsigned long long pos = tail + off[blockIdx.x].x + block_excl_scan(cnt, sh, tot);
+    for (int k = 0; k < SEL_ITEMS; ++k)
+        if (alive[k]) {
+            if (pos < cap) {
+                q[pos] = kids[base + k];
+                keys[pos] = order_key(__double2float_rd(kids[base + k].lb));
+            }
+            ++pos;
+        }
+}
+
+// Publish the iteration's results (one thread).
+__global__ void app_finish(const Node *__restrict__ kids, const double *__restrict__ kid_ub, Status *st) {
+    st->tail = st->new_tail;
+    if (st->best_key != ~0ULL) {
+        int c = (int)st->best_child_u;
+        st->best_child = c;
+        st->best_ub = kid_ub[c];
+        st->best_node = kids[c];
+    } else {
+        st->best_child = -1;
+    }
+}
+
+// ---------------------------------------------------------------- 5. min / compaction
+__global__ void min_key(const uint32_t *__restrict__ keys, unsigned long long nmax, Status *st) {
+    const unsigned long long n = st->tail < nmax ? st->tail : nmax;
+    uint32_t m = DEAD;
+    for (unsigned long long q = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; q < n;
+         q += (unsigned long long)gridDim.x * blockDim.x)
+        m = min(m, keys[q]);
+    for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_down_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMin(&st->minkey, m);
+}
+
+// Compaction: keep live nodes with lb < d*.  Count, scan and scatter reuse
+// the extract machinery with "popped" meaning "kept".
+__global__ void cmp_count(const uint32_t *__restrict__ keys, const Node *__restrict__ q, unsigned long long n,
+                          const double *__restrict__ dstar, int2 *__restrict__ cnt) {
+    __shared__ int sh[32];
+    double ds = *dstar;
+    unsigned long long base = (unsigned long long)blockIdx.x * SEL_TILE + threadIdx.x * SEL_ITEMS;
+    int keep = 0;
+    for (int k = 0; k < SEL_ITEMS; ++k) {
+        unsigned long long qq = base + k;
+        keep += qq < n && keys[qq] != DEAD && q[qq].lb < ds;
+    }
+    int tot;
+    block_excl_scan(keep, sh, tot);
+    if (threadIdx.x == 0) cnt[blockIdx.x] = make_int2(tot, 0);
+}
+
+__global__ void cmp_scan(const int2 *__restrict__ cnt, int ntile, int2 *__restrict__ off,
+                         unsigned long long *__restrict__ total) {
+    __shared__ int sh[32];
+    __shared__ unsigned long long carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < ntile; b0 += SEL_BLOCK) {
+        int b = b0 + threadIdx.x;
+        int v = b < ntile ? cnt[b].x : 0;
+        int tot;
+        int ex = block_excl_scan(v, sh, tot);
+        if (b < ntile) off[b] = make_int2((int)(carry + ex), 0);
+        __syncthreads();
+        if (threadIdx.x == 0) carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void cmp_scatter(const uint32_t *__restrict__ keys, const Node *__restrict__ q, unsigned long long n,
+                            const double *__restrict__ dstar, const int2 *__restrict__ off,
+                            uint32_t *__restrict__ keys2, Node *__restrict__ q2) {
+    __shared__ int sh[32];
+    double ds = *dstar;
+    unsigned long long base = (unsigned long long)blockIdx.x * SEL_TILE + threadIdx.x * SEL_ITEMS;
+    bool keep[SEL_ITEMS];
+    int cnt = 0;
+    for (int k = 0; k < SEL_ITEMS; ++k) {
+        unsigned long long qq = base + k;
+        keep[k] = qq < n && keys[qq] != DEAD && q[qq].lb < ds;
+        cnt += keep[k];
+    }
+    int tot;
+    long long pos = off[blockIdx.x].x + block_excl_scan(cnt, sh, tot);
+    for (int k = 0; k < SEL_ITEMS; ++k)
+        if (keep[k]) {
+            q2[pos] = q[base + k];
+            keys2[pos] = keys[base + k];
+            ++pos;
+        }
+}
+
+// ---------------------------------------------------------------- host side
+struct BnbState {
+    unsigned long long cap = 0;
+    int pop = 0;
+    Node *q[2] = {nullptr, nullptr};
+    uint32_t *keys[2] = {nullptr, nullptr};
+    int cur = 0;
+    Node *parents = nullptr, *kids = nullptr;
+    double *kid_ub = nullptr, *dstar = nullptr;
+    unsigned int *hist = nullptr;
+    int2 *cnt = nullptr, *off = nullptr;
+    unsigned long long *total = nullptr;
+    Status *st = nullptr;
+    Status *h_st = nullptr;  // pinned
+};
+
+static void free_state(BnbState *s) {
+    if (!s) return;
+    cudaFree(s->q[0]);
+    cudaFree(s->q[1]);
+    cudaFree(s->keys[0]);
+    cudaFree(s->keys[1]);
+    cudaFree(s->parents);
+    cudaFree(s->kids);
+    cudaFree(s->kid_ub);
+    cudaFree(s->dstar);
+    cudaFree(s->hist);
+    cudaFree(s->cnt);
+    cudaFree(s->off);
+    cudaFree(s->total);
+    cudaFree(s->st);
+    if (s->h_st) cudaFreeHost(s->h_st);
+    delete s;
+}
+
+void bnb_release(gosma_ctx *ctx) {
+    free_state((BnbState *)ctx->bnb);
+    ctx->bnb = nullptr;
+}
+
+static int alloc_state(gosma_ctx *ctx, unsigned long long cap, int pop, BnbState **out) {
+    BnbState *s = (BnbState *)ctx->bnb;
+    if (s && s->cap == cap && s->pop == pop) {
+        *out = s;
+        return GOSMA_OK;
+    }
+    bnb_release(ctx);
+    s = new BnbState();
+    s->cap = cap;
+    s->pop = pop;
+    unsigned long long ntile = (cap + SEL_TILE - 1) / SEL_TILE;
+    cudaError_t e = cudaSuccess;
+#define ALLOC(ptr, bytes)                                        \
+    if (e == cudaSuccess) e = cudaMalloc((void **)&(ptr), (bytes));
+    ALLOC(s->q[0], sizeof(Node) * cap);
+    ALLOC(s->q[1], sizeof(Node) * cap);
+    ALLOC(s->keys[0], sizeof(uint32_t) * cap);
+    ALLOC(s->keys[1], sizeof(uint32_t) * cap);
+    ALLOC(s->parents, sizeof(Node) * pop);
+    ALLOC(s->kids, sizeof(Node) * 8 * pop);
+    ALLOC(s->kid_ub, sizeof(double) * 8 * pop);
+    ALLOC(s->dstar, sizeof(double));
+    ALLOC(s->hist, sizeof(unsigned int) * 2048);
+    ALLOC(s->cnt, sizeof(int2) * ntile);
+    ALLOC(s->off, sizeof(int2) * ntile);
+    ALLOC(s->total, sizeof(unsigned long long));
+    ALLOC(s->st, sizeof(Status));
+#undef ALLOC
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&s->h_st, sizeof(Status));
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->hist, 0, sizeof(unsigned int) * 2048, ctx->stream);
+    if (e != cudaSuccess) {
+        free_state(s);
+        return cuda_fail(ctx, e, "allocate branch-and-bound state");
+    }
+    ctx->bnb = s;
+    *out = s;
+    return GOSMA_OK;
+}
+
+template <int BLOCK>
+static int launch_children(gosma_ctx *ctx, const Domain &dom, BnbState *s, int np) {
+    size_t smem = bounds_smem_bytes(ctx->n1, ctx->n2);
+    auto kern = bound_children<BLOCK>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFuncSetAttribute(children)");
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BLOCK, smem);
+    if (e != cudaSuccess || per_sm < 1) return fail(ctx, GOSMA_ECUDA, "children kernel does not fit");
+    long long grid = (long long)ctx->sm_count * per_sm;
+    if (grid > 8LL * np) grid = 8LL * np;
+    kern<<<(int)grid, BLOCK, smem, ctx->stream>>>(ctx->mix, dom, s->parents, np, s->kids, s->kid_ub);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? GOSMA_OK : cuda_fail(ctx, e, "launch(children)");
+}
+
+static int launch_children_any(gosma_ctx *ctx, const Domain &dom, BnbState *s, int np) {
+    switch (bounds_block_size(ctx->n1, ctx->n2)) {
+    case 32: return launch_children<32>(ctx, dom, s, np);
+    case 64: return launch_children<64>(ctx, dom, s, np);
+    case 128: return launch_children<128>(ctx, dom, s, np);
+    default: return launch_children<256>(ctx, dom, s, np);
+    }
+}
+
+static int grid_for(unsigned long long n, int block, int sm) {
+    unsigned long long g = (n + block - 1) / block;
+    unsigned long long cap = 8ULL * sm;
+    if (g > cap) g = cap;
+    return g < 1 ? 1 : (int)g;
+}
+
+// One iteration on the device: select, extract, bound, append, min.
+static int iterate(gosma_ctx *ctx, const Domain &dom, BnbState *s, unsigned long long tail, int np) {
+    cudaStream_t st = ctx->stream;
+    uint32_t *keys = s->keys[s->cur];
+    Node *q = s->q[s->cur];
+    int ntile = (int)((tail + SEL_TILE - 1) / SEL_TILE);
+    int g = grid_for(tail, 256, ctx->sm_count);
+    for (int pass = 0; pass < 3; ++pass) {
+        sel_hist<<<g, 256, 0, st>>>(keys, tail, pass, s->st, s->hist);
+        sel_find<<<1, 1024, 0, st>>>(s->hist, pass, s->st, (unsigned)np);
+    }
+    ext_count<<<ntile, SEL_BLOCK, 0, st>>>(keys, tail, s->st, s->cnt);
+    ext_scan<<<1, SEL_BLOCK, 0, st>>>(s->cnt, ntile, s->st, s->off);
+    ext_scatter<<<ntile, SEL_BLOCK, 0, st>>>(keys, q, tail, s->st, s->off, s->parents);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "launch(select/extract)");
+    int rc = launch_children_any(ctx, dom, s, np);
+    if (rc) return rc;
+    const int nk = 8 * np, ktile = (nk + SEL_TILE - 1) / SEL_TILE;
+    // reset best_key, best_child_u and minkey (contiguous in Status)
+    e = cudaMemsetAsync(&s->st->best_key, 0xFF, offsetof(Status, best_child) - offsetof(Status, best_key), st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "memset(status)");
+    app_count<<<ktile, SEL_BLOCK, 0, st>>>(s->kids, s->kid_ub, nk, s->dstar, s->cnt, s->st);
+    app_scan<<<1, SEL_BLOCK, 0, st>>>(s->cnt, ktile, s->off, s->st, s->cap);
+    app_scatter<<<ktile, SEL_BLOCK, 0, st>>>(s->kids, s->kid_ub, nk, s->dstar, s->off, q, keys, s->cap, s->st);
+    app_finish<<<1, 1, 0, st>>>(s->kids, s->kid_ub, s->st);
+    unsigned long long ntail = tail + 8ULL * np;  // upper bound of the new tail
+    if (ntail > s->cap) ntail = s->cap;
+    min_key<<<grid_for(ntail, 256, ctx->sm_count), 256, 0, st>>>(keys, ntail, s->st);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "launch(append/min)");
+    e = cudaMemcpyAsync(s->h_st, s->st, sizeof(Status), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "sync(iteration)");
+    return GOSMA_OK;
+}
+
+// Remove dead nodes and nodes with lb >= d*; returns the new tail.
+static int compact(gosma_ctx *ctx, BnbState *s, unsigned long long tail, unsigned long long *new_tail) {
+    cudaStream_t st = ctx->stream;
+    int ntile = (int)((tail + SEL_TILE - 1) / SEL_TILE);
+    int o = s->cur, n = 1 - s->cur;
+    cmp_count<<<ntile, SEL_BLOCK, 0, st>>>(s->keys[o], s->q[o], tail, s->dstar, s->cnt);
+    cmp_scan<<<1, SEL_BLOCK, 0, st>>>(s->cnt, ntile, s->off, s->total);
+    cmp_scatter<<<ntile, SEL_BLOCK, 0, st>>>(s->keys[o], s->q[o], tail, s->dstar, s->off, s->keys[n], s->q[n]);
+    unsigned long long t = 0;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&t, s->total, sizeof t, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "compaction");
+    s->cur = n;
+    *new_tail = t;
+    return GOSMA_OK;
+}
+
+// ---------------------------------------------------------------- SMA (Sec. 5)
+// Local refinement: L-BFGS (memory 8) with a backtracking Armijo line search
+// on the FP64 objective and gradient computed on the device.  Trial poses
+// that leave the translation domain or come within zeta of a mean are
+// rejected, so the result is always a feasible pose.
+struct Refiner {
+    gosma_ctx *ctx;
+    long long evals = 0;
+    bool feasible(const double x[6]) const {
+        for (int k = 0; k < 3; ++k)
+            if (x[3 + k] < ctx->t_lo[k] || x[3 + k] > ctx->t_hi[k]) return false;
+        double z2 = ctx->zeta * ctx->zeta;
+        for (int i = 0; i < ctx->n1; ++i) {
+            double d0 = ctx->h_mu1[3 * i] - x[3], d1 = ctx->h_mu1[3 * i + 1] - x[4], d2 = ctx->h_mu1[3 * i + 2] - x[5];
+            if (d0 * d0 + d1 * d1 + d2 * d2 < z2) return false;
+        }
+        return true;
+    }
+    int fg(const double x[6], double *f, double g[6]) {
+        ++evals;
+        return objective_grad_device(ctx, 1, x, f, g);
+    }
+    // Minimise from x (in place); f holds f(x) on entry and the result on exit.
+    int run(double x[6], double *f, int max_iter) {
+        const int M = 8;
+        double S[M][6], Y[M][6], rho[M], g[6], fx;
+        int rc = fg(x, &fx, g);
+        if (rc) return rc;
+        int head = 0, used = 0;
+        for (int it = 0; it < max_iter; ++it) {
+            double gn = 0;
+            for (int k = 0; k < 6; ++k) gn = fmax(gn, fabs(g[k]));
+            if (!(gn > 1e-10)) break;
+            double d[6], al[M];
+            for (int k = 0; k < 6; ++k) d[k] = -g[k];
+            for (int h = 0; h < used; ++h) {
+                int j = (head - 1 - h + M) % M;
+                double a = 0;
+                for (int k = 0; k < 6; ++k) a += S[j][k] * d[k];
+                al[h] = rho[j] * a;
+                for (int k = 0; k < 6; ++k) d[k] -= al[h] * Y[j][k];
+            }
+            double scale = 0.01 / gn;
+            if (used) {
+                int j = (head - 1 + M) % M;
+                double sy = 0, yy = 0;
+                for (int k = 0; k < 6; ++k) {
+                    sy += S[j][k] * Y[j][k];
+                    yy += Y[j][k] * Y[j][k];
+                }
+                scale = sy / yy;
+            }
+            for (int k = 0; k < 6; ++k) d[k] *= scale;
+            for (int h = used - 1; h >= 0; --h) {
+                int j = (head - 1 - h + M) % M;
+                double b = 0;
+                for (int k = 0; k < 6; ++k) b += Y[j][k] * d[k];
+                b *= rho[j];
+                for (int k = 0; k < 6; ++k) d[k] += S[j][k] * (al[h] - b);
+            }
+            double slope = 0;
+            for (int k = 0; k < 6; ++k) slope += g[k] * d[k];
+            if (!(slope < 0)) {  // lost descent: restart from a scaled gradient step
+                used = 0;
+                for (int k = 0; k < 6; ++k) d[k] = -g[k] * (0.01 / gn);
+                slope = 0;
+                for (int k = 0; k < 6; ++k) slope += g[k] * d[k];
+            }
+            double step = 1.0, xn[6], gn6[6], fn = 0;
+            bool ok = false;
+            for (int ls = 0; ls < 40 && !ok; ++ls, step *= 0.5) {
+                for (int k = 0; k < 6; ++k) xn[k] = x[k] + step * d[k];
+                if (!feasible(xn)) continue;
+                rc = fg(xn, &fn, gn6);
+                if (rc) return rc;
+                ok = fn <= fx + 1e-4 * step * slope;
+            }
+            if (!ok) break;
+            double sy = 0;
+            for (int k = 0; k < 6; ++k) {
+                S[head][k] = xn[k] - x[k];
+                Y[head][k] = gn6[k] - g[k];
+                sy += S[head][k] * Y[head][k];
+            }
+            if (sy > 0) {
+                rho[head] = 1.0 / sy;
+                head = (head + 1) % M;
+                used = used < M ? used + 1 : M;
+            }
+            double fprev = fx;
+            memcpy(x, xn, sizeof(double) * 6);
+            memcpy(g, gn6, sizeof g);
+            fx = fn;
+            if (fabs(fprev - fx) <= 1e-15 * (1.0 + fabs(fx))) break;
+        }
+        *f = fx;
+        return GOSMA_OK;
+    }
+};
+
+static void rodrigues_host(const double r[3], double R[9]) {
+    double th2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2], th = sqrt(th2), A, B;
+    if (th < 1e-8) {
+        A = 1.0 - th2 / 6.0;
+        B = 0.5 - th2 / 24.0;
+    } else {
+        A = sin(th) / th;
+        B = (1.0 - cos(th)) / th2;
+    }
+    double x = r[0], y = r[1], z = r[2];
+    double M[9] = {1.0 - B * (y * y + z * z), -A * z + B * x * y,        A * y + B * x * z,
+                   A * z + B * x * y,         1.0 - B * (x * x + z * z), -A * x + B * y * z,
+                   -A * y + B * x * z,        A * x + B * y * z,         1.0 - B * (x * x + y * y)};
+    memcpy(R, M, sizeof M);
+}
+
+}  // namespace gosma
+
+using namespace gosma;
+
+extern "C" int gosma_bnb_solve(gosma_ctx *ctx, const gosma_opts *opts_in, gosma_result *out) {
+    if (!ctx || !out) return GOSMA_EINVAL;
+    ctx->err.clear();
+    if (!ctx->have_mix || !ctx->have_dom) return fail(ctx, GOSMA_ENOTREADY, "bnb_solve: set mixtures and domain first");
+    gosma_opts o;
+    o.eps = 0.1;
+    o.pop = 1024;
+    o.max_nodes = 0;
+    o.max_seconds = 0;
+    o.use_sma = 1;
+    o.sma_max_iter = 100;
+    o.queue_capacity = 0;
+    if (opts_in) o = *opts_in;
+    if (!(o.eps >= 0) || o.pop < 1 || o.pop > 131072) return fail(ctx, GOSMA_EINVAL, "bnb_solve: eps >= 0, 1 <= pop <= 131072");
+    if (o.sma_max_iter <= 0) o.sma_max_iter = 100;
+    unsigned long long cap = o.queue_capacity > 0 ? (unsigned long long)o.queue_capacity : (1ULL << 24);
+    if (cap < 16ULL * o.pop) cap = 16ULL * o.pop;
+    cudaSetDevice(ctx->device);
+    auto t_start = std::chrono::steady_clock::now();
+    auto seconds = [&]() {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+    };
+    BnbState *s = nullptr;
+    int rc = alloc_state(ctx, cap, o.pop, &s);
+    if (rc) return rc;
+    Domain dom;
+    for (int k = 0; k < 3; ++k) {
+        dom.t_lo[k] = ctx->t_lo[k];
+        dom.t_hi[k] = ctx->t_hi[k];
+    }
+    memset(out, 0, sizeof *out);
+    const double c22 = ctx->c22, eps_f = o.eps * c22;
+    const double inf = INFINITY;
+    double dstar = inf;
+    double best[6] = {0, 0, 0, 0.5 * (dom.t_lo[0] + dom.t_hi[0]), 0.5 * (dom.t_lo[1] + dom.t_hi[1]),
+                      0.5 * (dom.t_lo[2] + dom.t_hi[2])};
+    // root: the cube circumscribing the pi-ball times the translation cuboid
+    Node root;
+    memset(&root, 0, sizeof root);
+    root.lb = -inf;
+    root.psit = (float)M_PI;
+    s->cur = 0;
+    uint32_t rkey = order_key(-INFINITY);
+    cudaError_t e = cudaMemcpyAsync(s->q[0], &root, sizeof root, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->keys[0], &rkey, sizeof rkey, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->dstar, &dstar, sizeof dstar, cudaMemcpyHostToDevice, ctx->stream);
+    Status init;
+    memset(&init, 0, sizeof init);
+    init.tail = 1;
+    init.minkey = rkey;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->st, &init, sizeof init, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "bnb init");
+    unsigned long long tail = 1, live = 1;
+    double dlb = -inf;
+    long long nodes = 0, iters = 0, sma_calls = 0, peak = 1;
+    int status = GOSMA_OPTIMAL;
+    Refiner ref{ctx};
+    for (;;) {
+        if (live == 0) {
+            dlb = dstar;
+            break;
+        }
+        if (dstar - dlb <= eps_f) break;
+        if (o.max_nodes > 0 && nodes >= o.max_nodes) {
+            status = GOSMA_NODE_LIMIT;
+            break;
+        }
+        if (o.max_seconds > 0 && seconds() > o.max_seconds) {
+            status = GOSMA_TIME_LIMIT;
+            break;
+        }
+        int np = (int)(live < (unsigned long long)o.pop ? live : (unsigned long long)o.pop);
+        if (tail + 8ULL * np > cap || (tail > 4ULL * live && tail > (1ULL << 20))) {
+            unsigned long long nt = 0;
+            rc = compact(ctx, s, tail, &nt);
+            if (rc) return rc;
+            tail = nt;
+            live = nt;
+            e = cudaMemcpyAsync(&s->st->tail, &tail, sizeof tail, cudaMemcpyHostToDevice, ctx->stream);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "set tail");
+            if (live == 0) {
+                dlb = dstar;
+                break;
+            }
+            np = (int)(live < (unsigned long long)o.pop ? live : (unsigned long long)o.pop);
+            if (tail + 8ULL * np > cap) {
+                status = GOSMA_QUEUE_FULL;
+                break;
+            }
+        }
+        rc = iterate(ctx, dom, s, tail, np);
+        if (rc) return rc;
+        const Status &h = *s->h_st;
+        nodes += 8LL * np;
+        iters += 1;
+        tail = h.tail;
+        live = live - np + h.appended;
+        if ((long long)live > peak) peak = (long long)live;
+        if (h.best_child >= 0 && h.best_ub < dstar) {
+            CubeGeom g;
+            decode(h.best_node, dom, g);
+            double x[6] = {g.r0[0], g.r0[1], g.r0[2], g.t0[0], g.t0[1], g.t0[2]};
+            double f0 = 0;
+            double g6[6];
+            rc = ref.fg(x, &f0, g6);  // exact objective at the centre
+            if (rc) return rc;
+            double f1 = f0, x1[6];
+            memcpy(x1, x, sizeof x);
+            if (o.use_sma) {
+                rc = ref.run(x1, &f1, o.sma_max_iter);
+                if (rc) return rc;
+                ++sma_calls;
+                if (!(f1 < f0)) {
+                    f1 = f0;
+                    memcpy(x1, x, sizeof x);
+                }
+            }
+            if (f1 < dstar) {
+                dstar = f1;
+                memcpy(best, x1, sizeof best);
+                e = cudaMemcpyAsync(s->dstar, &dstar, sizeof dstar, cudaMemcpyHostToDevice, ctx->stream);
+                if (e != cudaSuccess) return cuda_fail(ctx, e, "set d*");
+            }
+        }
+        dlb = h.minkey == DEAD ? dstar : (double)key_value(h.minkey);
+        if (dlb > dstar) dlb = dstar;
+    }
+    // canonical angle-axis vector, |r| <= pi
+    double rn = sqrt(best[0] * best[0] + best[1] * best[1] + best[2] * best[2]);
+    if (rn > M_PI) {
+        double k = (rn - 2.0 * M_PI) / rn;
+        for (int a = 0; a < 3; ++a) best[a] *= k;
+    }
+    for (int k = 0; k < 3; ++k) {
+        out->r[k] = best[k];
+        out->t[k] = best[3 + k];
+    }
+    rodrigues_host(out->r, out->R);
+    out->objective = dstar;
+    out->objective_norm = dstar / c22 + 1.0;
+    out->lower_bound = dlb;
+    out->gap_norm = (dstar - dlb) / c22;
+    out->c22 = c22;
+    out->nodes = nodes;
+    out->iterations = iters;
+    out->sma_calls = sma_calls;
+    out->queue_peak = peak;
+    out->seconds = seconds();
+    out->status = status;
+    return GOSMA_OK;
 }

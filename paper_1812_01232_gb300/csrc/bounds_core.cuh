@@ -11,11 +11,11 @@
 //            arrays in shared memory (broadcast reads within a warp).
 //   phase 3  block reduction of the four FP64 sums.
 //
-// Pair terms are computed in log2 space in FP32.  The closed forms follow
-// Theorem 1 with the translation dependence of kappa bounded over [a_i, b_i]:
+// Pair terms are computed in FP32.  The closed forms follow Theorem 1 with
+// the translation dependence of kappa bounded over [a_i, b_i]:
 //   K^2 = (k1 - k2)^2 + 4 k1 k2 cos^2(B/2),
 //   K - k1 - k2 = -4 k1 k2 sin^2(B/2) / (k1 + k2 + K)     (no cancellation),
-//   log2 Z(x) = x log2 e + phiZ2(x).
+//   Z(x) = e^x g(x) / x with g(x) = 1 - e^{-2x}.
 // Every rounding that could raise a lower bound is covered: angle sines and
 // cosines are widened by an absolute error bound, kappa intervals by a
 // relative one, and the exponent of each term by a bound on its error, in
@@ -39,26 +39,37 @@ struct CubeShared {
     double red[4][32];
 };
 
+// Directions are kept as FP32 hi/lo pairs (hi + lo equals the FP64 unit
+// vector to ~2^-48), so differences of nearly parallel directions keep full
+// FP32 relative accuracy.
 struct SmemArrays {
     // model rows (n1)
-    float *vx, *vy, *vz, *a, *b, *k0, *cps, *sps, *Pself, *Ea, *Pub;
+    float *vx, *vy, *vz, *wx, *wy, *wz;  // v_i hi / lo
+    float *a, *b, *k0, *cps, *sps, *Aw, *Uw;
     // image columns (n2)
-    float *ux, *uy, *uz, *k2, *P2;
+    float *ux, *uy, *uz, *lx, *ly, *lz;  // u_j hi / lo
+    float *k2, *Q;
 };
 
+constexpr int MODEL_FLOATS = 13, IMAGE_FLOATS = 8;
+
 __host__ __device__ inline size_t bounds_smem_arrays_bytes(int n1, int n2) {
-    return (size_t)(11 * n1 + 5 * n2) * sizeof(float);
+    return (size_t)(MODEL_FLOATS * n1 + IMAGE_FLOATS * n2) * sizeof(float);
 }
 
 __device__ inline SmemArrays carve(float *base, int n1, int n2) {
     SmemArrays s;
     float *p = base;
-    s.vx = p; p += n1; s.vy = p; p += n1; s.vz = p; p += n1;
-    s.a = p; p += n1; s.b = p; p += n1; s.k0 = p; p += n1;
-    s.cps = p; p += n1; s.sps = p; p += n1;
-    s.Pself = p; p += n1; s.Ea = p; p += n1; s.Pub = p; p += n1;
-    s.ux = p; p += n2; s.uy = p; p += n2; s.uz = p; p += n2;
-    s.k2 = p; p += n2; s.P2 = p; p += n2;
+    float **m[MODEL_FLOATS] = {&s.vx, &s.vy, &s.vz, &s.wx, &s.wy, &s.wz, &s.a, &s.b, &s.k0, &s.cps, &s.sps, &s.Aw, &s.Uw};
+    for (int k = 0; k < MODEL_FLOATS; ++k) {
+        *m[k] = p;
+        p += n1;
+    }
+    float **q[IMAGE_FLOATS] = {&s.ux, &s.uy, &s.uz, &s.lx, &s.ly, &s.lz, &s.k2, &s.Q};
+    for (int k = 0; k < IMAGE_FLOATS; ++k) {
+        *q[k] = p;
+        p += n2;
+    }
     return s;
 }
 
@@ -94,114 +105,137 @@ __device__ inline void rodrigues_d(const double r[3], double R[9]) {
     R[8] = 1.0 - B * (x * x + y * y);
 }
 
-// One cross pair (i, j): adds the upper bound of the pair's term over the
-// cube (Theorem 1, Eq. K1i2j_ub with B of Eq. K1i2j_ub_B) to cl and the
-// term at the centre (Lemma 1) to cu.
-__device__ __forceinline__ void cross_pair(float vx, float vy, float vz, float a, float b, float k0, float Cs,
-                                           float Ss, float Plb, float Eb, float Pub, float ux, float uy, float uz,
-                                           float k2, float P2, Acc &cl, Acc &cu) {
-    const float U = GOSMA_U;
-    float dx = vx - ux, dy = vy - uy, dz = vz - uz;
-    float px = vx + ux, py = vy + uy, pz = vz + uz;
+// g(x) = 1 - e^{-2x}, so that Z(x) = e^x g(x) / x (Eq. Z).  For x >= 9,
+// g(x) > 1 - 2^-25 and rounds to 1 in FP32.
+__device__ __forceinline__ float gZ(float x) { return 1.f - ex2a(-2.f * GOSMA_LOG2E * x); }
+
+// Half-angle sine and cosine of the angle between two unit directions
+// given as hi/lo pairs: sin(theta/2) = |v - u|/2, cos(theta/2) = |v + u|/2.
+__device__ __forceinline__ void half_angle(float vx, float vy, float vz, float wx, float wy, float wz, float ux,
+                                           float uy, float uz, float lx, float ly, float lz, float &sth, float &cth) {
+    float dx = (vx - ux) + (wx - lx), dy = (vy - uy) + (wy - ly), dz = (vz - uz) + (wz - lz);
+    float px = (vx + ux) + (wx + lx), py = (vy + uy) + (wy + ly), pz = (vz + uz) + (wz + lz);
     float x2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     float y2 = fmaf(px, px, fmaf(py, py, pz * pz));
-    float sth = 0.5f * sqrta(x2);  // sin(theta / 2)
-    float cth = 0.5f * sqrta(y2);  // cos(theta / 2)
+    sth = 0.5f * sqrta(x2);
+    cth = 0.5f * sqrta(y2);
+}
+
+// Every pair term is written in linear form:
+//   Z(K) / (Z(k1) Z(k2)) = e^{K - k1 - k2} * (g(K) / K) * (k1 / g(k1)) * (k2 / g(k2)),
+// the last two factors (times the weights phi) being per-row and per-column
+// multipliers.  Only K - k1 - k2 goes through the exponential.
+//
+// Error budget of one term, beyond the directed widening of the angles and
+// of K: the factor outside the exponential carries ex2 (4u), rcp (4u) and
+// four roundings (4u), 12u relative or 17.3u in log2 units; the exponent
+// K - k1 - k2 has a relative error of at most 9u.  The exponent (log2
+// units) is therefore moved by 12u |K - k1 - k2| log2 e + TERM_SLACK.
+//
+// Angles: hi/lo directions make sin(theta/2) and cos(theta/2) accurate to
+// 3.5u relative; the uncertainty angles psi_t are widened by 16u relative
+// (their sin^2(psi/2) is accurate to 14u), psi_r is rounded outwards; the
+// half-angle sine/cosine of B (or A) is then uncertain by at most
+// 8u (sin(theta/2) + sin(s/2)), which is added or subtracted ("es").
+#define GOSMA_TERM_SLACK (24.f * GOSMA_U)
+
+// One cross pair (i, j): adds the upper bound of the pair's term over the
+// cube (Theorem 1, Eq. K1i2j_ub with B of Eq. K1i2j_ub_B), without the row
+// multiplier B_i, to cl, and the term at the centre (Lemma 1), without
+// U_i, to cu.
+__device__ __forceinline__ void cross_pair(float sth, float cth, float a, float b, float k0, float Cs, float Ss,
+                                           float k2, float Q, Acc &cl, Acc &cu) {
+    const float U = GOSMA_U;
     // centre: kappa_1i(t0) = k0, angle theta
     float kk = k0 * k2;
     float dk0 = k0 - k2;
     float K0 = sqrta(fmaf(dk0, dk0, 4.f * kk * (cth * cth)));
-    float D0 = -4.f * kk * (sth * sth) * rcpa(k0 + k2 + K0);
-    float L0 = fmaf(D0, GOSMA_LOG2E, phiZ2(K0) + (Pub + P2));
-    cu.add(ex2a(L0));
+    float den0 = k0 + k2 + K0;
+    float K0c = fmaxf(K0, 1e-20f);
+    float r0 = rcpa(den0 * K0c);
+    float D0 = -4.f * kk * (sth * sth) * (K0c * r0);
+    float w0 = den0 * r0;  // 1/K0, times g(K0) below (g(K)/K -> 2 as K -> 0)
+    if (K0 < 9.f) w0 = K0 < 1e-3f ? 2.f - 2.f * K0 : gZ(K0) * w0;
+    cu.add(ex2a(D0 * GOSMA_LOG2E) * w0 * Q);
     // bound: B = max(0, theta - s), s = psi_t,i + psi_r (Cs, Ss = cos, sin of s/2)
     float sB = fmaf(sth, Cs, -cth * Ss);
     float cB = fmaf(cth, Cs, sth * Ss);
-    float es = fmaf(8.f * U, sth + Ss, 4.f * U);
+    float es = 8.f * U * (sth + Ss);
     float slo = fmaxf(sB - es, 0.f);
     float cBc = sB <= 0.f ? 1.f : cB;
     float chi = fminf(cBc + es, 1.f);
     float clo = fmaxf(cBc - es, 0.f);
-    // K - a - k2 at kappa_1 = a: an upper bound uses the smallest sin, largest K
+    // K(a) - a - k2: an upper bound uses the smallest sin and the largest K
     float ka = a * k2;
     float dka = a - k2;
     float Khi = sqrta(fmaf(dka, dka, 4.f * ka * (chi * chi))) * (1.f + 8.f * U);
-    float D = -4.f * ka * (slo * slo) * rcpa(a + k2 + Khi);
     // smallest K over kappa_1 in [a, b] (minimiser -k2 cos B, clamped), from below
     float cosBlo = fmaf(2.f * clo, clo, -1.f);
     float ks = fminf(fmaxf(-k2 * cosBlo, a), b);
     float dks = ks - k2;
     float Kmin = sqrta(fmaf(dks, dks, 4.f * ks * k2 * (clo * clo))) * (1.f - 8.f * U);
-    float ph = phiZ2(Kmin);
-    float DL = D * GOSMA_LOG2E;
-    float L = DL + ph + (Plb + P2);
-    float E = fmaf(6.f * U, fabsf(DL) + fabsf(ph) + fabsf(Plb) + fabsf(P2), phiZ2_err(Kmin, ph) + Eb + 32.f * U);
-    cl.add(ex2a(L + E));
+    float den = a + k2 + Khi;
+    float Kc = fmaxf(Kmin, 1e-20f);
+    float r = rcpa(den * Kc);
+    float DL = -4.f * ka * (slo * slo) * (Kc * r) * GOSMA_LOG2E;
+    // g(K)/K <= min(1/K, 2): an upper bound without evaluating g
+    float w = fminf(den * r, 2.f);
+    cl.add(ex2a(fmaf(12.f * U, fabsf(DL), DL + GOSMA_TERM_SLACK)) * w * Q);
 }
 
 // One self pair (i, m), i != m: adds the lower bound of the pair's term over
-// the cuboid (Theorem 1, Eq. K1i1j_lb with A of Eq. K1i1j_lb_A) to sl and the
-// term at the centre to su.
-__device__ __forceinline__ void self_pair(float vx, float vy, float vz, float ai, float bi, float k0i, float cpi,
-                                          float spi, float Psi, float Eai, float Pui, float wx, float wy, float wz,
-                                          float am, float bm, float k0m, float cpm, float spm, float Psm, float Eam,
-                                          float Pum, Acc &sl, Acc &su) {
+// the cuboid (Theorem 1, Eq. K1i1j_lb with A of Eq. K1i1j_lb_A), without the
+// row multiplier A_i, to sl, and the centre term, without U_i, to su.
+__device__ __forceinline__ void self_pair(float sth, float cth, float ai, float bi, float k0i, float cpi, float spi,
+                                          float am, float bm, float k0m, float cpm, float spm, float Am, float Um,
+                                          Acc &sl, Acc &su) {
     const float U = GOSMA_U;
-    float dx = vx - wx, dy = vy - wy, dz = vz - wz;
-    float px = vx + wx, py = vy + wy, pz = vz + wz;
-    float x2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    float y2 = fmaf(px, px, fmaf(py, py, pz * pz));
-    float sth = 0.5f * sqrta(x2);
-    float cth = 0.5f * sqrta(y2);
     // centre
     float kk = k0i * k0m;
     float dk0 = k0i - k0m;
     float K0 = sqrta(fmaf(dk0, dk0, 4.f * kk * (cth * cth)));
-    float D0 = -4.f * kk * (sth * sth) * rcpa(k0i + k0m + K0);
-    float L0 = fmaf(D0, GOSMA_LOG2E, phiZ2(K0) + (Pui + Pum));
-    su.add(ex2a(L0));
+    float den0 = k0i + k0m + K0;
+    float K0c = fmaxf(K0, 1e-20f);
+    float r0 = rcpa(den0 * K0c);
+    float D0 = -4.f * kk * (sth * sth) * (K0c * r0);
+    float w0 = den0 * r0;
+    if (K0 < 9.f) w0 = K0 < 1e-3f ? 2.f - 2.f * K0 : gZ(K0) * w0;
+    su.add(ex2a(D0 * GOSMA_LOG2E) * w0 * Um);
     // bound: A = min(pi, theta + psi_i + psi_m)
     float C = fmaf(cpi, cpm, -spi * spm);  // cos((psi_i + psi_m)/2)
     float S = fmaf(spi, cpm, cpi * spm);   // sin((psi_i + psi_m)/2)
     float cA = fmaf(cth, C, -sth * S);     // cos(A/2) before the clamp at pi
     float sA = fmaf(sth, C, cth * S);
-    float es = fmaf(8.f * U, sth + fabsf(S), 4.f * U);
+    float es = 8.f * U * (sth + fabsf(S));
     bool api = cA <= es;
     float clo = api ? 0.f : cA - es;
     float chi = fminf(fmaxf(cA, 0.f) + es, 1.f);
     float shi = api ? 1.f : fminf(sA + es, 1.f);
-    // K - b_i - b_m at (b_i, b_m): a lower bound uses the largest sin, smallest K
+    // K(b_i, b_m) - b_i - b_m: a lower bound uses the largest sin and the smallest K
     float bb = bi * bm;
     float dbb = bi - bm;
     float Klo = sqrta(fmaf(dbb, dbb, 4.f * bb * (clo * clo))) * (1.f - 8.f * U);
-    float D = -4.f * bb * (shi * shi) * rcpa(bi + bm + Klo) * (1.f + 8.f * U);
     // largest K over the four corners of [a_i, b_i] x [a_m, b_m], from above
     float c4 = 4.f * (chi * chi);
     float q1 = ai - am, q2 = ai - bm, q3 = bi - am;
-    float k1 = fmaf(q1, q1, c4 * ai * am);
-    float k2 = fmaf(q2, q2, c4 * ai * bm);
-    float k3 = fmaf(q3, q3, c4 * bi * am);
-    float k4 = fmaf(dbb, dbb, c4 * bb);
-    float Kmax = sqrta(fmaxf(fmaxf(k1, k2), fmaxf(k3, k4))) * (1.f + 8.f * U);
-    float ph = phiZ2(Kmax);
-    float DL = D * GOSMA_LOG2E;
-    float L = DL + ph + (Psi + Psm);
-    float E = fmaf(6.f * U, fabsf(DL) + fabsf(ph) + fabsf(Psi) + fabsf(Psm),
-                   phiZ2_err(Kmax, ph) + (Eai + Eam) + 32.f * U);
-    sl.add(ex2a(L - E));
+    float e1 = fmaf(q1, q1, c4 * ai * am);
+    float e2 = fmaf(q2, q2, c4 * ai * bm);
+    float e3 = fmaf(q3, q3, c4 * bi * am);
+    float e4 = fmaf(dbb, dbb, c4 * bb);
+    float Kmax = sqrta(fmaxf(fmaxf(e1, e2), fmaxf(e3, e4))) * (1.f + 8.f * U);
+    float den = bi + bm + Klo;
+    float r = rcpa(den * Kmax);
+    float DL = -4.f * bb * (shi * shi) * (Kmax * r) * GOSMA_LOG2E;
+    // g(K)/K from below: g(K)/K >= 2 - 2K for small K; g rounded with <= 64u error otherwise
+    float w = den * r;
+    if (Kmax < 9.f) w = Kmax < 0.25f ? fmaxf(2.f - 2.f * Kmax, 0.f) : gZ(Kmax) * w * (1.f - 64.f * U);
+    sl.add(ex2a(DL - fmaf(12.f * U, fabsf(DL), GOSMA_TERM_SLACK)) * w * Am);
 }
 
-// log2 of k coth(k) (the diagonal self term Z(2k)/Z(k)^2 = k coth k / 2),
-// k >= 1 for every model concentration; err receives a bound on its error.
-__device__ __forceinline__ float log2_kcothk(float k, float &err) {
-    float l = lg2a(k);
-    float t = 0.f;
-    if (k < 9.0f) {
-        float e = ex2a(-2.f * GOSMA_LOG2E * k);
-        t = lg2a((1.f + e) * rcpa(1.f - e));
-    }
-    err = 4.f * GOSMA_U * fabsf(l) + 40.f * GOSMA_U;
-    return l + t;
+// k coth(k) / 2 = Z(2k) / Z(k)^2, the diagonal self term without phi^2.
+__device__ __forceinline__ float half_kcothk(float k) {
+    float e = ex2a(-2.f * GOSMA_LOG2E * k);
+    return 0.5f * k * (1.f + e) * rcpa(1.f - e);
 }
 
 // The whole per-cube computation.  Every thread of the block must call it
@@ -235,30 +269,35 @@ __device__ void cube_bounds(const MixDev &mx, const CubeGeom &g, bool need_self,
     }
     __syncthreads();
 
-    // ---------------- phase 1a: image columns u_j = R_r0^T mu_2j
+    // ---------------- phase 1a: image columns u_j = R_r0^T mu_2j (FP64, split hi/lo)
     for (int j = tid; j < n2; j += BLOCK) {
         const double *m = mx.mu2 + 3 * j;
         double u0 = cs.R0[0] * m[0] + cs.R0[3] * m[1] + cs.R0[6] * m[2];
         double u1 = cs.R0[1] * m[0] + cs.R0[4] * m[1] + cs.R0[7] * m[2];
         double u2 = cs.R0[2] * m[0] + cs.R0[5] * m[1] + cs.R0[8] * m[2];
-        sm.ux[j] = (float)u0;
-        sm.uy[j] = (float)u1;
-        sm.uz[j] = (float)u2;
+        float h0 = (float)u0, h1 = (float)u1, h2 = (float)u2;
+        sm.ux[j] = h0;
+        sm.uy[j] = h1;
+        sm.uz[j] = h2;
+        sm.lx[j] = (float)(u0 - (double)h0);
+        sm.ly[j] = (float)(u1 - (double)h1);
+        sm.lz[j] = (float)(u2 - (double)h2);
         sm.k2[j] = mx.kappa2[j];
-        sm.P2[j] = mx.P2[j];
+        sm.Q[j] = mx.Q2[j];
     }
 
     // ---------------- phase 1b: model rows
     Acc dsl, dsu;  // diagonal self terms of this thread
     dsl.zero();
     dsu.zero();
-    const float zeta2 = (float)(mx.zeta * mx.zeta);
+    const double zeta2d = mx.zeta * mx.zeta;
+    const float zeta2 = (float)zeta2d;
     const float thx = (float)g.thw[0], thy = (float)g.thw[1], thz = (float)g.thw[2];
     for (int i = tid; i < n1; i += BLOCK) {
         const double *p = mx.mu1 + 3 * i;
         double cxd = p[0] - g.t0[0], cyd = p[1] - g.t0[1], czd = p[2] - g.t0[2];
         double cd2 = cxd * cxd + cyd * cyd + czd * czd;
-        if (cd2 < mx.zeta * mx.zeta) atomicOr(&cs.centre_infeasible, 1);
+        if (cd2 < zeta2d) atomicOr(&cs.centre_infeasible, 1);
         bool inside = fabs(cxd) <= g.thw[0] && fabs(cyd) <= g.thw[1] && fabs(czd) <= g.thw[2];
         // distance to the cuboid (differences in FP64) and to its far corner
         float ex = (float)fmax(fabs(cxd) - g.thw[0], 0.0);
@@ -273,12 +312,23 @@ __device__ void cube_bounds(const MixDev &mx, const CubeGeom &g, bool need_self,
         // kappa range over the feasible part of the cuboid (nearest point clamped to zeta)
         float a = fmaf(fmaxf(dmin2, zeta2), is2, 1.f) * (1.f - 8.f * U);
         float b = fmaf(dmax2, is2, 1.f) * (1.f + 8.f * U);
-        float d2 = fmaf(cx, cx, fmaf(cy, cy, cz * cz));
-        float rin = d2 > 0.f ? rsqrta(d2) : 0.f;
-        float vx = d2 > 0.f ? cx * rin : 1.f, vy = cy * rin, vz = cz * rin;
+        float d2 = (float)cd2;
         float k0 = fmaf(d2, is2, 1.f);
+        // unit direction v_i: FP32 rsqrt refined by one FP64 Newton step, split hi/lo
+        float vx = 1.f, vy = 0.f, vz = 0.f, wx = 0.f, wy = 0.f, wz = 0.f;
+        if (cd2 > 0.0) {
+            double r = (double)rsqrta(d2);
+            r = r * (1.5 - 0.5 * cd2 * r * r);
+            double v0 = cxd * r, v1 = cyd * r, v2 = czd * r;
+            vx = (float)v0;
+            vy = (float)v1;
+            vz = (float)v2;
+            wx = (float)(v0 - (double)vx);
+            wy = (float)(v1 - (double)vy);
+            wz = (float)(v2 - (double)vz);
+        }
         // Lemma 3: largest angle between mu - t_vertex and mu - t0, as sin^2(psi/2);
-        // pi when mu is in the cuboid or a vertex angle exceeds pi/2
+        // pi when mu is in the cuboid or a vertex angle reaches pi/2
         float sp2 = 1.f;
         if (!inside) {
             float m2 = 0.f;
@@ -294,38 +344,34 @@ __device__ void cube_bounds(const MixDev &mx, const CubeGeom &g, bool need_self,
                 float ac = fmaf(ax, cx, fmaf(ay, cy, az * cz));
                 float a2 = fmaf(ax, ax, fmaf(ay, ay, az * az));
                 float nn = sqrta(a2 * d2);
-                wide |= ac <= 0.f;
+                wide |= ac <= 64.f * U * nn;
                 // sin^2(psi/2) = sin^2 psi / (2 (1 + cos psi)) = |o x c|^2 / (2 |a||c| (|a||c| + a.c))
                 float s2 = cr2 * rcpa(2.f * nn * (nn + ac));
                 m2 = fmaxf(m2, s2);
             }
             sp2 = wide ? 1.f : fminf(m2, 1.f);
         }
-        float sps = sp2 >= 1.f ? 1.f : fminf(fmaf(sqrta(sp2), 1.f + 16.f * U, 4.f * U), 1.f);
-        float cps = sqrta(fmaxf(fmaf(-sps, sps, 1.f), 0.f)) * (1.f - 4.f * U);
-        if (sps >= 1.f) cps = 0.f;
+        float sps = sp2 >= 1.f ? 1.f : fminf(sqrta(sp2) * (1.f + 16.f * U), 1.f);
+        float cps = sps >= 1.f ? 0.f : sqrta(fmaxf(fmaf(-sps, sps, 1.f), 0.f)) * (1.f - 4.f * U);
         atomicMax(&cs.spsi_max, __float_as_uint(sps));
-        float lphi = mx.lphi1[i];
-        float pa = phiZ2(a), pk = phiZ2(k0);
-        float Ps = lphi - pa;
+        float ph = mx.phi1f[i];
+        float ga = a < 9.f ? gZ(a) : 1.f, gk = k0 < 9.f ? gZ(k0) : 1.f;
         sm.vx[i] = vx;
         sm.vy[i] = vy;
         sm.vz[i] = vz;
+        sm.wx[i] = wx;
+        sm.wy[i] = wy;
+        sm.wz[i] = wz;
         sm.a[i] = a;
         sm.b[i] = b;
         sm.k0[i] = k0;
         sm.cps[i] = cps;
         sm.sps[i] = sps;
-        sm.Pself[i] = Ps;
-        sm.Ea[i] = phiZ2_err(a, pa) + 2.f * U * fabsf(Ps);
-        sm.Pub[i] = lphi - pk;
-        // diagonal self term: phi_i^2 k coth(k) / 2, minimum over [a_i, b_i] at a_i
-        float ea, ek;
-        float la = log2_kcothk(a, ea), lk = log2_kcothk(k0, ek);
-        float Ld = 2.f * lphi + la - 1.f;
-        float Ed = 6.f * U * (2.f * fabsf(lphi) + fabsf(la) + 1.f) + ea + 16.f * U;
-        dsl.add(ex2a(Ld - Ed));
-        dsu.add(ex2a(2.f * lphi + lk - 1.f));
+        sm.Aw[i] = ph * a * rcpa(ga) * (1.f - 16.f * U);  // phi_i a_i / g(a_i), from below
+        sm.Uw[i] = ph * k0 * rcpa(gk);                    // phi_i k0_i / g(k0_i)
+        // diagonal self term phi_i^2 k coth(k) / 2, smallest over [a_i, b_i] at a_i
+        dsl.add(ph * ph * half_kcothk(a) * (1.f - 16.f * U));
+        dsu.add(ph * ph * half_kcothk(k0));
     }
     __syncthreads();
 
@@ -339,8 +385,8 @@ __device__ void cube_bounds(const MixDev &mx, const CubeGeom &g, bool need_self,
         const int ti = tid % Ti, tj = tid / Ti;
         const float Cr = cs.Cr, Sr = cs.Sr;
         for (int i = ti; i < n1; i += Ti) {
-            float vx = sm.vx[i], vy = sm.vy[i], vz = sm.vz[i];
-            float a = sm.a[i], b = sm.b[i], k0 = sm.k0[i], Pub = sm.Pub[i];
+            float vx = sm.vx[i], vy = sm.vy[i], vz = sm.vz[i], wx = sm.wx[i], wy = sm.wy[i], wz = sm.wz[i];
+            float a = sm.a[i], b = sm.b[i], k0 = sm.k0[i];
             float cps = sm.cps[i], sps = sm.sps[i];
             // s = psi_t,i + psi_r as half-angle cosine/sine; s >= pi means B = 0 everywhere
             float Cs = fmaf(cps, Cr, -sps * Sr);
@@ -349,17 +395,19 @@ __device__ void cube_bounds(const MixDev &mx, const CubeGeom &g, bool need_self,
                 Cs = 0.f;
                 Ss = 1.f;
             }
-            float pb = phiZ2(b);
-            float Plb = mx.lphi1[i] - pb;
-            float Eb = phiZ2_err(b, pb) + 2.f * U * fabsf(Plb);
+            float gb = b < 9.f ? gZ(b) : 1.f;
+            // phi_i b_i / g(b_i) from above (g rounded to 1 for b >= 9 is 2^-25 low at most)
+            float Bw = mx.phi1f[i] * b * rcpa(gb) * (1.f + 16.f * U);
             Acc cl, cu;
             cl.zero();
             cu.zero();
-            for (int j = tj; j < n2; j += Tj)
-                cross_pair(vx, vy, vz, a, b, k0, Cs, Ss, Plb, Eb, Pub, sm.ux[j], sm.uy[j], sm.uz[j], sm.k2[j],
-                           sm.P2[j], cl, cu);
-            cross_ub += cl.value() * (1.0 + 4.0 * (double)U);
-            cross_c += cu.value();
+            for (int j = tj; j < n2; j += Tj) {
+                float sth, cth;
+                half_angle(vx, vy, vz, wx, wy, wz, sm.ux[j], sm.uy[j], sm.uz[j], sm.lx[j], sm.ly[j], sm.lz[j], sth, cth);
+                cross_pair(sth, cth, a, b, k0, Cs, Ss, sm.k2[j], sm.Q[j], cl, cu);
+            }
+            cross_ub += cl.value() * (double)Bw * (1.0 + 4.0 * (double)U);
+            cross_c += cu.value() * (double)sm.Uw[i];
         }
         // ---------------- phase 2b: self pairs i < m, rows paired (p, n1-2-p) for balance
         if (need_self && n1 > 1) {
@@ -371,18 +419,20 @@ __device__ void cube_bounds(const MixDev &mx, const CubeGeom &g, bool need_self,
                 for (int h = 0; h < 2; ++h) {
                     int i = h == 0 ? pp : n1 - 2 - pp;
                     if (h == 1 && i == pp) break;
-                    float vx = sm.vx[i], vy = sm.vy[i], vz = sm.vz[i];
+                    float vx = sm.vx[i], vy = sm.vy[i], vz = sm.vz[i], wx = sm.wx[i], wy = sm.wy[i], wz = sm.wz[i];
                     float ai = sm.a[i], bi = sm.b[i], k0i = sm.k0[i], cpi = sm.cps[i], spi = sm.sps[i];
-                    float Psi = sm.Pself[i], Eai = sm.Ea[i], Pui = sm.Pub[i];
                     Acc sl, su;
                     sl.zero();
                     su.zero();
-                    for (int m = i + 1 + sj; m < n1; m += Sj)
-                        self_pair(vx, vy, vz, ai, bi, k0i, cpi, spi, Psi, Eai, Pui, sm.vx[m], sm.vy[m], sm.vz[m],
-                                  sm.a[m], sm.b[m], sm.k0[m], sm.cps[m], sm.sps[m], sm.Pself[m], sm.Ea[m], sm.Pub[m],
-                                  sl, su);
-                    self_lb += 2.0 * sl.value() * (1.0 - 4.0 * (double)U);
-                    self_c += 2.0 * su.value();
+                    for (int m = i + 1 + sj; m < n1; m += Sj) {
+                        float sth, cth;
+                        half_angle(vx, vy, vz, wx, wy, wz, sm.vx[m], sm.vy[m], sm.vz[m], sm.wx[m], sm.wy[m], sm.wz[m],
+                                   sth, cth);
+                        self_pair(sth, cth, ai, bi, k0i, cpi, spi, sm.a[m], sm.b[m], sm.k0[m], sm.cps[m], sm.sps[m],
+                                  sm.Aw[m], sm.Uw[m], sl, su);
+                    }
+                    self_lb += 2.0 * sl.value() * (double)sm.Aw[i] * (1.0 - 4.0 * (double)U);
+                    self_c += 2.0 * su.value() * (double)sm.Uw[i];
                 }
             }
         }

@@ -21,12 +21,12 @@ struct MixDev {
     int n1, n2;
     const double *mu1;     // n1 x 3
     const float *inv_sig2; // n1: 1 / sigma_1i^2
-    const float *lphi1;    // n1: log2(phi_1i), clamped at -200
+    const float *phi1f;    // n1: phi_1i
     const double *sigma1d; // n1: sigma_1i (FP64, objective kernels)
     const double *phi1d;   // n1
     const double *mu2;     // n2 x 3 (unit)
     const float *kappa2;   // n2
-    const float *P2;       // n2: log2(phi_2j) - phiZ2(kappa_2j)  (computed in FP64)
+    const float *Q2;       // n2: phi_2j kappa_2j / (1 - e^{-2 kappa_2j})  (computed in FP64)
     const double *kappa2d; // n2
     const double *phi2d;   // n2
     double zeta;           // point-to-camera limit (Sec. 4.1)
@@ -50,12 +50,11 @@ struct CubeSums {
 // by gosma_selftest_approx; the kernel's slack assumes the bounds below.
 #define GOSMA_U 5.9604644775390625e-8f   // 2^-24, unit roundoff of FP32
 #define GOSMA_LOG2E 1.4426950408889634f
-#define GOSMA_LN2 0.69314718055994531f
 
-// Relative error assumed for ex2/rcp/rsqrt/sqrt (2^-21) and the absolute +
-// relative error assumed for lg2 (2^-21 each).
-#define GOSMA_APPROX_REL (8.0f * GOSMA_U)
-#define GOSMA_LG2_ABS (8.0f * GOSMA_U)
+// Relative error assumed for ex2/rcp/rsqrt/sqrt (2^-22) and the absolute +
+// relative error assumed for lg2 (2^-22 each).
+#define GOSMA_APPROX_REL (4.0f * GOSMA_U)
+#define GOSMA_LG2_ABS (4.0f * GOSMA_U)
 
 __device__ __forceinline__ float ex2a(float x) {
     float y;
@@ -81,27 +80,6 @@ __device__ __forceinline__ float sqrta(float x) {
     float y;
     asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
-}
-
-// phiZ2(x) = log2((1 - e^{-2x}) / x) = (log Z(x) - x) / ln 2, the
-// decreasing part of log Z in Eq. (Z), for x >= 0.
-//   x >= 9    : -log2 x (the dropped log2(1 - e^{-2x}) is in (-2.3e-8, 0])
-//   x >= 1/4  : log2(1 - 2^{-2x log2 e}) - log2 x
-//   x <  1/4  : series of log(sinh x / x) - x + log 2
-__device__ __forceinline__ float phiZ2(float x) {
-    if (x >= 9.0f) return -lg2a(x);
-    if (x >= 0.25f) return lg2a(1.0f - ex2a(-2.0f * GOSMA_LOG2E * x)) - lg2a(x);
-    float x2 = x * x;
-    float s = x2 * (1.0f / 6.0f + x2 * (-1.0f / 180.0f + x2 * (1.0f / 2835.0f)));
-    return (GOSMA_LN2 - x + s) * GOSMA_LOG2E;
-}
-
-// Bound on |phiZ2 computed - phiZ2 exact| for the value v = phiZ2(x)
-// (derivation: rounding of the exponent argument, of 1 - e, and the
-// assumed lg2/ex2 errors; one-sided 2.3e-8 of the x >= 9 branch included).
-__device__ __forceinline__ float phiZ2_err(float x, float v) {
-    float c = x >= 9.0f ? 10.0f * GOSMA_U : (x >= 1.0f ? 32.0f * GOSMA_U : 96.0f * GOSMA_U);
-    return c + 4.0f * GOSMA_U * fabsf(v);
 }
 
 // Compensated FP32 accumulation (TwoSum): s + c carries the running sum

@@ -225,10 +225,11 @@ int objective_grad_device(gosma_ctx *ctx, int count, const double *h_x, double *
 }
 
 // ---------------------------------------------------------------- set-up constants
-// P2_j = log2(phi_2j) - phiZ2(kappa_2j), FP64, and C22 = sum_jj' phi phi
+// Q2_j = phi_2j kappa_2j / (1 - e^{-2 kappa_2j}) (the column factor of the
+// linear-form pair terms), FP64 rounded once, and C22 = sum_jj' phi phi
 // Z(|k_j mu_j + k_j' mu_j'|)/(Z(k_j) Z(k_j')) (2 pi times the integral of
 // p2^2, proof of Lemma 1) as per-block partial sums.
-__global__ void setup_image(MixDev mx, float *P2, double *c22part) {
+__global__ void setup_image(MixDev mx, float *Q2, double *c22part) {
     __shared__ double red[8];
     double acc = 0.0;
     const int n2 = mx.n2;
@@ -244,10 +245,7 @@ __global__ void setup_image(MixDev mx, float *P2, double *c22part) {
     }
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n2; j += gridDim.x * blockDim.x) {
         double k = mx.kappa2d[j];
-        double ph = mx.phi2d[j];
-        double lp = ph > 0 ? log2(ph) : -200.0;
-        if (lp < -200.0) lp = -200.0;
-        P2[j] = (float)(lp - (logZ_d(k) - k) * 1.4426950408889634);
+        Q2[j] = (float)(mx.phi2d[j] * k / -expm1(-2.0 * k));
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
@@ -259,23 +257,21 @@ __global__ void setup_image(MixDev mx, float *P2, double *c22part) {
     }
 }
 
-__global__ void setup_model(MixDev mx, float *inv_sig2, float *lphi1) {
+__global__ void setup_model(MixDev mx, float *inv_sig2, float *phi1f) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < mx.n1; i += gridDim.x * blockDim.x) {
         double s = mx.sigma1d[i];
         inv_sig2[i] = (float)(1.0 / (s * s));
-        double ph = mx.phi1d[i];
-        double lp = ph > 0 ? log2(ph) : -200.0;
-        lphi1[i] = (float)(lp < -200.0 ? -200.0 : lp);
+        phi1f[i] = (float)mx.phi1d[i];
     }
 }
 
-int setup_constants(gosma_ctx *ctx, float *P2, float *inv_sig2, float *lphi1, double *c22_out) {
+int setup_constants(gosma_ctx *ctx, float *Q2, float *inv_sig2, float *phi1f, double *c22_out) {
     const int nb = 64;
     double *dpart = nullptr;
     cudaError_t e = cudaMalloc(&dpart, sizeof(double) * nb);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(setup)");
-    setup_image<<<nb, 256, 0, ctx->stream>>>(ctx->mix, P2, dpart);
-    setup_model<<<(ctx->n1 + 255) / 256, 256, 0, ctx->stream>>>(ctx->mix, inv_sig2, lphi1);
+    setup_image<<<nb, 256, 0, ctx->stream>>>(ctx->mix, Q2, dpart);
+    setup_model<<<(ctx->n1 + 255) / 256, 256, 0, ctx->stream>>>(ctx->mix, inv_sig2, phi1f);
     double hp[nb];
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(hp, dpart, sizeof hp, cudaMemcpyDeviceToHost, ctx->stream);
