@@ -1,0 +1,336 @@
+#!/usr/bin/env python
+"""Benchmark of the GOSMA branch-and-bound hot path on GB300.
+
+Metric: pair-bound evaluations per second, counting (sub-cube, model
+component i, image component j) cross pairs, each bounded from below and
+evaluated at the centre (Theorem 1).  A step is one full iteration of
+Algorithm 1 on the device: radix-select pop of 8,192 parents, branching into
+65,536 children, the bound kernel, pruning/appending by scan, the smallest
+live key, and the FP64 incumbent refinement (SMA) when a child improves d*.
+
+Workload: one 128 x 64 component problem (10 x 10 x 3 m room, sigma in
+U[0.03, 0.1], Dirichlet weights, 48 noisy inliers + 16 outliers, kappa in
+U[20, 200], translation domain [-2, 2]^3, eps = 1e-4), seeded synthetic.
+Steps are taken after the queue holds at least 8,192 live sub-cubes, so
+every timed step bounds exactly 65,536 children.  L2 is flushed (a 512 MB
+write) between timed steps, outside the timed region.
+
+e2e: the same metric through gosma_eval_bounds with host buffers: every step
+copies a batch of 65,536 sub-cubes of the same tree depths from host memory
+and reads back their lower and upper bounds.
+
+--impl reference: the FP64 CPU oracle, as it stands, on the host cores, on a
+bounded sample of the same workload per step.
+
+Multi-GPU (torchrun): every rank solves its own independent problem (seed +
+rank); no data-path collective; value = pairs of all ranks / max rank time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pair-bound evals/s (cube*i*j/s)"
+UNIT = "pairs/s"
+POP = 8192
+SEED = 2000
+# FP32-pipe operations per pair of the bound kernel, counted from its
+# source (half-angle, centre term, bound term, compensated accumulation);
+# MUFU operations (9 per pair) run on a separate pipe with 32 lanes per SM.
+OPS_CROSS = 112
+OPS_SELF = 120
+FP32_LANES_PER_SM = 128
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.p = None
+        self.path = None
+
+    def start(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.p is None:
+            return out
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if sm:
+            out = {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                   "samples": len(sm)}
+        return out
+
+
+def kernel_traffic():
+    """DRAM bytes per launch of the bound kernel from the committed ncu capture,
+    or None when the kernel source changed since the capture."""
+    import hashlib
+    prof = os.path.join(ROOT, "profiles", "bound_children_traffic.json")
+    if not os.path.exists(prof):
+        return None
+    rec = json.load(open(prof))
+    h = hashlib.sha256()
+    for f in ("bounds_core.cuh", "bnb.cu"):
+        h.update(open(os.path.join(ROOT, "paper_1812_01232_gb300", "csrc", f), "rb").read())
+    return rec.get("bytes_per_launch") if rec.get("source_sha256") == h.hexdigest() else None
+
+
+def make_problem(rank):
+    from paper_1812_01232_gb300 import synth
+    return synth.paper_scale_problem(SEED + rank)
+
+
+def cpu_sample(prob, target_s, seed):
+    """Time the FP64 oracle's Theorem 1 bounds on a bounded sample of cubes."""
+    import oracle
+    from paper_1812_01232_gb300 import synth
+    mix = oracle.Mixtures.from_problem(prob)
+    n1, n2 = len(prob["sigma1"]), len(prob["kappa2"])
+    cubes = synth.tree_cubes(seed, 65536, prob["t_lo"], prob["t_hi"], 2, 12)
+    n = 16
+    t0 = time.perf_counter()
+    oracle.bounds(mix, cubes[:n], prob["zeta"])
+    dt = time.perf_counter() - t0
+    n = int(min(len(cubes), max(16, n * target_s / max(dt, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.bounds(mix, cubes[:n], prob["zeta"])
+    dt = time.perf_counter() - t0
+    return n, dt, n * n1 * n2 / dt, oracle.max_threads()
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    prob = make_problem(0)
+    n1, n2 = len(prob["sigma1"]), len(prob["kappa2"])
+    per_step = max(2.0, 150.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        cpu_sample(prob, min(per_step, 2.0), 11)
+    tot_pairs, tot_t, cubes = 0.0, 0.0, 0
+    for k in range(args.steps):
+        n, dt, _, cores = cpu_sample(prob, per_step, 100 + k)
+        tot_pairs += n * n1 * n2
+        tot_t += dt
+        cubes += n
+    value = tot_pairs / tot_t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "paper_scale 128x64 components, sub-cubes at tree depths 2-12",
+                   "n1": n1, "n2": n2},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "%d sub-cubes over %d steps, Theorem 1 lb+ub in FP64 (self pairs included)"
+                                   % (cubes, args.steps)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1812_01232_gb300 import synth
+    from paper_1812_01232_gb300.gosma import Gosma
+    prob = make_problem(rank)
+    ctx = Gosma(local)
+    ctx.set_problem(prob)
+    n1, n2 = ctx.n1, ctx.n2
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    # ---------------- warm-up: grow the queue until a full pop is possible, then W steps
+    ctx.bnb_start(eps=prob["eps"], pop=POP, queue_capacity=args.queue_capacity)
+    r = ctx.bnb_step(1)
+    while r["queue_size"] < POP and r["status_name"] == "running":
+        r = ctx.bnb_step(1)
+    for _ in range(args.warmup):
+        r = ctx.bnb_step(1)
+    if r["status_name"] != "running":
+        raise RuntimeError("branch-and-bound stopped during warm-up: %s" % r["status_name"])
+
+    # ---------------- timed steps
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    times = []
+    pairs = 0
+    self_pairs = 0
+    b0, l0 = r["bound_ms"], r["launches"]
+    bound_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        prev = r
+        r = ctx.bnb_step(1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if r["iterations"] != prev["iterations"] + 1 or r["cross_pairs"] - prev["cross_pairs"] != 8 * POP * n1 * n2:
+            raise RuntimeError("a timed step did not bound a full batch")
+        times.append(e0.elapsed_time(e1))
+        pairs += r["cross_pairs"] - prev["cross_pairs"]
+        self_pairs += r["self_pairs"] - prev["self_pairs"]
+    bound_ms = r["bound_ms"] - b0
+    launches = r["launches"] - l0
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    t_total = sum(times) / 1e3
+    if dist:
+        tt = torch.tensor([t_total], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_total = float(tt.item())
+        pp = torch.tensor([float(pairs)], device="cuda")
+        dist.all_reduce(pp)
+        pairs_all = float(pp.item())
+    else:
+        pairs_all = float(pairs)
+    value = pairs_all / t_total
+
+    # ---------------- e2e through the host-buffer C-ABI call
+    cubes = synth.tree_cubes(SEED + 17 + rank, 8 * POP, prob["t_lo"], prob["t_hi"], 2, 12)
+    ctx.eval_bounds(cubes)  # warm the staging buffers
+    e2e_t = []
+    for _ in range(max(3, args.steps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lb, ub = ctx.eval_bounds(cubes)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_value = 8 * POP * n1 * n2 / float(np.mean(e2e_t))
+
+    # ---------------- roofline of the bound kernel (FP32 pipe)
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+    max_mhz = ck["sm_max_mhz"] or 2070.0
+    peak = sm_count * FP32_LANES_PER_SM * max_mhz * 1e6 / 1e9  # Gop/s
+    achieved = (OPS_CROSS * pairs + OPS_SELF * self_pairs) / (bound_ms / 1e3) / 1e9
+    traffic = kernel_traffic()
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+    # ---------------- CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only)
+    cpu = None
+    if world == 1 and not args.no_cpu:
+        import oracle
+        oracle.build()
+        n, dt, v, cores = cpu_sample(prob, args.cpu_seconds, 99)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "%d sub-cubes of the same workload (depths 2-12), Theorem 1 lb+ub in FP64, %.1f s" % (n, dt)}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 pair terms, f64 per-cube sums", "data": "synthetic",
+        "config": {"workload": "paper_scale: one problem per GPU, 128 model x 64 image components, "
+                               "branch-and-bound step of %d parents -> %d children, eps 1e-4" % (POP, 8 * POP),
+                   "n1": n1, "n2": n2, "children_per_step": 8 * POP,
+                   "self_pairs_per_step": self_pairs / args.steps, "l2": "flushed between steps (512 MB write)",
+                   "queue_size_end": r["queue_size"]},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(cubes.nbytes),
+                "d2h_bytes_per_step": int(2 * 8 * len(cubes)),
+                "call": "gosma_eval_bounds on host buffers, %d sub-cubes per step" % len(cubes)},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s (FP32 pipe)",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "bound_children", "kernel_ms_per_step": bound_ms / args.steps,
+                     "peak_basis": "%d SMs x %d FP32 lanes x %.0f MHz" % (sm_count, FP32_LANES_PER_SM, max_mhz)},
+        "cpu_baseline": cpu,
+        "clocks": ck,
+        "gpu_launches": launches,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--queue-capacity", type=int, default=1 << 27,
+                    help="device queue capacity in sub-cubes (64 bytes each, twice)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -39,6 +39,7 @@ extern "C" {
 #define GOSMA_NODE_LIMIT 1   /* stopped at opts.max_nodes */
 #define GOSMA_TIME_LIMIT 2   /* stopped at opts.max_seconds */
 #define GOSMA_QUEUE_FULL 3   /* the device queue reached its capacity */
+#define GOSMA_RUNNING 4      /* gosma_bnb_step returned before termination */
 
 typedef struct gosma_ctx gosma_ctx;
 
@@ -87,6 +88,12 @@ typedef struct {
     long long queue_peak;
     double seconds;
     int status;              /* GOSMA_OPTIMAL, GOSMA_NODE_LIMIT, ... */
+    long long cross_pairs;   /* (cube, i, j) cross pairs bounded so far        */
+    long long self_pairs;    /* (cube, i < m) self pairs bounded so far        */
+    double bound_ms;         /* device time of the bound kernel (CUDA events)  */
+    double iteration_ms;     /* device time of whole iterations (CUDA events)  */
+    long long queue_size;    /* live sub-cubes in the queue                    */
+    long long launches;      /* kernels the context has launched so far        */
 } gosma_result;
 
 /* Create a context on CUDA device `device`, issuing all work on `stream`
@@ -135,9 +142,23 @@ int gosma_eval_objective(gosma_ctx *ctx, const double r[3], const double t[3], d
 int gosma_eval_objective_grad(gosma_ctx *ctx, int count, const double *x, double *f, double *grad);
 
 /* Algorithm 1 (GOSMA) on the device: branch, bound, prune and select run in
- * device kernels; d* is always an FP64 evaluation of f.  opts may be NULL
- * (eps = 0.1, pop = 1024, no limits, SMA on). */
+ * device kernels; d* is always an FP64 evaluation of f, refined by SMA
+ * (Sec. 5) whenever a sub-cube's upper bound beats it.  opts may be NULL
+ * (eps = 0.1, pop = 1024, no limits, SMA on).  Equivalent to
+ * gosma_bnb_start followed by gosma_bnb_step(ctx, 0, out). */
 int gosma_bnb_solve(gosma_ctx *ctx, const gosma_opts *opts, gosma_result *out);
+
+/* Start a branch-and-bound run (the queue holds the root Omega_r x Omega_t).
+ * The run's device state belongs to the context until the next start. */
+int gosma_bnb_start(gosma_ctx *ctx, const gosma_opts *opts);
+
+/* Run at most max_iters iterations of Algorithm 1 (max_iters <= 0: until a
+ * stopping rule fires) and report the state in out (status GOSMA_RUNNING
+ * while none has).  GOSMA_ENOTREADY without a prior gosma_bnb_start. */
+int gosma_bnb_step(gosma_ctx *ctx, int max_iters, gosma_result *out);
+
+/* Number of kernels the context has launched since it was created. */
+long long gosma_kernel_launches(const gosma_ctx *ctx);
 
 /* Diagnostics: measured maximum relative error of the device's approximate
  * ex2, lg2, rcp, rsqrt and sqrt against FP64 over dense samples (5 values,

@@ -88,6 +88,8 @@ void gosma_destroy(gosma_ctx *ctx) {
 
 const char *gosma_last_error(const gosma_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
+long long gosma_kernel_launches(const gosma_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
 int gosma_set_mixtures(gosma_ctx *ctx, int n1, const double *mu1, const double *sigma1, const double *phi1, int n2,
                        const double *mu2, const double *kappa2, const double *phi2) {
     if (!ctx) return GOSMA_EINVAL;
@@ -220,6 +222,7 @@ static int eval_common(gosma_ctx *ctx, const gosma_cube *cubes, int n, gosma_bou
         if (rc) return rc;
         if (!detail) {
             split_bounds<<<(n + 255) / 256, 256, 0, ctx->stream>>>(dout, n, lb, ub);
+            ++ctx->launches;
             e = cudaGetLastError();
             if (e != cudaSuccess) return cuda_fail(ctx, e, "launch(split)");
         }

@@ -289,7 +289,7 @@ __global__ void ext_scatter(uint32_t *__restrict__ keys, const Node *__restrict_
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK)
     bound_children(MixDev mx, Domain dom, const Node *__restrict__ parents, int np, Node *__restrict__ kids,
-                   double *__restrict__ kid_ub) {
+                   double *__restrict__ kid_ub, unsigned int *__restrict__ n_self) {
     extern __shared__ float smem_f[];
     __shared__ CubeShared cs;
     __shared__ CubeSums sums;
@@ -304,6 +304,7 @@ __global__ void __launch_bounds__(BLOCK)
         bool need_self = !(ch.flags & 1u);
         cube_bounds<BLOCK>(mx, g, need_self, cs, sm, sums);
         if (threadIdx.x == 0) {
+            if (need_self) atomicAdd(n_self, 1u);
             double sl = need_self ? sums.self_lb : p.self_lb;
             double sc = need_self ? sums.self_c : p.self_c;
             double lb, ub;
@@ -504,7 +505,13 @@ struct BnbState {
     unsigned long long *total = nullptr;
     Status *st = nullptr;
     Status *h_st = nullptr;  // pinned
+    unsigned int *kid_rot = nullptr;  // children that computed their own self sums
+    unsigned int *h_flags = nullptr;  // pinned copy
+    struct Solve *solve = nullptr;
 };
+
+struct Solve;
+static void delete_solve(Solve *v);
 
 static void free_state(BnbState *s) {
     if (!s) return;
@@ -521,7 +528,10 @@ static void free_state(BnbState *s) {
     cudaFree(s->off);
     cudaFree(s->total);
     cudaFree(s->st);
+    cudaFree(s->kid_rot);
     if (s->h_st) cudaFreeHost(s->h_st);
+    if (s->h_flags) cudaFreeHost(s->h_flags);
+    delete_solve(s->solve);
     delete s;
 }
 
@@ -557,8 +567,10 @@ static int alloc_state(gosma_ctx *ctx, unsigned long long cap, int pop, BnbState
     ALLOC(s->off, sizeof(int2) * ntile);
     ALLOC(s->total, sizeof(unsigned long long));
     ALLOC(s->st, sizeof(Status));
+    ALLOC(s->kid_rot, sizeof(unsigned int));
 #undef ALLOC
     if (e == cudaSuccess) e = cudaMallocHost((void **)&s->h_st, sizeof(Status));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&s->h_flags, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMemsetAsync(s->hist, 0, sizeof(unsigned int) * 2048, ctx->stream);
     if (e != cudaSuccess) {
         free_state(s);
@@ -580,7 +592,10 @@ static int launch_children(gosma_ctx *ctx, const Domain &dom, BnbState *s, int n
     if (e != cudaSuccess || per_sm < 1) return fail(ctx, GOSMA_ECUDA, "children kernel does not fit");
     long long grid = (long long)ctx->sm_count * per_sm;
     if (grid > 8LL * np) grid = 8LL * np;
-    kern<<<(int)grid, BLOCK, smem, ctx->stream>>>(ctx->mix, dom, s->parents, np, s->kids, s->kid_ub);
+    e = cudaMemsetAsync(s->kid_rot, 0, sizeof(unsigned int), ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "memset(children)");
+    kern<<<(int)grid, BLOCK, smem, ctx->stream>>>(ctx->mix, dom, s->parents, np, s->kids, s->kid_ub, s->kid_rot);
+    ++ctx->launches;
     e = cudaGetLastError();
     return e == cudaSuccess ? GOSMA_OK : cuda_fail(ctx, e, "launch(children)");
 }
@@ -602,39 +617,56 @@ static int grid_for(unsigned long long n, int block, int sm) {
 }
 
 // One iteration on the device: select, extract, bound, append, min.
-static int iterate(gosma_ctx *ctx, const Domain &dom, BnbState *s, unsigned long long tail, int np) {
+static int iterate(gosma_ctx *ctx, const Domain &dom, BnbState *s, unsigned long long tail, int np, cudaEvent_t *ev,
+                   long long *self_children) {
     cudaStream_t st = ctx->stream;
+    cudaEventRecord(ev[0], st);
     uint32_t *keys = s->keys[s->cur];
     Node *q = s->q[s->cur];
     int ntile = (int)((tail + SEL_TILE - 1) / SEL_TILE);
     int g = grid_for(tail, 256, ctx->sm_count);
     for (int pass = 0; pass < 3; ++pass) {
         sel_hist<<<g, 256, 0, st>>>(keys, tail, pass, s->st, s->hist);
+        ++ctx->launches;
         sel_find<<<1, 1024, 0, st>>>(s->hist, pass, s->st, (unsigned)np);
+        ++ctx->launches;
     }
     ext_count<<<ntile, SEL_BLOCK, 0, st>>>(keys, tail, s->st, s->cnt);
+    ++ctx->launches;
     ext_scan<<<1, SEL_BLOCK, 0, st>>>(s->cnt, ntile, s->st, s->off);
+    ++ctx->launches;
     ext_scatter<<<ntile, SEL_BLOCK, 0, st>>>(keys, q, tail, s->st, s->off, s->parents);
+    ++ctx->launches;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "launch(select/extract)");
+    cudaEventRecord(ev[1], st);
     int rc = launch_children_any(ctx, dom, s, np);
     if (rc) return rc;
+    cudaEventRecord(ev[2], st);
     const int nk = 8 * np, ktile = (nk + SEL_TILE - 1) / SEL_TILE;
     // reset best_key, best_child_u and minkey (contiguous in Status)
     e = cudaMemsetAsync(&s->st->best_key, 0xFF, offsetof(Status, best_child) - offsetof(Status, best_key), st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "memset(status)");
     app_count<<<ktile, SEL_BLOCK, 0, st>>>(s->kids, s->kid_ub, nk, s->dstar, s->cnt, s->st);
+    ++ctx->launches;
     app_scan<<<1, SEL_BLOCK, 0, st>>>(s->cnt, ktile, s->off, s->st, s->cap);
+    ++ctx->launches;
     app_scatter<<<ktile, SEL_BLOCK, 0, st>>>(s->kids, s->kid_ub, nk, s->dstar, s->off, q, keys, s->cap, s->st);
+    ++ctx->launches;
     app_finish<<<1, 1, 0, st>>>(s->kids, s->kid_ub, s->st);
+    ++ctx->launches;
     unsigned long long ntail = tail + 8ULL * np;  // upper bound of the new tail
     if (ntail > s->cap) ntail = s->cap;
     min_key<<<grid_for(ntail, 256, ctx->sm_count), 256, 0, st>>>(keys, ntail, s->st);
+    ++ctx->launches;
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "launch(append/min)");
+    cudaEventRecord(ev[3], st);
     e = cudaMemcpyAsync(s->h_st, s->st, sizeof(Status), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->h_flags, s->kid_rot, sizeof(unsigned int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "sync(iteration)");
+    *self_children = *s->h_flags;
     return GOSMA_OK;
 }
 
@@ -644,8 +676,11 @@ static int compact(gosma_ctx *ctx, BnbState *s, unsigned long long tail, unsigne
     int ntile = (int)((tail + SEL_TILE - 1) / SEL_TILE);
     int o = s->cur, n = 1 - s->cur;
     cmp_count<<<ntile, SEL_BLOCK, 0, st>>>(s->keys[o], s->q[o], tail, s->dstar, s->cnt);
+    ++ctx->launches;
     cmp_scan<<<1, SEL_BLOCK, 0, st>>>(s->cnt, ntile, s->off, s->total);
+    ++ctx->launches;
     cmp_scatter<<<ntile, SEL_BLOCK, 0, st>>>(s->keys[o], s->q[o], tail, s->dstar, s->off, s->keys[n], s->q[n]);
+    ++ctx->launches;
     unsigned long long t = 0;
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(&t, s->total, sizeof t, cudaMemcpyDeviceToHost, st);
@@ -772,141 +807,36 @@ static void rodrigues_host(const double r[3], double R[9]) {
     memcpy(R, M, sizeof M);
 }
 
-}  // namespace gosma
-
-using namespace gosma;
-
-extern "C" int gosma_bnb_solve(gosma_ctx *ctx, const gosma_opts *opts_in, gosma_result *out) {
-    if (!ctx || !out) return GOSMA_EINVAL;
-    ctx->err.clear();
-    if (!ctx->have_mix || !ctx->have_dom) return fail(ctx, GOSMA_ENOTREADY, "bnb_solve: set mixtures and domain first");
+// Solver state kept between gosma_bnb_step calls.
+struct Solve {
     gosma_opts o;
-    o.eps = 0.1;
-    o.pop = 1024;
-    o.max_nodes = 0;
-    o.max_seconds = 0;
-    o.use_sma = 1;
-    o.sma_max_iter = 100;
-    o.queue_capacity = 0;
-    if (opts_in) o = *opts_in;
-    if (!(o.eps >= 0) || o.pop < 1 || o.pop > 131072) return fail(ctx, GOSMA_EINVAL, "bnb_solve: eps >= 0, 1 <= pop <= 131072");
-    if (o.sma_max_iter <= 0) o.sma_max_iter = 100;
-    unsigned long long cap = o.queue_capacity > 0 ? (unsigned long long)o.queue_capacity : (1ULL << 24);
-    if (cap < 16ULL * o.pop) cap = 16ULL * o.pop;
-    cudaSetDevice(ctx->device);
-    auto t_start = std::chrono::steady_clock::now();
-    auto seconds = [&]() {
-        return std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
-    };
-    BnbState *s = nullptr;
-    int rc = alloc_state(ctx, cap, o.pop, &s);
-    if (rc) return rc;
     Domain dom;
-    for (int k = 0; k < 3; ++k) {
-        dom.t_lo[k] = ctx->t_lo[k];
-        dom.t_hi[k] = ctx->t_hi[k];
-    }
+    double eps_f = 0, dstar = INFINITY, dlb = -INFINITY;
+    double best[6] = {0, 0, 0, 0, 0, 0};
+    unsigned long long tail = 0, live = 0;
+    long long nodes = 0, iters = 0, sma_calls = 0, peak = 0;
+    long long cross_pairs = 0, self_pairs = 0;
+    double t_bound_ms = 0, t_iter_ms = 0, seconds = 0;
+    int status = GOSMA_RUNNING;
+    bool active = false;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+
+static void delete_solve(Solve *v) {
+    if (!v) return;
+    for (int k = 0; k < 4; ++k)
+        if (v->ev[k]) cudaEventDestroy(v->ev[k]);
+    delete v;
+}
+
+static Solve *solve_of(gosma_ctx *ctx) { return ctx->bnb ? ((BnbState *)ctx->bnb)->solve : nullptr; }
+
+static void fill_result(gosma_ctx *ctx, const Solve &v, gosma_result *out) {
     memset(out, 0, sizeof *out);
-    const double c22 = ctx->c22, eps_f = o.eps * c22;
-    const double inf = INFINITY;
-    double dstar = inf;
-    double best[6] = {0, 0, 0, 0.5 * (dom.t_lo[0] + dom.t_hi[0]), 0.5 * (dom.t_lo[1] + dom.t_hi[1]),
-                      0.5 * (dom.t_lo[2] + dom.t_hi[2])};
-    // root: the cube circumscribing the pi-ball times the translation cuboid
-    Node root;
-    memset(&root, 0, sizeof root);
-    root.lb = -inf;
-    root.psit = (float)M_PI;
-    s->cur = 0;
-    uint32_t rkey = order_key(-INFINITY);
-    cudaError_t e = cudaMemcpyAsync(s->q[0], &root, sizeof root, cudaMemcpyHostToDevice, ctx->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(s->keys[0], &rkey, sizeof rkey, cudaMemcpyHostToDevice, ctx->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(s->dstar, &dstar, sizeof dstar, cudaMemcpyHostToDevice, ctx->stream);
-    Status init;
-    memset(&init, 0, sizeof init);
-    init.tail = 1;
-    init.minkey = rkey;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(s->st, &init, sizeof init, cudaMemcpyHostToDevice, ctx->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "bnb init");
-    unsigned long long tail = 1, live = 1;
-    double dlb = -inf;
-    long long nodes = 0, iters = 0, sma_calls = 0, peak = 1;
-    int status = GOSMA_OPTIMAL;
-    Refiner ref{ctx};
-    for (;;) {
-        if (live == 0) {
-            dlb = dstar;
-            break;
-        }
-        if (dstar - dlb <= eps_f) break;
-        if (o.max_nodes > 0 && nodes >= o.max_nodes) {
-            status = GOSMA_NODE_LIMIT;
-            break;
-        }
-        if (o.max_seconds > 0 && seconds() > o.max_seconds) {
-            status = GOSMA_TIME_LIMIT;
-            break;
-        }
-        int np = (int)(live < (unsigned long long)o.pop ? live : (unsigned long long)o.pop);
-        if (tail + 8ULL * np > cap || (tail > 4ULL * live && tail > (1ULL << 20))) {
-            unsigned long long nt = 0;
-            rc = compact(ctx, s, tail, &nt);
-            if (rc) return rc;
-            tail = nt;
-            live = nt;
-            e = cudaMemcpyAsync(&s->st->tail, &tail, sizeof tail, cudaMemcpyHostToDevice, ctx->stream);
-            if (e != cudaSuccess) return cuda_fail(ctx, e, "set tail");
-            if (live == 0) {
-                dlb = dstar;
-                break;
-            }
-            np = (int)(live < (unsigned long long)o.pop ? live : (unsigned long long)o.pop);
-            if (tail + 8ULL * np > cap) {
-                status = GOSMA_QUEUE_FULL;
-                break;
-            }
-        }
-        rc = iterate(ctx, dom, s, tail, np);
-        if (rc) return rc;
-        const Status &h = *s->h_st;
-        nodes += 8LL * np;
-        iters += 1;
-        tail = h.tail;
-        live = live - np + h.appended;
-        if ((long long)live > peak) peak = (long long)live;
-        if (h.best_child >= 0 && h.best_ub < dstar) {
-            CubeGeom g;
-            decode(h.best_node, dom, g);
-            double x[6] = {g.r0[0], g.r0[1], g.r0[2], g.t0[0], g.t0[1], g.t0[2]};
-            double f0 = 0;
-            double g6[6];
-            rc = ref.fg(x, &f0, g6);  // exact objective at the centre
-            if (rc) return rc;
-            double f1 = f0, x1[6];
-            memcpy(x1, x, sizeof x);
-            if (o.use_sma) {
-                rc = ref.run(x1, &f1, o.sma_max_iter);
-                if (rc) return rc;
-                ++sma_calls;
-                if (!(f1 < f0)) {
-                    f1 = f0;
-                    memcpy(x1, x, sizeof x);
-                }
-            }
-            if (f1 < dstar) {
-                dstar = f1;
-                memcpy(best, x1, sizeof best);
-                e = cudaMemcpyAsync(s->dstar, &dstar, sizeof dstar, cudaMemcpyHostToDevice, ctx->stream);
-                if (e != cudaSuccess) return cuda_fail(ctx, e, "set d*");
-            }
-        }
-        dlb = h.minkey == DEAD ? dstar : (double)key_value(h.minkey);
-        if (dlb > dstar) dlb = dstar;
-    }
-    // canonical angle-axis vector, |r| <= pi
+    double best[6];
+    memcpy(best, v.best, sizeof best);
     double rn = sqrt(best[0] * best[0] + best[1] * best[1] + best[2] * best[2]);
-    if (rn > M_PI) {
+    if (rn > M_PI) {  // canonical angle-axis vector, |r| <= pi
         double k = (rn - 2.0 * M_PI) / rn;
         for (int a = 0; a < 3; ++a) best[a] *= k;
     }
@@ -915,16 +845,199 @@ extern "C" int gosma_bnb_solve(gosma_ctx *ctx, const gosma_opts *opts_in, gosma_
         out->t[k] = best[3 + k];
     }
     rodrigues_host(out->r, out->R);
-    out->objective = dstar;
-    out->objective_norm = dstar / c22 + 1.0;
-    out->lower_bound = dlb;
-    out->gap_norm = (dstar - dlb) / c22;
+    const double c22 = ctx->c22;
+    out->objective = v.dstar;
+    out->objective_norm = v.dstar / c22 + 1.0;
+    out->lower_bound = v.dlb;
+    out->gap_norm = (v.dstar - v.dlb) / c22;
     out->c22 = c22;
-    out->nodes = nodes;
-    out->iterations = iters;
-    out->sma_calls = sma_calls;
-    out->queue_peak = peak;
-    out->seconds = seconds();
-    out->status = status;
+    out->nodes = v.nodes;
+    out->iterations = v.iters;
+    out->sma_calls = v.sma_calls;
+    out->queue_peak = v.peak;
+    out->seconds = v.seconds;
+    out->status = v.status;
+    out->cross_pairs = v.cross_pairs;
+    out->self_pairs = v.self_pairs;
+    out->bound_ms = v.t_bound_ms;
+    out->iteration_ms = v.t_iter_ms;
+    out->queue_size = (long long)v.live;
+    out->launches = ctx->launches;
+}
+
+}  // namespace gosma
+
+using namespace gosma;
+
+extern "C" int gosma_bnb_start(gosma_ctx *ctx, const gosma_opts *opts_in) {
+    if (!ctx) return GOSMA_EINVAL;
+    ctx->err.clear();
+    if (!ctx->have_mix || !ctx->have_dom) return fail(ctx, GOSMA_ENOTREADY, "bnb_start: set mixtures and domain first");
+    gosma_opts o;
+    memset(&o, 0, sizeof o);
+    o.eps = 0.1;
+    o.pop = 1024;
+    o.use_sma = 1;
+    o.sma_max_iter = 100;
+    if (opts_in) o = *opts_in;
+    if (!(o.eps >= 0) || o.pop < 1 || o.pop > 131072)
+        return fail(ctx, GOSMA_EINVAL, "bnb_start: need eps >= 0 and 1 <= pop <= 131072");
+    if (o.sma_max_iter <= 0) o.sma_max_iter = 100;
+    unsigned long long cap = o.queue_capacity > 0 ? (unsigned long long)o.queue_capacity : (1ULL << 24);
+    if (cap < 16ULL * o.pop) cap = 16ULL * o.pop;
+    if (cap > (1ULL << 31)) return fail(ctx, GOSMA_EINVAL, "bnb_start: queue_capacity above 2^31");
+    cudaSetDevice(ctx->device);
+    BnbState *s = nullptr;
+    int rc = alloc_state(ctx, cap, o.pop, &s);
+    if (rc) return rc;
+    if (!s->solve) s->solve = new Solve();
+    Solve &v = *s->solve;
+    cudaEvent_t ev[4];
+    memcpy(ev, v.ev, sizeof ev);
+    v = Solve();
+    memcpy(v.ev, ev, sizeof ev);
+    for (int k = 0; k < 4; ++k)
+        if (!v.ev[k] && cudaEventCreate(&v.ev[k]) != cudaSuccess) return fail(ctx, GOSMA_ECUDA, "cudaEventCreate");
+    v.o = o;
+    for (int k = 0; k < 3; ++k) {
+        v.dom.t_lo[k] = ctx->t_lo[k];
+        v.dom.t_hi[k] = ctx->t_hi[k];
+        v.best[3 + k] = 0.5 * (ctx->t_lo[k] + ctx->t_hi[k]);
+    }
+    v.eps_f = o.eps * ctx->c22;
+    // root: the cube circumscribing the pi-ball times the translation cuboid (Algorithm 1)
+    Node root;
+    memset(&root, 0, sizeof root);
+    root.lb = -INFINITY;
+    root.psit = (float)M_PI;
+    s->cur = 0;
+    uint32_t rkey = order_key(-INFINITY);
+    double dstar = INFINITY;
+    Status init;
+    memset(&init, 0, sizeof init);
+    init.tail = 1;
+    init.minkey = rkey;
+    cudaError_t e = cudaMemcpyAsync(s->q[0], &root, sizeof root, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->keys[0], &rkey, sizeof rkey, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->dstar, &dstar, sizeof dstar, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->st, &init, sizeof init, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "bnb_start");
+    v.tail = 1;
+    v.live = 1;
+    v.peak = 1;
+    v.active = true;
     return GOSMA_OK;
+}
+
+extern "C" int gosma_bnb_step(gosma_ctx *ctx, int max_iters, gosma_result *out) {
+    if (!ctx) return GOSMA_EINVAL;
+    ctx->err.clear();
+    Solve *vp = solve_of(ctx);
+    if (!vp || !vp->active) return fail(ctx, GOSMA_ENOTREADY, "bnb_step: call gosma_bnb_start first");
+    Solve &v = *vp;
+    BnbState *s = (BnbState *)ctx->bnb;
+    cudaSetDevice(ctx->device);
+    auto t0 = std::chrono::steady_clock::now();
+    const double base_seconds = v.seconds;
+    auto seconds = [&]() {
+        return base_seconds + std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    };
+    Refiner ref{ctx};
+    cudaError_t e;
+    int rc;
+    for (int it = 0; (max_iters <= 0 || it < max_iters) && v.status == GOSMA_RUNNING; ++it) {
+        // Algorithm 1: stop when d* - (lowest lower bound in the queue) <= eps
+        if (v.live == 0) {
+            v.dlb = v.dstar;
+            v.status = GOSMA_OPTIMAL;
+            break;
+        }
+        if (v.dstar - v.dlb <= v.eps_f) {
+            v.status = GOSMA_OPTIMAL;
+            break;
+        }
+        if (v.o.max_nodes > 0 && v.nodes >= v.o.max_nodes) {
+            v.status = GOSMA_NODE_LIMIT;
+            break;
+        }
+        if (v.o.max_seconds > 0 && seconds() > v.o.max_seconds) {
+            v.status = GOSMA_TIME_LIMIT;
+            break;
+        }
+        int np = (int)(v.live < (unsigned long long)v.o.pop ? v.live : (unsigned long long)v.o.pop);
+        if (v.tail + 8ULL * np > s->cap || (v.tail > 4ULL * v.live && v.tail > (1ULL << 20))) {
+            unsigned long long nt = 0;
+            rc = compact(ctx, s, v.tail, &nt);
+            if (rc) return rc;
+            v.tail = nt;
+            v.live = nt;
+            e = cudaMemcpyAsync(&s->st->tail, &v.tail, sizeof v.tail, cudaMemcpyHostToDevice, ctx->stream);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "set tail");
+            if (v.live == 0) {
+                v.dlb = v.dstar;
+                v.status = GOSMA_OPTIMAL;
+                break;
+            }
+            np = (int)(v.live < (unsigned long long)v.o.pop ? v.live : (unsigned long long)v.o.pop);
+            if (v.tail + 8ULL * np > s->cap) {
+                v.status = GOSMA_QUEUE_FULL;
+                break;
+            }
+        }
+        long long self_children = 0;
+        rc = iterate(ctx, v.dom, s, v.tail, np, v.ev, &self_children);
+        if (rc) return rc;
+        float ms_b = 0, ms_i = 0;
+        cudaEventElapsedTime(&ms_b, v.ev[1], v.ev[2]);
+        cudaEventElapsedTime(&ms_i, v.ev[0], v.ev[3]);
+        v.t_bound_ms += ms_b;
+        v.t_iter_ms += ms_i;
+        const Status &h = *s->h_st;
+        v.nodes += 8LL * np;
+        v.iters += 1;
+        v.cross_pairs += 8LL * np * ctx->n1 * ctx->n2;
+        v.self_pairs += self_children * (long long)ctx->n1 * (ctx->n1 - 1) / 2;
+        v.tail = h.tail;
+        v.live = v.live - np + h.appended;
+        if ((long long)v.live > v.peak) v.peak = (long long)v.live;
+        if (h.best_child >= 0 && h.best_ub < v.dstar) {
+            // the FP32 upper bound beat d*: evaluate f exactly, then refine (SMA)
+            CubeGeom g;
+            decode(h.best_node, v.dom, g);
+            double x[6] = {g.r0[0], g.r0[1], g.r0[2], g.t0[0], g.t0[1], g.t0[2]};
+            double f0 = 0, g6[6];
+            rc = ref.fg(x, &f0, g6);
+            if (rc) return rc;
+            double f1 = f0, x1[6];
+            memcpy(x1, x, sizeof x);
+            if (v.o.use_sma) {
+                rc = ref.run(x1, &f1, v.o.sma_max_iter);
+                if (rc) return rc;
+                ++v.sma_calls;
+                if (!(f1 < f0)) {
+                    f1 = f0;
+                    memcpy(x1, x, sizeof x);
+                }
+            }
+            if (f1 < v.dstar) {
+                v.dstar = f1;
+                memcpy(v.best, x1, sizeof x1);
+                e = cudaMemcpyAsync(s->dstar, &v.dstar, sizeof v.dstar, cudaMemcpyHostToDevice, ctx->stream);
+                if (e != cudaSuccess) return cuda_fail(ctx, e, "set d*");
+            }
+        }
+        v.dlb = h.minkey == DEAD ? v.dstar : (double)key_value(h.minkey);
+        if (v.dlb > v.dstar) v.dlb = v.dstar;
+    }
+    v.seconds = seconds();
+    if (out) fill_result(ctx, v, out);
+    return GOSMA_OK;
+}
+
+extern "C" int gosma_bnb_solve(gosma_ctx *ctx, const gosma_opts *opts, gosma_result *out) {
+    if (!out) return gosma::fail(ctx, GOSMA_EINVAL, "bnb_solve: null result");
+    int rc = gosma_bnb_start(ctx, opts);
+    if (rc) return rc;
+    return gosma_bnb_step(ctx, 0, out);
 }

@@ -54,6 +54,7 @@ static int launch_t(gosma_ctx *ctx, const gosma_cube *d_cubes, int n, gosma_boun
     long long grid = (long long)ctx->sm_count * per_sm;
     if (grid > n) grid = n;
     kern<<<(int)grid, BLOCK, smem, ctx->stream>>>(ctx->mix, d_cubes, n, d_out);
+    ++ctx->launches;
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "launch(bounds)");
     return GOSMA_OK;

@@ -291,7 +291,6 @@ __device__ void cube_bounds(const MixDev &mx, const CubeGeom &g, bool need_self,
     dsl.zero();
     dsu.zero();
     const double zeta2d = mx.zeta * mx.zeta;
-    const float zeta2 = (float)zeta2d;
     const float thx = (float)g.thw[0], thy = (float)g.thw[1], thz = (float)g.thw[2];
     for (int i = tid; i < n1; i += BLOCK) {
         const double *p = mx.mu1 + 3 * i;
@@ -299,19 +298,18 @@ __device__ void cube_bounds(const MixDev &mx, const CubeGeom &g, bool need_self,
         double cd2 = cxd * cxd + cyd * cyd + czd * czd;
         if (cd2 < zeta2d) atomicOr(&cs.centre_infeasible, 1);
         bool inside = fabs(cxd) <= g.thw[0] && fabs(cyd) <= g.thw[1] && fabs(czd) <= g.thw[2];
-        // distance to the cuboid (differences in FP64) and to its far corner
-        float ex = (float)fmax(fabs(cxd) - g.thw[0], 0.0);
-        float ey = (float)fmax(fabs(cyd) - g.thw[1], 0.0);
-        float ez = (float)fmax(fabs(czd) - g.thw[2], 0.0);
+        // squared distances to the cuboid and to its far corner (FP64, rounded once)
+        double exd = fmax(fabs(cxd) - g.thw[0], 0.0), eyd = fmax(fabs(cyd) - g.thw[1], 0.0),
+               ezd = fmax(fabs(czd) - g.thw[2], 0.0);
+        double fxd = fabs(cxd) + g.thw[0], fyd = fabs(cyd) + g.thw[1], fzd = fabs(czd) + g.thw[2];
+        double dmin2d = exd * exd + eyd * eyd + ezd * ezd, dmax2d = fxd * fxd + fyd * fyd + fzd * fzd;
+        if (dmax2d < zeta2d) atomicOr(&cs.infeasible, 1);
         float cx = (float)cxd, cy = (float)cyd, cz = (float)czd;
-        float fx = fabsf(cx) + thx, fy = fabsf(cy) + thy, fz = fabsf(cz) + thz;
-        float dmin2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-        float dmax2 = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
-        if (dmax2 * (1.f + 8.f * U) < zeta2) atomicOr(&cs.infeasible, 1);
         float is2 = mx.inv_sig2[i];
-        // kappa range over the feasible part of the cuboid (nearest point clamped to zeta)
-        float a = fmaf(fmaxf(dmin2, zeta2), is2, 1.f) * (1.f - 8.f * U);
-        float b = fmaf(dmax2, is2, 1.f) * (1.f + 8.f * U);
+        // kappa range over the feasible part of the cuboid (nearest point clamped to zeta);
+        // each end carries at most 3u (rounding of d^2, of 1/sigma^2, and the fma)
+        float a = fmaf((float)fmax(dmin2d, zeta2d), is2, 1.f) * (1.f - 4.f * U);
+        float b = fmaf((float)dmax2d, is2, 1.f) * (1.f + 4.f * U);
         float d2 = (float)cd2;
         float k0 = fmaf(d2, is2, 1.f);
         // unit direction v_i: FP32 rsqrt refined by one FP64 Newton step, split hi/lo

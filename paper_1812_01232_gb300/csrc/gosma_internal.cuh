@@ -129,6 +129,9 @@ struct gosma_ctx {
 
     // branch-and-bound state (bnb.cu)
     void *bnb = nullptr;
+
+    // number of kernels this context has launched
+    long long launches = 0;
 };
 
 namespace gosma {

@@ -207,8 +207,11 @@ int objective_grad_device(gosma_ctx *ctx, int count, const double *h_x, double *
     cudaError_t e = cudaMemcpyAsync(dx, hp, bx, cudaMemcpyHostToDevice, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "copy poses");
     obj_prep<<<dim3((n1 + 127) / 128, count), 128, 0, ctx->stream>>>(ctx->mix, count, dx, di);
+    ++ctx->launches;
     obj_pairs<<<dim3(nblk, count), OBJ_BLOCK, 0, ctx->stream>>>(ctx->mix, count, dx, di, dp, nblk);
+    ++ctx->launches;
     obj_final<<<(count + 63) / 64, 64, 0, ctx->stream>>>(count, dx, dp, nblk, dout);
+    ++ctx->launches;
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "launch(objective)");
     double *ho = hp + 6 * count;
@@ -271,7 +274,9 @@ int setup_constants(gosma_ctx *ctx, float *Q2, float *inv_sig2, float *phi1f, do
     cudaError_t e = cudaMalloc(&dpart, sizeof(double) * nb);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(setup)");
     setup_image<<<nb, 256, 0, ctx->stream>>>(ctx->mix, Q2, dpart);
+    ++ctx->launches;
     setup_model<<<(ctx->n1 + 255) / 256, 256, 0, ctx->stream>>>(ctx->mix, inv_sig2, phi1f);
+    ++ctx->launches;
     double hp[nb];
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(hp, dpart, sizeof hp, cudaMemcpyDeviceToHost, ctx->stream);
@@ -319,6 +324,7 @@ int selftest_approx(gosma_ctx *ctx, double measured[5], double assumed[5]) {
     e = cudaMemsetAsync(d, 0, sizeof h, ctx->stream);
     if (e == cudaSuccess) {
         approx_selftest<<<4 * ctx->sm_count, 256, 0, ctx->stream>>>(d);
+        ++ctx->launches;
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, sizeof h, cudaMemcpyDeviceToHost, ctx->stream);

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libgosma.so")
 
 GOSMA_OK = 0
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "ENOTREADY"}
-STATUS = {0: "optimal", 1: "node_limit", 2: "time_limit", 3: "queue_full"}
+STATUS = {0: "optimal", 1: "node_limit", 2: "time_limit", 3: "queue_full", 4: "running"}
 
 D = C.POINTER(C.c_double)
 
@@ -40,7 +40,9 @@ class Result(C.Structure):
                 ("objective_norm", C.c_double), ("lower_bound", C.c_double), ("gap_norm", C.c_double),
                 ("c22", C.c_double), ("nodes", C.c_longlong), ("iterations", C.c_longlong),
                 ("sma_calls", C.c_longlong), ("queue_peak", C.c_longlong), ("seconds", C.c_double),
-                ("status", C.c_int)]
+                ("status", C.c_int), ("cross_pairs", C.c_longlong), ("self_pairs", C.c_longlong),
+                ("bound_ms", C.c_double), ("iteration_ms", C.c_double), ("queue_size", C.c_longlong),
+                ("launches", C.c_longlong)]
 
 
 # exported symbols and their signatures (restype, argtypes); the header is the authority
@@ -55,7 +57,10 @@ SIGNATURES = {
     "gosma_eval_objective": (C.c_int, [C.c_void_p, D, D, D]),
     "gosma_eval_objective_grad": (C.c_int, [C.c_void_p, C.c_int, D, D, D]),
     "gosma_bnb_solve": (C.c_int, [C.c_void_p, C.POINTER(Opts), C.POINTER(Result)]),
+    "gosma_bnb_start": (C.c_int, [C.c_void_p, C.POINTER(Opts)]),
+    "gosma_bnb_step": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(Result)]),
     "gosma_selftest_approx": (C.c_int, [C.c_void_p, D, D]),
+    "gosma_kernel_launches": (C.c_longlong, [C.c_void_p]),
 }
 
 _lib = None
@@ -204,18 +209,42 @@ class Gosma:
         return f, g
 
     # ---------------------------------------------------------------- branch-and-bound
-    def bnb_solve(self, eps=0.1, pop=1024, max_nodes=0, max_seconds=0.0, use_sma=True, sma_max_iter=100,
-                  queue_capacity=0):
-        o = Opts(float(eps), int(pop), int(max_nodes), float(max_seconds), int(bool(use_sma)), int(sma_max_iter),
-                 int(queue_capacity))
-        r = Result()
-        self._check(self.L.gosma_bnb_solve(self.h, C.byref(o), C.byref(r)), "bnb_solve")
+    @staticmethod
+    def _opts(eps, pop, max_nodes, max_seconds, use_sma, sma_max_iter, queue_capacity):
+        return Opts(float(eps), int(pop), int(max_nodes), float(max_seconds), int(bool(use_sma)), int(sma_max_iter),
+                    int(queue_capacity))
+
+    @staticmethod
+    def _result(r):
         return {
             "f": r.objective, "f_norm": r.objective_norm, "lb": r.lower_bound, "gap_norm": r.gap_norm,
             "c22": r.c22, "R": np.array(r.R[:]).reshape(3, 3), "r": np.array(r.r[:]), "t": np.array(r.t[:]),
             "nodes": r.nodes, "iterations": r.iterations, "sma_calls": r.sma_calls, "queue_peak": r.queue_peak,
             "seconds": r.seconds, "status": r.status, "status_name": STATUS.get(r.status, str(r.status)),
+            "cross_pairs": r.cross_pairs, "self_pairs": r.self_pairs, "bound_ms": r.bound_ms,
+            "iteration_ms": r.iteration_ms, "queue_size": r.queue_size, "launches": r.launches,
         }
+
+    def bnb_solve(self, eps=0.1, pop=1024, max_nodes=0, max_seconds=0.0, use_sma=True, sma_max_iter=100,
+                  queue_capacity=0):
+        """Algorithm 1 to termination; returns the certificate and the pose."""
+        o = self._opts(eps, pop, max_nodes, max_seconds, use_sma, sma_max_iter, queue_capacity)
+        r = Result()
+        self._check(self.L.gosma_bnb_solve(self.h, C.byref(o), C.byref(r)), "bnb_solve")
+        return self._result(r)
+
+    def bnb_start(self, eps=0.1, pop=1024, max_nodes=0, max_seconds=0.0, use_sma=True, sma_max_iter=100,
+                  queue_capacity=0):
+        o = self._opts(eps, pop, max_nodes, max_seconds, use_sma, sma_max_iter, queue_capacity)
+        self._check(self.L.gosma_bnb_start(self.h, C.byref(o)), "bnb_start")
+
+    def bnb_step(self, max_iters=1):
+        r = Result()
+        self._check(self.L.gosma_bnb_step(self.h, int(max_iters), C.byref(r)), "bnb_step")
+        return self._result(r)
+
+    def kernel_launches(self):
+        return int(self.L.gosma_kernel_launches(self.h))
 
     def selftest_approx(self):
         m = np.zeros(5)

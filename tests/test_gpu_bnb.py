@@ -1,0 +1,111 @@
+"""GPU branch-and-bound (Algorithm 1) against the FP64 oracle.
+
+* the certified optimum agrees with the oracle's within eps (normalised,
+  times C22), and each side's lower bound stays below the other's optimum;
+* on noise-free data the true pose is recovered (Sec. 6 success criterion);
+* the stepping interface, limits and queue overflow behave as documented.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_1812_01232_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "bnb_tiny_oracle.json")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1812_01232_gb300 import build
+    build.build()
+    from paper_1812_01232_gb300.gosma import Gosma
+    c = Gosma(0)
+    yield c
+    c.close()
+
+
+def _rot_err(R, Rgt):
+    return np.arccos(np.clip((np.trace(R.T @ Rgt) - 1) / 2, -1, 1))
+
+
+def _noise_free(seed, n1, sigma):
+    p = synth.noise_free_problem(seed, n1=n1)
+    p["sigma1"] = np.full(n1, sigma)
+    p["kappa2"] = (np.linalg.norm(p["mu1"] - p["t_gt"], axis=1) / sigma) ** 2 + 1
+    return p
+
+
+@pytest.mark.parametrize("seed", [2, 3])
+def test_noise_free_recovery(ctx, oracle_mod, seed):
+    p = _noise_free(seed, 4, 0.1)
+    ctx.set_problem(p)
+    r = ctx.bnb_solve(eps=1e-2, pop=64, max_seconds=120)
+    c22 = oracle_mod.c22(oracle_mod.Mixtures.from_problem(p))
+    assert r["status_name"] == "optimal"
+    assert r["c22"] == pytest.approx(c22, rel=1e-12)
+    assert r["gap_norm"] <= 1e-2
+    assert r["f"] == pytest.approx(-c22, abs=1e-2 * c22)
+    assert r["lb"] <= -c22 + 1e-9
+    assert _rot_err(r["R"], p["R_gt"]) < 0.1
+    assert np.linalg.norm(r["t"] - p["t_gt"]) < 0.05 * np.linalg.norm(p["t_gt"]) + 1e-3
+    # the reported objective is f at the reported pose (FP64, checked by the oracle)
+    f = oracle_mod.objective_r(oracle_mod.Mixtures.from_problem(p), r["r"], r["t"])
+    assert f == pytest.approx(r["f"], rel=1e-10, abs=1e-12)
+
+
+@pytest.mark.parametrize("seed", [1000, 1001, 1002])
+def test_tiny_problem_matches_oracle_certificate(ctx, oracle_mod, seed):
+    """10 x 8 components, eps = 1e-3: the GPU optimum and the stored oracle
+    optimum (tests/golden/make_bnb_golden.py) certify each other."""
+    gold = json.load(open(GOLDEN))[str(seed)]
+    p = synth.tiny_problem(seed)
+    ctx.set_problem(p)
+    r = ctx.bnb_solve(eps=p["eps"], pop=1024, max_seconds=300)
+    assert r["status_name"] == "optimal"
+    epsf = p["eps"] * gold["c22"]
+    assert r["c22"] == pytest.approx(gold["c22"], rel=1e-12)
+    assert abs(r["f"] - gold["f"]) <= epsf
+    assert r["lb"] <= gold["f"] + 1e-9 and gold["lb"] <= r["f"] + 1e-9
+    mix = oracle_mod.Mixtures.from_problem(p)
+    assert oracle_mod.objective_r(mix, r["r"], r["t"]) == pytest.approx(r["f"], rel=1e-10)
+    # both poses are optimal to within eps of each other's certificate
+    assert oracle_mod.objective_r(mix, gold["r"], gold["t"]) - epsf <= r["f"]
+
+
+def test_step_interface_matches_solve(ctx):
+    p = _noise_free(2, 4, 0.1)
+    ctx.set_problem(p)
+    a = ctx.bnb_solve(eps=2e-2, pop=128, max_seconds=120)
+    ctx.bnb_start(eps=2e-2, pop=128, max_seconds=120)
+    r = ctx.bnb_step(3)
+    assert r["status_name"] == "running" and r["iterations"] == 3
+    while r["status_name"] == "running":
+        r = ctx.bnb_step(50)
+    for k in ("f", "lb", "nodes", "iterations", "sma_calls"):
+        assert r[k] == a[k], k
+    assert r["bound_ms"] > 0 and r["iteration_ms"] >= r["bound_ms"]
+
+
+def test_limits_and_queue_capacity(ctx):
+    p = synth.paper_scale_problem(2000)
+    ctx.set_problem(p)
+    r = ctx.bnb_solve(eps=p["eps"], pop=512, max_nodes=20000)
+    assert r["status_name"] == "node_limit" and r["nodes"] >= 20000
+    assert r["lb"] <= r["f"]
+    r = ctx.bnb_solve(eps=p["eps"], pop=512, queue_capacity=16 * 512)
+    assert r["status_name"] == "queue_full"
+    assert r["lb"] <= r["f"]
+    r = ctx.bnb_solve(eps=p["eps"], pop=512, max_seconds=0.5)
+    assert r["status_name"] == "time_limit"
+
+
+def test_step_before_start_is_an_error():
+    from paper_1812_01232_gb300.gosma import Gosma, GosmaError
+    c = Gosma(0)
+    c.set_problem(synth.tiny_problem(3))
+    with pytest.raises(GosmaError):
+        c.bnb_step(1)
+    c.close()
