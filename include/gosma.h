@@ -141,6 +141,24 @@ int gosma_eval_objective(gosma_ctx *ctx, const double r[3], const double t[3], d
  * `count` poses x (count x 6: r then t, host pointers). */
 int gosma_eval_objective_grad(gosma_ctx *ctx, int count, const double *x, double *f, double *grad);
 
+/* Allocation-free variant of gosma_eval_objective_grad (the paper has no
+ * counterpart; it exists for callers that cannot let the library allocate
+ * device memory while they run: real-time loops that size all memory at
+ * start-up and cannot afford cudaMalloc's implicit device synchronisation,
+ * and applications that own the device-memory budget themselves).
+ * d_x: device pointer, count x 6 doubles (r then t per pose).
+ * d_out: device pointer, count x 7 doubles (f, df/dr (3), df/dt (3) per pose).
+ * Both stay owned by the caller.  The kernels run asynchronously on the
+ * context's stream; no host copy, no synchronisation, no allocation.
+ * Scratch lives in one fixed 8 MiB device array inside the library, held by
+ * every GPU that loads it until the process exits: the call returns
+ * GOSMA_EINVAL when count * (128 n1 + 56 ceil((n1^2 + n1 n2) / 4096)) bytes
+ * exceeds it.  All calls on a device share that array, so calls whose kernels
+ * overlap on the GPU (e.g. issued on different streams) race.  The first call
+ * on each device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture. */
+int gosma_eval_objective_grad_noalloc(gosma_ctx *ctx, int count, const double *d_x, double *d_out);
+
 /* Algorithm 1 (GOSMA) on the device: branch, bound, prune and select run in
  * device kernels; d* is always an FP64 evaluation of f, refined by SMA
  * (Sec. 5) whenever a sub-cube's upper bound beats it.  opts may be NULL

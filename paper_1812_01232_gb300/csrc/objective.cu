@@ -4,6 +4,8 @@
 //   - a self-test of the FP32 approximate instructions the bound kernel uses.
 #include <math.h>
 
+#include <mutex>
+
 #include "gosma_internal.cuh"
 
 namespace gosma {
@@ -342,3 +344,79 @@ int selftest_approx(gosma_ctx *ctx, double measured[5], double assumed[5]) {
 }
 
 }  // namespace gosma
+
+namespace gosma {
+
+// ---------------------------------------------------------------- allocation-free objective
+// Some callers of this library cannot let it allocate device memory once they
+// are running: real-time tracking loops that size every buffer at start-up and
+// must not stall on cudaMalloc's implicit device synchronisation, and host
+// applications that own the whole device-memory budget and forbid libraries
+// from allocating behind their back.  gosma_eval_objective_grad_noalloc serves
+// them: the caller passes device buffers for the poses and the results, and the
+// kernels' scratch lives in the fixed array below instead of in cudaMalloc'd
+// memory.
+//
+// The array is a file-scope device variable, so every GPU that loads the
+// library holds NOALLOC_SCRATCH_BYTES for as long as the library stays loaded.
+// All calls on a device share it: two calls whose kernels overlap on the GPU
+// (for example on two streams) race on it.  The scratch needs no clearing:
+// every byte a call reads was written earlier in the same call.
+constexpr size_t NOALLOC_SCRATCH_BYTES = (size_t)8 << 20;  // 8 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+// Device address of g_noalloc_scratch per device, looked up once per device
+// (in host code the array's name is only a host-side stand-in, not a device
+// address).
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_ptr[128];
+
+static int noalloc_scratch(gosma_ctx *ctx, void **out) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (ctx->device < 0 || ctx->device >= 128) return fail(ctx, GOSMA_EINVAL, "device index out of range");
+    if (!g_noalloc_ptr[ctx->device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return cuda_fail(ctx, e, "cudaGetSymbolAddress(no-alloc scratch)");
+        g_noalloc_ptr[ctx->device] = p;
+    }
+    *out = g_noalloc_ptr[ctx->device];
+    return GOSMA_OK;
+}
+
+}  // namespace gosma
+
+extern "C" int gosma_eval_objective_grad_noalloc(gosma_ctx *ctx, int count, const double *d_x, double *d_out) {
+    using namespace gosma;
+    if (!ctx) return GOSMA_EINVAL;
+    ctx->err.clear();
+    if (!ctx->have_mix) return fail(ctx, GOSMA_ENOTREADY, "eval_objective_grad_noalloc: set mixtures first");
+    if (count < 0 || (count > 0 && (!d_x || !d_out)))
+        return fail(ctx, GOSMA_EINVAL, "eval_objective_grad_noalloc: bad poses or output");
+    if (count == 0) return GOSMA_OK;
+    const int n1 = ctx->n1, n2 = ctx->n2;
+    long long total = (long long)n1 * n1 + (long long)n1 * n2;
+    int nblk = (int)((total + OBJ_CHUNK - 1) / OBJ_CHUNK);
+    size_t bi = sizeof(double) * OBJ_STRIDE * (size_t)n1 * count;
+    size_t bp = sizeof(double) * 7 * (size_t)nblk * count;
+    bi = (bi + 255) & ~(size_t)255;
+    if (bi + bp > NOALLOC_SCRATCH_BYTES)
+        return fail(ctx, GOSMA_EINVAL,
+                    "eval_objective_grad_noalloc: count * (128 n1 + 56 ceil((n1^2 + n1 n2) / 4096)) bytes "
+                    "exceeds the 8 MiB scratch; use fewer poses per call");
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
+    void *scratch = nullptr;
+    int rc = noalloc_scratch(ctx, &scratch);
+    if (rc) return rc;
+    double *di = (double *)scratch, *dp = (double *)((char *)scratch + bi);
+    obj_prep<<<dim3((n1 + 127) / 128, count), 128, 0, ctx->stream>>>(ctx->mix, count, d_x, di);
+    ++ctx->launches;
+    obj_pairs<<<dim3(nblk, count), OBJ_BLOCK, 0, ctx->stream>>>(ctx->mix, count, d_x, di, dp, nblk);
+    ++ctx->launches;
+    obj_final<<<(count + 63) / 64, 64, 0, ctx->stream>>>(count, d_x, dp, nblk, d_out);
+    ++ctx->launches;
+    e = cudaGetLastError();
+    return e == cudaSuccess ? GOSMA_OK : cuda_fail(ctx, e, "launch(objective, no-alloc)");
+}
+

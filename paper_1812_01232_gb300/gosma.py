@@ -56,6 +56,7 @@ SIGNATURES = {
     "gosma_eval_bounds_detail": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int]),
     "gosma_eval_objective": (C.c_int, [C.c_void_p, D, D, D]),
     "gosma_eval_objective_grad": (C.c_int, [C.c_void_p, C.c_int, D, D, D]),
+    "gosma_eval_objective_grad_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "gosma_bnb_solve": (C.c_int, [C.c_void_p, C.POINTER(Opts), C.POINTER(Result)]),
     "gosma_bnb_start": (C.c_int, [C.c_void_p, C.POINTER(Opts)]),
     "gosma_bnb_step": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(Result)]),
@@ -207,6 +208,16 @@ class Gosma:
         g = np.empty((n, 6))
         self._check(self.L.gosma_eval_objective_grad(self.h, n, _p(x), _p(f), _p(g)), "eval_objective_grad")
         return f, g
+
+    def eval_objective_grad_noalloc(self, x_dev, out_dev):
+        """Allocation-free f and gradient for callers that cannot let the
+        library allocate: x_dev (count, 6) and out_dev (count, 7) are CUDA
+        float64 tensors owned by the caller; asynchronous on the context stream."""
+        n = x_dev.shape[0]
+        self._check(self.L.gosma_eval_objective_grad_noalloc(self.h, n, C.c_void_p(x_dev.data_ptr()),
+                                                             C.c_void_p(out_dev.data_ptr())),
+                    "eval_objective_grad_noalloc")
+        return out_dev
 
     # ---------------------------------------------------------------- branch-and-bound
     @staticmethod
