@@ -152,7 +152,7 @@ int gosma_eval_objective_grad(gosma_ctx *ctx, int count, const double *x, double
  * context's stream; no host copy, no synchronisation, no allocation.
  * Scratch lives in one fixed 8 MiB device array inside the library, held by
  * every GPU that loads it until the process exits: the call returns
- * GOSMA_EINVAL when count * (128 n1 + 56 ceil((n1^2 + n1 n2) / 4096)) bytes
+ * GOSMA_EINVAL when count * (128 n1 + 56 ceil((n1^2 + n1 n2) / 512)) bytes
  * exceeds it.  All calls on a device share that array, so calls whose kernels
  * overlap on the GPU (e.g. issued on different streams) race.  The first call
  * on each device looks up the array's device address (cudaGetSymbolAddress);

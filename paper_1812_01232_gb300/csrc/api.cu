@@ -40,7 +40,7 @@ int ensure_pinned(gosma_ctx *ctx, size_t bytes) {
     return GOSMA_OK;
 }
 
-int setup_constants(gosma_ctx *ctx, float *Q2, float *inv_sig2, float *phi1f, double *c22_out);
+int setup_constants(gosma_ctx *ctx, double *c22_out);
 int selftest_approx(gosma_ctx *ctx, double measured[5], double assumed[5]);
 
 __global__ void split_bounds(const gosma_bound *__restrict__ in, int n, double *lb, double *ub) {
@@ -82,6 +82,7 @@ void gosma_destroy(gosma_ctx *ctx) {
     if (ctx->d_mix) cudaFree(ctx->d_mix);
     if (ctx->d_stage) cudaFree(ctx->d_stage);
     if (ctx->d_obj) cudaFree(ctx->d_obj);
+    if (ctx->d_rot) cudaFree(ctx->d_rot);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
     delete ctx;
 }
@@ -115,7 +116,7 @@ int gosma_set_mixtures(gosma_ctx *ctx, int n1, const double *mu1, const double *
         return fail(ctx, GOSMA_EINVAL, "set_mixtures: mixture weights must sum to 1");
     cudaSetDevice(ctx->device);
     size_t nd = 3 * (size_t)n1 + 2 * n1 + 3 * (size_t)n2 + 2 * n2;
-    size_t nf = 2 * (size_t)n1 + 2 * (size_t)n2;
+    size_t nf = 8 * (size_t)n1 + 8 * (size_t)n2;
     size_t bytes = nd * sizeof(double) + nf * sizeof(float) + 256;
     void *d = nullptr;
     cudaError_t e = cudaMalloc(&d, bytes);
@@ -125,14 +126,22 @@ int gosma_set_mixtures(gosma_ctx *ctx, int n1, const double *mu1, const double *
            *dphi2 = dk2 + n2;
     float *pf = (float *)(dphi2 + n2);
     float *inv_sig2 = pf, *phi1f = pf + n1, *k2f = phi1f + n1, *Q2 = k2f + n2;
+    float *mu1h = Q2 + n2, *mu1l = mu1h + 3 * n1, *mu2h = mu1l + 3 * n1, *mu2l = mu2h + 3 * n2;
     std::vector<float> hk2(n2);
     for (int j = 0; j < n2; ++j) hk2[j] = (float)kappa2[j];
+    // image mean directions are used as exact unit vectors: normalise them (FP64)
+    std::vector<double> mu2n(mu2, mu2 + 3 * (size_t)n2);
+    for (int j = 0; j < n2; ++j) {
+        double *m = &mu2n[3 * (size_t)j];
+        double nn = sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+        for (int k = 0; k < 3; ++k) m[k] /= nn;
+    }
     struct {
         void *dst;
         const void *src;
         size_t n;
     } cp[] = {{dmu1, mu1, 3 * (size_t)n1 * 8}, {dsig, sigma1, (size_t)n1 * 8}, {dphi1, phi1, (size_t)n1 * 8},
-              {dmu2, mu2, 3 * (size_t)n2 * 8}, {dk2, kappa2, (size_t)n2 * 8},  {dphi2, phi2, (size_t)n2 * 8},
+              {dmu2, mu2n.data(), 3 * (size_t)n2 * 8}, {dk2, kappa2, (size_t)n2 * 8},  {dphi2, phi2, (size_t)n2 * 8},
               {k2f, hk2.data(), (size_t)n2 * 4}};
     for (auto &c : cp) {
         e = cudaMemcpyAsync(c.dst, c.src, c.n, cudaMemcpyHostToDevice, ctx->stream);
@@ -154,6 +163,10 @@ int gosma_set_mixtures(gosma_ctx *ctx, int n1, const double *mu1, const double *
     mx.Q2 = Q2;
     mx.kappa2d = dk2;
     mx.phi2d = dphi2;
+    mx.mu1h = mu1h;
+    mx.mu1l = mu1l;
+    mx.mu2h = mu2h;
+    mx.mu2l = mu2l;
     mx.zeta = ctx->zeta;
     void *old = ctx->d_mix;
     MixDev old_mix = ctx->mix;
@@ -162,7 +175,7 @@ int gosma_set_mixtures(gosma_ctx *ctx, int n1, const double *mu1, const double *
     ctx->n1 = n1;
     ctx->n2 = n2;
     double c22 = 0;
-    int rc = setup_constants(ctx, Q2, inv_sig2, phi1f, &c22);
+    int rc = setup_constants(ctx, &c22);
     if (rc) {
         cudaFree(d);
         ctx->mix = old_mix;
@@ -176,7 +189,7 @@ int gosma_set_mixtures(gosma_ctx *ctx, int n1, const double *mu1, const double *
     ctx->h_mu1.assign(mu1, mu1 + 3 * (size_t)n1);
     ctx->h_sigma1.assign(sigma1, sigma1 + n1);
     ctx->h_phi1.assign(phi1, phi1 + n1);
-    ctx->h_mu2.assign(mu2, mu2 + 3 * (size_t)n2);
+    ctx->h_mu2 = mu2n;
     ctx->h_kappa2.assign(kappa2, kappa2 + n2);
     ctx->h_phi2.assign(phi2, phi2 + n2);
     ctx->have_mix = true;

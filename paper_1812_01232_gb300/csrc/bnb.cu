@@ -286,24 +286,34 @@ __global__ void ext_scatter(uint32_t *__restrict__ keys, const Node *__restrict_
 }
 
 // ---------------------------------------------------------------- 3. bound
+// Pre-pass for the children: one thread per child.
+__global__ void cube_prep_children(Domain dom, const Node *__restrict__ parents, int np, CubePrep *__restrict__ prep) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= 8 * np) return;
+    const Node p = parents[c >> 3];
+    Node ch = child_of(p, c & 7, split_rotation(p));
+    CubeGeom g;
+    decode(ch, dom, g);
+    cube_prepare(g.r0, g.rhw, g.t0, g.thw, prep[c]);
+}
+
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK)
-    bound_children(MixDev mx, Domain dom, const Node *__restrict__ parents, int np, Node *__restrict__ kids,
-                   double *__restrict__ kid_ub, unsigned int *__restrict__ n_self) {
+    bound_children(MixDev mx, Domain dom, df zeta2, const Node *__restrict__ parents, int np,
+                   const CubePrep *__restrict__ prep, Node *__restrict__ kids, double *__restrict__ kid_ub,
+                   unsigned int *__restrict__ n_self) {
     extern __shared__ float smem_f[];
     __shared__ CubeShared cs;
     __shared__ CubeSums sums;
     SmemArrays sm = carve(smem_f, mx.n1, mx.n2);
     const double inf = __longlong_as_double(0x7ff0000000000000LL);
     for (int c = blockIdx.x; c < 8 * np; c += gridDim.x) {
-        const Node p = parents[c >> 3];
-        bool rot = split_rotation(p);
-        Node ch = child_of(p, c & 7, rot);
-        CubeGeom g;
-        decode(ch, dom, g);
-        bool need_self = !(ch.flags & 1u);
-        cube_bounds<BLOCK>(mx, g, need_self, cs, sm, sums);
+        // a child keeps its parent's cuboid, and so its self sums, after a rotation split
+        const bool need_self = !(parents[c >> 3].flags & 1u) || !split_rotation(parents[c >> 3]);
+        cube_bounds<BLOCK>(mx, prep[c], zeta2, need_self, cs, sm, sums);
         if (threadIdx.x == 0) {
+            const Node p = parents[c >> 3];
+            Node ch = child_of(p, c & 7, split_rotation(p));
             if (need_self) atomicAdd(n_self, 1u);
             double sl = need_self ? sums.self_lb : p.self_lb;
             double sc = need_self ? sums.self_c : p.self_c;
@@ -506,6 +516,7 @@ struct BnbState {
     Status *st = nullptr;
     Status *h_st = nullptr;  // pinned
     unsigned int *kid_rot = nullptr;  // children that computed their own self sums
+    CubePrep *rot = nullptr;          // pre-pass of the children
     unsigned int *h_flags = nullptr;  // pinned copy
     struct Solve *solve = nullptr;
 };
@@ -529,6 +540,7 @@ static void free_state(BnbState *s) {
     cudaFree(s->total);
     cudaFree(s->st);
     cudaFree(s->kid_rot);
+    cudaFree(s->rot);
     if (s->h_st) cudaFreeHost(s->h_st);
     if (s->h_flags) cudaFreeHost(s->h_flags);
     delete_solve(s->solve);
@@ -568,6 +580,7 @@ static int alloc_state(gosma_ctx *ctx, unsigned long long cap, int pop, BnbState
     ALLOC(s->total, sizeof(unsigned long long));
     ALLOC(s->st, sizeof(Status));
     ALLOC(s->kid_rot, sizeof(unsigned int));
+    ALLOC(s->rot, sizeof(CubePrep) * 8 * pop);
 #undef ALLOC
     if (e == cudaSuccess) e = cudaMallocHost((void **)&s->h_st, sizeof(Status));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&s->h_flags, sizeof(unsigned int));
@@ -594,7 +607,12 @@ static int launch_children(gosma_ctx *ctx, const Domain &dom, BnbState *s, int n
     if (grid > 8LL * np) grid = 8LL * np;
     e = cudaMemsetAsync(s->kid_rot, 0, sizeof(unsigned int), ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "memset(children)");
-    kern<<<(int)grid, BLOCK, smem, ctx->stream>>>(ctx->mix, dom, s->parents, np, s->kids, s->kid_ub, s->kid_rot);
+    cube_prep_children<<<(8 * np + 127) / 128, 128, 0, ctx->stream>>>(dom, s->parents, np, s->rot);
+    ++ctx->launches;
+    df z2;
+    split_double(ctx->zeta * ctx->zeta, z2.h, z2.l);
+    kern<<<(int)grid, BLOCK, smem, ctx->stream>>>(ctx->mix, dom, z2, s->parents, np, s->rot, s->kids, s->kid_ub,
+                                                   s->kid_rot);
     ++ctx->launches;
     e = cudaGetLastError();
     return e == cudaSuccess ? GOSMA_OK : cuda_fail(ctx, e, "launch(children)");

@@ -5,23 +5,22 @@
 
 namespace gosma {
 
+// Pre-pass: one thread per cube.
+__global__ void cube_prep_cubes(const gosma_cube *__restrict__ cubes, int n, CubePrep *__restrict__ prep) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < n) cube_prepare(cubes[c].r0, cubes[c].r_hw, cubes[c].t0, cubes[c].t_hw, prep[c]);
+}
+
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK) eval_bounds_kernel(MixDev mx, const gosma_cube *__restrict__ cubes, int n,
+                                                            const CubePrep *__restrict__ prep, df zeta2,
                                                             gosma_bound *__restrict__ out) {
     extern __shared__ float smem_f[];
     __shared__ CubeShared cs;
     __shared__ CubeSums sums;
     SmemArrays sm = carve(smem_f, mx.n1, mx.n2);
     for (int c = blockIdx.x; c < n; c += gridDim.x) {
-        const gosma_cube &q = cubes[c];
-        CubeGeom g;
-        for (int k = 0; k < 3; ++k) {
-            g.r0[k] = q.r0[k];
-            g.t0[k] = q.t0[k];
-            g.thw[k] = q.t_hw[k];
-        }
-        g.rhw = q.r_hw;
-        cube_bounds<BLOCK>(mx, g, true, cs, sm, sums);
+        cube_bounds<BLOCK>(mx, prep[c], zeta2, true, cs, sm, sums);
         if (threadIdx.x == 0) {
             gosma_bound o;
             finish_bound(sums, o);
@@ -42,7 +41,7 @@ int bounds_block_size(int n1, int n2) {
 }
 
 template <int BLOCK>
-static int launch_t(gosma_ctx *ctx, const gosma_cube *d_cubes, int n, gosma_bound *d_out) {
+static int launch_t(gosma_ctx *ctx, const gosma_cube *d_cubes, int n, gosma_bound *d_out, const CubePrep *d_rot) {
     size_t smem = bounds_smem_bytes(ctx->n1, ctx->n2);
     auto kern = eval_bounds_kernel<BLOCK>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -53,7 +52,9 @@ static int launch_t(gosma_ctx *ctx, const gosma_cube *d_cubes, int n, gosma_boun
     if (per_sm < 1) return fail(ctx, GOSMA_EINVAL, "mixtures too large for one thread block's shared memory");
     long long grid = (long long)ctx->sm_count * per_sm;
     if (grid > n) grid = n;
-    kern<<<(int)grid, BLOCK, smem, ctx->stream>>>(ctx->mix, d_cubes, n, d_out);
+    df z2;
+    split_double(ctx->zeta * ctx->zeta, z2.h, z2.l);
+    kern<<<(int)grid, BLOCK, smem, ctx->stream>>>(ctx->mix, d_cubes, n, d_rot, z2, d_out);
     ++ctx->launches;
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "launch(bounds)");
@@ -62,11 +63,23 @@ static int launch_t(gosma_ctx *ctx, const gosma_cube *d_cubes, int n, gosma_boun
 
 int launch_bounds(gosma_ctx *ctx, const gosma_cube *d_cubes, int n, gosma_bound *d_out) {
     if (n <= 0) return GOSMA_OK;
+    size_t need = sizeof(CubePrep) * (size_t)n;
+    if (need > ctx->rot_bytes) {
+        if (ctx->d_rot) cudaFree(ctx->d_rot);
+        ctx->d_rot = nullptr;
+        ctx->rot_bytes = 0;
+        cudaError_t e = cudaMalloc(&ctx->d_rot, need);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(cube pre-pass)");
+        ctx->rot_bytes = need;
+    }
+    CubePrep *rot = (CubePrep *)ctx->d_rot;
+    cube_prep_cubes<<<(n + 127) / 128, 128, 0, ctx->stream>>>(d_cubes, n, rot);
+    ++ctx->launches;
     switch (bounds_block_size(ctx->n1, ctx->n2)) {
-    case 32: return launch_t<32>(ctx, d_cubes, n, d_out);
-    case 64: return launch_t<64>(ctx, d_cubes, n, d_out);
-    case 128: return launch_t<128>(ctx, d_cubes, n, d_out);
-    default: return launch_t<256>(ctx, d_cubes, n, d_out);
+    case 32: return launch_t<32>(ctx, d_cubes, n, d_out, rot);
+    case 64: return launch_t<64>(ctx, d_cubes, n, d_out, rot);
+    case 128: return launch_t<128>(ctx, d_cubes, n, d_out, rot);
+    default: return launch_t<256>(ctx, d_cubes, n, d_out, rot);
     }
 }
 

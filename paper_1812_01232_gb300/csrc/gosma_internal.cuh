@@ -29,6 +29,8 @@ struct MixDev {
     const float *Q2;       // n2: phi_2j kappa_2j / (1 - e^{-2 kappa_2j})  (computed in FP64)
     const double *kappa2d; // n2
     const double *phi2d;   // n2
+    const float *mu1h, *mu1l;  // n1 x 3: mu1 as double-floats (hi, lo)
+    const float *mu2h, *mu2l;  // n2 x 3: unit mu2 as double-floats
     double zeta;           // point-to-camera limit (Sec. 4.1)
 };
 
@@ -126,6 +128,10 @@ struct gosma_ctx {
     // objective scratch
     void *d_obj = nullptr;
     size_t obj_bytes = 0;
+
+    // per-cube rotation pre-pass (gosma_eval_bounds)
+    void *d_rot = nullptr;
+    size_t rot_bytes = 0;
 
     // branch-and-bound state (bnb.cu)
     void *bnb = nullptr;

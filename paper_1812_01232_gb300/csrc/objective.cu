@@ -47,7 +47,7 @@ __device__ void rodrigues_dev(const double r[3], double R[9]) {
 //   v(3) d kappa lZ dlZ Rv(3) dk(3) pad(3)
 constexpr int OBJ_STRIDE = 16;
 constexpr int OBJ_BLOCK = 256;
-constexpr int OBJ_CHUNK = 4096;  // pair indices per block
+constexpr int OBJ_CHUNK = 512;  // pair indices per block
 
 __global__ void obj_prep(MixDev mx, int count, const double *__restrict__ x, double *__restrict__ idata) {
     int p = blockIdx.y;
@@ -234,7 +234,8 @@ int objective_grad_device(gosma_ctx *ctx, int count, const double *h_x, double *
 // linear-form pair terms), FP64 rounded once, and C22 = sum_jj' phi phi
 // Z(|k_j mu_j + k_j' mu_j'|)/(Z(k_j) Z(k_j')) (2 pi times the integral of
 // p2^2, proof of Lemma 1) as per-block partial sums.
-__global__ void setup_image(MixDev mx, float *Q2, double *c22part) {
+__global__ void setup_image(MixDev mx, double *c22part) {
+    float *Q2 = const_cast<float *>(mx.Q2), *mh = const_cast<float *>(mx.mu2h), *ml = const_cast<float *>(mx.mu2l);
     __shared__ double red[8];
     double acc = 0.0;
     const int n2 = mx.n2;
@@ -251,6 +252,12 @@ __global__ void setup_image(MixDev mx, float *Q2, double *c22part) {
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n2; j += gridDim.x * blockDim.x) {
         double k = mx.kappa2d[j];
         Q2[j] = (float)(mx.phi2d[j] * k / -expm1(-2.0 * k));
+        for (int c = 0; c < 3; ++c) {
+            double m = mx.mu2[3 * j + c];
+            float h = (float)m;
+            mh[3 * j + c] = h;
+            ml[3 * j + c] = (float)(m - (double)h);
+        }
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
@@ -262,22 +269,30 @@ __global__ void setup_image(MixDev mx, float *Q2, double *c22part) {
     }
 }
 
-__global__ void setup_model(MixDev mx, float *inv_sig2, float *phi1f) {
+__global__ void setup_model(MixDev mx) {
+    float *inv_sig2 = const_cast<float *>(mx.inv_sig2), *phi1f = const_cast<float *>(mx.phi1f);
+    float *mh = const_cast<float *>(mx.mu1h), *ml = const_cast<float *>(mx.mu1l);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < mx.n1; i += gridDim.x * blockDim.x) {
         double s = mx.sigma1d[i];
         inv_sig2[i] = (float)(1.0 / (s * s));
         phi1f[i] = (float)mx.phi1d[i];
+        for (int c = 0; c < 3; ++c) {
+            double m = mx.mu1[3 * i + c];
+            float h = (float)m;
+            mh[3 * i + c] = h;
+            ml[3 * i + c] = (float)(m - (double)h);
+        }
     }
 }
 
-int setup_constants(gosma_ctx *ctx, float *Q2, float *inv_sig2, float *phi1f, double *c22_out) {
+int setup_constants(gosma_ctx *ctx, double *c22_out) {
     const int nb = 64;
     double *dpart = nullptr;
     cudaError_t e = cudaMalloc(&dpart, sizeof(double) * nb);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(setup)");
-    setup_image<<<nb, 256, 0, ctx->stream>>>(ctx->mix, Q2, dpart);
+    setup_image<<<nb, 256, 0, ctx->stream>>>(ctx->mix, dpart);
     ++ctx->launches;
-    setup_model<<<(ctx->n1 + 255) / 256, 256, 0, ctx->stream>>>(ctx->mix, inv_sig2, phi1f);
+    setup_model<<<(ctx->n1 + 255) / 256, 256, 0, ctx->stream>>>(ctx->mix);
     ++ctx->launches;
     double hp[nb];
     e = cudaGetLastError();
@@ -402,7 +417,7 @@ extern "C" int gosma_eval_objective_grad_noalloc(gosma_ctx *ctx, int count, cons
     bi = (bi + 255) & ~(size_t)255;
     if (bi + bp > NOALLOC_SCRATCH_BYTES)
         return fail(ctx, GOSMA_EINVAL,
-                    "eval_objective_grad_noalloc: count * (128 n1 + 56 ceil((n1^2 + n1 n2) / 4096)) bytes "
+                    "eval_objective_grad_noalloc: count * (128 n1 + 56 ceil((n1^2 + n1 n2) / 512)) bytes "
                     "exceeds the 8 MiB scratch; use fewer poses per call");
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");

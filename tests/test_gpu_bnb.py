@@ -63,7 +63,7 @@ def test_tiny_problem_matches_oracle_certificate(ctx, oracle_mod, seed):
     gold = json.load(open(GOLDEN))[str(seed)]
     p = synth.tiny_problem(seed)
     ctx.set_problem(p)
-    r = ctx.bnb_solve(eps=p["eps"], pop=1024, max_seconds=300)
+    r = ctx.bnb_solve(eps=p["eps"], pop=1024, max_seconds=300, queue_capacity=1 << 27)
     assert r["status_name"] == "optimal"
     epsf = p["eps"] * gold["c22"]
     assert r["c22"] == pytest.approx(gold["c22"], rel=1e-12)
