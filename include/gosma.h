@@ -94,7 +94,19 @@ typedef struct {
     double iteration_ms;     /* device time of whole iterations (CUDA events)  */
     long long queue_size;    /* live sub-cubes in the queue                    */
     long long launches;      /* kernels the context has launched so far        */
+    int block_size;          /* threads per cube chosen by the batch autotuner  */
 } gosma_result;
+
+/* One independent alignment problem for gosma_bnb_solve_batch: the mixtures
+ * (as in gosma_set_mixtures, host pointers, read during the call only) and
+ * the translation domain (as in gosma_set_domain). */
+typedef struct {
+    int n1;
+    const double *mu1, *sigma1, *phi1;
+    int n2;
+    const double *mu2, *kappa2, *phi2;
+    double t_lo[3], t_hi[3], zeta;
+} gosma_problem;
 
 /* Create a context on CUDA device `device`, issuing all work on `stream`
  * (a cudaStream_t; NULL means the legacy default stream).  The context owns
@@ -165,6 +177,26 @@ int gosma_eval_objective_grad_noalloc(gosma_ctx *ctx, int count, const double *d
  * (eps = 0.1, pop = 1024, no limits, SMA on).  Equivalent to
  * gosma_bnb_start followed by gosma_bnb_step(ctx, 0, out). */
 int gosma_bnb_solve(gosma_ctx *ctx, const gosma_opts *opts, gosma_result *out);
+
+/* Algorithm 1 for nprob (<= 65535) independent problems at once, each with
+ * its own mixtures, domain and queue segment.  Every iteration pops the
+ * opts->pop best hypercubes (exact radix select on the FP32 lower-bound key,
+ * ties in queue order) from each unfinished problem, bounds the children of
+ * all problems in one persistent kernel launch, and replaces each problem's
+ * d* by the exact FP64 objective at its best child's centre when smaller.
+ * Every 8 iterations the host refines each problem whose d* improved with
+ * L-BFGS (SMA, Sec. 5) in lock step, all such problems' poses in one FP64
+ * launch per step (opts->use_sma, opts->sma_max_iter).  The iteration runs
+ * as a captured CUDA graph on a private stream; the bound kernel's block size
+ * is picked by timing the candidates (results[k].block_size).
+ * results[k].seconds is the device time from the start to problem k's
+ * certificate.  opts->queue_capacity is per problem (default 2^18
+ * sub-cubes; two buffers of that size are allocated per problem),
+ * opts->max_nodes per problem.  opts may be NULL (eps = 0.1, pop = 64, SMA
+ * on).  Problems with invalid data make the call fail with GOSMA_EINVAL
+ * before any work. */
+int gosma_bnb_solve_batch(gosma_ctx *ctx, int nprob, const gosma_problem *probs, const gosma_opts *opts,
+                          gosma_result *results);
 
 /* Start a branch-and-bound run (the queue holds the root Omega_r x Omega_t).
  * The run's device state belongs to the context until the next start. */

@@ -31,30 +31,10 @@
 #include <chrono>
 #include <vector>
 
-#include "bounds_core.cuh"
+#include "bnb_common.cuh"
+#include "lbfgs.h"
 
 namespace gosma {
-
-struct Node {
-    double lb;
-    double self_lb, self_c;  // self sums of the translation cuboid (valid when flags & 1)
-    uint32_t r[3], t[3];     // cell coordinates at levels lr, lt
-    uint16_t lr, lt;
-    float psit;              // max_i psi_t over the cuboid
-    uint32_t flags;
-    uint32_t pad;
-};
-static_assert(sizeof(Node) == 64, "node layout");
-
-struct Domain {
-    double t_lo[3], t_hi[3];
-};
-
-constexpr uint32_t DEAD = 0xFFFFFFFFu;
-constexpr int MAX_LEVEL = 30;
-constexpr int SEL_BLOCK = 256;
-constexpr int SEL_ITEMS = 8;  // keys per thread in the scan kernels
-constexpr int SEL_TILE = SEL_BLOCK * SEL_ITEMS;
 
 struct Status {
     unsigned long long tail;      // slots used in the queue
@@ -71,55 +51,6 @@ struct Status {
     unsigned int sel_bin[3];
     unsigned int sel_need[3];
 };
-
-__host__ __device__ inline uint32_t order_key(float f) {
-    uint32_t u;
-    memcpy(&u, &f, 4);
-    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
-}
-__host__ __device__ inline float key_value(uint32_t k) {
-    uint32_t u = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
-    float f;
-    memcpy(&f, &u, 4);
-    return f;
-}
-
-__host__ __device__ inline double psi_r_level(int lr) {
-    double p = sqrt(3.0) * ldexp(M_PI, -lr);
-    return p < M_PI ? p : M_PI;
-}
-
-__host__ __device__ inline void decode(const Node &n, const Domain &d, CubeGeom &g) {
-    double rh = ldexp(M_PI, -(int)n.lr);
-    g.rhw = rh;
-    for (int k = 0; k < 3; ++k) {
-        g.r0[k] = -M_PI + (2.0 * n.r[k] + 1.0) * rh;
-        double th = ldexp(d.t_hi[k] - d.t_lo[k], -(int)n.lt - 1);
-        g.thw[k] = th;
-        g.t0[k] = d.t_lo[k] + (2.0 * n.t[k] + 1.0) * th;
-    }
-}
-
-// Child k of a parent (Sec. 4.1: the split halves the rotation cube or the
-// translation cuboid, whichever has the greater angular uncertainty).
-__host__ __device__ inline bool split_rotation(const Node &p) {
-    if (p.lr >= MAX_LEVEL) return false;
-    if (p.lt >= MAX_LEVEL) return true;
-    return psi_r_level(p.lr) >= (double)p.psit;
-}
-
-__host__ __device__ inline Node child_of(const Node &p, int k, bool rot) {
-    Node c = p;
-    if (rot) {
-        c.lr = p.lr + 1;
-        for (int a = 0; a < 3; ++a) c.r[a] = 2u * p.r[a] + ((k >> a) & 1u);
-    } else {
-        c.lt = p.lt + 1;
-        for (int a = 0; a < 3; ++a) c.t[a] = 2u * p.t[a] + ((k >> a) & 1u);
-        c.flags &= ~1u;  // the cuboid changed: self sums must be recomputed
-    }
-    return c;
-}
 
 // ---------------------------------------------------------------- 1. select
 __global__ void sel_hist(const uint32_t *__restrict__ keys, unsigned long long n, int pass, const Status *st,
@@ -710,22 +641,21 @@ static int compact(gosma_ctx *ctx, BnbState *s, unsigned long long tail, unsigne
 }
 
 // ---------------------------------------------------------------- SMA (Sec. 5)
-// Local refinement: L-BFGS (memory 8) with a backtracking Armijo line search
-// on the FP64 objective and gradient computed on the device.  Trial poses
-// that leave the translation domain or come within zeta of a mean are
-// rejected, so the result is always a feasible pose.
+// Local refinement of the incumbent: the L-BFGS machine of lbfgs.h driven
+// with one device evaluation of the FP64 objective and gradient per step.
 struct Refiner {
     gosma_ctx *ctx;
     long long evals = 0;
-    bool feasible(const double x[6]) const {
-        for (int k = 0; k < 3; ++k)
-            if (x[3 + k] < ctx->t_lo[k] || x[3 + k] > ctx->t_hi[k]) return false;
-        double z2 = ctx->zeta * ctx->zeta;
-        for (int i = 0; i < ctx->n1; ++i) {
-            double d0 = ctx->h_mu1[3 * i] - x[3], d1 = ctx->h_mu1[3 * i + 1] - x[4], d2 = ctx->h_mu1[3 * i + 2] - x[5];
-            if (d0 * d0 + d1 * d1 + d2 * d2 < z2) return false;
+    Feasibility feas() const {
+        Feasibility F;
+        for (int k = 0; k < 3; ++k) {
+            F.t_lo[k] = ctx->t_lo[k];
+            F.t_hi[k] = ctx->t_hi[k];
         }
-        return true;
+        F.zeta = ctx->zeta;
+        F.mu1 = ctx->h_mu1.data();
+        F.n1 = ctx->n1;
+        return F;
     }
     int fg(const double x[6], double *f, double g[6]) {
         ++evals;
@@ -733,78 +663,17 @@ struct Refiner {
     }
     // Minimise from x (in place); f holds f(x) on entry and the result on exit.
     int run(double x[6], double *f, int max_iter) {
-        const int M = 8;
-        double S[M][6], Y[M][6], rho[M], g[6], fx;
-        int rc = fg(x, &fx, g);
-        if (rc) return rc;
-        int head = 0, used = 0;
-        for (int it = 0; it < max_iter; ++it) {
-            double gn = 0;
-            for (int k = 0; k < 6; ++k) gn = fmax(gn, fabs(g[k]));
-            if (!(gn > 1e-10)) break;
-            double d[6], al[M];
-            for (int k = 0; k < 6; ++k) d[k] = -g[k];
-            for (int h = 0; h < used; ++h) {
-                int j = (head - 1 - h + M) % M;
-                double a = 0;
-                for (int k = 0; k < 6; ++k) a += S[j][k] * d[k];
-                al[h] = rho[j] * a;
-                for (int k = 0; k < 6; ++k) d[k] -= al[h] * Y[j][k];
-            }
-            double scale = 0.01 / gn;
-            if (used) {
-                int j = (head - 1 + M) % M;
-                double sy = 0, yy = 0;
-                for (int k = 0; k < 6; ++k) {
-                    sy += S[j][k] * Y[j][k];
-                    yy += Y[j][k] * Y[j][k];
-                }
-                scale = sy / yy;
-            }
-            for (int k = 0; k < 6; ++k) d[k] *= scale;
-            for (int h = used - 1; h >= 0; --h) {
-                int j = (head - 1 - h + M) % M;
-                double b = 0;
-                for (int k = 0; k < 6; ++k) b += Y[j][k] * d[k];
-                b *= rho[j];
-                for (int k = 0; k < 6; ++k) d[k] += S[j][k] * (al[h] - b);
-            }
-            double slope = 0;
-            for (int k = 0; k < 6; ++k) slope += g[k] * d[k];
-            if (!(slope < 0)) {  // lost descent: restart from a scaled gradient step
-                used = 0;
-                for (int k = 0; k < 6; ++k) d[k] = -g[k] * (0.01 / gn);
-                slope = 0;
-                for (int k = 0; k < 6; ++k) slope += g[k] * d[k];
-            }
-            double step = 1.0, xn[6], gn6[6], fn = 0;
-            bool ok = false;
-            for (int ls = 0; ls < 40 && !ok; ++ls, step *= 0.5) {
-                for (int k = 0; k < 6; ++k) xn[k] = x[k] + step * d[k];
-                if (!feasible(xn)) continue;
-                rc = fg(xn, &fn, gn6);
-                if (rc) return rc;
-                ok = fn <= fx + 1e-4 * step * slope;
-            }
-            if (!ok) break;
-            double sy = 0;
-            for (int k = 0; k < 6; ++k) {
-                S[head][k] = xn[k] - x[k];
-                Y[head][k] = gn6[k] - g[k];
-                sy += S[head][k] * Y[head][k];
-            }
-            if (sy > 0) {
-                rho[head] = 1.0 / sy;
-                head = (head + 1) % M;
-                used = used < M ? used + 1 : M;
-            }
-            double fprev = fx;
-            memcpy(x, xn, sizeof(double) * 6);
-            memcpy(g, gn6, sizeof g);
-            fx = fn;
-            if (fabs(fprev - fx) <= 1e-15 * (1.0 + fabs(fx))) break;
+        Lbfgs L;
+        L.feas = feas();
+        L.start(x, max_iter);
+        double p[6], fv, gv[6];
+        while (L.want(p)) {
+            int rc = fg(p, &fv, gv);
+            if (rc) return rc;
+            L.give(fv, gv);
         }
-        *f = fx;
+        memcpy(x, L.x, sizeof(double) * 6);
+        *f = L.fx;
         return GOSMA_OK;
     }
 };

@@ -1,0 +1,1363 @@
+// Algorithm 1 for many independent problems at once (batched GOSMA).
+//
+// All problems' queues live in one node/key buffer, one segment per problem.
+// One iteration advances every unfinished problem:
+//   mp_select    one block per problem: in-place compaction of the segment
+//                when half of it is dead, the smallest live key (the
+//                problem's global lower bound) and the stopping test
+//                d* - lb <= eps, then the `pop` best hypercubes by an exact
+//                radix select (ties in queue order);
+//   mp_worklist  prefix sums of the children counts;
+//   mp_prep      per child: cell decode and the per-cube pre-pass;
+//   mp_bound     one persistent launch bounds the children of all problems
+//                (each block looks up its child's problem and mixtures);
+//   mp_append    one block per problem: children with lb < d* go to the
+//                segment's tail (block scan, in child order) and the child
+//                with the smallest upper bound becomes the candidate;
+//   mp_obj_*     the exact FP64 objective at every candidate's centre, which
+//                replaces d* when smaller.
+// The sequence is captured once in a CUDA graph and replayed; the host only
+// polls the number of finished problems.  The block size of mp_bound is
+// chosen by timing the candidates on the first iteration's children.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <vector>
+
+#include "bnb_common.cuh"
+#include "lbfgs.h"
+#include "objective_core.cuh"
+
+namespace gosma {
+
+struct ProbDev {
+    MixDev mx;
+    Domain dom;
+    double zeta, eps_f, c22;
+    unsigned long long base, cap;  // queue segment
+    df zeta2;
+};
+
+struct ProbState {
+    double dstar, lb;
+    double best_x[6];
+    unsigned long long tail, live, peak;
+    long long nodes, cross_pairs;
+    int done;  // 0 running, else 1 + GOSMA_* status
+    int done_iter;
+    int np;
+    int best_child;  // candidate child (index into the children arrays) or -1
+    double cand_x[6];
+    unsigned int minkey;  // smallest live key (atomic minimum over the chunks)
+    int cur;              // which of the two segment buffers holds the queue
+    // selection state of the current iteration
+    unsigned int sel_prefix, sel_need, sel_T, sel_quota;
+    int sel_skip;  // the threshold is already exact
+    int cmp;       // compact the segment after this iteration's pop
+    unsigned long long cmp_tail;
+};
+
+constexpr int MP_BLOCK = 512;
+constexpr int MP_ITEMS = 8;
+constexpr int MP_TILE = MP_BLOCK * MP_ITEMS;
+// queue chunks: the unit of work of the select and compaction kernels
+constexpr int CH_KEYS = 8192;
+constexpr int CH_BLOCK = 256;
+constexpr int CH_ITEMS = 8;  // keys per thread per ordered tile
+constexpr int CH_TILE = CH_BLOCK * CH_ITEMS;
+
+// Queue buffers: two segment sets (keys and nodes), one segment of `cap`
+// entries per problem in each; ProbState::cur says which holds the queue.
+struct QueueBufs {
+    uint32_t *keys[2];
+    Node *q[2];
+    unsigned int *hist;  // nprob x 2048
+    int *ch_off;         // nprob + 1: first chunk of each problem
+    int *c_lt, *c_eq, *c_out, *c_eqb, *c_live, *c_base;  // per chunk
+};
+
+// block-wide exclusive scan (blockDim.x threads, a multiple of 32, <= 1024)
+__device__ inline int mp_scan(int v, int *sh, int &total) {
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5, nw = blockDim.x >> 5;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int s = lane < nw ? sh[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < nw) sh[lane] = s;
+    }
+    __syncthreads();
+    int base = w ? sh[w - 1] : 0;
+    total = sh[nw - 1];
+    __syncthreads();
+    return base + x - v;
+}
+
+// The bin at which the running count of hist[0..nb) reaches need (1 <= need
+// <= total): *bin and the count of the bins before it.  nb is a multiple of
+// blockDim.x; every thread of the block must call it.
+__device__ inline void mp_find_bin(const unsigned int *hist, int nb, unsigned int need, int *sh, int *bin,
+                                   unsigned int *before) {
+    const int per = nb / blockDim.x, b0 = threadIdx.x * per;
+    if (threadIdx.x == 0) {  // ordered before the finder's write by the scan's barriers
+        *bin = nb - 1;
+        *before = 0;
+    }
+    unsigned int loc = 0;
+    for (int q = 0; q < per; ++q) loc += hist[b0 + q];
+    int tot;
+    const unsigned int ex = (unsigned int)mp_scan((int)loc, sh, tot);
+    if (ex < need && ex + loc >= need) {
+        unsigned int c = ex;
+        for (int q = 0; q < per; ++q) {
+            if (c + hist[b0 + q] >= need) {
+                *bin = b0 + q;
+                *before = c;
+                break;
+            }
+            c += hist[b0 + q];
+        }
+    }
+    __syncthreads();
+}
+
+// Problem owning chunk c: off[lo] <= c < off[lo + 1] (problems without
+// chunks have off[k] == off[k + 1] and are never returned).
+__device__ inline int mp_find(const int *__restrict__ off, int nprob, int c) {
+    int lo = 0, hi = nprob;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (off[mid] <= c) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------- selection
+// One iteration's pop for every problem is an exact radix select of its `pop`
+// smallest keys (11, 11 and 10 key bits) spread over fixed-size chunks of the
+// queue segments, so that all SMs share the work whatever the queue sizes:
+//   mp_chunks   chunk offsets of the running problems;
+//   mp_hist     (per pass) per-problem key histograms and the smallest key;
+//   mp_decide   lower bound, stopping test, take, first threshold bin;
+//   mp_refine   (passes 2, 3) the next threshold digits;
+//   mp_ecount / mp_escan / mp_escatter  ordered extraction: keys below the
+//               threshold, then `quota` keys equal to it in queue order;
+//   mp_ccount / mp_cscan / mp_cscatter  compaction into the other buffer
+//               when half of a segment is dead or the tail nears capacity.
+
+__global__ void mp_chunks(ProbState *__restrict__ S, int nprob, int *__restrict__ ch_off) {
+    __shared__ int sh[32];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < nprob; b0 += blockDim.x) {
+        const int k = b0 + threadIdx.x;
+        int v = 0;
+        if (k < nprob && !S[k].done) v = (int)((S[k].tail + CH_KEYS - 1) / CH_KEYS);
+        int tot;
+        int ex = mp_scan(v, sh, tot);
+        if (k < nprob) ch_off[k] = carry + ex;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) ch_off[nprob] = carry;
+}
+
+// Histogram pass 1, 2 or 3 over the chunks; pass 1 also takes the minimum.
+template <int PASS>
+__global__ void __launch_bounds__(CH_BLOCK)
+    mp_hist(const ProbDev *__restrict__ P, ProbState *__restrict__ S, QueueBufs Qb, int nprob) {
+    __shared__ unsigned int h[2048];
+    __shared__ unsigned int smin;
+    const int nch = Qb.ch_off[nprob];
+    for (int c = blockIdx.x; c < nch; c += gridDim.x) {
+        const int k = mp_find(Qb.ch_off, nprob, c);
+        const ProbState &st = S[k];
+        if (PASS > 1 && (st.np == 0 || st.sel_skip)) continue;  // uniform over the block
+        const unsigned long long j0 = (unsigned long long)(c - Qb.ch_off[k]) * CH_KEYS;
+        const unsigned long long n = st.tail;
+        const uint32_t *keys = Qb.keys[st.cur] + P[k].base;
+        const uint32_t pre = st.sel_prefix;
+        for (int b = threadIdx.x; b < 2048; b += CH_BLOCK) h[b] = 0;
+        if (threadIdx.x == 0) smin = DEAD;
+        __syncthreads();
+        unsigned int m = DEAD;
+        for (int q = threadIdx.x; q < CH_KEYS; q += CH_BLOCK) {
+            const unsigned long long i = j0 + q;
+            if (i >= n) break;
+            const uint32_t key = keys[i];
+            if (key == DEAD) continue;
+            if (PASS == 1) {
+                m = min(m, key);
+                atomicAdd(&h[key >> 21], 1u);
+            } else if (PASS == 2) {
+                if ((key >> 21) == pre) atomicAdd(&h[(key >> 10) & 2047u], 1u);
+            } else {
+                if ((key >> 10) == pre) atomicAdd(&h[key & 1023u], 1u);
+            }
+        }
+        if (PASS == 1) {
+            for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_down_sync(0xffffffffu, m, o));
+            if ((threadIdx.x & 31) == 0 && m != DEAD) atomicMin(&smin, m);
+        }
+        __syncthreads();
+        unsigned int *gh = Qb.hist + (size_t)k * 2048;
+        for (int b = threadIdx.x; b < 2048; b += CH_BLOCK)
+            if (h[b]) atomicAdd(&gh[b], h[b]);
+        if (PASS == 1 && threadIdx.x == 0 && smin != DEAD) atomicMin(&S[k].minkey, smin);
+        __syncthreads();
+    }
+}
+
+// One block per problem: lower bound and stopping test (Algorithm 1), the
+// number of hypercubes to pop, the compaction decision and the first digit of
+// the threshold key.  Leaves the problem's histogram zeroed.
+__global__ void __launch_bounds__(MP_BLOCK)
+    mp_decide(const ProbDev *__restrict__ P, ProbState *__restrict__ S, QueueBufs Qb, int pop,
+              const int *__restrict__ d_iter, long long max_nodes) {
+    __shared__ int sh[32];
+    __shared__ int s_bin;
+    __shared__ unsigned int s_before;
+    const int k = blockIdx.x, t = threadIdx.x;
+    ProbState &st = S[k];
+    unsigned int *gh = Qb.hist + (size_t)k * 2048;
+    if (st.done) {
+        if (t == 0) st.np = 0;
+        return;  // chunks of finished problems are not histogrammed
+    }
+    __shared__ unsigned long long s_live;
+    if (t == 0) {
+        const unsigned long long live = st.live;
+        int take = 0;
+        const unsigned int mk = st.minkey;
+        double lb = mk == DEAD ? st.dstar : (double)key_value(mk);
+        if (lb > st.dstar) lb = st.dstar;
+        st.lb = lb;
+        if (live == 0 || st.dstar - lb <= P[k].eps_f) {
+            st.done = 1 + GOSMA_OPTIMAL;
+            st.done_iter = *d_iter;
+        } else if (max_nodes > 0 && st.nodes >= max_nodes) {
+            st.done = 1 + GOSMA_NODE_LIMIT;
+            st.done_iter = *d_iter;
+        } else {
+            take = (int)(live < (unsigned long long)pop ? live : (unsigned long long)pop);
+        }
+        st.np = take;
+        st.nodes += 8LL * take;
+        st.live = live - take;
+        st.minkey = DEAD;  // reset for the next iteration's pass 1
+        const unsigned long long rest = live - take;
+        st.cmp = take > 0 && (st.tail >= 2 * rest + CH_KEYS || st.tail + 8ULL * pop > P[k].cap);
+        s_bin = take;
+        s_live = live;
+    }
+    __syncthreads();
+    const int take = s_bin;
+    const unsigned long long live = s_live;
+    __syncthreads();
+    if (take > 0 && (unsigned long long)take < live) {
+        mp_find_bin(gh, 2048, (unsigned)take, sh, &s_bin, &s_before);
+        if (t == 0) {
+            const unsigned int b1 = (unsigned)s_bin, need = (unsigned)take - s_before;
+            if (gh[b1] == need) {  // the whole bin is taken: the threshold is its end
+                st.sel_T = b1 == 2047u ? DEAD : (b1 + 1u) << 21;
+                st.sel_quota = 0;
+                st.sel_skip = 1;
+            } else {
+                st.sel_prefix = b1;
+                st.sel_need = need;
+                st.sel_skip = 0;
+            }
+        }
+    } else if (t == 0) {
+        st.sel_T = DEAD;  // every live key goes
+        st.sel_quota = 0;
+        st.sel_skip = 1;
+    }
+    __syncthreads();
+    for (int b = t; b < 2048; b += MP_BLOCK) gh[b] = 0;
+}
+
+// Passes 2 and 3: the next digit of the threshold from the problem's histogram.
+template <int PASS>
+__global__ void __launch_bounds__(MP_BLOCK) mp_refine(ProbState *__restrict__ S, QueueBufs Qb) {
+    __shared__ int sh[32];
+    __shared__ int s_bin;
+    __shared__ unsigned int s_before;
+    const int k = blockIdx.x, t = threadIdx.x;
+    ProbState &st = S[k];
+    if (st.np == 0 || st.sel_skip) return;
+    unsigned int *gh = Qb.hist + (size_t)k * 2048;
+    const int nb = PASS == 2 ? 2048 : 1024;
+    mp_find_bin(gh, nb, st.sel_need, sh, &s_bin, &s_before);
+    if (t == 0) {
+        const unsigned int b = (unsigned)s_bin, need = st.sel_need - s_before;
+        if (PASS == 2) {
+            const unsigned int p2 = (st.sel_prefix << 11) | b;
+            if (gh[b] == need) {
+                st.sel_T = p2 == 0x3FFFFFu ? DEAD : (p2 + 1u) << 10;
+                st.sel_quota = 0;
+                st.sel_skip = 1;
+            } else {
+                st.sel_prefix = p2;
+                st.sel_need = need;
+            }
+        } else {
+            st.sel_T = (st.sel_prefix << 10) | b;
+            st.sel_quota = need;
+            st.sel_skip = 1;
+        }
+    }
+    __syncthreads();
+    for (int b = t; b < nb; b += MP_BLOCK) gh[b] = 0;
+}
+
+// Per chunk: keys below the threshold and keys equal to it (extraction), or
+// live keys (compaction).
+template <bool CMP>
+__global__ void __launch_bounds__(CH_BLOCK)
+    mp_count(const ProbDev *__restrict__ P, const ProbState *__restrict__ S, QueueBufs Qb, int nprob) {
+    __shared__ int red[2][CH_BLOCK / 32];
+    const int nch = Qb.ch_off[nprob];
+    for (int c = blockIdx.x; c < nch; c += gridDim.x) {
+        const int k = mp_find(Qb.ch_off, nprob, c);
+        const ProbState &st = S[k];
+        if (CMP ? !st.cmp : st.np == 0) continue;
+        const unsigned long long j0 = (unsigned long long)(c - Qb.ch_off[k]) * CH_KEYS, n = st.tail;
+        const uint32_t *keys = Qb.keys[st.cur] + P[k].base;
+        const uint32_t T = st.sel_T;
+        int a = 0, b = 0;
+        for (int q = threadIdx.x; q < CH_KEYS; q += CH_BLOCK) {
+            const unsigned long long i = j0 + q;
+            if (i >= n) break;
+            const uint32_t key = keys[i];
+            if (key == DEAD) continue;
+            if (CMP) ++a;
+            else {
+                a += key < T;
+                b += key == T;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_down_sync(0xffffffffu, a, o);
+            b += __shfl_down_sync(0xffffffffu, b, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            red[0][threadIdx.x >> 5] = a;
+            red[1][threadIdx.x >> 5] = b;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int sa = 0, sb = 0;
+            for (int w = 0; w < CH_BLOCK / 32; ++w) {
+                sa += red[0][w];
+                sb += red[1][w];
+            }
+            if (CMP) Qb.c_live[c] = sa;
+            else {
+                Qb.c_lt[c] = sa;
+                Qb.c_eq[c] = sb;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// One block per problem: exclusive scans over the problem's chunks.
+template <bool CMP>
+__global__ void __launch_bounds__(MP_BLOCK)
+    mp_cscan_any(ProbState *__restrict__ S, QueueBufs Qb, int nprob) {
+    __shared__ int sh[32];
+    const int k = blockIdx.x;
+    ProbState &st = S[k];
+    if (CMP ? !st.cmp : st.np == 0) return;
+    const int c0 = Qb.ch_off[k], c1 = Qb.ch_off[k + 1];
+    const unsigned int quota = st.sel_quota;
+    long long carry_a = 0, carry_b = 0;
+    for (int b0 = c0; b0 < c1; b0 += MP_BLOCK) {
+        const int c = b0 + threadIdx.x;
+        const bool in = c < c1;
+        int ta, tb = 0;
+        if (CMP) {
+            const int ex = mp_scan(in ? Qb.c_live[c] : 0, sh, ta);
+            if (in) Qb.c_base[c] = (int)(carry_a + ex);
+        } else {
+            const int lt = in ? Qb.c_lt[c] : 0, eq = in ? Qb.c_eq[c] : 0;
+            const int exa = mp_scan(lt, sh, ta);
+            const int exb = mp_scan(eq, sh, tb);
+            if (in) {
+                const long long eqb = carry_b + exb;
+                const long long taken_before = eqb < (long long)quota ? eqb : (long long)quota;
+                Qb.c_eqb[c] = (int)eqb;
+                Qb.c_out[c] = (int)(carry_a + exa + taken_before);
+            }
+        }
+        carry_a += ta;
+        carry_b += tb;
+    }
+    if (CMP && threadIdx.x == 0) st.cmp_tail = (unsigned long long)carry_a;
+}
+
+// Per chunk, in queue order: extraction into the parents array (keys marked
+// dead), or compaction into the other buffer.
+template <bool CMP>
+__global__ void __launch_bounds__(CH_BLOCK)
+    mp_scatter(const ProbDev *__restrict__ P, const ProbState *__restrict__ S, QueueBufs Qb, int nprob,
+               Node *__restrict__ parents, int pop) {
+    __shared__ int sh[32];
+    const int nch = Qb.ch_off[nprob];
+    for (int c = blockIdx.x; c < nch; c += gridDim.x) {
+        const int k = mp_find(Qb.ch_off, nprob, c);
+        const ProbState &st = S[k];
+        if (CMP ? !st.cmp : st.np == 0) continue;
+        const unsigned long long j0 = (unsigned long long)(c - Qb.ch_off[k]) * CH_KEYS, n = st.tail;
+        const unsigned long long base = P[k].base;
+        uint32_t *keys = Qb.keys[st.cur] + base;
+        const Node *q = Qb.q[st.cur] + base;
+        uint32_t *okeys = Qb.keys[st.cur ^ 1] + base;
+        Node *oq = Qb.q[st.cur ^ 1] + base;
+        const uint32_t T = st.sel_T;
+        const unsigned int quota = st.sel_quota;
+        int out = CMP ? Qb.c_base[c] : Qb.c_out[c];
+        int eqr = CMP ? 0 : Qb.c_eqb[c];
+        for (int t0 = 0; t0 < CH_KEYS; t0 += CH_TILE) {
+            uint32_t kk[CH_ITEMS];
+            int e = 0;
+#pragma unroll
+            for (int j = 0; j < CH_ITEMS; ++j) {
+                const unsigned long long i = j0 + t0 + threadIdx.x * CH_ITEMS + j;
+                kk[j] = i < n && t0 + threadIdx.x * CH_ITEMS + j < CH_KEYS ? keys[i] : DEAD;
+                e += !CMP && kk[j] != DEAD && kk[j] == T;
+            }
+            int tot_e = 0;
+            int er = CMP ? 0 : eqr + mp_scan(e, sh, tot_e);
+            bool take[CH_ITEMS];
+            int cnt = 0;
+#pragma unroll
+            for (int j = 0; j < CH_ITEMS; ++j) {
+                bool p = false;
+                if (kk[j] != DEAD) {
+                    if (CMP) p = true;
+                    else if (kk[j] < T) p = true;
+                    else if (kk[j] == T) p = (unsigned)(er++) < quota;
+                }
+                take[j] = p;
+                cnt += p;
+            }
+            int tot;
+            int pos = out + mp_scan(cnt, sh, tot);
+#pragma unroll
+            for (int j = 0; j < CH_ITEMS; ++j)
+                if (take[j]) {
+                    const unsigned long long i = j0 + t0 + threadIdx.x * CH_ITEMS + j;
+                    if (CMP) {
+                        if ((unsigned long long)pos < P[k].cap) {  // holds when the counts agree
+                            oq[pos] = q[i];
+                            okeys[pos] = kk[j];
+                        }
+                    } else if (pos < pop) {
+                        parents[(size_t)k * pop + pos] = q[i];
+                        keys[i] = DEAD;
+                    }
+                    ++pos;
+                }
+            out += tot;
+            eqr += tot_e;
+        }
+    }
+}
+
+// Prefix sums of the children counts (one block); compacted segments take
+// over from the old buffers.
+__global__ void mp_worklist(ProbState *__restrict__ S, int nprob, int *__restrict__ off) {
+    __shared__ int sh[32];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int b0 = 0; b0 < nprob; b0 += MP_BLOCK) {
+        int k = b0 + threadIdx.x;
+        if (k < nprob && S[k].cmp) {  // the compacted copy becomes the queue
+            S[k].cur ^= 1;
+            S[k].tail = S[k].cmp_tail;
+            S[k].cmp = 0;
+        }
+        int v = k < nprob ? 8 * S[k].np : 0;
+        int tot;
+        int ex = mp_scan(v, sh, tot);
+        if (k < nprob) off[k] = carry + ex;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) off[nprob] = carry;
+}
+
+__global__ void mp_prep(const ProbDev *__restrict__ P, const int *__restrict__ off, int nprob,
+                        const Node *__restrict__ parents, int pop, CubePrep *__restrict__ prep) {
+    const int N = off[nprob];
+    for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < N; w += gridDim.x * blockDim.x) {
+        int k = mp_find(off, nprob, w), c = w - off[k];
+        const Node p = parents[(size_t)k * pop + (c >> 3)];
+        Node ch = child_of(p, c & 7, split_rotation(p));
+        CubeGeom g;
+        decode(ch, P[k].dom, g);
+        cube_prepare(g.r0, g.rhw, g.t0, g.thw, prep[w]);
+    }
+}
+
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+    mp_bound(const ProbDev *__restrict__ P, const int *__restrict__ off, int nprob, const Node *__restrict__ parents,
+             int pop, const CubePrep *__restrict__ prep, Node *__restrict__ kids, double *__restrict__ kid_ub) {
+    extern __shared__ float smem_f[];
+    __shared__ CubeShared cs;
+    __shared__ CubeSums sums;
+    const double inf = __longlong_as_double(0x7ff0000000000000LL);
+    const int N = off[nprob];
+    for (int w = blockIdx.x; w < N; w += gridDim.x) {
+        const int k = mp_find(off, nprob, w), c = w - off[k];
+        const MixDev &mx = P[k].mx;
+        SmemArrays sm = carve(smem_f, mx.n1, mx.n2);
+        const Node &pr = parents[(size_t)k * pop + (c >> 3)];
+        const bool rot = split_rotation(pr);
+        const bool need_self = !(pr.flags & 1u) || !rot;
+        cube_bounds<BLOCK>(mx, prep[w], P[k].zeta2, need_self, cs, sm, sums);
+        if (threadIdx.x == 0) {
+            const Node p = pr;
+            Node ch = child_of(p, c & 7, rot);
+            double sl = need_self ? sums.self_lb : p.self_lb;
+            double sc = need_self ? sums.self_c : p.self_c;
+            double lb, ub;
+            if (!sums.feasible) {
+                lb = ub = inf;
+            } else {
+                double Ssum = sl + 2.0 * sums.cross_ub;
+                lb = sl - 2.0 * sums.cross_ub - 1e-12 * Ssum;
+                ub = sums.centre_feasible ? sc - 2.0 * sums.cross_c : inf;
+            }
+            ch.lb = lb;
+            ch.self_lb = sl;
+            ch.self_c = sc;
+            ch.psit = sums.psi_t_max;
+            ch.flags |= 1u;
+            kids[w] = ch;
+            kid_ub[w] = ub;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(MP_BLOCK)
+    mp_append(const ProbDev *__restrict__ P, ProbState *__restrict__ S, const int *__restrict__ off,
+              const Node *__restrict__ kids, const double *__restrict__ kid_ub, QueueBufs Qb) {
+    __shared__ int sh[32];
+    __shared__ unsigned long long sbest;
+    const int k = blockIdx.x, t = threadIdx.x;
+    ProbState &st = S[k];
+    if (t == 0) {
+        sbest = ~0ULL;
+        st.best_child = -1;
+    }
+    __syncthreads();
+    const int n = 8 * st.np;
+    if (n == 0) return;
+    const int c0 = off[k];
+    const double ds = st.dstar;
+    const unsigned long long base = P[k].base, cap = P[k].cap, tail = st.tail;
+    uint32_t *keys = Qb.keys[st.cur];
+    Node *q = Qb.q[st.cur];
+    int appended = 0;
+    for (int j0 = 0; j0 < n; j0 += MP_BLOCK) {
+        int j = j0 + t;
+        bool alive = j < n && kids[c0 + j].lb < ds;
+        if (j < n && kid_ub[c0 + j] < ds) {
+            // smallest upper bound first, then smallest child index (ub order key has 44 high bits)
+            unsigned long long u = (unsigned long long)__double_as_longlong(kid_ub[c0 + j]);
+            u = (u & 0x8000000000000000ULL) ? ~u : (u | 0x8000000000000000ULL);
+            atomicMin(&sbest, (u & ~0xFFFFFULL) | (unsigned long long)j);
+        }
+        int tot;
+        int pos = mp_scan(alive ? 1 : 0, sh, tot);
+        if (alive && tail + appended + pos < cap) {
+            unsigned long long dst = base + tail + appended + pos;
+            q[dst] = kids[c0 + j];
+            keys[dst] = order_key(__double2float_rd(kids[c0 + j].lb));
+        }
+        appended += tot;
+    }
+    __syncthreads();
+    if (t == 0) {
+        unsigned long long fit = tail + appended <= cap ? appended : cap - tail;
+        st.tail = tail + fit;
+        st.live += fit;
+        if (st.live > st.peak) st.peak = st.live;
+        st.cross_pairs += (long long)n * P[k].mx.n1 * P[k].mx.n2;
+        if (fit < (unsigned long long)appended) {
+            st.done = 1 + GOSMA_QUEUE_FULL;
+            st.done_iter = -1;
+        }
+        if (sbest != ~0ULL) {
+            // the packed order kept 44 bits of ub: take the exact smallest of the candidates
+            int j = (int)(sbest & 0xFFFFFULL);
+            double bu = kid_ub[c0 + j];
+            for (int q2 = 0; q2 < n; ++q2)
+                if (kid_ub[c0 + q2] < bu) {
+                    bu = kid_ub[c0 + q2];
+                    j = q2;
+                }
+            st.best_child = c0 + j;
+            CubeGeom g;
+            decode(kids[c0 + j], P[k].dom, g);
+            for (int a = 0; a < 3; ++a) {
+                st.cand_x[a] = g.r0[a];
+                st.cand_x[3 + a] = g.t0[a];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- exact FP64 objective at the candidates
+constexpr int MPO_BLOCK = 256;
+constexpr int MPO_CHUNK = 1024;
+
+// per (problem, model component): v, Rv, kappa, log Z(kappa)  (8 doubles)
+__global__ void mp_obj_prep(const ProbDev *__restrict__ P, const ProbState *__restrict__ S,
+                            const long long *__restrict__ ioff, double *__restrict__ idata) {
+    const int k = blockIdx.y;
+    const ProbState &st = S[k];
+    if (st.best_child < 0) return;
+    const MixDev &mx = P[k].mx;
+    const double *x = st.cand_x;
+    __shared__ double R[9];
+    if (threadIdx.x == 0) rodrigues_dev(x, R);
+    __syncthreads();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < mx.n1; i += gridDim.x * blockDim.x) {
+        const double *mu = mx.mu1 + 3 * i;
+        double m0 = mu[0] - x[3], m1 = mu[1] - x[4], m2 = mu[2] - x[5];
+        double d = sqrt(m0 * m0 + m1 * m1 + m2 * m2);
+        double v0 = m0 / d, v1 = m1 / d, v2 = m2 / d, s = mx.sigma1d[i];
+        double kap = d * d / (s * s) + 1.0;  // Eq. (kappa1)
+        double *o = idata + (ioff[k] + i) * 8;
+        o[0] = v0;
+        o[1] = v1;
+        o[2] = v2;
+        o[3] = R[0] * v0 + R[1] * v1 + R[2] * v2;
+        o[4] = R[3] * v0 + R[4] * v1 + R[5] * v2;
+        o[5] = R[6] * v0 + R[7] * v1 + R[8] * v2;
+        o[6] = kap;
+        o[7] = logZ_d(kap);
+    }
+}
+
+// f (Lemma 1) = sum_ij self - 2 sum_ij cross, partial sums per block
+__global__ void __launch_bounds__(MPO_BLOCK)
+    mp_obj_pairs(const ProbDev *__restrict__ P, const ProbState *__restrict__ S, const long long *__restrict__ ioff,
+                 const double *__restrict__ idata, double *__restrict__ part, int nblk) {
+    const int k = blockIdx.y;
+    const ProbState &st = S[k];
+    __shared__ double red[MPO_BLOCK / 32];
+    if (st.best_child < 0) return;
+    const MixDev &mx = P[k].mx;
+    const int n1 = mx.n1, n2 = mx.n2;
+    const long long nself = (long long)n1 * n1, total = nself + (long long)n1 * n2;
+    const double *I = idata + ioff[k] * 8;
+    double acc = 0.0;
+    for (long long qq = (long long)blockIdx.x * MPO_BLOCK + threadIdx.x; qq < total;
+         qq += (long long)gridDim.x * MPO_BLOCK) {
+        if (qq < nself) {
+            int i = (int)(qq / n1), j = (int)(qq % n1);
+            const double *A = I + 8 * i, *B = I + 8 * j;
+            double w0 = A[6] * A[0] + B[6] * B[0], w1 = A[6] * A[1] + B[6] * B[1], w2 = A[6] * A[2] + B[6] * B[2];
+            acc += mx.phi1d[i] * mx.phi1d[j] * exp(logZ_d(sqrt(w0 * w0 + w1 * w1 + w2 * w2)) - A[7] - B[7]);
+        } else {
+            long long r = qq - nself;
+            int i = (int)(r / n2), j = (int)(r % n2);
+            const double *A = I + 8 * i, *mu = mx.mu2 + 3 * j;
+            double k2 = mx.kappa2d[j];
+            double w0 = A[6] * A[3] + k2 * mu[0], w1 = A[6] * A[4] + k2 * mu[1], w2 = A[6] * A[5] + k2 * mu[2];
+            acc -= 2.0 * mx.phi1d[i] * mx.phi2d[j] *
+                   exp(logZ_d(sqrt(w0 * w0 + w1 * w1 + w2 * w2)) - A[7] - logZ_d(k2));
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < MPO_BLOCK / 32; ++w) s += red[w];
+        part[(size_t)k * nblk + blockIdx.x] = s;
+    }
+}
+
+// sum the partials in a fixed order and replace d* when the candidate is better
+__global__ void mp_obj_final(ProbState *__restrict__ S, int nprob, const double *__restrict__ part, int nblk) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nprob) return;
+    ProbState &st = S[k];
+    if (st.best_child < 0) return;
+    double f = 0.0;
+    for (int b = 0; b < nblk; ++b) f += part[(size_t)k * nblk + b];
+    if (f < st.dstar) {
+        st.dstar = f;
+        for (int a = 0; a < 6; ++a) st.best_x[a] = st.cand_x[a];
+    }
+}
+
+__global__ void mp_start(unsigned long long *__restrict__ d_time) {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    d_time[0] = t;
+}
+
+// End of an iteration: device timestamp, iteration counter and the number of
+// finished problems (read by the host every few iterations).
+__global__ void mp_tick(const ProbState *__restrict__ S, int nprob, int *__restrict__ d_iter,
+                        unsigned long long *__restrict__ d_time, int *__restrict__ d_ndone) {
+    int cnt = 0;
+    for (int k = threadIdx.x; k < nprob; k += blockDim.x) cnt += S[k].done != 0;
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+    if (threadIdx.x == 0) {
+        unsigned long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        int it = *d_iter + 1;
+        *d_iter = it;
+        if (it < (1 << 20)) d_time[it] = t;
+        *d_ndone = cnt;
+    }
+}
+
+// ---------------------------------------------------------------- incumbent refinement (SMA, Sec. 5)
+// Poses of several problems evaluated in one launch: pose p belongs to
+// problem pid[p] and its component rows start at row[p].
+struct ManyMix {
+    const MixDev *mixes;
+    const int *pid;
+    const long long *row;
+    __device__ const MixDev &mix(int p) const { return mixes[pid[p]]; }
+    __device__ size_t row0(int p) const { return (size_t)row[p]; }
+};
+
+struct Incumbent {
+    double f;
+    double x[6];
+    int k, pad;
+};
+
+// Refined incumbents replace d* and the best pose where they are better.
+__global__ void mp_apply(ProbState *__restrict__ S, const Incumbent *__restrict__ u, int n) {
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    ProbState &st = S[u[q].k];
+    if (u[q].f < st.dstar) {
+        st.dstar = u[q].f;
+        for (int a = 0; a < 6; ++a) st.best_x[a] = u[q].x[a];
+    }
+}
+
+// ---------------------------------------------------------------- host driver
+struct MultiBuffers {
+    std::vector<void *> allocs;
+    ~MultiBuffers() {
+        for (void *p : allocs) cudaFree(p);
+    }
+    template <class T>
+    cudaError_t get(T **p, size_t n) {
+        void *q = nullptr;
+        cudaError_t e = cudaMalloc(&q, sizeof(T) * (n ? n : 1));
+        if (e == cudaSuccess) allocs.push_back(q);
+        *p = (T *)q;
+        return e;
+    }
+};
+
+template <int BLOCK>
+static cudaError_t mp_bound_launch(gosma_ctx *ctx, cudaStream_t st, const ProbDev *P, const int *off, int nprob, const Node *parents,
+                                   int pop, const CubePrep *prep, Node *kids, double *kid_ub, size_t smem) {
+    auto kern = mp_bound<BLOCK>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BLOCK, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    kern<<<ctx->sm_count * per_sm, BLOCK, smem, st>>>(P, off, nprob, parents, pop, prep, kids, kid_ub);
+    ++ctx->launches;
+    return cudaGetLastError();
+}
+
+static cudaError_t mp_bound_any(int block, gosma_ctx *ctx, cudaStream_t st, const ProbDev *P, const int *off, int nprob,
+                                const Node *parents, int pop, const CubePrep *prep, Node *kids, double *kid_ub,
+                                size_t smem) {
+    switch (block) {
+    case 64: return mp_bound_launch<64>(ctx, st, P, off, nprob, parents, pop, prep, kids, kid_ub, smem);
+    case 128: return mp_bound_launch<128>(ctx, st, P, off, nprob, parents, pop, prep, kids, kid_ub, smem);
+    default: return mp_bound_launch<256>(ctx, st, P, off, nprob, parents, pop, prep, kids, kid_ub, smem);
+    }
+}
+
+static int validate_problem(gosma_ctx *ctx, const gosma_problem &p, int k) {
+    char msg[160];
+    if (p.n1 < 1 || p.n2 < 1 || !p.mu1 || !p.sigma1 || !p.phi1 || !p.mu2 || !p.kappa2 || !p.phi2) {
+        snprintf(msg, sizeof msg, "bnb_solve_batch: problem %d: empty mixture or null pointer", k);
+        return fail(ctx, GOSMA_EINVAL, msg);
+    }
+    double s1 = 0, s2 = 0;
+    for (int i = 0; i < p.n1; ++i) {
+        if (!(p.sigma1[i] > 0) || !(p.phi1[i] >= 0)) {
+            snprintf(msg, sizeof msg, "bnb_solve_batch: problem %d: sigma1 > 0 and phi1 >= 0 required", k);
+            return fail(ctx, GOSMA_EINVAL, msg);
+        }
+        s1 += p.phi1[i];
+    }
+    for (int j = 0; j < p.n2; ++j) {
+        const double *m = p.mu2 + 3 * j;
+        double nn = sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+        if (!(p.kappa2[j] > 0) || !(p.phi2[j] >= 0) || !(fabs(nn - 1.0) <= 1e-6)) {
+            snprintf(msg, sizeof msg, "bnb_solve_batch: problem %d: kappa2 > 0, phi2 >= 0, |mu2| = 1 required", k);
+            return fail(ctx, GOSMA_EINVAL, msg);
+        }
+        s2 += p.phi2[j];
+    }
+    if (fabs(s1 - 1.0) > 1e-9 || fabs(s2 - 1.0) > 1e-9) {
+        snprintf(msg, sizeof msg, "bnb_solve_batch: problem %d: weights must sum to 1", k);
+        return fail(ctx, GOSMA_EINVAL, msg);
+    }
+    for (int a = 0; a < 3; ++a)
+        if (!(p.t_lo[a] < p.t_hi[a]) || !(p.zeta >= 0)) {
+            snprintf(msg, sizeof msg, "bnb_solve_batch: problem %d: need t_lo < t_hi and zeta >= 0", k);
+            return fail(ctx, GOSMA_EINVAL, msg);
+        }
+    if (bounds_smem_bytes(p.n1, p.n2) > 200 * 1024) {
+        snprintf(msg, sizeof msg, "bnb_solve_batch: problem %d: mixtures exceed the shared-memory budget", k);
+        return fail(ctx, GOSMA_EINVAL, msg);
+    }
+    return GOSMA_OK;
+}
+
+int setup_constants_mix(gosma_ctx *ctx, cudaStream_t st, const MixDev &mx, double *c22_out);
+
+// Lock-step L-BFGS for every unfinished problem whose d* improved since its
+// last refinement: each round evaluates the pending pose of every such
+// problem in one batched FP64 launch; improvements go back through mp_apply.
+struct BatchRefiner {
+    gosma_ctx *ctx = nullptr;
+    cudaStream_t st = nullptr;
+    int nprob = 0, nblk = 0, max_n1 = 0, max_iter = 100;
+    ManyMix mm{};
+    double *d_x = nullptr, *d_ri = nullptr, *d_part = nullptr, *d_out = nullptr;
+    int *d_pid = nullptr;
+    long long *d_row = nullptr;
+    Incumbent *d_upd = nullptr;
+    void *h_pin = nullptr;
+    double *hx = nullptr, *hout = nullptr;
+    int *hpid = nullptr;
+    long long *hrow = nullptr;
+    Incumbent *hupd = nullptr;
+    std::vector<Lbfgs> L;
+    std::vector<Feasibility> F;
+    std::vector<int> n1;
+    std::vector<double> refined_f;
+    std::vector<long long> calls;
+    std::vector<int> act, who;
+
+    ~BatchRefiner() {
+        if (h_pin) cudaFreeHost(h_pin);
+    }
+
+    cudaError_t init(MultiBuffers &B, const std::vector<ProbDev> &hp, const gosma_problem *probs, long long sum_n1) {
+        n1.resize(nprob);
+        F.resize(nprob);
+        L.resize(nprob);
+        refined_f.assign(nprob, INFINITY);
+        calls.assign(nprob, 0);
+        long long max_total = 0;
+        std::vector<MixDev> mixes(nprob);
+        for (int k = 0; k < nprob; ++k) {
+            const gosma_problem &p = probs[k];
+            n1[k] = p.n1;
+            max_n1 = std::max(max_n1, p.n1);
+            max_total = std::max(max_total, (long long)p.n1 * p.n1 + (long long)p.n1 * p.n2);
+            for (int a = 0; a < 3; ++a) {
+                F[k].t_lo[a] = p.t_lo[a];
+                F[k].t_hi[a] = p.t_hi[a];
+            }
+            F[k].zeta = p.zeta;
+            F[k].mu1 = p.mu1;
+            F[k].n1 = p.n1;
+            mixes[k] = hp[k].mx;
+        }
+        nblk = (int)((max_total + OBJ_CHUNK - 1) / OBJ_CHUNK);
+        MixDev *d_mixes = nullptr;
+        cudaError_t e;
+        if ((e = B.get(&d_mixes, nprob)) != cudaSuccess || (e = B.get(&d_x, 6 * (size_t)nprob)) != cudaSuccess ||
+            (e = B.get(&d_ri, OBJ_STRIDE * (size_t)sum_n1)) != cudaSuccess ||
+            (e = B.get(&d_part, 7 * (size_t)nblk * nprob)) != cudaSuccess ||
+            (e = B.get(&d_out, 7 * (size_t)nprob)) != cudaSuccess || (e = B.get(&d_pid, nprob)) != cudaSuccess ||
+            (e = B.get(&d_row, nprob)) != cudaSuccess || (e = B.get(&d_upd, nprob)) != cudaSuccess)
+            return e;
+        const size_t n = (size_t)nprob;
+        const size_t bytes = n * (sizeof(double) * 13 + sizeof(long long) + sizeof(int) + sizeof(Incumbent)) + 64;
+        if ((e = cudaMallocHost(&h_pin, bytes)) != cudaSuccess) return e;
+        char *c = (char *)h_pin;
+        hupd = (Incumbent *)c;
+        hx = (double *)(c + n * sizeof(Incumbent));
+        hout = hx + 6 * n;
+        hrow = (long long *)(hout + 7 * n);
+        hpid = (int *)(hrow + n);
+        mm.mixes = d_mixes;
+        mm.pid = d_pid;
+        mm.row = d_row;
+        return cudaMemcpyAsync(d_mixes, mixes.data(), sizeof(MixDev) * nprob, cudaMemcpyHostToDevice, st);
+    }
+
+    // One refinement wave; hs is the host copy of the problem states (its
+    // d* and best poses are updated with what is sent to the device).
+    cudaError_t wave(std::vector<ProbState> &hs) {
+        act.clear();
+        for (int k = 0; k < nprob; ++k)
+            if (!hs[k].done && hs[k].dstar < refined_f[k]) {
+                L[k].feas = F[k];
+                L[k].start(hs[k].best_x, max_iter);
+                act.push_back(k);
+                ++calls[k];
+            }
+        if (act.empty()) return cudaSuccess;
+        cudaError_t e = cudaSuccess;
+        for (;;) {
+            who.clear();
+            long long rows = 0;
+            for (int k : act) {
+                const int q = (int)who.size();
+                if (!L[k].want(hx + 6 * q)) continue;
+                hpid[q] = k;
+                hrow[q] = rows;
+                rows += n1[k];
+                who.push_back(k);
+            }
+            const int cnt = (int)who.size();
+            if (!cnt) break;
+            e = cudaMemcpyAsync(d_x, hx, sizeof(double) * 6 * cnt, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(d_pid, hpid, sizeof(int) * cnt, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(d_row, hrow, sizeof(long long) * cnt, cudaMemcpyHostToDevice, st);
+            if (e != cudaSuccess) return e;
+            obj_prep<<<dim3((max_n1 + 127) / 128, cnt), 128, 0, st>>>(mm, d_x, d_ri);
+            obj_pairs<<<dim3(nblk, cnt), OBJ_BLOCK, 0, st>>>(mm, d_x, d_ri, d_part, nblk);
+            obj_final<<<(cnt + 63) / 64, 64, 0, st>>>(cnt, d_x, d_part, nblk, d_out);
+            ctx->launches += 3;
+            e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaMemcpyAsync(hout, d_out, sizeof(double) * 7 * cnt, cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) return e;
+            for (int q = 0; q < cnt; ++q) L[who[q]].give(hout[7 * q], hout + 7 * q + 1);
+        }
+        int nu = 0;
+        for (int k : act) {
+            const Lbfgs &l = L[k];
+            if (l.fx < hs[k].dstar) {
+                Incumbent &u = hupd[nu++];
+                u.f = l.fx;
+                memcpy(u.x, l.x, sizeof u.x);
+                u.k = k;
+                u.pad = 0;
+                hs[k].dstar = l.fx;
+                memcpy(hs[k].best_x, l.x, sizeof u.x);
+            }
+            refined_f[k] = hs[k].dstar;
+        }
+        if (!nu) return cudaSuccess;
+        e = cudaMemcpyAsync(d_upd, hupd, sizeof(Incumbent) * nu, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return e;
+        mp_apply<<<(nu + 127) / 128, 128, 0, st>>>(S_dev, d_upd, nu);
+        ++ctx->launches;
+        e = cudaGetLastError();
+        // the staging buffer is reused by the next wave: wait for the copy
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        return e;
+    }
+    ProbState *S_dev = nullptr;
+};
+
+
+}  // namespace gosma
+
+using namespace gosma;
+
+extern "C" int gosma_bnb_solve_batch(gosma_ctx *ctx, int nprob, const gosma_problem *probs, const gosma_opts *opts_in,
+                                     gosma_result *results) {
+    if (!ctx) return GOSMA_EINVAL;
+    ctx->err.clear();
+    if (nprob < 0 || (nprob > 0 && (!probs || !results))) return fail(ctx, GOSMA_EINVAL, "bnb_solve_batch: bad arguments");
+    if (nprob == 0) return GOSMA_OK;
+    if (nprob > 65535) return fail(ctx, GOSMA_EINVAL, "bnb_solve_batch: at most 65535 problems");
+    gosma_opts o;
+    memset(&o, 0, sizeof o);
+    o.eps = 0.1;
+    o.pop = 64;
+    o.use_sma = 1;
+    o.sma_max_iter = 100;
+    if (opts_in) o = *opts_in;
+    if (o.sma_max_iter <= 0) o.sma_max_iter = 100;
+    if (!(o.eps >= 0) || o.pop < 1 || o.pop > 8192) return fail(ctx, GOSMA_EINVAL, "bnb_solve_batch: eps >= 0, 1 <= pop <= 8192");
+    const unsigned long long cap = o.queue_capacity > 0 ? (unsigned long long)o.queue_capacity : (1ULL << 18);
+    if (cap < 16ULL * o.pop) return fail(ctx, GOSMA_EINVAL, "bnb_solve_batch: queue_capacity below 16 * pop");
+    for (int k = 0; k < nprob; ++k) {
+        int rc = validate_problem(ctx, probs[k], k);
+        if (rc) return rc;
+    }
+    cudaSetDevice(ctx->device);
+    auto t_start = std::chrono::steady_clock::now();
+    // a private non-blocking stream, ordered after the context's stream: the
+    // iteration is captured into a CUDA graph, which the legacy stream forbids
+    cudaStream_t st = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamCreate");
+    struct StreamGuard {
+        cudaStream_t s;
+        ~StreamGuard() {
+            cudaStreamSynchronize(s);
+            cudaStreamDestroy(s);
+        }
+    } stream_guard{st};
+    e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "sync(context stream)");
+    MultiBuffers B;
+
+    // ---- mixtures of every problem in one allocation (FP64 + FP32 copies, as gosma_set_mixtures)
+    std::vector<size_t> d_off(nprob + 1, 0), f_off(nprob + 1, 0);
+    int max_n1 = 0, max_n2 = 0;
+    long long sum_n1 = 0;
+    for (int k = 0; k < nprob; ++k) {
+        const int n1 = probs[k].n1, n2 = probs[k].n2;
+        d_off[k + 1] = d_off[k] + 5 * (size_t)n1 + 5 * (size_t)n2;
+        f_off[k + 1] = f_off[k] + 8 * (size_t)n1 + 8 * (size_t)n2;
+        max_n1 = std::max(max_n1, n1);
+        max_n2 = std::max(max_n2, n2);
+        sum_n1 += n1;
+    }
+    std::vector<double> hd(d_off[nprob]);
+    std::vector<float> hf(f_off[nprob], 0.f);
+    for (int k = 0; k < nprob; ++k) {
+        const gosma_problem &p = probs[k];
+        double *d = hd.data() + d_off[k];
+        memcpy(d, p.mu1, sizeof(double) * 3 * p.n1);
+        memcpy(d + 3 * p.n1, p.sigma1, sizeof(double) * p.n1);
+        memcpy(d + 4 * p.n1, p.phi1, sizeof(double) * p.n1);
+        double *d2 = d + 5 * p.n1;
+        for (int j = 0; j < p.n2; ++j) {  // unit image directions
+            const double *m = p.mu2 + 3 * j;
+            double nn = sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+            for (int a = 0; a < 3; ++a) d2[3 * j + a] = m[a] / nn;
+        }
+        memcpy(d2 + 3 * p.n2, p.kappa2, sizeof(double) * p.n2);
+        memcpy(d2 + 4 * p.n2, p.phi2, sizeof(double) * p.n2);
+        float *f = hf.data() + f_off[k];
+        for (int j = 0; j < p.n2; ++j) f[2 * p.n1 + j] = (float)p.kappa2[j];
+    }
+    double *dmix = nullptr;
+    float *fmix = nullptr;
+    if ((e = B.get(&dmix, hd.size())) != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(batch mixtures)");
+    if ((e = B.get(&fmix, hf.size())) != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(batch mixtures)");
+    e = cudaMemcpyAsync(dmix, hd.data(), sizeof(double) * hd.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(fmix, hf.data(), sizeof(float) * hf.size(), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "copy batch mixtures");
+    std::vector<ProbDev> hp(nprob);
+    std::vector<ProbState> hs(nprob);
+    for (int k = 0; k < nprob; ++k) {
+        const gosma_problem &p = probs[k];
+        const int n1 = p.n1, n2 = p.n2;
+        double *d = dmix + d_off[k];
+        float *f = fmix + f_off[k];
+        MixDev &mx = hp[k].mx;
+        mx.n1 = n1;
+        mx.n2 = n2;
+        mx.mu1 = d;
+        mx.sigma1d = d + 3 * n1;
+        mx.phi1d = d + 4 * n1;
+        mx.mu2 = d + 5 * n1;
+        mx.kappa2d = d + 5 * n1 + 3 * n2;
+        mx.phi2d = d + 5 * n1 + 4 * n2;
+        mx.inv_sig2 = f;
+        mx.phi1f = f + n1;
+        mx.kappa2 = f + 2 * n1;
+        mx.Q2 = f + 2 * n1 + n2;
+        mx.mu1h = f + 2 * n1 + 2 * n2;
+        mx.mu1l = mx.mu1h + 3 * n1;
+        mx.mu2h = mx.mu1l + 3 * n1;
+        mx.mu2l = mx.mu2h + 3 * n2;
+        mx.zeta = p.zeta;
+        double c22 = 0;
+        int rc = setup_constants_mix(ctx, st, mx, &c22);
+        if (rc) return rc;
+        for (int a = 0; a < 3; ++a) {
+            hp[k].dom.t_lo[a] = p.t_lo[a];
+            hp[k].dom.t_hi[a] = p.t_hi[a];
+        }
+        hp[k].zeta = p.zeta;
+        split_double(p.zeta * p.zeta, hp[k].zeta2.h, hp[k].zeta2.l);
+        hp[k].c22 = c22;
+        hp[k].eps_f = o.eps * c22;
+        hp[k].base = (unsigned long long)k * cap;
+        hp[k].cap = cap;
+        ProbState &s = hs[k];
+        memset(&s, 0, sizeof s);
+        s.dstar = INFINITY;
+        s.lb = -INFINITY;
+        s.tail = 1;
+        s.live = 1;
+        s.peak = 1;
+        s.best_child = -1;
+        s.done_iter = -1;
+        s.minkey = DEAD;
+        for (int a = 0; a < 3; ++a) s.best_x[3 + a] = 0.5 * (p.t_lo[a] + p.t_hi[a]);
+    }
+
+    // ---- device state
+    const int pop = o.pop;
+    const size_t nkids = (size_t)8 * pop * nprob;
+    ProbDev *dP = nullptr;
+    ProbState *dS = nullptr;
+    Node *parents = nullptr, *kids = nullptr;
+    QueueBufs Qb;
+    memset(&Qb, 0, sizeof Qb);
+    const size_t max_chunks = (size_t)nprob * ((cap + CH_KEYS - 1) / CH_KEYS);
+    CubePrep *prep = nullptr;
+    double *kid_ub = nullptr, *idata = nullptr, *part = nullptr;
+    int *off = nullptr;
+    long long *ioff = nullptr;
+    const int nblk = (int)std::min<long long>(64, ((long long)max_n1 * max_n1 + (long long)max_n1 * max_n2 +
+                                                   MPO_CHUNK - 1) / MPO_CHUNK);
+    if ((e = B.get(&dP, nprob)) == cudaSuccess && (e = B.get(&dS, nprob)) == cudaSuccess &&
+        (e = B.get(&Qb.q[0], cap * nprob)) == cudaSuccess && (e = B.get(&Qb.keys[0], cap * nprob)) == cudaSuccess &&
+        (e = B.get(&Qb.q[1], cap * nprob)) == cudaSuccess && (e = B.get(&Qb.keys[1], cap * nprob)) == cudaSuccess &&
+        (e = B.get(&Qb.hist, 2048 * (size_t)nprob)) == cudaSuccess && (e = B.get(&Qb.ch_off, nprob + 1)) == cudaSuccess &&
+        (e = B.get(&Qb.c_lt, max_chunks)) == cudaSuccess && (e = B.get(&Qb.c_eq, max_chunks)) == cudaSuccess &&
+        (e = B.get(&Qb.c_out, max_chunks)) == cudaSuccess && (e = B.get(&Qb.c_eqb, max_chunks)) == cudaSuccess &&
+        (e = B.get(&Qb.c_live, max_chunks)) == cudaSuccess && (e = B.get(&Qb.c_base, max_chunks)) == cudaSuccess &&
+        (e = B.get(&parents, (size_t)pop * nprob)) == cudaSuccess && (e = B.get(&kids, nkids)) == cudaSuccess &&
+        (e = B.get(&kid_ub, nkids)) == cudaSuccess && (e = B.get(&prep, nkids)) == cudaSuccess &&
+        (e = B.get(&off, nprob + 1)) == cudaSuccess && (e = B.get(&ioff, nprob)) == cudaSuccess &&
+        (e = B.get(&idata, 8 * (size_t)sum_n1)) == cudaSuccess &&
+        (e = B.get(&part, (size_t)nblk * nprob)) == cudaSuccess) {
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(batch state)");
+    std::vector<long long> hio(nprob, 0);
+    for (int k = 1; k < nprob; ++k) hio[k] = hio[k - 1] + probs[k - 1].n1;
+    e = cudaMemcpyAsync(dP, hp.data(), sizeof(ProbDev) * nprob, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dS, hs.data(), sizeof(ProbState) * nprob, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ioff, hio.data(), sizeof(long long) * nprob, cudaMemcpyHostToDevice, st);
+    // roots: the cube circumscribing the pi-ball times each problem's translation cuboid
+    Node root;
+    memset(&root, 0, sizeof root);
+    root.lb = -INFINITY;
+    root.psit = (float)M_PI;
+    const uint32_t rkey = order_key(-INFINITY), dead = DEAD;
+    if (e == cudaSuccess) e = cudaMemsetAsync(Qb.hist, 0, sizeof(unsigned int) * 2048 * nprob, st);
+    for (int k = 0; k < nprob && e == cudaSuccess; ++k) {
+        e = cudaMemcpyAsync(Qb.q[0] + (size_t)k * cap, &root, sizeof root, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(Qb.keys[0] + (size_t)k * cap, &rkey, sizeof rkey, cudaMemcpyHostToDevice, st);
+    }
+    (void)dead;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "batch init");
+
+    const size_t smem = bounds_smem_bytes(max_n1, max_n2);
+    const int prep_grid = 4 * ctx->sm_count;
+    const int chunk_grid = 8 * ctx->sm_count;
+    int *d_iter = nullptr, *d_ndone = nullptr, *h_ndone = nullptr;
+    unsigned long long *d_time = nullptr;
+    const int max_iters = 1 << 20;
+    if ((e = B.get(&d_iter, 1)) != cudaSuccess || (e = B.get(&d_ndone, 1)) != cudaSuccess ||
+        (e = B.get(&d_time, (size_t)max_iters + 1)) != cudaSuccess)
+        return cuda_fail(ctx, e, "cudaMalloc(batch counters)");
+    if ((e = cudaMallocHost((void **)&h_ndone, sizeof(int))) != cudaSuccess) return cuda_fail(ctx, e, "cudaMallocHost");
+    struct PinnedFree {
+        int *p;
+        ~PinnedFree() { cudaFreeHost(p); }
+    } pin_guard{h_ndone};
+    e = cudaMemsetAsync(d_iter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "batch counters");
+    BatchRefiner refine;
+    refine.ctx = ctx;
+    refine.st = st;
+    refine.nprob = nprob;
+    refine.max_iter = o.sma_max_iter;
+    refine.S_dev = dS;
+    if (o.use_sma && (e = refine.init(B, hp, probs, sum_n1)) != cudaSuccess) return cuda_fail(ctx, e, "batch refinement set-up");
+    // SMA wave: read the problem states, refine the improved incumbents
+    auto sma_wave = [&]() -> cudaError_t {
+        if (!o.use_sma) return cudaSuccess;
+        cudaError_t e1 = cudaMemcpyAsync(hs.data(), dS, sizeof(ProbState) * nprob, cudaMemcpyDeviceToHost, st);
+        if (e1 == cudaSuccess) e1 = cudaStreamSynchronize(st);
+        if (e1 == cudaSuccess) e1 = refine.wave(hs);
+        return e1;
+    };
+    mp_start<<<1, 1, 0, st>>>(d_time);
+    ++ctx->launches;
+    const long long max_nodes = o.max_nodes;
+
+    auto front = [&]() {
+        mp_chunks<<<1, MP_BLOCK, 0, st>>>(dS, nprob, Qb.ch_off);
+        mp_hist<1><<<chunk_grid, CH_BLOCK, 0, st>>>(dP, dS, Qb, nprob);
+        mp_decide<<<nprob, MP_BLOCK, 0, st>>>(dP, dS, Qb, pop, d_iter, max_nodes);
+        mp_hist<2><<<chunk_grid, CH_BLOCK, 0, st>>>(dP, dS, Qb, nprob);
+        mp_refine<2><<<nprob, MP_BLOCK, 0, st>>>(dS, Qb);
+        mp_hist<3><<<chunk_grid, CH_BLOCK, 0, st>>>(dP, dS, Qb, nprob);
+        mp_refine<3><<<nprob, MP_BLOCK, 0, st>>>(dS, Qb);
+        mp_count<false><<<chunk_grid, CH_BLOCK, 0, st>>>(dP, dS, Qb, nprob);
+        mp_cscan_any<false><<<nprob, MP_BLOCK, 0, st>>>(dS, Qb, nprob);
+        mp_scatter<false><<<chunk_grid, CH_BLOCK, 0, st>>>(dP, dS, Qb, nprob, parents, pop);
+        mp_count<true><<<chunk_grid, CH_BLOCK, 0, st>>>(dP, dS, Qb, nprob);
+        mp_cscan_any<true><<<nprob, MP_BLOCK, 0, st>>>(dS, Qb, nprob);
+        mp_scatter<true><<<chunk_grid, CH_BLOCK, 0, st>>>(dP, dS, Qb, nprob, parents, pop);
+        mp_worklist<<<1, MP_BLOCK, 0, st>>>(dS, nprob, off);
+        mp_prep<<<prep_grid, 128, 0, st>>>(dP, off, nprob, parents, pop, prep);
+        ctx->launches += 15;
+    };
+    auto back = [&]() {
+        mp_append<<<nprob, MP_BLOCK, 0, st>>>(dP, dS, off, kids, kid_ub, Qb);
+        mp_obj_prep<<<dim3((max_n1 + 127) / 128, nprob), 128, 0, st>>>(dP, dS, ioff, idata);
+        mp_obj_pairs<<<dim3(nblk, nprob), MPO_BLOCK, 0, st>>>(dP, dS, ioff, idata, part, nblk);
+        mp_obj_final<<<(nprob + 127) / 128, 128, 0, st>>>(dS, nprob, part, nblk);
+        mp_tick<<<1, 32, 0, st>>>(dS, nprob, d_iter, d_time, d_ndone);
+        ctx->launches += 5;
+    };
+
+    // ---- eager iterations; at TUNE_ITER the candidate block sizes of the bound kernel are timed
+    // on the same prepared children (the bound kernel only writes the children's records)
+    const int TUNE_ITER = 3;
+    int block = 128, iter = 0;
+    cudaEvent_t ta, tb;
+    cudaEventCreate(&ta);
+    cudaEventCreate(&tb);
+    for (; iter <= TUNE_ITER && e == cudaSuccess; ++iter) {
+        front();
+        if (iter == TUNE_ITER) {
+            float best = 1e30f;
+            for (int cand : {64, 128, 256}) {
+                cudaEventRecord(ta, st);
+                e = mp_bound_any(cand, ctx, st, dP, off, nprob, parents, pop, prep, kids, kid_ub, smem);
+                cudaEventRecord(tb, st);
+                if (e == cudaSuccess) e = cudaEventSynchronize(tb);
+                float ms = 0;
+                cudaEventElapsedTime(&ms, ta, tb);
+                if (e == cudaSuccess && ms < best) {
+                    best = ms;
+                    block = cand;
+                }
+            }
+        } else {
+            e = mp_bound_any(block, ctx, st, dP, off, nprob, parents, pop, prep, kids, kid_ub, smem);
+        }
+        if (e == cudaSuccess) {
+            back();
+            e = cudaGetLastError();
+        }
+    }
+    cudaEventDestroy(ta);
+    cudaEventDestroy(tb);
+    if (e == cudaSuccess) e = sma_wave();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "batch iterations");
+
+    // ---- one iteration captured in a CUDA graph, replayed until every problem is done
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        front();
+        cudaError_t e2 = mp_bound_any(block, ctx, st, dP, off, nprob, parents, pop, prep, kids, kid_ub, smem);
+        back();
+        cudaMemcpyAsync(h_ndone, d_ndone, sizeof(int), cudaMemcpyDeviceToHost, st);
+        e = cudaStreamEndCapture(st, &graph);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(ctx, e, "batch graph capture");
+    }
+    const int poll = 8;
+    bool timed_out = false;
+    for (; iter < max_iters && e == cudaSuccess; ++iter) {
+        e = cudaGraphLaunch(exec, st);
+        if (e == cudaSuccess && (iter % poll) == poll - 1) {
+            e = cudaStreamSynchronize(st);
+            if (e == cudaSuccess && *h_ndone >= nprob) break;
+            if (e == cudaSuccess) e = sma_wave();
+            double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+            if (o.max_seconds > 0 && el > o.max_seconds) {
+                timed_out = true;
+                break;
+            }
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "batch replay");
+
+    // ---- results
+    int n_iter = 0;
+    e = cudaMemcpy(&n_iter, d_iter, sizeof(int), cudaMemcpyDeviceToHost);
+    std::vector<unsigned long long> times((size_t)n_iter + 1);
+    if (e == cudaSuccess) e = cudaMemcpy(times.data(), d_time, sizeof(unsigned long long) * times.size(), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(hs.data(), dS, sizeof(ProbState) * nprob, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "batch results");
+    const double total_s = (times[n_iter] - times[0]) * 1e-9;
+    for (int k = 0; k < nprob; ++k) {
+        const ProbState &s = hs[k];
+        gosma_result &r = results[k];
+        memset(&r, 0, sizeof r);
+        double x[6];
+        memcpy(x, s.best_x, sizeof x);
+        double rn = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+        if (rn > M_PI) {
+            double f = (rn - 2.0 * M_PI) / rn;
+            for (int a = 0; a < 3; ++a) x[a] *= f;
+        }
+        for (int a = 0; a < 3; ++a) {
+            r.r[a] = x[a];
+            r.t[a] = x[3 + a];
+        }
+        double th2 = x[0] * x[0] + x[1] * x[1] + x[2] * x[2], th = sqrt(th2), A, Bc;
+        if (th < 1e-8) {
+            A = 1.0 - th2 / 6.0;
+            Bc = 0.5 - th2 / 24.0;
+        } else {
+            A = sin(th) / th;
+            Bc = (1.0 - cos(th)) / th2;
+        }
+        double R[9] = {1.0 - Bc * (x[1] * x[1] + x[2] * x[2]), -A * x[2] + Bc * x[0] * x[1], A * x[1] + Bc * x[0] * x[2],
+                       A * x[2] + Bc * x[0] * x[1], 1.0 - Bc * (x[0] * x[0] + x[2] * x[2]), -A * x[0] + Bc * x[1] * x[2],
+                       -A * x[1] + Bc * x[0] * x[2], A * x[0] + Bc * x[1] * x[2], 1.0 - Bc * (x[0] * x[0] + x[1] * x[1])};
+        memcpy(r.R, R, sizeof R);
+        r.objective = s.dstar;
+        r.c22 = hp[k].c22;
+        r.objective_norm = s.dstar / r.c22 + 1.0;
+        r.lower_bound = s.lb;
+        r.gap_norm = (s.dstar - s.lb) / r.c22;
+        r.nodes = s.nodes;
+        r.iterations = s.done ? (s.done_iter >= 0 ? s.done_iter : n_iter) : n_iter;
+        r.queue_peak = (long long)s.peak;
+        r.queue_size = (long long)s.live;
+        r.cross_pairs = s.cross_pairs;
+        r.sma_calls = o.use_sma ? refine.calls[k] : 0;
+        r.status = s.done ? s.done - 1 : (timed_out ? GOSMA_TIME_LIMIT : GOSMA_NODE_LIMIT);
+        int it = s.done && s.done_iter >= 0 && s.done_iter <= n_iter ? s.done_iter : n_iter;
+        r.seconds = (times[it] - times[0]) * 1e-9;
+        r.iteration_ms = total_s * 1e3;
+        r.launches = ctx->launches;
+        r.block_size = block;
+    }
+    return GOSMA_OK;
+}

@@ -42,7 +42,12 @@ class Result(C.Structure):
                 ("sma_calls", C.c_longlong), ("queue_peak", C.c_longlong), ("seconds", C.c_double),
                 ("status", C.c_int), ("cross_pairs", C.c_longlong), ("self_pairs", C.c_longlong),
                 ("bound_ms", C.c_double), ("iteration_ms", C.c_double), ("queue_size", C.c_longlong),
-                ("launches", C.c_longlong)]
+                ("launches", C.c_longlong), ("block_size", C.c_int)]
+
+
+class Problem(C.Structure):
+    _fields_ = [("n1", C.c_int), ("mu1", D), ("sigma1", D), ("phi1", D), ("n2", C.c_int), ("mu2", D),
+                ("kappa2", D), ("phi2", D), ("t_lo", C.c_double * 3), ("t_hi", C.c_double * 3), ("zeta", C.c_double)]
 
 
 # exported symbols and their signatures (restype, argtypes); the header is the authority
@@ -59,6 +64,7 @@ SIGNATURES = {
     "gosma_eval_objective_grad_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     "gosma_bnb_solve": (C.c_int, [C.c_void_p, C.POINTER(Opts), C.POINTER(Result)]),
     "gosma_bnb_start": (C.c_int, [C.c_void_p, C.POINTER(Opts)]),
+    "gosma_bnb_solve_batch": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(Opts), C.c_void_p]),
     "gosma_bnb_step": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(Result)]),
     "gosma_selftest_approx": (C.c_int, [C.c_void_p, D, D]),
     "gosma_kernel_launches": (C.c_longlong, [C.c_void_p]),
@@ -234,6 +240,7 @@ class Gosma:
             "seconds": r.seconds, "status": r.status, "status_name": STATUS.get(r.status, str(r.status)),
             "cross_pairs": r.cross_pairs, "self_pairs": r.self_pairs, "bound_ms": r.bound_ms,
             "iteration_ms": r.iteration_ms, "queue_size": r.queue_size, "launches": r.launches,
+            "block_size": r.block_size,
         }
 
     def bnb_solve(self, eps=0.1, pop=1024, max_nodes=0, max_seconds=0.0, use_sma=True, sma_max_iter=100,
@@ -243,6 +250,31 @@ class Gosma:
         r = Result()
         self._check(self.L.gosma_bnb_solve(self.h, C.byref(o), C.byref(r)), "bnb_solve")
         return self._result(r)
+
+    def bnb_solve_batch(self, problems, eps=0.1, pop=64, max_nodes=0, max_seconds=0.0, use_sma=True,
+                        sma_max_iter=100, queue_capacity=0):
+        """Algorithm 1 for many independent problems at once (list of problem
+        dicts as produced by synth); returns one result dict per problem."""
+        if not problems:
+            return []
+        keep = []
+        arr = (Problem * len(problems))()
+        for k, pr in enumerate(problems):
+            a = [_f64(pr["mu1"], (-1, 3)), _f64(pr["sigma1"], (-1,)), _f64(pr["phi1"], (-1,)),
+                 _f64(pr["mu2"], (-1, 3)), _f64(pr["kappa2"], (-1,)), _f64(pr["phi2"], (-1,))]
+            keep.append(a)
+            p = arr[k]
+            p.n1, p.mu1, p.sigma1, p.phi1 = len(a[1]), _p(a[0]), _p(a[1]), _p(a[2])
+            p.n2, p.mu2, p.kappa2, p.phi2 = len(a[4]), _p(a[3]), _p(a[4]), _p(a[5])
+            for q in range(3):
+                p.t_lo[q] = float(pr["t_lo"][q])
+                p.t_hi[q] = float(pr["t_hi"][q])
+            p.zeta = float(pr["zeta"])
+        o = self._opts(eps, pop, max_nodes, max_seconds, use_sma, sma_max_iter, queue_capacity)
+        res = (Result * len(problems))()
+        self._check(self.L.gosma_bnb_solve_batch(self.h, len(problems), C.cast(arr, C.c_void_p), C.byref(o),
+                                                 C.cast(res, C.c_void_p)), "bnb_solve_batch")
+        return [self._result(r) for r in res]
 
     def bnb_start(self, eps=0.1, pop=1024, max_nodes=0, max_seconds=0.0, use_sma=True, sma_max_iter=100,
                   queue_capacity=0):

@@ -109,3 +109,71 @@ def test_step_before_start_is_an_error():
     with pytest.raises(GosmaError):
         c.bnb_step(1)
     c.close()
+
+
+# ---------------------------------------------------------------- batched problems (one launch, CUDA graph)
+def test_batch_matches_oracle_certificates(ctx, oracle_mod):
+    """Two stored oracle certificates and a third problem of other sizes
+    solved together in one batch: each result certifies against the oracle's
+    optimum exactly as a single-problem solve does."""
+    gold = json.load(open(GOLDEN))
+    probs = [synth.tiny_problem(1000), synth.tiny_problem(11, n1=20, n_in=8, n_out=2), synth.tiny_problem(1001)]
+    res = ctx.bnb_solve_batch(probs, eps=1e-3, pop=1024, max_seconds=300, queue_capacity=1 << 26)
+    assert [r["status_name"] for r in res] == ["optimal"] * 3
+    for p, r, seed in ((probs[0], res[0], 1000), (probs[2], res[2], 1001)):
+        g = gold[str(seed)]
+        epsf = 1e-3 * g["c22"]
+        assert r["c22"] == pytest.approx(g["c22"], rel=1e-12)
+        assert abs(r["f"] - g["f"]) <= epsf
+        assert r["lb"] <= g["f"] + 1e-9 and g["lb"] <= r["f"] + 1e-9
+        assert r["gap_norm"] <= 1e-3
+    for p, r in zip(probs, res):
+        mix = oracle_mod.Mixtures.from_problem(p)
+        assert oracle_mod.objective_r(mix, r["r"], r["t"]) == pytest.approx(r["f"], rel=1e-10)
+        assert r["sma_calls"] >= 1
+    assert res[0]["block_size"] in (64, 128, 256)
+
+
+def test_batch_noise_free_recovery(ctx, oracle_mod):
+    probs = [_noise_free(2, 4, 0.1), _noise_free(3, 4, 0.1)]
+    res = ctx.bnb_solve_batch(probs, eps=1e-2, pop=64, max_seconds=120, queue_capacity=1 << 24)
+    for p, r in zip(probs, res):
+        c22 = oracle_mod.c22(oracle_mod.Mixtures.from_problem(p))
+        assert r["status_name"] == "optimal"
+        assert r["f"] == pytest.approx(-c22, abs=1e-2 * c22)
+        assert _rot_err(r["R"], p["R_gt"]) < 0.1
+        assert np.linalg.norm(r["t"] - p["t_gt"]) < 0.05 * np.linalg.norm(p["t_gt"]) + 1e-3
+
+
+def test_batch_member_agrees_with_single_solve(ctx):
+    """A problem solved alone, in a batch with a neighbour of other sizes, and
+    by the single-problem solver reaches the same certified optimum."""
+    a = synth.tiny_problem(1000)
+    b = _noise_free(2, 4, 0.1)
+    alone = ctx.bnb_solve_batch([a], eps=1e-2, pop=256, max_seconds=120, queue_capacity=1 << 24)[0]
+    both = ctx.bnb_solve_batch([b, a], eps=1e-2, pop=256, max_seconds=120, queue_capacity=1 << 24)
+    ctx.set_problem(a)
+    single = ctx.bnb_solve(eps=1e-2, pop=256, max_seconds=120, queue_capacity=1 << 24)
+    epsf = 1e-2 * single["c22"]
+    for r in (alone, both[1]):
+        assert r["status_name"] == "optimal"
+        assert abs(r["f"] - single["f"]) <= epsf
+        assert r["lb"] <= single["f"] + 1e-9 and single["lb"] <= r["f"] + 1e-9
+    assert both[0]["status_name"] == "optimal" and both[0]["gap_norm"] <= 1e-2
+
+
+def test_batch_limits_and_errors(ctx):
+    from paper_1812_01232_gb300.gosma import GosmaError
+    probs = [synth.tiny_problem(1000), synth.tiny_problem(1001)]
+    res = ctx.bnb_solve_batch(probs, eps=1e-3, pop=64, max_nodes=4096)
+    assert [r["status_name"] for r in res] == ["node_limit"] * 2
+    assert all(r["nodes"] >= 4096 and r["lb"] <= r["f"] for r in res)
+    res = ctx.bnb_solve_batch(probs, eps=1e-3, pop=64, queue_capacity=16 * 64)
+    assert [r["status_name"] for r in res] == ["queue_full"] * 2
+    assert ctx.bnb_solve_batch([], eps=1e-3) == []
+    bad = dict(probs[0])
+    bad["phi1"] = bad["phi1"] * 2.0
+    with pytest.raises(GosmaError):
+        ctx.bnb_solve_batch([probs[1], bad], eps=1e-3)
+    with pytest.raises(GosmaError):
+        ctx.bnb_solve_batch(probs, eps=1e-3, pop=0)
