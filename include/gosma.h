@@ -207,6 +207,41 @@ int gosma_bnb_start(gosma_ctx *ctx, const gosma_opts *opts);
  * while none has).  GOSMA_ENOTREADY without a prior gosma_bnb_start. */
 int gosma_bnb_step(gosma_ctx *ctx, int max_iters, gosma_result *out);
 
+/* ---------------------------------------------------------------------
+ * Queue-ordering network (an extension of the method, not in the paper): a
+ * 16 -> 128 -> 128 -> 16 MLP with GELU (exact erf form) whose output 0 is a
+ * priority logit for a sub-cube and outputs 1..6 a seed-pose offset from the
+ * cube centre in half-width units.  Weights and activations are BF16 on the
+ * tensor cores with FP32 accumulation; an FP32 master copy of the
+ * parameters is kept for training.  Packed parameter layout (FP32,
+ * GOSMA_MLP_NPARAM values): W1 [128 x 16], b1 [128], W2 [128 x 128],
+ * b2 [128], W3 [16 x 128], b3 [16], matrices row-major [out x in].
+ * --------------------------------------------------------------------- */
+#define GOSMA_MLP_NPARAM 20752
+
+/* Load parameters (host array, copied) and reset the optimiser state. */
+int gosma_mlp_set_params(gosma_ctx *ctx, const float *params);
+
+/* Copy the FP32 master parameters to the host.  GOSMA_ENOTREADY before
+ * gosma_mlp_set_params. */
+int gosma_mlp_get_params(gosma_ctx *ctx, float *params);
+
+/* Forward pass: x (n x 16, host) -> y (n x 16, host), FP32. */
+int gosma_mlp_forward(gosma_ctx *ctx, int n, const float *x, float *y);
+
+/* Parameter gradient (packed layout, host) of sum_rows dy . y(x) for an
+ * upstream gradient dy (n x 16, host); dy is rounded to BF16 as in training. */
+int gosma_mlp_grad(gosma_ctx *ctx, int n, const float *x, const float *dy, float *grad);
+
+/* `steps` Adam steps (lr, betas 0.9 / 0.999) on minibatches of `batch` rows
+ * (a multiple of 128; n a multiple of batch) taken in order, cyclically, from
+ * the device-resident data set x (n x 16), label (n, in [0, 1]) and target
+ * (n x 6).  Loss per row: logistic loss of y[0] against label plus
+ * lam * label * |y[1..6] - target|^2.  losses (host, steps values, may be
+ * NULL) receives the mean loss of each minibatch before its step. */
+int gosma_mlp_train(gosma_ctx *ctx, int n, const float *x, const float *label, const float *target, int batch,
+                    int steps, float lr, float lam, float *losses);
+
 /* Number of kernels the context has launched since it was created. */
 long long gosma_kernel_launches(const gosma_ctx *ctx);
 

@@ -36,7 +36,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     """Compile every csrc/*.cu and link libgosma.so; returns its path."""
     os.makedirs(BUILD, exist_ok=True)
     sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
-    headers = sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [os.path.join(HERE, "..", "include", "gosma.h")]
+    headers = (sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + sorted(glob.glob(os.path.join(CSRC, "*.h"))) +
+               [os.path.join(HERE, "..", "include", "gosma.h")])
     objs = []
     jobs = []
     for s in sources:

@@ -79,6 +79,7 @@ void gosma_destroy(gosma_ctx *ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     bnb_release(ctx);
+    gosma::mlp_free(ctx->mlp);
     if (ctx->d_mix) cudaFree(ctx->d_mix);
     if (ctx->d_stage) cudaFree(ctx->d_stage);
     if (ctx->d_obj) cudaFree(ctx->d_obj);

@@ -101,6 +101,11 @@ struct Acc {
 }  // namespace gosma
 
 // ---------------------------------------------------------------- context
+namespace gosma {
+struct Mlp;
+void mlp_free(Mlp *m);
+}  // namespace gosma
+
 struct gosma_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -135,6 +140,8 @@ struct gosma_ctx {
 
     // branch-and-bound state (bnb.cu)
     void *bnb = nullptr;
+    // queue-ordering network (mlp.cu)
+    gosma::Mlp *mlp = nullptr;
 
     // number of kernels this context has launched
     long long launches = 0;

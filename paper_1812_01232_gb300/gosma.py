@@ -51,6 +51,8 @@ class Problem(C.Structure):
 
 
 # exported symbols and their signatures (restype, argtypes); the header is the authority
+FP = C.POINTER(C.c_float)
+
 SIGNATURES = {
     "gosma_create": (C.c_int, [C.c_int, C.c_void_p, C.POINTER(C.c_void_p)]),
     "gosma_destroy": (None, [C.c_void_p]),
@@ -68,7 +70,13 @@ SIGNATURES = {
     "gosma_bnb_step": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(Result)]),
     "gosma_selftest_approx": (C.c_int, [C.c_void_p, D, D]),
     "gosma_kernel_launches": (C.c_longlong, [C.c_void_p]),
+    "gosma_mlp_set_params": (C.c_int, [C.c_void_p, FP]),
+    "gosma_mlp_get_params": (C.c_int, [C.c_void_p, FP]),
+    "gosma_mlp_forward": (C.c_int, [C.c_void_p, C.c_int, FP, FP]),
+    "gosma_mlp_grad": (C.c_int, [C.c_void_p, C.c_int, FP, FP, FP]),
+    "gosma_mlp_train": (C.c_int, [C.c_void_p, C.c_int, FP, FP, FP, C.c_int, C.c_int, C.c_float, C.c_float, FP]),
 }
+MLP_NPARAM = 20752
 
 _lib = None
 
@@ -99,6 +107,15 @@ def _f64(a, shape=None):
 
 def _p(a):
     return a.ctypes.data_as(D)
+
+
+def _f32(a, shape=None):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    return a.reshape(shape) if shape is not None else a
+
+
+def _pf(a):
+    return a.ctypes.data_as(FP)
 
 
 def _is_torch_cuda(x):
@@ -285,6 +302,38 @@ class Gosma:
         r = Result()
         self._check(self.L.gosma_bnb_step(self.h, int(max_iters), C.byref(r)), "bnb_step")
         return self._result(r)
+
+    # ---- queue-ordering network
+    def mlp_set_params(self, params):
+        p = _f32(params, (MLP_NPARAM,))
+        self._check(self.L.gosma_mlp_set_params(self.h, _pf(p)), "mlp_set_params")
+
+    def mlp_get_params(self):
+        p = np.zeros(MLP_NPARAM, dtype=np.float32)
+        self._check(self.L.gosma_mlp_get_params(self.h, _pf(p)), "mlp_get_params")
+        return p
+
+    def mlp_forward(self, x):
+        x = _f32(x, (-1, 16))
+        y = np.zeros((len(x), 16), dtype=np.float32)
+        self._check(self.L.gosma_mlp_forward(self.h, len(x), _pf(x), _pf(y)), "mlp_forward")
+        return y
+
+    def mlp_grad(self, x, dy):
+        x = _f32(x, (-1, 16))
+        dy = _f32(dy, (len(x), 16))
+        g = np.zeros(MLP_NPARAM, dtype=np.float32)
+        self._check(self.L.gosma_mlp_grad(self.h, len(x), _pf(x), _pf(dy), _pf(g)), "mlp_grad")
+        return g
+
+    def mlp_train(self, x, label, target, batch, steps, lr=1e-3, lam=1.0):
+        x = _f32(x, (-1, 16))
+        label = _f32(label, (len(x),))
+        target = _f32(target, (len(x), 6))
+        losses = np.zeros(max(steps, 1), dtype=np.float32)
+        self._check(self.L.gosma_mlp_train(self.h, len(x), _pf(x), _pf(label), _pf(target), int(batch), int(steps),
+                                           float(lr), float(lam), _pf(losses)), "mlp_train")
+        return losses[:steps]
 
     def kernel_launches(self):
         return int(self.L.gosma_kernel_launches(self.h))

@@ -156,3 +156,22 @@ def test_paper_scale_parity_full_batch(ctx, oracle_mod):
     # every cube: lb <= ub where both finite, and ub equals the FP64 objective at the centre for a few
     both = np.isfinite(got[:, 0]) & np.isfinite(got[:, 1])
     assert np.all(got[both, 0] <= got[both, 1])
+
+
+def test_stress_parity_full_size(ctx, oracle_mod):
+    """Precision stress at full size: 2048 x 512 components with kappa_2 up
+    to 2000 and near-antipodal pairs, 2^20 sub-cubes at depths 2-12 in one
+    call; the oracle checks a sample of the cubes, and every cube is checked
+    for lb <= ub."""
+    prob = synth.stress_problem(4000)
+    ctx.set_problem(prob)
+    cubes = synth.tree_cubes(4001, 1 << 20, prob["t_lo"], prob["t_hi"], 2, 12,
+                             near=(prob["r_gt"], prob["t_gt"]), near_frac=0.3)
+    got = ctx.eval_bounds_detail(cubes)
+    assert got.shape == (1 << 20, 8)
+    idx = np.random.default_rng(6).choice(len(cubes), 24, replace=False)
+    ref = oracle_mod.bounds(oracle_mod.Mixtures.from_problem(prob), cubes[idx], prob["zeta"])
+    compare(got[idx], ref, "stress")
+    both = np.isfinite(got[:, 0]) & np.isfinite(got[:, 1])
+    assert both.sum() > len(cubes) // 2
+    assert np.all(got[both, 0] <= got[both, 1])
