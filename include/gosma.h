@@ -198,6 +198,44 @@ int gosma_bnb_solve(gosma_ctx *ctx, const gosma_opts *opts, gosma_result *out);
 int gosma_bnb_solve_batch(gosma_ctx *ctx, int nprob, const gosma_problem *probs, const gosma_opts *opts,
                           gosma_result *results);
 
+/* Options of the learned form of the batched solver (an extension of the
+ * method, not in the paper).  With use_mlp set (parameters loaded by
+ * gosma_mlp_set_params), the queue-ordering network scores every child on
+ * the tensor cores inside the iteration:
+ *   - ordering: a child's pop priority is lb - beta * C22 * sigmoid(logit);
+ *     the lower bound, pruning and the stopping test still use lb alone, so
+ *     the certificate is the plain method's;
+ *   - seeding (seed != 0): the best-scored child of each problem proposes a
+ *     pose (its centre plus the predicted offset times its half-widths,
+ *     clamped to the cube) whose exact FP64 objective competes for d* and is
+ *     then refined by SMA.
+ * trace_cap > 0 records up to trace_cap popped sub-cubes per problem. */
+typedef struct {
+    int use_mlp;
+    float beta;
+    int seed;
+    int trace_cap;
+} gosma_learn_opts;
+
+/* One popped sub-cube of a trace: the network's 16 input features as the
+ * device computed them at pop time, the cube (r0, r half-width, t0,
+ * t half-widths), its bounds and the incumbent at that time. */
+typedef struct {
+    float feat[16];
+    double cube[10];
+    double lb, ub, dstar;
+    int problem, iteration;
+} gosma_trace_rec;
+
+/* gosma_bnb_solve_batch with the learned form and tracing.  lopts may be
+ * NULL (plain).  trace (host, nprob * lopts->trace_cap records) and
+ * trace_count (host, nprob) receive each problem's records in pop order
+ * when lopts->trace_cap > 0.  GOSMA_ENOTREADY if use_mlp is set without
+ * parameters. */
+int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_problem *probs, const gosma_opts *opts,
+                             const gosma_learn_opts *lopts, gosma_result *results, gosma_trace_rec *trace,
+                             int *trace_count);
+
 /* Start a branch-and-bound run (the queue holds the root Omega_r x Omega_t).
  * The run's device state belongs to the context until the next start. */
 int gosma_bnb_start(gosma_ctx *ctx, const gosma_opts *opts);

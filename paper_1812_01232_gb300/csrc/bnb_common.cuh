@@ -17,7 +17,7 @@ struct Node {
     uint16_t lr, lt;
     float psit;              // max_i psi_t over the cuboid
     uint32_t flags;
-    uint32_t pad;
+    float ubf;               // upper bound at the centre, FP32 (batched solver)
 };
 static_assert(sizeof(Node) == 64, "node layout");
 

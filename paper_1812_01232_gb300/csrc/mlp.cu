@@ -19,12 +19,9 @@
 
 #include <vector>
 
-#include "gosma_internal.cuh"
-#include "tc_gemm.cuh"
+#include "mlp.cuh"
 
 namespace gosma {
-
-constexpr int MLP_IN = 16, MLP_HID = 128, MLP_OUT = 16, MLP_SEED = 6;
 // packed parameter layout (FP32): W1 [128 x 16], b1, W2 [128 x 128], b2, W3 [16 x 128], b3
 constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + MLP_HID * MLP_IN, OFF_W2 = OFF_B1 + MLP_HID,
               OFF_B2 = OFF_W2 + MLP_HID * MLP_HID, OFF_W3 = OFF_B2 + MLP_HID, OFF_B3 = OFF_W3 + MLP_OUT * MLP_HID,
@@ -38,7 +35,8 @@ struct GemmArgs {
     long long lda;
     const bf16 *B;
     long long ldb;
-    int M;      // rows of D (row-tiled mode); 128 in split mode
+    int M;      // rows of D (row-tiled mode): a bound, see Mdev; 128 in split mode
+    const int *Mdev;  // if set, the row count is read from device memory (<= M)
     int K;      // contraction length (split mode: a multiple of 128)
     int split;  // contraction split into 128-wide chunks over the CTAs, FP32 atomics
     const float *bias;
@@ -90,7 +88,8 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(GemmArgs g) {
     const uint32_t taddr = tbase + ((uint32_t)(32 * warp) << 16);
     uint32_t phase = 0;
     bool ok = true;
-    const int nunits = g.split ? g.K / KC : (g.M + 127) / 128;
+    const int Mrows = g.Mdev ? min(*g.Mdev, g.M) : g.M;
+    const int nunits = g.split ? g.K / KC : (Mrows + 127) / 128;
     int done_units = 0;
     for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
         // ---- stage operands (all K in one chunk in row-tiled mode)
@@ -99,7 +98,7 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(GemmArgs g) {
             tc_stage<KC>(sB, g.B + (long long)u * KC, g.ldb, N, N);
         } else {
             const int row0 = u * 128;
-            tc_stage<KC>(sA, g.A + (long long)row0 * g.lda, g.lda, 128, min(128, g.M - row0));
+            tc_stage<KC>(sA, g.A + (long long)row0 * g.lda, g.lda, 128, min(128, Mrows - row0));
             tc_stage<KC>(sB, g.B, g.ldb, N, N);
         }
         tc_fence_proxy();
@@ -123,7 +122,7 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(GemmArgs g) {
         if (g.split) continue;  // keep accumulating; one epilogue at the end
         // ---- row-tiled epilogue: thread = row
         const int row = u * 128 + 32 * warp + lane;
-        const bool valid = row < g.M;
+        const bool valid = row < Mrows;
 #pragma unroll 1
         for (int c0 = 0; c0 < N; c0 += 16) {
             float v[16];
@@ -155,7 +154,7 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(GemmArgs g) {
                     hv[i] = valid ? __bfloat162float(hb[i]) : 0.f;
                 }
                 if (valid) {
-                    if (EPI == EPI_GELU) {
+                    if (EPI == EPI_GELU && g.outF) {  // pre-activations, kept for training only
                         float *o = g.outF + (long long)row * N + c0;
 #pragma unroll
                         for (int i = 0; i < 16; i += 4)
@@ -164,8 +163,10 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(GemmArgs g) {
                     uint4 *oh = reinterpret_cast<uint4 *>(g.outH + (long long)row * N + c0);
                     oh[0] = reinterpret_cast<const uint4 *>(hb)[0];
                     oh[1] = reinterpret_cast<const uint4 *>(hb)[1];
+                    if (g.outHT) {
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) g.outHT[(long long)(c0 + i) * g.ldt + row] = hb[i];
+                        for (int i = 0; i < 16; ++i) g.outHT[(long long)(c0 + i) * g.ldt + row] = hb[i];
+                    }
                 }
                 if (EPI == EPI_DGELU && g.colsum) {
 #pragma unroll
@@ -456,6 +457,32 @@ static int mlp_stage_x(gosma_ctx *ctx, Mlp *m, int n, const float *h_x, int *npa
     if (e != cudaSuccess) return cuda_fail(ctx, e, "mlp inputs");
     *npad_out = npad;
     return GOSMA_OK;
+}
+
+int mlp_reserve(gosma_ctx *ctx, int rows) {
+    if (!ctx->mlp) return fail(ctx, GOSMA_ENOTREADY, "queue-ordering network: no parameters set");
+    return mlp_act_alloc(ctx, rows);
+}
+bf16 *mlp_input(Mlp *m) { return m->X; }
+const float *mlp_output(Mlp *m) { return m->Y; }
+int *mlp_error_flag(Mlp *m) { return m->err; }
+
+cudaError_t mlp_forward_rows(gosma_ctx *ctx, int max_rows, const int *d_rows, cudaStream_t st) {
+    Mlp *m = ctx->mlp;
+    GemmArgs g;
+    memset(&g, 0, sizeof g);
+    g.err = m->err;
+    g.Mdev = d_rows;
+    g.A = m->X, g.lda = MLP_IN, g.B = m->W1b, g.ldb = MLP_IN, g.M = max_rows, g.K = MLP_IN;
+    g.bias = m->P + OFF_B1, g.outH = m->H1;
+    cudaError_t e = tc_gemm<MLP_HID, MLP_IN, EPI_GELU>(g, ctx->sm_count, st);
+    g.A = m->H1, g.lda = MLP_HID, g.B = m->W2b, g.ldb = MLP_HID, g.K = MLP_HID;
+    g.bias = m->P + OFF_B2, g.outH = m->H2;
+    if (e == cudaSuccess) e = tc_gemm<MLP_HID, MLP_HID, EPI_GELU>(g, ctx->sm_count, st);
+    g.A = m->H2, g.B = m->W3b, g.ldb = MLP_HID, g.bias = m->P + OFF_B3, g.outF = m->Y, g.outH = nullptr;
+    if (e == cudaSuccess) e = tc_gemm<MLP_OUT, MLP_HID, EPI_F32>(g, ctx->sm_count, st);
+    ctx->launches += 3;
+    return e;
 }
 
 }  // namespace gosma

@@ -28,6 +28,7 @@
 
 #include "bnb_common.cuh"
 #include "lbfgs.h"
+#include "mlp.cuh"
 #include "objective_core.cuh"
 
 namespace gosma {
@@ -48,9 +49,11 @@ struct ProbState {
     int done;  // 0 running, else 1 + GOSMA_* status
     int done_iter;
     int np;
-    int best_child;  // candidate child (index into the children arrays) or -1
-    double cand_x[6];
-    unsigned int minkey;  // smallest live key (atomic minimum over the chunks)
+    // incumbent candidates of this iteration: 0 = centre of the child with the
+    // smallest upper bound, 1 = the network's seed pose (learned form)
+    int cand_ok[2], cand_bad[2];
+    double cand_x[2][6];
+    unsigned int minkey;  // smallest live lower-bound key (atomic minimum over the chunks)
     int cur;              // which of the two segment buffers holds the queue
     // selection state of the current iteration
     unsigned int sel_prefix, sel_need, sel_T, sel_quota;
@@ -71,7 +74,8 @@ constexpr int CH_TILE = CH_BLOCK * CH_ITEMS;
 // Queue buffers: two segment sets (keys and nodes), one segment of `cap`
 // entries per problem in each; ProbState::cur says which holds the queue.
 struct QueueBufs {
-    uint32_t *keys[2];
+    uint32_t *keys[2];  // pop priority (the lower bound, or the learned priority)
+    uint32_t *lbk[2];   // lower bound, for the stopping test
     Node *q[2];
     unsigned int *hist;  // nprob x 2048
     int *ch_off;         // nprob + 1: first chunk of each problem
@@ -188,7 +192,7 @@ __global__ void __launch_bounds__(CH_BLOCK)
         if (PASS > 1 && (st.np == 0 || st.sel_skip)) continue;  // uniform over the block
         const unsigned long long j0 = (unsigned long long)(c - Qb.ch_off[k]) * CH_KEYS;
         const unsigned long long n = st.tail;
-        const uint32_t *keys = Qb.keys[st.cur] + P[k].base;
+        const uint32_t *keys = Qb.keys[st.cur] + P[k].base, *lbk = Qb.lbk[st.cur] + P[k].base;
         const uint32_t pre = st.sel_prefix;
         for (int b = threadIdx.x; b < 2048; b += CH_BLOCK) h[b] = 0;
         if (threadIdx.x == 0) smin = DEAD;
@@ -200,7 +204,7 @@ __global__ void __launch_bounds__(CH_BLOCK)
             const uint32_t key = keys[i];
             if (key == DEAD) continue;
             if (PASS == 1) {
-                m = min(m, key);
+                m = min(m, lbk[i]);
                 atomicAdd(&h[key >> 21], 1u);
             } else if (PASS == 2) {
                 if ((key >> 21) == pre) atomicAdd(&h[(key >> 10) & 2047u], 1u);
@@ -426,7 +430,8 @@ __global__ void __launch_bounds__(CH_BLOCK)
         const unsigned long long base = P[k].base;
         uint32_t *keys = Qb.keys[st.cur] + base;
         const Node *q = Qb.q[st.cur] + base;
-        uint32_t *okeys = Qb.keys[st.cur ^ 1] + base;
+        uint32_t *okeys = Qb.keys[st.cur ^ 1] + base, *olbk = Qb.lbk[st.cur ^ 1] + base;
+        const uint32_t *lbk = Qb.lbk[st.cur] + base;
         Node *oq = Qb.q[st.cur ^ 1] + base;
         const uint32_t T = st.sel_T;
         const unsigned int quota = st.sel_quota;
@@ -466,6 +471,7 @@ __global__ void __launch_bounds__(CH_BLOCK)
                         if ((unsigned long long)pos < P[k].cap) {  // holds when the counts agree
                             oq[pos] = q[i];
                             okeys[pos] = kk[j];
+                            olbk[pos] = lbk[i];
                         }
                     } else if (pos < pop) {
                         parents[(size_t)k * pop + pos] = q[i];
@@ -481,7 +487,8 @@ __global__ void __launch_bounds__(CH_BLOCK)
 
 // Prefix sums of the children counts (one block); compacted segments take
 // over from the old buffers.
-__global__ void mp_worklist(ProbState *__restrict__ S, int nprob, int *__restrict__ off) {
+__global__ void mp_worklist(ProbState *__restrict__ S, int nprob, int *__restrict__ off, int *__restrict__ tcount,
+                            int tcap) {
     __shared__ int sh[32];
     __shared__ int carry;
     if (threadIdx.x == 0) carry = 0;
@@ -493,6 +500,7 @@ __global__ void mp_worklist(ProbState *__restrict__ S, int nprob, int *__restric
             S[k].tail = S[k].cmp_tail;
             S[k].cmp = 0;
         }
+        if (k < nprob && tcount) tcount[k] = min(tcap, tcount[k] + S[k].np);
         int v = k < nprob ? 8 * S[k].np : 0;
         int tot;
         int ex = mp_scan(v, sh, tot);
@@ -558,47 +566,76 @@ __global__ void __launch_bounds__(BLOCK)
     }
 }
 
+__device__ __forceinline__ unsigned long long dbl_order(double d) {
+    unsigned long long u = (unsigned long long)__double_as_longlong(d);
+    return (u & 0x8000000000000000ULL) ? ~u : (u | 0x8000000000000000ULL);
+}
+
+// One block per problem: children with lb < d* go to the segment's tail in
+// child order (pop key: lb, or lb - beta C22 sigmoid(logit) in the learned
+// form; the lower-bound key is kept beside it).  Candidate 0 is the centre of
+// the child with the smallest upper bound below d* (ties: smallest index);
+// candidate 1 (learned form with seeding) is the seed pose of the surviving
+// child with the largest logit.
 __global__ void __launch_bounds__(MP_BLOCK)
     mp_append(const ProbDev *__restrict__ P, ProbState *__restrict__ S, const int *__restrict__ off,
-              const Node *__restrict__ kids, const double *__restrict__ kid_ub, QueueBufs Qb) {
+              const Node *__restrict__ kids, const double *__restrict__ kid_ub, QueueBufs Qb,
+              const float *__restrict__ Y, float beta, int seed) {
     __shared__ int sh[32];
-    __shared__ unsigned long long sbest;
+    __shared__ unsigned long long s_ub;
+    __shared__ unsigned int s_lg;
+    __shared__ int s_jub, s_jlg;
     const int k = blockIdx.x, t = threadIdx.x;
     ProbState &st = S[k];
     if (t == 0) {
-        sbest = ~0ULL;
-        st.best_child = -1;
+        s_ub = ~0ULL;
+        s_lg = 0u;
+        s_jub = s_jlg = 0x7fffffff;
+        st.cand_ok[0] = st.cand_ok[1] = 0;
+        st.cand_bad[0] = st.cand_bad[1] = 0;
     }
     __syncthreads();
     const int n = 8 * st.np;
     if (n == 0) return;
     const int c0 = off[k];
-    const double ds = st.dstar;
+    const double ds = st.dstar, c22 = P[k].c22;
     const unsigned long long base = P[k].base, cap = P[k].cap, tail = st.tail;
-    uint32_t *keys = Qb.keys[st.cur];
+    uint32_t *keys = Qb.keys[st.cur], *lbk = Qb.lbk[st.cur];
     Node *q = Qb.q[st.cur];
     int appended = 0;
     for (int j0 = 0; j0 < n; j0 += MP_BLOCK) {
-        int j = j0 + t;
-        bool alive = j < n && kids[c0 + j].lb < ds;
-        if (j < n && kid_ub[c0 + j] < ds) {
-            // smallest upper bound first, then smallest child index (ub order key has 44 high bits)
-            unsigned long long u = (unsigned long long)__double_as_longlong(kid_ub[c0 + j]);
-            u = (u & 0x8000000000000000ULL) ? ~u : (u | 0x8000000000000000ULL);
-            atomicMin(&sbest, (u & ~0xFFFFFULL) | (unsigned long long)j);
+        const int j = j0 + t;
+        const bool alive = j < n && kids[c0 + j].lb < ds;
+        if (j < n && kid_ub[c0 + j] < ds) atomicMin(&s_ub, dbl_order(kid_ub[c0 + j]));
+        float logit = 0.f;
+        if (Y && alive) {
+            logit = Y[(size_t)(c0 + j) * MLP_OUT];
+            if (seed) atomicMax(&s_lg, order_key(logit));
         }
         int tot;
-        int pos = mp_scan(alive ? 1 : 0, sh, tot);
+        const int pos = mp_scan(alive ? 1 : 0, sh, tot);
         if (alive && tail + appended + pos < cap) {
-            unsigned long long dst = base + tail + appended + pos;
-            q[dst] = kids[c0 + j];
-            keys[dst] = order_key(__double2float_rd(kids[c0 + j].lb));
+            const unsigned long long dst = base + tail + appended + pos;
+            Node nd = kids[c0 + j];
+            nd.ubf = __double2float_ru(kid_ub[c0 + j]);
+            q[dst] = nd;
+            const uint32_t lkey = order_key(__double2float_rd(nd.lb));
+            lbk[dst] = lkey;
+            keys[dst] = Y ? order_key(__double2float_rd(nd.lb - (double)beta * c22 / (1.0 + exp(-(double)logit))))
+                          : lkey;
         }
         appended += tot;
     }
     __syncthreads();
+    // ties: the smallest child index
+    for (int j = t; j < n; j += MP_BLOCK) {
+        if (s_ub != ~0ULL && kid_ub[c0 + j] < ds && dbl_order(kid_ub[c0 + j]) == s_ub) atomicMin(&s_jub, j);
+        if (Y && seed && s_lg != 0u && kids[c0 + j].lb < ds && order_key(Y[(size_t)(c0 + j) * MLP_OUT]) == s_lg)
+            atomicMin(&s_jlg, j);
+    }
+    __syncthreads();
     if (t == 0) {
-        unsigned long long fit = tail + appended <= cap ? appended : cap - tail;
+        const unsigned long long fit = tail + appended <= cap ? appended : cap - tail;
         st.tail = tail + fit;
         st.live += fit;
         if (st.live > st.peak) st.peak = st.live;
@@ -607,22 +644,24 @@ __global__ void __launch_bounds__(MP_BLOCK)
             st.done = 1 + GOSMA_QUEUE_FULL;
             st.done_iter = -1;
         }
-        if (sbest != ~0ULL) {
-            // the packed order kept 44 bits of ub: take the exact smallest of the candidates
-            int j = (int)(sbest & 0xFFFFFULL);
-            double bu = kid_ub[c0 + j];
-            for (int q2 = 0; q2 < n; ++q2)
-                if (kid_ub[c0 + q2] < bu) {
-                    bu = kid_ub[c0 + q2];
-                    j = q2;
-                }
-            st.best_child = c0 + j;
+        if (s_jub != 0x7fffffff) {
             CubeGeom g;
-            decode(kids[c0 + j], P[k].dom, g);
+            decode(kids[c0 + s_jub], P[k].dom, g);
             for (int a = 0; a < 3; ++a) {
-                st.cand_x[a] = g.r0[a];
-                st.cand_x[3 + a] = g.t0[a];
+                st.cand_x[0][a] = g.r0[a];
+                st.cand_x[0][3 + a] = g.t0[a];
             }
+            st.cand_ok[0] = 1;
+        }
+        if (s_jlg != 0x7fffffff) {
+            CubeGeom g;
+            decode(kids[c0 + s_jlg], P[k].dom, g);
+            const float *y = Y + (size_t)(c0 + s_jlg) * MLP_OUT;
+            for (int a = 0; a < 3; ++a) {
+                st.cand_x[1][a] = g.r0[a] + fminf(fmaxf(y[1 + a], -1.f), 1.f) * g.rhw;
+                st.cand_x[1][3 + a] = g.t0[a] + fminf(fmaxf(y[4 + a], -1.f), 1.f) * g.thw[a];
+            }
+            st.cand_ok[1] = 1;
         }
     }
 }
@@ -631,24 +670,29 @@ __global__ void __launch_bounds__(MP_BLOCK)
 constexpr int MPO_BLOCK = 256;
 constexpr int MPO_CHUNK = 1024;
 
-// per (problem, model component): v, Rv, kappa, log Z(kappa)  (8 doubles)
-__global__ void mp_obj_prep(const ProbDev *__restrict__ P, const ProbState *__restrict__ S,
+// Candidate c of problem k is row 2k + c of the launch (blockIdx.y); its
+// per-component data start at row 2 ioff[k] + c n1.
+// per (candidate, model component): v, Rv, kappa, log Z(kappa)  (8 doubles);
+// a candidate within zeta of a model mean is flagged infeasible.
+__global__ void mp_obj_prep(const ProbDev *__restrict__ P, ProbState *__restrict__ S,
                             const long long *__restrict__ ioff, double *__restrict__ idata) {
-    const int k = blockIdx.y;
-    const ProbState &st = S[k];
-    if (st.best_child < 0) return;
+    const int k = blockIdx.y >> 1, c = blockIdx.y & 1;
+    ProbState &st = S[k];
+    if (!st.cand_ok[c]) return;
     const MixDev &mx = P[k].mx;
-    const double *x = st.cand_x;
+    const double *x = st.cand_x[c];
+    const double z2 = P[k].zeta * P[k].zeta;
     __shared__ double R[9];
     if (threadIdx.x == 0) rodrigues_dev(x, R);
     __syncthreads();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < mx.n1; i += gridDim.x * blockDim.x) {
         const double *mu = mx.mu1 + 3 * i;
         double m0 = mu[0] - x[3], m1 = mu[1] - x[4], m2 = mu[2] - x[5];
-        double d = sqrt(m0 * m0 + m1 * m1 + m2 * m2);
+        double d2 = m0 * m0 + m1 * m1 + m2 * m2, d = sqrt(d2);
+        if (d2 < z2) atomicOr(&st.cand_bad[c], 1);
         double v0 = m0 / d, v1 = m1 / d, v2 = m2 / d, s = mx.sigma1d[i];
-        double kap = d * d / (s * s) + 1.0;  // Eq. (kappa1)
-        double *o = idata + (ioff[k] + i) * 8;
+        double kap = d2 / (s * s) + 1.0;  // Eq. (kappa1)
+        double *o = idata + (2 * ioff[k] + (long long)c * mx.n1 + i) * 8;
         o[0] = v0;
         o[1] = v1;
         o[2] = v2;
@@ -664,14 +708,14 @@ __global__ void mp_obj_prep(const ProbDev *__restrict__ P, const ProbState *__re
 __global__ void __launch_bounds__(MPO_BLOCK)
     mp_obj_pairs(const ProbDev *__restrict__ P, const ProbState *__restrict__ S, const long long *__restrict__ ioff,
                  const double *__restrict__ idata, double *__restrict__ part, int nblk) {
-    const int k = blockIdx.y;
+    const int k = blockIdx.y >> 1, c = blockIdx.y & 1;
     const ProbState &st = S[k];
     __shared__ double red[MPO_BLOCK / 32];
-    if (st.best_child < 0) return;
+    if (!st.cand_ok[c]) return;
     const MixDev &mx = P[k].mx;
     const int n1 = mx.n1, n2 = mx.n2;
     const long long nself = (long long)n1 * n1, total = nself + (long long)n1 * n2;
-    const double *I = idata + ioff[k] * 8;
+    const double *I = idata + (2 * ioff[k] + (long long)c * n1) * 8;
     double acc = 0.0;
     for (long long qq = (long long)blockIdx.x * MPO_BLOCK + threadIdx.x; qq < total;
          qq += (long long)gridDim.x * MPO_BLOCK) {
@@ -696,21 +740,99 @@ __global__ void __launch_bounds__(MPO_BLOCK)
     if (threadIdx.x == 0) {
         double s = 0.0;
         for (int w = 0; w < MPO_BLOCK / 32; ++w) s += red[w];
-        part[(size_t)k * nblk + blockIdx.x] = s;
+        part[(size_t)blockIdx.y * nblk + blockIdx.x] = s;
     }
 }
 
-// sum the partials in a fixed order and replace d* when the candidate is better
+// Sum the partials in a fixed order; the best feasible candidate replaces d*
+// when smaller.
 __global__ void mp_obj_final(ProbState *__restrict__ S, int nprob, const double *__restrict__ part, int nblk) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nprob) return;
     ProbState &st = S[k];
-    if (st.best_child < 0) return;
-    double f = 0.0;
-    for (int b = 0; b < nblk; ++b) f += part[(size_t)k * nblk + b];
-    if (f < st.dstar) {
-        st.dstar = f;
-        for (int a = 0; a < 6; ++a) st.best_x[a] = st.cand_x[a];
+    for (int c = 0; c < 2; ++c) {
+        if (!st.cand_ok[c] || st.cand_bad[c]) continue;
+        double f = 0.0;
+        for (int b = 0; b < nblk; ++b) f += part[(size_t)(2 * k + c) * nblk + b];
+        if (f < st.dstar) {
+            st.dstar = f;
+            for (int a = 0; a < 6; ++a) st.best_x[a] = st.cand_x[c][a];
+        }
+    }
+}
+
+// ---------------------------------------------------------------- learned form: network inputs and traces
+// The 16 inputs of the queue-ordering network for one sub-cube: centre
+// (rotation / pi, translation in domain units), log2 half-widths relative to
+// the root (/16), lower bound, upper bound and incumbent as f / C22 + 1 (the
+// normalised objective, clipped to [-8, 8]), the gap
+// between incumbent and lower bound, the largest psi_t / pi, and 1.
+__device__ inline void cube_features(const CubeGeom &g, const Domain &dom, double lb, double ub, double dstar,
+                                     double c22, float psit, float *f) {
+    auto nz = [&](double v) -> float {  // -inf -> -8, +inf -> +8
+        const double x = v / c22 + 1.0;
+        return isnan(x) ? 8.f : (float)fmin(fmax(x, -8.0), 8.0);
+    };
+    for (int a = 0; a < 3; ++a) {
+        const double mid = 0.5 * (dom.t_lo[a] + dom.t_hi[a]), half = 0.5 * (dom.t_hi[a] - dom.t_lo[a]);
+        f[a] = (float)(g.r0[a] / M_PI);
+        f[3 + a] = (float)((g.t0[a] - mid) / half);
+        f[7 + a] = (float)(log2(g.thw[a] / half) / 16.0);
+    }
+    f[6] = (float)(log2(g.rhw / M_PI) / 16.0);
+    f[10] = nz(lb);
+    f[11] = nz(ub);
+    f[12] = nz(dstar);
+    f[13] = fminf(fmaxf(f[12] - f[10], -8.f), 8.f);
+    f[14] = psit / (float)M_PI;
+    f[15] = 1.f;
+}
+
+// Network input rows for every child of this iteration.
+__global__ void mp_features(const ProbDev *__restrict__ P, const ProbState *__restrict__ S, const int *__restrict__ off,
+                            int nprob, const Node *__restrict__ kids, const double *__restrict__ kid_ub,
+                            bf16 *__restrict__ X) {
+    const int N = off[nprob];
+    for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < N; w += gridDim.x * blockDim.x) {
+        const int k = mp_find(off, nprob, w);
+        CubeGeom g;
+        decode(kids[w], P[k].dom, g);
+        float f[MLP_IN];
+        cube_features(g, P[k].dom, kids[w].lb, kid_ub[w], S[k].dstar, P[k].c22, kids[w].psit, f);
+        __align__(16) bf16 b[MLP_IN];
+        for (int a = 0; a < MLP_IN; ++a) b[a] = __float2bfloat16_rn(f[a]);
+        uint4 *o = reinterpret_cast<uint4 *>(X + (size_t)w * MLP_IN);
+        o[0] = reinterpret_cast<const uint4 *>(b)[0];
+        o[1] = reinterpret_cast<const uint4 *>(b)[1];
+    }
+}
+
+// Popped sub-cubes of this iteration into each problem's trace (slots from
+// tcount[k]; the count advances in mp_worklist).
+__global__ void mp_trace(const ProbDev *__restrict__ P, const ProbState *__restrict__ S, int nprob,
+                         const Node *__restrict__ parents, int pop, const int *__restrict__ d_iter,
+                         gosma_trace_rec *__restrict__ trace, const int *__restrict__ tcount, int tcap) {
+    const int k = blockIdx.y;
+    const ProbState &st = S[k];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < st.np; i += gridDim.x * blockDim.x) {
+        const int slot = tcount[k] + i;
+        if (slot >= tcap) break;
+        const Node &nd = parents[(size_t)k * pop + i];
+        CubeGeom g;
+        decode(nd, P[k].dom, g);
+        gosma_trace_rec &r = trace[(size_t)k * tcap + slot];
+        cube_features(g, P[k].dom, nd.lb, (double)nd.ubf, st.dstar, P[k].c22, nd.psit, r.feat);
+        for (int a = 0; a < 3; ++a) {
+            r.cube[a] = g.r0[a];
+            r.cube[4 + a] = g.t0[a];
+            r.cube[7 + a] = g.thw[a];
+        }
+        r.cube[3] = g.rhw;
+        r.lb = nd.lb;
+        r.ub = (double)nd.ubf;
+        r.dstar = st.dstar;
+        r.problem = k;
+        r.iteration = *d_iter;
     }
 }
 
@@ -995,8 +1117,20 @@ using namespace gosma;
 
 extern "C" int gosma_bnb_solve_batch(gosma_ctx *ctx, int nprob, const gosma_problem *probs, const gosma_opts *opts_in,
                                      gosma_result *results) {
+    return gosma_bnb_solve_batch_ex(ctx, nprob, probs, opts_in, nullptr, results, nullptr, nullptr);
+}
+
+extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_problem *probs,
+                                        const gosma_opts *opts_in, const gosma_learn_opts *lopts,
+                                        gosma_result *results, gosma_trace_rec *trace, int *trace_count) {
     if (!ctx) return GOSMA_EINVAL;
     ctx->err.clear();
+    gosma_learn_opts lo;
+    memset(&lo, 0, sizeof lo);
+    if (lopts) lo = *lopts;
+    if (lo.trace_cap < 0 || (lo.trace_cap > 0 && (!trace || !trace_count)) || !(lo.beta >= 0))
+        return fail(ctx, GOSMA_EINVAL, "bnb_solve_batch: bad learned-form options");
+    if (lo.use_mlp && !ctx->mlp) return fail(ctx, GOSMA_ENOTREADY, "bnb_solve_batch: no network parameters set");
     if (nprob < 0 || (nprob > 0 && (!probs || !results))) return fail(ctx, GOSMA_EINVAL, "bnb_solve_batch: bad arguments");
     if (nprob == 0) return GOSMA_OK;
     if (nprob > 65535) return fail(ctx, GOSMA_EINVAL, "bnb_solve_batch: at most 65535 problems");
@@ -1116,7 +1250,6 @@ extern "C" int gosma_bnb_solve_batch(gosma_ctx *ctx, int nprob, const gosma_prob
         s.tail = 1;
         s.live = 1;
         s.peak = 1;
-        s.best_child = -1;
         s.done_iter = -1;
         s.minkey = DEAD;
         for (int a = 0; a < 3; ++a) s.best_x[3 + a] = 0.5 * (p.t_lo[a] + p.t_hi[a]);
@@ -1140,6 +1273,7 @@ extern "C" int gosma_bnb_solve_batch(gosma_ctx *ctx, int nprob, const gosma_prob
     if ((e = B.get(&dP, nprob)) == cudaSuccess && (e = B.get(&dS, nprob)) == cudaSuccess &&
         (e = B.get(&Qb.q[0], cap * nprob)) == cudaSuccess && (e = B.get(&Qb.keys[0], cap * nprob)) == cudaSuccess &&
         (e = B.get(&Qb.q[1], cap * nprob)) == cudaSuccess && (e = B.get(&Qb.keys[1], cap * nprob)) == cudaSuccess &&
+        (e = B.get(&Qb.lbk[0], cap * nprob)) == cudaSuccess && (e = B.get(&Qb.lbk[1], cap * nprob)) == cudaSuccess &&
         (e = B.get(&Qb.hist, 2048 * (size_t)nprob)) == cudaSuccess && (e = B.get(&Qb.ch_off, nprob + 1)) == cudaSuccess &&
         (e = B.get(&Qb.c_lt, max_chunks)) == cudaSuccess && (e = B.get(&Qb.c_eq, max_chunks)) == cudaSuccess &&
         (e = B.get(&Qb.c_out, max_chunks)) == cudaSuccess && (e = B.get(&Qb.c_eqb, max_chunks)) == cudaSuccess &&
@@ -1147,8 +1281,8 @@ extern "C" int gosma_bnb_solve_batch(gosma_ctx *ctx, int nprob, const gosma_prob
         (e = B.get(&parents, (size_t)pop * nprob)) == cudaSuccess && (e = B.get(&kids, nkids)) == cudaSuccess &&
         (e = B.get(&kid_ub, nkids)) == cudaSuccess && (e = B.get(&prep, nkids)) == cudaSuccess &&
         (e = B.get(&off, nprob + 1)) == cudaSuccess && (e = B.get(&ioff, nprob)) == cudaSuccess &&
-        (e = B.get(&idata, 8 * (size_t)sum_n1)) == cudaSuccess &&
-        (e = B.get(&part, (size_t)nblk * nprob)) == cudaSuccess) {
+        (e = B.get(&idata, 16 * (size_t)sum_n1)) == cudaSuccess &&
+        (e = B.get(&part, 2 * (size_t)nblk * nprob)) == cudaSuccess) {
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(batch state)");
     std::vector<long long> hio(nprob, 0);
@@ -1163,11 +1297,30 @@ extern "C" int gosma_bnb_solve_batch(gosma_ctx *ctx, int nprob, const gosma_prob
     root.psit = (float)M_PI;
     const uint32_t rkey = order_key(-INFINITY), dead = DEAD;
     if (e == cudaSuccess) e = cudaMemsetAsync(Qb.hist, 0, sizeof(unsigned int) * 2048 * nprob, st);
+    root.ubf = INFINITY;
     for (int k = 0; k < nprob && e == cudaSuccess; ++k) {
         e = cudaMemcpyAsync(Qb.q[0] + (size_t)k * cap, &root, sizeof root, cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(Qb.keys[0] + (size_t)k * cap, &rkey, sizeof rkey, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(Qb.lbk[0] + (size_t)k * cap, &rkey, sizeof rkey, cudaMemcpyHostToDevice, st);
     }
     (void)dead;
+    // learned form: network input rows for every child, and the traces
+    const int max_rows = (int)nkids;
+    const float *Yd = nullptr;
+    bf16 *Xd = nullptr;
+    if (lo.use_mlp) {
+        int rc = mlp_reserve(ctx, max_rows);
+        if (rc) return rc;
+        Xd = mlp_input(ctx->mlp);
+        Yd = mlp_output(ctx->mlp);
+        if (e == cudaSuccess) e = cudaMemsetAsync(mlp_error_flag(ctx->mlp), 0, sizeof(int), st);
+    }
+    gosma_trace_rec *d_trace = nullptr;
+    int *d_tcount = nullptr;
+    if (lo.trace_cap > 0 && e == cudaSuccess) {
+        if ((e = B.get(&d_trace, (size_t)lo.trace_cap * nprob)) == cudaSuccess && (e = B.get(&d_tcount, nprob)) == cudaSuccess)
+            e = cudaMemsetAsync(d_tcount, 0, sizeof(int) * nprob, st);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "batch init");
 
@@ -1217,20 +1370,32 @@ extern "C" int gosma_bnb_solve_batch(gosma_ctx *ctx, int nprob, const gosma_prob
         mp_count<false><<<chunk_grid, CH_BLOCK, 0, st>>>(dP, dS, Qb, nprob);
         mp_cscan_any<false><<<nprob, MP_BLOCK, 0, st>>>(dS, Qb, nprob);
         mp_scatter<false><<<chunk_grid, CH_BLOCK, 0, st>>>(dP, dS, Qb, nprob, parents, pop);
+        if (d_trace) {
+            mp_trace<<<dim3((pop + 127) / 128, nprob), 128, 0, st>>>(dP, dS, nprob, parents, pop, d_iter, d_trace,
+                                                                    d_tcount, lo.trace_cap);
+            ++ctx->launches;
+        }
         mp_count<true><<<chunk_grid, CH_BLOCK, 0, st>>>(dP, dS, Qb, nprob);
         mp_cscan_any<true><<<nprob, MP_BLOCK, 0, st>>>(dS, Qb, nprob);
         mp_scatter<true><<<chunk_grid, CH_BLOCK, 0, st>>>(dP, dS, Qb, nprob, parents, pop);
-        mp_worklist<<<1, MP_BLOCK, 0, st>>>(dS, nprob, off);
+        mp_worklist<<<1, MP_BLOCK, 0, st>>>(dS, nprob, off, d_tcount, lo.trace_cap);
         mp_prep<<<prep_grid, 128, 0, st>>>(dP, off, nprob, parents, pop, prep);
         ctx->launches += 15;
     };
-    auto back = [&]() {
-        mp_append<<<nprob, MP_BLOCK, 0, st>>>(dP, dS, off, kids, kid_ub, Qb);
-        mp_obj_prep<<<dim3((max_n1 + 127) / 128, nprob), 128, 0, st>>>(dP, dS, ioff, idata);
-        mp_obj_pairs<<<dim3(nblk, nprob), MPO_BLOCK, 0, st>>>(dP, dS, ioff, idata, part, nblk);
+    auto back = [&]() -> cudaError_t {
+        cudaError_t eb = cudaSuccess;
+        if (lo.use_mlp) {  // score every child on the tensor cores
+            mp_features<<<prep_grid, 128, 0, st>>>(dP, dS, off, nprob, kids, kid_ub, Xd);
+            ++ctx->launches;
+            eb = mlp_forward_rows(ctx, max_rows, off + nprob, st);
+        }
+        mp_append<<<nprob, MP_BLOCK, 0, st>>>(dP, dS, off, kids, kid_ub, Qb, Yd, lo.beta, lo.seed);
+        mp_obj_prep<<<dim3((max_n1 + 127) / 128, 2 * nprob), 128, 0, st>>>(dP, dS, ioff, idata);
+        mp_obj_pairs<<<dim3(nblk, 2 * nprob), MPO_BLOCK, 0, st>>>(dP, dS, ioff, idata, part, nblk);
         mp_obj_final<<<(nprob + 127) / 128, 128, 0, st>>>(dS, nprob, part, nblk);
         mp_tick<<<1, 32, 0, st>>>(dS, nprob, d_iter, d_time, d_ndone);
         ctx->launches += 5;
+        return eb;
     };
 
     // ---- eager iterations; at TUNE_ITER the candidate block sizes of the bound kernel are timed
@@ -1259,10 +1424,8 @@ extern "C" int gosma_bnb_solve_batch(gosma_ctx *ctx, int nprob, const gosma_prob
         } else {
             e = mp_bound_any(block, ctx, st, dP, off, nprob, parents, pop, prep, kids, kid_ub, smem);
         }
-        if (e == cudaSuccess) {
-            back();
-            e = cudaGetLastError();
-        }
+        if (e == cudaSuccess) e = back();
+        if (e == cudaSuccess) e = cudaGetLastError();
     }
     cudaEventDestroy(ta);
     cudaEventDestroy(tb);
@@ -1276,10 +1439,11 @@ extern "C" int gosma_bnb_solve_batch(gosma_ctx *ctx, int nprob, const gosma_prob
     if (e == cudaSuccess) {
         front();
         cudaError_t e2 = mp_bound_any(block, ctx, st, dP, off, nprob, parents, pop, prep, kids, kid_ub, smem);
-        back();
+        cudaError_t e3 = back();
         cudaMemcpyAsync(h_ndone, d_ndone, sizeof(int), cudaMemcpyDeviceToHost, st);
         e = cudaStreamEndCapture(st, &graph);
         if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = e3;
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
     if (e != cudaSuccess) {
@@ -1358,6 +1522,20 @@ extern "C" int gosma_bnb_solve_batch(gosma_ctx *ctx, int nprob, const gosma_prob
         r.iteration_ms = total_s * 1e3;
         r.launches = ctx->launches;
         r.block_size = block;
+    }
+    if (d_trace) {
+        std::vector<int> cnt(nprob);
+        e = cudaMemcpy(cnt.data(), d_tcount, sizeof(int) * nprob, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(trace, d_trace, sizeof(gosma_trace_rec) * (size_t)lo.trace_cap * nprob, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "batch traces");
+        memcpy(trace_count, cnt.data(), sizeof(int) * nprob);
+    }
+    if (lo.use_mlp) {
+        int herr = 0;
+        e = cudaMemcpy(&herr, mlp_error_flag(ctx->mlp), sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "batch network status");
+        if (herr) return fail(ctx, GOSMA_ETIMEOUT, "bnb_solve_batch: a tensor-core wait timed out");
     }
     return GOSMA_OK;
 }

@@ -53,6 +53,16 @@ class Problem(C.Structure):
 # exported symbols and their signatures (restype, argtypes); the header is the authority
 FP = C.POINTER(C.c_float)
 
+
+class LearnOpts(C.Structure):
+    _fields_ = [("use_mlp", C.c_int), ("beta", C.c_float), ("seed", C.c_int), ("trace_cap", C.c_int)]
+
+
+# gosma_trace_rec as a numpy record
+TRACE_DTYPE = np.dtype([("feat", "<f4", (16,)), ("cube", "<f8", (10,)), ("lb", "<f8"), ("ub", "<f8"),
+                        ("dstar", "<f8"), ("problem", "<i4"), ("iteration", "<i4")])
+assert TRACE_DTYPE.itemsize == 176
+
 SIGNATURES = {
     "gosma_create": (C.c_int, [C.c_int, C.c_void_p, C.POINTER(C.c_void_p)]),
     "gosma_destroy": (None, [C.c_void_p]),
@@ -67,6 +77,8 @@ SIGNATURES = {
     "gosma_bnb_solve": (C.c_int, [C.c_void_p, C.POINTER(Opts), C.POINTER(Result)]),
     "gosma_bnb_start": (C.c_int, [C.c_void_p, C.POINTER(Opts)]),
     "gosma_bnb_solve_batch": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(Opts), C.c_void_p]),
+    "gosma_bnb_solve_batch_ex": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(Opts), C.c_void_p, C.c_void_p,
+                                           C.c_void_p, C.c_void_p]),
     "gosma_bnb_step": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(Result)]),
     "gosma_selftest_approx": (C.c_int, [C.c_void_p, D, D]),
     "gosma_kernel_launches": (C.c_longlong, [C.c_void_p]),
@@ -269,11 +281,16 @@ class Gosma:
         return self._result(r)
 
     def bnb_solve_batch(self, problems, eps=0.1, pop=64, max_nodes=0, max_seconds=0.0, use_sma=True,
-                        sma_max_iter=100, queue_capacity=0):
+                        sma_max_iter=100, queue_capacity=0, learned=None, trace_cap=0):
         """Algorithm 1 for many independent problems at once (list of problem
-        dicts as produced by synth); returns one result dict per problem."""
+        dicts as produced by synth); returns one result dict per problem.
+
+        ``learned``: None (plain) or a dict with ``beta`` and ``seed`` for the
+        network-ordered form (parameters loaded with mlp_set_params).  With
+        ``trace_cap > 0`` returns ``(results, traces)``, traces a list of
+        TRACE_DTYPE arrays, one per problem, in pop order."""
         if not problems:
-            return []
+            return ([], []) if trace_cap > 0 else []
         keep = []
         arr = (Problem * len(problems))()
         for k, pr in enumerate(problems):
@@ -289,9 +306,20 @@ class Gosma:
             p.zeta = float(pr["zeta"])
         o = self._opts(eps, pop, max_nodes, max_seconds, use_sma, sma_max_iter, queue_capacity)
         res = (Result * len(problems))()
-        self._check(self.L.gosma_bnb_solve_batch(self.h, len(problems), C.cast(arr, C.c_void_p), C.byref(o),
-                                                 C.cast(res, C.c_void_p)), "bnb_solve_batch")
-        return [self._result(r) for r in res]
+        lo = LearnOpts(0, 0.0, 0, int(trace_cap))
+        if learned is not None:
+            lo.use_mlp, lo.beta, lo.seed = 1, float(learned.get("beta", 0.0)), int(bool(learned.get("seed", True)))
+        tr = np.zeros(max(1, len(problems) * int(trace_cap)), dtype=TRACE_DTYPE)
+        cnt = np.zeros(len(problems), dtype=np.int32)
+        self._check(self.L.gosma_bnb_solve_batch_ex(self.h, len(problems), C.cast(arr, C.c_void_p), C.byref(o),
+                                                    C.byref(lo), C.cast(res, C.c_void_p),
+                                                    tr.ctypes.data_as(C.c_void_p), cnt.ctypes.data_as(C.c_void_p)),
+                    "bnb_solve_batch")
+        out = [self._result(r) for r in res]
+        if trace_cap > 0:
+            tr = tr.reshape(len(problems), trace_cap)
+            return out, [tr[k, :cnt[k]].copy() for k in range(len(problems))]
+        return out
 
     def bnb_start(self, eps=0.1, pop=1024, max_nodes=0, max_seconds=0.0, use_sma=True, sma_max_iter=100,
                   queue_capacity=0):

@@ -177,3 +177,55 @@ def test_batch_limits_and_errors(ctx):
         ctx.bnb_solve_batch([probs[1], bad], eps=1e-3)
     with pytest.raises(GosmaError):
         ctx.bnb_solve_batch(probs, eps=1e-3, pop=0)
+
+
+# ---------------------------------------------------------------- learned form (network-ordered queue, seeds, traces)
+def _params(seed):
+    from paper_1812_01232_gb300 import learn
+    return learn.init_params(seed)
+
+
+@pytest.mark.parametrize("beta", [0.0, 1e-4])
+def test_learned_form_keeps_the_certificate(ctx, oracle_mod, beta):
+    """The network only reorders pops and proposes seeds: with any weights the
+    certified optimum is the oracle's."""
+    gold = json.load(open(GOLDEN))["1000"]
+    ctx.mlp_set_params(_params(3))
+    p = synth.tiny_problem(1000)
+    r = ctx.bnb_solve_batch([p], eps=1e-3, pop=1024, max_seconds=120, queue_capacity=1 << 26,
+                            learned=dict(beta=beta, seed=True))[0]
+    assert r["status_name"] == "optimal"
+    assert abs(r["f"] - gold["f"]) <= 1e-3 * gold["c22"]
+    assert r["lb"] <= gold["f"] + 1e-9 and gold["lb"] <= r["f"] + 1e-9
+    mix = oracle_mod.Mixtures.from_problem(p)
+    assert oracle_mod.objective_r(mix, r["r"], r["t"]) == pytest.approx(r["f"], rel=1e-10)
+
+
+def test_learned_form_needs_parameters():
+    from paper_1812_01232_gb300.gosma import Gosma, GosmaError
+    c = Gosma(0)
+    with pytest.raises(GosmaError):
+        c.bnb_solve_batch([synth.tiny_problem(1)], eps=1e-2, learned=dict(beta=0.0))
+    c.close()
+
+
+def test_traces(ctx):
+    """Trace records: pop order, the root first, features as documented and
+    cubes inside the search domain."""
+    probs = [synth.tiny_problem(1000), synth.tiny_problem(7, n1=14, n_in=6, n_out=2)]
+    res, tr = ctx.bnb_solve_batch(probs, eps=1e-3, pop=64, max_nodes=20000, trace_cap=256)
+    for k, (p, t) in enumerate(zip(probs, tr)):
+        assert 0 < len(t) <= 256
+        assert np.all(t["problem"] == k) and np.all(np.diff(t["iteration"]) >= 0)
+        assert t["iteration"][0] == 0 and t["lb"][0] == -np.inf
+        f = t["feat"]
+        assert np.all(np.isfinite(f)) and np.all(np.abs(f) <= 8.0) and np.all(f[:, 15] == 1.0)
+        assert f[0, 10] == -8.0 and f[0, 6] == pytest.approx(0.0, abs=1e-6)
+        c = t["cube"]
+        assert np.all(c[:, 4:7] - c[:, 7:10] >= p["t_lo"] - 1e-12) and np.all(c[:, 4:7] + c[:, 7:10] <= p["t_hi"] + 1e-12)
+        assert np.all(np.abs(c[:, 0:3]) + c[:, 3:4] <= np.pi + 1e-12)
+        # features carry the cube: rotation centre / pi and log2 half-width / 16
+        assert np.allclose(f[:, 0:3], c[:, 0:3] / np.pi, atol=1e-2)
+        assert np.allclose(f[:, 6], np.log2(c[:, 3] / np.pi) / 16, atol=1e-2)
+        finite = np.isfinite(t["lb"])
+        assert np.all(t["lb"][finite] <= t["ub"][finite] + 1e-6 * np.abs(t["ub"][finite]))
