@@ -24,6 +24,19 @@ bounded sample of the same workload per step.
 
 Multi-GPU (torchrun): every rank solves its own independent problem (seed +
 rank); no data-path collective; value = pairs of all ranks / max rank time.
+
+Two more measurements ride on the same line (rank 0, N = 1, unless
+--no-extra):
+* "batched": 256 independent problems of uneven sizes (model components
+  U{16..256}, image U{8..128} with 20% outliers, tiny-problem generator,
+  eps 1e-3) in one batched solve (one captured CUDA graph per iteration)
+  under a time budget: aggregate pair-bound evals/s and per-problem time to
+  the certified optimum (p50/p99 over the problems certified in the budget,
+  with the count);
+* "time_to_certified": tiny problems (10 x 8 components, eps 1e-3) solved
+  to the certified optimum by the plain single-problem solver (one after the
+  other), the plain batched solver and the learned batched solver (network
+  weights from paper_1812_01232_gb300/weights), on the same problems.
 """
 from __future__ import annotations
 
@@ -308,10 +321,65 @@ def run_ours(args):
         "clocks": ck,
         "gpu_launches": launches,
     }
+    if world == 1 and not args.no_extra:
+        ctx.close()
+        line["batched"] = run_batched(args.batch_budget)
+        line["time_to_certified"] = run_time_to_certified(8)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def run_batched(budget_s):
+    """Config of 256 uneven problems in one batched solve (see module doc)."""
+    from paper_1812_01232_gb300 import synth
+    from paper_1812_01232_gb300.gosma import Gosma
+    ctx = Gosma(0)
+    probs = synth.uneven_problems(3000, count=256)
+    t0 = time.perf_counter()
+    res = ctx.bnb_solve_batch(probs, eps=1e-3, pop=64, max_seconds=budget_s, queue_capacity=1 << 20)
+    wall = time.perf_counter() - t0
+    dev_s = res[0]["iteration_ms"] / 1e3
+    pairs = float(sum(r["cross_pairs"] for r in res))
+    cert = [r["seconds"] for r in res if r["status_name"] == "optimal"]
+    st = [r["status_name"] for r in res]
+    ctx.close()
+    return {"workload": "256 problems, n1 ~ U{16..256}, n2 ~ U{8..128}, 20%% outliers, eps 1e-3, pop 64 per problem, "
+                        "queue 2^20 per problem, budget %.0f s" % budget_s,
+            "pairs_per_s": pairs / dev_s, "device_s": dev_s, "wall_s": wall,
+            "certified": len(cert), "statuses": {k: st.count(k) for k in sorted(set(st))},
+            "p50_s": float(np.percentile(cert, 50)) if cert else None,
+            "p99_s": float(np.percentile(cert, 99)) if cert else None,
+            "block_size": res[0]["block_size"]}
+
+
+def run_time_to_certified(n_prob):
+    """Plain single, plain batched and learned batched solves of the same tiny problems."""
+    from paper_1812_01232_gb300 import learn, synth
+    from paper_1812_01232_gb300.gosma import Gosma
+    ctx = Gosma(0)
+    eps = 1e-3
+    probs = [synth.tiny_problem(200000 + s) for s in range(n_prob)]
+    out = {"workload": "%d tiny problems (10 x 8 components), eps 1e-3, pop 1024" % n_prob}
+    single = []
+    t0 = time.perf_counter()
+    for p in probs:
+        ctx.set_problem(p)
+        single.append(ctx.bnb_solve(eps=eps, pop=1024, max_seconds=60, queue_capacity=1 << 25))
+    out["plain_single"] = {"wall_s": time.perf_counter() - t0, "nodes": int(sum(r["nodes"] for r in single)),
+                           "certified": int(sum(r["status_name"] == "optimal" for r in single))}
+    ctx.mlp_set_params(learn.load(os.path.join(ROOT, "paper_1812_01232_gb300", "weights", "gosma_mlp.npz")))
+    for name, learned in (("plain_batched", None), ("learned_batched", {"beta": 1e-4, "seed": True})):
+        t0 = time.perf_counter()
+        res = ctx.bnb_solve_batch(probs, eps=eps, pop=1024, max_seconds=120, queue_capacity=1 << 25, learned=learned)
+        out[name] = {"wall_s": time.perf_counter() - t0, "nodes": int(sum(r["nodes"] for r in res)),
+                     "certified": int(sum(r["status_name"] == "optimal" for r in res)),
+                     "agree_with_single": int(sum(abs(r["f"] - q["f"]) <= eps * q["c22"]
+                                                  for r, q in zip(res, single))),
+                     "p50_s": float(np.median([r["seconds"] for r in res]))}
+    ctx.close()
+    return out
 
 
 def main():
@@ -322,6 +390,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the batched and time-to-certificate measurements")
+    ap.add_argument("--batch-budget", type=float, default=20.0, help="seconds for the 256-problem batched solve")
     ap.add_argument("--queue-capacity", type=int, default=1 << 27,
                     help="device queue capacity in sub-cubes (64 bytes each, twice)")
     args = ap.parse_args()
