@@ -130,18 +130,29 @@ class Clocks:
         return out
 
 
+def kernel_source_sha256():
+    """Fingerprint of the bound kernel's device code: the bound core, the
+    double-float helpers, the queue-node helpers and the kernel function."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_1812_01232_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in ("bounds_core.cuh", "dfloat.cuh", "bnb_common.cuh"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    src = open(os.path.join(csrc, "bnb.cu")).read()
+    i = src.index("bound_children(MixDev mx")
+    j = src.index("\n}\n", i)
+    h.update(src[i:j].encode())
+    return h.hexdigest()
+
+
 def kernel_traffic():
     """DRAM bytes per launch of the bound kernel from the committed ncu capture,
-    or None when the kernel source changed since the capture."""
-    import hashlib
+    or None when the kernel's device code changed since the capture."""
     prof = os.path.join(ROOT, "profiles", "bound_children_traffic.json")
     if not os.path.exists(prof):
         return None
     rec = json.load(open(prof))
-    h = hashlib.sha256()
-    for f in ("bounds_core.cuh", "bnb.cu"):
-        h.update(open(os.path.join(ROOT, "paper_1812_01232_gb300", "csrc", f), "rb").read())
-    return rec.get("bytes_per_launch") if rec.get("source_sha256") == h.hexdigest() else None
+    return rec.get("bytes_per_launch") if rec.get("source_sha256") == kernel_source_sha256() else None
 
 
 def make_problem(rank):

@@ -554,7 +554,9 @@ static int launch_children_any(gosma_ctx *ctx, const Domain &dom, BnbState *s, i
     case 32: return launch_children<32>(ctx, dom, s, np);
     case 64: return launch_children<64>(ctx, dom, s, np);
     case 128: return launch_children<128>(ctx, dom, s, np);
-    default: return launch_children<256>(ctx, dom, s, np);
+    case 256: return launch_children<256>(ctx, dom, s, np);
+    case 512: return launch_children<512>(ctx, dom, s, np);
+    default: return launch_children<1024>(ctx, dom, s, np);
     }
 }
 

@@ -34,10 +34,17 @@ size_t bounds_smem_bytes(int n1, int n2) { return bounds_smem_arrays_bytes(n1, n
 // Threads per cube: enough to give every thread a few model rows.
 int bounds_block_size(int n1, int n2) {
     long long work = (long long)n1 * n2 + (long long)n1 * (n1 - 1) / 2;
-    if (work <= 1024) return 32;
-    if (work <= 8192) return 64;
-    if (n1 <= 256) return 128;
-    return 256;
+    int b;
+    if (work <= 1024) b = 32;
+    else if (work <= 8192) b = 64;
+    else if (n1 <= 256) b = 128;
+    else b = 256;
+    // Large mixtures leave room for few blocks per SM in shared memory: widen
+    // the block (up to one thread per model row, at most 1024) until 32 warps
+    // per SM can hide the latencies.
+    const long long per_sm = (227LL * 1024) / (long long)(bounds_smem_bytes(n1, n2) + sizeof(CubeShared) + 1024);
+    while (b < 1024 && b < n1 && per_sm * b < 1024) b *= 2;
+    return b;
 }
 
 template <int BLOCK>
@@ -79,7 +86,9 @@ int launch_bounds(gosma_ctx *ctx, const gosma_cube *d_cubes, int n, gosma_bound 
     case 32: return launch_t<32>(ctx, d_cubes, n, d_out, rot);
     case 64: return launch_t<64>(ctx, d_cubes, n, d_out, rot);
     case 128: return launch_t<128>(ctx, d_cubes, n, d_out, rot);
-    default: return launch_t<256>(ctx, d_cubes, n, d_out, rot);
+    case 256: return launch_t<256>(ctx, d_cubes, n, d_out, rot);
+    case 512: return launch_t<512>(ctx, d_cubes, n, d_out, rot);
+    default: return launch_t<1024>(ctx, d_cubes, n, d_out, rot);
     }
 }
 

@@ -924,7 +924,9 @@ static cudaError_t mp_bound_any(int block, gosma_ctx *ctx, cudaStream_t st, cons
     switch (block) {
     case 64: return mp_bound_launch<64>(ctx, st, P, off, nprob, parents, pop, prep, kids, kid_ub, smem);
     case 128: return mp_bound_launch<128>(ctx, st, P, off, nprob, parents, pop, prep, kids, kid_ub, smem);
-    default: return mp_bound_launch<256>(ctx, st, P, off, nprob, parents, pop, prep, kids, kid_ub, smem);
+    case 256: return mp_bound_launch<256>(ctx, st, P, off, nprob, parents, pop, prep, kids, kid_ub, smem);
+    case 512: return mp_bound_launch<512>(ctx, st, P, off, nprob, parents, pop, prep, kids, kid_ub, smem);
+    default: return mp_bound_launch<1024>(ctx, st, P, off, nprob, parents, pop, prep, kids, kid_ub, smem);
     }
 }
 
@@ -1075,7 +1077,7 @@ struct BatchRefiner {
             if (e != cudaSuccess) return e;
             obj_prep<<<dim3((max_n1 + 127) / 128, cnt), 128, 0, st>>>(mm, d_x, d_ri);
             obj_pairs<<<dim3(nblk, cnt), OBJ_BLOCK, 0, st>>>(mm, d_x, d_ri, d_part, nblk);
-            obj_final<<<(cnt + 63) / 64, 64, 0, st>>>(cnt, d_x, d_part, nblk, d_out);
+            obj_final<<<(cnt + OBJ_FINAL_WARPS - 1) / OBJ_FINAL_WARPS, 32 * OBJ_FINAL_WARPS, 0, st>>>(cnt, d_x, d_part, nblk, d_out);
             ctx->launches += 3;
             e = cudaGetLastError();
             if (e == cudaSuccess) e = cudaMemcpyAsync(hout, d_out, sizeof(double) * 7 * cnt, cudaMemcpyDeviceToHost, st);
@@ -1409,7 +1411,9 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
         front();
         if (iter == TUNE_ITER) {
             float best = 1e30f;
-            for (int cand : {64, 128, 256}) {
+            const int wide = bounds_block_size(max_n1, max_n2);  // > 256 for large mixtures
+            for (int cand : {64, 128, 256, wide > 256 ? wide : 0}) {
+                if (!cand) continue;
                 cudaEventRecord(ta, st);
                 e = mp_bound_any(cand, ctx, st, dP, off, nprob, parents, pop, prep, kids, kid_ub, smem);
                 cudaEventRecord(tb, st);

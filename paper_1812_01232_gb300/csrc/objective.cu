@@ -39,7 +39,8 @@ int objective_grad_device(gosma_ctx *ctx, int count, const double *h_x, double *
     ++ctx->launches;
     obj_pairs<<<dim3(nblk, count), OBJ_BLOCK, 0, ctx->stream>>>(OneMix{ctx->mix}, dx, di, dp, nblk);
     ++ctx->launches;
-    obj_final<<<(count + 63) / 64, 64, 0, ctx->stream>>>(count, dx, dp, nblk, dout);
+    obj_final<<<(count + OBJ_FINAL_WARPS - 1) / OBJ_FINAL_WARPS, 32 * OBJ_FINAL_WARPS, 0, ctx->stream>>>(count, dx, dp, nblk,
+                                                                                                   dout);
     ++ctx->launches;
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "launch(objective)");
@@ -258,7 +259,8 @@ extern "C" int gosma_eval_objective_grad_noalloc(gosma_ctx *ctx, int count, cons
     ++ctx->launches;
     obj_pairs<<<dim3(nblk, count), OBJ_BLOCK, 0, ctx->stream>>>(OneMix{ctx->mix}, d_x, di, dp, nblk);
     ++ctx->launches;
-    obj_final<<<(count + 63) / 64, 64, 0, ctx->stream>>>(count, d_x, dp, nblk, d_out);
+    obj_final<<<(count + OBJ_FINAL_WARPS - 1) / OBJ_FINAL_WARPS, 32 * OBJ_FINAL_WARPS, 0, ctx->stream>>>(count, d_x, dp, nblk,
+                                                                                                   d_out);
     ++ctx->launches;
     e = cudaGetLastError();
     return e == cudaSuccess ? GOSMA_OK : cuda_fail(ctx, e, "launch(objective, no-alloc)");

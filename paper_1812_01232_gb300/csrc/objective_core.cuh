@@ -167,14 +167,20 @@ __global__ void __launch_bounds__(OBJ_BLOCK) obj_pairs(Src src, const double *__
     }
 }
 
+// One warp per pose (launch OBJ_FINAL_WARPS warps per block): lanes sum
+// strided block partials, then a warp reduction in a fixed order.
+constexpr int OBJ_FINAL_WARPS = 4;
 template <int = 0>
 __global__ void obj_final(int count, const double *__restrict__ x, const double *__restrict__ part, int nblk,
                           double *__restrict__ out) {
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= count) return;
+    const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (p >= count) return;  // warp-uniform
     double s[7] = {0, 0, 0, 0, 0, 0, 0};
-    for (int b = 0; b < nblk; ++b)
+    for (int b = lane; b < nblk; b += 32)
         for (int k = 0; k < 7; ++k) s[k] += part[((size_t)p * nblk + b) * 7 + k];
+    for (int k = 0; k < 7; ++k)
+        for (int o = 16; o > 0; o >>= 1) s[k] += __shfl_down_sync(0xffffffffu, s[k], o);
+    if (lane != 0) return;
     // d/dr = J_l(r)^T d/domega, J_l = I + a [r]x + b [r]x^2 (left Jacobian of SO(3))
     const double *r = x + 6 * p;
     double th2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2], th = sqrt(th2), a, b;

@@ -1,0 +1,93 @@
+"""Small, fixed GPU workloads for profiler captures (ncu), one per kernel family.
+
+    python -m paper_1812_01232_gb300.profile_cases stress --cubes 4096 --reps 2
+    python -m paper_1812_01232_gb300.profile_cases mlp --steps 4
+    python -m paper_1812_01232_gb300.profile_cases batch --problems 64 --max-nodes 100000
+
+stress  Theorem 1 bounds of `cubes` sub-cubes of the 2048 x 512 stress problem
+        (device buffers), `reps` launches of the bound kernel.
+mlp     `steps` training steps of the queue-ordering network on 65,536 random
+        rows (batch 4,096): forward, backward and Adam on the tensor cores.
+batch   one batched solve of `problems` uneven problems (tiny generator,
+        n1 ~ U{16..256}, n2 ~ U{8..128}) with a per-problem node limit.
+Each prints one line of timing so that the plain run can be compared.
+"""
+from __future__ import annotations
+
+import argparse
+import sys
+import time
+
+import numpy as np
+
+from . import learn, synth
+from .gosma import Gosma
+
+
+def stress(a):
+    import torch
+    prob = synth.stress_problem(4000)
+    ctx = Gosma(0)
+    ctx.set_problem(prob)
+    cubes = synth.tree_cubes(4001, a.cubes, prob["t_lo"], prob["t_hi"], 2, 12,
+                             near=(prob["r_gt"], prob["t_gt"]), near_frac=0.3)
+    dc = torch.from_numpy(cubes).cuda()
+    lb = torch.empty(len(cubes), dtype=torch.float64, device="cuda")
+    ub = torch.empty_like(lb)
+    ctx.eval_bounds(dc, lb, ub)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(a.reps):
+        ctx.eval_bounds(dc, lb, ub)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / a.reps
+    n1, n2 = len(prob["sigma1"]), len(prob["kappa2"])
+    print("stress: %d cubes, %.3f ms per launch, %.3e cross pairs/s, %.3e self pairs/s" % (
+        len(cubes), 1e3 * dt, len(cubes) * n1 * n2 / dt, len(cubes) * n1 * (n1 - 1) / 2 / dt))
+
+
+def mlp(a):
+    ctx = Gosma(0)
+    rng = np.random.default_rng(0)
+    n = 65536
+    x = rng.standard_normal((n, 16)).astype(np.float32)
+    label = (rng.random(n) < 0.2).astype(np.float32)
+    target = rng.uniform(-1, 1, (n, 6)).astype(np.float32)
+    ctx.mlp_set_params(learn.init_params(0))
+    t0 = time.perf_counter()
+    losses = ctx.mlp_train(x, label, target, batch=4096, steps=a.steps, lr=1e-3)
+    dt = time.perf_counter() - t0
+    y = ctx.mlp_forward(x)
+    print("mlp: %d steps in %.3f s, loss %.4f -> %.4f, forward %d rows ok=%s" % (
+        a.steps, dt, losses[0], losses[-1], n, bool(np.isfinite(y).all())))
+
+
+def batch(a):
+    ctx = Gosma(0)
+    probs = synth.uneven_problems(3000, count=a.problems)
+    t0 = time.perf_counter()
+    res = ctx.bnb_solve_batch(probs, eps=1e-3, pop=64, max_nodes=a.max_nodes, queue_capacity=1 << 20)
+    dt = time.perf_counter() - t0
+    pairs = sum(r["cross_pairs"] for r in res)
+    print("batch: %d problems, %.3f s wall, %.3f s device, %.3e pairs/s, block %d" % (
+        len(res), dt, res[0]["iteration_ms"] / 1e3, pairs / (res[0]["iteration_ms"] / 1e3), res[0]["block_size"]))
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    sub = ap.add_subparsers(dest="case", required=True)
+    s = sub.add_parser("stress")
+    s.add_argument("--cubes", type=int, default=4096)
+    s.add_argument("--reps", type=int, default=2)
+    m = sub.add_parser("mlp")
+    m.add_argument("--steps", type=int, default=4)
+    b = sub.add_parser("batch")
+    b.add_argument("--problems", type=int, default=64)
+    b.add_argument("--max-nodes", type=int, default=100000)
+    a = ap.parse_args(argv)
+    {"stress": stress, "mlp": mlp, "batch": batch}[a.case](a)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
