@@ -23,7 +23,10 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <mutex>
+#include <thread>
 #include <vector>
 
 #include "bnb_common.cuh"
@@ -1045,9 +1048,9 @@ struct BatchRefiner {
         return cudaMemcpyAsync(d_mixes, mixes.data(), sizeof(MixDev) * nprob, cudaMemcpyHostToDevice, st);
     }
 
-    // One refinement wave; hs is the host copy of the problem states (its
-    // d* and best poses are updated with what is sent to the device).
-    cudaError_t wave(std::vector<ProbState> &hs) {
+    // One refinement wave over a host snapshot hs of the problem states: the
+    // improved incumbents are appended to out (and written into hs).
+    cudaError_t wave(ProbState *hs, std::vector<Incumbent> &out) {
         act.clear();
         for (int k = 0; k < nprob; ++k)
             if (!hs[k].done && hs[k].dstar < refined_f[k]) {
@@ -1059,6 +1062,7 @@ struct BatchRefiner {
         if (act.empty()) return cudaSuccess;
         cudaError_t e = cudaSuccess;
         for (;;) {
+            if (stop_flag && stop_flag->load()) break;
             who.clear();
             long long rows = 0;
             for (int k : act) {
@@ -1078,38 +1082,47 @@ struct BatchRefiner {
             obj_prep<<<dim3((max_n1 + 127) / 128, cnt), 128, 0, st>>>(mm, d_x, d_ri);
             obj_pairs<<<dim3(nblk, cnt), OBJ_BLOCK, 0, st>>>(mm, d_x, d_ri, d_part, nblk);
             obj_final<<<(cnt + OBJ_FINAL_WARPS - 1) / OBJ_FINAL_WARPS, 32 * OBJ_FINAL_WARPS, 0, st>>>(cnt, d_x, d_part, nblk, d_out);
-            ctx->launches += 3;
+            launches += 3;
             e = cudaGetLastError();
             if (e == cudaSuccess) e = cudaMemcpyAsync(hout, d_out, sizeof(double) * 7 * cnt, cudaMemcpyDeviceToHost, st);
             if (e == cudaSuccess) e = cudaStreamSynchronize(st);
             if (e != cudaSuccess) return e;
             for (int q = 0; q < cnt; ++q) L[who[q]].give(hout[7 * q], hout + 7 * q + 1);
         }
-        int nu = 0;
         for (int k : act) {
             const Lbfgs &l = L[k];
             if (l.fx < hs[k].dstar) {
-                Incumbent &u = hupd[nu++];
+                Incumbent u;
                 u.f = l.fx;
                 memcpy(u.x, l.x, sizeof u.x);
                 u.k = k;
                 u.pad = 0;
+                out.push_back(u);
                 hs[k].dstar = l.fx;
                 memcpy(hs[k].best_x, l.x, sizeof u.x);
             }
             refined_f[k] = hs[k].dstar;
         }
-        if (!nu) return cudaSuccess;
-        e = cudaMemcpyAsync(d_upd, hupd, sizeof(Incumbent) * nu, cudaMemcpyHostToDevice, st);
+        return cudaSuccess;
+    }
+
+    // Improvements go to the device through mp_apply on the iteration's stream
+    // (ordered between graph replays); mp_apply keeps the smaller of the two.
+    cudaError_t apply(cudaStream_t sm, ProbState *S_dev, const std::vector<Incumbent> &u) {
+        if (u.empty()) return cudaSuccess;
+        const int nu = (int)std::min<size_t>(u.size(), (size_t)nprob);
+        memcpy(hupd, u.data(), sizeof(Incumbent) * nu);
+        cudaError_t e = cudaMemcpyAsync(d_upd, hupd, sizeof(Incumbent) * nu, cudaMemcpyHostToDevice, sm);
         if (e != cudaSuccess) return e;
-        mp_apply<<<(nu + 127) / 128, 128, 0, st>>>(S_dev, d_upd, nu);
-        ++ctx->launches;
+        mp_apply<<<(nu + 127) / 128, 128, 0, sm>>>(S_dev, d_upd, nu);
+        ++launches;
         e = cudaGetLastError();
-        // the staging buffer is reused by the next wave: wait for the copy
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        // the staging buffer is reused by the next apply: wait for the copy
+        if (e == cudaSuccess) e = cudaStreamSynchronize(sm);
         return e;
     }
-    ProbState *S_dev = nullptr;
+    long long launches = 0;
+    const std::atomic<bool> *stop_flag = nullptr;  // ends a wave between rounds
 };
 
 
@@ -1161,6 +1174,7 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
     struct StreamGuard {
         cudaStream_t s;
         ~StreamGuard() {
+            if (!s) return;
             cudaStreamSynchronize(s);
             cudaStreamDestroy(s);
         }
@@ -1342,20 +1356,80 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
     } pin_guard{h_ndone};
     e = cudaMemsetAsync(d_iter, 0, sizeof(int), st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "batch counters");
+    // ---- incumbent refinement (SMA, Sec. 5), overlapped with the iterations:
+    // a host thread copies a snapshot of the problem states on its own
+    // stream (fields it reads may be mid-update; that only affects which
+    // starting poses it picks), refines every improved incumbent in lock step
+    // and hands the results to this thread, which applies them on the
+    // iteration stream between graph replays (mp_apply keeps the smaller d*).
+    cudaStream_t st2 = nullptr;
+    if (o.use_sma && (e = cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking)) != cudaSuccess)
+        return cuda_fail(ctx, e, "cudaStreamCreate");
+    StreamGuard stream2_guard{st2};
     BatchRefiner refine;
     refine.ctx = ctx;
-    refine.st = st;
+    refine.st = st2;
     refine.nprob = nprob;
     refine.max_iter = o.sma_max_iter;
-    refine.S_dev = dS;
-    if (o.use_sma && (e = refine.init(B, hp, probs, sum_n1)) != cudaSuccess) return cuda_fail(ctx, e, "batch refinement set-up");
-    // SMA wave: read the problem states, refine the improved incumbents
-    auto sma_wave = [&]() -> cudaError_t {
+    ProbState *h_snap = nullptr;
+    if (o.use_sma) {
+        if ((e = refine.init(B, hp, probs, sum_n1)) != cudaSuccess) return cuda_fail(ctx, e, "batch refinement set-up");
+        if ((e = cudaMallocHost((void **)&h_snap, sizeof(ProbState) * nprob)) != cudaSuccess)
+            return cuda_fail(ctx, e, "cudaMallocHost");
+    }
+    struct SnapFree {
+        ProbState *p;
+        ~SnapFree() {
+            if (p) cudaFreeHost(p);
+        }
+    } snap_guard{h_snap};
+    struct Worker {
+        std::thread th;
+        std::mutex mu;
+        std::atomic<bool> stop{false};
+        std::vector<Incumbent> pending;
+        cudaError_t err = cudaSuccess;
+        ~Worker() {
+            stop = true;
+            if (th.joinable()) th.join();
+        }
+    } wk;
+    refine.stop_flag = &wk.stop;
+    auto worker = [&]() {
+        cudaSetDevice(ctx->device);
+        std::vector<Incumbent> out;
+        while (!wk.stop.load()) {
+            cudaError_t e1 = cudaMemcpyAsync(h_snap, dS, sizeof(ProbState) * nprob, cudaMemcpyDeviceToHost, st2);
+            if (e1 == cudaSuccess) e1 = cudaStreamSynchronize(st2);
+            out.clear();
+            if (e1 == cudaSuccess) e1 = refine.wave(h_snap, out);
+            {
+                std::lock_guard<std::mutex> lock(wk.mu);
+                if (e1 != cudaSuccess) {
+                    wk.err = e1;
+                    return;
+                }
+                wk.pending.insert(wk.pending.end(), out.begin(), out.end());
+            }
+            if (out.empty()) std::this_thread::sleep_for(std::chrono::microseconds(200));
+        }
+    };
+    // the best pending improvement per problem, applied on the iteration stream
+    auto apply_pending = [&]() -> cudaError_t {
         if (!o.use_sma) return cudaSuccess;
-        cudaError_t e1 = cudaMemcpyAsync(hs.data(), dS, sizeof(ProbState) * nprob, cudaMemcpyDeviceToHost, st);
-        if (e1 == cudaSuccess) e1 = cudaStreamSynchronize(st);
-        if (e1 == cudaSuccess) e1 = refine.wave(hs);
-        return e1;
+        std::vector<Incumbent> u;
+        {
+            std::lock_guard<std::mutex> lock(wk.mu);
+            if (wk.err != cudaSuccess) return wk.err;
+            u.swap(wk.pending);
+        }
+        if (u.empty()) return cudaSuccess;
+        std::sort(u.begin(), u.end(), [](const Incumbent &a, const Incumbent &b) { return a.k < b.k || (a.k == b.k && a.f < b.f); });
+        size_t w = 0;
+        for (size_t i = 0; i < u.size(); ++i)
+            if (w == 0 || u[w - 1].k != u[i].k) u[w++] = u[i];
+        u.resize(w);
+        return refine.apply(st, dS, u);
     };
     mp_start<<<1, 1, 0, st>>>(d_time);
     ++ctx->launches;
@@ -1433,7 +1507,6 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
     }
     cudaEventDestroy(ta);
     cudaEventDestroy(tb);
-    if (e == cudaSuccess) e = sma_wave();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "batch iterations");
 
     // ---- one iteration captured in a CUDA graph, replayed until every problem is done
@@ -1454,6 +1527,7 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
         if (graph) cudaGraphDestroy(graph);
         return cuda_fail(ctx, e, "batch graph capture");
     }
+    if (o.use_sma) wk.th = std::thread(worker);
     const int poll = 8;
     bool timed_out = false;
     for (; iter < max_iters && e == cudaSuccess; ++iter) {
@@ -1461,7 +1535,7 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
         if (e == cudaSuccess && (iter % poll) == poll - 1) {
             e = cudaStreamSynchronize(st);
             if (e == cudaSuccess && *h_ndone >= nprob) break;
-            if (e == cudaSuccess) e = sma_wave();
+            if (e == cudaSuccess) e = apply_pending();
             double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
             if (o.max_seconds > 0 && el > o.max_seconds) {
                 timed_out = true;
@@ -1470,6 +1544,13 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
         }
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    wk.stop = true;
+    if (wk.th.joinable()) wk.th.join();
+    // improvements that arrived after the last poll still count for problems
+    // that are not certified (they never move a certified d* past its bound)
+    if (e == cudaSuccess) e = apply_pending();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    ctx->launches += refine.launches;
     cudaGraphExecDestroy(exec);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "batch replay");
