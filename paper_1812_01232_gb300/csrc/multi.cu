@@ -7,7 +7,9 @@
 //                problem's global lower bound) and the stopping test
 //                d* - lb <= eps, then the `pop` best hypercubes by an exact
 //                radix select (ties in queue order);
-//   mp_worklist  prefix sums of the children counts;
+//   mp_offsets   prefix sums of the children counts (each unfinished problem
+//                pops up to pop x nprob / (unfinished problems), so the last
+//                problems of a batch keep the GPU busy);
 //   mp_prep      per child: cell decode and the per-cube pre-pass;
 //   mp_bound     one persistent launch bounds the children of all problems
 //                (each block looks up its child's problem and mixtures);
@@ -83,6 +85,7 @@ struct QueueBufs {
     unsigned int *hist;  // nprob x 2048
     int *ch_off;         // nprob + 1: first chunk of each problem
     int *c_lt, *c_eq, *c_out, *c_eqb, *c_live, *c_base;  // per chunk
+    int *quota;  // hypercubes each unfinished problem may pop this iteration
 };
 
 // block-wide exclusive scan (blockDim.x threads, a multiple of 32, <= 1024)
@@ -163,10 +166,14 @@ __device__ inline int mp_find(const int *__restrict__ off, int nprob, int c) {
 //   mp_ccount / mp_cscan / mp_cscatter  compaction into the other buffer
 //               when half of a segment is dead or the tail nears capacity.
 
-__global__ void mp_chunks(ProbState *__restrict__ S, int nprob, int *__restrict__ ch_off) {
+// Chunk offsets of the running problems, and this iteration's pop quota: the
+// unfinished problems share the children buffer (pop x nprob parents), so a
+// problem that is left alone pops more, within its segment's capacity / 16.
+__global__ void mp_chunks(const ProbDev *__restrict__ P, ProbState *__restrict__ S, int nprob, QueueBufs Qb,
+                          int pop) {
     __shared__ int sh[32];
-    __shared__ int carry;
-    if (threadIdx.x == 0) carry = 0;
+    __shared__ int carry, running;
+    if (threadIdx.x == 0) carry = running = 0;
     __syncthreads();
     for (int b0 = 0; b0 < nprob; b0 += blockDim.x) {
         const int k = b0 + threadIdx.x;
@@ -174,12 +181,22 @@ __global__ void mp_chunks(ProbState *__restrict__ S, int nprob, int *__restrict_
         if (k < nprob && !S[k].done) v = (int)((S[k].tail + CH_KEYS - 1) / CH_KEYS);
         int tot;
         int ex = mp_scan(v, sh, tot);
-        if (k < nprob) ch_off[k] = carry + ex;
-        __syncthreads();
-        if (threadIdx.x == 0) carry += tot;
+        if (k < nprob) Qb.ch_off[k] = carry + ex;
+        int rt;
+        mp_scan(k < nprob && !S[k].done ? 1 : 0, sh, rt);
+        if (threadIdx.x == 0) {
+            carry += tot;
+            running += rt;
+        }
         __syncthreads();
     }
-    if (threadIdx.x == 0) ch_off[nprob] = carry;
+    if (threadIdx.x == 0) {
+        Qb.ch_off[nprob] = carry;
+        long long q = running > 0 ? (long long)pop * nprob / running : pop;
+        const long long cap16 = (long long)(P[0].cap / 16);
+        q = q < cap16 ? q : cap16;
+        *Qb.quota = (int)(q > pop ? q : pop);
+    }
 }
 
 // Histogram pass 1, 2 or 3 over the chunks; pass 1 also takes the minimum.
@@ -232,8 +249,8 @@ __global__ void __launch_bounds__(CH_BLOCK)
 // number of hypercubes to pop, the compaction decision and the first digit of
 // the threshold key.  Leaves the problem's histogram zeroed.
 __global__ void __launch_bounds__(MP_BLOCK)
-    mp_decide(const ProbDev *__restrict__ P, ProbState *__restrict__ S, QueueBufs Qb, int pop,
-              const int *__restrict__ d_iter, long long max_nodes) {
+    mp_decide(const ProbDev *__restrict__ P, ProbState *__restrict__ S, QueueBufs Qb, const int *__restrict__ d_iter,
+              long long max_nodes) {
     __shared__ int sh[32];
     __shared__ int s_bin;
     __shared__ unsigned int s_before;
@@ -259,14 +276,15 @@ __global__ void __launch_bounds__(MP_BLOCK)
             st.done = 1 + GOSMA_NODE_LIMIT;
             st.done_iter = *d_iter;
         } else {
-            take = (int)(live < (unsigned long long)pop ? live : (unsigned long long)pop);
+            const unsigned long long qt = (unsigned long long)*Qb.quota;
+            take = (int)(live < qt ? live : qt);
         }
         st.np = take;
         st.nodes += 8LL * take;
         st.live = live - take;
         st.minkey = DEAD;  // reset for the next iteration's pass 1
         const unsigned long long rest = live - take;
-        st.cmp = take > 0 && (st.tail >= 2 * rest + CH_KEYS || st.tail + 8ULL * pop > P[k].cap);
+        st.cmp = take > 0 && (st.tail >= 2 * rest + CH_KEYS || st.tail + 8ULL * (unsigned)*Qb.quota > P[k].cap);
         s_bin = take;
         s_live = live;
     }
@@ -422,7 +440,7 @@ __global__ void __launch_bounds__(MP_BLOCK)
 template <bool CMP>
 __global__ void __launch_bounds__(CH_BLOCK)
     mp_scatter(const ProbDev *__restrict__ P, const ProbState *__restrict__ S, QueueBufs Qb, int nprob,
-               Node *__restrict__ parents, int pop) {
+               Node *__restrict__ parents, const int *__restrict__ off) {
     __shared__ int sh[32];
     const int nch = Qb.ch_off[nprob];
     for (int c = blockIdx.x; c < nch; c += gridDim.x) {
@@ -476,8 +494,8 @@ __global__ void __launch_bounds__(CH_BLOCK)
                             okeys[pos] = kk[j];
                             olbk[pos] = lbk[i];
                         }
-                    } else if (pos < pop) {
-                        parents[(size_t)k * pop + pos] = q[i];
+                    } else if (pos < st.np) {  // holds when the counts agree
+                        parents[(size_t)(off[k] >> 3) + pos] = q[i];
                         keys[i] = DEAD;
                     }
                     ++pos;
@@ -488,22 +506,15 @@ __global__ void __launch_bounds__(CH_BLOCK)
     }
 }
 
-// Prefix sums of the children counts (one block); compacted segments take
-// over from the old buffers.
-__global__ void mp_worklist(ProbState *__restrict__ S, int nprob, int *__restrict__ off, int *__restrict__ tcount,
-                            int tcap) {
+// Prefix sums of the children counts (one block): problem k's children are
+// [off[k], off[k + 1]) and its parents start at off[k] / 8.
+__global__ void mp_offsets(const ProbState *__restrict__ S, int nprob, int *__restrict__ off) {
     __shared__ int sh[32];
     __shared__ int carry;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
     for (int b0 = 0; b0 < nprob; b0 += MP_BLOCK) {
-        int k = b0 + threadIdx.x;
-        if (k < nprob && S[k].cmp) {  // the compacted copy becomes the queue
-            S[k].cur ^= 1;
-            S[k].tail = S[k].cmp_tail;
-            S[k].cmp = 0;
-        }
-        if (k < nprob && tcount) tcount[k] = min(tcap, tcount[k] + S[k].np);
+        const int k = b0 + threadIdx.x;
         int v = k < nprob ? 8 * S[k].np : 0;
         int tot;
         int ex = mp_scan(v, sh, tot);
@@ -515,12 +526,24 @@ __global__ void mp_worklist(ProbState *__restrict__ S, int nprob, int *__restric
     if (threadIdx.x == 0) off[nprob] = carry;
 }
 
+// After compaction: the compacted copies become the queues; trace counts advance.
+__global__ void mp_flip(ProbState *__restrict__ S, int nprob, int *__restrict__ tcount, int tcap) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nprob; k += gridDim.x * blockDim.x) {
+        if (S[k].cmp) {
+            S[k].cur ^= 1;
+            S[k].tail = S[k].cmp_tail;
+            S[k].cmp = 0;
+        }
+        if (tcount) tcount[k] = min(tcap, tcount[k] + S[k].np);
+    }
+}
+
 __global__ void mp_prep(const ProbDev *__restrict__ P, const int *__restrict__ off, int nprob,
-                        const Node *__restrict__ parents, int pop, CubePrep *__restrict__ prep) {
+                        const Node *__restrict__ parents, CubePrep *__restrict__ prep) {
     const int N = off[nprob];
     for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < N; w += gridDim.x * blockDim.x) {
         int k = mp_find(off, nprob, w), c = w - off[k];
-        const Node p = parents[(size_t)k * pop + (c >> 3)];
+        const Node p = parents[w >> 3];
         Node ch = child_of(p, c & 7, split_rotation(p));
         CubeGeom g;
         decode(ch, P[k].dom, g);
@@ -531,7 +554,7 @@ __global__ void mp_prep(const ProbDev *__restrict__ P, const int *__restrict__ o
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK)
     mp_bound(const ProbDev *__restrict__ P, const int *__restrict__ off, int nprob, const Node *__restrict__ parents,
-             int pop, const CubePrep *__restrict__ prep, Node *__restrict__ kids, double *__restrict__ kid_ub) {
+             const CubePrep *__restrict__ prep, Node *__restrict__ kids, double *__restrict__ kid_ub) {
     extern __shared__ float smem_f[];
     __shared__ CubeShared cs;
     __shared__ CubeSums sums;
@@ -541,7 +564,7 @@ __global__ void __launch_bounds__(BLOCK)
         const int k = mp_find(off, nprob, w), c = w - off[k];
         const MixDev &mx = P[k].mx;
         SmemArrays sm = carve(smem_f, mx.n1, mx.n2);
-        const Node &pr = parents[(size_t)k * pop + (c >> 3)];
+        const Node &pr = parents[w >> 3];
         const bool rot = split_rotation(pr);
         const bool need_self = !(pr.flags & 1u) || !rot;
         cube_bounds<BLOCK>(mx, prep[w], P[k].zeta2, need_self, cs, sm, sums);
@@ -811,16 +834,16 @@ __global__ void mp_features(const ProbDev *__restrict__ P, const ProbState *__re
 }
 
 // Popped sub-cubes of this iteration into each problem's trace (slots from
-// tcount[k]; the count advances in mp_worklist).
+// tcount[k]; the count advances in mp_flip).
 __global__ void mp_trace(const ProbDev *__restrict__ P, const ProbState *__restrict__ S, int nprob,
-                         const Node *__restrict__ parents, int pop, const int *__restrict__ d_iter,
+                         const Node *__restrict__ parents, const int *__restrict__ off, const int *__restrict__ d_iter,
                          gosma_trace_rec *__restrict__ trace, const int *__restrict__ tcount, int tcap) {
     const int k = blockIdx.y;
     const ProbState &st = S[k];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < st.np; i += gridDim.x * blockDim.x) {
         const int slot = tcount[k] + i;
         if (slot >= tcap) break;
-        const Node &nd = parents[(size_t)k * pop + i];
+        const Node &nd = parents[(size_t)(off[k] >> 3) + i];
         CubeGeom g;
         decode(nd, P[k].dom, g);
         gosma_trace_rec &r = trace[(size_t)k * tcap + slot];
@@ -908,7 +931,7 @@ struct MultiBuffers {
 
 template <int BLOCK>
 static cudaError_t mp_bound_launch(gosma_ctx *ctx, cudaStream_t st, const ProbDev *P, const int *off, int nprob, const Node *parents,
-                                   int pop, const CubePrep *prep, Node *kids, double *kid_ub, size_t smem) {
+                                   const CubePrep *prep, Node *kids, double *kid_ub, size_t smem) {
     auto kern = mp_bound<BLOCK>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -916,20 +939,19 @@ static cudaError_t mp_bound_launch(gosma_ctx *ctx, cudaStream_t st, const ProbDe
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BLOCK, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    kern<<<ctx->sm_count * per_sm, BLOCK, smem, st>>>(P, off, nprob, parents, pop, prep, kids, kid_ub);
+    kern<<<ctx->sm_count * per_sm, BLOCK, smem, st>>>(P, off, nprob, parents, prep, kids, kid_ub);
     ++ctx->launches;
     return cudaGetLastError();
 }
 
 static cudaError_t mp_bound_any(int block, gosma_ctx *ctx, cudaStream_t st, const ProbDev *P, const int *off, int nprob,
-                                const Node *parents, int pop, const CubePrep *prep, Node *kids, double *kid_ub,
-                                size_t smem) {
+                                const Node *parents, const CubePrep *prep, Node *kids, double *kid_ub, size_t smem) {
     switch (block) {
-    case 64: return mp_bound_launch<64>(ctx, st, P, off, nprob, parents, pop, prep, kids, kid_ub, smem);
-    case 128: return mp_bound_launch<128>(ctx, st, P, off, nprob, parents, pop, prep, kids, kid_ub, smem);
-    case 256: return mp_bound_launch<256>(ctx, st, P, off, nprob, parents, pop, prep, kids, kid_ub, smem);
-    case 512: return mp_bound_launch<512>(ctx, st, P, off, nprob, parents, pop, prep, kids, kid_ub, smem);
-    default: return mp_bound_launch<1024>(ctx, st, P, off, nprob, parents, pop, prep, kids, kid_ub, smem);
+    case 64: return mp_bound_launch<64>(ctx, st, P, off, nprob, parents, prep, kids, kid_ub, smem);
+    case 128: return mp_bound_launch<128>(ctx, st, P, off, nprob, parents, prep, kids, kid_ub, smem);
+    case 256: return mp_bound_launch<256>(ctx, st, P, off, nprob, parents, prep, kids, kid_ub, smem);
+    case 512: return mp_bound_launch<512>(ctx, st, P, off, nprob, parents, prep, kids, kid_ub, smem);
+    default: return mp_bound_launch<1024>(ctx, st, P, off, nprob, parents, prep, kids, kid_ub, smem);
     }
 }
 
@@ -1294,6 +1316,7 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
         (e = B.get(&Qb.c_lt, max_chunks)) == cudaSuccess && (e = B.get(&Qb.c_eq, max_chunks)) == cudaSuccess &&
         (e = B.get(&Qb.c_out, max_chunks)) == cudaSuccess && (e = B.get(&Qb.c_eqb, max_chunks)) == cudaSuccess &&
         (e = B.get(&Qb.c_live, max_chunks)) == cudaSuccess && (e = B.get(&Qb.c_base, max_chunks)) == cudaSuccess &&
+        (e = B.get(&Qb.quota, 1)) == cudaSuccess &&
         (e = B.get(&parents, (size_t)pop * nprob)) == cudaSuccess && (e = B.get(&kids, nkids)) == cudaSuccess &&
         (e = B.get(&kid_ub, nkids)) == cudaSuccess && (e = B.get(&prep, nkids)) == cudaSuccess &&
         (e = B.get(&off, nprob + 1)) == cudaSuccess && (e = B.get(&ioff, nprob)) == cudaSuccess &&
@@ -1436,27 +1459,28 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
     const long long max_nodes = o.max_nodes;
 
     auto front = [&]() {
-        mp_chunks<<<1, MP_BLOCK, 0, st>>>(dS, nprob, Qb.ch_off);
+        mp_chunks<<<1, MP_BLOCK, 0, st>>>(dP, dS, nprob, Qb, pop);
         mp_hist<1><<<chunk_grid, CH_BLOCK, 0, st>>>(dP, dS, Qb, nprob);
-        mp_decide<<<nprob, MP_BLOCK, 0, st>>>(dP, dS, Qb, pop, d_iter, max_nodes);
+        mp_decide<<<nprob, MP_BLOCK, 0, st>>>(dP, dS, Qb, d_iter, max_nodes);
+        mp_offsets<<<1, MP_BLOCK, 0, st>>>(dS, nprob, off);
         mp_hist<2><<<chunk_grid, CH_BLOCK, 0, st>>>(dP, dS, Qb, nprob);
         mp_refine<2><<<nprob, MP_BLOCK, 0, st>>>(dS, Qb);
         mp_hist<3><<<chunk_grid, CH_BLOCK, 0, st>>>(dP, dS, Qb, nprob);
         mp_refine<3><<<nprob, MP_BLOCK, 0, st>>>(dS, Qb);
         mp_count<false><<<chunk_grid, CH_BLOCK, 0, st>>>(dP, dS, Qb, nprob);
         mp_cscan_any<false><<<nprob, MP_BLOCK, 0, st>>>(dS, Qb, nprob);
-        mp_scatter<false><<<chunk_grid, CH_BLOCK, 0, st>>>(dP, dS, Qb, nprob, parents, pop);
+        mp_scatter<false><<<chunk_grid, CH_BLOCK, 0, st>>>(dP, dS, Qb, nprob, parents, off);
         if (d_trace) {
-            mp_trace<<<dim3((pop + 127) / 128, nprob), 128, 0, st>>>(dP, dS, nprob, parents, pop, d_iter, d_trace,
+            mp_trace<<<dim3((pop + 127) / 128, nprob), 128, 0, st>>>(dP, dS, nprob, parents, off, d_iter, d_trace,
                                                                     d_tcount, lo.trace_cap);
             ++ctx->launches;
         }
         mp_count<true><<<chunk_grid, CH_BLOCK, 0, st>>>(dP, dS, Qb, nprob);
         mp_cscan_any<true><<<nprob, MP_BLOCK, 0, st>>>(dS, Qb, nprob);
-        mp_scatter<true><<<chunk_grid, CH_BLOCK, 0, st>>>(dP, dS, Qb, nprob, parents, pop);
-        mp_worklist<<<1, MP_BLOCK, 0, st>>>(dS, nprob, off, d_tcount, lo.trace_cap);
-        mp_prep<<<prep_grid, 128, 0, st>>>(dP, off, nprob, parents, pop, prep);
-        ctx->launches += 15;
+        mp_scatter<true><<<chunk_grid, CH_BLOCK, 0, st>>>(dP, dS, Qb, nprob, parents, off);
+        mp_flip<<<(nprob + 255) / 256, 256, 0, st>>>(dS, nprob, d_tcount, lo.trace_cap);
+        mp_prep<<<prep_grid, 128, 0, st>>>(dP, off, nprob, parents, prep);
+        ctx->launches += 16;
     };
     auto back = [&]() -> cudaError_t {
         cudaError_t eb = cudaSuccess;
@@ -1489,7 +1513,7 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
             for (int cand : {64, 128, 256, wide > 256 ? wide : 0}) {
                 if (!cand) continue;
                 cudaEventRecord(ta, st);
-                e = mp_bound_any(cand, ctx, st, dP, off, nprob, parents, pop, prep, kids, kid_ub, smem);
+                e = mp_bound_any(cand, ctx, st, dP, off, nprob, parents, prep, kids, kid_ub, smem);
                 cudaEventRecord(tb, st);
                 if (e == cudaSuccess) e = cudaEventSynchronize(tb);
                 float ms = 0;
@@ -1500,7 +1524,7 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
                 }
             }
         } else {
-            e = mp_bound_any(block, ctx, st, dP, off, nprob, parents, pop, prep, kids, kid_ub, smem);
+            e = mp_bound_any(block, ctx, st, dP, off, nprob, parents, prep, kids, kid_ub, smem);
         }
         if (e == cudaSuccess) e = back();
         if (e == cudaSuccess) e = cudaGetLastError();
@@ -1515,7 +1539,7 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
     e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         front();
-        cudaError_t e2 = mp_bound_any(block, ctx, st, dP, off, nprob, parents, pop, prep, kids, kid_ub, smem);
+        cudaError_t e2 = mp_bound_any(block, ctx, st, dP, off, nprob, parents, prep, kids, kid_ub, smem);
         cudaError_t e3 = back();
         cudaMemcpyAsync(h_ndone, d_ndone, sizeof(int), cudaMemcpyDeviceToHost, st);
         e = cudaStreamEndCapture(st, &graph);
