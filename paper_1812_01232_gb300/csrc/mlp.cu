@@ -213,6 +213,109 @@ static cudaError_t tc_gemm(const GemmArgs &g, int sm_count, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- fused inference
+// Y = W3 GELU(W2 GELU(W1 x + b1) + b2) + b3 for 128-row tiles in one kernel:
+// the BF16 weights are staged once per CTA and stay in shared memory, the
+// hidden activations go from TMEM through registers (bias, GELU, BF16) back
+// to shared memory as the next layer's A operand, and never reach HBM.
+// TMEM columns [0, 128) hold the layer-1 and then the layer-2 accumulator,
+// [128, 144) the outputs.
+constexpr int INF_X = 128 * MLP_IN * 2, INF_H = 128 * MLP_HID * 2, INF_W1 = MLP_HID * MLP_IN * 2,
+              INF_W2 = MLP_HID * MLP_HID * 2, INF_W3 = MLP_OUT * MLP_HID * 2;
+constexpr int INF_SMEM = INF_X + INF_H + INF_W1 + INF_W2 + INF_W3;  // 76 KB: at most 2 CTAs (512 TMEM columns) per SM
+constexpr int INF_COLS = 256;
+
+// 16 consecutive BF16 values of row r, columns c0..c0+15, into a K = 128
+// core-matrix tile.
+__device__ __forceinline__ void tc_put16(unsigned char *tile, int r, int c0, const bf16 *v) {
+    unsigned char *base = tile + ((r >> 3) * (MLP_HID / 8) + (c0 >> 3)) * 128 + (r & 7) * 16;
+    *reinterpret_cast<uint4 *>(base) = reinterpret_cast<const uint4 *>(v)[0];
+    *reinterpret_cast<uint4 *>(base + 128) = reinterpret_cast<const uint4 *>(v)[1];
+}
+
+__global__ void __launch_bounds__(128)
+    mlp_infer_kernel(const bf16 *__restrict__ X, const int *__restrict__ d_rows, int max_rows, const bf16 *__restrict__ W1b,
+                     const bf16 *__restrict__ W2b, const bf16 *__restrict__ W3b, const float *__restrict__ P,
+                     float *__restrict__ Y, int *__restrict__ err) {
+    extern __shared__ __align__(128) unsigned char inf_smem[];
+    __shared__ uint64_t mbar;
+    __shared__ uint32_t tbase_s;
+    unsigned char *sX = inf_smem, *sH = sX + INF_X, *sW1 = sH + INF_H, *sW2 = sW1 + INF_W1, *sW3 = sW2 + INF_W2;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == 0) tc_alloc(&tbase_s, INF_COLS);
+    if (threadIdx.x == 0) {
+        mbar_init(&mbar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_stage<MLP_IN>(sW1, W1b, MLP_IN, MLP_HID, MLP_HID);
+    tc_stage<MLP_HID>(sW2, W2b, MLP_HID, MLP_HID, MLP_HID);
+    tc_stage<MLP_HID>(sW3, W3b, MLP_HID, MLP_OUT, MLP_OUT);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = tbase_s, taddr = tbase + ((uint32_t)(32 * warp) << 16);
+    const int rows = min(*d_rows, max_rows), ntiles = (rows + 127) / 128;
+    const float *b1 = P + OFF_B1, *b2 = P + OFF_B2, *b3 = P + OFF_B3;
+    uint32_t phase = 0;
+    bool ok = true;
+    // issue the MMAs of one layer from one thread and wait for them (bounded)
+    auto layer = [&](unsigned char *A, uint32_t sboA, unsigned char *B, uint32_t sboB, int ksteps, uint32_t dcol,
+                     uint32_t idesc) {
+        tc_fence_proxy();
+        tc_fence_before();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(A), b0 = smem_u32(B);
+            for (int s = 0; s < ksteps; ++s)
+                tc_mma(tbase + dcol, tc_sdesc(a0 + s * 256, 128, sboA), tc_sdesc(b0 + s * 256, 128, sboB), idesc,
+                       s > 0 ? 1u : 0u);
+            tc_commit(&mbar);
+        }
+        bool w = mbar_wait(&mbar, phase, TC_WAIT_NS);
+        phase ^= 1u;
+        w = __syncthreads_and(w);
+        tc_fence_after();
+        return w;
+    };
+    for (int u = blockIdx.x; u < ntiles && ok; u += gridDim.x) {
+        const int row0 = u * 128, row = row0 + threadIdx.x;
+        tc_stage<MLP_IN>(sX, X + (size_t)row0 * MLP_IN, MLP_IN, 128, min(128, rows - row0));
+        ok = layer(sX, 2 * 128, sW1, 2 * 128, 1, 0, tc_idesc_bf16(128, MLP_HID));
+        if (!ok) break;
+        for (int l = 0; l < 2 && ok; ++l) {  // hidden layer l: TMEM -> bias, GELU -> BF16 tile
+            const float *b = l == 0 ? b1 : b2;
+#pragma unroll 1
+            for (int c0 = 0; c0 < MLP_HID; c0 += 16) {
+                float v[16];
+                tc_ld16(taddr + c0, v);
+                __align__(16) bf16 h[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) h[i] = __float2bfloat16_rn(gelu_f(v[i] + b[c0 + i]));
+                tc_put16(sH, threadIdx.x, c0, h);
+            }
+            if (l == 0) ok = layer(sH, 16 * 128, sW2, 16 * 128, MLP_HID / 16, 0, tc_idesc_bf16(128, MLP_HID));
+            else ok = layer(sH, 16 * 128, sW3, 16 * 128, MLP_HID / 16, MLP_HID, tc_idesc_bf16(128, MLP_OUT));
+        }
+        if (!ok) break;
+        float v[16];
+        tc_ld16(taddr + MLP_HID, v);
+        if (row < rows) {
+            float *o = Y + (size_t)row * MLP_OUT;
+#pragma unroll
+            for (int i = 0; i < 16; i += 4)
+                *reinterpret_cast<float4 *>(o + i) =
+                    make_float4(v[i] + b3[i], v[i + 1] + b3[i + 1], v[i + 2] + b3[i + 2], v[i + 3] + b3[i + 3]);
+        }
+        tc_fence_before();
+        __syncthreads();  // TMEM reads and the H tile done before the next tile's MMAs
+    }
+    if (!ok && threadIdx.x == 0) atomicExch(err, 1);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tc_dealloc(tbase, INF_COLS);
+}
+
 // ---------------------------------------------------------------- small kernels
 __global__ void mlp_cast(const float *__restrict__ P, bf16 *W1b, bf16 *W2b, bf16 *W3b, bf16 *W2Tb, bf16 *W3Tb) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < MLP_HID * MLP_HID; i += gridDim.x * blockDim.x) {
@@ -469,20 +572,14 @@ int *mlp_error_flag(Mlp *m) { return m->err; }
 
 cudaError_t mlp_forward_rows(gosma_ctx *ctx, int max_rows, const int *d_rows, cudaStream_t st) {
     Mlp *m = ctx->mlp;
-    GemmArgs g;
-    memset(&g, 0, sizeof g);
-    g.err = m->err;
-    g.Mdev = d_rows;
-    g.A = m->X, g.lda = MLP_IN, g.B = m->W1b, g.ldb = MLP_IN, g.M = max_rows, g.K = MLP_IN;
-    g.bias = m->P + OFF_B1, g.outH = m->H1;
-    cudaError_t e = tc_gemm<MLP_HID, MLP_IN, EPI_GELU>(g, ctx->sm_count, st);
-    g.A = m->H1, g.lda = MLP_HID, g.B = m->W2b, g.ldb = MLP_HID, g.K = MLP_HID;
-    g.bias = m->P + OFF_B2, g.outH = m->H2;
-    if (e == cudaSuccess) e = tc_gemm<MLP_HID, MLP_HID, EPI_GELU>(g, ctx->sm_count, st);
-    g.A = m->H2, g.B = m->W3b, g.ldb = MLP_HID, g.bias = m->P + OFF_B3, g.outF = m->Y, g.outH = nullptr;
-    if (e == cudaSuccess) e = tc_gemm<MLP_OUT, MLP_HID, EPI_F32>(g, ctx->sm_count, st);
-    ctx->launches += 3;
-    return e;
+    cudaError_t e = cudaFuncSetAttribute(mlp_infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, INF_SMEM);
+    if (e != cudaSuccess) return e;
+    const int tiles = (max_rows + 127) / 128;
+    const int grid = tiles < 2 * ctx->sm_count ? tiles : 2 * ctx->sm_count;
+    if (grid <= 0) return cudaSuccess;
+    mlp_infer_kernel<<<grid, 128, INF_SMEM, st>>>(m->X, d_rows, max_rows, m->W1b, m->W2b, m->W3b, m->P, m->Y, m->err);
+    ++ctx->launches;
+    return cudaGetLastError();
 }
 
 }  // namespace gosma
@@ -532,9 +629,13 @@ extern "C" int gosma_mlp_forward(gosma_ctx *ctx, int n, const float *x, float *y
     int npad = 0;
     int rc = mlp_stage_x(ctx, m, n, x, &npad);
     if (rc) return rc;
+    // inference through the fused kernel (row count read from the device)
+    int *rows = m->err + 1;
     cudaError_t e = cudaMemsetAsync(m->err, 0, sizeof(int), ctx->stream);
-    if (e == cudaSuccess) e = mlp_forward_dev(ctx, m, npad, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(rows, &n, sizeof(int), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = mlp_forward_rows(ctx, npad, rows, ctx->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(y, m->Y, sizeof(float) * (size_t)n * MLP_OUT, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);  // the host copy of n must outlive its upload
     if (e != cudaSuccess) return cuda_fail(ctx, e, "mlp_forward");
     return mlp_check_err(ctx, m);
 }
