@@ -232,13 +232,14 @@ template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK)
     bound_children(MixDev mx, Domain dom, df zeta2, const Node *__restrict__ parents, int np,
                    const CubePrep *__restrict__ prep, Node *__restrict__ kids, double *__restrict__ kid_ub,
-                   unsigned int *__restrict__ n_self) {
+                   unsigned int *__restrict__ n_self, int *__restrict__ counter) {
     extern __shared__ float smem_f[];
     __shared__ CubeShared cs;
     __shared__ CubeSums sums;
+    __shared__ int slot;
     SmemArrays sm = carve(smem_f, mx.n1, mx.n2);
     const double inf = __longlong_as_double(0x7ff0000000000000LL);
-    for (int c = blockIdx.x; c < 8 * np; c += gridDim.x) {
+    for (int c = next_cube(counter, &slot); c < 8 * np; c = next_cube(counter, &slot)) {
         // a child keeps its parent's cuboid, and so its self sums, after a rotation split
         const bool need_self = !(parents[c >> 3].flags & 1u) || !split_rotation(parents[c >> 3]);
         cube_bounds<BLOCK>(mx, prep[c], zeta2, need_self, cs, sm, sums);
@@ -446,7 +447,7 @@ struct BnbState {
     unsigned long long *total = nullptr;
     Status *st = nullptr;
     Status *h_st = nullptr;  // pinned
-    unsigned int *kid_rot = nullptr;  // children that computed their own self sums
+    unsigned int *kid_rot = nullptr;  // [0]: children that computed their own self sums; [1]: work counter
     CubePrep *rot = nullptr;          // pre-pass of the children
     unsigned int *h_flags = nullptr;  // pinned copy
     struct Solve *solve = nullptr;
@@ -510,7 +511,7 @@ static int alloc_state(gosma_ctx *ctx, unsigned long long cap, int pop, BnbState
     ALLOC(s->off, sizeof(int2) * ntile);
     ALLOC(s->total, sizeof(unsigned long long));
     ALLOC(s->st, sizeof(Status));
-    ALLOC(s->kid_rot, sizeof(unsigned int));
+    ALLOC(s->kid_rot, 2 * sizeof(unsigned int));
     ALLOC(s->rot, sizeof(CubePrep) * 8 * pop);
 #undef ALLOC
     if (e == cudaSuccess) e = cudaMallocHost((void **)&s->h_st, sizeof(Status));
@@ -536,14 +537,14 @@ static int launch_children(gosma_ctx *ctx, const Domain &dom, BnbState *s, int n
     if (e != cudaSuccess || per_sm < 1) return fail(ctx, GOSMA_ECUDA, "children kernel does not fit");
     long long grid = (long long)ctx->sm_count * per_sm;
     if (grid > 8LL * np) grid = 8LL * np;
-    e = cudaMemsetAsync(s->kid_rot, 0, sizeof(unsigned int), ctx->stream);
+    e = cudaMemsetAsync(s->kid_rot, 0, 2 * sizeof(unsigned int), ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "memset(children)");
     cube_prep_children<<<(8 * np + 127) / 128, 128, 0, ctx->stream>>>(dom, s->parents, np, s->rot);
     ++ctx->launches;
     df z2;
     split_double(ctx->zeta * ctx->zeta, z2.h, z2.l);
     kern<<<(int)grid, BLOCK, smem, ctx->stream>>>(ctx->mix, dom, z2, s->parents, np, s->rot, s->kids, s->kid_ub,
-                                                   s->kid_rot);
+                                                   s->kid_rot, (int *)(s->kid_rot + 1));
     ++ctx->launches;
     e = cudaGetLastError();
     return e == cudaSuccess ? GOSMA_OK : cuda_fail(ctx, e, "launch(children)");

@@ -14,12 +14,13 @@ __global__ void cube_prep_cubes(const gosma_cube *__restrict__ cubes, int n, Cub
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK) eval_bounds_kernel(MixDev mx, const gosma_cube *__restrict__ cubes, int n,
                                                             const CubePrep *__restrict__ prep, df zeta2,
-                                                            gosma_bound *__restrict__ out) {
+                                                            gosma_bound *__restrict__ out, int *__restrict__ counter) {
     extern __shared__ float smem_f[];
     __shared__ CubeShared cs;
     __shared__ CubeSums sums;
+    __shared__ int slot;
     SmemArrays sm = carve(smem_f, mx.n1, mx.n2);
-    for (int c = blockIdx.x; c < n; c += gridDim.x) {
+    for (int c = next_cube(counter, &slot); c < n; c = next_cube(counter, &slot)) {
         cube_bounds<BLOCK>(mx, prep[c], zeta2, true, cs, sm, sums);
         if (threadIdx.x == 0) {
             gosma_bound o;
@@ -47,6 +48,9 @@ int bounds_block_size(int n1, int n2) {
     return b;
 }
 
+// The per-cube pre-pass records are followed by the work counter.
+static size_t rot_counter_offset(int n) { return sizeof(CubePrep) * (size_t)n; }
+
 template <int BLOCK>
 static int launch_t(gosma_ctx *ctx, const gosma_cube *d_cubes, int n, gosma_bound *d_out, const CubePrep *d_rot) {
     size_t smem = bounds_smem_bytes(ctx->n1, ctx->n2);
@@ -61,7 +65,10 @@ static int launch_t(gosma_ctx *ctx, const gosma_cube *d_cubes, int n, gosma_boun
     if (grid > n) grid = n;
     df z2;
     split_double(ctx->zeta * ctx->zeta, z2.h, z2.l);
-    kern<<<(int)grid, BLOCK, smem, ctx->stream>>>(ctx->mix, d_cubes, n, d_rot, z2, d_out);
+    int *counter = (int *)((char *)ctx->d_rot + rot_counter_offset(n));
+    e = cudaMemsetAsync(counter, 0, sizeof(int), ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "memset(bounds)");
+    kern<<<(int)grid, BLOCK, smem, ctx->stream>>>(ctx->mix, d_cubes, n, d_rot, z2, d_out, counter);
     ++ctx->launches;
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "launch(bounds)");
@@ -70,7 +77,7 @@ static int launch_t(gosma_ctx *ctx, const gosma_cube *d_cubes, int n, gosma_boun
 
 int launch_bounds(gosma_ctx *ctx, const gosma_cube *d_cubes, int n, gosma_bound *d_out) {
     if (n <= 0) return GOSMA_OK;
-    size_t need = sizeof(CubePrep) * (size_t)n;
+    size_t need = rot_counter_offset(n) + 16;
     if (need > ctx->rot_bytes) {
         if (ctx->d_rot) cudaFree(ctx->d_rot);
         ctx->d_rot = nullptr;

@@ -307,6 +307,18 @@ __device__ inline void block_reduce_df(df v[4], CubeShared &cs) {
         }
 }
 
+// Work distribution of the persistent bound kernels: cubes are handed out
+// one at a time from a device counter that is zero at launch, so that blocks
+// drawing cheap cubes (infeasible ones, children reusing cached self sums)
+// take more of them.  Every thread of the block calls it; the leading barrier
+// keeps the slot from being overwritten before all threads have read it.
+__device__ __forceinline__ int next_cube(int *counter, int *slot) {
+    __syncthreads();
+    if (threadIdx.x == 0) *slot = atomicAdd(counter, 1);
+    __syncthreads();
+    return *slot;
+}
+
 // The whole per-cube computation.  Every thread of the block must call it
 // with the same cube; sums are valid in thread 0 on return.  need_self = 0
 // skips the self pairs (the caller reuses cached self sums).

@@ -554,13 +554,15 @@ __global__ void mp_prep(const ProbDev *__restrict__ P, const int *__restrict__ o
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK)
     mp_bound(const ProbDev *__restrict__ P, const int *__restrict__ off, int nprob, const Node *__restrict__ parents,
-             const CubePrep *__restrict__ prep, Node *__restrict__ kids, double *__restrict__ kid_ub) {
+             const CubePrep *__restrict__ prep, Node *__restrict__ kids, double *__restrict__ kid_ub,
+             int *__restrict__ counter) {
     extern __shared__ float smem_f[];
     __shared__ CubeShared cs;
     __shared__ CubeSums sums;
+    __shared__ int slot;
     const double inf = __longlong_as_double(0x7ff0000000000000LL);
     const int N = off[nprob];
-    for (int w = blockIdx.x; w < N; w += gridDim.x) {
+    for (int w = next_cube(counter, &slot); w < N; w = next_cube(counter, &slot)) {
         const int k = mp_find(off, nprob, w), c = w - off[k];
         const MixDev &mx = P[k].mx;
         SmemArrays sm = carve(smem_f, mx.n1, mx.n2);
@@ -931,7 +933,7 @@ struct MultiBuffers {
 
 template <int BLOCK>
 static cudaError_t mp_bound_launch(gosma_ctx *ctx, cudaStream_t st, const ProbDev *P, const int *off, int nprob, const Node *parents,
-                                   const CubePrep *prep, Node *kids, double *kid_ub, size_t smem) {
+                                   const CubePrep *prep, Node *kids, double *kid_ub, int *counter, size_t smem) {
     auto kern = mp_bound<BLOCK>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -939,19 +941,22 @@ static cudaError_t mp_bound_launch(gosma_ctx *ctx, cudaStream_t st, const ProbDe
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BLOCK, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    kern<<<ctx->sm_count * per_sm, BLOCK, smem, st>>>(P, off, nprob, parents, prep, kids, kid_ub);
+    e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    kern<<<ctx->sm_count * per_sm, BLOCK, smem, st>>>(P, off, nprob, parents, prep, kids, kid_ub, counter);
     ++ctx->launches;
     return cudaGetLastError();
 }
 
 static cudaError_t mp_bound_any(int block, gosma_ctx *ctx, cudaStream_t st, const ProbDev *P, const int *off, int nprob,
-                                const Node *parents, const CubePrep *prep, Node *kids, double *kid_ub, size_t smem) {
+                                const Node *parents, const CubePrep *prep, Node *kids, double *kid_ub, int *counter,
+                                size_t smem) {
     switch (block) {
-    case 64: return mp_bound_launch<64>(ctx, st, P, off, nprob, parents, prep, kids, kid_ub, smem);
-    case 128: return mp_bound_launch<128>(ctx, st, P, off, nprob, parents, prep, kids, kid_ub, smem);
-    case 256: return mp_bound_launch<256>(ctx, st, P, off, nprob, parents, prep, kids, kid_ub, smem);
-    case 512: return mp_bound_launch<512>(ctx, st, P, off, nprob, parents, prep, kids, kid_ub, smem);
-    default: return mp_bound_launch<1024>(ctx, st, P, off, nprob, parents, prep, kids, kid_ub, smem);
+    case 64: return mp_bound_launch<64>(ctx, st, P, off, nprob, parents, prep, kids, kid_ub, counter, smem);
+    case 128: return mp_bound_launch<128>(ctx, st, P, off, nprob, parents, prep, kids, kid_ub, counter, smem);
+    case 256: return mp_bound_launch<256>(ctx, st, P, off, nprob, parents, prep, kids, kid_ub, counter, smem);
+    case 512: return mp_bound_launch<512>(ctx, st, P, off, nprob, parents, prep, kids, kid_ub, counter, smem);
+    default: return mp_bound_launch<1024>(ctx, st, P, off, nprob, parents, prep, kids, kid_ub, counter, smem);
     }
 }
 
@@ -1316,7 +1321,7 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
         (e = B.get(&Qb.c_lt, max_chunks)) == cudaSuccess && (e = B.get(&Qb.c_eq, max_chunks)) == cudaSuccess &&
         (e = B.get(&Qb.c_out, max_chunks)) == cudaSuccess && (e = B.get(&Qb.c_eqb, max_chunks)) == cudaSuccess &&
         (e = B.get(&Qb.c_live, max_chunks)) == cudaSuccess && (e = B.get(&Qb.c_base, max_chunks)) == cudaSuccess &&
-        (e = B.get(&Qb.quota, 1)) == cudaSuccess &&
+        (e = B.get(&Qb.quota, 2)) == cudaSuccess &&  // [1]: the bound kernel's work counter
         (e = B.get(&parents, (size_t)pop * nprob)) == cudaSuccess && (e = B.get(&kids, nkids)) == cudaSuccess &&
         (e = B.get(&kid_ub, nkids)) == cudaSuccess && (e = B.get(&prep, nkids)) == cudaSuccess &&
         (e = B.get(&off, nprob + 1)) == cudaSuccess && (e = B.get(&ioff, nprob)) == cudaSuccess &&
@@ -1513,7 +1518,7 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
             for (int cand : {64, 128, 256, wide > 256 ? wide : 0}) {
                 if (!cand) continue;
                 cudaEventRecord(ta, st);
-                e = mp_bound_any(cand, ctx, st, dP, off, nprob, parents, prep, kids, kid_ub, smem);
+                e = mp_bound_any(cand, ctx, st, dP, off, nprob, parents, prep, kids, kid_ub, Qb.quota + 1, smem);
                 cudaEventRecord(tb, st);
                 if (e == cudaSuccess) e = cudaEventSynchronize(tb);
                 float ms = 0;
@@ -1524,7 +1529,7 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
                 }
             }
         } else {
-            e = mp_bound_any(block, ctx, st, dP, off, nprob, parents, prep, kids, kid_ub, smem);
+            e = mp_bound_any(block, ctx, st, dP, off, nprob, parents, prep, kids, kid_ub, Qb.quota + 1, smem);
         }
         if (e == cudaSuccess) e = back();
         if (e == cudaSuccess) e = cudaGetLastError();
@@ -1539,7 +1544,7 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
     e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         front();
-        cudaError_t e2 = mp_bound_any(block, ctx, st, dP, off, nprob, parents, prep, kids, kid_ub, smem);
+        cudaError_t e2 = mp_bound_any(block, ctx, st, dP, off, nprob, parents, prep, kids, kid_ub, Qb.quota + 1, smem);
         cudaError_t e3 = back();
         cudaMemcpyAsync(h_ndone, d_ndone, sizeof(int), cudaMemcpyDeviceToHost, st);
         e = cudaStreamEndCapture(st, &graph);
