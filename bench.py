@@ -155,6 +155,19 @@ def kernel_traffic():
     return rec.get("bytes_per_launch") if rec.get("source_sha256") == kernel_source_sha256() else None
 
 
+def reduce_over_ranks(t_local, pairs_local, dist, device):
+    """Whole-job aggregation over the ranks: the slowest rank's time and the
+    pairs of all ranks (every rank works on its own problem)."""
+    if dist is None:
+        return t_local, float(pairs_local)
+    import torch
+    tt = torch.tensor([t_local], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    pp = torch.tensor([float(pairs_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(pp)
+    return float(tt.item()), float(pp.item())
+
+
 def make_problem(rank):
     from paper_1812_01232_gb300 import synth
     return synth.paper_scale_problem(SEED + rank)
@@ -270,16 +283,7 @@ def run_ours(args):
         dist.barrier()
     torch.cuda.synchronize()
     ck = clocks.stop()
-    t_total = sum(times) / 1e3
-    if dist:
-        tt = torch.tensor([t_total], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_total = float(tt.item())
-        pp = torch.tensor([float(pairs)], device="cuda")
-        dist.all_reduce(pp)
-        pairs_all = float(pp.item())
-    else:
-        pairs_all = float(pairs)
+    t_total, pairs_all = reduce_over_ranks(sum(times) / 1e3, pairs, dist, "cuda")
     value = pairs_all / t_total
 
     # ---------------- e2e through the host-buffer C-ABI call
