@@ -3,6 +3,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <vector>
+
 #include <new>
 
 #include "gosma_internal.cuh"
@@ -42,6 +44,12 @@ int ensure_pinned(gosma_ctx *ctx, size_t bytes) {
 
 int setup_constants(gosma_ctx *ctx, double *c22_out);
 int selftest_approx(gosma_ctx *ctx, double measured[5], double assumed[5]);
+
+// (lb, ub) pairs of n records, for the host path: 16 bytes per cube cross the bus.
+__global__ void pack_bounds(const gosma_bound *__restrict__ in, int n, double2 *__restrict__ out) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) out[k] = make_double2(in[k].lb, in[k].ub);
+}
 
 __global__ void split_bounds(const gosma_bound *__restrict__ in, int n, double *lb, double *ub) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -242,26 +250,65 @@ static int eval_common(gosma_ctx *ctx, const gosma_cube *cubes, int n, gosma_bou
         }
         return GOSMA_OK;
     }
-    rc = ensure_stage(ctx, bc + bo);
+    // Host buffers: pipelined over chunks, so that staging the next chunk on
+    // the host, the copies and the kernels of the current chunk and the
+    // unpacking of finished chunks overlap; only the requested results cross
+    // the bus (lb and ub: 16 bytes per cube, or the full records).
+    const int CH = 16384;
+    const int nch = (n + CH - 1) / CH;
+    const size_t out_per = detail ? sizeof(gosma_bound) : sizeof(double2);
+    rc = ensure_stage(ctx, bc + bo + sizeof(double2) * (size_t)n);
     if (rc) return rc;
-    rc = ensure_pinned(ctx, bc > bo ? bc : bo);
+    rc = ensure_pinned(ctx, bc + out_per * (size_t)n);
     if (rc) return rc;
     gosma_cube *dc = (gosma_cube *)ctx->d_stage;
-    gosma_bound *dout = (gosma_bound *)((char *)ctx->d_stage + bc);
-    memcpy(ctx->h_pinned, cubes, bc);
-    e = cudaMemcpyAsync(dc, ctx->h_pinned, bc, cudaMemcpyHostToDevice, ctx->stream);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "copy cubes");
-    rc = launch_bounds(ctx, dc, n, dout);
-    if (rc) return rc;
-    e = cudaMemcpyAsync(ctx->h_pinned, dout, bo, cudaMemcpyDeviceToHost, ctx->stream);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "copy bounds");
-    e = cudaStreamSynchronize(ctx->stream);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "sync(bounds)");
-    const gosma_bound *hb = (const gosma_bound *)ctx->h_pinned;
-    if (detail) memcpy(detail, hb, bo);
-    for (int k = 0; k < n; ++k) {
-        if (lb) lb[k] = hb[k].lb;
-        if (ub) ub[k] = hb[k].ub;
+    gosma_bound *drec = (gosma_bound *)((char *)ctx->d_stage + bc);
+    double2 *dlu = (double2 *)((char *)drec + bo);
+    unsigned char *hin = (unsigned char *)ctx->h_pinned, *hout = hin + bc;
+    std::vector<cudaEvent_t> ev(nch, nullptr);
+    struct EventsFree {
+        std::vector<cudaEvent_t> &v;
+        ~EventsFree() {
+            for (cudaEvent_t x : v)
+                if (x) cudaEventDestroy(x);
+        }
+    } ev_guard{ev};
+    for (int c = 0; c < nch; ++c) {
+        const int off = c * CH, m = n - off < CH ? n - off : CH;
+        e = cudaEventCreateWithFlags(&ev[c], cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaEventCreate");
+        memcpy(hin + sizeof(gosma_cube) * (size_t)off, cubes + off, sizeof(gosma_cube) * (size_t)m);
+        e = cudaMemcpyAsync(dc + off, hin + sizeof(gosma_cube) * (size_t)off, sizeof(gosma_cube) * (size_t)m,
+                            cudaMemcpyHostToDevice, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "copy cubes");
+        rc = launch_bounds(ctx, dc + off, m, drec + off);
+        if (rc) return rc;
+        const void *src = drec + off;
+        if (!detail) {
+            pack_bounds<<<(m + 255) / 256, 256, 0, ctx->stream>>>(drec + off, m, dlu + off);
+            ++ctx->launches;
+            src = dlu + off;
+        }
+        e = cudaGetLastError();
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(hout + out_per * (size_t)off, src, out_per * (size_t)m, cudaMemcpyDeviceToHost,
+                                ctx->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[c], ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "copy bounds");
+    }
+    for (int c = 0; c < nch; ++c) {
+        const int off = c * CH, m = n - off < CH ? n - off : CH;
+        e = cudaEventSynchronize(ev[c]);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "sync(bounds)");
+        if (detail) {
+            memcpy(detail + off, hout + out_per * (size_t)off, out_per * (size_t)m);
+        } else {
+            const double2 *h = (const double2 *)hout + off;
+            for (int k = 0; k < m; ++k) {
+                if (lb) lb[off + k] = h[k].x;
+                if (ub) ub[off + k] = h[k].y;
+            }
+        }
     }
     return GOSMA_OK;
 }
