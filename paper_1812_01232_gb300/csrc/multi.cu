@@ -1,26 +1,36 @@
 // Algorithm 1 for many independent problems at once (batched GOSMA).
 //
-// All problems' queues live in one node/key buffer, one segment per problem.
-// One iteration advances every unfinished problem:
-//   mp_select    one block per problem: in-place compaction of the segment
-//                when half of it is dead, the smallest live key (the
-//                problem's global lower bound) and the stopping test
-//                d* - lb <= eps, then the `pop` best hypercubes by an exact
-//                radix select (ties in queue order);
-//   mp_offsets   prefix sums of the children counts (each unfinished problem
-//                pops up to pop x nprob / (unfinished problems), so the last
-//                problems of a batch keep the GPU busy);
+// Every problem owns a segment of `cap` entries in each of two queue buffers
+// (nodes, pop keys, lower-bound keys); ProbState::cur says which buffer holds
+// its queue.  One iteration advances every unfinished problem:
+//   mp_chunks .. mp_scatter<false>
+//                the pop: per-problem lower bound (smallest live lower-bound
+//                key) and stopping test d* - lb <= eps, then the best
+//                hypercubes by an exact radix select over 8,192-key chunks
+//                of all segments (ties in queue order); each unfinished
+//                problem pops up to max(pop, pop x nprob / unfinished), so
+//                the last problems of a batch keep the GPU busy;
+//   mp_offsets   prefix sums of the children counts;
+//   mp_count/cscan/scatter<true>, mp_flip
+//                compaction into the other buffer when half of a segment
+//                is dead or its tail nears capacity;
 //   mp_prep      per child: cell decode and the per-cube pre-pass;
 //   mp_bound     one persistent launch bounds the children of all problems
-//                (each block looks up its child's problem and mixtures);
+//                (cubes handed out by an atomic counter; each block looks up
+//                its child's problem and mixtures);
+//   mp_features + the network (learned form): a score and a seed pose per
+//                child on the tensor cores;
 //   mp_append    one block per problem: children with lb < d* go to the
-//                segment's tail (block scan, in child order) and the child
-//                with the smallest upper bound becomes the candidate;
-//   mp_obj_*     the exact FP64 objective at every candidate's centre, which
-//                replaces d* when smaller.
-// The sequence is captured once in a CUDA graph and replayed; the host only
-// polls the number of finished problems.  The block size of mp_bound is
-// chosen by timing the candidates on the first iteration's children.
+//                segment's tail (block scan, in child order); candidates for
+//                d*: the centre of the child with the smallest upper bound
+//                and, in the learned form, the best-scored child's seed;
+//   mp_obj_*     the exact FP64 objective at every candidate, which replaces
+//                d* when smaller.
+// The sequence is captured once in a CUDA graph and replayed; the host polls
+// the number of finished problems every 8 replays and applies the results of
+// the SMA refinement that a host thread runs on a second stream.  The block
+// size of mp_bound is chosen by timing the candidates on one iteration's
+// children.
 #include <math.h>
 #include <string.h>
 
@@ -1339,7 +1349,7 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
     memset(&root, 0, sizeof root);
     root.lb = -INFINITY;
     root.psit = (float)M_PI;
-    const uint32_t rkey = order_key(-INFINITY), dead = DEAD;
+    const uint32_t rkey = order_key(-INFINITY);
     if (e == cudaSuccess) e = cudaMemsetAsync(Qb.hist, 0, sizeof(unsigned int) * 2048 * nprob, st);
     root.ubf = INFINITY;
     for (int k = 0; k < nprob && e == cudaSuccess; ++k) {
@@ -1347,7 +1357,6 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
         if (e == cudaSuccess) e = cudaMemcpyAsync(Qb.keys[0] + (size_t)k * cap, &rkey, sizeof rkey, cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(Qb.lbk[0] + (size_t)k * cap, &rkey, sizeof rkey, cudaMemcpyHostToDevice, st);
     }
-    (void)dead;
     // learned form: network input rows for every child, and the traces
     const int max_rows = (int)nkids;
     const float *Yd = nullptr;
