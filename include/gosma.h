@@ -128,6 +128,19 @@ const char *gosma_last_error(const gosma_ctx *ctx);
 int gosma_set_mixtures(gosma_ctx *ctx, int n1, const double *mu1, const double *sigma1, const double *phi1, int n2,
                        const double *mu2, const double *kappa2, const double *phi2);
 
+/* Semantic form (Sec. 4.2): f = sum_l w_l f_l over nclass classes, f_l the
+ * objective of Lemma 1 between class l's model and image mixtures.  The
+ * components are given class by class: the first n1c[0] model and n2c[0]
+ * image components belong to class 0, and so on; each class's weights phi1
+ * and phi2 sum to 1; w_l >= 0 (the paper uses 1 / nclass).  Pairs interact
+ * only within a class; ε applies to f / C22 + 1 with C22 = sum_l w_l C22_l.
+ * The translation domain excludes the points within zeta of any class's
+ * means.  Validation as in gosma_set_mixtures, per class; GOSMA_EINVAL for
+ * an empty class. */
+int gosma_set_mixtures_classes(gosma_ctx *ctx, int nclass, const int *n1c, const int *n2c, const double *w,
+                               const double *mu1, const double *sigma1, const double *phi1, const double *mu2,
+                               const double *kappa2, const double *phi2);
+
 /* Translation domain Omega_t: the cuboid [t_lo, t_hi] minus the points
  * within zeta of any model mean (Sec. 4.1).  zeta >= 0, t_lo < t_hi. */
 int gosma_set_domain(gosma_ctx *ctx, const double t_lo[3], const double t_hi[3], double zeta);

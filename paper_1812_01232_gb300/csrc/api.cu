@@ -100,33 +100,68 @@ const char *gosma_last_error(const gosma_ctx *ctx) { return ctx ? ctx->err.c_str
 
 long long gosma_kernel_launches(const gosma_ctx *ctx) { return ctx ? ctx->launches : 0; }
 
-int gosma_set_mixtures(gosma_ctx *ctx, int n1, const double *mu1, const double *sigma1, const double *phi1, int n2,
-                       const double *mu2, const double *kappa2, const double *phi2) {
+// Shared by the single-class and the semantic entry points: nclass classes
+// of n1c[l] model and n2c[l] image components (given class by class), class
+// weights w (w = NULL: one class of weight 1).  Each class's mixture weights
+// sum to 1; they are scaled by sqrt(w_l) so that the within-class pair sums
+// give sum_l w_l f_l (Sec. 4.2).
+static int set_mixtures_impl(gosma_ctx *ctx, int nclass, const int *n1c, const int *n2c, const double *w, int n1,
+                             const double *mu1, const double *sigma1, const double *phi1_in, int n2,
+                             const double *mu2, const double *kappa2, const double *phi2_in) {
     if (!ctx) return GOSMA_EINVAL;
     ctx->err.clear();
-    if (n1 < 1 || n2 < 1 || !mu1 || !sigma1 || !phi1 || !mu2 || !kappa2 || !phi2)
+    if (n1 < 1 || n2 < 1 || !mu1 || !sigma1 || !phi1_in || !mu2 || !kappa2 || !phi2_in)
         return fail(ctx, GOSMA_EINVAL, "set_mixtures: empty mixture or null pointer");
     if (bounds_smem_bytes(n1, n2) > 200 * 1024)
         return fail(ctx, GOSMA_EINVAL, "set_mixtures: 13*n1 + 8*n2 floats exceed the 200 KB shared-memory budget");
-    double s1 = 0, s2 = 0;
-    for (int i = 0; i < n1; ++i) {
-        if (!(sigma1[i] > 0) || !(phi1[i] >= 0) || !isfinite(mu1[3 * i]) || !isfinite(mu1[3 * i + 1]) ||
+    for (int i = 0; i < n1; ++i)
+        if (!(sigma1[i] > 0) || !(phi1_in[i] >= 0) || !isfinite(mu1[3 * i]) || !isfinite(mu1[3 * i + 1]) ||
             !isfinite(mu1[3 * i + 2]) || !isfinite(sigma1[i]))
             return fail(ctx, GOSMA_EINVAL, "set_mixtures: sigma1 must be > 0, phi1 >= 0, means finite");
-        s1 += phi1[i];
-    }
     for (int j = 0; j < n2; ++j) {
         double nn = sqrt(mu2[3 * j] * mu2[3 * j] + mu2[3 * j + 1] * mu2[3 * j + 1] + mu2[3 * j + 2] * mu2[3 * j + 2]);
-        if (!(kappa2[j] > 0) || !isfinite(kappa2[j]) || !(phi2[j] >= 0) || !(fabs(nn - 1.0) <= 1e-6))
+        if (!(kappa2[j] > 0) || !isfinite(kappa2[j]) || !(phi2_in[j] >= 0) || !(fabs(nn - 1.0) <= 1e-6))
             return fail(ctx, GOSMA_EINVAL, "set_mixtures: kappa2 must be > 0, phi2 >= 0, |mu2_j| = 1");
-        s2 += phi2[j];
     }
-    if (fabs(s1 - 1.0) > 1e-9 || fabs(s2 - 1.0) > 1e-9)
-        return fail(ctx, GOSMA_EINVAL, "set_mixtures: mixture weights must sum to 1");
+    // classes: per-class weight sums, class ids, pair ranges; weights scaled by sqrt(w_l)
+    std::vector<double> phi1(phi1_in, phi1_in + n1), phi2(phi2_in, phi2_in + n2);
+    std::vector<int> cls1(n1), cls2(n2), rj0(n1), rj1(n1), rm1(n1);
+    {
+        int i0 = 0, j0 = 0;
+        for (int l = 0; l < nclass; ++l) {
+            const int a = n1c ? n1c[l] : n1, b = n2c ? n2c[l] : n2;
+            const double wl = w ? w[l] : 1.0;
+            if (a < 1 || b < 1 || i0 + a > n1 || j0 + b > n2 || !(wl >= 0) || !isfinite(wl))
+                return fail(ctx, GOSMA_EINVAL, "set_mixtures: class sizes must be >= 1, sum to n1 and n2; w >= 0");
+            double s1 = 0, s2 = 0;
+            for (int i = i0; i < i0 + a; ++i) s1 += phi1[i];
+            for (int j = j0; j < j0 + b; ++j) s2 += phi2[j];
+            if (fabs(s1 - 1.0) > 1e-9 || fabs(s2 - 1.0) > 1e-9)
+                return fail(ctx, GOSMA_EINVAL, "set_mixtures: each class's mixture weights must sum to 1");
+            const double sw = sqrt(wl);
+            for (int i = i0; i < i0 + a; ++i) {
+                phi1[i] *= sw;
+                cls1[i] = l;
+                rj0[i] = j0;
+                rj1[i] = j0 + b;
+                rm1[i] = i0 + a;
+            }
+            for (int j = j0; j < j0 + b; ++j) {
+                phi2[j] *= sw;
+                cls2[j] = l;
+            }
+            i0 += a;
+            j0 += b;
+        }
+        if (i0 != n1 || j0 != n2)
+            return fail(ctx, GOSMA_EINVAL, "set_mixtures: class sizes must sum to n1 and n2");
+    }
+    const bool classes = nclass > 1;
     cudaSetDevice(ctx->device);
     size_t nd = 3 * (size_t)n1 + 2 * n1 + 3 * (size_t)n2 + 2 * n2;
     size_t nf = 8 * (size_t)n1 + 8 * (size_t)n2;
-    size_t bytes = nd * sizeof(double) + nf * sizeof(float) + 256;
+    const size_t ni = classes ? 5 * (size_t)n1 + (size_t)n2 : 0;  // class ids and pair ranges
+    size_t bytes = nd * sizeof(double) + nf * sizeof(float) + ni * sizeof(int) + 256;
     void *d = nullptr;
     cudaError_t e = cudaMalloc(&d, bytes);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(mixtures)");
@@ -136,6 +171,8 @@ int gosma_set_mixtures(gosma_ctx *ctx, int n1, const double *mu1, const double *
     float *pf = (float *)(dphi2 + n2);
     float *inv_sig2 = pf, *phi1f = pf + n1, *k2f = phi1f + n1, *Q2 = k2f + n2;
     float *mu1h = Q2 + n2, *mu1l = mu1h + 3 * n1, *mu2h = mu1l + 3 * n1, *mu2l = mu2h + 3 * n2;
+    int *pi = (int *)(mu2l + 3 * n2);
+    int *dcls1 = pi, *drj0 = pi + n1, *drj1 = pi + 2 * n1, *drm1 = pi + 3 * n1, *dcls2 = pi + 4 * n1;
     std::vector<float> hk2(n2);
     for (int j = 0; j < n2; ++j) hk2[j] = (float)kappa2[j];
     // image mean directions are used as exact unit vectors: normalise them (FP64)
@@ -149,17 +186,21 @@ int gosma_set_mixtures(gosma_ctx *ctx, int n1, const double *mu1, const double *
         void *dst;
         const void *src;
         size_t n;
-    } cp[] = {{dmu1, mu1, 3 * (size_t)n1 * 8}, {dsig, sigma1, (size_t)n1 * 8}, {dphi1, phi1, (size_t)n1 * 8},
-              {dmu2, mu2n.data(), 3 * (size_t)n2 * 8}, {dk2, kappa2, (size_t)n2 * 8},  {dphi2, phi2, (size_t)n2 * 8},
-              {k2f, hk2.data(), (size_t)n2 * 4}};
+    } cp[] = {{dmu1, mu1, 3 * (size_t)n1 * 8}, {dsig, sigma1, (size_t)n1 * 8}, {dphi1, phi1.data(), (size_t)n1 * 8},
+              {dmu2, mu2n.data(), 3 * (size_t)n2 * 8}, {dk2, kappa2, (size_t)n2 * 8},  {dphi2, phi2.data(), (size_t)n2 * 8},
+              {k2f, hk2.data(), (size_t)n2 * 4},
+              {dcls1, cls1.data(), classes ? (size_t)n1 * 4 : 0}, {drj0, rj0.data(), classes ? (size_t)n1 * 4 : 0},
+              {drj1, rj1.data(), classes ? (size_t)n1 * 4 : 0}, {drm1, rm1.data(), classes ? (size_t)n1 * 4 : 0},
+              {dcls2, cls2.data(), classes ? (size_t)n2 * 4 : 0}};
     for (auto &c : cp) {
+        if (!c.n) continue;
         e = cudaMemcpyAsync(c.dst, c.src, c.n, cudaMemcpyHostToDevice, ctx->stream);
         if (e != cudaSuccess) {
             cudaFree(d);
             return cuda_fail(ctx, e, "copy mixtures");
         }
     }
-    MixDev mx;
+    MixDev mx{};
     mx.n1 = n1;
     mx.n2 = n2;
     mx.mu1 = dmu1;
@@ -177,6 +218,11 @@ int gosma_set_mixtures(gosma_ctx *ctx, int n1, const double *mu1, const double *
     mx.mu2h = mu2h;
     mx.mu2l = mu2l;
     mx.zeta = ctx->zeta;
+    mx.cls1 = classes ? dcls1 : nullptr;
+    mx.cls2 = classes ? dcls2 : nullptr;
+    mx.rj0 = classes ? drj0 : nullptr;
+    mx.rj1 = classes ? drj1 : nullptr;
+    mx.rm1 = classes ? drm1 : nullptr;
     void *old = ctx->d_mix;
     MixDev old_mix = ctx->mix;
     int old_n1 = ctx->n1, old_n2 = ctx->n2;
@@ -197,12 +243,32 @@ int gosma_set_mixtures(gosma_ctx *ctx, int n1, const double *mu1, const double *
     ctx->c22 = c22;
     ctx->h_mu1.assign(mu1, mu1 + 3 * (size_t)n1);
     ctx->h_sigma1.assign(sigma1, sigma1 + n1);
-    ctx->h_phi1.assign(phi1, phi1 + n1);
+    ctx->h_phi1 = phi1;
     ctx->h_mu2 = mu2n;
     ctx->h_kappa2.assign(kappa2, kappa2 + n2);
-    ctx->h_phi2.assign(phi2, phi2 + n2);
+    ctx->h_phi2 = phi2;
     ctx->have_mix = true;
     return GOSMA_OK;
+}
+
+int gosma_set_mixtures(gosma_ctx *ctx, int n1, const double *mu1, const double *sigma1, const double *phi1, int n2,
+                       const double *mu2, const double *kappa2, const double *phi2) {
+    return set_mixtures_impl(ctx, 1, nullptr, nullptr, nullptr, n1, mu1, sigma1, phi1, n2, mu2, kappa2, phi2);
+}
+
+int gosma_set_mixtures_classes(gosma_ctx *ctx, int nclass, const int *n1c, const int *n2c, const double *w,
+                               const double *mu1, const double *sigma1, const double *phi1, const double *mu2,
+                               const double *kappa2, const double *phi2) {
+    if (!ctx) return GOSMA_EINVAL;
+    if (nclass < 1 || !n1c || !n2c || !w) return fail(ctx, GOSMA_EINVAL, "set_mixtures_classes: bad class arrays");
+    long long n1 = 0, n2 = 0;
+    for (int l = 0; l < nclass; ++l) {
+        if (n1c[l] < 1 || n2c[l] < 1) return fail(ctx, GOSMA_EINVAL, "set_mixtures_classes: empty class");
+        n1 += n1c[l];
+        n2 += n2c[l];
+    }
+    if (n1 > (1 << 20) || n2 > (1 << 20)) return fail(ctx, GOSMA_EINVAL, "set_mixtures_classes: too many components");
+    return set_mixtures_impl(ctx, nclass, n1c, n2c, w, (int)n1, mu1, sigma1, phi1, (int)n2, mu2, kappa2, phi2);
 }
 
 int gosma_set_domain(gosma_ctx *ctx, const double t_lo[3], const double t_hi[3], double zeta) {

@@ -501,8 +501,9 @@ __device__ void cube_bounds(const MixDev &mx, const CubePrep &prep, df zeta2, bo
             cu.zero();
             float pl = 0.f, pc = 0.f;
             int cnt = 0;
+            const int j1 = mx.rj1 ? mx.rj1[i] : n2;
 #pragma unroll 1
-            for (int j = tj; j < n2; j += Tj) {
+            for (int j = (mx.rj0 ? mx.rj0[i] : 0) + tj; j < j1; j += Tj) {
                 cross_pair(R, sm.J1[j], sm.J2[j], pl, pc);
                 if (++cnt == CHUNK) {
                     cl.add(pl);
@@ -544,8 +545,9 @@ __device__ void cube_bounds(const MixDev &mx, const CubePrep &prep, df zeta2, bo
                     su.zero();
                     float pl = 0.f, pc = 0.f;
                     int cnt = 0;
+                    const int mend = mx.rm1 ? mx.rm1[i] : n1;
 #pragma unroll 1
-                    for (int m = i + 1 + sj; m < n1; m += Sj) {
+                    for (int m = i + 1 + sj; m < mend; m += Sj) {
                         self_pair(R, sm.M1[m], sm.M2[m], sm.M3[m], sm.Uw[m], pl, pc);
                         if (++cnt == CHUNK) {
                             sl.add(pl);

@@ -32,6 +32,12 @@ struct MixDev {
     const float *mu1h, *mu1l;  // n1 x 3: mu1 as double-floats (hi, lo)
     const float *mu2h, *mu2l;  // n2 x 3: unit mu2 as double-floats
     double zeta;           // point-to-camera limit (Sec. 4.1)
+    // Semantic classes (Sec. 4.2); all null for one class.  Pairs interact
+    // only within a class: model row i pairs with image columns
+    // [rj0[i], rj1[i]) and with model rows below rm1[i]; cls1 / cls2 give
+    // each component's class.
+    const int *cls1, *cls2;
+    const int *rj0, *rj1, *rm1;
 };
 
 // One sub-cube decoded to FP64 geometry.

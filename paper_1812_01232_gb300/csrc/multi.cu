@@ -759,12 +759,14 @@ __global__ void __launch_bounds__(MPO_BLOCK)
          qq += (long long)gridDim.x * MPO_BLOCK) {
         if (qq < nself) {
             int i = (int)(qq / n1), j = (int)(qq % n1);
+            if (mx.cls1 && mx.cls1[i] != mx.cls1[j]) continue;
             const double *A = I + 8 * i, *B = I + 8 * j;
             double w0 = A[6] * A[0] + B[6] * B[0], w1 = A[6] * A[1] + B[6] * B[1], w2 = A[6] * A[2] + B[6] * B[2];
             acc += mx.phi1d[i] * mx.phi1d[j] * exp(logZ_d(sqrt(w0 * w0 + w1 * w1 + w2 * w2)) - A[7] - B[7]);
         } else {
             long long r = qq - nself;
             int i = (int)(r / n2), j = (int)(r % n2);
+            if (mx.cls1 && mx.cls1[i] != mx.cls2[j]) continue;
             const double *A = I + 8 * i, *mu = mx.mu2 + 3 * j;
             double k2 = mx.kappa2d[j];
             double w0 = A[6] * A[3] + k2 * mu[0], w1 = A[6] * A[4] + k2 * mu[1], w2 = A[6] * A[5] + k2 * mu[2];

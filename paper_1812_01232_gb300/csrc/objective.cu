@@ -71,6 +71,7 @@ __global__ void setup_image(MixDev mx, double *c22part) {
     for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total;
          q += (long long)gridDim.x * blockDim.x) {
         int a = (int)(q / n2), b = (int)(q % n2);
+        if (mx.cls2 && mx.cls2[a] != mx.cls2[b]) continue;  // C22 = sum over classes of w_l C22_l
         const double *ma = mx.mu2 + 3 * a, *mb = mx.mu2 + 3 * b;
         double ka = mx.kappa2d[a], kb = mx.kappa2d[b];
         double w0 = ka * ma[0] + kb * mb[0], w1 = ka * ma[1] + kb * mb[1], w2 = ka * ma[2] + kb * mb[2];

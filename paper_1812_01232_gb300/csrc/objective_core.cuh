@@ -110,6 +110,7 @@ __global__ void __launch_bounds__(OBJ_BLOCK) obj_pairs(Src src, const double *__
     for (long long q = q0 + threadIdx.x; q < q1; q += OBJ_BLOCK) {
         if (q < nself) {
             int i = (int)(q / n1), j = (int)(q % n1);
+            if (mx.cls1 && mx.cls1[i] != mx.cls1[j]) continue;  // pairs only within a class
             const double *A = I + (size_t)i * OBJ_STRIDE, *B = I + (size_t)j * OBJ_STRIDE;
             double w0 = A[4] * A[0] + B[4] * B[0], w1 = A[4] * A[1] + B[4] * B[1], w2 = A[4] * A[2] + B[4] * B[2];
             double K = sqrt(w0 * w0 + w1 * w1 + w2 * w2);
@@ -128,6 +129,7 @@ __global__ void __launch_bounds__(OBJ_BLOCK) obj_pairs(Src src, const double *__
         } else {
             long long qq = q - nself;
             int i = (int)(qq / n2), j = (int)(qq % n2);
+            if (mx.cls1 && mx.cls1[i] != mx.cls2[j]) continue;
             const double *A = I + (size_t)i * OBJ_STRIDE;
             const double *mu = mx.mu2 + 3 * j;
             double k2 = mx.kappa2d[j];

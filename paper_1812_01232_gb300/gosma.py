@@ -68,6 +68,8 @@ SIGNATURES = {
     "gosma_destroy": (None, [C.c_void_p]),
     "gosma_last_error": (C.c_char_p, [C.c_void_p]),
     "gosma_set_mixtures": (C.c_int, [C.c_void_p, C.c_int, D, D, D, C.c_int, D, D, D]),
+    "gosma_set_mixtures_classes": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), D, D, D, D,
+                                             D, D, D]),
     "gosma_set_domain": (C.c_int, [C.c_void_p, D, D, C.c_double]),
     "gosma_eval_bounds": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int]),
     "gosma_eval_bounds_detail": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int]),
@@ -185,8 +187,27 @@ class Gosma:
         lo, hi = _f64(t_lo, (3,)), _f64(t_hi, (3,))
         self._check(self.L.gosma_set_domain(self.h, _p(lo), _p(hi), float(zeta)), "set_domain")
 
+    def set_mixtures_classes(self, n1c, n2c, w, mu1, sigma1, phi1, mu2, kappa2, phi2):
+        """Semantic form: per-class sizes n1c, n2c and weights w; arrays class by class."""
+        n1c = np.ascontiguousarray(np.asarray(n1c, dtype=np.int32))
+        n2c = np.ascontiguousarray(np.asarray(n2c, dtype=np.int32))
+        w = _f64(w, (-1,))
+        mu1, sigma1, phi1 = _f64(mu1, (-1, 3)), _f64(sigma1, (-1,)), _f64(phi1, (-1,))
+        mu2, kappa2, phi2 = _f64(mu2, (-1, 3)), _f64(kappa2, (-1,)), _f64(phi2, (-1,))
+        ip = C.POINTER(C.c_int)
+        self._check(self.L.gosma_set_mixtures_classes(self.h, len(n1c), n1c.ctypes.data_as(ip), n2c.ctypes.data_as(ip),
+                                                      _p(w), _p(mu1), _p(sigma1), _p(phi1), _p(mu2), _p(kappa2),
+                                                      _p(phi2)), "set_mixtures_classes")
+        self.n1, self.n2 = len(sigma1), len(kappa2)
+
     def set_problem(self, prob):
-        self.set_mixtures(prob["mu1"], prob["sigma1"], prob["phi1"], prob["mu2"], prob["kappa2"], prob["phi2"])
+        """Mixtures and domain of a problem dict (synth); semantic problems
+        (with "n1c", "n2c", "w") go through the class entry point."""
+        if "n1c" in prob:
+            self.set_mixtures_classes(prob["n1c"], prob["n2c"], prob["w"], prob["mu1"], prob["sigma1"], prob["phi1"],
+                                      prob["mu2"], prob["kappa2"], prob["phi2"])
+        else:
+            self.set_mixtures(prob["mu1"], prob["sigma1"], prob["phi1"], prob["mu2"], prob["kappa2"], prob["phi2"])
         self.set_domain(prob["t_lo"], prob["t_hi"], prob["zeta"])
 
     # ---------------------------------------------------------------- bounds

@@ -115,6 +115,39 @@ def tiny_problem(seed: int, n1: int = 10, n_in: int = 7, n_out: int = 1, zeta: f
                 R_gt=R, r_gt=r, t_gt=t_gt)
 
 
+def semantic_problem(seed: int, nclass: int = 3, n1: int = 4, n_in: int = 3, n_out: int = 1, zeta: float = 0.5,
+                     noise_free: bool = False, sigma: float = None):
+    """Semantic scene (Sec. 4.2): nclass classes sharing one true pose, each
+    with its own model mixture (n1 components in the 4 x 4 x 3 m room,
+    sigma = 0.05 m, or 0.1 m noise-free, unless given) and image mixture (n_in projected
+    components with the qPN concentration + n_out outliers with kappa = 50;
+    noise-free: every component projected, no outliers).  Equal weights
+    within a class, class weights 1 / nclass.  Also returns the
+    concatenation (class by class) with the class sizes n1c, n2c."""
+    rng = np.random.default_rng(seed)
+    R, r = random_rotation(rng)
+    t_gt = rng.uniform(-0.5, 0.5, 3)
+    half = np.array([2.0, 2.0, 1.5])
+    classes = []
+    for _ in range(nclass):
+        mu1 = _means_in_room(rng, n1, half, t_gt, 1.2 * zeta)
+        sig = sigma if sigma is not None else (0.1 if noise_free else 0.05)
+        sigma1 = np.full(n1, sig)
+        phi1 = np.full(n1, 1.0 / n1)
+        idx = np.arange(n1) if noise_free else rng.permutation(n1)[:n_in]
+        dirs = _camera_dirs(R, mu1[idx], t_gt)
+        kap = (np.linalg.norm(mu1[idx] - t_gt, axis=1) / sigma1[idx]) ** 2 + 1.0
+        no = 0 if noise_free else n_out
+        mu2 = np.concatenate([dirs, _uniform_sphere(rng, no)]) if no else dirs
+        kappa2 = np.concatenate([kap, np.full(no, 50.0)]) if no else kap
+        phi2 = np.full(len(kappa2), 1.0 / len(kappa2))
+        classes.append(dict(mu1=mu1, sigma1=sigma1, phi1=phi1, mu2=mu2, kappa2=kappa2, phi2=phi2))
+    cat = {k: np.concatenate([c[k] for c in classes]) for k in ("mu1", "sigma1", "phi1", "mu2", "kappa2", "phi2")}
+    return dict(name="semantic", classes=classes, w=np.full(nclass, 1.0 / nclass),
+                n1c=np.array([len(c["sigma1"]) for c in classes]), n2c=np.array([len(c["kappa2"]) for c in classes]),
+                t_lo=np.full(3, -1.0), t_hi=np.full(3, 1.0), zeta=zeta, eps=1e-3, R_gt=R, r_gt=r, t_gt=t_gt, **cat)
+
+
 def noise_free_problem(seed: int, n1: int = 6, zeta: float = 0.5):
     """Every model component projected at the true pose with its own qPN
     concentration and weight: the image mixture equals the projected model
