@@ -296,6 +296,17 @@ int gosma_mlp_train(gosma_ctx *ctx, int n, const float *x, const float *label, c
 /* Number of kernels the context has launched since it was created. */
 long long gosma_kernel_launches(const gosma_ctx *ctx);
 
+/* Failure detection without a fault: a kernel waits, with the time limit
+ * the tensor-core kernels use (here limit_seconds, 0 < limit <= 10), on an
+ * mbarrier that nothing arrives on.  The wait gives up and the call returns
+ * GOSMA_ETIMEOUT; the context stays usable. */
+int gosma_selftest_wait_timeout(gosma_ctx *ctx, double limit_seconds);
+
+/* Testing of error paths: the next n device allocations of this context
+ * fail as if the device were out of memory (the calls that needed them
+ * return GOSMA_ECUDA and leave the context usable).  n = 0 turns it off. */
+int gosma_debug_fail_allocations(gosma_ctx *ctx, int n);
+
 /* Diagnostics: measured maximum relative error of the device's approximate
  * ex2, lg2, rcp, rsqrt and sqrt against FP64 over dense samples (5 values,
  * in that order), and the error bounds the bound kernel's slack assumes. */

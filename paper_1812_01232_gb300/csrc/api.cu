@@ -25,7 +25,7 @@ int ensure_stage(gosma_ctx *ctx, size_t bytes) {
     if (ctx->d_stage) cudaFree(ctx->d_stage);
     ctx->d_stage = nullptr;
     ctx->stage_bytes = 0;
-    cudaError_t e = cudaMalloc(&ctx->d_stage, bytes);
+    cudaError_t e = dev_malloc(ctx, &ctx->d_stage, bytes);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(stage)");
     ctx->stage_bytes = bytes;
     return GOSMA_OK;
@@ -44,6 +44,7 @@ int ensure_pinned(gosma_ctx *ctx, size_t bytes) {
 
 int setup_constants(gosma_ctx *ctx, double *c22_out);
 int selftest_approx(gosma_ctx *ctx, double measured[5], double assumed[5]);
+int selftest_wait_timeout(gosma_ctx *ctx, double limit_s, int *timed_out);
 
 // (lb, ub) pairs of n records, for the host path: 16 bytes per cube cross the bus.
 __global__ void pack_bounds(const gosma_bound *__restrict__ in, int n, double2 *__restrict__ out) {
@@ -163,7 +164,7 @@ static int set_mixtures_impl(gosma_ctx *ctx, int nclass, const int *n1c, const i
     const size_t ni = classes ? 5 * (size_t)n1 + (size_t)n2 : 0;  // class ids and pair ranges
     size_t bytes = nd * sizeof(double) + nf * sizeof(float) + ni * sizeof(int) + 256;
     void *d = nullptr;
-    cudaError_t e = cudaMalloc(&d, bytes);
+    cudaError_t e = dev_malloc(ctx, &d, bytes);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(mixtures)");
     double *pd = (double *)d;
     double *dmu1 = pd, *dsig = pd + 3 * n1, *dphi1 = dsig + n1, *dmu2 = dphi1 + n1, *dk2 = dmu2 + 3 * n2,
@@ -401,6 +402,24 @@ int gosma_eval_objective(gosma_ctx *ctx, const double r[3], const double t[3], d
     if (!r || !t || !f) return fail(ctx, GOSMA_EINVAL, "eval_objective: null pointer");
     double x[6] = {r[0], r[1], r[2], t[0], t[1], t[2]};
     return gosma_eval_objective_grad(ctx, 1, x, f, nullptr);
+}
+
+int gosma_selftest_wait_timeout(gosma_ctx *ctx, double limit_seconds) {
+    if (!ctx) return GOSMA_EINVAL;
+    ctx->err.clear();
+    if (!(limit_seconds > 0) || limit_seconds > 10) return fail(ctx, GOSMA_EINVAL, "selftest_wait_timeout: 0 < limit <= 10 s");
+    cudaSetDevice(ctx->device);
+    int timed_out = 0;
+    int rc = selftest_wait_timeout(ctx, limit_seconds, &timed_out);
+    if (rc) return rc;
+    return timed_out ? fail(ctx, GOSMA_ETIMEOUT, "selftest_wait_timeout: the wait gave up (as designed)") : GOSMA_OK;
+}
+
+int gosma_debug_fail_allocations(gosma_ctx *ctx, int n) {
+    if (!ctx) return GOSMA_EINVAL;
+    if (n < 0) return fail(ctx, GOSMA_EINVAL, "debug_fail_allocations: n >= 0");
+    ctx->fail_allocs = n;
+    return GOSMA_OK;
 }
 
 int gosma_selftest_approx(gosma_ctx *ctx, double measured[5], double assumed[5]) {

@@ -497,7 +497,7 @@ static int alloc_state(gosma_ctx *ctx, unsigned long long cap, int pop, BnbState
     unsigned long long ntile = (cap + SEL_TILE - 1) / SEL_TILE;
     cudaError_t e = cudaSuccess;
 #define ALLOC(ptr, bytes)                                        \
-    if (e == cudaSuccess) e = cudaMalloc((void **)&(ptr), (bytes));
+    if (e == cudaSuccess) e = dev_malloc(ctx, (void **)&(ptr), (bytes));
     ALLOC(s->q[0], sizeof(Node) * cap);
     ALLOC(s->q[1], sizeof(Node) * cap);
     ALLOC(s->keys[0], sizeof(uint32_t) * cap);

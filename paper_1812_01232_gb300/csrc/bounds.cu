@@ -82,7 +82,7 @@ int launch_bounds(gosma_ctx *ctx, const gosma_cube *d_cubes, int n, gosma_bound 
         if (ctx->d_rot) cudaFree(ctx->d_rot);
         ctx->d_rot = nullptr;
         ctx->rot_bytes = 0;
-        cudaError_t e = cudaMalloc(&ctx->d_rot, need);
+        cudaError_t e = dev_malloc(ctx, &ctx->d_rot, need);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(cube pre-pass)");
         ctx->rot_bytes = need;
     }

@@ -148,10 +148,26 @@ struct gosma_ctx {
     void *bnb = nullptr;
     // queue-ordering network (mlp.cu)
     gosma::Mlp *mlp = nullptr;
+    // error-path testing: the next fail_allocs device allocations fail
+    int fail_allocs = 0;
 
     // number of kernels this context has launched
     long long launches = 0;
 };
+
+
+namespace gosma {
+// Device allocations of the library go through here, so that tests can make
+// them fail (gosma_debug_fail_allocations) and check the error paths.
+inline cudaError_t dev_malloc(gosma_ctx *ctx, void **p, size_t bytes) {
+    if (ctx && ctx->fail_allocs > 0) {
+        --ctx->fail_allocs;
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+}  // namespace gosma
 
 namespace gosma {
 int fail(gosma_ctx *ctx, int code, const std::string &msg);

@@ -429,7 +429,7 @@ static int mlp_params_alloc(gosma_ctx *ctx) {
     Mlp *m = new Mlp();
     const size_t nf = (size_t)MLP_NPARAM * 4 + MLP_HID * MLP_OUT + 16 + MLP_NPARAM;
     const size_t nb = (size_t)MLP_HID * MLP_IN + 2 * MLP_HID * MLP_HID + 2 * MLP_OUT * MLP_HID;
-    cudaError_t e = cudaMalloc(&m->par, nf * 4 + nb * 2 + 256);
+    cudaError_t e = dev_malloc(ctx, &m->par, nf * 4 + nb * 2 + 256);
     if (e != cudaSuccess) {
         delete m;
         return cuda_fail(ctx, e, "cudaMalloc(mlp parameters)");
@@ -468,7 +468,7 @@ static int mlp_act_alloc(gosma_ctx *ctx, int rows) {
     const size_t R = (size_t)need;
     const size_t nb = R * (2 * MLP_IN + 8 * MLP_HID + 2 * MLP_OUT);  // BF16 elements
     const size_t nf = R * (2 * MLP_HID + MLP_OUT);                      // FP32 elements
-    cudaError_t e = cudaMalloc(&m->act, nb * 2 + nf * 4 + 1024);
+    cudaError_t e = dev_malloc(ctx, &m->act, nb * 2 + nf * 4 + 1024);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(mlp activations)");
     bf16 *b = (bf16 *)m->act;
     m->X = b;
@@ -580,6 +580,36 @@ cudaError_t mlp_forward_rows(gosma_ctx *ctx, int max_rows, const int *d_rows, cu
     mlp_infer_kernel<<<grid, 128, INF_SMEM, st>>>(m->X, d_rows, max_rows, m->W1b, m->W2b, m->W3b, m->P, m->Y, m->err);
     ++ctx->launches;
     return cudaGetLastError();
+}
+
+// Self-test of the bounded waits: one block waits on an mbarrier that nothing
+// arrives on, with the given limit; the wait must give up and report it.
+__global__ void wait_timeout_selftest(uint64_t limit_ns, int *out) {
+    __shared__ uint64_t mbar;
+    if (threadIdx.x == 0) {
+        mbar_init(&mbar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    bool ok = mbar_wait(&mbar, 0, limit_ns);
+    ok = __syncthreads_or(ok);
+    if (threadIdx.x == 0) out[0] = ok ? 0 : 1;
+}
+
+int selftest_wait_timeout(gosma_ctx *ctx, double limit_s, int *timed_out) {
+    int *d = nullptr;
+    cudaError_t e = dev_malloc(ctx, (void **)&d, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(selftest)");
+    int h = -1;
+    wait_timeout_selftest<<<1, 32, 0, ctx->stream>>>((uint64_t)(limit_s * 1e9), d);
+    ++ctx->launches;
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "selftest_wait_timeout");
+    *timed_out = h;
+    return GOSMA_OK;
 }
 
 }  // namespace gosma

@@ -929,6 +929,7 @@ __global__ void mp_apply(ProbState *__restrict__ S, const Incumbent *__restrict_
 
 // ---------------------------------------------------------------- host driver
 struct MultiBuffers {
+    gosma_ctx *ctx = nullptr;
     std::vector<void *> allocs;
     ~MultiBuffers() {
         for (void *p : allocs) cudaFree(p);
@@ -936,7 +937,7 @@ struct MultiBuffers {
     template <class T>
     cudaError_t get(T **p, size_t n) {
         void *q = nullptr;
-        cudaError_t e = cudaMalloc(&q, sizeof(T) * (n ? n : 1));
+        cudaError_t e = dev_malloc(ctx, &q, sizeof(T) * (n ? n : 1));
         if (e == cudaSuccess) allocs.push_back(q);
         *p = (T *)q;
         return e;
@@ -1221,6 +1222,7 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
     e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "sync(context stream)");
     MultiBuffers B;
+    B.ctx = ctx;
 
     // ---- mixtures of every problem in one allocation (FP64 + FP32 copies, as gosma_set_mixtures)
     std::vector<size_t> d_off(nprob + 1, 0), f_off(nprob + 1, 0);

@@ -22,7 +22,7 @@ int objective_grad_device(gosma_ctx *ctx, int count, const double *h_x, double *
         if (ctx->d_obj) cudaFree(ctx->d_obj);
         ctx->d_obj = nullptr;
         ctx->obj_bytes = 0;
-        cudaError_t e = cudaMalloc(&ctx->d_obj, need);
+        cudaError_t e = dev_malloc(ctx, &ctx->d_obj, need);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(objective)");
         ctx->obj_bytes = need;
     }
@@ -117,7 +117,7 @@ __global__ void setup_model(MixDev mx) {
 int setup_constants_mix(gosma_ctx *ctx, cudaStream_t st, const MixDev &mx, double *c22_out) {
     const int nb = 64;
     double *dpart = nullptr;
-    cudaError_t e = cudaMalloc(&dpart, sizeof(double) * nb);
+    cudaError_t e = dev_malloc(ctx, (void **)&dpart, sizeof(double) * nb);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(setup)");
     setup_image<<<nb, 256, 0, st>>>(mx, dpart);
     ++ctx->launches;
@@ -166,7 +166,7 @@ __global__ void approx_selftest(unsigned *maxbits) {
 
 int selftest_approx(gosma_ctx *ctx, double measured[5], double assumed[5]) {
     unsigned *d = nullptr;
-    cudaError_t e = cudaMalloc(&d, 5 * sizeof(unsigned));
+    cudaError_t e = dev_malloc(ctx, (void **)&d, 5 * sizeof(unsigned));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(selftest)");
     unsigned h[5] = {0, 0, 0, 0, 0};
     e = cudaMemsetAsync(d, 0, sizeof h, ctx->stream);

@@ -83,6 +83,8 @@ SIGNATURES = {
                                            C.c_void_p, C.c_void_p]),
     "gosma_bnb_step": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(Result)]),
     "gosma_selftest_approx": (C.c_int, [C.c_void_p, D, D]),
+    "gosma_selftest_wait_timeout": (C.c_int, [C.c_void_p, C.c_double]),
+    "gosma_debug_fail_allocations": (C.c_int, [C.c_void_p, C.c_int]),
     "gosma_kernel_launches": (C.c_longlong, [C.c_void_p]),
     "gosma_mlp_set_params": (C.c_int, [C.c_void_p, FP]),
     "gosma_mlp_get_params": (C.c_int, [C.c_void_p, FP]),
@@ -386,6 +388,13 @@ class Gosma:
 
     def kernel_launches(self):
         return int(self.L.gosma_kernel_launches(self.h))
+
+    def selftest_wait_timeout(self, limit_seconds=0.05):
+        """Returns the library's return code (GOSMA_ETIMEOUT when the bounded wait gave up)."""
+        return int(self.L.gosma_selftest_wait_timeout(self.h, float(limit_seconds)))
+
+    def debug_fail_allocations(self, n):
+        self._check(self.L.gosma_debug_fail_allocations(self.h, int(n)), "debug_fail_allocations")
 
     def selftest_approx(self):
         m = np.zeros(5)
