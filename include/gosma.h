@@ -293,6 +293,16 @@ int gosma_mlp_grad(gosma_ctx *ctx, int n, const float *x, const float *dy, float
 int gosma_mlp_train(gosma_ctx *ctx, int n, const float *x, const float *label, const float *target, int batch,
                     int steps, float lr, float lam, float *losses);
 
+/* Checkpoint of a run between two gosma_bnb_step calls: the solver record,
+ * the incumbent and its pose, and every queue slot (keys and sub-cubes) go
+ * to the file at path.  GOSMA_ENOTREADY without a run. */
+int gosma_bnb_save(gosma_ctx *ctx, const char *path);
+
+/* Resume a checkpoint on a context holding the same mixtures and domain
+ * (GOSMA_EINVAL otherwise): later gosma_bnb_step calls continue the run
+ * exactly as the saved one would have continued. */
+int gosma_bnb_load(gosma_ctx *ctx, const char *path);
+
 /* Number of kernels the context has launched since it was created. */
 long long gosma_kernel_launches(const gosma_ctx *ctx);
 

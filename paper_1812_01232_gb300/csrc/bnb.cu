@@ -28,6 +28,8 @@
 #include <stddef.h>
 #include <string.h>
 
+#include <stdio.h>
+
 #include <chrono>
 #include <vector>
 
@@ -930,4 +932,158 @@ extern "C" int gosma_bnb_solve(gosma_ctx *ctx, const gosma_opts *opts, gosma_res
     int rc = gosma_bnb_start(ctx, opts);
     if (rc) return rc;
     return gosma_bnb_step(ctx, 0, out);
+}
+
+// ---------------------------------------------------------------- checkpoint / resume
+// A run between two steps is fully described by the solver record, the
+// device status block, d* and the queue slots [0, tail) (keys and nodes,
+// dead slots included, so that compaction and selection replay exactly).
+namespace {
+constexpr char CK_MAGIC[8] = {'G', 'O', 'S', 'M', 'A', 'C', 'K', '1'};
+struct CkHeader {
+    char magic[8];
+    int n1, n2;
+    double c22, t_lo[3], t_hi[3], zeta;
+    unsigned long long cap;
+    int pop, node_bytes, status_bytes, pad;
+    unsigned long long tail;
+};
+struct CkSolve {  // the solver record without its events
+    gosma_opts o;
+    double eps_f, dstar, dlb, best[6];
+    unsigned long long tail, live;
+    long long nodes, iters, sma_calls, peak, cross_pairs, self_pairs;
+    double t_bound_ms, t_iter_ms, seconds;
+    int status, cur;
+};
+struct FileCloser {
+    FILE *f;
+    ~FileCloser() {
+        if (f) fclose(f);
+    }
+};
+}  // namespace
+
+extern "C" int gosma_bnb_save(gosma_ctx *ctx, const char *path) {
+    if (!ctx) return GOSMA_EINVAL;
+    ctx->err.clear();
+    Solve *vp = solve_of(ctx);
+    if (!vp || !vp->active) return fail(ctx, GOSMA_ENOTREADY, "bnb_save: no run in progress");
+    if (!path) return fail(ctx, GOSMA_EINVAL, "bnb_save: null path");
+    const Solve &v = *vp;
+    BnbState *s = (BnbState *)ctx->bnb;
+    cudaSetDevice(ctx->device);
+    CkHeader h;
+    memset(&h, 0, sizeof h);
+    memcpy(h.magic, CK_MAGIC, 8);
+    h.n1 = ctx->n1;
+    h.n2 = ctx->n2;
+    h.c22 = ctx->c22;
+    for (int k = 0; k < 3; ++k) {
+        h.t_lo[k] = ctx->t_lo[k];
+        h.t_hi[k] = ctx->t_hi[k];
+    }
+    h.zeta = ctx->zeta;
+    h.cap = s->cap;
+    h.pop = s->pop;
+    h.node_bytes = (int)sizeof(Node);
+    h.status_bytes = (int)sizeof(Status);
+    h.tail = v.tail;
+    CkSolve c;
+    memset(&c, 0, sizeof c);
+    c.o = v.o;
+    c.eps_f = v.eps_f;
+    c.dstar = v.dstar;
+    c.dlb = v.dlb;
+    memcpy(c.best, v.best, sizeof c.best);
+    c.tail = v.tail;
+    c.live = v.live;
+    c.nodes = v.nodes;
+    c.iters = v.iters;
+    c.sma_calls = v.sma_calls;
+    c.peak = v.peak;
+    c.cross_pairs = v.cross_pairs;
+    c.self_pairs = v.self_pairs;
+    c.t_bound_ms = v.t_bound_ms;
+    c.t_iter_ms = v.t_iter_ms;
+    c.seconds = v.seconds;
+    c.status = v.status;
+    c.cur = s->cur;
+    Status hs;
+    std::vector<uint32_t> keys(v.tail);
+    std::vector<Node> nodes(v.tail);
+    cudaError_t e = cudaMemcpyAsync(&hs, s->st, sizeof hs, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess && v.tail)
+        e = cudaMemcpyAsync(keys.data(), s->keys[s->cur], sizeof(uint32_t) * v.tail, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess && v.tail)
+        e = cudaMemcpyAsync(nodes.data(), s->q[s->cur], sizeof(Node) * v.tail, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "bnb_save: read state");
+    FILE *f = fopen(path, "wb");
+    if (!f) return fail(ctx, GOSMA_EINVAL, "bnb_save: cannot open the file");
+    FileCloser fc{f};
+    bool ok = fwrite(&h, sizeof h, 1, f) == 1 && fwrite(&c, sizeof c, 1, f) == 1 && fwrite(&hs, sizeof hs, 1, f) == 1;
+    if (ok && v.tail)
+        ok = fwrite(keys.data(), sizeof(uint32_t), v.tail, f) == v.tail && fwrite(nodes.data(), sizeof(Node), v.tail, f) == v.tail;
+    if (!ok) return fail(ctx, GOSMA_EINVAL, "bnb_save: write failed");
+    return GOSMA_OK;
+}
+
+extern "C" int gosma_bnb_load(gosma_ctx *ctx, const char *path) {
+    if (!ctx) return GOSMA_EINVAL;
+    ctx->err.clear();
+    if (!path) return fail(ctx, GOSMA_EINVAL, "bnb_load: null path");
+    if (!ctx->have_mix || !ctx->have_dom) return fail(ctx, GOSMA_ENOTREADY, "bnb_load: set mixtures and domain first");
+    FILE *f = fopen(path, "rb");
+    if (!f) return fail(ctx, GOSMA_EINVAL, "bnb_load: cannot open the file");
+    FileCloser fc{f};
+    CkHeader h;
+    CkSolve c;
+    Status hs;
+    if (fread(&h, sizeof h, 1, f) != 1 || memcmp(h.magic, CK_MAGIC, 8) != 0 || h.node_bytes != (int)sizeof(Node) ||
+        h.status_bytes != (int)sizeof(Status) || fread(&c, sizeof c, 1, f) != 1 || fread(&hs, sizeof hs, 1, f) != 1)
+        return fail(ctx, GOSMA_EINVAL, "bnb_load: not a checkpoint of this library");
+    bool same = h.n1 == ctx->n1 && h.n2 == ctx->n2 && fabs(h.c22 - ctx->c22) <= 1e-12 * fabs(ctx->c22) &&
+                h.zeta == ctx->zeta;
+    for (int k = 0; k < 3; ++k) same = same && h.t_lo[k] == ctx->t_lo[k] && h.t_hi[k] == ctx->t_hi[k];
+    if (!same) return fail(ctx, GOSMA_EINVAL, "bnb_load: the checkpoint belongs to other mixtures or another domain");
+    if (h.tail > h.cap || c.tail != h.tail) return fail(ctx, GOSMA_EINVAL, "bnb_load: inconsistent checkpoint");
+    std::vector<uint32_t> keys(h.tail);
+    std::vector<Node> nodes(h.tail);
+    if (h.tail && (fread(keys.data(), sizeof(uint32_t), h.tail, f) != h.tail ||
+                   fread(nodes.data(), sizeof(Node), h.tail, f) != h.tail))
+        return fail(ctx, GOSMA_EINVAL, "bnb_load: truncated checkpoint");
+    // a fresh run with the saved options, then the saved state on top of it
+    int rc = gosma_bnb_start(ctx, &c.o);
+    if (rc) return rc;
+    BnbState *s = (BnbState *)ctx->bnb;
+    if (s->cap != h.cap || s->pop != h.pop) return fail(ctx, GOSMA_EINVAL, "bnb_load: queue geometry differs");
+    Solve &v = *s->solve;
+    s->cur = 0;
+    cudaError_t e = cudaMemcpyAsync(s->st, &hs, sizeof hs, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->dstar, &c.dstar, sizeof c.dstar, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess && h.tail)
+        e = cudaMemcpyAsync(s->keys[0], keys.data(), sizeof(uint32_t) * h.tail, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess && h.tail)
+        e = cudaMemcpyAsync(s->q[0], nodes.data(), sizeof(Node) * h.tail, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "bnb_load: write state");
+    v.eps_f = c.eps_f;
+    v.dstar = c.dstar;
+    v.dlb = c.dlb;
+    memcpy(v.best, c.best, sizeof v.best);
+    v.tail = c.tail;
+    v.live = c.live;
+    v.nodes = c.nodes;
+    v.iters = c.iters;
+    v.sma_calls = c.sma_calls;
+    v.peak = c.peak;
+    v.cross_pairs = c.cross_pairs;
+    v.self_pairs = c.self_pairs;
+    v.t_bound_ms = c.t_bound_ms;
+    v.t_iter_ms = c.t_iter_ms;
+    v.seconds = c.seconds;
+    v.status = c.status;
+    v.active = true;
+    return GOSMA_OK;
 }

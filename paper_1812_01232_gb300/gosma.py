@@ -82,6 +82,8 @@ SIGNATURES = {
     "gosma_bnb_solve_batch_ex": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(Opts), C.c_void_p, C.c_void_p,
                                            C.c_void_p, C.c_void_p]),
     "gosma_bnb_step": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(Result)]),
+    "gosma_bnb_save": (C.c_int, [C.c_void_p, C.c_char_p]),
+    "gosma_bnb_load": (C.c_int, [C.c_void_p, C.c_char_p]),
     "gosma_selftest_approx": (C.c_int, [C.c_void_p, D, D]),
     "gosma_selftest_wait_timeout": (C.c_int, [C.c_void_p, C.c_double]),
     "gosma_debug_fail_allocations": (C.c_int, [C.c_void_p, C.c_int]),
@@ -385,6 +387,12 @@ class Gosma:
         self._check(self.L.gosma_mlp_train(self.h, len(x), _pf(x), _pf(label), _pf(target), int(batch), int(steps),
                                            float(lr), float(lam), _pf(losses)), "mlp_train")
         return losses[:steps]
+
+    def bnb_save(self, path):
+        self._check(self.L.gosma_bnb_save(self.h, os.fsencode(path)), "bnb_save")
+
+    def bnb_load(self, path):
+        self._check(self.L.gosma_bnb_load(self.h, os.fsencode(path)), "bnb_load")
 
     def kernel_launches(self):
         return int(self.L.gosma_kernel_launches(self.h))
