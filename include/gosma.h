@@ -293,6 +293,22 @@ int gosma_mlp_grad(gosma_ctx *ctx, int n, const float *x, const float *dy, float
 int gosma_mlp_train(gosma_ctx *ctx, int n, const float *x, const float *label, const float *target, int batch,
                     int steps, float lr, float lam, float *losses);
 
+/* One iteration of a run (the quantities of Fig. 5): iteration number,
+ * seconds since the start, d*, the global lower bound, live sub-cubes and
+ * nodes so far. */
+typedef struct {
+    long long iteration;
+    double seconds, dstar, lower_bound;
+    long long queue_size, nodes;
+} gosma_trace_point;
+
+/* The per-iteration history of the current (or last) run of
+ * gosma_bnb_start / gosma_bnb_step / gosma_bnb_solve: *count receives the
+ * number of iterations, and the first min(count, max_points) points are
+ * copied to out (max_points = 0: count only).  A resumed run starts a new
+ * history. */
+int gosma_bnb_history(gosma_ctx *ctx, long long max_points, gosma_trace_point *out, long long *count);
+
 /* Checkpoint of a run between two gosma_bnb_step calls: the solver record,
  * the incumbent and its pose, and every queue slot (keys and sub-cubes) go
  * to the file at path.  GOSMA_ENOTREADY without a run. */

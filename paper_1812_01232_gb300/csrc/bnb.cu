@@ -712,6 +712,7 @@ struct Solve {
     int status = GOSMA_RUNNING;
     bool active = false;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    std::vector<gosma_trace_point> history;  // one point per iteration (Fig. 5)
 };
 
 static void delete_solve(Solve *v) {
@@ -921,6 +922,14 @@ extern "C" int gosma_bnb_step(gosma_ctx *ctx, int max_iters, gosma_result *out) 
         }
         v.dlb = h.minkey == DEAD ? v.dstar : (double)key_value(h.minkey);
         if (v.dlb > v.dstar) v.dlb = v.dstar;
+        gosma_trace_point tp;
+        tp.iteration = v.iters;
+        tp.seconds = seconds();
+        tp.dstar = v.dstar;
+        tp.lower_bound = v.dlb;
+        tp.queue_size = (long long)v.live;
+        tp.nodes = v.nodes;
+        v.history.push_back(tp);
     }
     v.seconds = seconds();
     if (out) fill_result(ctx, v, out);
@@ -1085,5 +1094,17 @@ extern "C" int gosma_bnb_load(gosma_ctx *ctx, const char *path) {
     v.seconds = c.seconds;
     v.status = c.status;
     v.active = true;
+    return GOSMA_OK;
+}
+
+extern "C" int gosma_bnb_history(gosma_ctx *ctx, long long max_points, gosma_trace_point *out, long long *count) {
+    if (!ctx) return GOSMA_EINVAL;
+    ctx->err.clear();
+    Solve *vp = solve_of(ctx);
+    if (!vp) return fail(ctx, GOSMA_ENOTREADY, "bnb_history: no run");
+    if (!count || (max_points > 0 && !out)) return fail(ctx, GOSMA_EINVAL, "bnb_history: bad arguments");
+    const long long n = (long long)vp->history.size();
+    *count = n;
+    if (max_points > 0) memcpy(out, vp->history.data(), sizeof(gosma_trace_point) * (size_t)(n < max_points ? n : max_points));
     return GOSMA_OK;
 }

@@ -58,6 +58,10 @@ class LearnOpts(C.Structure):
     _fields_ = [("use_mlp", C.c_int), ("beta", C.c_float), ("seed", C.c_int), ("trace_cap", C.c_int)]
 
 
+# gosma_trace_point as a numpy record
+HISTORY_DTYPE = np.dtype([("iteration", "<i8"), ("seconds", "<f8"), ("dstar", "<f8"), ("lower_bound", "<f8"),
+                          ("queue_size", "<i8"), ("nodes", "<i8")])
+
 # gosma_trace_rec as a numpy record
 TRACE_DTYPE = np.dtype([("feat", "<f4", (16,)), ("cube", "<f8", (10,)), ("lb", "<f8"), ("ub", "<f8"),
                         ("dstar", "<f8"), ("problem", "<i4"), ("iteration", "<i4")])
@@ -82,6 +86,7 @@ SIGNATURES = {
     "gosma_bnb_solve_batch_ex": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(Opts), C.c_void_p, C.c_void_p,
                                            C.c_void_p, C.c_void_p]),
     "gosma_bnb_step": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(Result)]),
+    "gosma_bnb_history": (C.c_int, [C.c_void_p, C.c_longlong, C.c_void_p, C.POINTER(C.c_longlong)]),
     "gosma_bnb_save": (C.c_int, [C.c_void_p, C.c_char_p]),
     "gosma_bnb_load": (C.c_int, [C.c_void_p, C.c_char_p]),
     "gosma_selftest_approx": (C.c_int, [C.c_void_p, D, D]),
@@ -387,6 +392,16 @@ class Gosma:
         self._check(self.L.gosma_mlp_train(self.h, len(x), _pf(x), _pf(label), _pf(target), int(batch), int(steps),
                                            float(lr), float(lam), _pf(losses)), "mlp_train")
         return losses[:steps]
+
+    def bnb_history(self):
+        """Per-iteration (iteration, seconds, dstar, lower_bound, queue_size, nodes) of the run (Fig. 5)."""
+        n = C.c_longlong(0)
+        self._check(self.L.gosma_bnb_history(self.h, 0, None, C.byref(n)), "bnb_history")
+        out = np.zeros(n.value, dtype=HISTORY_DTYPE)
+        if n.value:
+            self._check(self.L.gosma_bnb_history(self.h, n.value, out.ctypes.data_as(C.c_void_p), C.byref(n)),
+                        "bnb_history")
+        return out
 
     def bnb_save(self, path):
         self._check(self.L.gosma_bnb_save(self.h, os.fsencode(path)), "bnb_save")

@@ -229,3 +229,20 @@ def test_traces(ctx):
         assert np.allclose(f[:, 6], np.log2(c[:, 3] / np.pi) / 16, atol=1e-2)
         finite = np.isfinite(t["lb"])
         assert np.all(t["lb"][finite] <= t["ub"][finite] + 1e-6 * np.abs(t["ub"][finite]))
+
+
+def test_history_follows_the_run(ctx):
+    """Per-iteration history (the quantities of Fig. 5): d* never rises, the
+    node count grows by 8 per popped cube, the last point is the result."""
+    p = synth.tiny_problem(1000)
+    ctx.set_problem(p)
+    r = ctx.bnb_solve(eps=1e-3, pop=1024, max_seconds=120, queue_capacity=1 << 26)
+    h = ctx.bnb_history()
+    assert len(h) == r["iterations"]
+    assert np.all(np.diff(h["dstar"]) <= 0) and np.all(np.diff(h["nodes"]) > 0)
+    assert np.all(np.diff(h["seconds"]) >= 0) and np.array_equal(h["iteration"], np.arange(1, len(h) + 1))
+    assert h["dstar"][-1] == r["f"] and h["lower_bound"][-1] == pytest.approx(r["lb"], abs=1e-12)
+    assert h["nodes"][-1] == r["nodes"]
+    # the incumbent reaches its final value early; most of the run raises the lower bound
+    first = np.flatnonzero(h["dstar"] - r["f"] <= 1e-3 * r["c22"])[0]
+    assert first < 0.5 * len(h)
