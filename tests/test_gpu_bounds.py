@@ -178,3 +178,24 @@ def test_stress_parity_full_size(ctx, oracle_mod):
     ref = oracle_mod.bounds(oracle_mod.Mixtures.from_problem(prob), cubes[idx], prob["zeta"])
     compare(got[idx], ref, "stress")
     assert np.all(got[both, 0] <= got[both, 1])
+
+
+def test_largest_mixture_that_fits(ctx, oracle_mod):
+    """The largest model mixture whose per-component records fit the 200 KB
+    shared-memory budget (with 64 image components): parity on a sample,
+    and one component more is rejected."""
+    from paper_1812_01232_gb300.gosma import GosmaError
+    n2 = 64
+    n1 = (200 * 1024 - 32 * n2 - 16) // 52
+    prob = synth.stress_problem(4100, n1=n1, n2=n2)
+    ctx.set_problem(prob)
+    cubes = synth.tree_cubes(4101, 64, prob["t_lo"], prob["t_hi"], 4, 12, near=(prob["r_gt"], prob["t_gt"]),
+                             near_frac=0.5)
+    got = ctx.eval_bounds_detail(cubes)
+    both = np.isfinite(got[:, 0]) & np.isfinite(got[:, 1])
+    idx = np.concatenate([np.arange(4), np.flatnonzero(both)[:4]])
+    ref = oracle_mod.bounds(oracle_mod.Mixtures.from_problem(prob), cubes[idx], prob["zeta"])
+    compare(got[idx], ref, "largest")
+    big = synth.stress_problem(4100, n1=n1 + 1, n2=n2)
+    with pytest.raises(GosmaError):
+        ctx.set_problem(big)
