@@ -99,13 +99,18 @@ typedef struct {
 
 /* One independent alignment problem for gosma_bnb_solve_batch: the mixtures
  * (as in gosma_set_mixtures, host pointers, read during the call only) and
- * the translation domain (as in gosma_set_domain). */
+ * the translation domain (as in gosma_set_domain).  nclass > 1 makes it a
+ * semantic problem with class sizes n1c, n2c and class weights w, as in
+ * gosma_set_mixtures_classes; nclass <= 1 ignores those arrays. */
 typedef struct {
     int n1;
     const double *mu1, *sigma1, *phi1;
     int n2;
     const double *mu2, *kappa2, *phi2;
     double t_lo[3], t_hi[3], zeta;
+    int nclass;
+    const int *n1c, *n2c;
+    const double *w;
 } gosma_problem;
 
 /* Create a context on CUDA device `device`, issuing all work on `stream`

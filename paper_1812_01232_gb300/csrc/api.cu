@@ -7,6 +7,7 @@
 
 #include <new>
 
+#include "classes.h"
 #include "gosma_internal.cuh"
 
 namespace gosma {
@@ -125,39 +126,14 @@ static int set_mixtures_impl(gosma_ctx *ctx, int nclass, const int *n1c, const i
             return fail(ctx, GOSMA_EINVAL, "set_mixtures: kappa2 must be > 0, phi2 >= 0, |mu2_j| = 1");
     }
     // classes: per-class weight sums, class ids, pair ranges; weights scaled by sqrt(w_l)
-    std::vector<double> phi1(phi1_in, phi1_in + n1), phi2(phi2_in, phi2_in + n2);
-    std::vector<int> cls1(n1), cls2(n2), rj0(n1), rj1(n1), rm1(n1);
-    {
-        int i0 = 0, j0 = 0;
-        for (int l = 0; l < nclass; ++l) {
-            const int a = n1c ? n1c[l] : n1, b = n2c ? n2c[l] : n2;
-            const double wl = w ? w[l] : 1.0;
-            if (a < 1 || b < 1 || i0 + a > n1 || j0 + b > n2 || !(wl >= 0) || !isfinite(wl))
-                return fail(ctx, GOSMA_EINVAL, "set_mixtures: class sizes must be >= 1, sum to n1 and n2; w >= 0");
-            double s1 = 0, s2 = 0;
-            for (int i = i0; i < i0 + a; ++i) s1 += phi1[i];
-            for (int j = j0; j < j0 + b; ++j) s2 += phi2[j];
-            if (fabs(s1 - 1.0) > 1e-9 || fabs(s2 - 1.0) > 1e-9)
-                return fail(ctx, GOSMA_EINVAL, "set_mixtures: each class's mixture weights must sum to 1");
-            const double sw = sqrt(wl);
-            for (int i = i0; i < i0 + a; ++i) {
-                phi1[i] *= sw;
-                cls1[i] = l;
-                rj0[i] = j0;
-                rj1[i] = j0 + b;
-                rm1[i] = i0 + a;
-            }
-            for (int j = j0; j < j0 + b; ++j) {
-                phi2[j] *= sw;
-                cls2[j] = l;
-            }
-            i0 += a;
-            j0 += b;
-        }
-        if (i0 != n1 || j0 != n2)
-            return fail(ctx, GOSMA_EINVAL, "set_mixtures: class sizes must sum to n1 and n2");
+    ClassLayout CL;
+    if (const char *msg = class_layout(nclass, n1c, n2c, w, n1, n2, phi1_in, phi2_in, CL)) {
+        std::string m = std::string("set_mixtures: ") + msg;
+        return fail(ctx, GOSMA_EINVAL, m.c_str());
     }
-    const bool classes = nclass > 1;
+    const std::vector<double> &phi1 = CL.phi1, &phi2 = CL.phi2;
+    const std::vector<int> &cls1 = CL.cls1, &cls2 = CL.cls2, &rj0 = CL.rj0, &rj1 = CL.rj1, &rm1 = CL.rm1;
+    const bool classes = CL.classes;
     cudaSetDevice(ctx->device);
     size_t nd = 3 * (size_t)n1 + 2 * n1 + 3 * (size_t)n2 + 2 * n2;
     size_t nf = 8 * (size_t)n1 + 8 * (size_t)n2;

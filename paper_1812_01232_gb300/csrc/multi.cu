@@ -42,6 +42,7 @@
 #include <vector>
 
 #include "bnb_common.cuh"
+#include "classes.h"
 #include "lbfgs.h"
 #include "mlp.cuh"
 #include "objective_core.cuh"
@@ -979,13 +980,11 @@ static int validate_problem(gosma_ctx *ctx, const gosma_problem &p, int k) {
         snprintf(msg, sizeof msg, "bnb_solve_batch: problem %d: empty mixture or null pointer", k);
         return fail(ctx, GOSMA_EINVAL, msg);
     }
-    double s1 = 0, s2 = 0;
     for (int i = 0; i < p.n1; ++i) {
         if (!(p.sigma1[i] > 0) || !(p.phi1[i] >= 0)) {
             snprintf(msg, sizeof msg, "bnb_solve_batch: problem %d: sigma1 > 0 and phi1 >= 0 required", k);
             return fail(ctx, GOSMA_EINVAL, msg);
         }
-        s1 += p.phi1[i];
     }
     for (int j = 0; j < p.n2; ++j) {
         const double *m = p.mu2 + 3 * j;
@@ -994,10 +993,16 @@ static int validate_problem(gosma_ctx *ctx, const gosma_problem &p, int k) {
             snprintf(msg, sizeof msg, "bnb_solve_batch: problem %d: kappa2 > 0, phi2 >= 0, |mu2| = 1 required", k);
             return fail(ctx, GOSMA_EINVAL, msg);
         }
-        s2 += p.phi2[j];
     }
-    if (fabs(s1 - 1.0) > 1e-9 || fabs(s2 - 1.0) > 1e-9) {
-        snprintf(msg, sizeof msg, "bnb_solve_batch: problem %d: weights must sum to 1", k);
+    ClassLayout CL;
+    const bool sem = p.nclass > 1;
+    if (sem && (!p.n1c || !p.n2c || !p.w)) {
+        snprintf(msg, sizeof msg, "bnb_solve_batch: problem %d: class arrays missing", k);
+        return fail(ctx, GOSMA_EINVAL, msg);
+    }
+    if (const char *m = class_layout(sem ? p.nclass : 1, sem ? p.n1c : nullptr, sem ? p.n2c : nullptr,
+                                     sem ? p.w : nullptr, p.n1, p.n2, p.phi1, p.phi2, CL)) {
+        snprintf(msg, sizeof msg, "bnb_solve_batch: problem %d: %s", k, m);
         return fail(ctx, GOSMA_EINVAL, msg);
     }
     for (int a = 0; a < 3; ++a)
@@ -1238,12 +1243,32 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
     }
     std::vector<double> hd(d_off[nprob]);
     std::vector<float> hf(f_off[nprob], 0.f);
+    // semantic problems: class ids and pair ranges (ints), weights scaled per class
+    std::vector<size_t> i_off(nprob + 1, 0);
+    std::vector<ClassLayout> layouts(nprob);
     for (int k = 0; k < nprob; ++k) {
         const gosma_problem &p = probs[k];
+        const bool sem = p.nclass > 1;
+        class_layout(sem ? p.nclass : 1, sem ? p.n1c : nullptr, sem ? p.n2c : nullptr, sem ? p.w : nullptr, p.n1,
+                     p.n2, p.phi1, p.phi2, layouts[k]);  // validated above
+        i_off[k + 1] = i_off[k] + (layouts[k].classes ? 5 * (size_t)p.n1 + p.n2 : 0);
+    }
+    std::vector<int> hi(i_off[nprob] ? i_off[nprob] : 1);
+    for (int k = 0; k < nprob; ++k) {
+        const gosma_problem &p = probs[k];
+        const ClassLayout &CL = layouts[k];
         double *d = hd.data() + d_off[k];
         memcpy(d, p.mu1, sizeof(double) * 3 * p.n1);
         memcpy(d + 3 * p.n1, p.sigma1, sizeof(double) * p.n1);
-        memcpy(d + 4 * p.n1, p.phi1, sizeof(double) * p.n1);
+        memcpy(d + 4 * p.n1, CL.phi1.data(), sizeof(double) * p.n1);
+        if (CL.classes) {
+            int *q = hi.data() + i_off[k];
+            memcpy(q, CL.cls1.data(), sizeof(int) * p.n1);
+            memcpy(q + p.n1, CL.rj0.data(), sizeof(int) * p.n1);
+            memcpy(q + 2 * p.n1, CL.rj1.data(), sizeof(int) * p.n1);
+            memcpy(q + 3 * p.n1, CL.rm1.data(), sizeof(int) * p.n1);
+            memcpy(q + 4 * p.n1, CL.cls2.data(), sizeof(int) * p.n2);
+        }
         double *d2 = d + 5 * p.n1;
         for (int j = 0; j < p.n2; ++j) {  // unit image directions
             const double *m = p.mu2 + 3 * j;
@@ -1251,7 +1276,7 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
             for (int a = 0; a < 3; ++a) d2[3 * j + a] = m[a] / nn;
         }
         memcpy(d2 + 3 * p.n2, p.kappa2, sizeof(double) * p.n2);
-        memcpy(d2 + 4 * p.n2, p.phi2, sizeof(double) * p.n2);
+        memcpy(d2 + 4 * p.n2, CL.phi2.data(), sizeof(double) * p.n2);
         float *f = hf.data() + f_off[k];
         for (int j = 0; j < p.n2; ++j) f[2 * p.n1 + j] = (float)p.kappa2[j];
     }
@@ -1259,8 +1284,11 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
     float *fmix = nullptr;
     if ((e = B.get(&dmix, hd.size())) != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(batch mixtures)");
     if ((e = B.get(&fmix, hf.size())) != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(batch mixtures)");
+    int *imix = nullptr;
+    if ((e = B.get(&imix, hi.size())) != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(batch mixtures)");
     e = cudaMemcpyAsync(dmix, hd.data(), sizeof(double) * hd.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(fmix, hf.data(), sizeof(float) * hf.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(imix, hi.data(), sizeof(int) * hi.size(), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "copy batch mixtures");
     std::vector<ProbDev> hp(nprob);
     std::vector<ProbState> hs(nprob);
@@ -1287,6 +1315,14 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
         mx.mu2h = mx.mu1l + 3 * n1;
         mx.mu2l = mx.mu2h + 3 * n2;
         mx.zeta = p.zeta;
+        if (layouts[k].classes) {
+            int *q = imix + i_off[k];
+            mx.cls1 = q;
+            mx.rj0 = q + n1;
+            mx.rj1 = q + 2 * n1;
+            mx.rm1 = q + 3 * n1;
+            mx.cls2 = q + 4 * n1;
+        }
         double c22 = 0;
         int rc = setup_constants_mix(ctx, st, mx, &c22);
         if (rc) return rc;

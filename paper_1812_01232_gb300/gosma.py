@@ -47,7 +47,8 @@ class Result(C.Structure):
 
 class Problem(C.Structure):
     _fields_ = [("n1", C.c_int), ("mu1", D), ("sigma1", D), ("phi1", D), ("n2", C.c_int), ("mu2", D),
-                ("kappa2", D), ("phi2", D), ("t_lo", C.c_double * 3), ("t_hi", C.c_double * 3), ("zeta", C.c_double)]
+                ("kappa2", D), ("phi2", D), ("t_lo", C.c_double * 3), ("t_hi", C.c_double * 3), ("zeta", C.c_double),
+                ("nclass", C.c_int), ("n1c", C.POINTER(C.c_int)), ("n2c", C.POINTER(C.c_int)), ("w", D)]
 
 
 # exported symbols and their signatures (restype, argtypes); the header is the authority
@@ -334,6 +335,12 @@ class Gosma:
                 p.t_lo[q] = float(pr["t_lo"][q])
                 p.t_hi[q] = float(pr["t_hi"][q])
             p.zeta = float(pr["zeta"])
+            if "n1c" in pr:  # semantic problem
+                c = [np.ascontiguousarray(np.asarray(pr["n1c"], dtype=np.int32)),
+                     np.ascontiguousarray(np.asarray(pr["n2c"], dtype=np.int32)), _f64(pr["w"], (-1,))]
+                keep.append(c)
+                ip = C.POINTER(C.c_int)
+                p.nclass, p.n1c, p.n2c, p.w = len(c[0]), c[0].ctypes.data_as(ip), c[1].ctypes.data_as(ip), _p(c[2])
         o = self._opts(eps, pop, max_nodes, max_seconds, use_sma, sma_max_iter, queue_capacity)
         res = (Result * len(problems))()
         lo = LearnOpts(0, 0.0, 0, int(trace_cap))

@@ -123,3 +123,22 @@ def test_invalid_classes(ctx):
     with pytest.raises(GosmaError):
         ctx.set_mixtures_classes([p["n1c"][0], 0], p["n2c"], p["w"], p["mu1"], p["sigma1"], p["phi1"], p["mu2"],
                                  p["kappa2"], p["phi2"])
+
+
+def test_batched_semantic_problems(ctx, oracle_mod):
+    """Semantic and plain problems in one batch reach the certificates of
+    their single-problem solves."""
+    probs = [synth.semantic_problem(11, nclass=2, n1=4, n_in=3, n_out=1), synth.tiny_problem(1000),
+             synth.semantic_problem(3, nclass=2, n1=3, noise_free=True)]
+    res = ctx.bnb_solve_batch(probs, eps=1e-2, pop=256, max_seconds=120, queue_capacity=1 << 25)
+    for p, r in zip(probs, res):
+        ctx.set_problem(p)
+        s = ctx.bnb_solve(eps=1e-2, pop=256, max_seconds=120, queue_capacity=1 << 25)
+        assert r["status_name"] == s["status_name"] == "optimal"
+        assert r["c22"] == pytest.approx(s["c22"], rel=1e-12)
+        assert abs(r["f"] - s["f"]) <= 1e-2 * s["c22"]
+        assert r["lb"] <= s["f"] + 1e-9 and s["lb"] <= r["f"] + 1e-9
+    p = probs[0]
+    mixes = _mixes(oracle_mod, p)
+    f = sum(w * oracle_mod.objective_r(m, res[0]["r"], res[0]["t"]) for w, m in zip(p["w"], mixes))
+    assert f == pytest.approx(res[0]["f"], rel=1e-10, abs=1e-12)
