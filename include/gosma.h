@@ -156,7 +156,12 @@ int gosma_set_domain(gosma_ctx *ctx, const double t_lo[3], const double t_hi[3],
  * translation part within zeta of one mean) get lb = ub = +inf.
  * Pair terms are computed in FP32 (log domain) with a rounding slack that
  * keeps lb at or below the exact-arithmetic bound; per-cube sums are FP64.
- * on_device = 0: cubes, lb, ub are host pointers (copied in and out).
+ * on_device = 0: cubes, lb, ub are host pointers; the call returns when the
+ * results are in place.  Where the device can address ordinary host memory
+ * through the host page tables (a coherent CPU-GPU link), the kernels read
+ * and write these arrays in place; otherwise they are staged through pinned
+ * buffers in pipelined chunks (environment GOSMA_STAGED_HOST_IO=1 at
+ * gosma_create forces the staged path).
  * on_device = 1: they are device pointers on the context's device; the call
  * is then asynchronous on the context's stream.  n = 0 is a no-op. */
 int gosma_eval_bounds(gosma_ctx *ctx, const gosma_cube *cubes, int n, double *lb, double *ub, int on_device);

@@ -1,6 +1,7 @@
 // C ABI entry points of libgosma (declared in include/gosma.h): context,
 // mixtures, domain, bounds and objective.  Branch-and-bound is in bnb.cu.
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <vector>
@@ -53,6 +54,11 @@ __global__ void pack_bounds(const gosma_bound *__restrict__ in, int n, double2 *
     if (k < n) out[k] = make_double2(in[k].lb, in[k].ub);
 }
 
+__global__ void copy_records(const gosma_bound *__restrict__ in, int n, gosma_bound *__restrict__ out) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) out[k] = in[k];
+}
+
 __global__ void split_bounds(const gosma_bound *__restrict__ in, int n, double *lb, double *ub) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < n) {
@@ -81,6 +87,12 @@ int gosma_create(int device, void *stream, gosma_ctx **out) {
     c->device = device;
     c->stream = (cudaStream_t)stream;
     c->sm_count = prop.multiProcessorCount;
+    int pageable = 0, host_tables = 0;
+    if (cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, device) != cudaSuccess) pageable = 0;
+    if (cudaDeviceGetAttribute(&host_tables, cudaDevAttrPageableMemoryAccessUsesHostPageTables, device) != cudaSuccess)
+        host_tables = 0;
+    const char *staged = getenv("GOSMA_STAGED_HOST_IO");  // force the staged path (tests of both paths)
+    c->direct_host = pageable && host_tables && !(staged && staged[0] == '1');
     *out = c;
     return GOSMA_OK;
 }
@@ -291,6 +303,22 @@ static int eval_common(gosma_ctx *ctx, const gosma_cube *cubes, int n, gosma_bou
             e = cudaGetLastError();
             if (e != cudaSuccess) return cuda_fail(ctx, e, "launch(split)");
         }
+        return GOSMA_OK;
+    }
+    if (ctx->direct_host) {
+        // the kernels read the caller's cubes and write the caller's results in
+        // place over the coherent link: no staging copies
+        rc = ensure_stage(ctx, bo);
+        if (rc) return rc;
+        gosma_bound *drec = (gosma_bound *)ctx->d_stage;
+        rc = launch_bounds(ctx, cubes, n, drec);
+        if (rc) return rc;
+        if (detail) copy_records<<<(n + 255) / 256, 256, 0, ctx->stream>>>(drec, n, detail);
+        else split_bounds<<<(n + 255) / 256, 256, 0, ctx->stream>>>(drec, n, lb, ub);
+        ++ctx->launches;
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "bounds (host buffers)");
         return GOSMA_OK;
     }
     // Host buffers: pipelined over chunks, so that staging the next chunk on

@@ -150,6 +150,9 @@ struct gosma_ctx {
     gosma::Mlp *mlp = nullptr;
     // error-path testing: the next fail_allocs device allocations fail
     int fail_allocs = 0;
+    // kernels may address ordinary host memory (coherent CPU-GPU link with
+    // the host page tables): host-buffer calls then skip the staging copies
+    bool direct_host = false;
 
     // number of kernels this context has launched
     long long launches = 0;

@@ -199,3 +199,25 @@ def test_largest_mixture_that_fits(ctx, oracle_mod):
     big = synth.stress_problem(4100, n1=n1 + 1, n2=n2)
     with pytest.raises(GosmaError):
         ctx.set_problem(big)
+
+
+def test_direct_and_staged_host_paths_agree(ctx):
+    """Host-buffer calls give the same bits whether the kernels address the
+    caller's arrays in place or go through staging copies."""
+    import os
+    from paper_1812_01232_gb300.gosma import Gosma
+    prob = synth.paper_scale_problem(2000)
+    cubes = synth.tree_cubes(2002, 40000, prob["t_lo"], prob["t_hi"], 2, 12)
+    ctx.set_problem(prob)
+    lb_a, ub_a = ctx.eval_bounds(cubes)
+    det_a = ctx.eval_bounds_detail(cubes[:1000])
+    os.environ["GOSMA_STAGED_HOST_IO"] = "1"
+    try:
+        staged = Gosma(0)
+    finally:
+        del os.environ["GOSMA_STAGED_HOST_IO"]
+    staged.set_problem(prob)
+    lb_b, ub_b = staged.eval_bounds(cubes)
+    det_b = staged.eval_bounds_detail(cubes[:1000])
+    staged.close()
+    assert np.array_equal(lb_a, lb_b) and np.array_equal(ub_a, ub_b) and np.array_equal(det_a, det_b)
