@@ -238,6 +238,7 @@ typedef struct {
     float beta;
     int seed;
     int trace_cap;
+    int active_iters;  /* score only during the first active_iters iterations (0: always) */
 } gosma_learn_opts;
 
 /* One popped sub-cube of a trace: the network's 16 input features as the

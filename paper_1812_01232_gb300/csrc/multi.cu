@@ -619,7 +619,8 @@ __device__ __forceinline__ unsigned long long dbl_order(double d) {
 __global__ void __launch_bounds__(MP_BLOCK)
     mp_append(const ProbDev *__restrict__ P, ProbState *__restrict__ S, const int *__restrict__ off,
               const Node *__restrict__ kids, const double *__restrict__ kid_ub, QueueBufs Qb,
-              const float *__restrict__ Y, float beta, int seed) {
+              const float *__restrict__ Yin, const int *__restrict__ scored, float beta, int seed) {
+    const float *__restrict__ Y = Yin && *scored > 0 ? Yin : nullptr;  // scores of this iteration, if any
     __shared__ int sh[32];
     __shared__ unsigned long long s_ub;
     __shared__ unsigned int s_lg;
@@ -830,10 +831,17 @@ __device__ inline void cube_features(const CubeGeom &g, const Domain &dom, doubl
 }
 
 // Network input rows for every child of this iteration.
+// Rows the network scores this iteration: every child while the learned form
+// is active (the first active_iters iterations, or always when 0), else none.
+__global__ void mp_learn_rows(const int *__restrict__ off, int nprob, const int *__restrict__ d_iter, int active_iters,
+                              int *__restrict__ rows) {
+    *rows = (active_iters <= 0 || *d_iter < active_iters) ? off[nprob] : 0;
+}
+
 __global__ void mp_features(const ProbDev *__restrict__ P, const ProbState *__restrict__ S, const int *__restrict__ off,
                             int nprob, const Node *__restrict__ kids, const double *__restrict__ kid_ub,
-                            bf16 *__restrict__ X) {
-    const int N = off[nprob];
+                            const int *__restrict__ rows, bf16 *__restrict__ X) {
+    const int N = *rows;
     for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < N; w += gridDim.x * blockDim.x) {
         const int k = mp_find(off, nprob, w);
         CubeGeom g;
@@ -1371,7 +1379,7 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
         (e = B.get(&Qb.c_lt, max_chunks)) == cudaSuccess && (e = B.get(&Qb.c_eq, max_chunks)) == cudaSuccess &&
         (e = B.get(&Qb.c_out, max_chunks)) == cudaSuccess && (e = B.get(&Qb.c_eqb, max_chunks)) == cudaSuccess &&
         (e = B.get(&Qb.c_live, max_chunks)) == cudaSuccess && (e = B.get(&Qb.c_base, max_chunks)) == cudaSuccess &&
-        (e = B.get(&Qb.quota, 2)) == cudaSuccess &&  // [1]: the bound kernel's work counter
+        (e = B.get(&Qb.quota, 3)) == cudaSuccess &&  // [1]: the bound kernel's work counter, [2]: rows to score
         (e = B.get(&parents, (size_t)pop * nprob)) == cudaSuccess && (e = B.get(&kids, nkids)) == cudaSuccess &&
         (e = B.get(&kid_ub, nkids)) == cudaSuccess && (e = B.get(&prep, nkids)) == cudaSuccess &&
         (e = B.get(&off, nprob + 1)) == cudaSuccess && (e = B.get(&ioff, nprob)) == cudaSuccess &&
@@ -1399,6 +1407,7 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
     }
     // learned form: network input rows for every child, and the traces
     const int max_rows = (int)nkids;
+    int *d_lrows = Qb.quota + 2;  // rows the network scores this iteration
     const float *Yd = nullptr;
     bf16 *Xd = nullptr;
     if (lo.use_mlp) {
@@ -1539,11 +1548,12 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
     auto back = [&]() -> cudaError_t {
         cudaError_t eb = cudaSuccess;
         if (lo.use_mlp) {  // score every child on the tensor cores
-            mp_features<<<prep_grid, 128, 0, st>>>(dP, dS, off, nprob, kids, kid_ub, Xd);
-            ++ctx->launches;
-            eb = mlp_forward_rows(ctx, max_rows, off + nprob, st);
+            mp_learn_rows<<<1, 1, 0, st>>>(off, nprob, d_iter, lo.active_iters, d_lrows);
+            mp_features<<<prep_grid, 128, 0, st>>>(dP, dS, off, nprob, kids, kid_ub, d_lrows, Xd);
+            ctx->launches += 2;
+            eb = mlp_forward_rows(ctx, max_rows, d_lrows, st);
         }
-        mp_append<<<nprob, MP_BLOCK, 0, st>>>(dP, dS, off, kids, kid_ub, Qb, Yd, lo.beta, lo.seed);
+        mp_append<<<nprob, MP_BLOCK, 0, st>>>(dP, dS, off, kids, kid_ub, Qb, Yd, d_lrows, lo.beta, lo.seed);
         mp_obj_prep<<<dim3((max_n1 + 127) / 128, 2 * nprob), 128, 0, st>>>(dP, dS, ioff, idata);
         mp_obj_pairs<<<dim3(nblk, 2 * nprob), MPO_BLOCK, 0, st>>>(dP, dS, ioff, idata, part, nblk);
         mp_obj_final<<<(nprob + 127) / 128, 128, 0, st>>>(dS, nprob, part, nblk);

@@ -56,7 +56,8 @@ FP = C.POINTER(C.c_float)
 
 
 class LearnOpts(C.Structure):
-    _fields_ = [("use_mlp", C.c_int), ("beta", C.c_float), ("seed", C.c_int), ("trace_cap", C.c_int)]
+    _fields_ = [("use_mlp", C.c_int), ("beta", C.c_float), ("seed", C.c_int), ("trace_cap", C.c_int),
+                ("active_iters", C.c_int)]
 
 
 # gosma_trace_point as a numpy record
@@ -316,8 +317,9 @@ class Gosma:
         """Algorithm 1 for many independent problems at once (list of problem
         dicts as produced by synth); returns one result dict per problem.
 
-        ``learned``: None (plain) or a dict with ``beta`` and ``seed`` for the
-        network-ordered form (parameters loaded with mlp_set_params).  With
+        ``learned``: None (plain) or a dict with ``beta``, ``seed`` and
+        ``active_iters`` for the network-ordered form (parameters loaded with
+        mlp_set_params).  With
         ``trace_cap > 0`` returns ``(results, traces)``, traces a list of
         TRACE_DTYPE arrays, one per problem, in pop order."""
         if not problems:
@@ -343,9 +345,10 @@ class Gosma:
                 p.nclass, p.n1c, p.n2c, p.w = len(c[0]), c[0].ctypes.data_as(ip), c[1].ctypes.data_as(ip), _p(c[2])
         o = self._opts(eps, pop, max_nodes, max_seconds, use_sma, sma_max_iter, queue_capacity)
         res = (Result * len(problems))()
-        lo = LearnOpts(0, 0.0, 0, int(trace_cap))
+        lo = LearnOpts(0, 0.0, 0, int(trace_cap), 0)
         if learned is not None:
             lo.use_mlp, lo.beta, lo.seed = 1, float(learned.get("beta", 0.0)), int(bool(learned.get("seed", True)))
+            lo.active_iters = int(learned.get("active_iters", 0))
         tr = np.zeros(max(1, len(problems) * int(trace_cap)), dtype=TRACE_DTYPE)
         cnt = np.zeros(len(problems), dtype=np.int32)
         self._check(self.L.gosma_bnb_solve_batch_ex(self.h, len(problems), C.cast(arr, C.c_void_p), C.byref(o),

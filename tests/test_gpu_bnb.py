@@ -185,15 +185,15 @@ def _params(seed):
     return learn.init_params(seed)
 
 
-@pytest.mark.parametrize("beta", [0.0, 1e-4])
-def test_learned_form_keeps_the_certificate(ctx, oracle_mod, beta):
+@pytest.mark.parametrize("beta,active", [(0.0, 0), (1e-4, 0), (1e-3, 8)])
+def test_learned_form_keeps_the_certificate(ctx, oracle_mod, beta, active):
     """The network only reorders pops and proposes seeds: with any weights the
     certified optimum is the oracle's."""
     gold = json.load(open(GOLDEN))["1000"]
     ctx.mlp_set_params(_params(3))
     p = synth.tiny_problem(1000)
     r = ctx.bnb_solve_batch([p], eps=1e-3, pop=1024, max_seconds=120, queue_capacity=1 << 26,
-                            learned=dict(beta=beta, seed=True))[0]
+                            learned=dict(beta=beta, seed=True, active_iters=active))[0]
     assert r["status_name"] == "optimal"
     assert abs(r["f"] - gold["f"]) <= 1e-3 * gold["c22"]
     assert r["lb"] <= gold["f"] + 1e-9 and gold["lb"] <= r["f"] + 1e-9
