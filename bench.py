@@ -149,7 +149,7 @@ def kernel_source_sha256():
 def kernel_traffic():
     """DRAM bytes per launch of the bound kernel from the committed ncu capture,
     or None when the kernel's device code changed since the capture."""
-    prof = os.path.join(ROOT, "profiles", "bound_children_traffic.json")
+    prof = os.path.join(ROOT, "profiles", "bound_children_traffic.txt")
     if not os.path.exists(prof):
         return None
     rec = json.load(open(prof))
