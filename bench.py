@@ -377,19 +377,20 @@ def run_time_to_certified(n_prob):
     ctx = Gosma(0)
     eps = 1e-3
     probs = [synth.tiny_problem(200000 + s) for s in range(n_prob)]
-    out = {"workload": "%d tiny problems (10 x 8 components), eps 1e-3, pop 1024, queue 2^26 per problem" % n_prob}
+    out = {"workload": "%d tiny problems (10 x 8 components), eps 1e-3, pop %d (%d children per iteration), "
+                       "queue 2^26 per problem" % (n_prob, POP, 8 * POP)}
     single = []
     t0 = time.perf_counter()
     for p in probs:
         ctx.set_problem(p)
-        single.append(ctx.bnb_solve(eps=eps, pop=1024, max_seconds=60, queue_capacity=1 << 26))
+        single.append(ctx.bnb_solve(eps=eps, pop=POP, max_seconds=60, queue_capacity=1 << 26))
     out["plain_single"] = {"wall_s": time.perf_counter() - t0, "nodes": int(sum(r["nodes"] for r in single)),
                            "certified": int(sum(r["status_name"] == "optimal" for r in single))}
     ctx.mlp_set_params(learn.load(os.path.join(ROOT, "paper_1812_01232_gb300", "weights", "gosma_mlp.npz")))
     for name, learned in (("plain_batched", None),
                           ("learned_batched", {"beta": 1e-4, "seed": True, "active_iters": 32})):
         t0 = time.perf_counter()
-        res = ctx.bnb_solve_batch(probs, eps=eps, pop=1024, max_seconds=120, queue_capacity=1 << 26, learned=learned)
+        res = ctx.bnb_solve_batch(probs, eps=eps, pop=POP, max_seconds=120, queue_capacity=1 << 26, learned=learned)
         out[name] = {"wall_s": time.perf_counter() - t0, "nodes": int(sum(r["nodes"] for r in res)),
                      "certified": int(sum(r["status_name"] == "optimal" for r in res)),
                      "agree_with_single": int(sum(abs(r["f"] - q["f"]) <= eps * q["c22"]

@@ -197,7 +197,7 @@ int gosma_eval_objective_grad_noalloc(gosma_ctx *ctx, int count, const double *d
 /* Algorithm 1 (GOSMA) on the device: branch, bound, prune and select run in
  * device kernels; d* is always an FP64 evaluation of f, refined by SMA
  * (Sec. 5) whenever a sub-cube's upper bound beats it.  opts may be NULL
- * (eps = 0.1, pop = 1024, no limits, SMA on).  Equivalent to
+ * (eps = 0.1, pop = 8192, no limits, SMA on).  Equivalent to
  * gosma_bnb_start followed by gosma_bnb_step(ctx, 0, out). */
 int gosma_bnb_solve(gosma_ctx *ctx, const gosma_opts *opts, gosma_result *out);
 

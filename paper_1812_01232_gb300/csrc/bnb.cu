@@ -769,7 +769,7 @@ extern "C" int gosma_bnb_start(gosma_ctx *ctx, const gosma_opts *opts_in) {
     gosma_opts o;
     memset(&o, 0, sizeof o);
     o.eps = 0.1;
-    o.pop = 1024;
+    o.pop = 8192;  // 65,536 children per iteration fill the GPU
     o.use_sma = 1;
     o.sma_max_iter = 100;
     if (opts_in) o = *opts_in;
