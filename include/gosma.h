@@ -194,6 +194,31 @@ int gosma_eval_objective_grad(gosma_ctx *ctx, int count, const double *x, double
  * make that first call before any stream capture. */
 int gosma_eval_objective_grad_noalloc(gosma_ctx *ctx, int count, const double *d_x, double *d_out);
 
+/* SMA (Sec. 5) from `count` seed poses at once, on the device: each seed is
+ * refined by L-BFGS (memory 8, backtracking Armijo line search, first step
+ * 0.01 in the largest coordinate) on f of Lemma 1, restricted to feasible
+ * poses (translation inside the domain of gosma_set_domain and at least zeta
+ * from every model mean; infeasible trial poses halve the step unevaluated).
+ * A thread block runs a seed's whole refinement with no host round trip.
+ * x0: count x 6 seeds (r then t).  max_iter >= 0: L-BFGS iterations per seed
+ * (0 returns the seeds with their f).
+ * precision 64: f and its gradient in FP64 throughout.  precision 32: the
+ * search evaluates them in FP32 and also stops once an iteration gains less
+ * than 2^-26 times the sum of the terms' magnitudes or 20 halvings of the
+ * step find no decrease; the returned f is still FP64.
+ * Outputs: x (count x 6, may alias x0) the refined poses; f (count) the FP64
+ * objective at x, +inf for an infeasible seed (whose x is the seed); grad
+ * (count x 6 or NULL) the FP64 gradient at x (0 for infeasible seeds); iters
+ * (count or NULL) the accepted iterations per seed, -1 for infeasible seeds.
+ * on_device = 0: host pointers, the call returns with the results in place.
+ * on_device = 1: device pointers on the context's device; asynchronous on
+ * the context's stream.  Requires gosma_set_mixtures and gosma_set_domain
+ * (GOSMA_ENOTREADY otherwise); GOSMA_EINVAL for count < 0, max_iter < 0,
+ * another precision, null seeds or outputs, or mixtures whose FP32 tables
+ * (36 n1 + 24 n2 bytes) exceed one block's shared memory. */
+int gosma_sma_batch(gosma_ctx *ctx, int count, const double *x0, int max_iter, int precision, double *x, double *f,
+                    double *grad, int *iters, int on_device);
+
 /* Algorithm 1 (GOSMA) on the device: branch, bound, prune and select run in
  * device kernels; d* is always an FP64 evaluation of f, refined by SMA
  * (Sec. 5) whenever a sub-cube's upper bound beats it.  opts may be NULL

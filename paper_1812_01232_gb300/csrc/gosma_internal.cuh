@@ -140,6 +140,10 @@ struct gosma_ctx {
     void *d_obj = nullptr;
     size_t obj_bytes = 0;
 
+    // batched SMA scratch (sma.cu)
+    void *d_sma = nullptr;
+    size_t sma_bytes = 0;
+
     // per-cube rotation pre-pass (gosma_eval_bounds)
     void *d_rot = nullptr;
     size_t rot_bytes = 0;

@@ -82,6 +82,8 @@ SIGNATURES = {
     "gosma_eval_objective": (C.c_int, [C.c_void_p, D, D, D]),
     "gosma_eval_objective_grad": (C.c_int, [C.c_void_p, C.c_int, D, D, D]),
     "gosma_eval_objective_grad_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "gosma_sma_batch": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                  C.c_void_p, C.c_void_p, C.c_int]),
     "gosma_bnb_solve": (C.c_int, [C.c_void_p, C.POINTER(Opts), C.POINTER(Result)]),
     "gosma_bnb_start": (C.c_int, [C.c_void_p, C.POINTER(Opts)]),
     "gosma_bnb_solve_batch": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(Opts), C.c_void_p]),
@@ -285,6 +287,29 @@ class Gosma:
                                                              C.c_void_p(out_dev.data_ptr())),
                     "eval_objective_grad_noalloc")
         return out_dev
+
+    def sma_batch(self, x0, max_iter=100, precision=32, x=None, f=None, grad=None, iters=None, with_grad=True):
+        """SMA (Sec. 5) from many seed poses at once on the device.
+
+        Host call: x0 is an (n, 6) array; returns dict(x, f, grad, iters) of
+        numpy arrays (grad None unless with_grad).  Device call: x0 is a CUDA
+        float64 tensor (n, 6) and x (n, 6), f (n,) and optionally grad (n, 6),
+        iters (n,) int32 are CUDA tensors filled asynchronously on the context
+        stream; returns them."""
+        if _is_torch_cuda(x0):
+            n = x0.shape[0]
+            ptr = lambda a: C.c_void_p(a.data_ptr()) if a is not None else None
+            self._check(self.L.gosma_sma_batch(self.h, n, ptr(x0), int(max_iter), int(precision), ptr(x), ptr(f),
+                                               ptr(grad), ptr(iters), 1), "sma_batch")
+            return dict(x=x, f=f, grad=grad, iters=iters)
+        x0 = _f64(x0, (-1, 6))
+        n = x0.shape[0]
+        xo, fo, it = np.empty((n, 6)), np.empty(n), np.empty(n, dtype=np.int32)
+        go = np.empty((n, 6)) if with_grad else None
+        self._check(self.L.gosma_sma_batch(self.h, n, x0.ctypes.data, int(max_iter), int(precision), xo.ctypes.data,
+                                           fo.ctypes.data, go.ctypes.data if with_grad else None, it.ctypes.data, 0),
+                    "sma_batch")
+        return dict(x=xo, f=fo, grad=go, iters=it)
 
     # ---------------------------------------------------------------- branch-and-bound
     @staticmethod

@@ -3,6 +3,7 @@
     python -m paper_1812_01232_gb300.profile_cases stress --cubes 4096 --reps 2
     python -m paper_1812_01232_gb300.profile_cases mlp --steps 4
     python -m paper_1812_01232_gb300.profile_cases batch --problems 64 --max-nodes 100000
+    python -m paper_1812_01232_gb300.profile_cases sma --seeds 1216 --precision 32
 
 stress  Theorem 1 bounds of `cubes` sub-cubes of the 2048 x 512 stress problem
         (device buffers), `reps` launches of the bound kernel.
@@ -10,6 +11,9 @@ mlp     `steps` training steps of the queue-ordering network on 65,536 random
         rows (batch 4,096): forward, backward and Adam on the tensor cores.
 batch   one batched solve of `problems` uneven problems (tiny generator,
         n1 ~ U{16..256}, n2 ~ U{8..128}) with a per-problem node limit.
+sma     SMA from `seeds` seed poses of the 128 x 64 paper-scale problem
+        (half near the true pose, half uniform over the domain), `reps`
+        launches of the batched refinement at the given precision.
 Each prints one line of timing so that the plain run can be compared.
 """
 from __future__ import annotations
@@ -73,6 +77,26 @@ def batch(a):
         len(res), dt, res[0]["iteration_ms"] / 1e3, pairs / (res[0]["iteration_ms"] / 1e3), res[0]["block_size"]))
 
 
+def sma(a):
+    import torch
+    prob = synth.paper_scale_problem(7)
+    ctx = Gosma(0)
+    ctx.set_problem(prob)
+    xs = torch.from_numpy(synth.pose_seeds(prob, a.seeds, 8)).cuda()
+    xo = torch.empty_like(xs)
+    f = torch.empty(a.seeds, dtype=torch.float64, device="cuda")
+    it = torch.empty(a.seeds, dtype=torch.int32, device="cuda")
+    ctx.sma_batch(xs, 100, a.precision, xo, f, None, it)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(a.reps):
+        ctx.sma_batch(xs, 100, a.precision, xo, f, None, it)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / a.reps
+    print("sma: %d seeds, precision %d, %.3f ms per call, %.0f seeds/s, median iterations %d" % (
+        a.seeds, a.precision, 1e3 * dt, a.seeds / dt, int(it.median().item())))
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     sub = ap.add_subparsers(dest="case", required=True)
@@ -84,8 +108,12 @@ def main(argv=None):
     b = sub.add_parser("batch")
     b.add_argument("--problems", type=int, default=64)
     b.add_argument("--max-nodes", type=int, default=100000)
+    q = sub.add_parser("sma")
+    q.add_argument("--seeds", type=int, default=1216)
+    q.add_argument("--precision", type=int, default=32)
+    q.add_argument("--reps", type=int, default=2)
     a = ap.parse_args(argv)
-    {"stress": stress, "mlp": mlp, "batch": batch}[a.case](a)
+    {"stress": stress, "mlp": mlp, "batch": batch, "sma": sma}[a.case](a)
     return 0
 
 

@@ -239,6 +239,21 @@ def stress_problem(seed: int, n1: int = 2048, n2: int = 512, antipodal_frac: flo
                 R_gt=R, r_gt=r, t_gt=t_gt)
 
 
+def pose_seeds(prob, n: int, seed: int):
+    """n seed poses (r then t) for local refinement: every other one near the
+    true pose (r, t perturbed by N(0, 0.1^2) per coordinate), the rest with
+    r uniform in the pi-ball and t uniform over the translation domain."""
+    rng = np.random.default_rng(seed)
+    r = rng.normal(size=(n, 3))
+    r /= np.linalg.norm(r, axis=1)[:, None]
+    r *= (np.pi * rng.random(n) ** (1 / 3))[:, None]
+    t = rng.uniform(prob["t_lo"], prob["t_hi"], (n, 3))
+    near = np.arange(n) % 2 == 0
+    r[near] = prob["r_gt"] + rng.normal(scale=0.1, size=(int(near.sum()), 3))
+    t[near] = prob["t_gt"] + rng.normal(scale=0.1, size=(int(near.sum()), 3))
+    return np.hstack([r, t])
+
+
 def root_cube(t_lo, t_hi):
     t_lo = np.asarray(t_lo, dtype=np.float64)
     t_hi = np.asarray(t_hi, dtype=np.float64)
