@@ -207,7 +207,9 @@ int gosma_eval_objective_grad_noalloc(gosma_ctx *ctx, int count, const double *d
  * than 2^-26 times the sum of the terms' magnitudes or 20 halvings of the
  * step find no decrease; the returned f is still FP64.
  * Outputs: x (count x 6, may alias x0) the refined poses; f (count) the FP64
- * objective at x, +inf for an infeasible seed (whose x is the seed); grad
+ * objective at x, +inf for an infeasible seed (whose x is the seed).  f is
+ * evaluated in FP64 at the refined pose and at the seed, and the better of
+ * the two is returned, so f never exceeds the seed's f; grad
  * (count x 6 or NULL) the FP64 gradient at x (0 for infeasible seeds); iters
  * (count or NULL) the accepted iterations per seed, -1 for infeasible seeds.
  * on_device = 0: host pointers, the call returns with the results in place.

@@ -34,7 +34,6 @@
 #include <vector>
 
 #include "bnb_common.cuh"
-#include "lbfgs.h"
 
 namespace gosma {
 
@@ -645,44 +644,6 @@ static int compact(gosma_ctx *ctx, BnbState *s, unsigned long long tail, unsigne
     return GOSMA_OK;
 }
 
-// ---------------------------------------------------------------- SMA (Sec. 5)
-// Local refinement of the incumbent: the L-BFGS machine of lbfgs.h driven
-// with one device evaluation of the FP64 objective and gradient per step.
-struct Refiner {
-    gosma_ctx *ctx;
-    long long evals = 0;
-    Feasibility feas() const {
-        Feasibility F;
-        for (int k = 0; k < 3; ++k) {
-            F.t_lo[k] = ctx->t_lo[k];
-            F.t_hi[k] = ctx->t_hi[k];
-        }
-        F.zeta = ctx->zeta;
-        F.mu1 = ctx->h_mu1.data();
-        F.n1 = ctx->n1;
-        return F;
-    }
-    int fg(const double x[6], double *f, double g[6]) {
-        ++evals;
-        return objective_grad_device(ctx, 1, x, f, g);
-    }
-    // Minimise from x (in place); f holds f(x) on entry and the result on exit.
-    int run(double x[6], double *f, int max_iter) {
-        Lbfgs L;
-        L.feas = feas();
-        L.start(x, max_iter);
-        double p[6], fv, gv[6];
-        while (L.want(p)) {
-            int rc = fg(p, &fv, gv);
-            if (rc) return rc;
-            L.give(fv, gv);
-        }
-        memcpy(x, L.x, sizeof(double) * 6);
-        *f = L.fx;
-        return GOSMA_OK;
-    }
-};
-
 static void rodrigues_host(const double r[3], double R[9]) {
     double th2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2], th = sqrt(th2), A, B;
     if (th < 1e-8) {
@@ -836,7 +797,6 @@ extern "C" int gosma_bnb_step(gosma_ctx *ctx, int max_iters, gosma_result *out) 
     auto seconds = [&]() {
         return base_seconds + std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     };
-    Refiner ref{ctx};
     cudaError_t e;
     int rc;
     for (int it = 0; (max_iters <= 0 || it < max_iters) && v.status == GOSMA_RUNNING; ++it) {
@@ -895,24 +855,17 @@ extern "C" int gosma_bnb_step(gosma_ctx *ctx, int max_iters, gosma_result *out) 
         v.live = v.live - np + h.appended;
         if ((long long)v.live > v.peak) v.peak = (long long)v.live;
         if (h.best_child >= 0 && h.best_ub < v.dstar) {
-            // the FP32 upper bound beat d*: evaluate f exactly, then refine (SMA)
+            // the FP32 upper bound beat d*: refine from the sub-cube's centre on
+            // the device (SMA) and take the exact FP64 f of the better of the
+            // centre and the refined pose
             CubeGeom g;
             decode(h.best_node, v.dom, g);
             double x[6] = {g.r0[0], g.r0[1], g.r0[2], g.t0[0], g.t0[1], g.t0[2]};
-            double f0 = 0, g6[6];
-            rc = ref.fg(x, &f0, g6);
+            double f1 = INFINITY, x1[6];
+            int its = 0;
+            rc = gosma_sma_batch(ctx, 1, x, v.o.use_sma ? v.o.sma_max_iter : 0, 32, x1, &f1, nullptr, &its, 0);
             if (rc) return rc;
-            double f1 = f0, x1[6];
-            memcpy(x1, x, sizeof x);
-            if (v.o.use_sma) {
-                rc = ref.run(x1, &f1, v.o.sma_max_iter);
-                if (rc) return rc;
-                ++v.sma_calls;
-                if (!(f1 < f0)) {
-                    f1 = f0;
-                    memcpy(x1, x, sizeof x);
-                }
-            }
+            if (v.o.use_sma) ++v.sma_calls;
             if (f1 < v.dstar) {
                 v.dstar = f1;
                 memcpy(v.best, x1, sizeof x1);

@@ -40,6 +40,12 @@ struct MixDev {
     const int *rj0, *rj1, *rm1;
 };
 
+// Feasible translations of a refinement (Sec. 4.1): inside [t_lo, t_hi] and
+// at least sqrt(zeta2) from every model mean.
+struct SmaBox {
+    double t_lo[3], t_hi[3], zeta2;
+};
+
 // One sub-cube decoded to FP64 geometry.
 struct CubeGeom {
     double r0[3], rhw, t0[3], thw[3];
@@ -189,5 +195,10 @@ int bounds_block_size(int n1, int n2);
 
 // objective.cu
 int objective_grad_device(gosma_ctx *ctx, int count, const double *h_x, double *h_f, double *h_g);
+
+// sma.cu: FP32-search SMA of count device seeds, seed s on problem d_pid[s]
+int sma_refine_many(gosma_ctx *ctx, cudaStream_t st, const MixDev *d_mixes, const SmaBox *d_boxes, const int *d_pid,
+                    int max_n1, int max_n2, int count, const double *d_x0, int max_iter, double *d_x, int *d_it,
+                    int *d_counter, long long *launches);
 void bnb_release(gosma_ctx *ctx);
 }  // namespace gosma

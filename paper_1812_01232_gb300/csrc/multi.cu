@@ -43,7 +43,6 @@
 
 #include "bnb_common.cuh"
 #include "classes.h"
-#include "lbfgs.h"
 #include "mlp.cuh"
 #include "objective_core.cuh"
 
@@ -1027,29 +1026,30 @@ static int validate_problem(gosma_ctx *ctx, const gosma_problem &p, int k) {
 
 int setup_constants_mix(gosma_ctx *ctx, cudaStream_t st, const MixDev &mx, double *c22_out);
 
-// Lock-step L-BFGS for every unfinished problem whose d* improved since its
-// last refinement: each round evaluates the pending pose of every such
-// problem in one batched FP64 launch; improvements go back through mp_apply.
+// SMA (Sec. 5) for every unfinished problem whose d* improved since its last
+// refinement: one device launch refines all their incumbents at once (FP32
+// search, sma.cu), then one batched FP64 evaluation gives f at the refined
+// poses; improvements go back through mp_apply.
 struct BatchRefiner {
     gosma_ctx *ctx = nullptr;
     cudaStream_t st = nullptr;
-    int nprob = 0, nblk = 0, max_n1 = 0, max_iter = 100;
+    int nprob = 0, nblk = 0, max_n1 = 0, max_n2 = 0, max_iter = 100;
     ManyMix mm{};
-    double *d_x = nullptr, *d_ri = nullptr, *d_part = nullptr, *d_out = nullptr;
-    int *d_pid = nullptr;
+    MixDev *d_mixes = nullptr;
+    SmaBox *d_boxes = nullptr;
+    double *d_x = nullptr, *d_xo = nullptr, *d_ri = nullptr, *d_part = nullptr, *d_out = nullptr;
+    int *d_pid = nullptr, *d_it = nullptr, *d_counter = nullptr;
     long long *d_row = nullptr;
     Incumbent *d_upd = nullptr;
     void *h_pin = nullptr;
     double *hx = nullptr, *hout = nullptr;
-    int *hpid = nullptr;
+    int *hpid = nullptr, *hit = nullptr;
     long long *hrow = nullptr;
     Incumbent *hupd = nullptr;
-    std::vector<Lbfgs> L;
-    std::vector<Feasibility> F;
     std::vector<int> n1;
     std::vector<double> refined_f;
     std::vector<long long> calls;
-    std::vector<int> act, who;
+    std::vector<int> act;
 
     ~BatchRefiner() {
         if (h_pin) cudaFreeHost(h_pin);
@@ -1057,37 +1057,36 @@ struct BatchRefiner {
 
     cudaError_t init(MultiBuffers &B, const std::vector<ProbDev> &hp, const gosma_problem *probs, long long sum_n1) {
         n1.resize(nprob);
-        F.resize(nprob);
-        L.resize(nprob);
         refined_f.assign(nprob, INFINITY);
         calls.assign(nprob, 0);
         long long max_total = 0;
         std::vector<MixDev> mixes(nprob);
+        std::vector<SmaBox> boxes(nprob);
         for (int k = 0; k < nprob; ++k) {
             const gosma_problem &p = probs[k];
             n1[k] = p.n1;
             max_n1 = std::max(max_n1, p.n1);
+            max_n2 = std::max(max_n2, p.n2);
             max_total = std::max(max_total, (long long)p.n1 * p.n1 + (long long)p.n1 * p.n2);
             for (int a = 0; a < 3; ++a) {
-                F[k].t_lo[a] = p.t_lo[a];
-                F[k].t_hi[a] = p.t_hi[a];
+                boxes[k].t_lo[a] = p.t_lo[a];
+                boxes[k].t_hi[a] = p.t_hi[a];
             }
-            F[k].zeta = p.zeta;
-            F[k].mu1 = p.mu1;
-            F[k].n1 = p.n1;
+            boxes[k].zeta2 = p.zeta * p.zeta;
             mixes[k] = hp[k].mx;
         }
         nblk = (int)((max_total + OBJ_CHUNK - 1) / OBJ_CHUNK);
-        MixDev *d_mixes = nullptr;
         cudaError_t e;
-        if ((e = B.get(&d_mixes, nprob)) != cudaSuccess || (e = B.get(&d_x, 6 * (size_t)nprob)) != cudaSuccess ||
+        if ((e = B.get(&d_mixes, nprob)) != cudaSuccess || (e = B.get(&d_boxes, nprob)) != cudaSuccess ||
+            (e = B.get(&d_x, 6 * (size_t)nprob)) != cudaSuccess || (e = B.get(&d_xo, 6 * (size_t)nprob)) != cudaSuccess ||
             (e = B.get(&d_ri, OBJ_STRIDE * (size_t)sum_n1)) != cudaSuccess ||
             (e = B.get(&d_part, 7 * (size_t)nblk * nprob)) != cudaSuccess ||
             (e = B.get(&d_out, 7 * (size_t)nprob)) != cudaSuccess || (e = B.get(&d_pid, nprob)) != cudaSuccess ||
+            (e = B.get(&d_it, nprob)) != cudaSuccess || (e = B.get(&d_counter, 1)) != cudaSuccess ||
             (e = B.get(&d_row, nprob)) != cudaSuccess || (e = B.get(&d_upd, nprob)) != cudaSuccess)
             return e;
         const size_t n = (size_t)nprob;
-        const size_t bytes = n * (sizeof(double) * 13 + sizeof(long long) + sizeof(int) + sizeof(Incumbent)) + 64;
+        const size_t bytes = n * (sizeof(double) * 13 + sizeof(long long) + 2 * sizeof(int) + sizeof(Incumbent)) + 64;
         if ((e = cudaMallocHost(&h_pin, bytes)) != cudaSuccess) return e;
         char *c = (char *)h_pin;
         hupd = (Incumbent *)c;
@@ -1095,64 +1094,65 @@ struct BatchRefiner {
         hout = hx + 6 * n;
         hrow = (long long *)(hout + 7 * n);
         hpid = (int *)(hrow + n);
+        hit = hpid + n;
         mm.mixes = d_mixes;
         mm.pid = d_pid;
         mm.row = d_row;
-        return cudaMemcpyAsync(d_mixes, mixes.data(), sizeof(MixDev) * nprob, cudaMemcpyHostToDevice, st);
+        e = cudaMemcpyAsync(d_mixes, mixes.data(), sizeof(MixDev) * nprob, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d_boxes, boxes.data(), sizeof(SmaBox) * nprob, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host vectors go out of scope
+        return e;
     }
 
     // One refinement wave over a host snapshot hs of the problem states: the
     // improved incumbents are appended to out (and written into hs).
     cudaError_t wave(ProbState *hs, std::vector<Incumbent> &out) {
         act.clear();
+        if (stop_flag && stop_flag->load()) return cudaSuccess;
+        long long rows = 0;
         for (int k = 0; k < nprob; ++k)
             if (!hs[k].done && hs[k].dstar < refined_f[k]) {
-                L[k].feas = F[k];
-                L[k].start(hs[k].best_x, max_iter);
-                act.push_back(k);
-                ++calls[k];
-            }
-        if (act.empty()) return cudaSuccess;
-        cudaError_t e = cudaSuccess;
-        for (;;) {
-            if (stop_flag && stop_flag->load()) break;
-            who.clear();
-            long long rows = 0;
-            for (int k : act) {
-                const int q = (int)who.size();
-                if (!L[k].want(hx + 6 * q)) continue;
+                const int q = (int)act.size();
+                memcpy(hx + 6 * q, hs[k].best_x, sizeof(double) * 6);
                 hpid[q] = k;
                 hrow[q] = rows;
                 rows += n1[k];
-                who.push_back(k);
+                act.push_back(k);
+                ++calls[k];
             }
-            const int cnt = (int)who.size();
-            if (!cnt) break;
-            e = cudaMemcpyAsync(d_x, hx, sizeof(double) * 6 * cnt, cudaMemcpyHostToDevice, st);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(d_pid, hpid, sizeof(int) * cnt, cudaMemcpyHostToDevice, st);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(d_row, hrow, sizeof(long long) * cnt, cudaMemcpyHostToDevice, st);
-            if (e != cudaSuccess) return e;
-            obj_prep<<<dim3((max_n1 + 127) / 128, cnt), 128, 0, st>>>(mm, d_x, d_ri);
-            obj_pairs<<<dim3(nblk, cnt), OBJ_BLOCK, 0, st>>>(mm, d_x, d_ri, d_part, nblk);
-            obj_final<<<(cnt + OBJ_FINAL_WARPS - 1) / OBJ_FINAL_WARPS, 32 * OBJ_FINAL_WARPS, 0, st>>>(cnt, d_x, d_part, nblk, d_out);
-            launches += 3;
-            e = cudaGetLastError();
-            if (e == cudaSuccess) e = cudaMemcpyAsync(hout, d_out, sizeof(double) * 7 * cnt, cudaMemcpyDeviceToHost, st);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-            if (e != cudaSuccess) return e;
-            for (int q = 0; q < cnt; ++q) L[who[q]].give(hout[7 * q], hout + 7 * q + 1);
-        }
-        for (int k : act) {
-            const Lbfgs &l = L[k];
-            if (l.fx < hs[k].dstar) {
+        const int cnt = (int)act.size();
+        if (!cnt) return cudaSuccess;
+        cudaError_t e = cudaMemcpyAsync(d_x, hx, sizeof(double) * 6 * cnt, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_pid, hpid, sizeof(int) * cnt, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_row, hrow, sizeof(long long) * cnt, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return e;
+        if (sma_refine_many(ctx, st, d_mixes, d_boxes, d_pid, max_n1, max_n2, cnt, d_x, max_iter, d_xo, d_it,
+                            d_counter, &launches))
+            return cudaErrorLaunchFailure;
+        obj_prep<<<dim3((max_n1 + 127) / 128, cnt), 128, 0, st>>>(mm, d_xo, d_ri);
+        obj_pairs<<<dim3(nblk, cnt), OBJ_BLOCK, 0, st>>>(mm, d_xo, d_ri, d_part, nblk);
+        obj_final<<<(cnt + OBJ_FINAL_WARPS - 1) / OBJ_FINAL_WARPS, 32 * OBJ_FINAL_WARPS, 0, st>>>(cnt, d_xo, d_part, nblk, d_out);
+        launches += 3;
+        e = cudaGetLastError();
+        // hx is read by the upload above before these downloads overwrite it (stream order)
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hout, d_out, sizeof(double) * 7 * cnt, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hx, d_xo, sizeof(double) * 6 * cnt, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hit, d_it, sizeof(int) * cnt, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return e;
+        for (int q = 0; q < cnt; ++q) {
+            const int k = act[q];
+            const double f = hout[7 * q];
+            if (hit[q] >= 0 && f < hs[k].dstar) {
                 Incumbent u;
-                u.f = l.fx;
-                memcpy(u.x, l.x, sizeof u.x);
+                u.f = f;
+                memcpy(u.x, hx + 6 * q, sizeof u.x);
                 u.k = k;
                 u.pad = 0;
                 out.push_back(u);
-                hs[k].dstar = l.fx;
-                memcpy(hs[k].best_x, l.x, sizeof u.x);
+                hs[k].dstar = f;
+                memcpy(hs[k].best_x, u.x, sizeof u.x);
             }
             refined_f[k] = hs[k].dstar;
         }

@@ -26,10 +26,6 @@ namespace gosma {
 constexpr int SMA_BLOCK = 128;
 constexpr int SMA_M = 8;  // L-BFGS memory
 
-struct SmaBox {
-    double t_lo[3], t_hi[3], zeta2;
-};
-
 // L-BFGS state of the block's current seed (shared memory; thread 0 writes).
 struct SmaState {
     double x[6], g[6], f, fmag;    // iterate, gradient, f, sum of |terms|
@@ -442,15 +438,36 @@ __device__ __forceinline__ int sma_next(int *counter, int *slot) {
     return *slot;
 }
 
+// Seeds over one mixture and domain.
+struct SmaOne {
+    MixDev mx;
+    SmaBox box;
+    __device__ int problem(int) const { return 0; }
+    __device__ const MixDev &mix(int) const { return mx; }
+    __device__ const SmaBox &dom(int) const { return box; }
+};
+// Seed s belongs to problem pid[s] with its own mixtures and domain.
+struct SmaMany {
+    const MixDev *mixes;
+    const SmaBox *boxes;
+    const int *pid;
+    __device__ int problem(int s) const { return pid[s]; }
+    __device__ const MixDev &mix(int s) const { return mixes[pid[s]]; }
+    __device__ const SmaBox &dom(int s) const { return boxes[pid[s]]; }
+};
+
 // iters[s] = L-BFGS iterations taken (-1: infeasible seed, x = seed).
 // Every loop is bounded: at most max_iter iterations of at most `halvings`
-// trial poses each.
-template <bool F64>
-__global__ void __launch_bounds__(SMA_BLOCK) sma_kernel(MixDev mx, SmaBox box, int count, const double *__restrict__ x0,
-                                                        int max_iter, double *__restrict__ xout, int *__restrict__ iters,
-                                                        double *__restrict__ rows64, int *__restrict__ counter) {
+// trial poses each.  The dynamic shared memory holds the FP32 tables of the
+// largest mixture (FP32 search); rows64 one FP64 table per block (FP64).
+template <bool F64, class Src>
+__global__ void __launch_bounds__(SMA_BLOCK) sma_kernel(Src src, int count, const double *__restrict__ x0, int max_iter,
+                                                        double *__restrict__ xout, int *__restrict__ iters,
+                                                        double *__restrict__ rows64, int max_n1, int *__restrict__ counter) {
     extern __shared__ float4 sma_smem[];
     __shared__ SmaState st;
+    __shared__ MixDev mx;
+    __shared__ SmaBox box;
     __shared__ double fg[7];
     __shared__ int slot;
     __shared__ float red32[9][SMA_BLOCK / 32];
@@ -458,15 +475,8 @@ __global__ void __launch_bounds__(SMA_BLOCK) sma_kernel(MixDev mx, SmaBox box, i
     const int tid = threadIdx.x;
     constexpr int halvings = F64 ? 40 : 20;
     Sma32Tab tb;
-    double *rows = nullptr;
-    if (F64) {
-        rows = rows64 + (size_t)blockIdx.x * mx.n1 * OBJ_STRIDE;
-    } else {
-        tb = sma32_carve(sma_smem, mx.n1, mx.n2);
-        for (int i = tid; i < mx.n1; i += SMA_BLOCK) tb.phi1[i] = mx.phi1f[i];
-        for (int j = tid; j < mx.n2; j += SMA_BLOCK)
-            tb.jb[j] = make_float2(phiz32((float)mx.kappa2d[j]), (float)mx.phi2d[j]);
-    }
+    double *rows = F64 ? rows64 + (size_t)blockIdx.x * max_n1 * OBJ_STRIDE : nullptr;
+    int loaded = -1;  // problem whose constant tables are in shared memory
     // f and gradient at st.x (trial = false) or st.xn (trial = true)
     auto eval = [&](bool trial) {
         double mag = 0.0;
@@ -487,6 +497,21 @@ __global__ void __launch_bounds__(SMA_BLOCK) sma_kernel(MixDev mx, SmaBox box, i
         __syncthreads();
     };
     for (int s = sma_next(counter, &slot); s < count; s = sma_next(counter, &slot)) {
+        const int prob = src.problem(s);
+        if (prob != loaded) {  // uniform: every thread read the same slot
+            if (tid == 0) {
+                mx = src.mix(s);
+                box = src.dom(s);
+            }
+            __syncthreads();
+            if (!F64) {
+                tb = sma32_carve(sma_smem, mx.n1, mx.n2);
+                for (int i = tid; i < mx.n1; i += SMA_BLOCK) tb.phi1[i] = mx.phi1f[i];
+                for (int j = tid; j < mx.n2; j += SMA_BLOCK)
+                    tb.jb[j] = make_float2(phiz32((float)mx.kappa2d[j]), (float)mx.phi2d[j]);
+            }
+            loaded = prob;
+        }
         if (tid < 6) st.x[tid] = x0[6 * s + tid];
         if (tid == 0) st.head = st.used = 0;
         __syncthreads();
@@ -585,21 +610,23 @@ __global__ void objf_reduce(int count, const double *__restrict__ part, int nblk
     if (lane == 0) fsum[p] = v;
 }
 
-// Outputs: f (FP64, +inf for infeasible seeds) from the f-only sums fsum
-// (grad == NULL) or from the full objective records rec (count x 7).
-__global__ void sma_outputs(int count, const int *__restrict__ iters, const double *__restrict__ fsum,
-                            const double *__restrict__ rec, double *__restrict__ f, double *__restrict__ grad) {
+// Outputs from the FP64 records of the 2 count poses xs = [refined; seeds]:
+// per seed the better of the two (the refined pose on a tie), so f never
+// exceeds the seed's f; +inf and the seed for infeasible seeds.  The records
+// are f alone (fsum, grad == NULL) or f and gradient (rec, 7 per pose).
+__global__ void sma_outputs(int count, const int *__restrict__ iters, const double *__restrict__ xs,
+                            const double *__restrict__ fsum, const double *__restrict__ rec, double *__restrict__ x,
+                            double *__restrict__ f, double *__restrict__ grad) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= count) return;
     const bool ok = iters[s] >= 0;
-    double v;
-    if (rec) {
-        v = rec[7 * (size_t)s];
-        for (int k = 0; k < 6; ++k) grad[6 * (size_t)s + k] = ok ? rec[7 * (size_t)s + 1 + k] : 0.0;
-    } else {
-        v = fsum[s];
-    }
-    f[s] = ok ? v : INFINITY;
+    const size_t a = s, b = (size_t)count + s;  // refined, seed
+    const double fa = rec ? rec[7 * a] : fsum[a], fb = rec ? rec[7 * b] : fsum[b];
+    const size_t c = ok && fa <= fb ? a : b;
+    for (int k = 0; k < 6; ++k) x[6 * (size_t)s + k] = xs[6 * c + k];
+    f[s] = ok ? (c == a ? fa : fb) : INFINITY;
+    if (grad)
+        for (int k = 0; k < 6; ++k) grad[6 * (size_t)s + k] = ok ? rec[7 * c + 1 + k] : 0.0;
 }
 
 // FP64 records of count device poses: f alone into fsum (count) when rec is
@@ -630,6 +657,54 @@ static int objective_records(gosma_ctx *ctx, int count, const double *d_x, doubl
     return e == cudaSuccess ? GOSMA_OK : cuda_fail(ctx, e, "launch(objective records)");
 }
 
+// Dynamic shared memory and persistent grid of the SMA kernel.
+template <bool F64, class Src>
+static int sma_config(gosma_ctx *ctx, int max_n1, int max_n2, int count, int *grid, size_t *smem) {
+    *smem = F64 ? 0 : sma32_smem_bytes(max_n1, max_n2);
+    auto kern = sma_kernel<F64, Src>;
+    if (*smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, GOSMA_EINVAL, "sma: mixtures too large for one block's shared memory");
+        }
+    }
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SMA_BLOCK, *smem);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "occupancy(sma)");
+    if (per_sm < 1) return fail(ctx, GOSMA_EINVAL, "sma: mixtures too large for one block's shared memory");
+    long long g = (long long)ctx->sm_count * per_sm;
+    *grid = (int)(g < count ? g : count);
+    return GOSMA_OK;
+}
+
+template <bool F64, class Src>
+static int sma_run(gosma_ctx *ctx, cudaStream_t st, const Src &src, int grid, size_t smem, int count,
+                   const double *d_x0, int max_iter, double *d_x, int *d_it, double *d_rows, int max_n1,
+                   int *d_counter, long long *launches) {
+    cudaError_t e = cudaMemsetAsync(d_counter, 0, sizeof(int), st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "memset(sma counter)");
+    sma_kernel<F64, Src><<<grid, SMA_BLOCK, smem, st>>>(src, count, d_x0, max_iter, d_x, d_it, d_rows, max_n1,
+                                                        d_counter);
+    ++*launches;
+    e = cudaGetLastError();
+    return e == cudaSuccess ? GOSMA_OK : cuda_fail(ctx, e, "launch(sma)");
+}
+
+// FP32-search SMA of count seeds, seed s on problem d_pid[s] (the batched
+// solver's refinement); asynchronous on st.
+int sma_refine_many(gosma_ctx *ctx, cudaStream_t st, const MixDev *d_mixes, const SmaBox *d_boxes, const int *d_pid,
+                    int max_n1, int max_n2, int count, const double *d_x0, int max_iter, double *d_x, int *d_it,
+                    int *d_counter, long long *launches) {
+    if (count <= 0) return GOSMA_OK;
+    int grid = 0;
+    size_t smem = 0;
+    int rc = sma_config<false, SmaMany>(ctx, max_n1, max_n2, count, &grid, &smem);
+    if (rc) return rc;
+    return sma_run<false, SmaMany>(ctx, st, SmaMany{d_mixes, d_boxes, d_pid}, grid, smem, count, d_x0, max_iter, d_x,
+                                   d_it, nullptr, max_n1, d_counter, launches);
+}
+
 }  // namespace gosma
 
 extern "C" int gosma_sma_batch(gosma_ctx *ctx, int count, const double *x0, int max_iter, int precision, double *x,
@@ -647,18 +722,11 @@ extern "C" int gosma_sma_batch(gosma_ctx *ctx, int count, const double *x0, int 
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
     const bool f64 = precision == 64;
     const int n1 = ctx->n1, n2 = ctx->n2;
-    const size_t smem = f64 ? 0 : sma32_smem_bytes(n1, n2);
-    auto kern = f64 ? sma_kernel<true> : sma_kernel<false>;
-    if (smem > 48 * 1024) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return fail(ctx, GOSMA_EINVAL, "sma_batch: mixtures too large for one block's shared memory");
-    }
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SMA_BLOCK, smem);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "occupancy(sma)");
-    if (per_sm < 1) return fail(ctx, GOSMA_EINVAL, "sma_batch: mixtures too large for one block's shared memory");
-    long long grid = (long long)ctx->sm_count * per_sm;
-    if (grid > count) grid = count;
+    int grid = 0;
+    size_t smem = 0;
+    int rc = f64 ? sma_config<true, SmaOne>(ctx, n1, n2, count, &grid, &smem)
+                 : sma_config<false, SmaOne>(ctx, n1, n2, count, &grid, &smem);
+    if (rc) return rc;
 
     // device scratch: seeds and poses (host calls), iterations, counter,
     // FP64 rows (one table per block), objective records (f alone when no
@@ -668,19 +736,20 @@ extern "C" int gosma_sma_batch(gosma_ctx *ctx, int count, const double *x0, int 
     const size_t per_pose = sizeof(double) * ((size_t)OBJ_STRIDE * n1 + 7 * (size_t)nblk);
     int chunk = (int)((64u << 20) / per_pose);
     if (chunk < 1) chunk = 1;
-    if (chunk > count) chunk = count;
+    if (chunk > 2 * count) chunk = 2 * count;
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
     const size_t b_x0 = on_device ? 0 : al(sizeof(double) * 6 * (size_t)count);
     const size_t b_x = on_device ? 0 : al(sizeof(double) * 6 * (size_t)count);
     const size_t b_f = on_device ? 0 : al(sizeof(double) * (size_t)count);
     const size_t b_g = on_device || !grad ? 0 : al(sizeof(double) * 6 * (size_t)count);
+    const size_t b_xs = al(sizeof(double) * 12 * (size_t)count);
     const size_t b_it = al(sizeof(int) * (size_t)count) + 256;
     const size_t b_rows = f64 ? al(sizeof(double) * OBJ_STRIDE * (size_t)n1 * grid) : 0;
-    const size_t b_rec = grad ? al(sizeof(double) * 7 * (size_t)count) : 0;
-    const size_t b_part = grad ? 0 : al(sizeof(double) * (size_t)count);
+    const size_t b_rec = grad ? al(sizeof(double) * 14 * (size_t)count) : 0;
+    const size_t b_part = grad ? 0 : al(sizeof(double) * 2 * (size_t)count);
     const size_t b_lz = al(sizeof(double) * (size_t)n2);
     const size_t b_scr = al(per_pose * (size_t)chunk);
-    const size_t need = b_x0 + b_x + b_f + b_g + b_it + b_rows + b_rec + b_part + b_lz + b_scr;
+    const size_t need = b_x0 + b_x + b_f + b_g + b_xs + b_it + b_rows + b_rec + b_part + b_lz + b_scr;
     if (need > ctx->sma_bytes) {
         if (ctx->d_sma) cudaFree(ctx->d_sma);
         ctx->d_sma = nullptr;
@@ -698,6 +767,8 @@ extern "C" int gosma_sma_batch(gosma_ctx *ctx, int count, const double *x0, int 
     p += b_f;
     double *d_g = on_device ? grad : (grad ? (double *)p : nullptr);
     p += b_g;
+    double *d_xs = (double *)p;  // refined poses, then the seeds
+    p += b_xs;
     int *d_it = (int *)p;
     int *d_counter = (int *)(p + al(sizeof(int) * (size_t)count));
     p += b_it;
@@ -716,25 +787,28 @@ extern "C" int gosma_sma_batch(gosma_ctx *ctx, int count, const double *x0, int 
         e = cudaMemcpyAsync(d_x0, x0, sizeof(double) * 6 * (size_t)count, cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "copy seeds");
     }
-    e = cudaMemsetAsync(d_counter, 0, sizeof(int), st);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "memset(sma counter)");
-    SmaBox box;
+    SmaOne one;
+    one.mx = ctx->mix;
     for (int k = 0; k < 3; ++k) {
-        box.t_lo[k] = ctx->t_lo[k];
-        box.t_hi[k] = ctx->t_hi[k];
+        one.box.t_lo[k] = ctx->t_lo[k];
+        one.box.t_hi[k] = ctx->t_hi[k];
     }
-    box.zeta2 = ctx->zeta * ctx->zeta;
-    kern<<<(int)grid, SMA_BLOCK, smem, st>>>(ctx->mix, box, count, d_x0, max_iter, d_x, d_it, d_rows, d_counter);
-    ++ctx->launches;
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "launch(sma)");
+    one.box.zeta2 = ctx->zeta * ctx->zeta;
+    e = cudaMemcpyAsync(d_xs + 6 * (size_t)count, d_x0, sizeof(double) * 6 * (size_t)count, cudaMemcpyDeviceToDevice,
+                        st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "copy seeds");
+    rc = f64 ? sma_run<true>(ctx, st, one, grid, smem, count, d_x0, max_iter, d_xs, d_it, d_rows, n1, d_counter,
+                             &ctx->launches)
+             : sma_run<false>(ctx, st, one, grid, smem, count, d_x0, max_iter, d_xs, d_it, d_rows, n1, d_counter,
+                              &ctx->launches);
+    if (rc) return rc;
     if (!grad) {
         logz_table<<<(n2 + 127) / 128, 128, 0, st>>>(ctx->mix, d_lz);
         ++ctx->launches;
     }
-    int rc = objective_records(ctx, count, d_x, d_fsum, d_rec, d_lz, d_scr, chunk);
+    rc = objective_records(ctx, 2 * count, d_xs, d_fsum, d_rec, d_lz, d_scr, chunk);
     if (rc) return rc;
-    sma_outputs<<<(count + 127) / 128, 128, 0, st>>>(count, d_it, d_fsum, d_rec, d_f, d_g);
+    sma_outputs<<<(count + 127) / 128, 128, 0, st>>>(count, d_it, d_xs, d_fsum, d_rec, d_x, d_f, d_g);
     ++ctx->launches;
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "launch(sma outputs)");
