@@ -37,7 +37,12 @@ Two more measurements ride on the same line (rank 0, N = 1, unless
   to the certified optimum by the plain single-problem solver (one after the
   other), the plain batched solver and the learned batched solver (network
   weights from paper_1812_01232_gb300/weights, scoring during the first 32
-  iterations, where the incumbent is found), on the same problems.
+  iterations, where the incumbent is found), on the same problems;
+* "sma": the batched device refinement (SMA, Sec. 5) of many seed poses of
+  the 128 x 64 paper-scale problem (half near the true pose, half uniform),
+  seeds refined per second with the FP32 and the FP64 search (CUDA events
+  around the whole call, the FP64 f of the results included), beside the
+  oracle's L-BFGS on one host core.
 """
 from __future__ import annotations
 
@@ -341,6 +346,7 @@ def run_ours(args):
         ctx.close()
         line["batched"] = run_batched(args.batch_budget)
         line["time_to_certified"] = run_time_to_certified(8)
+        line["sma"] = run_sma()
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -368,6 +374,43 @@ def run_batched(budget_s):
             "p50_s": float(np.percentile(cert, 50)) if cert else None,
             "p99_s": float(np.percentile(cert, 99)) if cert else None,
             "block_size": res[0]["block_size"]}
+
+
+def run_sma():
+    """Seeds refined per second by gosma_sma_batch (see module doc)."""
+    import torch
+    from paper_1812_01232_gb300 import synth
+    from paper_1812_01232_gb300.gosma import Gosma
+    import oracle
+    prob = synth.paper_scale_problem(7)
+    ctx = Gosma(0)
+    ctx.set_problem(prob)
+    out = {"workload": "128 x 64 paper-scale problem, seeds half near the true pose, half uniform, up to 100 L-BFGS "
+                       "iterations each"}
+    for prec, n in ((32, 152 * 32), (64, 152 * 4)):
+        xs = torch.from_numpy(synth.pose_seeds(prob, n, 8)).cuda()
+        xo = torch.empty_like(xs)
+        f = torch.empty(n, dtype=torch.float64, device="cuda")
+        it = torch.empty(n, dtype=torch.int32, device="cuda")
+        ctx.sma_batch(xs[:152], 100, prec, xo[:152], f[:152], None, it[:152])  # warm-up
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        ctx.sma_batch(xs, 100, prec, xo, f, None, it)
+        e1.record()
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3
+        out["fp%d" % prec] = {"seeds": n, "seconds": sec, "seeds_per_s": n / sec,
+                              "median_iterations": int(it.median().item())}
+    ctx.close()
+    mix = oracle.Mixtures.from_problem(prob)
+    x0 = synth.pose_seeds(prob, 8, 8)
+    t0 = time.perf_counter()
+    for x in x0:
+        oracle.sma(mix, x, prob["t_lo"], prob["t_hi"], prob["zeta"], max_iter=100, memory=8, gtol=1e-10)
+    sec = time.perf_counter() - t0
+    out["oracle"] = {"seeds": len(x0), "seconds": sec, "seeds_per_s": len(x0) / sec, "cores": 1, "kind": "oracle"}
+    return out
 
 
 def run_time_to_certified(n_prob):
