@@ -1,4 +1,5 @@
-"""FP64 CPU oracle for GOSMA: ctypes binding of ``gosma_oracle.c``.
+"""FP64 CPU oracle for GOSMA: ctypes binding of ``gosma_oracle.c`` and
+``mixgen.c`` (mixture generation, Sec. 6).
 
 TEST INFRASTRUCTURE ONLY.  The test-suite, ``__graft_entry__.smoke()`` and
 the CPU-baseline leg of ``bench.py`` are the only callers.  The product
@@ -19,6 +20,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "gosma_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "mixgen.c")]
 _LIB = os.path.join(_HERE, "liboracle_gosma.so")
 _lock = threading.Lock()
 _lib = None
@@ -56,9 +58,9 @@ class BnbResult(C.Structure):
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (OpenMP when available)."""
     with _lock:
-        if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        if not force and os.path.exists(_LIB) and all(os.path.getmtime(_LIB) >= os.path.getmtime(f) for f in _SRCS):
             return _LIB
-        base = ["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", _SRC, "-o", _LIB + ".tmp", "-lm"]
+        base = ["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared"] + _SRCS + ["-o", _LIB + ".tmp", "-lm"]
         r = subprocess.run(base[:1] + ["-fopenmp"] + base[1:], capture_output=True, text=True)
         if r.returncode != 0:
             r = subprocess.run(base, capture_output=True, text=True)
@@ -109,6 +111,9 @@ def lib():
         L.om_sma.argtypes = [C.POINTER(Mix), C.POINTER(Domain), C.POINTER(SmaOpts), D, D, D]
         L.om_bnb.restype = C.c_int
         L.om_bnb.argtypes = [C.POINTER(Mix), C.POINTER(Domain), C.POINTER(BnbOpts), C.POINTER(BnbResult)]
+        L.om_dp_cluster.restype = C.c_int
+        L.om_dp_cluster.argtypes = [C.c_int, C.c_int, D, C.c_double, C.c_int, C.c_int, C.c_double, C.c_double, D, D, D,
+                                    C.POINTER(C.c_int), C.POINTER(C.c_int)]
         _lib = L
     return _lib
 
@@ -286,3 +291,26 @@ def bnb(mix: Mixtures, t_lo, t_hi, zeta, eps, pop=128, max_nodes=0, max_seconds=
         "nodes": res.nodes, "iterations": res.iterations, "sma_calls": res.sma_calls,
         "queue_peak": res.queue_peak, "seconds": res.seconds, "status": res.status,
     }
+
+
+def dp_cluster(x, lam, vmf=False, max_iter=100, kmax=1024, sigma_min=1e-3, kappa_max=1e5):
+    """Mixture generation (Sec. 6; mixgen.c): DP-means (vmf False, lam a
+    squared-distance penalty) or DP-vMF-means (vmf True, lam a cosine
+    threshold), then the maximum-likelihood GMM (sigma) or vMFMM (kappa).
+    Returns dict(k, mu, sigma | kappa, phi, labels, passes); k = -1 when
+    more than kmax clusters would be needed."""
+    x = _f64(x, (-1, 3))
+    n = len(x)
+    mu = np.zeros((kmax, 3))
+    spread = np.zeros(kmax)
+    phi = np.zeros(kmax)
+    labels = np.zeros(n, dtype=np.int32)
+    passes = C.c_int()
+    k = lib().om_dp_cluster(int(bool(vmf)), n, _p(x), float(lam), int(max_iter), int(kmax), float(sigma_min),
+                            float(kappa_max), _p(mu), _p(spread), _p(phi),
+                            labels.ctypes.data_as(C.POINTER(C.c_int)), C.byref(passes))
+    out = {"k": k, "labels": labels, "passes": passes.value}
+    if k > 0:
+        out.update(mu=mu[:k], phi=phi[:k])
+        out["kappa" if vmf else "sigma"] = spread[:k]
+    return out
