@@ -221,6 +221,43 @@ int gosma_eval_objective_grad_noalloc(gosma_ctx *ctx, int count, const double *d
 int gosma_sma_batch(gosma_ctx *ctx, int count, const double *x0, int max_iter, int precision, double *x, double *f,
                     double *grad, int *iters, int on_device);
 
+/* Mixture generation (Sec. 6): the model's point set is clustered with
+ * DP-means and a maximum-likelihood GMM is fitted to the clusters, the
+ * theta_1 of gosma_set_mixtures.  One pass visits the points in index order;
+ * a point whose squared distance to every current centre exceeds lambda
+ * opens a new cluster centred on itself (seen by the later points of the
+ * pass), every other point joins its nearest centre (lowest index on ties);
+ * after the pass each centre becomes its cluster's mean and empty clusters
+ * are removed, the others keeping their order.  Start: one cluster at the
+ * mean of all points; stop: a pass that changes no label, or max_iter
+ * passes.  Coordinates are first rounded to multiples of 2^-32 (of the
+ * input's unit), which makes every cluster sum exact; the result is
+ * deterministic and equals a serial double-precision run of the same steps.
+ * Fit: phi_k = n_k / n, mu_k the mean, sigma_k = sqrt(sum |x - mu_k|^2 /
+ * (3 n_k)) floored at sigma_min.
+ * x: n x 3 host array, n >= 1, n * max|x| < 2^30.  lambda > 0 (squared
+ * distance), max_iter >= 1, 1 <= kmax <= 8192, sigma_min > 0.
+ * Outputs (host): *k clusters; mu (kmax x 3), sigma (kmax), phi (kmax), of
+ * which the first *k entries are written; labels (n, or NULL) the cluster of
+ * every point; passes (or NULL) the passes run.  GOSMA_EINVAL (with *k = -1)
+ * when more than kmax clusters would be needed. */
+int gosma_dp_means(gosma_ctx *ctx, int n, const double *x, double lambda, int max_iter, int kmax, double sigma_min,
+                   int *k, double *mu, double *sigma, double *phi, int *labels, int *passes);
+
+/* Mixture generation (Sec. 6) for the image: the bearing vectors (n x 3,
+ * unit length within 1e-6, n < 2^22) are clustered with DP-vMF-means, the
+ * same passes as gosma_dp_means with the cosine x . mu as the similarity: a
+ * vector whose cosine with every centre is below lambda opens a cluster, the
+ * others join the most similar centre, and a centre is the normalised sum of
+ * its members (its lowest-index member if that sum is exactly zero).
+ * Coordinates are rounded to multiples of 2^-40 first.  Fit: phi_k = n_k /
+ * n, mu_k the mean direction, kappa_k the maximum-likelihood concentration
+ * on S^2, solving coth(kappa) - 1/kappa = |sum x| / n_k, capped at kappa_max
+ * (> 1e-12).  The theta_2 of gosma_set_mixtures.  Arguments and errors as in
+ * gosma_dp_means. */
+int gosma_dp_vmf_means(gosma_ctx *ctx, int n, const double *x, double lambda, int max_iter, int kmax,
+                       double kappa_max, int *k, double *mu, double *kappa, double *phi, int *labels, int *passes);
+
 /* Algorithm 1 (GOSMA) on the device: branch, bound, prune and select run in
  * device kernels; d* is always an FP64 evaluation of f, refined by SMA
  * (Sec. 5) whenever a sub-cube's upper bound beats it.  opts may be NULL

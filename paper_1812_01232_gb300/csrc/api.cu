@@ -106,6 +106,7 @@ void gosma_destroy(gosma_ctx *ctx) {
     if (ctx->d_stage) cudaFree(ctx->d_stage);
     if (ctx->d_obj) cudaFree(ctx->d_obj);
     if (ctx->d_sma) cudaFree(ctx->d_sma);
+    if (ctx->d_mg) cudaFree(ctx->d_mg);
     if (ctx->d_rot) cudaFree(ctx->d_rot);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
     delete ctx;

@@ -150,6 +150,10 @@ struct gosma_ctx {
     void *d_sma = nullptr;
     size_t sma_bytes = 0;
 
+    // mixture generation scratch (mixgen.cu)
+    void *d_mg = nullptr;
+    size_t mg_bytes = 0;
+
     // per-cube rotation pre-pass (gosma_eval_bounds)
     void *d_rot = nullptr;
     size_t rot_bytes = 0;

@@ -82,6 +82,10 @@ SIGNATURES = {
     "gosma_eval_objective": (C.c_int, [C.c_void_p, D, D, D]),
     "gosma_eval_objective_grad": (C.c_int, [C.c_void_p, C.c_int, D, D, D]),
     "gosma_eval_objective_grad_noalloc": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "gosma_dp_means": (C.c_int, [C.c_void_p, C.c_int, D, C.c_double, C.c_int, C.c_int, C.c_double,
+                                 C.POINTER(C.c_int), D, D, D, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "gosma_dp_vmf_means": (C.c_int, [C.c_void_p, C.c_int, D, C.c_double, C.c_int, C.c_int, C.c_double,
+                                     C.POINTER(C.c_int), D, D, D, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "gosma_sma_batch": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                                   C.c_void_p, C.c_void_p, C.c_int]),
     "gosma_bnb_solve": (C.c_int, [C.c_void_p, C.POINTER(Opts), C.POINTER(Result)]),
@@ -287,6 +291,28 @@ class Gosma:
                                                              C.c_void_p(out_dev.data_ptr())),
                     "eval_objective_grad_noalloc")
         return out_dev
+
+    def _dp(self, fn, name, x, lam, max_iter, kmax, param, key):
+        x = _f64(x, (-1, 3))
+        n = len(x)
+        mu, spread, phi = np.zeros((kmax, 3)), np.zeros(kmax), np.zeros(kmax)
+        labels = np.zeros(n, dtype=np.int32)
+        k, passes = C.c_int(), C.c_int()
+        ip = C.POINTER(C.c_int)
+        self._check(fn(self.h, n, _p(x), float(lam), int(max_iter), int(kmax), float(param), C.byref(k), _p(mu),
+                       _p(spread), _p(phi), labels.ctypes.data_as(ip), C.byref(passes)), name)
+        K = k.value
+        return {"k": K, "mu": mu[:K], key: spread[:K], "phi": phi[:K], "labels": labels, "passes": passes.value}
+
+    def dp_means(self, x, lam, max_iter=100, kmax=1024, sigma_min=1e-3):
+        """Mixture generation (Sec. 6): DP-means of the (n, 3) points and the
+        fitted GMM; returns dict(k, mu, sigma, phi, labels, passes)."""
+        return self._dp(self.L.gosma_dp_means, "dp_means", x, lam, max_iter, kmax, sigma_min, "sigma")
+
+    def dp_vmf_means(self, x, lam, max_iter=100, kmax=1024, kappa_max=1e5):
+        """Mixture generation (Sec. 6): DP-vMF-means of the (n, 3) unit vectors
+        and the fitted vMFMM; returns dict(k, mu, kappa, phi, labels, passes)."""
+        return self._dp(self.L.gosma_dp_vmf_means, "dp_vmf_means", x, lam, max_iter, kmax, kappa_max, "kappa")
 
     def sma_batch(self, x0, max_iter=100, precision=32, x=None, f=None, grad=None, iters=None, with_grad=True):
         """SMA (Sec. 5) from many seed poses at once on the device.

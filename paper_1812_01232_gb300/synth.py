@@ -254,6 +254,52 @@ def pose_seeds(prob, n: int, seed: int):
     return np.hstack([r, t])
 
 
+def scene_points(seed: int, n: int = 100_000, n_bear: int = 100_000, noise: float = 0.01):
+    """A synthetic indoor scene for mixture generation (Sec. 6 clusters a
+    point set and an image's bearing vectors; the real-data runs downsample
+    both to 100k).  Points lie on the floor, ceiling and walls of a
+    10 x 10 x 3 m room and on 20 axis-aligned boxes, uniformly by area, with
+    N(0, noise^2) jitter.  Bearing vectors are the unit directions
+    R (p - t) / |p - t| of other surface points seen by a camera at t (random
+    near the room centre, random rotation R) within a 60-degree half-angle
+    cone.  Returns dict(points (n, 3), bearings (n_bear, 3), R, r, t)."""
+    rng = np.random.default_rng(seed)
+    L, W, H = 10.0, 10.0, 3.0
+    faces = [  # (origin, edge u, edge v): rectangles of the room ...
+        ((-L / 2, -W / 2, 0), (L, 0, 0), (0, W, 0)), ((-L / 2, -W / 2, H), (L, 0, 0), (0, W, 0)),
+        ((-L / 2, -W / 2, 0), (L, 0, 0), (0, 0, H)), ((-L / 2, W / 2, 0), (L, 0, 0), (0, 0, H)),
+        ((-L / 2, -W / 2, 0), (0, W, 0), (0, 0, H)), ((L / 2, -W / 2, 0), (0, W, 0), (0, 0, H))]
+    for _ in range(20):  # ... and the five visible faces of each box
+        c = rng.uniform([-4, -4, 0], [4, 4, 0])
+        sx, sy, sz = rng.uniform([0.3, 0.3, 0.3], [1.5, 1.5, 1.2])
+        o = c - [sx / 2, sy / 2, 0]
+        faces += [(tuple(o + [0, 0, sz]), (sx, 0, 0), (0, sy, 0)), (tuple(o), (sx, 0, 0), (0, 0, sz)),
+                  (tuple(o + [0, sy, 0]), (sx, 0, 0), (0, 0, sz)), (tuple(o), (0, sy, 0), (0, 0, sz)),
+                  (tuple(o + [sx, 0, 0]), (0, sy, 0), (0, 0, sz))]
+    O = np.array([f[0] for f in faces], float)
+    U = np.array([f[1] for f in faces], float)
+    V = np.array([f[2] for f in faces], float)
+    area = np.linalg.norm(np.cross(U, V), axis=1)
+
+    def sample(m):
+        k = rng.choice(len(faces), size=m, p=area / area.sum())
+        a, b = rng.random((2, m))
+        return O[k] + a[:, None] * U[k] + b[:, None] * V[k] + noise * rng.normal(size=(m, 3))
+
+    pts = sample(n)
+    R, r = random_rotation(rng)
+    t = rng.uniform([-1, -1, 1.2], [1, 1, 1.8])
+    bear = np.zeros((0, 3))
+    while len(bear) < n_bear:
+        d = sample(4 * n_bear) - t
+        d /= np.linalg.norm(d, axis=1)[:, None]
+        d = d @ R.T
+        bear = np.concatenate([bear, d[d[:, 2] > np.cos(np.radians(60))]])
+    bear = bear[:n_bear]
+    bear /= np.linalg.norm(bear, axis=1)[:, None]
+    return {"points": pts, "bearings": bear, "R": R, "r": r, "t": t}
+
+
 def root_cube(t_lo, t_hi):
     t_lo = np.asarray(t_lo, dtype=np.float64)
     t_hi = np.asarray(t_hi, dtype=np.float64)

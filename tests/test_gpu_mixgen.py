@@ -1,0 +1,113 @@
+"""Mixture generation on the device (Sec. 6: DP-means for the point set,
+DP-vMF-means for the bearing vectors, maximum-likelihood fits) against the
+oracle.  Labels, cluster counts, passes and centres are integer or exact
+results (cluster sums are exact integers on both sides and every distance is
+formed with the same rounded operations), so they must agree bit for bit;
+the fitted sigma and kappa sum per-point terms in different orders and agree
+to 1e-13 and 1e-12 relative."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_1812_01232_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "dp_means_worked.json")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1812_01232_gb300 import build
+    build.build()
+    from paper_1812_01232_gb300.gosma import Gosma
+    c = Gosma(0)
+    yield c
+    c.close()
+
+
+def _compare(g, o, key, tol):
+    assert g["k"] == o["k"] and g["passes"] == o["passes"]
+    np.testing.assert_array_equal(g["labels"], o["labels"])
+    np.testing.assert_array_equal(g["mu"], o["mu"])
+    np.testing.assert_array_equal(g["phi"], o["phi"])
+    np.testing.assert_allclose(g[key], o[key], rtol=tol)
+
+
+def test_worked_examples(ctx):
+    for case in json.load(open(GOLDEN))["cases"]:
+        r = ctx.dp_means(np.array(case["points"], float), case["lambda"], sigma_min=case.get("sigma_min", 1e-3))
+        assert r["k"] == case["k"] and r["passes"] == case["passes"]
+        np.testing.assert_array_equal(r["labels"], case["labels"])
+        np.testing.assert_array_equal(r["mu"], np.array(case["mu"], float))
+        np.testing.assert_allclose(r["sigma"], case["sigma"], rtol=1e-14)
+
+
+@pytest.mark.parametrize("n,lam,seed", [(1, 1.0, 0), (2, 0.5, 1), (1007, 1.5, 2), (20000, 1.0, 3), (5000, 1e-9, 4),
+                                        (3000, 1e9, 5)])
+def test_dp_means_matches_oracle(ctx, oracle_mod, n, lam, seed):
+    """Ragged sizes, one point, every point alone, one cluster, many clusters."""
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(-4, 4, (n, 3)) * [1.0, 1.0, 0.4]
+    kmax = max(64, n + 1) if lam < 1e-6 else 1024
+    g = ctx.dp_means(x, lam, max_iter=40, kmax=kmax, sigma_min=0.01)
+    o = oracle_mod.dp_cluster(x, lam, max_iter=40, kmax=kmax, sigma_min=0.01)
+    _compare(g, o, "sigma", 1e-13)
+
+
+@pytest.mark.parametrize("n,deg,seed", [(1, 10.0, 0), (999, 15.0, 1), (20000, 8.0, 2), (4000, 200.0, 3)])
+def test_dp_vmf_means_matches_oracle(ctx, oracle_mod, n, deg, seed):
+    """deg = 200 puts the threshold below -1: one cluster at the mean direction."""
+    x = np.random.default_rng(seed).normal(size=(n, 3)) + [0.5, 0.0, 1.0]
+    x /= np.linalg.norm(x, axis=1)[:, None]
+    lam = np.cos(np.radians(deg)) if deg <= 180 else -1.5
+    g = ctx.dp_vmf_means(x, lam, max_iter=40, kappa_max=1e4)
+    o = oracle_mod.dp_cluster(x, lam, vmf=True, max_iter=40, kappa_max=1e4)
+    _compare(g, o, "kappa", 1e-12)
+
+
+def test_scene_at_paper_size(ctx, oracle_mod):
+    """100k scene points and 100k bearing vectors (the size the paper
+    downsamples to), about 100 and 70 clusters, 30 passes."""
+    sc = synth.scene_points(11)
+    g = ctx.dp_means(sc["points"], 2.0, max_iter=30)
+    o = oracle_mod.dp_cluster(sc["points"], 2.0, max_iter=30)
+    _compare(g, o, "sigma", 1e-13)
+    assert 60 <= g["k"] <= 120
+    lam = np.cos(np.radians(12.0))
+    g = ctx.dp_vmf_means(sc["bearings"], lam, max_iter=30)
+    o = oracle_mod.dp_cluster(sc["bearings"], lam, vmf=True, max_iter=30)
+    _compare(g, o, "kappa", 1e-12)
+    assert 50 <= g["k"] <= 100
+
+
+def test_generated_mixtures_feed_the_objective(ctx, oracle_mod):
+    """The generated GMM and vMFMM are valid gosma_set_mixtures inputs and the
+    device objective on them equals the oracle objective on the oracle's."""
+    sc = synth.scene_points(12, n=20000, n_bear=20000)
+    gm = ctx.dp_means(sc["points"], 2.0, max_iter=20, sigma_min=0.05)
+    gv = ctx.dp_vmf_means(sc["bearings"], np.cos(np.radians(12.0)), max_iter=20, kappa_max=2000.0)
+    ctx.set_mixtures(gm["mu"], gm["sigma"], gm["phi"] / gm["phi"].sum(), gv["mu"], gv["kappa"],
+                     gv["phi"] / gv["phi"].sum())
+    ctx.set_domain([-4, -4, 0.5], [4, 4, 2.5], 0.5)
+    mix = oracle_mod.Mixtures(gm["mu"], gm["sigma"], gm["phi"] / gm["phi"].sum(), gv["mu"], gv["kappa"],
+                              gv["phi"] / gv["phi"].sum())
+    f_dev = ctx.eval_objective(sc["r"], sc["t"])
+    assert f_dev == pytest.approx(oracle_mod.objective_r(mix, sc["r"], sc["t"]), rel=1e-10)
+
+
+def test_errors(ctx):
+    from paper_1812_01232_gb300.gosma import GosmaError
+    x = np.random.default_rng(0).uniform(-1, 1, (100, 3))
+    with pytest.raises(GosmaError):
+        ctx.dp_means(x, 0.0)
+    with pytest.raises(GosmaError):
+        ctx.dp_means(x, 1.0, kmax=0)
+    with pytest.raises(GosmaError):
+        ctx.dp_vmf_means(x, 0.5)  # not unit vectors
+    centres = np.array([[0, 0, 0], [50, 0, 0], [0, 50, 0], [0, 0, 50]], float)
+    y = np.repeat(centres, 10, axis=0)
+    with pytest.raises(GosmaError):
+        ctx.dp_means(y, 1.0, kmax=3)  # more than kmax clusters
