@@ -42,7 +42,11 @@ Two more measurements ride on the same line (rank 0, N = 1, unless
   the 128 x 64 paper-scale problem (half near the true pose, half uniform),
   seeds refined per second with the FP32 and the FP64 search (CUDA events
   around the whole call, the FP64 f of the results included), beside the
-  oracle's L-BFGS on one host core.
+  oracle's L-BFGS on one host core;
+* "mixgen": mixture generation (Sec. 6) for a synthetic indoor scene at the
+  size the paper downsamples to: DP-means of 100k points (lambda 2 m^2) and
+  DP-vMF-means of 100k bearing vectors (12-degree threshold), 30 passes
+  each, through the host-buffer C-ABI calls, beside the oracle on one core.
 """
 from __future__ import annotations
 
@@ -347,6 +351,7 @@ def run_ours(args):
         line["batched"] = run_batched(args.batch_budget)
         line["time_to_certified"] = run_time_to_certified(8)
         line["sma"] = run_sma()
+        line["mixgen"] = run_mixgen()
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -410,6 +415,33 @@ def run_sma():
         oracle.sma(mix, x, prob["t_lo"], prob["t_hi"], prob["zeta"], max_iter=100, memory=8, gtol=1e-10)
     sec = time.perf_counter() - t0
     out["oracle"] = {"seeds": len(x0), "seconds": sec, "seeds_per_s": len(x0) / sec, "cores": 1, "kind": "oracle"}
+    return out
+
+
+def run_mixgen():
+    """Mixture generation of a 100k-point scene (see module doc)."""
+    from paper_1812_01232_gb300 import synth
+    from paper_1812_01232_gb300.gosma import Gosma
+    import oracle
+    sc = synth.scene_points(11)
+    ctx = Gosma(0)
+    lam_v = float(np.cos(np.radians(12.0)))
+    ctx.dp_means(sc["points"][:1000], 2.0, max_iter=2)  # warm-up
+    out = {"workload": "100k scene points (lambda 2 m^2) and 100k bearing vectors (cosine threshold cos 12 deg), "
+                       "30 passes each, host buffers"}
+    for name, call in (("dp_means", lambda: ctx.dp_means(sc["points"], 2.0, max_iter=30)),
+                       ("dp_vmf_means", lambda: ctx.dp_vmf_means(sc["bearings"], lam_v, max_iter=30))):
+        t0 = time.perf_counter()
+        r = call()
+        sec = time.perf_counter() - t0
+        out[name] = {"seconds": sec, "clusters": r["k"], "passes": r["passes"]}
+    ctx.close()
+    t0 = time.perf_counter()
+    oracle.dp_cluster(sc["points"], 2.0, max_iter=30)
+    t1 = time.perf_counter()
+    oracle.dp_cluster(sc["bearings"], lam_v, vmf=True, max_iter=30)
+    t2 = time.perf_counter()
+    out["oracle"] = {"dp_means_seconds": t1 - t0, "dp_vmf_means_seconds": t2 - t1, "cores": 1, "kind": "oracle"}
     return out
 
 

@@ -4,6 +4,7 @@
     python -m paper_1812_01232_gb300.profile_cases mlp --steps 4
     python -m paper_1812_01232_gb300.profile_cases batch --problems 64 --max-nodes 100000
     python -m paper_1812_01232_gb300.profile_cases sma --seeds 1216 --precision 32
+    python -m paper_1812_01232_gb300.profile_cases mixgen --points 100000 --passes 30
 
 stress  Theorem 1 bounds of `cubes` sub-cubes of the 2048 x 512 stress problem
         (device buffers), `reps` launches of the bound kernel.
@@ -14,6 +15,9 @@ batch   one batched solve of `problems` uneven problems (tiny generator,
 sma     SMA from `seeds` seed poses of the 128 x 64 paper-scale problem
         (half near the true pose, half uniform over the domain), `reps`
         launches of the batched refinement at the given precision.
+mixgen  DP-means of `points` points of the synthetic indoor scene
+        (lambda 2 m^2) with at most `passes` passes, then DP-vMF-means of as
+        many bearing vectors (12-degree threshold).
 Each prints one line of timing so that the plain run can be compared.
 """
 from __future__ import annotations
@@ -97,6 +101,18 @@ def sma(a):
         a.seeds, a.precision, 1e3 * dt, a.seeds / dt, int(it.median().item())))
 
 
+def mixgen(a):
+    prob = synth.scene_points(11, n=a.points, n_bear=a.points)
+    ctx = Gosma(0)
+    t0 = time.perf_counter()
+    r = ctx.dp_means(prob["points"], 2.0, max_iter=a.passes)
+    t1 = time.perf_counter()
+    v = ctx.dp_vmf_means(prob["bearings"], float(np.cos(np.radians(12.0))), max_iter=a.passes)
+    t2 = time.perf_counter()
+    print("mixgen: %d points -> %d clusters in %d passes, %.3f s; %d vectors -> %d clusters in %d passes, %.3f s" % (
+        a.points, r["k"], r["passes"], t1 - t0, a.points, v["k"], v["passes"], t2 - t1))
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     sub = ap.add_subparsers(dest="case", required=True)
@@ -112,8 +128,11 @@ def main(argv=None):
     q.add_argument("--seeds", type=int, default=1216)
     q.add_argument("--precision", type=int, default=32)
     q.add_argument("--reps", type=int, default=2)
+    g = sub.add_parser("mixgen")
+    g.add_argument("--points", type=int, default=100000)
+    g.add_argument("--passes", type=int, default=30)
     a = ap.parse_args(argv)
-    {"stress": stress, "mlp": mlp, "batch": batch, "sma": sma}[a.case](a)
+    {"stress": stress, "mlp": mlp, "batch": batch, "sma": sma, "mixgen": mixgen}[a.case](a)
     return 0
 
 
