@@ -657,51 +657,53 @@ static int objective_records(gosma_ctx *ctx, int count, const double *d_x, doubl
     return e == cudaSuccess ? GOSMA_OK : cuda_fail(ctx, e, "launch(objective records)");
 }
 
-// Dynamic shared memory and persistent grid of the SMA kernel.
+// Dynamic shared memory and persistent grid of the SMA kernel.  Errors are
+// recorded on ectx (NULL: not recorded, for calls from a worker thread).
 template <bool F64, class Src>
-static int sma_config(gosma_ctx *ctx, int max_n1, int max_n2, int count, int *grid, size_t *smem) {
+static int sma_config(gosma_ctx *ctx, gosma_ctx *ectx, int max_n1, int max_n2, int count, int *grid, size_t *smem) {
     *smem = F64 ? 0 : sma32_smem_bytes(max_n1, max_n2);
     auto kern = sma_kernel<F64, Src>;
     if (*smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
         if (e != cudaSuccess) {
             cudaGetLastError();
-            return fail(ctx, GOSMA_EINVAL, "sma: mixtures too large for one block's shared memory");
+            return fail(ectx, GOSMA_EINVAL, "sma: mixtures too large for one block's shared memory");
         }
     }
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SMA_BLOCK, *smem);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "occupancy(sma)");
-    if (per_sm < 1) return fail(ctx, GOSMA_EINVAL, "sma: mixtures too large for one block's shared memory");
+    if (e != cudaSuccess) return cuda_fail(ectx, e, "occupancy(sma)");
+    if (per_sm < 1) return fail(ectx, GOSMA_EINVAL, "sma: mixtures too large for one block's shared memory");
     long long g = (long long)ctx->sm_count * per_sm;
     *grid = (int)(g < count ? g : count);
     return GOSMA_OK;
 }
 
 template <bool F64, class Src>
-static int sma_run(gosma_ctx *ctx, cudaStream_t st, const Src &src, int grid, size_t smem, int count,
+static int sma_run(gosma_ctx *ectx, cudaStream_t st, const Src &src, int grid, size_t smem, int count,
                    const double *d_x0, int max_iter, double *d_x, int *d_it, double *d_rows, int max_n1,
                    int *d_counter, long long *launches) {
     cudaError_t e = cudaMemsetAsync(d_counter, 0, sizeof(int), st);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "memset(sma counter)");
+    if (e != cudaSuccess) return cuda_fail(ectx, e, "memset(sma counter)");
     sma_kernel<F64, Src><<<grid, SMA_BLOCK, smem, st>>>(src, count, d_x0, max_iter, d_x, d_it, d_rows, max_n1,
                                                         d_counter);
     ++*launches;
     e = cudaGetLastError();
-    return e == cudaSuccess ? GOSMA_OK : cuda_fail(ctx, e, "launch(sma)");
+    return e == cudaSuccess ? GOSMA_OK : cuda_fail(ectx, e, "launch(sma)");
 }
 
 // FP32-search SMA of count seeds, seed s on problem d_pid[s] (the batched
-// solver's refinement); asynchronous on st.
+// solver's refinement, run from its worker thread: errors are returned, not
+// recorded on the context); asynchronous on st.
 int sma_refine_many(gosma_ctx *ctx, cudaStream_t st, const MixDev *d_mixes, const SmaBox *d_boxes, const int *d_pid,
                     int max_n1, int max_n2, int count, const double *d_x0, int max_iter, double *d_x, int *d_it,
                     int *d_counter, long long *launches) {
     if (count <= 0) return GOSMA_OK;
     int grid = 0;
     size_t smem = 0;
-    int rc = sma_config<false, SmaMany>(ctx, max_n1, max_n2, count, &grid, &smem);
+    int rc = sma_config<false, SmaMany>(ctx, nullptr, max_n1, max_n2, count, &grid, &smem);
     if (rc) return rc;
-    return sma_run<false, SmaMany>(ctx, st, SmaMany{d_mixes, d_boxes, d_pid}, grid, smem, count, d_x0, max_iter, d_x,
+    return sma_run<false, SmaMany>(nullptr, st, SmaMany{d_mixes, d_boxes, d_pid}, grid, smem, count, d_x0, max_iter, d_x,
                                    d_it, nullptr, max_n1, d_counter, launches);
 }
 
@@ -724,8 +726,8 @@ extern "C" int gosma_sma_batch(gosma_ctx *ctx, int count, const double *x0, int 
     const int n1 = ctx->n1, n2 = ctx->n2;
     int grid = 0;
     size_t smem = 0;
-    int rc = f64 ? sma_config<true, SmaOne>(ctx, n1, n2, count, &grid, &smem)
-                 : sma_config<false, SmaOne>(ctx, n1, n2, count, &grid, &smem);
+    int rc = f64 ? sma_config<true, SmaOne>(ctx, ctx, n1, n2, count, &grid, &smem)
+                 : sma_config<false, SmaOne>(ctx, ctx, n1, n2, count, &grid, &smem);
     if (rc) return rc;
 
     // device scratch: seeds and poses (host calls), iterations, counter,
