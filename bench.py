@@ -35,7 +35,7 @@ Two more measurements ride on the same line (rank 0, N = 1, unless
   with the count);
 * "time_to_certified": tiny problems (10 x 8 components, eps 1e-3) solved
   to the certified optimum by the plain single-problem solver (one after the
-  other), the plain batched solver and the learned batched solver (network
+  other, automatic pop), the plain batched solver and the learned batched solver (network
   weights from paper_1812_01232_gb300/weights, scoring during the first 32
   iterations, where the incumbent is found), on the same problems;
 * "sma": the batched device refinement (SMA, Sec. 5) of many seed poses of
@@ -452,13 +452,14 @@ def run_time_to_certified(n_prob):
     ctx = Gosma(0)
     eps = 1e-3
     probs = [synth.tiny_problem(200000 + s) for s in range(n_prob)]
-    out = {"workload": "%d tiny problems (10 x 8 components), eps 1e-3, pop %d (%d children per iteration), "
-                       "queue 2^26 per problem" % (n_prob, POP, 8 * POP)}
+    out = {"workload": "%d tiny problems (10 x 8 components), eps 1e-3, queue 2^26 per problem; single-problem "
+                       "solver with its automatic pop (65536 sub-cubes per iteration for 10 x 8), batched solvers "
+                       "with pop %d per problem (their maximum)" % (n_prob, POP)}
     single = []
     t0 = time.perf_counter()
     for p in probs:
         ctx.set_problem(p)
-        single.append(ctx.bnb_solve(eps=eps, pop=POP, max_seconds=60, queue_capacity=1 << 26))
+        single.append(ctx.bnb_solve(eps=eps, max_seconds=60, queue_capacity=1 << 26))
     out["plain_single"] = {"wall_s": time.perf_counter() - t0, "nodes": int(sum(r["nodes"] for r in single)),
                            "certified": int(sum(r["status_name"] == "optimal" for r in single))}
     ctx.mlp_set_params(learn.load(os.path.join(ROOT, "paper_1812_01232_gb300", "weights", "gosma_mlp.npz")))

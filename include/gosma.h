@@ -67,7 +67,9 @@ typedef struct {
 
 typedef struct {
     double eps;          /* tolerance on the normalised L2 distance f/C22 + 1 (Sec. 6 uses 0.1) */
-    int pop;             /* hypercubes removed from the queue per iteration (Algorithm 1); each gives 8 children */
+    int pop;             /* hypercubes removed from the queue per iteration (Algorithm 1); each gives 8 children.
+                            gosma_bnb_solve / _start: 0 = automatic, 2^23 / (n1 n2) clamped to [8192, 65536]
+                            (8192 from 1024 pairs per cube up); gosma_bnb_solve_batch: 1..8192 per problem */
     long long max_nodes; /* stop after this many evaluated sub-cubes (<= 0: no limit) */
     double max_seconds;  /* wall-clock limit (<= 0: no limit) */
     int use_sma;         /* run local refinement (SMA, Sec. 5) when a sub-cube improves d* */
@@ -261,7 +263,7 @@ int gosma_dp_vmf_means(gosma_ctx *ctx, int n, const double *x, double lambda, in
 /* Algorithm 1 (GOSMA) on the device: branch, bound, prune and select run in
  * device kernels; d* is always an FP64 evaluation of f, refined by SMA
  * (Sec. 5) whenever a sub-cube's upper bound beats it.  opts may be NULL
- * (eps = 0.1, pop = 8192, no limits, SMA on).  Equivalent to
+ * (eps = 0.1, automatic pop, no limits, SMA on).  Equivalent to
  * gosma_bnb_start followed by gosma_bnb_step(ctx, 0, out). */
 int gosma_bnb_solve(gosma_ctx *ctx, const gosma_opts *opts, gosma_result *out);
 

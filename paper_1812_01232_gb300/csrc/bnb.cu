@@ -730,12 +730,21 @@ extern "C" int gosma_bnb_start(gosma_ctx *ctx, const gosma_opts *opts_in) {
     gosma_opts o;
     memset(&o, 0, sizeof o);
     o.eps = 0.1;
-    o.pop = 8192;  // 65,536 children per iteration fill the GPU
+    o.pop = 0;  // automatic
     o.use_sma = 1;
     o.sma_max_iter = 100;
     if (opts_in) o = *opts_in;
-    if (!(o.eps >= 0) || o.pop < 1 || o.pop > 131072)
-        return fail(ctx, GOSMA_EINVAL, "bnb_start: need eps >= 0 and 1 <= pop <= 131072");
+    if (!(o.eps >= 0) || o.pop < 0 || o.pop > 131072)
+        return fail(ctx, GOSMA_EINVAL, "bnb_start: need eps >= 0 and 0 <= pop <= 131072");
+    if (o.pop == 0) {
+        // about 2^23 pair bounds per iteration, at least 65,536 children (a
+        // few hundred sub-cubes per SM for the persistent bound kernel) and
+        // at most 524,288: small mixtures are otherwise bound by the fixed
+        // cost of an iteration (selection, compaction, launches, the host
+        // read of the status record)
+        long long p = (1LL << 23) / ((long long)ctx->n1 * ctx->n2);
+        o.pop = (int)(p < 8192 ? 8192 : p > 65536 ? 65536 : p);
+    }
     if (o.sma_max_iter <= 0) o.sma_max_iter = 100;
     unsigned long long cap = o.queue_capacity > 0 ? (unsigned long long)o.queue_capacity : (1ULL << 24);
     if (cap < 16ULL * o.pop) cap = 16ULL * o.pop;

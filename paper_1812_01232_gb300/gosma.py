@@ -355,7 +355,7 @@ class Gosma:
             "block_size": r.block_size,
         }
 
-    def bnb_solve(self, eps=0.1, pop=8192, max_nodes=0, max_seconds=0.0, use_sma=True, sma_max_iter=100,
+    def bnb_solve(self, eps=0.1, pop=0, max_nodes=0, max_seconds=0.0, use_sma=True, sma_max_iter=100,
                   queue_capacity=0):
         """Algorithm 1 to termination; returns the certificate and the pose."""
         o = self._opts(eps, pop, max_nodes, max_seconds, use_sma, sma_max_iter, queue_capacity)
@@ -412,7 +412,7 @@ class Gosma:
             return out, [tr[k, :cnt[k]].copy() for k in range(len(problems))]
         return out
 
-    def bnb_start(self, eps=0.1, pop=8192, max_nodes=0, max_seconds=0.0, use_sma=True, sma_max_iter=100,
+    def bnb_start(self, eps=0.1, pop=0, max_nodes=0, max_seconds=0.0, use_sma=True, sma_max_iter=100,
                   queue_capacity=0):
         o = self._opts(eps, pop, max_nodes, max_seconds, use_sma, sma_max_iter, queue_capacity)
         self._check(self.L.gosma_bnb_start(self.h, C.byref(o)), "bnb_start")

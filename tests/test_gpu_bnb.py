@@ -89,6 +89,25 @@ def test_step_interface_matches_solve(ctx):
     assert r["bound_ms"] > 0 and r["iteration_ms"] >= r["bound_ms"]
 
 
+def test_automatic_pop(ctx):
+    """pop = 0 takes 2^23 / (n1 n2) sub-cubes per iteration, clamped to
+    [8192, 65536]: 65536 for 10 x 8 mixtures, 8192 for 128 x 64; the run is
+    the same as with that pop given explicitly."""
+    p = synth.tiny_problem(1000)
+    ctx.set_problem(p)
+    a = ctx.bnb_solve(eps=p["eps"], queue_capacity=1 << 26)
+    b = ctx.bnb_solve(eps=p["eps"], pop=65536, queue_capacity=1 << 26)
+    assert a["status_name"] == "optimal"
+    for k in ("f", "lb", "nodes", "iterations"):
+        assert a[k] == b[k], k
+    q = synth.paper_scale_problem(2000)
+    ctx.set_problem(q)
+    a = ctx.bnb_solve(eps=q["eps"], max_nodes=200000)
+    b = ctx.bnb_solve(eps=q["eps"], pop=8192, max_nodes=200000)
+    for k in ("f", "lb", "nodes", "iterations"):
+        assert a[k] == b[k], k
+
+
 def test_limits_and_queue_capacity(ctx):
     p = synth.paper_scale_problem(2000)
     ctx.set_problem(p)
