@@ -16,9 +16,18 @@
 //
 // Exactness: coordinates are rounded to multiples of 2^-32 (points) or 2^-40
 // (unit vectors) so that cluster sums are exact 64-bit integer atomics, and
-// distances and cosines are formed with explicitly rounded FP64 operations
-// (no contraction), so labels and centres equal those of a serial FP64
-// implementation of the same steps bit for bit.
+// every decision (nearest centre, a new centre beating the current one,
+// opening a cluster) compares distances or cosines formed with explicitly
+// rounded FP64 operations (no contraction), so labels and centres equal those
+// of a serial FP64 implementation of the same steps bit for bit.  GB300 runs
+// FP64 at about 1/64 of its FP32 rate, so the candidates are screened in
+// FP32 first: with every coordinate of points and centres at most A in
+// magnitude, an FP32 squared distance is within E = 128 u A^2 of the FP64
+// one (u = 2^-24; the sum of (|x_k| + |m_k|)^2 is at most 12 A^2 and each
+// term carries at most 8u), an FP32 cosine of unit vectors within 8u; only
+// centres whose FP32 value is within 2E of the best FP32 value (nearest
+// centre) or within E of beating the exact current best (new centre) are
+// evaluated in FP64.  The exact winner is always among them.
 #include <cooperative_groups.h>
 #include <math.h>
 
@@ -93,6 +102,20 @@ __global__ void mg_quantize(int n3, const double *__restrict__ x, double scale, 
     xq[i] = __ddiv_rn(__ll2double_rn(v), scale);
 }
 
+// FP32 copies of the quantized points for the screening.
+__global__ void mg_pack(int n, const double *__restrict__ xq, float4 *__restrict__ xf) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) xf[i] = make_float4((float)xq[3 * i], (float)xq[3 * i + 1], (float)xq[3 * i + 2], 0.f);
+}
+
+// FP32 screening value (squared distance or cosine).
+template <bool VMF>
+__device__ __forceinline__ float mg_score32(float4 x, float4 m) {
+    if (VMF) return fmaf(x.z, m.z, fmaf(x.y, m.y, x.x * m.x));
+    const float d0 = x.x - m.x, d1 = x.y - m.y, d2 = x.z - m.z;
+    return fmaf(d2, d2, fmaf(d1, d1, d0 * d0));
+}
+
 __global__ void mg_fill(int count, int value, int *__restrict__ a) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < count) a[i] = value;
@@ -127,12 +150,13 @@ __device__ __forceinline__ long long mg_block_sum(long long v, long long *sred) 
 // passes, at most kmax rounds per pass.
 template <bool VMF>
 __global__ void __launch_bounds__(MG_BLOCK) mg_cluster(int n, const double *__restrict__ xq,
-                                                       const long long *__restrict__ q, double lam, int max_iter,
+                                                       const long long *__restrict__ q,
+                                                       const float4 *__restrict__ xf, float E, double lam, int max_iter,
                                                        int kmax, double *cen, int *lab, double *best, int *arg,
                                                        unsigned long long *sums, unsigned long long *cnt, int *first,
                                                        int *remap, MgState *S) {
     cg::grid_group grid = cg::this_grid();
-    extern __shared__ double sc[];  // centres of the previous pass, kmax x 3
+    extern __shared__ float4 scf[];  // FP32 copies of the previous pass's centres, kmax
     __shared__ int sred_i[MG_BLOCK / 32];
     __shared__ long long sred_l[MG_BLOCK / 32];
     const int tid = threadIdx.x, b = blockIdx.x, nb = gridDim.x;
@@ -165,15 +189,28 @@ __global__ void __launch_bounds__(MG_BLOCK) mg_cluster(int n, const double *__re
     for (; pass < max_iter; ++pass) {
         // 1. every point's nearest centre of the previous pass
         const int K0 = __ldcg(&S->K);
-        for (int k = tid; k < 3 * K0; k += MG_BLOCK) sc[k] = __ldcg(&cen[k]);
+        for (int c = tid; c < K0; c += MG_BLOCK)
+            scf[c] = make_float4((float)__ldcg(&cen[3 * c]), (float)__ldcg(&cen[3 * c + 1]),
+                                 (float)__ldcg(&cen[3 * c + 2]), 0.f);
         __syncthreads();
         for (int i = i0 + tid; i < i1; i += MG_BLOCK) {
-            const double *x = xq + 3 * i;
-            double bv = mg_score<VMF>(x, sc);
-            int a = 0;
+            const float4 xv = xf[i];
+            float b32 = mg_score32<VMF>(xv, scf[0]);
             for (int c = 1; c < K0; ++c) {
-                const double s = mg_score<VMF>(x, sc + 3 * c);
-                if (mg_better<VMF>(s, bv)) {
+                const float s = mg_score32<VMF>(xv, scf[c]);
+                b32 = VMF ? fmaxf(b32, s) : fminf(b32, s);
+            }
+            // 2E, and E/4 for the rounding of the limit itself
+            const float lim = VMF ? b32 - 2.25f * E : b32 + 2.25f * E;
+            const double *x = xq + 3 * i;
+            double bv = 0.0;
+            int a = -1;
+            for (int c = 0; c < K0; ++c) {
+                const float s32 = mg_score32<VMF>(xv, scf[c]);
+                if (VMF ? s32 < lim : s32 > lim) continue;
+                const double m[3] = {__ldcg(&cen[3 * c]), __ldcg(&cen[3 * c + 1]), __ldcg(&cen[3 * c + 2])};
+                const double s = mg_score<VMF>(x, m);
+                if (a < 0 || mg_better<VMF>(s, bv)) {
                     bv = s;
                     a = c;
                 }
@@ -211,13 +248,16 @@ __global__ void __launch_bounds__(MG_BLOCK) mg_cluster(int n, const double *__re
             if (lead)
                 for (int k = 0; k < 3; ++k) cen[3 * c + k] = xq[3 * istar + k];
             const double *m = xq + 3 * istar;
+            const float4 mv = xf[istar];
             for (int i = max(i0, istar) + tid; i < i1; i += MG_BLOCK) {
                 if (i == istar) {
                     arg[i] = c;
                     continue;
                 }
+                const double s32 = mg_score32<VMF>(xf[i], mv), bi = best[i];
+                if (VMF ? s32 + E <= bi : s32 - E >= bi) continue;  // cannot beat the current centre
                 const double s = mg_score<VMF>(xq + 3 * i, m);
-                if (mg_better<VMF>(s, best[i])) {
+                if (mg_better<VMF>(s, bi)) {
                     best[i] = s;
                     arg[i] = c;
                 }
@@ -342,12 +382,13 @@ static int mg_run(gosma_ctx *ctx, int n, const double *h_x, double lam, int max_
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaSetDevice");
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
     const size_t b_x = al(sizeof(double) * 3 * (size_t)n), b_q = al(sizeof(long long) * 3 * (size_t)n),
+                 b_xf = al(sizeof(float4) * (size_t)n),
                  b_n = al(sizeof(int) * (size_t)n), b_best = al(sizeof(double) * (size_t)n),
                  b_cen = al(sizeof(double) * 3 * (size_t)kmax), b_sums = al(sizeof(unsigned long long) * 3 * (size_t)kmax),
                  b_k = al(sizeof(unsigned long long) * (size_t)kmax), b_ki = al(sizeof(int) * (size_t)kmax),
                  b_kd = al(sizeof(double) * (size_t)kmax), b_st = al(sizeof(MgState));
-    // x, xq, q, lab, arg, best, cen, sums, cnt, first, remap, ss, spread, phi, state
-    const size_t need = 2 * b_x + b_q + 2 * b_n + b_best + b_cen + b_sums + b_k + 2 * b_ki + 3 * b_kd + b_st;
+    // x, xq, q, xf, lab, arg, best, cen, sums, cnt, first, remap, ss, spread, phi, state
+    const size_t need = 2 * b_x + b_q + b_xf + 2 * b_n + b_best + b_cen + b_sums + b_k + 2 * b_ki + 3 * b_kd + b_st;
     if (need > ctx->mg_bytes) {
         if (ctx->d_mg) cudaFree(ctx->d_mg);
         ctx->d_mg = nullptr;
@@ -363,6 +404,8 @@ static int mg_run(gosma_ctx *ctx, int n, const double *h_x, double lam, int max_
     p += b_x;
     long long *d_q = (long long *)p;
     p += b_q;
+    float4 *d_xf = (float4 *)p;
+    p += b_xf;
     int *d_lab = (int *)p;
     p += b_n;
     int *d_arg = (int *)p;
@@ -395,11 +438,19 @@ static int mg_run(gosma_ctx *ctx, int n, const double *h_x, double lam, int max_
     if (e == cudaSuccess) e = cudaMemsetAsync(d_st, 0, sizeof(MgState), st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "mixture generation set-up");
     mg_quantize<<<(3 * n + 255) / 256, 256, 0, st>>>(3 * n, d_x, scale, d_q, d_xq);
+    mg_pack<<<(n + 255) / 256, 256, 0, st>>>(n, d_xq, d_xf);
     mg_fill<<<(kmax + 255) / 256, 256, 0, st>>>(kmax, n, d_first);
-    ctx->launches += 2;
+    ctx->launches += 3;
+    // FP32 screening bound (see the top of the file): 128 u A^2, A the
+    // largest coordinate magnitude (2^-32 above the input's for the
+    // rounding); 8 u for unit vectors
+    double A = 0.0;
+    for (long long i = 0; i < 3LL * n; ++i) A = fmax(A, fabs(h_x[i]));
+    A += 0x1p-32;
+    float E = VMF ? (float)(8.0 * 0x1p-24) : (float)(128.0 * 0x1p-24 * A * A);
 
     auto kern = mg_cluster<VMF>;
-    const size_t smem = sizeof(double) * 3 * (size_t)kmax;
+    const size_t smem = sizeof(float4) * (size_t)kmax;
     if (smem > 48 * 1024) {
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFuncSetAttribute(mixture generation)");
@@ -410,7 +461,8 @@ static int mg_run(gosma_ctx *ctx, int n, const double *h_x, double lam, int max_
     if (per_sm < 1) return fail(ctx, GOSMA_EINVAL, "mixture generation: kmax too large for one block");
     int grid = ctx->sm_count * per_sm, need_blocks = (n + MG_BLOCK - 1) / MG_BLOCK;
     if (grid > need_blocks) grid = need_blocks;
-    void *args[] = {(void *)&n,      (void *)&d_xq,  (void *)&d_q,   (void *)&lam,     (void *)&max_iter,
+    void *args[] = {(void *)&n,      (void *)&d_xq,  (void *)&d_q,   (void *)&d_xf,    (void *)&E,
+                    (void *)&lam,    (void *)&max_iter,
                     (void *)&kmax,   (void *)&d_cen, (void *)&d_lab, (void *)&d_best,  (void *)&d_arg,
                     (void *)&d_sums, (void *)&d_cnt, (void *)&d_first, (void *)&d_remap, (void *)&d_st};
     e = cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(MG_BLOCK), args, smem, st);
