@@ -461,7 +461,7 @@ struct SmaMany {
 // trial poses each.  The dynamic shared memory holds the FP32 tables of the
 // largest mixture (FP32 search); rows64 one FP64 table per block (FP64).
 template <bool F64, class Src>
-__global__ void __launch_bounds__(SMA_BLOCK) sma_kernel(Src src, int count, const double *__restrict__ x0, int max_iter,
+__global__ void __launch_bounds__(SMA_BLOCK, F64 ? 1 : 8) sma_kernel(Src src, int count, const double *__restrict__ x0, int max_iter,
                                                         double *__restrict__ xout, int *__restrict__ iters,
                                                         double *__restrict__ rows64, int max_n1, int *__restrict__ counter) {
     extern __shared__ float4 sma_smem[];
