@@ -69,7 +69,8 @@ typedef struct {
     double eps;          /* tolerance on the normalised L2 distance f/C22 + 1 (Sec. 6 uses 0.1) */
     int pop;             /* hypercubes removed from the queue per iteration (Algorithm 1); each gives 8 children.
                             gosma_bnb_solve / _start: 0 = automatic, 2^23 / (n1 n2) clamped to [8192, 65536]
-                            (8192 from 1024 pairs per cube up); gosma_bnb_solve_batch: 1..8192 per problem */
+                            (8192 from 1024 pairs per cube up); gosma_bnb_solve_batch: 1..65536 per problem,
+                            with 8 x pop x problems < 2^31 */
     long long max_nodes; /* stop after this many evaluated sub-cubes (<= 0: no limit) */
     double max_seconds;  /* wall-clock limit (<= 0: no limit) */
     int use_sma;         /* run local refinement (SMA, Sec. 5) when a sub-cube improves d* */

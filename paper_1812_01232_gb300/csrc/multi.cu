@@ -1210,7 +1210,11 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
     o.sma_max_iter = 100;
     if (opts_in) o = *opts_in;
     if (o.sma_max_iter <= 0) o.sma_max_iter = 100;
-    if (!(o.eps >= 0) || o.pop < 1 || o.pop > 8192) return fail(ctx, GOSMA_EINVAL, "bnb_solve_batch: eps >= 0, 1 <= pop <= 8192");
+    if (!(o.eps >= 0) || o.pop < 1 || o.pop > 65536)
+        return fail(ctx, GOSMA_EINVAL, "bnb_solve_batch: eps >= 0, 1 <= pop <= 65536");
+    // children offsets are 32-bit prefix sums of 8 x pop per problem
+    if (8LL * o.pop * nprob > 0x7fffffffLL)
+        return fail(ctx, GOSMA_EINVAL, "bnb_solve_batch: 8 * pop * problems must be below 2^31");
     const unsigned long long cap = o.queue_capacity > 0 ? (unsigned long long)o.queue_capacity : (1ULL << 18);
     if (cap < 16ULL * o.pop) return fail(ctx, GOSMA_EINVAL, "bnb_solve_batch: queue_capacity below 16 * pop");
     for (int k = 0; k < nprob; ++k) {

@@ -196,6 +196,10 @@ def test_batch_limits_and_errors(ctx):
         ctx.bnb_solve_batch([probs[1], bad], eps=1e-3)
     with pytest.raises(GosmaError):
         ctx.bnb_solve_batch(probs, eps=1e-3, pop=0)
+    with pytest.raises(GosmaError):
+        ctx.bnb_solve_batch(probs, eps=1e-3, pop=65537)
+    with pytest.raises(GosmaError):  # 8 x pop x problems must stay below 2^31 (32-bit child offsets)
+        ctx.bnb_solve_batch([probs[0]] * 4097, eps=1e-3, pop=65536, queue_capacity=1 << 20)
 
 
 # ---------------------------------------------------------------- learned form (network-ordered queue, seeds, traces)
