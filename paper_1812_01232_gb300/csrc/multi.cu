@@ -29,8 +29,9 @@
 // The sequence is captured once in a CUDA graph and replayed; the host polls
 // the number of finished problems every 8 replays and applies the results of
 // the SMA refinement that a host thread runs on a second stream.  The block
-// size of mp_bound is chosen by timing the candidates on one iteration's
-// children.
+// size of mp_bound is chosen by timing the candidates (32 threads for small
+// mixtures, 64, 128, 256, a wider block for large ones) on the fifth
+// iteration's children.
 #include <math.h>
 #include <string.h>
 
@@ -973,6 +974,7 @@ static cudaError_t mp_bound_any(int block, gosma_ctx *ctx, cudaStream_t st, cons
                                 const Node *parents, const CubePrep *prep, Node *kids, double *kid_ub, int *counter,
                                 size_t smem) {
     switch (block) {
+    case 32: return mp_bound_launch<32>(ctx, st, P, off, nprob, parents, prep, kids, kid_ub, counter, smem);
     case 64: return mp_bound_launch<64>(ctx, st, P, off, nprob, parents, prep, kids, kid_ub, counter, smem);
     case 128: return mp_bound_launch<128>(ctx, st, P, off, nprob, parents, prep, kids, kid_ub, counter, smem);
     case 256: return mp_bound_launch<256>(ctx, st, P, off, nprob, parents, prep, kids, kid_ub, counter, smem);
@@ -1568,7 +1570,9 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
 
     // ---- eager iterations; at TUNE_ITER the candidate block sizes of the bound kernel are timed
     // on the same prepared children (the bound kernel only writes the children's records)
-    const int TUNE_ITER = 3;
+    // tune once the queues hold enough parents for a representative launch
+    // (8^5 per problem unless the pop quota is smaller)
+    const int TUNE_ITER = 5;
     int block = 128, iter = 0;
     cudaEvent_t ta, tb;
     cudaEventCreate(&ta);
@@ -1577,8 +1581,11 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
         front();
         if (iter == TUNE_ITER) {
             float best = 1e30f;
-            const int wide = bounds_block_size(max_n1, max_n2);  // > 256 for large mixtures
-            for (int cand : {64, 128, 256, wide > 256 ? wide : 0}) {
+            // 32 threads when even the largest mixture has few pairs per cube
+            // (as bounds_block_size picks for one problem), a wider block for
+            // large mixtures
+            const int wide = bounds_block_size(max_n1, max_n2);
+            for (int cand : {wide == 32 ? 32 : 0, 64, 128, 256, wide > 256 ? wide : 0}) {
                 if (!cand) continue;
                 cudaEventRecord(ta, st);
                 e = mp_bound_any(cand, ctx, st, dP, off, nprob, parents, prep, kids, kid_ub, Qb.quota + 1, smem);

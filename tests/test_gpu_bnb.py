@@ -150,7 +150,7 @@ def test_batch_matches_oracle_certificates(ctx, oracle_mod):
         mix = oracle_mod.Mixtures.from_problem(p)
         assert oracle_mod.objective_r(mix, r["r"], r["t"]) == pytest.approx(r["f"], rel=1e-10)
         assert r["sma_calls"] >= 1
-    assert res[0]["block_size"] in (64, 128, 256, 512, 1024)
+    assert res[0]["block_size"] in (32, 64, 128, 256, 512, 1024)
 
 
 def test_batch_noise_free_recovery(ctx, oracle_mod):
