@@ -23,7 +23,20 @@
 
 namespace gosma {
 
+// Threads per seed: about 2,048 threads per SM in all, i.e. 2048 SMs / seeds
+// rounded down to a power of two in [128, 1024] (at most 512 for the FP64
+// search, whose threads need more registers), and at most one thread per 16
+// pair terms of an evaluation: few seeds of large mixtures spread every
+// evaluation over many threads, many seeds or small mixtures fill the SMs
+// with small blocks.
 constexpr int SMA_BLOCK = 128;
+
+__host__ inline int sma_block_for(int count, int sm_count, bool f64, int n1, int n2) {
+    const long long pairs = (long long)n1 * (n1 + 1) / 2 + (long long)n1 * n2;
+    int b = SMA_BLOCK;
+    while (b < (f64 ? 512 : 1024) && (long long)count * 2 * b <= 2048LL * sm_count && 32LL * b <= pairs) b *= 2;
+    return b;
+}
 constexpr int SMA_M = 8;  // L-BFGS memory
 
 // L-BFGS state of the block's current seed (shared memory; thread 0 writes).
@@ -176,8 +189,9 @@ __device__ __forceinline__ void two_sum_add(float &s, float &c, float x) {
 // f, df/dr, df/dt at the pose xs (shared) with FP32 terms.  Thread 0 writes
 // out (7 doubles: f, df/dr, df/dt) and *mag (sum of |weighted terms|).
 // Every thread must call it; it ends with a barrier.
+template <int B>
 __device__ void sma_eval32(const MixDev &mx, const Sma32Tab &tb, const double *xs, double *out, double *mag,
-                           float (*red)[SMA_BLOCK / 32]) {
+                           float (*red)[B / 32]) {
     const int tid = threadIdx.x, n1 = mx.n1, n2 = mx.n2;
     float R[9];
     rodrigues32(xs, R);
@@ -187,7 +201,7 @@ __device__ void sma_eval32(const MixDev &mx, const Sma32Tab &tb, const double *x
         th[k] = (float)xs[3 + k];
         tl[k] = (float)(xs[3 + k] - (double)th[k]);
     }
-    for (int i = tid; i < n1; i += SMA_BLOCK) {
+    for (int i = tid; i < n1; i += B) {
         const float m0 = (mx.mu1h[3 * i] - th[0]) + (mx.mu1l[3 * i] - tl[0]);
         const float m1 = (mx.mu1h[3 * i + 1] - th[1]) + (mx.mu1l[3 * i + 1] - tl[1]);
         const float m2 = (mx.mu1h[3 * i + 2] - th[2]) + (mx.mu1l[3 * i + 2] - tl[2]);
@@ -196,7 +210,7 @@ __device__ void sma_eval32(const MixDev &mx, const Sma32Tab &tb, const double *x
         tb.ma[i] = make_float4(m0 * id, m1 * id, m2 * id, id);
         tb.mb[i] = make_float4(k, phiz32(k), cothm1_32(k), -2.f * (k - 1.f) * id);
     }
-    for (int j = tid; j < n2; j += SMA_BLOCK) {
+    for (int j = tid; j < n2; j += B) {
         const float u0 = mx.mu2h[3 * j], u1 = mx.mu2h[3 * j + 1], u2 = mx.mu2h[3 * j + 2];
         tb.ja[j] = make_float4(R[0] * u0 + R[3] * u1 + R[6] * u2, R[1] * u0 + R[4] * u1 + R[7] * u2,
                                R[2] * u0 + R[5] * u1 + R[8] * u2, mx.kappa2[j]);
@@ -205,9 +219,9 @@ __device__ void sma_eval32(const MixDev &mx, const Sma32Tab &tb, const double *x
     float fs = 0.f, fc = 0.f, fa = 0.f, gt0 = 0.f, gt1 = 0.f, gt2 = 0.f, gw0 = 0.f, gw1 = 0.f, gw2 = 0.f;
     // self pairs i <= j (weight 2 off the diagonal) over the flattened square
     {
-        const int nn = n1 * n1, si = SMA_BLOCK / n1, sj = SMA_BLOCK % n1;
+        const int nn = n1 * n1, si = B / n1, sj = B % n1;
         int i = tid / n1, j = tid % n1;
-        for (int q = tid; q < nn; q += SMA_BLOCK) {
+        for (int q = tid; q < nn; q += B) {
             if (j >= i && !(mx.cls1 && mx.cls1[i] != mx.cls1[j])) {
                 const float4 A = tb.ma[i], Ab = tb.mb[i], B = tb.ma[j], Bb = tb.mb[j];
                 const float e0 = A.x - B.x, e1 = A.y - B.y, e2 = A.z - B.z;
@@ -233,9 +247,9 @@ __device__ void sma_eval32(const MixDev &mx, const Sma32Tab &tb, const double *x
     }
     // cross pairs in the model frame: u = v_i, w = R^T mu_2j
     {
-        const int nn = n1 * n2, si = SMA_BLOCK / n2, sj = SMA_BLOCK % n2;
+        const int nn = n1 * n2, si = B / n2, sj = B % n2;
         int i = tid / n2, j = tid % n2;
-        for (int q = tid; q < nn; q += SMA_BLOCK) {
+        for (int q = tid; q < nn; q += B) {
             if (!(mx.cls1 && mx.cls1[i] != mx.cls2[j])) {
                 const float4 A = tb.ma[i], Ab = tb.mb[i], W = tb.ja[j];
                 const float2 Wb = tb.jb[j];
@@ -277,7 +291,7 @@ __device__ void sma_eval32(const MixDev &mx, const Sma32Tab &tb, const double *x
     if (tid == 0) {
         float f0 = red[0][0], f1 = red[1][0], fab = red[2][0], g[6];
         for (int k = 0; k < 6; ++k) g[k] = red[3 + k][0];
-        for (int w = 1; w < SMA_BLOCK / 32; ++w) {
+        for (int w = 1; w < B / 32; ++w) {
             two_sum_add(f0, f1, red[0][w]);
             f1 += red[1][w];
             fab += red[2][w];
@@ -295,16 +309,17 @@ __device__ void sma_eval32(const MixDev &mx, const Sma32Tab &tb, const double *x
 // ---------------------------------------------------------------- FP64 evaluation
 // Same outputs through the FP64 pair terms; rows is this block's n1 x
 // OBJ_STRIDE scratch.
+template <int B>
 __device__ void sma_eval64(const MixDev &mx, double *rows, double *Rs, const double *xs, double *out, double *mag,
-                           double (*red)[SMA_BLOCK / 32]) {
+                           double (*red)[B / 32]) {
     const int tid = threadIdx.x, n1 = mx.n1;
     if (tid == 0) rodrigues_dev(xs, Rs);
     __syncthreads();
-    for (int i = tid; i < n1; i += SMA_BLOCK) obj_row(mx, Rs, xs + 3, i, rows + (size_t)i * OBJ_STRIDE);
+    for (int i = tid; i < n1; i += B) obj_row(mx, Rs, xs + 3, i, rows + (size_t)i * OBJ_STRIDE);
     __syncthreads();
     double acc[7] = {0, 0, 0, 0, 0, 0, 0};
     const long long total = (long long)n1 * n1 + (long long)n1 * mx.n2;
-    for (long long q = tid; q < total; q += SMA_BLOCK) obj_pair(mx, rows, Rs, q, acc);
+    for (long long q = tid; q < total; q += B) obj_pair(mx, rows, Rs, q, acc);
     for (int k = 0; k < 7; ++k)
         for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_down_sync(0xffffffffu, acc[k], o);
     if ((tid & 31) == 0)
@@ -312,7 +327,7 @@ __device__ void sma_eval64(const MixDev &mx, double *rows, double *Rs, const dou
     __syncthreads();
     if (tid == 0) {
         double s[7] = {0, 0, 0, 0, 0, 0, 0};
-        for (int w = 0; w < SMA_BLOCK / 32; ++w)
+        for (int w = 0; w < B / 32; ++w)
             for (int k = 0; k < 7; ++k) s[k] += red[k][w];
         obj_finish(xs, s, out);
         *mag = fabs(s[0]);
@@ -418,12 +433,13 @@ __device__ void lbfgs_accept(SmaState &st) {
     }
 }
 
+template <int B>
 __device__ __forceinline__ bool sma_feasible(const MixDev &mx, const SmaBox &box, const double *x) {
     int bad = 0;
     if (threadIdx.x == 0)
         for (int k = 0; k < 3; ++k)
             if (x[3 + k] < box.t_lo[k] || x[3 + k] > box.t_hi[k]) bad = 1;
-    for (int i = threadIdx.x; i < mx.n1; i += SMA_BLOCK) {
+    for (int i = threadIdx.x; i < mx.n1; i += B) {
         const double *mu = mx.mu1 + 3 * i;
         double d0 = mu[0] - x[3], d1 = mu[1] - x[4], d2 = mu[2] - x[5];
         if (d0 * d0 + d1 * d1 + d2 * d2 < box.zeta2) bad = 1;
@@ -460,8 +476,8 @@ struct SmaMany {
 // Every loop is bounded: at most max_iter iterations of at most `halvings`
 // trial poses each.  The dynamic shared memory holds the FP32 tables of the
 // largest mixture (FP32 search); rows64 one FP64 table per block (FP64).
-template <bool F64, class Src>
-__global__ void __launch_bounds__(SMA_BLOCK, F64 ? 1 : 8) sma_kernel(Src src, int count, const double *__restrict__ x0, int max_iter,
+template <bool F64, class Src, int B>
+__global__ void __launch_bounds__(B, F64 || B > SMA_BLOCK ? 1 : 8) sma_kernel(Src src, int count, const double *__restrict__ x0, int max_iter,
                                                         double *__restrict__ xout, int *__restrict__ iters,
                                                         double *__restrict__ rows64, int max_n1, int *__restrict__ counter) {
     extern __shared__ float4 sma_smem[];
@@ -470,8 +486,8 @@ __global__ void __launch_bounds__(SMA_BLOCK, F64 ? 1 : 8) sma_kernel(Src src, in
     __shared__ SmaBox box;
     __shared__ double fg[7];
     __shared__ int slot;
-    __shared__ float red32[9][SMA_BLOCK / 32];
-    __shared__ double red64[7][SMA_BLOCK / 32];
+    __shared__ float red32[9][B / 32];
+    __shared__ double red64[7][B / 32];
     const int tid = threadIdx.x;
     constexpr int halvings = F64 ? 40 : 20;
     Sma32Tab tb;
@@ -481,8 +497,8 @@ __global__ void __launch_bounds__(SMA_BLOCK, F64 ? 1 : 8) sma_kernel(Src src, in
     auto eval = [&](bool trial) {
         double mag = 0.0;
         const double *xs = trial ? st.xn : st.x;
-        if (F64) sma_eval64(mx, rows, st.R, xs, fg, &mag, red64);
-        else sma_eval32(mx, tb, xs, fg, &mag, red32);
+        if (F64) sma_eval64<B>(mx, rows, st.R, xs, fg, &mag, red64);
+        else sma_eval32<B>(mx, tb, xs, fg, &mag, red32);
         if (tid == 0) {
             if (trial) {
                 st.fn = fg[0];
@@ -506,8 +522,8 @@ __global__ void __launch_bounds__(SMA_BLOCK, F64 ? 1 : 8) sma_kernel(Src src, in
             __syncthreads();
             if (!F64) {
                 tb = sma32_carve(sma_smem, mx.n1, mx.n2);
-                for (int i = tid; i < mx.n1; i += SMA_BLOCK) tb.phi1[i] = mx.phi1f[i];
-                for (int j = tid; j < mx.n2; j += SMA_BLOCK)
+                for (int i = tid; i < mx.n1; i += B) tb.phi1[i] = mx.phi1f[i];
+                for (int j = tid; j < mx.n2; j += B)
                     tb.jb[j] = make_float2(phiz32((float)mx.kappa2d[j]), (float)mx.phi2d[j]);
             }
             loaded = prob;
@@ -515,7 +531,7 @@ __global__ void __launch_bounds__(SMA_BLOCK, F64 ? 1 : 8) sma_kernel(Src src, in
         if (tid < 6) st.x[tid] = x0[6 * s + tid];
         if (tid == 0) st.head = st.used = 0;
         __syncthreads();
-        if (!sma_feasible(mx, box, st.x)) {
+        if (!sma_feasible<B>(mx, box, st.x)) {
             if (tid < 6) xout[6 * s + tid] = st.x[tid];
             if (tid == 0) iters[s] = -1;
             continue;
@@ -532,7 +548,7 @@ __global__ void __launch_bounds__(SMA_BLOCK, F64 ? 1 : 8) sma_kernel(Src src, in
                 __syncthreads();
                 if (tid < 6) st.xn[tid] = st.x[tid] + st.step * st.d[tid];
                 __syncthreads();
-                if (sma_feasible(mx, box, st.xn)) {
+                if (sma_feasible<B>(mx, box, st.xn)) {
                     eval(true);
                     if (tid == 0) st.flag = st.fn <= st.f + 1e-4 * st.step * st.slope;  // Armijo
                     __syncthreads();
@@ -659,10 +675,10 @@ static int objective_records(gosma_ctx *ctx, int count, const double *d_x, doubl
 
 // Dynamic shared memory and persistent grid of the SMA kernel.  Errors are
 // recorded on ectx (NULL: not recorded, for calls from a worker thread).
-template <bool F64, class Src>
+template <bool F64, class Src, int B>
 static int sma_config(gosma_ctx *ctx, gosma_ctx *ectx, int max_n1, int max_n2, int count, int *grid, size_t *smem) {
     *smem = F64 ? 0 : sma32_smem_bytes(max_n1, max_n2);
-    auto kern = sma_kernel<F64, Src>;
+    auto kern = sma_kernel<F64, Src, B>;
     if (*smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
         if (e != cudaSuccess) {
@@ -671,7 +687,7 @@ static int sma_config(gosma_ctx *ctx, gosma_ctx *ectx, int max_n1, int max_n2, i
         }
     }
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SMA_BLOCK, *smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, B, *smem);
     if (e != cudaSuccess) return cuda_fail(ectx, e, "occupancy(sma)");
     if (per_sm < 1) return fail(ectx, GOSMA_EINVAL, "sma: mixtures too large for one block's shared memory");
     long long g = (long long)ctx->sm_count * per_sm;
@@ -679,17 +695,48 @@ static int sma_config(gosma_ctx *ctx, gosma_ctx *ectx, int max_n1, int max_n2, i
     return GOSMA_OK;
 }
 
-template <bool F64, class Src>
+template <bool F64, class Src, int B>
 static int sma_run(gosma_ctx *ectx, cudaStream_t st, const Src &src, int grid, size_t smem, int count,
                    const double *d_x0, int max_iter, double *d_x, int *d_it, double *d_rows, int max_n1,
                    int *d_counter, long long *launches) {
     cudaError_t e = cudaMemsetAsync(d_counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return cuda_fail(ectx, e, "memset(sma counter)");
-    sma_kernel<F64, Src><<<grid, SMA_BLOCK, smem, st>>>(src, count, d_x0, max_iter, d_x, d_it, d_rows, max_n1,
+    sma_kernel<F64, Src, B><<<grid, B, smem, st>>>(src, count, d_x0, max_iter, d_x, d_it, d_rows, max_n1,
                                                         d_counter);
     ++*launches;
     e = cudaGetLastError();
     return e == cudaSuccess ? GOSMA_OK : cuda_fail(ectx, e, "launch(sma)");
+}
+
+// sma_config / sma_run for the block size b chosen at run time.
+template <bool F64, class Src>
+static int sma_plan(gosma_ctx *ctx, gosma_ctx *ectx, int b, int max_n1, int max_n2, int count, int *grid,
+                    size_t *smem) {
+    switch (b) {
+    case 128: return sma_config<F64, Src, 128>(ctx, ectx, max_n1, max_n2, count, grid, smem);
+    case 256: return sma_config<F64, Src, 256>(ctx, ectx, max_n1, max_n2, count, grid, smem);
+    case 512: return sma_config<F64, Src, 512>(ctx, ectx, max_n1, max_n2, count, grid, smem);
+    default: return sma_config<F64, Src, (F64 ? 512 : 1024)>(ctx, ectx, max_n1, max_n2, count, grid, smem);
+    }
+}
+template <bool F64, class Src>
+static int sma_go(gosma_ctx *ectx, int b, cudaStream_t st, const Src &src, int grid, size_t smem, int count,
+                  const double *d_x0, int max_iter, double *d_x, int *d_it, double *d_rows, int max_n1,
+                  int *d_counter, long long *launches) {
+    switch (b) {
+    case 128:
+        return sma_run<F64, Src, 128>(ectx, st, src, grid, smem, count, d_x0, max_iter, d_x, d_it, d_rows, max_n1,
+                                      d_counter, launches);
+    case 256:
+        return sma_run<F64, Src, 256>(ectx, st, src, grid, smem, count, d_x0, max_iter, d_x, d_it, d_rows, max_n1,
+                                      d_counter, launches);
+    case 512:
+        return sma_run<F64, Src, 512>(ectx, st, src, grid, smem, count, d_x0, max_iter, d_x, d_it, d_rows, max_n1,
+                                      d_counter, launches);
+    default:
+        return sma_run<F64, Src, (F64 ? 512 : 1024)>(ectx, st, src, grid, smem, count, d_x0, max_iter, d_x, d_it,
+                                                     d_rows, max_n1, d_counter, launches);
+    }
 }
 
 // FP32-search SMA of count seeds, seed s on problem d_pid[s] (the batched
@@ -701,10 +748,12 @@ int sma_refine_many(gosma_ctx *ctx, cudaStream_t st, const MixDev *d_mixes, cons
     if (count <= 0) return GOSMA_OK;
     int grid = 0;
     size_t smem = 0;
-    int rc = sma_config<false, SmaMany>(ctx, nullptr, max_n1, max_n2, count, &grid, &smem);
+    const SmaMany src{d_mixes, d_boxes, d_pid};
+    const int b = sma_block_for(count, ctx->sm_count, false, max_n1, max_n2);
+    int rc = sma_plan<false, SmaMany>(ctx, nullptr, b, max_n1, max_n2, count, &grid, &smem);
     if (rc) return rc;
-    return sma_run<false, SmaMany>(nullptr, st, SmaMany{d_mixes, d_boxes, d_pid}, grid, smem, count, d_x0, max_iter, d_x,
-                                   d_it, nullptr, max_n1, d_counter, launches);
+    return sma_go<false, SmaMany>(nullptr, b, st, src, grid, smem, count, d_x0, max_iter, d_x, d_it, nullptr, max_n1,
+                                  d_counter, launches);
 }
 
 }  // namespace gosma
@@ -726,8 +775,9 @@ extern "C" int gosma_sma_batch(gosma_ctx *ctx, int count, const double *x0, int 
     const int n1 = ctx->n1, n2 = ctx->n2;
     int grid = 0;
     size_t smem = 0;
-    int rc = f64 ? sma_config<true, SmaOne>(ctx, ctx, n1, n2, count, &grid, &smem)
-                 : sma_config<false, SmaOne>(ctx, ctx, n1, n2, count, &grid, &smem);
+    const int b = sma_block_for(count, ctx->sm_count, f64, n1, n2);
+    int rc = f64 ? sma_plan<true, SmaOne>(ctx, ctx, b, n1, n2, count, &grid, &smem)
+                 : sma_plan<false, SmaOne>(ctx, ctx, b, n1, n2, count, &grid, &smem);
     if (rc) return rc;
 
     // device scratch: seeds and poses (host calls), iterations, counter,
@@ -799,10 +849,11 @@ extern "C" int gosma_sma_batch(gosma_ctx *ctx, int count, const double *x0, int 
     e = cudaMemcpyAsync(d_xs + 6 * (size_t)count, d_x0, sizeof(double) * 6 * (size_t)count, cudaMemcpyDeviceToDevice,
                         st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "copy seeds");
-    rc = f64 ? sma_run<true>(ctx, st, one, grid, smem, count, d_x0, max_iter, d_xs, d_it, d_rows, n1, d_counter,
-                             &ctx->launches)
-             : sma_run<false>(ctx, st, one, grid, smem, count, d_x0, max_iter, d_xs, d_it, d_rows, n1, d_counter,
-                              &ctx->launches);
+    long long *nl = &ctx->launches;
+    rc = f64 ? sma_go<true, SmaOne>(ctx, b, st, one, grid, smem, count, d_x0, max_iter, d_xs, d_it, d_rows, n1,
+                                    d_counter, nl)
+             : sma_go<false, SmaOne>(ctx, b, st, one, grid, smem, count, d_x0, max_iter, d_xs, d_it, d_rows, n1,
+                                     d_counter, nl);
     if (rc) return rc;
     if (!grad) {
         logz_table<<<(n2 + 127) / 128, 128, 0, st>>>(ctx->mix, d_lz);

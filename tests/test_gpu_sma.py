@@ -75,6 +75,26 @@ def test_fp64_short_paths_match_oracle(ctx, oracle_mod, name, k):
         assert abs(r["f"][s] - f1) <= 1e-7 * (1 + abs(f1)), (s, r["f"][s], f1)
 
 
+def test_many_seeds_use_narrow_blocks(ctx, oracle_mod):
+    """With at least as many seeds as SMs every seed gets a 128-thread block
+    (fewer seeds get one wide block each): FP64 short paths still equal the
+    oracle's, checked on every 16th of 304 seeds."""
+    p = PROBLEMS["tiny1000"]()
+    ctx.set_problem(p)
+    mix = oracle_mod.Mixtures.from_problem(p)
+    x0 = synth.pose_seeds(p, 304, 21)
+    r = ctx.sma_batch(x0, 3, 64)
+    for s in range(0, len(x0), 16):
+        x1, f1, _ = _oracle_sma(oracle_mod, mix, p, x0[s], 3)
+        if not np.isfinite(f1):
+            assert r["iters"][s] == -1
+            continue
+        assert np.max(np.abs(r["x"][s] - x1)) <= 1e-6
+        assert abs(r["f"][s] - f1) <= 1e-7 * (1 + abs(f1))
+    r32 = ctx.sma_batch(x0, 100, 32)
+    _check_run(p, mix, oracle_mod, x0[::16], {k: v[::16] for k, v in r32.items()}, 100)
+
+
 @pytest.mark.parametrize("prec", [32, 64])
 def test_zero_iterations_return_the_seeds(ctx, oracle_mod, prec):
     p = PROBLEMS["tiny1000"]()
