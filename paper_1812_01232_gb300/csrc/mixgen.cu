@@ -152,7 +152,8 @@ template <bool VMF>
 __global__ void __launch_bounds__(MG_BLOCK) mg_cluster(int n, const double *__restrict__ xq,
                                                        const long long *__restrict__ q,
                                                        const float4 *__restrict__ xf, float E, double lam, int max_iter,
-                                                       int kmax, double *cen, int *lab, double *best, int *arg,
+                                                       int kmax, double *cen, int *lab, double *best, float *bestf,
+                                                       int *arg,
                                                        unsigned long long *sums, unsigned long long *cnt, int *first,
                                                        int *remap, MgState *S) {
     cg::grid_group grid = cg::this_grid();
@@ -216,6 +217,7 @@ __global__ void __launch_bounds__(MG_BLOCK) mg_cluster(int n, const double *__re
                 }
             }
             best[i] = bv;
+            bestf[i] = (float)bv;
             arg[i] = a;
         }
         grid.sync();
@@ -254,11 +256,14 @@ __global__ void __launch_bounds__(MG_BLOCK) mg_cluster(int n, const double *__re
                     arg[i] = c;
                     continue;
                 }
-                const double s32 = mg_score32<VMF>(xf[i], mv), bi = best[i];
-                if (VMF ? s32 + E <= bi : s32 - E >= bi) continue;  // cannot beat the current centre
+                // cannot beat the current centre: FP32 test with 1.25 E (rounding
+                // bestf and the difference each costs less than E / 10)
+                const float s32 = mg_score32<VMF>(xf[i], mv), bf = bestf[i];
+                if (VMF ? s32 + 1.25f * E <= bf : s32 - 1.25f * E >= bf) continue;
                 const double s = mg_score<VMF>(xq + 3 * i, m);
-                if (mg_better<VMF>(s, bi)) {
+                if (mg_better<VMF>(s, best[i])) {
                     best[i] = s;
+                    bestf[i] = (float)s;
                     arg[i] = c;
                 }
             }
@@ -384,11 +389,12 @@ static int mg_run(gosma_ctx *ctx, int n, const double *h_x, double lam, int max_
     const size_t b_x = al(sizeof(double) * 3 * (size_t)n), b_q = al(sizeof(long long) * 3 * (size_t)n),
                  b_xf = al(sizeof(float4) * (size_t)n),
                  b_n = al(sizeof(int) * (size_t)n), b_best = al(sizeof(double) * (size_t)n),
+                 b_bestf = al(sizeof(float) * (size_t)n),
                  b_cen = al(sizeof(double) * 3 * (size_t)kmax), b_sums = al(sizeof(unsigned long long) * 3 * (size_t)kmax),
                  b_k = al(sizeof(unsigned long long) * (size_t)kmax), b_ki = al(sizeof(int) * (size_t)kmax),
                  b_kd = al(sizeof(double) * (size_t)kmax), b_st = al(sizeof(MgState));
     // x, xq, q, xf, lab, arg, best, cen, sums, cnt, first, remap, ss, spread, phi, state
-    const size_t need = 2 * b_x + b_q + b_xf + 2 * b_n + b_best + b_cen + b_sums + b_k + 2 * b_ki + 3 * b_kd + b_st;
+    const size_t need = 2 * b_x + b_q + b_xf + 2 * b_n + b_best + b_bestf + b_cen + b_sums + b_k + 2 * b_ki + 3 * b_kd + b_st;
     if (need > ctx->mg_bytes) {
         if (ctx->d_mg) cudaFree(ctx->d_mg);
         ctx->d_mg = nullptr;
@@ -412,6 +418,8 @@ static int mg_run(gosma_ctx *ctx, int n, const double *h_x, double lam, int max_
     p += b_n;
     double *d_best = (double *)p;
     p += b_best;
+    float *d_bestf = (float *)p;
+    p += b_bestf;
     double *d_cen = (double *)p;
     p += b_cen;
     unsigned long long *d_sums = (unsigned long long *)p;
@@ -463,7 +471,8 @@ static int mg_run(gosma_ctx *ctx, int n, const double *h_x, double lam, int max_
     if (grid > need_blocks) grid = need_blocks;
     void *args[] = {(void *)&n,      (void *)&d_xq,  (void *)&d_q,   (void *)&d_xf,    (void *)&E,
                     (void *)&lam,    (void *)&max_iter,
-                    (void *)&kmax,   (void *)&d_cen, (void *)&d_lab, (void *)&d_best,  (void *)&d_arg,
+                    (void *)&kmax,   (void *)&d_cen, (void *)&d_lab, (void *)&d_best,  (void *)&d_bestf,
+                    (void *)&d_arg,
                     (void *)&d_sums, (void *)&d_cnt, (void *)&d_first, (void *)&d_remap, (void *)&d_st};
     e = cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(MG_BLOCK), args, smem, st);
     ++ctx->launches;
