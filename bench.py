@@ -454,7 +454,7 @@ def run_time_to_certified(n_prob):
     probs = [synth.tiny_problem(200000 + s) for s in range(n_prob)]
     out = {"workload": "%d tiny problems (10 x 8 components), eps 1e-3, queue 2^26 per problem; single-problem "
                        "solver with its automatic pop (65536 sub-cubes per iteration for 10 x 8), batched solvers "
-                       "with pop %d per problem (their maximum)" % (n_prob, POP)}
+                       "with pop %d per problem" % (n_prob, POP)}
     single = []
     t0 = time.perf_counter()
     for p in probs:
