@@ -238,7 +238,7 @@ int gosma_sma_batch(gosma_ctx *ctx, int count, const double *x0, int max_iter, i
  * deterministic and equals a serial double-precision run of the same steps.
  * Fit: phi_k = n_k / n, mu_k the mean, sigma_k = sqrt(sum |x - mu_k|^2 /
  * (3 n_k)) floored at sigma_min.
- * x: n x 3 host array, n >= 1, n * max|x| < 2^30.  lambda > 0 (squared
+ * x: n x 3 host array, 1 <= n <= 2^26, n * max|x| < 2^30.  lambda > 0 (squared
  * distance), max_iter >= 1, 1 <= kmax <= 8192, sigma_min > 0.
  * Outputs (host): *k clusters; mu (kmax x 3), sigma (kmax), phi (kmax), of
  * which the first *k entries are written; labels (n, or NULL) the cluster of

@@ -515,6 +515,7 @@ static int mg_check(gosma_ctx *ctx, int n, const double *x, int max_iter, int km
     if (!ctx) return GOSMA_EINVAL;
     ctx->err.clear();
     if (n < 1 || !x) return fail(ctx, GOSMA_EINVAL, "mixture generation: need n >= 1 points");
+    if (n > (1 << 26)) return fail(ctx, GOSMA_EINVAL, "mixture generation: at most 2^26 points");  // 32-bit indexing
     if (max_iter < 1) return fail(ctx, GOSMA_EINVAL, "mixture generation: max_iter must be >= 1");
     if (kmax < 1 || kmax > MG_KMAX) return fail(ctx, GOSMA_EINVAL, "mixture generation: kmax must be in [1, 8192]");
     if (!k || !mu || !spread || !phi) return fail(ctx, GOSMA_EINVAL, "mixture generation: null output");
