@@ -133,6 +133,11 @@ const char *gosma_last_error(const gosma_ctx *ctx);
  * (Sec. 4, Eq. GMM, Eq. vMFMM).  Deep-copies the arrays.  GOSMA_EINVAL when
  * n < 1, sigma <= 0, kappa <= 0, a weight < 0, |sum(phi) - 1| > 1e-9 or
  * ||mu2_j| - 1| > 1e-6. */
+/* New mixtures or a new domain (gosma_set_mixtures, _classes, gosma_set_domain)
+ * end a branch-and-bound run in progress: gosma_bnb_step, gosma_bnb_save and
+ * gosma_bnb_set_incumbent then return GOSMA_ENOTREADY until the next
+ * gosma_bnb_start or gosma_bnb_load; gosma_bnb_history still reads the
+ * ended run. */
 int gosma_set_mixtures(gosma_ctx *ctx, int n1, const double *mu1, const double *sigma1, const double *phi1, int n2,
                        const double *mu2, const double *kappa2, const double *phi2);
 
@@ -386,6 +391,18 @@ typedef struct {
  * copied to out (max_points = 0: count only).  A resumed run starts a new
  * history. */
 int gosma_bnb_history(gosma_ctx *ctx, long long max_points, gosma_trace_point *out, long long *count);
+
+/* Offer an incumbent found elsewhere to the run in progress (between
+ * gosma_bnb_step calls): another shard of the same problem, or a caller's own
+ * refinement.  x: the pose (r then t, 6 doubles), f its objective value, which
+ * the caller guarantees (the run does not re-evaluate it).  When f < d*, d*
+ * and the best pose become (f, x): the next iterations prune against f and
+ * Algorithm 1's stopping test uses it; otherwise nothing changes.  Used by
+ * the sharded solve across GPUs, where every rank searches a slab of the
+ * translation domain and the ranks exchange (d*, lower bound) between steps.
+ * GOSMA_ENOTREADY without a run in progress, GOSMA_EINVAL for a NaN f or a
+ * null x. */
+int gosma_bnb_set_incumbent(gosma_ctx *ctx, double f, const double x[6]);
 
 /* Checkpoint of a run between two gosma_bnb_step calls: the solver record,
  * the incumbent and its pose, and every queue slot (keys and sub-cubes) go

@@ -239,6 +239,7 @@ static int set_mixtures_impl(gosma_ctx *ctx, int nclass, const int *n1c, const i
     ctx->h_kappa2.assign(kappa2, kappa2 + n2);
     ctx->h_phi2 = phi2;
     ctx->have_mix = true;
+    bnb_end_run(ctx);
     return GOSMA_OK;
 }
 
@@ -276,6 +277,7 @@ int gosma_set_domain(gosma_ctx *ctx, const double t_lo[3], const double t_hi[3],
     ctx->zeta = zeta;
     ctx->mix.zeta = zeta;
     ctx->have_dom = true;
+    bnb_end_run(ctx);
     return GOSMA_OK;
 }
 

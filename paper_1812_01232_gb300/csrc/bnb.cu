@@ -685,6 +685,14 @@ static void delete_solve(Solve *v) {
 
 static Solve *solve_of(gosma_ctx *ctx) { return ctx->bnb ? ((BnbState *)ctx->bnb)->solve : nullptr; }
 
+// New mixtures or a new domain end the run in progress (its history stays
+// readable): stepping, saving or offering an incumbent then needs a new
+// gosma_bnb_start.
+void bnb_end_run(gosma_ctx *ctx) {
+    Solve *v = solve_of(ctx);
+    if (v) v->active = false;
+}
+
 static void fill_result(gosma_ctx *ctx, const Solve &v, gosma_result *out) {
     memset(out, 0, sizeof *out);
     double best[6];
@@ -1069,4 +1077,25 @@ extern "C" int gosma_bnb_history(gosma_ctx *ctx, long long max_points, gosma_tra
     *count = n;
     if (max_points > 0) memcpy(out, vp->history.data(), sizeof(gosma_trace_point) * (size_t)(n < max_points ? n : max_points));
     return GOSMA_OK;
+}
+
+// An incumbent found elsewhere (another shard of the same problem, a caller's
+// own refinement): d* becomes f when f is smaller, so that the next
+// iterations prune against it and the stopping test of Algorithm 1 uses it.
+extern "C" int gosma_bnb_set_incumbent(gosma_ctx *ctx, double f, const double x[6]) {
+    if (!ctx) return GOSMA_EINVAL;
+    ctx->err.clear();
+    Solve *vp = solve_of(ctx);
+    if (!vp || !vp->active) return fail(ctx, GOSMA_ENOTREADY, "bnb_set_incumbent: call gosma_bnb_start first");
+    if (!x || std::isnan(f)) return fail(ctx, GOSMA_EINVAL, "bnb_set_incumbent: bad incumbent");
+    Solve &v = *vp;
+    if (!(f < v.dstar)) return GOSMA_OK;
+    BnbState *s = (BnbState *)ctx->bnb;
+    cudaSetDevice(ctx->device);
+    v.dstar = f;
+    memcpy(v.best, x, sizeof v.best);
+    if (v.dlb > v.dstar) v.dlb = v.dstar;
+    cudaError_t e = cudaMemcpyAsync(s->dstar, &v.dstar, sizeof v.dstar, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    return e == cudaSuccess ? GOSMA_OK : cuda_fail(ctx, e, "bnb_set_incumbent");
 }

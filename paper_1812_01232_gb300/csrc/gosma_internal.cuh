@@ -205,4 +205,5 @@ int sma_refine_many(gosma_ctx *ctx, cudaStream_t st, const MixDev *d_mixes, cons
                     int max_n1, int max_n2, int count, const double *d_x0, int max_iter, double *d_x, int *d_it,
                     int *d_counter, long long *launches);
 void bnb_release(gosma_ctx *ctx);
+void bnb_end_run(gosma_ctx *ctx);
 }  // namespace gosma

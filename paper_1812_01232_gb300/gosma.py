@@ -95,6 +95,7 @@ SIGNATURES = {
                                            C.c_void_p, C.c_void_p]),
     "gosma_bnb_step": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(Result)]),
     "gosma_bnb_history": (C.c_int, [C.c_void_p, C.c_longlong, C.c_void_p, C.POINTER(C.c_longlong)]),
+    "gosma_bnb_set_incumbent": (C.c_int, [C.c_void_p, C.c_double, D]),
     "gosma_bnb_save": (C.c_int, [C.c_void_p, C.c_char_p]),
     "gosma_bnb_load": (C.c_int, [C.c_void_p, C.c_char_p]),
     "gosma_selftest_approx": (C.c_int, [C.c_void_p, D, D]),
@@ -453,6 +454,11 @@ class Gosma:
         self._check(self.L.gosma_mlp_train(self.h, len(x), _pf(x), _pf(label), _pf(target), int(batch), int(steps),
                                            float(lr), float(lam), _pf(losses)), "mlp_train")
         return losses[:steps]
+
+    def bnb_set_incumbent(self, f, x):
+        """Offer (f, x) as an incumbent to the run in progress; d* becomes f if smaller."""
+        x = _f64(x, (6,))
+        self._check(self.L.gosma_bnb_set_incumbent(self.h, float(f), _p(x)), "bnb_set_incumbent")
 
     def bnb_history(self):
         """Per-iteration (iteration, seconds, dstar, lower_bound, queue_size, nodes) of the run (Fig. 5)."""

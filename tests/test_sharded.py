@@ -1,0 +1,159 @@
+"""The sharded solve of one problem across ranks (paper_1812_01232_gb300/sharded.py)
+on CPU: two gloo ranks, and the same ranks stepped in one process.  The
+ranks run a small branch-and-bound with the stepping interface of the
+library (start, step, offer an incumbent) on a toy objective over the
+translation box, so the test covers the slab split, the exchange of
+(d*, lower bound) and the global stopping test without a GPU."""
+import os
+import socket
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+from paper_1812_01232_gb300 import sharded  # noqa: E402
+
+
+class ToySolver:
+    """Best-first interval branch-and-bound of f(t) = |t - c|^2 + 0.3 sin(7 t0)
+    over a box, bounded by f(mid) - L(box) |half-widths| with L an upper bound
+    of |grad f| on the box; the interface of Gosma's stepping solver."""
+
+    def set_problem(self, p):
+        self.lo, self.hi, self.c = np.array(p["t_lo"], float), np.array(p["t_hi"], float), np.array(p["c"], float)
+        self.max_nodes = p.get("max_nodes", 0)
+
+    def _f(self, t):
+        return float(np.sum((t - self.c) ** 2) + 0.3 * np.sin(7.0 * t[0]))
+
+    def _box(self, lo, hi):
+        mid, hw = 0.5 * (lo + hi), 0.5 * (hi - lo)
+        L = 2.0 * (np.linalg.norm(mid - self.c) + np.linalg.norm(hw)) + 2.1
+        fm = self._f(mid)
+        return fm - L * np.linalg.norm(hw), fm, mid
+
+    def bnb_start(self, eps, **opts):
+        self.eps = eps
+        lb, fm, mid = self._box(self.lo, self.hi)
+        self.q = [(lb, self.lo, self.hi)]
+        self.dstar, self.best, self.nodes, self.status = fm, mid, 1, "running"
+
+    def bnb_set_incumbent(self, f, x):
+        if f < self.dstar:
+            self.dstar, self.best = f, np.array(x[3:], float)
+
+    def _result(self):
+        lb = min([b[0] for b in self.q], default=self.dstar)
+        return {"f": self.dstar, "lb": min(lb, self.dstar), "status_name": self.status, "nodes": self.nodes,
+                "r": np.zeros(3), "t": self.best.copy(), "c22": 1.0}
+
+    def bnb_step(self, n):
+        for _ in range(n):
+            self.q = [b for b in self.q if b[0] < self.dstar]
+            if not self.q:
+                self.status = "optimal"
+                break
+            lbmin = min(b[0] for b in self.q)
+            if self.dstar - lbmin <= self.eps:
+                self.status = "optimal"
+                break
+            if self.max_nodes and self.nodes >= self.max_nodes:
+                self.status = "node_limit"
+                break
+            k = int(np.argmin([b[0] for b in self.q]))
+            _, lo, hi = self.q.pop(k)
+            ax = int(np.argmax(hi - lo))
+            m = 0.5 * (lo[ax] + hi[ax])
+            for a, b in ((lo, np.where(np.arange(3) == ax, m, hi)), (np.where(np.arange(3) == ax, m, lo), hi)):
+                lb, fm, mid = self._box(a, b)
+                self.nodes += 1
+                if fm < self.dstar:
+                    self.dstar, self.best = fm, mid
+                self.q.append((lb, a, b))
+        return self._result()
+
+
+PROB = {"t_lo": [-1.0, -1.0, -0.5], "t_hi": [1.0, 1.0, 0.5], "c": [0.6, -0.2, 0.1]}
+
+
+def _single(eps):
+    s = ToySolver()
+    s.set_problem(PROB)
+    s.bnb_start(eps)
+    r = s.bnb_step(10 ** 6)
+    assert r["status_name"] == "optimal"
+    return r
+
+
+def test_slabs_cover_the_domain():
+    lo, hi = np.array([-2.0, -1.0, 0.0]), np.array([2.0, 1.0, 3.0])
+    for world in (1, 2, 3, 8):
+        parts = [sharded.slab(lo, hi, k, world) for k in range(world)]
+        assert parts[0][0][0] == lo[0] and parts[-1][1][0] == hi[0]
+        for k in range(world - 1):
+            assert parts[k][1][0] == parts[k + 1][0][0]  # neighbours meet exactly
+            np.testing.assert_array_equal(parts[k][0][1:], lo[1:])
+            np.testing.assert_array_equal(parts[k][1][1:], hi[1:])
+
+
+EPS = 0.05
+
+
+def test_local_shards_certify_the_global_optimum():
+    eps = EPS
+    one = _single(eps)
+    r = sharded.solve_local([ToySolver(), ToySolver(), ToySolver()], PROB, eps=eps, steps=5)
+    assert r["status_name"] == "optimal"
+    assert r["f"] - r["lb"] <= eps
+    assert abs(r["f"] - one["f"]) <= eps and r["lb"] <= one["f"] + 1e-12
+    assert r["rounds"] > 1
+
+
+def test_local_shards_report_a_limit():
+    r = sharded.solve_local([ToySolver(), ToySolver()], dict(PROB, max_nodes=40), eps=1e-9, steps=5)
+    assert r["status_name"] == "node_limit" and r["lb"] <= r["f"]
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _rank(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    from paper_1812_01232_gb300 import sharded as sh
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    r = sh.solve_distributed(ToySolver(), PROB, eps=EPS, steps=5)
+    dist.barrier()
+    dist.destroy_process_group()
+    q.put((rank, r["f"], r["lb"], r["status_name"], r["nodes"], list(r["t"])))
+
+
+def test_two_gloo_ranks_certify_the_global_optimum():
+    mp = pytest.importorskip("torch.multiprocessing")
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    one = _single(EPS)
+    # every rank returns the same global result, which certifies the optimum
+    assert out[0][1:] == out[1][1:]
+    _, f, lb, status, nodes, t = out[0]
+    assert status == "optimal" and f - lb <= EPS
+    assert abs(f - one["f"]) <= EPS and lb <= one["f"] + 1e-12
+    # the optimum lies in the slab t0 > 0 (c0 = 0.6): rank 0 learnt it in the exchange
+    assert t[0] > 0
