@@ -333,3 +333,33 @@ def test_sma_reaches_true_pose_from_nearby(oracle_mod):
     assert f1 <= f0
     assert f1 == pytest.approx(-oracle_mod.c22(mix), rel=1e-8)
     assert np.linalg.norm(x1[3:] - prob["t_gt"]) < 1e-4
+
+
+def test_sma_results_are_local_minima(oracle_mod):
+    """From seeds away from the optimum, an SMA result that stopped inside
+    the feasible set (not on the domain box or a zeta-sphere) is a local
+    minimum: no pose +-h along any of the 12 coordinate directions lowers f by
+    more than a rounding-level amount (h = 1e-4 and 1e-3)."""
+    prob = synth.tiny_problem(1003)
+    mix = oracle_mod.Mixtures.from_problem(prob)
+    x0s = synth.pose_seeds(prob, 24, 7)
+    checked = 0
+    for x0 in x0s:
+        x1, f1, _ = oracle_mod.sma(mix, x0, prob["t_lo"], prob["t_hi"], prob["zeta"], max_iter=300, memory=8,
+                                   gtol=1e-10)
+        if not np.isfinite(f1):
+            continue
+        t = x1[3:]
+        margin = min(np.min(t - prob["t_lo"]), np.min(prob["t_hi"] - t),
+                     np.min(np.linalg.norm(prob["mu1"] - t, axis=1)) - prob["zeta"])
+        if margin < 1e-2:
+            continue  # stopped against the boundary of the feasible set
+        assert f1 == pytest.approx(oracle_mod.objective_r(mix, x1[:3], x1[3:]), rel=1e-12)
+        for h in (1e-4, 1e-3):
+            for k in range(6):
+                for sgn in (-1.0, 1.0):
+                    x = x1.copy()
+                    x[k] += sgn * h
+                    assert oracle_mod.objective_r(mix, x[:3], x[3:]) >= f1 - 1e-9 * (1 + abs(f1)), (k, sgn, h)
+        checked += 1
+    assert checked >= 8
