@@ -35,9 +35,10 @@ Two more measurements ride on the same line (rank 0, N = 1, unless
   with the count);
 * "time_to_certified": tiny problems (10 x 8 components, eps 1e-3) solved
   to the certified optimum by the plain single-problem solver (one after the
-  other, automatic pop), the plain batched solver and the learned batched solver (network
+  other), the plain batched solver and the learned batched solver (network
   weights from paper_1812_01232_gb300/weights, scoring during the first 32
-  iterations, where the incumbent is found), on the same problems;
+  iterations, where the incumbent is found), on the same problems, each with
+  its automatic pop;
 * "sma": the batched device refinement (SMA, Sec. 5) of many seed poses of
   the 128 x 64 paper-scale problem (half near the true pose, half uniform),
   seeds refined per second with the FP32 and the FP64 search (CUDA events
@@ -452,9 +453,9 @@ def run_time_to_certified(n_prob):
     ctx = Gosma(0)
     eps = 1e-3
     probs = [synth.tiny_problem(200000 + s) for s in range(n_prob)]
-    out = {"workload": "%d tiny problems (10 x 8 components), eps 1e-3, queue 2^26 per problem; single-problem "
-                       "solver with its automatic pop (65536 sub-cubes per iteration for 10 x 8), batched solvers "
-                       "with pop %d per problem" % (n_prob, POP)}
+    out = {"workload": "%d tiny problems (10 x 8 components), eps 1e-3, queue 2^26 per problem; every solver "
+                       "with its automatic pop (65536 sub-cubes per iteration and problem for 10 x 8 mixtures)"
+                       % n_prob}
     single = []
     t0 = time.perf_counter()
     for p in probs:
@@ -466,7 +467,7 @@ def run_time_to_certified(n_prob):
     for name, learned in (("plain_batched", None),
                           ("learned_batched", {"beta": 1e-4, "seed": True, "active_iters": 32})):
         t0 = time.perf_counter()
-        res = ctx.bnb_solve_batch(probs, eps=eps, pop=POP, max_seconds=120, queue_capacity=1 << 26, learned=learned)
+        res = ctx.bnb_solve_batch(probs, eps=eps, max_seconds=120, queue_capacity=1 << 26, learned=learned)
         out[name] = {"wall_s": time.perf_counter() - t0, "nodes": int(sum(r["nodes"] for r in res)),
                      "certified": int(sum(r["status_name"] == "optimal" for r in res)),
                      "agree_with_single": int(sum(abs(r["f"] - q["f"]) <= eps * q["c22"]

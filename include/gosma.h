@@ -69,8 +69,10 @@ typedef struct {
     double eps;          /* tolerance on the normalised L2 distance f/C22 + 1 (Sec. 6 uses 0.1) */
     int pop;             /* hypercubes removed from the queue per iteration (Algorithm 1); each gives 8 children.
                             gosma_bnb_solve / _start: 0 = automatic, 2^23 / (n1 n2) clamped to [8192, 65536]
-                            (8192 from 1024 pairs per cube up); gosma_bnb_solve_batch: 1..65536 per problem,
-                            with 8 x pop x problems < 2^31 */
+                            (8192 from 1024 pairs per cube up); gosma_bnb_solve_batch: per problem,
+                            0 = automatic (the same rule for the largest mixture, clamped to
+                            [64, 65536], at most capacity / 16 and 2^31 / (8 problems)), else
+                            1..65536 with 8 x pop x problems < 2^31 */
     long long max_nodes; /* stop after this many evaluated sub-cubes (<= 0: no limit) */
     double max_seconds;  /* wall-clock limit (<= 0: no limit) */
     int use_sma;         /* run local refinement (SMA, Sec. 5) when a sub-cube improves d* */
@@ -287,7 +289,7 @@ int gosma_bnb_solve(gosma_ctx *ctx, const gosma_opts *opts, gosma_result *out);
  * results[k].seconds is the device time from the start to problem k's
  * certificate.  opts->queue_capacity is per problem (default 2^18
  * sub-cubes; two buffers of that size are allocated per problem),
- * opts->max_nodes per problem.  opts may be NULL (eps = 0.1, pop = 64, SMA
+ * opts->max_nodes per problem.  opts may be NULL (eps = 0.1, automatic pop, SMA
  * on).  Problems with invalid data make the call fail with GOSMA_EINVAL
  * before any work. */
 int gosma_bnb_solve_batch(gosma_ctx *ctx, int nprob, const gosma_problem *probs, const gosma_opts *opts,

@@ -706,6 +706,180 @@ __global__ void __launch_bounds__(MP_BLOCK)
     }
 }
 
+// Multi-block form of mp_append, for problems with many children per
+// iteration: one block per 4,096 children counts the survivors of its tile
+// (and the smallest upper bound, the largest logit), one block per problem
+// scans the tile counts, the tiles scatter their survivors in child order,
+// and one thread per problem finishes.  Same results as mp_append.
+constexpr int AP_BLOCK = 256, AP_ITEMS = 16, AP_TILE = AP_BLOCK * AP_ITEMS;
+
+struct AppScratch {
+    unsigned long long ub;  // smallest upper bound below d* (dbl_order); ~0 if none
+    unsigned int lg;        // largest logit key of a survivor (learned form with seeding); 0 if none
+    int jub, jlg;           // smallest child index attaining them
+    int total;              // survivors of the problem
+};
+
+__global__ void mp_app_init(ProbState *__restrict__ S, int nprob, AppScratch *__restrict__ A) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nprob) return;
+    A[k].ub = ~0ULL;
+    A[k].lg = 0u;
+    A[k].jub = A[k].jlg = 0x7fffffff;
+    A[k].total = 0;
+    S[k].cand_ok[0] = S[k].cand_ok[1] = 0;
+    S[k].cand_bad[0] = S[k].cand_bad[1] = 0;
+}
+
+__global__ void __launch_bounds__(AP_BLOCK)
+    mp_app_count(const ProbState *__restrict__ S, const int *__restrict__ off, const Node *__restrict__ kids,
+                 const double *__restrict__ kid_ub, const float *__restrict__ Yin, const int *__restrict__ scored,
+                 int seed, AppScratch *__restrict__ A, int *__restrict__ cnt, int T) {
+    const int k = blockIdx.y, t = blockIdx.x;
+    const ProbState &st = S[k];
+    const int n = 8 * st.np, j0 = t * AP_TILE;
+    if (j0 >= n) return;  // block-uniform
+    const float *__restrict__ Y = Yin && *scored > 0 ? Yin : nullptr;
+    const int c0 = off[k];
+    const double ds = st.dstar;
+    __shared__ int sh[32];
+    __shared__ unsigned long long s_ub;
+    __shared__ unsigned int s_lg;
+    if (threadIdx.x == 0) {
+        s_ub = ~0ULL;
+        s_lg = 0u;
+    }
+    __syncthreads();
+    int alive = 0;
+    unsigned long long bub = ~0ULL;
+    unsigned int blg = 0u;
+    for (int i = 0; i < AP_ITEMS; ++i) {
+        const int j = j0 + i * AP_BLOCK + threadIdx.x;
+        if (j >= n) break;
+        const double ub = kid_ub[c0 + j];
+        if (ub < ds) bub = min(bub, dbl_order(ub));
+        const bool a = kids[c0 + j].lb < ds;
+        alive += a;
+        if (Y && seed && a) blg = max(blg, order_key(Y[(size_t)(c0 + j) * MLP_OUT]));
+    }
+    if (bub != ~0ULL) atomicMin(&s_ub, bub);
+    if (blg) atomicMax(&s_lg, blg);
+    int tot;
+    mp_scan(alive, sh, tot);
+    if (threadIdx.x == 0) {
+        cnt[(size_t)k * T + t] = tot;
+        if (s_ub != ~0ULL) atomicMin(&A[k].ub, s_ub);
+        if (s_lg) atomicMax(&A[k].lg, s_lg);
+    }
+}
+
+// Exclusive scan of a problem's tile counts (in place: counts -> offsets).
+__global__ void mp_app_scan(const ProbState *__restrict__ S, int *__restrict__ cnt, int T,
+                            AppScratch *__restrict__ A) {
+    const int k = blockIdx.x;
+    const int tiles = (8 * S[k].np + AP_TILE - 1) / AP_TILE;
+    __shared__ int sh[32];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    int *c = cnt + (size_t)k * T;
+    for (int b0 = 0; b0 < tiles; b0 += blockDim.x) {
+        const int b = b0 + threadIdx.x;
+        const int v = b < tiles ? c[b] : 0;
+        int tot;
+        const int ex = mp_scan(v, sh, tot);
+        if (b < tiles) c[b] = carry + ex;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) A[k].total = carry;
+}
+
+__global__ void __launch_bounds__(AP_BLOCK)
+    mp_app_scatter(const ProbDev *__restrict__ P, const ProbState *__restrict__ S, const int *__restrict__ off,
+                   const Node *__restrict__ kids, const double *__restrict__ kid_ub, QueueBufs Qb,
+                   const float *__restrict__ Yin, const int *__restrict__ scored, float beta, int seed,
+                   AppScratch *__restrict__ A, const int *__restrict__ toff, int T) {
+    const int k = blockIdx.y, t = blockIdx.x;
+    const ProbState &st = S[k];
+    const int n = 8 * st.np, j0 = t * AP_TILE;
+    if (j0 >= n) return;  // block-uniform
+    const float *__restrict__ Y = Yin && *scored > 0 ? Yin : nullptr;
+    const int c0 = off[k];
+    const double ds = st.dstar, c22 = P[k].c22;
+    const unsigned long long base = P[k].base, cap = P[k].cap;
+    const unsigned long long start = st.tail + (unsigned long long)toff[(size_t)k * T + t];
+    const unsigned long long ubk = A[k].ub;
+    const unsigned int lgk = A[k].lg;
+    uint32_t *keys = Qb.keys[st.cur], *lbk = Qb.lbk[st.cur];
+    Node *q = Qb.q[st.cur];
+    __shared__ int sh[32];
+    int run = 0;
+    for (int i = 0; i < AP_ITEMS; ++i) {  // rounds in child order; every thread takes part in the scans
+        const int j = j0 + i * AP_BLOCK + threadIdx.x;
+        const bool in = j < n;
+        const bool alive = in && kids[c0 + j].lb < ds;
+        int tot;
+        const int pos = mp_scan(alive ? 1 : 0, sh, tot);
+        if (alive && start + run + pos < cap) {
+            const unsigned long long dst = base + start + run + pos;
+            Node nd = kids[c0 + j];
+            nd.ubf = __double2float_ru(kid_ub[c0 + j]);
+            q[dst] = nd;
+            const uint32_t lkey = order_key(__double2float_rd(nd.lb));
+            lbk[dst] = lkey;
+            float logit = Y ? Y[(size_t)(c0 + j) * MLP_OUT] : 0.f;
+            keys[dst] = Y ? order_key(__double2float_rd(nd.lb - (double)beta * c22 / (1.0 + exp(-(double)logit))))
+                          : lkey;
+        }
+        run += tot;
+        // ties: the smallest child index
+        if (in && ubk != ~0ULL && kid_ub[c0 + j] < ds && dbl_order(kid_ub[c0 + j]) == ubk) atomicMin(&A[k].jub, j);
+        if (in && Y && seed && lgk != 0u && alive && order_key(Y[(size_t)(c0 + j) * MLP_OUT]) == lgk)
+            atomicMin(&A[k].jlg, j);
+    }
+}
+
+__global__ void mp_app_finish(const ProbDev *__restrict__ P, ProbState *__restrict__ S, const int *__restrict__ off,
+                              const Node *__restrict__ kids, const float *__restrict__ Yin,
+                              const int *__restrict__ scored, int nprob, const AppScratch *__restrict__ A) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nprob) return;
+    ProbState &st = S[k];
+    const float *__restrict__ Y = Yin && *scored > 0 ? Yin : nullptr;
+    const int n = 8 * st.np, c0 = off[k];
+    const unsigned long long cap = P[k].cap, tail = st.tail, appended = (unsigned long long)A[k].total;
+    const unsigned long long fit = tail + appended <= cap ? appended : cap - tail;
+    st.tail = tail + fit;
+    st.live += fit;
+    if (st.live > st.peak) st.peak = st.live;
+    st.cross_pairs += (long long)n * P[k].mx.n1 * P[k].mx.n2;
+    if (fit < appended) {
+        st.done = 1 + GOSMA_QUEUE_FULL;
+        st.done_iter = -1;
+    }
+    if (A[k].jub != 0x7fffffff) {
+        CubeGeom g;
+        decode(kids[c0 + A[k].jub], P[k].dom, g);
+        for (int a = 0; a < 3; ++a) {
+            st.cand_x[0][a] = g.r0[a];
+            st.cand_x[0][3 + a] = g.t0[a];
+        }
+        st.cand_ok[0] = 1;
+    }
+    if (Y && A[k].jlg != 0x7fffffff) {
+        CubeGeom g;
+        decode(kids[c0 + A[k].jlg], P[k].dom, g);
+        const float *y = Y + (size_t)(c0 + A[k].jlg) * MLP_OUT;
+        for (int a = 0; a < 3; ++a) {
+            st.cand_x[1][a] = g.r0[a] + fminf(fmaxf(y[1 + a], -1.f), 1.f) * g.rhw;
+            st.cand_x[1][3 + a] = g.t0[a] + fminf(fmaxf(y[4 + a], -1.f), 1.f) * g.thw[a];
+        }
+        st.cand_ok[1] = 1;
+    }
+}
+
 // ---------------------------------------------------------------- exact FP64 objective at the candidates
 constexpr int MPO_BLOCK = 256;
 constexpr int MPO_CHUNK = 1024;
@@ -1207,17 +1381,29 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
     gosma_opts o;
     memset(&o, 0, sizeof o);
     o.eps = 0.1;
-    o.pop = 64;
+    o.pop = 0;  // automatic
     o.use_sma = 1;
     o.sma_max_iter = 100;
     if (opts_in) o = *opts_in;
     if (o.sma_max_iter <= 0) o.sma_max_iter = 100;
-    if (!(o.eps >= 0) || o.pop < 1 || o.pop > 65536)
-        return fail(ctx, GOSMA_EINVAL, "bnb_solve_batch: eps >= 0, 1 <= pop <= 65536");
+    if (!(o.eps >= 0) || o.pop < 0 || o.pop > 65536)
+        return fail(ctx, GOSMA_EINVAL, "bnb_solve_batch: eps >= 0, 0 <= pop <= 65536");
+    const unsigned long long cap = o.queue_capacity > 0 ? (unsigned long long)o.queue_capacity : (1ULL << 18);
+    if (o.pop == 0) {
+        // automatic, as for one problem: about 2^23 pair bounds per problem and
+        // iteration for the largest mixture, clamped to [64, 65536], within
+        // capacity / 16 and the 32-bit children offsets
+        long long mp = 1;
+        for (int k = 0; k < nprob; ++k) mp = std::max(mp, (long long)probs[k].n1 * probs[k].n2);
+        long long p = (1LL << 23) / mp;
+        p = std::min(std::max(p, 64LL), 65536LL);
+        p = std::min(p, (long long)(cap / 16));
+        p = std::min(p, 0x7fffffffLL / (8LL * nprob));
+        o.pop = (int)std::max(p, 1LL);
+    }
     // children offsets are 32-bit prefix sums of 8 x pop per problem
     if (8LL * o.pop * nprob > 0x7fffffffLL)
         return fail(ctx, GOSMA_EINVAL, "bnb_solve_batch: 8 * pop * problems must be below 2^31");
-    const unsigned long long cap = o.queue_capacity > 0 ? (unsigned long long)o.queue_capacity : (1ULL << 18);
     if (cap < 16ULL * o.pop) return fail(ctx, GOSMA_EINVAL, "bnb_solve_batch: queue_capacity below 16 * pop");
     for (int k = 0; k < nprob; ++k) {
         int rc = validate_problem(ctx, probs[k], k);
@@ -1393,6 +1579,15 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
         (e = B.get(&part, 2 * (size_t)nblk * nprob)) == cudaSuccess) {
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(batch state)");
+    // append in tiles when a problem can have many children per iteration
+    // (its pop quota reaches min(pop x problems, capacity / 16))
+    const long long qmax = std::max<long long>(pop, std::min<long long>((long long)pop * nprob, (long long)(cap / 16)));
+    const bool tiled_append = 8 * qmax >= 4 * AP_TILE;
+    const int app_T = (int)((8 * qmax + AP_TILE - 1) / AP_TILE);
+    AppScratch *d_app = nullptr;
+    int *d_tcnt = nullptr;
+    if (tiled_append && ((e = B.get(&d_app, nprob)) != cudaSuccess || (e = B.get(&d_tcnt, (size_t)app_T * nprob)) != cudaSuccess))
+        return cuda_fail(ctx, e, "cudaMalloc(batch append)");
     std::vector<long long> hio(nprob, 0);
     for (int k = 1; k < nprob; ++k) hio[k] = hio[k - 1] + probs[k - 1].n1;
     e = cudaMemcpyAsync(dP, hp.data(), sizeof(ProbDev) * nprob, cudaMemcpyHostToDevice, st);
@@ -1559,7 +1754,18 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
             ctx->launches += 2;
             eb = mlp_forward_rows(ctx, max_rows, d_lrows, st);
         }
-        mp_append<<<nprob, MP_BLOCK, 0, st>>>(dP, dS, off, kids, kid_ub, Qb, Yd, d_lrows, lo.beta, lo.seed);
+        if (tiled_append) {
+            const dim3 tg(app_T, nprob);
+            mp_app_init<<<(nprob + 255) / 256, 256, 0, st>>>(dS, nprob, d_app);
+            mp_app_count<<<tg, AP_BLOCK, 0, st>>>(dS, off, kids, kid_ub, Yd, d_lrows, lo.seed, d_app, d_tcnt, app_T);
+            mp_app_scan<<<nprob, 1024, 0, st>>>(dS, d_tcnt, app_T, d_app);
+            mp_app_scatter<<<tg, AP_BLOCK, 0, st>>>(dP, dS, off, kids, kid_ub, Qb, Yd, d_lrows, lo.beta, lo.seed, d_app,
+                                                   d_tcnt, app_T);
+            mp_app_finish<<<(nprob + 127) / 128, 128, 0, st>>>(dP, dS, off, kids, Yd, d_lrows, nprob, d_app);
+            ctx->launches += 4;
+        } else {
+            mp_append<<<nprob, MP_BLOCK, 0, st>>>(dP, dS, off, kids, kid_ub, Qb, Yd, d_lrows, lo.beta, lo.seed);
+        }
         mp_obj_prep<<<dim3((max_n1 + 127) / 128, 2 * nprob), 128, 0, st>>>(dP, dS, ioff, idata);
         mp_obj_pairs<<<dim3(nblk, 2 * nprob), MPO_BLOCK, 0, st>>>(dP, dS, ioff, idata, part, nblk);
         mp_obj_final<<<(nprob + 127) / 128, 128, 0, st>>>(dS, nprob, part, nblk);

@@ -364,7 +364,7 @@ class Gosma:
         self._check(self.L.gosma_bnb_solve(self.h, C.byref(o), C.byref(r)), "bnb_solve")
         return self._result(r)
 
-    def bnb_solve_batch(self, problems, eps=0.1, pop=64, max_nodes=0, max_seconds=0.0, use_sma=True,
+    def bnb_solve_batch(self, problems, eps=0.1, pop=0, max_nodes=0, max_seconds=0.0, use_sma=True,
                         sma_max_iter=100, queue_capacity=0, learned=None, trace_cap=0):
         """Algorithm 1 for many independent problems at once (list of problem
         dicts as produced by synth); returns one result dict per problem.

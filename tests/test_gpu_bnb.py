@@ -164,6 +164,27 @@ def test_batch_noise_free_recovery(ctx, oracle_mod):
         assert np.linalg.norm(r["t"] - p["t_gt"]) < 0.05 * np.linalg.norm(p["t_gt"]) + 1e-3
 
 
+@pytest.mark.parametrize("learned", [False, True])
+def test_tiled_append_matches_the_oracle(ctx, oracle_mod, learned):
+    """With pop 4096 (32,768 children per problem) the batch appends children
+    in 4,096-child tiles (count, scan, scatter in child order): the
+    certificates still cover the stored oracle optima, plain and learned."""
+    gold = json.load(open(GOLDEN))
+    probs = [synth.tiny_problem(1000), synth.tiny_problem(1001)]
+    kw = dict(learned=dict(beta=1e-4, seed=True, active_iters=1000)) if learned else {}
+    if learned:
+        ctx.mlp_set_params(_params(5))
+    res = ctx.bnb_solve_batch(probs, eps=1e-3, pop=4096, max_seconds=300, queue_capacity=1 << 26, **kw)
+    for p, r, seed in zip(probs, res, (1000, 1001)):
+        g = gold[str(seed)]
+        epsf = 1e-3 * g["c22"]
+        assert r["status_name"] == "optimal"
+        assert abs(r["f"] - g["f"]) <= epsf
+        assert r["lb"] <= g["f"] + 1e-9 and g["lb"] <= r["f"] + 1e-9
+        mix = oracle_mod.Mixtures.from_problem(p)
+        assert oracle_mod.objective_r(mix, r["r"], r["t"]) == pytest.approx(r["f"], rel=1e-10)
+
+
 def test_batch_member_agrees_with_single_solve(ctx):
     """A problem solved alone, in a batch with a neighbour of other sizes, and
     by the single-problem solver reaches the same certified optimum."""
@@ -195,7 +216,7 @@ def test_batch_limits_and_errors(ctx):
     with pytest.raises(GosmaError):
         ctx.bnb_solve_batch([probs[1], bad], eps=1e-3)
     with pytest.raises(GosmaError):
-        ctx.bnb_solve_batch(probs, eps=1e-3, pop=0)
+        ctx.bnb_solve_batch(probs, eps=1e-3, pop=-1)
     with pytest.raises(GosmaError):
         ctx.bnb_solve_batch(probs, eps=1e-3, pop=65537)
     with pytest.raises(GosmaError):  # 8 x pop x problems must stay below 2^31 (32-bit child offsets)
