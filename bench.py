@@ -36,8 +36,9 @@ Two more measurements ride on the same line (rank 0, N = 1, unless
 * "time_to_certified": tiny problems (10 x 8 components, eps 1e-3) solved
   to the certified optimum by the plain single-problem solver (one after the
   other), the plain batched solver and the learned batched solver (network
-  weights from paper_1812_01232_gb300/weights, scoring during the first 32
-  iterations, where the incumbent is found), on the same problems, each with
+  weights from paper_1812_01232_gb300/weights, scoring during the first 8
+  iterations, about the first 10% of the nodes, where the incumbent is
+  found), on the same problems, each with
   its automatic pop;
 * "sma": the batched device refinement (SMA, Sec. 5) of many seed poses of
   the 128 x 64 paper-scale problem (half near the true pose, half uniform),
@@ -465,7 +466,7 @@ def run_time_to_certified(n_prob):
                            "certified": int(sum(r["status_name"] == "optimal" for r in single))}
     ctx.mlp_set_params(learn.load(os.path.join(ROOT, "paper_1812_01232_gb300", "weights", "gosma_mlp.npz")))
     for name, learned in (("plain_batched", None),
-                          ("learned_batched", {"beta": 1e-4, "seed": True, "active_iters": 32})):
+                          ("learned_batched", {"beta": 1e-4, "seed": True, "active_iters": 8})):
         t0 = time.perf_counter()
         res = ctx.bnb_solve_batch(probs, eps=eps, max_seconds=120, queue_capacity=1 << 26, learned=learned)
         out[name] = {"wall_s": time.perf_counter() - t0, "nodes": int(sum(r["nodes"] for r in res)),
