@@ -23,7 +23,10 @@
 //   mp_append    one block per problem: children with lb < d* go to the
 //                segment's tail (block scan, in child order); candidates for
 //                d*: the centre of the child with the smallest upper bound
-//                and, in the learned form, the best-scored child's seed;
+//                and, in the learned form, the best-scored child's seed
+//                (mp_app_* when a problem can have 16,384 children or more:
+//                4,096-child tiles counted, scanned per problem, scattered
+//                in child order, then finished per problem);
 //   mp_obj_*     the exact FP64 objective at every candidate, which replaces
 //                d* when smaller.
 // The sequence is captured once in a CUDA graph and replayed; the host polls
