@@ -157,3 +157,25 @@ def test_two_gloo_ranks_certify_the_global_optimum():
     assert abs(f - one["f"]) <= EPS and lb <= one["f"] + 1e-12
     # the optimum lies in the slab t0 > 0 (c0 = 0.6): rank 0 learnt it in the exchange
     assert t[0] > 0
+
+
+def _rec(f, lb, status, nodes=10, t=(0.0, 0.0, 0.0)):
+    return sharded._record({"f": f, "lb": lb, "status_name": status, "nodes": nodes, "r": np.zeros(3),
+                            "t": np.array(t, float)})
+
+
+def test_merge_rules():
+    c22, eps = 2.0, 0.01
+    # a running rank and an uncertified gap: keep going, incumbent = smallest d*
+    d, x, out = sharded._merge(np.stack([_rec(1.0, 0.5, "running", t=(1, 0, 0)), _rec(0.9, 0.85, "optimal",
+                                                                                      t=(2, 0, 0))]), c22, eps, 3)
+    assert out is None and d == 0.9 and x[3] == 2.0
+    # the global gap closes while a rank still runs: certified
+    d, x, out = sharded._merge(np.stack([_rec(1.0, 0.895, "running"), _rec(0.9, 0.89, "optimal")]), c22, eps, 4)
+    assert out["status_name"] == "optimal" and out["lb"] == 0.89 and out["f"] == 0.9 and out["nodes"] == 20
+    # nobody runs and a rank hit a limit: the gap stays open, the limit is reported
+    d, x, out = sharded._merge(np.stack([_rec(1.0, 0.5, "node_limit"), _rec(0.9, 0.89, "optimal")]), c22, eps, 5)
+    assert out["status_name"] == "node_limit" and out["gap_norm"] == pytest.approx((0.9 - 0.5) / c22)
+    # every rank certified its own slab: the global certificate holds
+    d, x, out = sharded._merge(np.stack([_rec(1.0, 0.995, "optimal"), _rec(0.9, 0.895, "optimal")]), c22, eps, 6)
+    assert out["status_name"] == "optimal" and out["f"] - out["lb"] <= eps * c22
