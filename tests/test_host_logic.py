@@ -1,0 +1,107 @@
+"""Host-side logic of the library that runs without a GPU, compiled with g++:
+the semantic class layout (Sec. 4.2) that turns plain pair sums into the
+weighted sum of the per-class objectives."""
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_1812_01232_gb300", "csrc")
+
+HARNESS = r"""
+#include <cstdio>
+#include <cstdlib>
+#include "classes.h"
+// argv: nclass n1 n2, then n1c[nclass] n2c[nclass] w[nclass] phi1[n1] phi2[n2]
+int main(int argc, char **argv) {
+    int a = 1;
+    const int nclass = atoi(argv[a++]), n1 = atoi(argv[a++]), n2 = atoi(argv[a++]);
+    std::vector<int> n1c(nclass), n2c(nclass);
+    std::vector<double> w(nclass), phi1(n1), phi2(n2);
+    for (int l = 0; l < nclass; ++l) n1c[l] = atoi(argv[a++]);
+    for (int l = 0; l < nclass; ++l) n2c[l] = atoi(argv[a++]);
+    for (int l = 0; l < nclass; ++l) w[l] = atof(argv[a++]);
+    for (int i = 0; i < n1; ++i) phi1[i] = atof(argv[a++]);
+    for (int j = 0; j < n2; ++j) phi2[j] = atof(argv[a++]);
+    gosma::ClassLayout L;
+    const char *err = gosma::class_layout(nclass, n1c.data(), n2c.data(), w.data(), n1, n2, phi1.data(), phi2.data(), L);
+    if (err) { printf("error %s\n", err); return 0; }
+    printf("classes %d\n", (int)L.classes);
+    for (int i = 0; i < n1; ++i) printf("row %.17g %d %d %d %d\n", L.phi1[i], L.cls1[i], L.rj0[i], L.rj1[i], L.rm1[i]);
+    for (int j = 0; j < n2; ++j) printf("col %.17g %d\n", L.phi2[j], L.cls2[j]);
+    return 0;
+}
+"""
+
+
+@pytest.fixture(scope="module")
+def harness(tmp_path_factory):
+    gxx = shutil.which("g++")
+    if not gxx:
+        pytest.skip("g++ not available")
+    d = tmp_path_factory.mktemp("host")
+    src, exe = d / "h.cpp", d / "h"
+    src.write_text(HARNESS)
+    subprocess.run([gxx, "-O1", "-std=c++17", "-I", CSRC, str(src), "-o", str(exe)], check=True)
+    return str(exe)
+
+
+def _run(exe, n1c, n2c, w, phi1, phi2):
+    args = [str(len(n1c)), str(len(phi1)), str(len(phi2))] + [str(v) for v in list(n1c) + list(n2c)]
+    args += ["%.17g" % v for v in list(w) + list(phi1) + list(phi2)]
+    out = subprocess.run([exe] + args, check=True, capture_output=True, text=True).stdout.split("\n")
+    if out[0].startswith("error"):
+        return out[0]
+    rows = [l.split()[1:] for l in out if l.startswith("row")]
+    cols = [l.split()[1:] for l in out if l.startswith("col")]
+    return {"classes": int(out[0].split()[1]),
+            "phi1": np.array([float(r[0]) for r in rows]), "cls1": [int(r[1]) for r in rows],
+            "rj0": [int(r[2]) for r in rows], "rj1": [int(r[3]) for r in rows], "rm1": [int(r[4]) for r in rows],
+            "phi2": np.array([float(c[0]) for c in cols]), "cls2": [int(c[1]) for c in cols]}
+
+
+def test_one_class_changes_nothing(harness):
+    phi1, phi2 = np.full(4, 0.25), np.array([0.5, 0.3, 0.2])
+    r = _run(harness, [4], [3], [1.0], phi1, phi2)
+    assert r["classes"] == 0
+    np.testing.assert_array_equal(r["phi1"], phi1)
+    np.testing.assert_array_equal(r["phi2"], phi2)
+    assert r["rj0"] == [0] * 4 and r["rj1"] == [3] * 4 and r["rm1"] == [4] * 4
+
+
+def test_classes_give_the_weighted_sum_of_class_pair_sums(harness):
+    rng = np.random.default_rng(0)
+    n1c, n2c, w = [2, 3, 1], [1, 2, 2], [0.25, 1.0, 4.0]
+    phi1 = np.concatenate([rng.dirichlet(np.ones(a)) for a in n1c])
+    phi2 = np.concatenate([rng.dirichlet(np.ones(b)) for b in n2c])
+    r = _run(harness, n1c, n2c, w, phi1, phi2)
+    assert r["classes"] == 1
+    assert r["cls1"] == [0, 0, 1, 1, 1, 2] and r["cls2"] == [0, 1, 1, 2, 2]
+    assert r["rj0"] == [0, 0, 1, 1, 1, 3] and r["rj1"] == [1, 1, 3, 3, 3, 5]
+    assert r["rm1"] == [2, 2, 5, 5, 5, 6]
+    # any pair term g: summing the scaled weights over within-class pairs gives sum_l w_l (class sum)
+    g1 = rng.random((6, 6))
+    g12 = rng.random((6, 5))
+    s = sum(r["phi1"][i] * r["phi1"][m] * g1[i, m] for i in range(6) for m in range(6) if r["cls1"][i] == r["cls1"][m])
+    c = sum(r["phi1"][i] * r["phi2"][j] * g12[i, j] for i in range(6) for j in range(r["rj0"][i], r["rj1"][i]))
+    i0 = j0 = 0
+    ref_s = ref_c = 0.0
+    for l, (a, b) in enumerate(zip(n1c, n2c)):
+        ii, jj = range(i0, i0 + a), range(j0, j0 + b)
+        ref_s += w[l] * sum(phi1[i] * phi1[m] * g1[i, m] for i in ii for m in ii)
+        ref_c += w[l] * sum(phi1[i] * phi2[j] * g12[i, j] for i in ii for j in jj)
+        i0, j0 = i0 + a, j0 + b
+    assert s == pytest.approx(ref_s, rel=1e-13) and c == pytest.approx(ref_c, rel=1e-13)
+
+
+@pytest.mark.parametrize("n1c,n2c,w,phi1,phi2", [
+    ([2, 2], [1, 1], [1.0, 1.0], [0.5, 0.5, 0.5, 0.4], [1.0, 1.0]),   # class weights do not sum to 1
+    ([2, 1], [1, 1], [1.0, 1.0], [0.5, 0.5, 1.0, 1.0], [1.0, 1.0]),   # sizes do not add up to n1
+    ([2, 2], [1, 1], [1.0, -1.0], [0.5, 0.5, 0.5, 0.5], [1.0, 1.0]),  # negative class weight
+    ([2, 0], [1, 1], [1.0, 1.0], [0.5, 0.5], [1.0, 1.0]),             # empty class
+])
+def test_invalid_layouts_are_rejected(harness, n1c, n2c, w, phi1, phi2):
+    assert str(_run(harness, n1c, n2c, w, phi1, phi2)).startswith("error")
