@@ -34,6 +34,7 @@
 #include <vector>
 
 #include "bnb_common.cuh"
+#include "host_rules.h"
 
 namespace gosma {
 
@@ -744,15 +745,7 @@ extern "C" int gosma_bnb_start(gosma_ctx *ctx, const gosma_opts *opts_in) {
     if (opts_in) o = *opts_in;
     if (!(o.eps >= 0) || o.pop < 0 || o.pop > 131072)
         return fail(ctx, GOSMA_EINVAL, "bnb_start: need eps >= 0 and 0 <= pop <= 131072");
-    if (o.pop == 0) {
-        // about 2^23 pair bounds per iteration, at least 65,536 children (a
-        // few hundred sub-cubes per SM for the persistent bound kernel) and
-        // at most 524,288: small mixtures are otherwise bound by the fixed
-        // cost of an iteration (selection, compaction, launches, the host
-        // read of the status record)
-        long long p = (1LL << 23) / ((long long)ctx->n1 * ctx->n2);
-        o.pop = (int)(p < 8192 ? 8192 : p > 65536 ? 65536 : p);
-    }
+    if (o.pop == 0) o.pop = auto_pop_single(ctx->n1, ctx->n2);
     if (o.sma_max_iter <= 0) o.sma_max_iter = 100;
     unsigned long long cap = o.queue_capacity > 0 ? (unsigned long long)o.queue_capacity : (1ULL << 24);
     if (cap < 16ULL * o.pop) cap = 16ULL * o.pop;

@@ -1,0 +1,42 @@
+// Launch-shape rules of the host code, kept free of CUDA so that they can be
+// compiled and tested on their own.
+#pragma once
+
+#include <algorithm>
+
+namespace gosma {
+
+// Sub-cubes popped per iteration by the single-problem solver when the caller
+// leaves it to the library: about 2^23 pair bounds per iteration, at least
+// 65,536 children (a few hundred sub-cubes per SM for the persistent bound
+// kernel) and at most 524,288; small mixtures are otherwise bound by the fixed
+// cost of an iteration (selection, compaction, launches, the host's read of
+// the status record).
+inline int auto_pop_single(int n1, int n2) {
+    const long long p = (1LL << 23) / ((long long)n1 * n2);
+    return (int)(p < 8192 ? 8192 : p > 65536 ? 65536 : p);
+}
+
+// The batched solver's pop per problem: the same rule for the largest mixture
+// (max_pairs = max n1 n2), clamped to [64, 65536], at most capacity / 16 and
+// within the 32-bit children offsets (8 pop nprob < 2^31).
+inline int auto_pop_batch(long long max_pairs, int nprob, unsigned long long cap) {
+    long long p = (1LL << 23) / std::max(max_pairs, 1LL);
+    p = std::min(std::max(p, 64LL), 65536LL);
+    p = std::min(p, (long long)(cap / 16));
+    p = std::min(p, 0x7fffffffLL / (8LL * std::max(nprob, 1)));
+    return (int)std::max(p, 1LL);
+}
+
+// Threads per seed of the batched SMA: about 2,048 threads per SM in all
+// (2048 SMs / seeds, a power of two in [128, 1024]; at most 512 for the FP64
+// search, whose threads need more registers) and at most one thread per 16
+// pair terms of an evaluation.
+inline int sma_block_for(int count, int sm_count, bool f64, int n1, int n2) {
+    const long long pairs = (long long)n1 * (n1 + 1) / 2 + (long long)n1 * n2;
+    int b = 128;
+    while (b < (f64 ? 512 : 1024) && (long long)count * 2 * b <= 2048LL * sm_count && 32LL * b <= pairs) b *= 2;
+    return b;
+}
+
+}  // namespace gosma

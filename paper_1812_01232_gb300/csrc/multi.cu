@@ -47,6 +47,7 @@
 
 #include "bnb_common.cuh"
 #include "classes.h"
+#include "host_rules.h"
 #include "mlp.cuh"
 #include "objective_core.cuh"
 
@@ -1392,17 +1393,10 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
     if (!(o.eps >= 0) || o.pop < 0 || o.pop > 65536)
         return fail(ctx, GOSMA_EINVAL, "bnb_solve_batch: eps >= 0, 0 <= pop <= 65536");
     const unsigned long long cap = o.queue_capacity > 0 ? (unsigned long long)o.queue_capacity : (1ULL << 18);
-    if (o.pop == 0) {
-        // automatic, as for one problem: about 2^23 pair bounds per problem and
-        // iteration for the largest mixture, clamped to [64, 65536], within
-        // capacity / 16 and the 32-bit children offsets
+    if (o.pop == 0) {  // automatic (host_rules.h)
         long long mp = 1;
         for (int k = 0; k < nprob; ++k) mp = std::max(mp, (long long)probs[k].n1 * probs[k].n2);
-        long long p = (1LL << 23) / mp;
-        p = std::min(std::max(p, 64LL), 65536LL);
-        p = std::min(p, (long long)(cap / 16));
-        p = std::min(p, 0x7fffffffLL / (8LL * nprob));
-        o.pop = (int)std::max(p, 1LL);
+        o.pop = auto_pop_batch(mp, nprob, cap);
     }
     // children offsets are 32-bit prefix sums of 8 x pop per problem
     if (8LL * o.pop * nprob > 0x7fffffffLL)

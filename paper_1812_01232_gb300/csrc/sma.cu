@@ -19,24 +19,14 @@
 //       exact objective value.
 #include <math.h>
 
+#include "host_rules.h"
 #include "objective_core.cuh"
 
 namespace gosma {
 
-// Threads per seed: about 2,048 threads per SM in all, i.e. 2048 SMs / seeds
-// rounded down to a power of two in [128, 1024] (at most 512 for the FP64
-// search, whose threads need more registers), and at most one thread per 16
-// pair terms of an evaluation: few seeds of large mixtures spread every
-// evaluation over many threads, many seeds or small mixtures fill the SMs
-// with small blocks.
+// Threads per seed: sma_block_for (host_rules.h), 128 to 1,024.
 constexpr int SMA_BLOCK = 128;
 
-__host__ inline int sma_block_for(int count, int sm_count, bool f64, int n1, int n2) {
-    const long long pairs = (long long)n1 * (n1 + 1) / 2 + (long long)n1 * n2;
-    int b = SMA_BLOCK;
-    while (b < (f64 ? 512 : 1024) && (long long)count * 2 * b <= 2048LL * sm_count && 32LL * b <= pairs) b *= 2;
-    return b;
-}
 constexpr int SMA_M = 8;  // L-BFGS memory
 
 // L-BFGS state of the block's current seed (shared memory; thread 0 writes).

@@ -105,3 +105,57 @@ def test_classes_give_the_weighted_sum_of_class_pair_sums(harness):
 ])
 def test_invalid_layouts_are_rejected(harness, n1c, n2c, w, phi1, phi2):
     assert str(_run(harness, n1c, n2c, w, phi1, phi2)).startswith("error")
+
+
+RULES = r"""
+#include <cstdio>
+#include <cstdlib>
+#include "host_rules.h"
+int main(int argc, char **argv) {
+    const char *what = argv[1];
+    if (what[0] == 's') printf("%d\n", gosma::auto_pop_single(atoi(argv[2]), atoi(argv[3])));
+    if (what[0] == 'b') printf("%d\n", gosma::auto_pop_batch(atoll(argv[2]), atoi(argv[3]), strtoull(argv[4], 0, 10)));
+    if (what[0] == 'm') printf("%d\n", gosma::sma_block_for(atoi(argv[2]), atoi(argv[3]), atoi(argv[4]) != 0,
+                                                            atoi(argv[5]), atoi(argv[6])));
+    return 0;
+}
+"""
+
+
+@pytest.fixture(scope="module")
+def rules(tmp_path_factory):
+    gxx = shutil.which("g++")
+    if not gxx:
+        pytest.skip("g++ not available")
+    d = tmp_path_factory.mktemp("rules")
+    src, exe = d / "r.cpp", d / "r"
+    src.write_text(RULES)
+    subprocess.run([gxx, "-O1", "-std=c++17", "-I", CSRC, str(src), "-o", str(exe)], check=True)
+    return lambda *a: int(subprocess.run([str(exe)] + [str(x) for x in a], check=True, capture_output=True,
+                                          text=True).stdout)
+
+
+def test_automatic_pop_of_one_problem(rules):
+    assert rules("s", 10, 8) == 65536      # small mixtures: the most children per iteration
+    assert rules("s", 128, 64) == 8192     # paper scale: 2^23 / 8192 = 1024, raised to the floor
+    assert rules("s", 32, 32) == 8192      # 1024 pairs per cube
+    assert rules("s", 16, 16) == 32768     # 2^23 / 256
+    assert rules("s", 2048, 512) == 8192
+
+
+def test_automatic_pop_of_a_batch(rules):
+    assert rules("b", 80, 8, 1 << 26) == 65536
+    assert rules("b", 256 * 128, 256, 1 << 18) == 256        # 2^23 / 32768
+    assert rules("b", 80, 8, 1 << 18) == (1 << 18) // 16     # capacity / 16
+    assert rules("b", 10 ** 7, 4, 1 << 26) == 64             # floor
+    assert rules("b", 80, 60000, 1 << 26) == 0x7fffffff // (8 * 60000)  # 32-bit children offsets
+    for nprob in (1, 7, 4096, 65535):
+        assert 8 * rules("b", 80, nprob, 1 << 30) * nprob < 2 ** 31
+
+
+def test_sma_threads_per_seed(rules):
+    assert rules("m", 1, 152, 0, 128, 64) == 1024    # one large seed: a wide block
+    assert rules("m", 1, 152, 1, 128, 64) == 512     # FP64 search: at most 512
+    assert rules("m", 1, 152, 0, 10, 8) == 128       # 135 pair terms: no wider than 128
+    assert rules("m", 1216, 152, 0, 128, 64) == 256  # 2048 x 152 / 1216 = 256 threads per seed
+    assert rules("m", 4864, 152, 0, 128, 64) == 128
