@@ -20,7 +20,9 @@ copies a batch of 65,536 sub-cubes of the same tree depths from host memory
 and reads back their lower and upper bounds.
 
 --impl reference: the FP64 CPU oracle, as it stands, on the host cores, on a
-bounded sample of the same workload per step.
+bounded sample of the same workload per step (sub-cubes of the same problem
+at tree depths 2-12, Theorem 1 bounds; --ref-seconds of host time spread over
+the warm-up and timed steps, 150 s by default, at least 0.25 s a step).
 
 Multi-GPU (torchrun): every rank solves its own independent problem (seed +
 rank); no data-path collective; value = pairs of all ranks / max rank time.
@@ -180,6 +182,13 @@ def reduce_over_ranks(t_local, pairs_local, dist, device):
     return float(tt.item()), float(pp.item())
 
 
+def workload_config(n1, n2):
+    """The workload both arms are quoted on (the `config` of either JSON line)."""
+    return {"workload": "paper_scale: one problem per GPU, 128 model x 64 image components, "
+                        "branch-and-bound step of %d parents -> %d children, eps 1e-4" % (POP, 8 * POP),
+            "n1": n1, "n2": n2, "children_per_step": 8 * POP, "l2": "flushed between steps (512 MB write)"}
+
+
 def make_problem(rank):
     from paper_1812_01232_gb300 import synth
     return synth.paper_scale_problem(SEED + rank)
@@ -211,7 +220,7 @@ def run_reference(args):
     oracle.build()
     prob = make_problem(0)
     n1, n2 = len(prob["sigma1"]), len(prob["kappa2"])
-    per_step = max(2.0, 150.0 / max(1, args.steps + args.warmup))
+    per_step = max(0.25, args.ref_seconds / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
         cpu_sample(prob, min(per_step, 2.0), 11)
     tot_pairs, tot_t, cubes = 0.0, 0.0, 0
@@ -225,8 +234,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "paper_scale 128x64 components, sub-cubes at tree depths 2-12",
-                   "n1": n1, "n2": n2},
+        "config": workload_config(n1, n2),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": "%d sub-cubes over %d steps, Theorem 1 lb+ub in FP64 (self pairs included)"
                                    % (cubes, args.steps)},
@@ -333,11 +341,8 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 pair terms, f64 per-cube sums", "data": "synthetic",
-        "config": {"workload": "paper_scale: one problem per GPU, 128 model x 64 image components, "
-                               "branch-and-bound step of %d parents -> %d children, eps 1e-4" % (POP, 8 * POP),
-                   "n1": n1, "n2": n2, "children_per_step": 8 * POP,
-                   "self_pairs_per_step": self_pairs / args.steps, "l2": "flushed between steps (512 MB write)",
-                   "queue_size_end": r["queue_size"]},
+        "config": dict(workload_config(n1, n2), self_pairs_per_step=self_pairs / args.steps,
+                       queue_size_end=r["queue_size"]),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(cubes.nbytes),
                 "d2h_bytes_per_step": int(2 * 8 * len(cubes)),
                 "call": "gosma_eval_bounds on host buffers, %d sub-cubes per step (self sums computed once per "
@@ -487,6 +492,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-seconds", type=float, default=150.0,
+                    help="--impl reference: host-core seconds spread over the warm-up and timed steps")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and time-to-certificate measurements")
     ap.add_argument("--batch-budget", type=float, default=20.0, help="seconds for the 256-problem batched solve")
