@@ -194,20 +194,32 @@ def make_problem(rank):
     return synth.paper_scale_problem(SEED + rank)
 
 
-def cpu_sample(prob, target_s, seed):
-    """Time the FP64 oracle's Theorem 1 bounds on a bounded sample of cubes."""
-    import oracle
+def cube_pool(prob, seed):
+    """65,536 sub-cubes of the problem at tree depths 2-12 (drawn once; the
+    samples below take windows of it)."""
     from paper_1812_01232_gb300 import synth
+    return synth.tree_cubes(seed, 65536, prob["t_lo"], prob["t_hi"], 2, 12)
+
+
+def cpu_sample(prob, target_s, pool, start=0):
+    """Time the FP64 oracle's Theorem 1 bounds on a bounded sample of cubes:
+    about `target_s` seconds of consecutive cubes of `pool` from `start`
+    (wrapping around)."""
+    import oracle
     mix = oracle.Mixtures.from_problem(prob)
     n1, n2 = len(prob["sigma1"]), len(prob["kappa2"])
-    cubes = synth.tree_cubes(seed, 65536, prob["t_lo"], prob["t_hi"], 2, 12)
+
+    def window(n):
+        return np.ascontiguousarray(pool[(start + np.arange(n)) % len(pool)])
+
     n = 16
     t0 = time.perf_counter()
-    oracle.bounds(mix, cubes[:n], prob["zeta"])
+    oracle.bounds(mix, window(n), prob["zeta"])
     dt = time.perf_counter() - t0
-    n = int(min(len(cubes), max(16, n * target_s / max(dt, 1e-6))))
+    n = int(min(len(pool), max(16, n * target_s / max(dt, 1e-6))))
+    cubes = window(n)
     t0 = time.perf_counter()
-    oracle.bounds(mix, cubes[:n], prob["zeta"])
+    oracle.bounds(mix, cubes, prob["zeta"])
     dt = time.perf_counter() - t0
     return n, dt, n * n1 * n2 / dt, oracle.max_threads()
 
@@ -221,11 +233,12 @@ def run_reference(args):
     prob = make_problem(0)
     n1, n2 = len(prob["sigma1"]), len(prob["kappa2"])
     per_step = max(0.25, args.ref_seconds / max(1, args.steps + args.warmup))
-    for _ in range(args.warmup):
-        cpu_sample(prob, min(per_step, 2.0), 11)
+    pool = cube_pool(prob, 100)
+    for k in range(args.warmup):
+        cpu_sample(prob, min(per_step, 2.0), pool, 7919 * k)
     tot_pairs, tot_t, cubes = 0.0, 0.0, 0
     for k in range(args.steps):
-        n, dt, _, cores = cpu_sample(prob, per_step, 100 + k)
+        n, dt, _, cores = cpu_sample(prob, per_step, pool, cubes)
         tot_pairs += n * n1 * n2
         tot_t += dt
         cubes += n
@@ -334,7 +347,7 @@ def run_ours(args):
     if world == 1 and not args.no_cpu:
         import oracle
         oracle.build()
-        n, dt, v, cores = cpu_sample(prob, args.cpu_seconds, 99)
+        n, dt, v, cores = cpu_sample(prob, args.cpu_seconds, cube_pool(prob, 99))
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": "%d sub-cubes of the same workload (depths 2-12), Theorem 1 lb+ub in FP64, %.1f s" % (n, dt)}
     line = {
