@@ -132,6 +132,11 @@ class GosmaError(RuntimeError):
     pass
 
 
+class GosmaArgumentError(GosmaError, ValueError):
+    """An argument refused before the library is called: array lengths that
+    disagree, or a device buffer of the wrong dtype, shape, layout or device."""
+
+
 def _f64(a, shape=None):
     a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
     return a.reshape(shape) if shape is not None else a
@@ -152,6 +157,55 @@ def _pf(a):
 
 def _is_torch_cuda(x):
     return type(x).__module__.startswith("torch") and getattr(x, "is_cuda", False)
+
+
+_MIX_NAMES = ("mu1", "sigma1", "phi1", "mu2", "kappa2", "phi2")
+
+
+def _mixture_arrays(mu1, sigma1, phi1, mu2, kappa2, phi2):
+    """FP64 C-contiguous copies of one problem's mixtures.  The library takes
+    n1 = len(sigma1) and n2 = len(kappa2) and reads n1 rows of mu1 and phi1
+    and n2 rows of mu2 and phi2, so every length is checked against those."""
+    a = [_f64(mu1, (-1, 3)), _f64(sigma1, (-1,)), _f64(phi1, (-1,)), _f64(mu2, (-1, 3)), _f64(kappa2, (-1,)),
+         _f64(phi2, (-1,))]
+    n1, n2 = len(a[1]), len(a[4])
+    for name, arr, n in zip(_MIX_NAMES, a, (n1, n1, n1, n2, n2, n2)):
+        if len(arr) != n:
+            raise GosmaArgumentError("%s has %d rows, expected %d" % (name, len(arr), n))
+    return a
+
+
+def _class_arrays(n1c, n2c, w, n1, n2):
+    """Class sizes (int32) and weights of a semantic problem; the sizes must
+    add up to the mixtures' lengths, which the library does not see."""
+    n1c = np.ascontiguousarray(np.asarray(n1c, dtype=np.int32).reshape(-1))
+    n2c = np.ascontiguousarray(np.asarray(n2c, dtype=np.int32).reshape(-1))
+    w = _f64(w, (-1,))
+    if not len(n1c) == len(n2c) == len(w):
+        raise GosmaArgumentError("n1c, n2c and w have %d, %d and %d entries" % (len(n1c), len(n2c), len(w)))
+    if int(n1c.astype(np.int64).sum()) != n1 or int(n2c.astype(np.int64).sum()) != n2:
+        raise GosmaArgumentError("class sizes add up to %d x %d components, the mixtures have %d x %d"
+                         % (n1c.astype(np.int64).sum(), n2c.astype(np.int64).sum(), n1, n2))
+    return n1c, n2c, w
+
+
+def _dev(t, name, dtype, shape, device):
+    """A device buffer handed to the library: a torch tensor of `dtype` and
+    exactly `shape`, C-contiguous, on CUDA device `device`.  The library sees
+    only the pointer, so a smaller or differently typed buffer would let a
+    kernel run past it; such tensors are refused here."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise GosmaArgumentError("%s: expected a torch tensor, got %s" % (name, type(t).__name__))
+    if t.dtype != dtype:
+        raise GosmaArgumentError("%s: expected %s, got %s" % (name, dtype, t.dtype))
+    if tuple(t.shape) != tuple(shape):
+        raise GosmaArgumentError("%s: expected shape %s, got %s" % (name, tuple(shape), tuple(t.shape)))
+    if not t.is_contiguous():
+        raise GosmaArgumentError("%s: must be contiguous" % name)
+    if not t.is_cuda or t.device.index != device:
+        raise GosmaArgumentError("%s: must be a CUDA tensor on cuda:%d, got %s" % (name, device, t.device))
+    return C.c_void_p(t.data_ptr())
 
 
 class Gosma:
@@ -195,8 +249,7 @@ class Gosma:
 
     # ---------------------------------------------------------------- set-up
     def set_mixtures(self, mu1, sigma1, phi1, mu2, kappa2, phi2):
-        mu1, sigma1, phi1 = _f64(mu1, (-1, 3)), _f64(sigma1, (-1,)), _f64(phi1, (-1,))
-        mu2, kappa2, phi2 = _f64(mu2, (-1, 3)), _f64(kappa2, (-1,)), _f64(phi2, (-1,))
+        mu1, sigma1, phi1, mu2, kappa2, phi2 = _mixture_arrays(mu1, sigma1, phi1, mu2, kappa2, phi2)
         self._check(self.L.gosma_set_mixtures(self.h, len(sigma1), _p(mu1), _p(sigma1), _p(phi1), len(kappa2),
                                               _p(mu2), _p(kappa2), _p(phi2)), "set_mixtures")
         self.n1, self.n2 = len(sigma1), len(kappa2)
@@ -207,11 +260,8 @@ class Gosma:
 
     def set_mixtures_classes(self, n1c, n2c, w, mu1, sigma1, phi1, mu2, kappa2, phi2):
         """Semantic form: per-class sizes n1c, n2c and weights w; arrays class by class."""
-        n1c = np.ascontiguousarray(np.asarray(n1c, dtype=np.int32))
-        n2c = np.ascontiguousarray(np.asarray(n2c, dtype=np.int32))
-        w = _f64(w, (-1,))
-        mu1, sigma1, phi1 = _f64(mu1, (-1, 3)), _f64(sigma1, (-1,)), _f64(phi1, (-1,))
-        mu2, kappa2, phi2 = _f64(mu2, (-1, 3)), _f64(kappa2, (-1,)), _f64(phi2, (-1,))
+        mu1, sigma1, phi1, mu2, kappa2, phi2 = _mixture_arrays(mu1, sigma1, phi1, mu2, kappa2, phi2)
+        n1c, n2c, w = _class_arrays(n1c, n2c, w, len(sigma1), len(kappa2))
         ip = C.POINTER(C.c_int)
         self._check(self.L.gosma_set_mixtures_classes(self.h, len(n1c), n1c.ctypes.data_as(ip), n2c.ctypes.data_as(ip),
                                                       _p(w), _p(mu1), _p(sigma1), _p(phi1), _p(mu2), _p(kappa2),
@@ -235,13 +285,14 @@ class Gosma:
         if _is_torch_cuda(cubes):
             import torch
             n = cubes.shape[0]
-            assert cubes.dtype == torch.float64 and cubes.is_contiguous() and cubes.shape[1] == 10
+            pc = _dev(cubes, "cubes", torch.float64, (n, 10), self.device)
             if lb is None:
                 lb = torch.empty(n, dtype=torch.float64, device=cubes.device)
             if ub is None:
                 ub = torch.empty(n, dtype=torch.float64, device=cubes.device)
-            self._check(self.L.gosma_eval_bounds(self.h, C.c_void_p(cubes.data_ptr()), n, C.c_void_p(lb.data_ptr()),
-                                                 C.c_void_p(ub.data_ptr()), 1), "eval_bounds")
+            pl = _dev(lb, "lb", torch.float64, (n,), self.device)
+            pu = _dev(ub, "ub", torch.float64, (n,), self.device)
+            self._check(self.L.gosma_eval_bounds(self.h, pc, n, pl, pu, 1), "eval_bounds")
             return lb, ub
         cubes = _f64(cubes, (-1, 10))
         n = cubes.shape[0]
@@ -256,10 +307,11 @@ class Gosma:
         if _is_torch_cuda(cubes):
             import torch
             n = cubes.shape[0]
+            pc = _dev(cubes, "cubes", torch.float64, (n, 10), self.device)
             if out is None:
                 out = torch.empty((n, 8), dtype=torch.float64, device=cubes.device)
-            self._check(self.L.gosma_eval_bounds_detail(self.h, C.c_void_p(cubes.data_ptr()), n,
-                                                        C.c_void_p(out.data_ptr()), 1), "eval_bounds_detail")
+            po = _dev(out, "out", torch.float64, (n, 8), self.device)
+            self._check(self.L.gosma_eval_bounds_detail(self.h, pc, n, po, 1), "eval_bounds_detail")
             return out
         cubes = _f64(cubes, (-1, 10))
         n = cubes.shape[0]
@@ -287,10 +339,11 @@ class Gosma:
         """Allocation-free f and gradient for callers that cannot let the
         library allocate: x_dev (count, 6) and out_dev (count, 7) are CUDA
         float64 tensors owned by the caller; asynchronous on the context stream."""
+        import torch
         n = x_dev.shape[0]
-        self._check(self.L.gosma_eval_objective_grad_noalloc(self.h, n, C.c_void_p(x_dev.data_ptr()),
-                                                             C.c_void_p(out_dev.data_ptr())),
-                    "eval_objective_grad_noalloc")
+        px = _dev(x_dev, "x_dev", torch.float64, (n, 6), self.device)
+        po = _dev(out_dev, "out_dev", torch.float64, (n, 7), self.device)
+        self._check(self.L.gosma_eval_objective_grad_noalloc(self.h, n, px, po), "eval_objective_grad_noalloc")
         return out_dev
 
     def _dp(self, fn, name, x, lam, max_iter, kmax, param, key):
@@ -324,10 +377,15 @@ class Gosma:
         iters (n,) int32 are CUDA tensors filled asynchronously on the context
         stream; returns them."""
         if _is_torch_cuda(x0):
+            import torch
             n = x0.shape[0]
-            ptr = lambda a: C.c_void_p(a.data_ptr()) if a is not None else None
-            self._check(self.L.gosma_sma_batch(self.h, n, ptr(x0), int(max_iter), int(precision), ptr(x), ptr(f),
-                                               ptr(grad), ptr(iters), 1), "sma_batch")
+            p0 = _dev(x0, "x0", torch.float64, (n, 6), self.device)
+            px = _dev(x, "x", torch.float64, (n, 6), self.device)
+            pf = _dev(f, "f", torch.float64, (n,), self.device)
+            pg = _dev(grad, "grad", torch.float64, (n, 6), self.device) if grad is not None else None
+            pi = _dev(iters, "iters", torch.int32, (n,), self.device) if iters is not None else None
+            self._check(self.L.gosma_sma_batch(self.h, n, p0, int(max_iter), int(precision), px, pf, pg, pi, 1),
+                        "sma_batch")
             return dict(x=x, f=f, grad=grad, iters=iters)
         x0 = _f64(x0, (-1, 6))
         n = x0.shape[0]
@@ -379,8 +437,7 @@ class Gosma:
         keep = []
         arr = (Problem * len(problems))()
         for k, pr in enumerate(problems):
-            a = [_f64(pr["mu1"], (-1, 3)), _f64(pr["sigma1"], (-1,)), _f64(pr["phi1"], (-1,)),
-                 _f64(pr["mu2"], (-1, 3)), _f64(pr["kappa2"], (-1,)), _f64(pr["phi2"], (-1,))]
+            a = _mixture_arrays(*(pr[k] for k in _MIX_NAMES))
             keep.append(a)
             p = arr[k]
             p.n1, p.mu1, p.sigma1, p.phi1 = len(a[1]), _p(a[0]), _p(a[1]), _p(a[2])
@@ -390,8 +447,7 @@ class Gosma:
                 p.t_hi[q] = float(pr["t_hi"][q])
             p.zeta = float(pr["zeta"])
             if "n1c" in pr:  # semantic problem
-                c = [np.ascontiguousarray(np.asarray(pr["n1c"], dtype=np.int32)),
-                     np.ascontiguousarray(np.asarray(pr["n2c"], dtype=np.int32)), _f64(pr["w"], (-1,))]
+                c = _class_arrays(pr["n1c"], pr["n2c"], pr["w"], len(a[1]), len(a[4]))
                 keep.append(c)
                 ip = C.POINTER(C.c_int)
                 p.nclass, p.n1c, p.n2c, p.w = len(c[0]), c[0].ctypes.data_as(ip), c[1].ctypes.data_as(ip), _p(c[2])
