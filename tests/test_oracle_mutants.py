@@ -1,0 +1,162 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each case below plants one mistake in a copy of the oracle's C source (a
+dropped term or factor, a wrong sign, index or comparison, a transposed
+operand, a missing clamp), builds that copy in a temporary directory and
+runs the pin tests (test_oracle_pins, test_oracle_mixgen, test_oracle_bnb)
+against it.  At least one pin must fail for every mutant; the oracle in the
+repository is not touched.  Mistakes that change only efficiency (which of
+rotation or translation is split, the L-BFGS direction's restart safeguard)
+or a documented reading (the scale of eps) are not listed: no correctness
+pin can see them.  Neither is phiZ of K at the (b_i, b_j) corner in place of
+the largest corner K in the self-pair bound: log Z(K) - k1 - k2 decreases in
+each concentration, so that form is a valid (slightly tighter) bound too.
+"""
+import concurrent.futures as cf
+import os
+import shutil
+import subprocess
+import sys
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+PINS = ["tests/test_oracle_pins.py", "tests/test_oracle_mixgen.py", "tests/test_oracle_bnb.py"]
+G = "gosma_oracle.c"
+M = "mixgen.c"
+
+# (what the mistake is, file, text in the oracle, text with the mistake)
+MUTANTS = [
+    # Eq. (Z), the vMF inner product, Eq. (vMF_PN_map)
+    ("log Z with e^-x for e^-2x", G, "return log(-expm1(-2.0 * x) / x);", "return log(-expm1(-x) / x);"),
+    ("qPN concentration without the +1", G, "    return q * q + 1.0;", "    return q * q;"),
+    ("pair term: difference in place of the sum in K", G, "w[k] = ka * ua[k] + kb * ub[k];",
+     "w[k] = ka * ua[k] - kb * ub[k];"),
+    ("pair term: normaliser of the wrong component", G, "return om_logZ(K) - om_logZ(ka) - om_logZ(kb);",
+     "return om_logZ(K) - om_logZ(ka) - om_logZ(ka);"),
+    # Rodrigues (Sec. 4.1)
+    ("Rodrigues: sign of one skew term", G, "R[1] = -A * z + B * (x * y);", "R[1] = A * z + B * (x * y);"),
+    ("Rodrigues: B over the angle, not its square", G, "B = (1.0 - cos(th)) / (th * th);",
+     "B = (1.0 - cos(th)) / th;"),
+    # Lemma 1
+    ("objective: cross sum not doubled", G, "    return self - 2.0 * cross;", "    return self - cross;"),
+    ("objective: model rotated by the transpose", G,
+     "        matvec(R, v + 3 * i, Rv);\n        for (int j = 0; j < n2; ++j)\n            cross +=",
+     "        matTvec(R, v + 3 * i, Rv);\n        for (int j = 0; j < n2; ++j)\n            cross +="),
+    ("C22: both means of a pair from the same component", G, "m->kappa2[j], m->mu2 + 3 * j));\n    return s;",
+     "m->kappa2[j], m->mu2 + 3 * i));\n    return s;"),
+    # gradient for SMA (Sec. 5)
+    ("gradient: sign of the rotation term", G, "gw[q] += -2.0 * term * gK * kap[i] * cr[q] / K;",
+     "gw[q] += 2.0 * term * gK * kap[i] * cr[q] / K;"),
+    ("gradient: sign of d kappa / dt", G, "dk[3 * i + q] = -2.0 * d[i] * v[3 * i + q] / s2;",
+     "dk[3 * i + q] = 2.0 * d[i] * v[3 * i + q] / s2;"),
+    ("gradient: right Jacobian of SO(3) in place of the left", G,
+     "J[k] = (k % 4 == 0 ? 1.0 : 0.0) + a * S[k] + b * S2[k];",
+     "J[k] = (k % 4 == 0 ? 1.0 : 0.0) - a * S[k] + b * S2[k];"),
+    ("gradient: sign of 1/x in d log Z / dx", G, "return 1.0 + 2.0 / expm1(2.0 * x) - 1.0 / x;",
+     "return 1.0 + 2.0 / expm1(2.0 * x) + 1.0 / x;"),
+    # Lemmas 2 and 3, the kappa interval
+    ("Lemma 2: sqrt(2) in place of sqrt(3)", G, "double p = sqrt(3.0) * r_hw;", "double p = sqrt(2.0) * r_hw;"),
+    ("Lemma 3: half of the vertices", G, "for (int vtx = 0; vtx < 8; ++vtx) {", "for (int vtx = 0; vtx < 4; ++vtx) {"),
+    ("Lemma 3: a point inside the cuboid gets 0", G, "if (inside) return M_PI;", "if (inside) return 0.0;"),
+    ("kappa interval: nearest face in place of the farthest", G, "double f = f1 > f2 ? f1 : f2;",
+     "double f = f1 < f2 ? f1 : f2;"),
+    ("kappa interval: distance to the far face below the cuboid", G, "if (p[k] < lo) e = lo - p[k];",
+     "if (p[k] < lo) e = hi - p[k];"),
+    # Theorem 1, self pairs
+    ("self pair i = j at the upper kappa", G, "        double k = a[i];\n        return w * 0.5 * k / tanh(k);",
+     "        double k = b[i];\n        return w * 0.5 * k / tanh(k);"),
+    ("self pair: one psi_t subtracted from A", G,
+     "double A = om_angle(v + 3 * i, v + 3 * j) + psi[i] + psi[j];",
+     "double A = om_angle(v + 3 * i, v + 3 * j) + psi[i] - psi[j];"),
+    ("self pair: A not clamped to pi", G, "    if (A > M_PI) A = M_PI;\n", "\n"),
+    ("self pair: exponent at the lower kappa ends", G, "double lg = (Kbb - b[i] - b[j]) + om_phiZ(Kmax)",
+     "double lg = (Kbb - a[i] - a[j]) + om_phiZ(Kmax)"),
+    # Theorem 1, cross pairs
+    ("cross pair: psi_r left out of B", G, "double B = om_angle(v + 3 * i, u) - psi[i] - psir;",
+     "double B = om_angle(v + 3 * i, u) - psi[i];"),
+    ("cross pair: B not clamped at 0", G, "    if (B < 0.0) B = 0.0;\n", "\n"),
+    ("cross pair: exponent at the upper kappa end", G, "double lg = (Ka - a[i] - k2)", "double lg = (Ka - b[i] - k2)"),
+    ("cross pair: phiZ at the lower kappa end", G, "- om_phiZ(b[i]) - om_phiZ(k2);", "- om_phiZ(a[i]) - om_phiZ(k2);"),
+    ("cross pair: image mean rotated by R0, not its inverse", G, "matTvec(R0, m->mu2 + 3 * j, u);",
+     "matvec(R0, m->mu2 + 3 * j, u);"),
+    # per-cube sums
+    ("cube lower bound: cross sum not doubled", G, "out[0] = slb - 2.0 * cub;", "out[0] = slb - cub;"),
+    ("cube upper bound: cross sum not doubled", G, "out[1] = cp.centre_feasible ? sc - 2.0 * cc : INFINITY;",
+     "out[1] = cp.centre_feasible ? sc - cc : INFINITY;"),
+    ("pi-ball test at radius 2 pi", G, "return sqrt(d2) > M_PI;", "return sqrt(d2) > 2.0 * M_PI;"),
+    # Algorithm 1
+    ("queue: highest lower bound first", G, "if (x->lb != y->lb) return x->lb < y->lb;",
+     "if (x->lb != y->lb) return x->lb > y->lb;"),
+    ("Algorithm 1: children kept when above d*", G, "if (lb < dstar) heap_push(&h, &ch[c]);",
+     "if (lb > dstar) heap_push(&h, &ch[c]);"),
+    ("branching: both rotation halves on the same side", G,
+     "c[CUBE_R0 + a] = p->cube[CUBE_R0 + a] + (((k >> a) & 1) ? h : -h);",
+     "c[CUBE_R0 + a] = p->cube[CUBE_R0 + a] + (((k >> a) & 1) ? h : h);"),
+    ("branching: both translation halves on the same side", G,
+     "c[CUBE_T0 + a] = p->cube[CUBE_T0 + a] + (((k >> a) & 1) ? h : -h);",
+     "c[CUBE_T0 + a] = p->cube[CUBE_T0 + a] + (((k >> a) & 1) ? -h : -h);"),
+    # SMA
+    ("SMA: Armijo test reversed", G, "if (fn <= f + 1e-4 * step * gd) {", "if (fn >= f + 1e-4 * step * gd) {"),
+    # mixture generation (Sec. 6)
+    ("GMM fit: sigma^2 without the factor 3", M, "double s = sqrt(ss[c] / (3.0 * (double)cnt[c]));",
+     "double s = sqrt(ss[c] / ((double)cnt[c]));"),
+    ("vMF fit: sign of 1/kappa in the mean resultant length", M, "return 1.0 / tanh(k) - 1.0 / k;",
+     "return 1.0 / tanh(k) + 1.0 / k;"),
+    ("vMF fit: mean length without the coordinate scale", M,
+     "sqrt((s0 * s0 + s1 * s1) + s2 * s2) / (scale * (double)cnt[c]);",
+     "sqrt((s0 * s0 + s1 * s1) + s2 * s2) / ((double)cnt[c]);"),
+    ("cosine: wrong coordinate of the centre", M, "if (vmf) return (x[0] * m[0] + x[1] * m[1]) + x[2] * m[2];",
+     "if (vmf) return (x[0] * m[0] + x[1] * m[1]) + x[2] * m[1];"),
+    ("DP-means: a new cluster below lambda", M, "return vmf ? best < lambda : best > lambda;",
+     "return vmf ? best < lambda : best < lambda;"),
+    ("DP-means: empty clusters kept", M, "            if (cnt[c] == 0) {\n                remap[c] = -1;",
+     "            if (0) {\n                remap[c] = -1;"),
+    ("DP-means: start at the first point, not the mean", M,
+     "    mg_centre(vmf, S, n, xq, cen);\n    for (pass = 0;", "    memcpy(cen, xq, 3 * sizeof(double));\n    for (pass = 0;"),
+    ("weights over the number of clusters", M, "phi[c] = (double)cnt[c] / (double)n;",
+     "phi[c] = (double)cnt[c] / (double)K;"),
+]
+
+
+def _workspace(tmp):
+    """A copy of tests/ and oracle/ (sources only) beside a link to the package."""
+    shutil.copytree(os.path.join(ROOT, "tests"), os.path.join(tmp, "tests"),
+                    ignore=shutil.ignore_patterns("__pycache__", "test_oracle_mutants.py"))
+    os.mkdir(os.path.join(tmp, "oracle"))
+    for f in ("__init__.py", G, M, "mlp_oracle.py"):
+        shutil.copy(os.path.join(ROOT, "oracle", f), os.path.join(tmp, "oracle", f))
+    os.symlink(os.path.join(ROOT, "paper_1812_01232_gb300"), os.path.join(tmp, "paper_1812_01232_gb300"))
+
+
+def _run(case):
+    name, fname, old, new = case
+    tmp = tempfile.mkdtemp(prefix="oracle_mutant_")
+    try:
+        _workspace(tmp)
+        path = os.path.join(tmp, "oracle", fname)
+        src = open(path).read()
+        assert src.count(old) == 1, "%s: the text to change must occur exactly once" % name
+        open(path, "w").write(src.replace(old, new))
+        env = dict(os.environ, PYTHONDONTWRITEBYTECODE="1", OMP_NUM_THREADS="2")
+        try:
+            p = subprocess.run([sys.executable, "-m", "pytest", *PINS, "-x", "-q", "-p", "no:cacheprovider",
+                                "-m", "not gpu"], cwd=tmp, env=env, capture_output=True, text=True, timeout=600)
+        except subprocess.TimeoutExpired:
+            return name, False, "timed out"
+        failed = [ln.split(" ")[1] for ln in p.stdout.splitlines() if ln.startswith("FAILED ")]
+        if p.returncode == 1 and failed:
+            return name, True, failed[0]
+        return name, False, "exit %d %s" % (p.returncode, p.stdout[-300:] + p.stderr[-300:])
+    finally:
+        shutil.rmtree(tmp, ignore_errors=True)
+
+
+@pytest.mark.skipif(shutil.which("gcc") is None, reason="the oracle is built with gcc")
+def test_every_planted_mistake_fails_a_pin():
+    workers = max(1, min(8, (os.cpu_count() or 2) // 2))
+    with cf.ThreadPoolExecutor(workers) as ex:
+        results = list(ex.map(_run, MUTANTS))
+    survivors = [(n, why) for n, caught, why in results if not caught]
+    assert not survivors, "mistakes no pin catches: %s" % survivors

@@ -206,6 +206,87 @@ def test_kappa_interval_contains_sampled_kappas(oracle_mod):
         assert k.min() >= ab[0] * (1 - 1e-12) and k.max() <= ab[1] * (1 + 1e-12)
 
 
+# ------------------------------------------------- Theorem 1 per pair, by brute force over its relaxation
+def _term_grid(oracle_mod, k1s, k2s, angles):
+    """Z(K)/(Z(k1)Z(k2)) from the pinned pair_log on a grid of concentrations
+    and angles between the two mean directions."""
+    u = np.array([1.0, 0.0, 0.0])
+    out = np.empty((len(k1s), len(k2s), len(angles)))
+    for c, ang in enumerate(angles):
+        w = np.array([np.cos(ang), np.sin(ang), 0.0])
+        for a, k1 in enumerate(k1s):
+            for b, k2 in enumerate(k2s):
+                out[a, b, c] = np.exp(oracle_mod.pair_log(k1, u, k2, w))
+    return out
+
+
+def _box_grid(lo, hi, n):
+    """Both ends, evenly and geometrically spaced points of [lo, hi]."""
+    return np.unique(np.concatenate([np.linspace(lo, hi, n), np.geomspace(lo, hi, n)]))
+
+
+def test_self_pair_bound_below_the_term_over_its_relaxation(oracle_mod):
+    """Theorem 1, self pairs: over the cuboid, kappa_1i and kappa_1j stay in
+    their intervals and the angle between the two mean directions stays at
+    most A (Eq. K1i1j_lb_A with Lemma 3), so the bound must not exceed the
+    pair term anywhere on that box of (kappa_1i, kappa_1j, angle); broad
+    components keep the concentrations small, where every factor matters."""
+    rng = np.random.default_rng(14)
+    zeta, checked, wide = 0.05, 0, 0
+    for _ in range(120):
+        mu1 = rng.uniform(-2, 2, (2, 3))
+        prob = {"mu1": mu1, "sigma1": rng.uniform(0.1, 1.0, 2), "phi1": np.array([0.3, 0.7]),
+                "mu2": np.array([[0.0, 0.0, 1.0]]), "kappa2": np.array([5.0]), "phi2": np.array([1.0])}
+        mix = oracle_mod.Mixtures.from_problem(prob)
+        cube = np.concatenate([[0.0, 0.0, 0.0, 0.1], rng.uniform(-1, 1, 3), rng.uniform(0.05, 1.0, 3)])
+        t0, thw = cube[4:7], cube[7:10]
+        ab = [oracle_mod.kappa_interval(mu1[i], prob["sigma1"][i], t0, thw, zeta) for i in range(2)]
+        if ab[0] is None or ab[1] is None:
+            continue
+        v = (mu1 - t0) / np.linalg.norm(mu1 - t0, axis=1, keepdims=True)
+        A = min(oracle_mod.angle(v[0], v[1]) + oracle_mod.psi_t(mu1[0], t0, thw) + oracle_mod.psi_t(mu1[1], t0, thw),
+                np.pi)
+        lb = oracle_mod.self_lb_term(mix, 0, 1, cube, zeta) / (0.3 * 0.7)
+        T = _term_grid(oracle_mod, _box_grid(*ab[0], 10), _box_grid(*ab[1], 10), np.linspace(0.0, A, 5))
+        assert lb <= T.min() * (1 + 1e-12)
+        # the diagonal pair (i, i): the same direction at every t, only kappa varies
+        lii = oracle_mod.self_lb_term(mix, 0, 0, cube, zeta) / 0.09
+        assert lii <= _term_grid(oracle_mod, _box_grid(*ab[0], 20), _box_grid(*ab[0], 20), [0.0]).min() * (1 + 1e-12)
+        checked += 1
+        wide += A > np.pi / 2
+    assert checked > 100 and wide > 10 and checked - wide > 10  # both sides of A = pi/2
+
+
+def test_cross_pair_bound_above_the_term_over_its_relaxation(oracle_mod):
+    """Theorem 1, cross pairs: over the cube, kappa_1i stays in its interval
+    and the angle between R v_i and mu_2j stays at least B (Eq. K1i2j_ub_B
+    with Lemmas 2 and 3), so the bound must not fall below the pair term
+    anywhere on that box of (kappa_1i, angle)."""
+    rng = np.random.default_rng(15)
+    zeta, checked = 0.05, 0
+    for _ in range(150):
+        mu1 = rng.uniform(-2, 2, (1, 3))
+        m2 = rng.standard_normal(3)
+        k2 = rng.uniform(1.0, 60.0)
+        prob = {"mu1": mu1, "sigma1": rng.uniform(0.1, 1.0, 1), "phi1": np.array([1.0]),
+                "mu2": (m2 / np.linalg.norm(m2))[None], "kappa2": np.array([k2]), "phi2": np.array([1.0])}
+        mix = oracle_mod.Mixtures.from_problem(prob)
+        r_hw = rng.uniform(0.05, 1.0)
+        cube = np.concatenate([rng.uniform(-1.5, 1.5, 3), [r_hw], rng.uniform(-1, 1, 3), rng.uniform(0.05, 1.0, 3)])
+        t0, thw = cube[4:7], cube[7:10]
+        ab = oracle_mod.kappa_interval(mu1[0], prob["sigma1"][0], t0, thw, zeta)
+        if ab is None:
+            continue
+        v = (mu1[0] - t0) / np.linalg.norm(mu1[0] - t0)
+        u = Rotation.from_rotvec(cube[0:3]).as_matrix().T @ prob["mu2"][0]
+        B = max(oracle_mod.angle(v, u) - oracle_mod.psi_t(mu1[0], t0, thw) - oracle_mod.psi_r(r_hw), 0.0)
+        ub = oracle_mod.cross_ub_term(mix, 0, 0, cube, zeta)
+        T = _term_grid(oracle_mod, _box_grid(*ab, 30), [k2], np.linspace(B, np.pi, 6))
+        assert ub >= T.max() * (1 - 1e-12)
+        checked += 1
+    assert checked > 100
+
+
 # ------------------------------------------------- Theorem 1 by dense sampling
 def _pose_pair_terms(oracle_mod, prob, R, t):
     """All self and cross pair terms of Eq. (objective_function) at one pose,
