@@ -1,16 +1,18 @@
 """The oracle's pins catch plausible mistakes.
 
-Each case below plants one mistake in a copy of the oracle's C source (a
+Each case below plants one mistake in a copy of the oracle's source (a
 dropped term or factor, a wrong sign, index or comparison, a transposed
 operand, a missing clamp), builds that copy in a temporary directory and
-runs the pin tests (test_oracle_pins, test_oracle_mixgen, test_oracle_bnb)
-against it.  At least one pin must fail for every mutant; the oracle in the
-repository is not touched.  Mistakes that change only efficiency (which of
-rotation or translation is split, the L-BFGS direction's restart safeguard)
-or a documented reading (the scale of eps) are not listed: no correctness
-pin can see them.  Neither is phiZ of K at the (b_i, b_j) corner in place of
-the largest corner K in the self-pair bound: log Z(K) - k1 - k2 decreases in
-each concentration, so that form is a valid (slightly tighter) bound too.
+runs the pin tests (test_oracle_pins, test_oracle_mixgen, test_oracle_mlp,
+test_oracle_bnb) against it; the network's FP64 reference (an extension)
+gets the same treatment.  At least one pin must fail for every mutant; the
+oracle in the repository is not touched.  Mistakes that change only
+efficiency (which of rotation or translation is split, the L-BFGS
+direction's restart safeguard) or a documented reading (the scale of eps)
+are not listed: no correctness pin can see them.  Neither is phiZ of K at
+the (b_i, b_j) corner in place of the largest corner K in the self-pair
+bound: log Z(K) - k1 - k2 decreases in each concentration, so that form is a
+valid (slightly tighter) bound too.
 """
 import concurrent.futures as cf
 import os
@@ -22,9 +24,11 @@ import tempfile
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-PINS = ["tests/test_oracle_pins.py", "tests/test_oracle_mixgen.py", "tests/test_oracle_bnb.py"]
+PINS = ["tests/test_oracle_pins.py", "tests/test_oracle_mixgen.py", "tests/test_oracle_mlp.py",
+        "tests/test_oracle_bnb.py"]
 G = "gosma_oracle.c"
 M = "mixgen.c"
+N = "mlp_oracle.py"
 
 # (what the mistake is, file, text in the oracle, text with the mistake)
 MUTANTS = [
@@ -117,6 +121,23 @@ MUTANTS = [
      "    mg_centre(vmf, S, n, xq, cen);\n    for (pass = 0;", "    memcpy(cen, xq, 3 * sizeof(double));\n    for (pass = 0;"),
     ("weights over the number of clusters", M, "phi[c] = (double)cnt[c] / (double)n;",
      "phi[c] = (double)cnt[c] / (double)K;"),
+    # the queue-ordering network's reference (an extension)
+    ("BF16: ties rounded up, not to even", N, "bias = 0x7FFF + ((u >> 16) & 1)", "bias = 0x8000 + 0 * u"),
+    ("GELU: erf of z, not z / sqrt 2", N, "return 0.5 * z * (1.0 + _erf(z / SQRT2))",
+     "return 0.5 * z * (1.0 + _erf(z))"),
+    ("GELU derivative: sign of the density term", N, "+ z * np.exp(-0.5 * z * z)", "- z * np.exp(-0.5 * z * z)"),
+    ("forward: second layer's weights transposed", N, 'z2 = h1 @ W2.T + p["b2"]', 'z2 = h1 @ W2 + p["b2"]'),
+    ("backward: W2 gradient from the wrong activation", N, 'g["W2"] = dz2.T @ cache["h1"]',
+     'g["W2"] = dz2.T @ cache["h2"]'),
+    ("backward: first layer's GELU derivative at z2", N, 'gelu_grad(cache["z1"])', 'gelu_grad(cache["z2"])'),
+    ("loss: sign in the logistic gradient", N, "dy[:, 0] = (1.0 / (1.0 + np.exp(-s)) - label) / n",
+     "dy[:, 0] = (1.0 / (1.0 + np.exp(s)) - label) / n"),
+    ("loss: seed gradient without the 2", N, "dy[:, 1:1 + N_SEED] = 2.0 * lam * label[:, None] * r / n",
+     "dy[:, 1:1 + N_SEED] = lam * label[:, None] * r / n"),
+    ("loss: seed term for negative labels too", N, "loss = (bce + lam * label * (r * r).sum(1)).mean()",
+     "loss = (bce + lam * (r * r).sum(1)).mean()"),
+    ("packing: biases and weights in another order", N,
+     'for k in ("W1", "b1", "W2", "b2", "W3", "b3")])', 'for k in ("W1", "W2", "b1", "b2", "W3", "b3")])'),
 ]
 
 
