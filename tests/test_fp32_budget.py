@@ -1,0 +1,303 @@
+"""The bound kernel's FP32 error budget, replayed on the CPU.
+
+On the device the pair terms of Theorem 1 run in FP32 with the approximate
+ex2 / rcp / sqrt instructions, and a slack is meant to keep every cross
+upper bound at or above, and every self lower bound at or below, the exact
+value (cross_pair and self_pair in csrc/bounds_core.cuh, whose header states
+the budget).  This test replays the bound part of those two functions in
+numpy float32, operation by operation: plain operations rounded to nearest,
+the fused multiply-adds the source writes rounded once, and every
+approximate instruction off by its documented error bound (ex2 3u, rcp and
+sqrt 2u, u = 2^-24) in either direction: all sign combinations for the
+cross pair, random ones plus the all-low and all-high cases for the self
+pair.  The inputs are what the kernel's first phase stores, at the edge of
+that phase's own allowances: directions as double-floats, kappa interval
+ends at a(1 - u) and b(1 + u), half-angle sines rounded up and cosines down,
+kappa_2 and the column factor rounded to nearest.  The geometry (kappa
+intervals, psi_t, psi_r, directions) comes from the FP64 oracle, and the
+replayed bound must never cross the oracle's pair bound for the same cube.
+On these 3,000 cubes the smallest margins are 22.5u (cross) and 36u (self):
+a dropped angle allowance, the wrong end of a sine interval or clamp, or a
+slack of the wrong sign crosses the oracle, while each few-u rounding
+direction on its own stays inside the margin.
+"""
+import itertools
+
+import numpy as np
+import pytest
+from scipy.spatial.transform import Rotation
+
+U = 2.0 ** -24
+F = np.float32
+
+
+def f32(x):
+    return np.asarray(x, dtype=np.float64).astype(np.float32)
+
+
+def fma(a, b, c):
+    """fmaf: the exact product plus c, rounded once (through FP64: the product
+    of two floats is exact there)."""
+    return (np.float64(1) * a.astype(np.float64) * b.astype(np.float64) + np.asarray(c, np.float64)).astype(np.float32)
+
+
+def ftz(x):
+    return np.where(np.abs(x) < 2.0 ** -126, np.float32(0), x).astype(np.float32)
+
+
+def toward(v, d):
+    """v (FP64) to float32, rounded down where d < 0 and up where d > 0."""
+    y = v.astype(np.float32)
+    yd = y.astype(np.float64)
+    y = np.where((d < 0) & (yd > v), np.nextafter(y, np.float32(-np.inf)), y)
+    y = np.where((d > 0) & (yd < v), np.nextafter(y, np.float32(np.inf)), y)
+    return y.astype(np.float32)
+
+
+def approx(exact, s, rel):
+    """An approximate instruction's result: exact (1 + s rel), rounded toward
+    exact so that it stays within the bound; outputs flushed to zero."""
+    v = exact * (1.0 + s * rel)
+    return ftz(toward(v, -s * np.ones_like(v)))
+
+
+def sqrta(x, s):
+    return approx(np.sqrt(ftz(x).astype(np.float64)), s, 2 * U)
+
+
+def rcpa(x, s):
+    return approx(1.0 / ftz(x).astype(np.float64), s, 2 * U)
+
+
+def ex2a(x, s):
+    return approx(np.exp2(ftz(x).astype(np.float64)), s, 3 * U)
+
+
+L2E = F(1.4426950408889634)
+FU = F(U)
+SLACK = F(15) * FU
+
+
+def c1(k):
+    """The float32 constant 1 + k u as the source writes it, (1.f + k * U)."""
+    return F(1) + F(k) * FU
+
+
+def c1m(k):
+    return F(1) - F(k) * FU
+
+
+def gZ(x, s):
+    return F(1) - ex2a(F(-2) * L2E * x, s)
+
+
+def split(v):
+    hi = f32(v)
+    return hi, f32(v - hi.astype(np.float64))
+
+
+def mul_rd(a, b):
+    return toward(a.astype(np.float64) * b.astype(np.float64), -np.ones(np.shape(a)))
+
+
+def mul_ru(a, b):
+    return toward(a.astype(np.float64) * b.astype(np.float64), np.ones(np.shape(a)))
+
+
+# ---------------------------------------------------------------- inputs from the oracle's geometry
+def _cases(oracle_mod, rng, n):
+    """Random two-component model, one image component and a cube, with the
+    oracle's kappa intervals, psi_t, psi_r, directions and pair bounds."""
+    out = []
+    while len(out) < n:
+        mu1 = rng.uniform(-3, 3, (2, 3))
+        sig = np.exp(rng.uniform(np.log(0.02), np.log(0.5), 2))
+        t0 = rng.uniform(-1, 1, 3)
+        thw = np.exp(rng.uniform(np.log(1e-4), np.log(1.0), 3))
+        if rng.random() < 0.2:  # row 0's mean next to or inside the cuboid: psi_t up to pi
+            mu1[0] = t0 + rng.uniform(-2, 2, 3) * thw
+        r0 = Rotation.random(random_state=rng).as_rotvec() * rng.uniform(0, 1)
+        rhw = np.exp(rng.uniform(np.log(1e-4), np.log(1.0)))
+        R0 = Rotation.from_rotvec(r0).as_matrix()
+        v = (mu1 - t0) / np.linalg.norm(mu1 - t0, axis=1, keepdims=True)
+        mode = rng.integers(3)  # image direction: anywhere, near R0 v_0, near -R0 v_0
+        ang = rng.uniform(0, 3.0 * rhw + 1e-3)
+        axis = np.cross(v[0], rng.standard_normal(3))
+        near = Rotation.from_rotvec(axis / np.linalg.norm(axis) * ang).apply(v[0])
+        m2 = [rng.standard_normal(3), R0 @ near, -(R0 @ near)][mode]
+        m2 /= np.linalg.norm(m2)
+        k2 = np.exp(rng.uniform(0, np.log(2000.0)))
+        prob = {"mu1": mu1, "sigma1": sig, "phi1": np.array([0.4, 0.6]), "mu2": m2[None], "kappa2": np.array([k2]),
+                "phi2": np.array([1.0])}
+        mix = oracle_mod.Mixtures.from_problem(prob)
+        zeta = 0.01
+        ab = [oracle_mod.kappa_interval(mu1[i], sig[i], t0, thw, zeta) for i in range(2)]
+        if ab[0] is None or ab[1] is None:
+            continue
+        cube = np.concatenate([r0, [rhw], t0, thw])
+        out.append(dict(
+            v=v, u=R0.T @ m2, k2=k2, phi1=prob["phi1"], phi2=1.0, a=np.array([ab[0][0], ab[1][0]]),
+            b=np.array([ab[0][1], ab[1][1]]),
+            psit=np.array([oracle_mod.psi_t(mu1[i], t0, thw) for i in range(2)]), psir=oracle_mod.psi_r(rhw),
+            cross=oracle_mod.cross_ub_term(mix, 0, 0, cube, zeta),
+            self2=oracle_mod.self_lb_term(mix, 0, 1, cube, zeta) + oracle_mod.self_lb_term(mix, 1, 0, cube, zeta)))
+    return {k: np.array([c[k] for c in out]) for k in out[0]}
+
+
+def _rows(c):
+    """What the first phase stores for each model row (at the edge of its allowances)."""
+    a = toward(c["a"] * (1 - U), -np.ones_like(c["a"]))
+    b = toward(c["b"] * (1 + U), np.ones_like(c["b"]))
+    wide = c["psit"] >= np.pi
+    sp = np.where(wide, F(1), toward(np.sin(0.5 * c["psit"]), np.ones_like(c["psit"])))
+    cp = np.where(wide, F(0), toward(np.cos(0.5 * c["psit"]), -np.ones_like(c["psit"])))
+    return a, b, sp.astype(np.float32), cp.astype(np.float32)
+
+
+# ---------------------------------------------------------------- cross pair
+def _cross(c, s):
+    """Upper bound of the cross pair (row 0, the image component) as the
+    kernel forms it, times its row factor; s: signs of the 10 approximate
+    instructions on the path."""
+    a, b, sp, cp = _rows(c)
+    a, b, sp, cp = a[:, 0], b[:, 0], sp[:, 0], cp[:, 0]
+    vh, vl = split(c["v"][:, 0])
+    uh, ul = split(c["u"])
+    k2 = f32(c["k2"])
+    Q = f32(c["phi2"] * c["k2"] / -np.expm1(-2 * c["k2"]))
+    Sr = toward(np.sin(0.5 * c["psir"]), np.ones_like(c["psir"]))
+    Cr = toward(np.cos(0.5 * c["psir"]), -np.ones_like(c["psir"]))
+    Cs = f32(cp.astype(np.float64) * Cr - sp.astype(np.float64) * Sr)
+    Ss = f32(sp.astype(np.float64) * Cr + cp.astype(np.float64) * Sr)
+    Ss = np.where(Cs <= 0, F(1), Ss).astype(np.float32)
+    Cs = np.where(Cs <= 0, F(0), Cs).astype(np.float32)
+    esS = (F(7.5) * FU) * Ss
+    d = [(vh[:, k] - uh[:, k]) + (vl[:, k] - ul[:, k]) for k in range(3)]
+    p = [(vh[:, k] + uh[:, k]) + (vl[:, k] + ul[:, k]) for k in range(3)]
+    x2 = fma(d[0], d[0], fma(d[1], d[1], d[2] * d[2]))
+    y2 = fma(p[0], p[0], fma(p[1], p[1], p[2] * p[2]))
+    sth, cth = F(0.5) * sqrta(x2, s[0]), F(0.5) * sqrta(y2, s[1])
+    sB = fma(sth, Cs, -(cth * Ss))
+    es = fma(np.full_like(sth, F(7.5) * FU), sth, esS)
+    slo = np.maximum(sB - es, F(0))
+    shi = np.minimum(np.maximum(sB, F(0)) + es, F(1))
+    chi = np.minimum(sqrta(fma(-slo, slo, np.ones_like(slo)), s[2]) * c1(3), F(1))
+    clo = sqrta(np.maximum(fma(-shi, shi, np.ones_like(shi)), F(0)), s[3]) * c1m(3)
+    A4 = F(4) * a
+    ak4 = A4 * k2
+    dka = a - k2
+    Khi = sqrta(fma(dka, dka, ak4 * (chi * chi)), s[4]) * c1(4)
+    cosBlo = fma(F(2) * clo, clo, -np.ones_like(clo))
+    ks = np.minimum(np.maximum(-k2 * cosBlo, a), b)
+    dks = ks - k2
+    Kmin = sqrta(fma(dks, dks, F(4) * ks * k2 * (clo * clo)), s[5]) * c1m(4)
+    den = (a + k2) + Khi
+    Kc = np.maximum(Kmin, F(1e-20))
+    r = rcpa(den * Kc, s[6])
+    DL = ak4 * (slo * slo) * (Kc * r) * (-L2E)
+    w = np.minimum(den * r, F(2))
+    term = fma(ex2a(fma(np.full_like(DL, F(12) * FU), np.abs(DL), DL + SLACK), s[7]), w * Q, np.zeros_like(w))
+    ph = f32(c["phi1"][:, 0])
+    Bw = np.where(b < F(9), ph * b * rcpa(gZ(b, s[8]), s[9]) * c1(12), ph * b).astype(np.float32)
+    Bw = mul_ru(Bw, np.full_like(Bw, c1(8 + 6)))
+    return term.astype(np.float64) * Bw.astype(np.float64)
+
+
+# ---------------------------------------------------------------- self pair
+def _aw(a, ph, s0, s1):
+    """phi a / g(a) from below (the row factor of the self lower bound)."""
+    return np.where(a < F(9), ph * a * rcpa(gZ(a, s0), s1) * c1m(12), mul_rd(ph * a, np.full_like(a, c1m(3))))
+
+
+def _self(c, s):
+    """Lower bound of the self pair (0, 1), both orders, as the kernel forms
+    it with its row factors; s: signs of the 13 approximate instructions."""
+    a, b, sp, cp = _rows(c)
+    vh, vl = split(c["v"][:, 0])
+    mh, ml = split(c["v"][:, 1])
+    ph = f32(c["phi1"])
+    Am = _aw(a[:, 1], ph[:, 1], s[9], s[10]).astype(np.float32)
+    Ai = _aw(a[:, 0], ph[:, 0], s[11], s[12]).astype(np.float32)
+    d = [(vh[:, k] - mh[:, k]) + (vl[:, k] - ml[:, k]) for k in range(3)]
+    p = [(vh[:, k] + mh[:, k]) + (vl[:, k] + ml[:, k]) for k in range(3)]
+    x2 = fma(d[0], d[0], fma(d[1], d[1], d[2] * d[2]))
+    y2 = fma(p[0], p[0], fma(p[1], p[1], p[2] * p[2]))
+    sth, cth = F(0.5) * sqrta(x2, s[0]), F(0.5) * sqrta(y2, s[1])
+    C = fma(cp[:, 0], cp[:, 1], -(sp[:, 0] * sp[:, 1]))
+    S = fma(sp[:, 0], cp[:, 1], cp[:, 0] * sp[:, 1])
+    cA = fma(cth, C, -(sth * S))
+    sA = fma(sth, C, cth * S)
+    es = (F(10) * FU) * (sth + np.abs(S))
+    api = cA <= F(16) * FU
+    shi = np.where(api, F(1), np.minimum(sA + es, F(1))).astype(np.float32)
+    slo = np.maximum(sA - es, F(0))
+    clo = sqrta(np.maximum(fma(-shi, shi, np.ones_like(shi)), F(0)), s[2]) * c1m(3)
+    chi = np.minimum(sqrta(fma(-slo, slo, np.ones_like(slo)), s[3]) * c1(3), F(1))
+    ai, bi, am, bm = a[:, 0], b[:, 0], a[:, 1], b[:, 1]
+    bb = bi * bm
+    dbb = bi - bm
+    Klo = sqrta(fma(dbb, dbb, F(4) * bb * (clo * clo)), s[4]) * c1m(4)
+    c4 = F(4) * (chi * chi)
+    q1, q2, q3 = ai - am, ai - bm, bi - am
+    e1 = fma(q1, q1, c4 * ai * am)
+    e2 = fma(q2, q2, c4 * ai * bm)
+    e3 = fma(q3, q3, c4 * bi * am)
+    e4 = fma(dbb, dbb, c4 * bb)
+    Kmax = sqrta(np.maximum(np.maximum(e1, e2), np.maximum(e3, e4)), s[5]) * c1(5)
+    den = (bi + bm) + Klo
+    r = rcpa(den * Kmax, s[6])
+    DL = bb * (shi * shi) * (Kmax * r) * (F(-4) * L2E)
+    w = den * r
+    small = Kmax < F(0.25)
+    w = np.where(Kmax < F(9), np.where(small, np.maximum(F(2) - F(2) * Kmax, F(0)), gZ(Kmax, s[7]) * w * c1m(64)), w)
+    w = w.astype(np.float32)
+    term = fma(ex2a(DL - fma(np.full_like(DL, F(12) * FU), np.abs(DL), np.full_like(DL, SLACK)), s[8]), w * Am,
+               np.zeros_like(w))
+    Awi = mul_rd(F(2) * Ai, np.full_like(Ai, c1m(8 + 3)))
+    return term.astype(np.float64) * Awi.astype(np.float64)
+
+
+# Terms below this leave FP32's normal range after the exponential and flush
+# to zero; the per-cube allowance of 1e-12 S (S >= the diagonal self terms
+# sum_i phi_i^2 a_i coth(a_i) / 2 >= 1 / (2 n1)) covers far more than all of
+# them together, so the cross check starts here.
+FLOOR = 1e-30
+
+
+@pytest.fixture(scope="module")
+def cases(oracle_mod):
+    return _cases(oracle_mod, np.random.default_rng(17), 3000)
+
+
+def test_cross_upper_bound_never_below_the_oracle(cases):
+    worst = np.inf
+    for signs in itertools.product((-1.0, 1.0), repeat=10):
+        ub = _cross(cases, signs)
+        ref = cases["cross"]
+        ok = ref > FLOOR
+        ratio = ub[ok] / ref[ok]
+        worst = min(worst, ratio.min())
+        assert np.all(ub[ok] >= ref[ok]), (signs, ratio.min())
+    assert worst >= 1.0
+
+
+def test_self_lower_bound_never_above_the_oracle(cases):
+    rng = np.random.default_rng(18)
+    combos = [(-1.0,) * 13, (1.0,) * 13] + [tuple(rng.choice([-1.0, 1.0], 13)) for _ in range(400)]
+    for signs in combos:
+        lb = _self(cases, signs)
+        ref = cases["self2"]
+        assert np.all(lb <= ref), (signs, np.max(lb / np.maximum(ref, 1e-300)))
+        # and it stays close: the slack costs little where the term matters
+        big = ref > FLOOR
+        assert np.median(lb[big] / ref[big]) > 0.999
+
+
+def test_the_cases_reach_every_regime(cases):
+    """Near-aligned and near-antipodal pairs, tiny and pi-wide uncertainty
+    angles, small and large concentrations."""
+    ang = np.arccos(np.clip(np.sum(cases["v"][:, 0] * cases["u"], 1), -1, 1))
+    assert (ang < 1e-2).sum() > 50 and (ang > np.pi - 1e-2).sum() > 50
+    assert (cases["psit"][:, 0] >= np.pi).sum() > 100 and (cases["psit"][:, 0] < 1e-2).sum() > 100
+    assert (cases["a"][:, 0] < 9).sum() > 100 and (cases["a"][:, 0] > 1e4).sum() > 100
+    assert (cases["k2"] < 9).sum() > 100
