@@ -140,7 +140,8 @@ def _cases(oracle_mod, rng, n):
             b=np.array([ab[0][1], ab[1][1]]),
             psit=np.array([oracle_mod.psi_t(mu1[i], t0, thw) for i in range(2)]), psir=oracle_mod.psi_r(rhw),
             cross=oracle_mod.cross_ub_term(mix, 0, 0, cube, zeta),
-            self2=oracle_mod.self_lb_term(mix, 0, 1, cube, zeta) + oracle_mod.self_lb_term(mix, 1, 0, cube, zeta)))
+            self2=oracle_mod.self_lb_term(mix, 0, 1, cube, zeta) + oracle_mod.self_lb_term(mix, 1, 0, cube, zeta),
+            diag=oracle_mod.self_lb_term(mix, 0, 0, cube, zeta)))
     return {k: np.array([c[k] for c in out]) for k in out[0]}
 
 
@@ -264,6 +265,16 @@ def _self(c, s):
 FLOOR = 1e-30
 
 
+def _diag(c, s):
+    """Diagonal self term phi^2 a coth(a) / 2 from below (half_kcothk at the
+    row's a, its 16u allowance, and the 3u the row sums start with)."""
+    a = _rows(c)[0][:, 0]
+    ph = f32(c["phi1"][:, 0])
+    e = ex2a(F(-2) * L2E * a, s[0])
+    h = F(0.5) * a * (F(1) + e) * rcpa(F(1) - e, s[1])
+    return (ph * ph * h * c1m(16)).astype(np.float64) * (1 - 3 * U)
+
+
 @pytest.fixture(scope="module")
 def cases(oracle_mod):
     return _cases(oracle_mod, np.random.default_rng(17), 3000)
@@ -291,6 +302,11 @@ def test_self_lower_bound_never_above_the_oracle(cases):
         # and it stays close: the slack costs little where the term matters
         big = ref > FLOOR
         assert np.median(lb[big] / ref[big]) > 0.999
+
+
+def test_diagonal_self_term_never_above_the_oracle(cases):
+    for signs in itertools.product((-1.0, 1.0), repeat=2):
+        assert np.all(_diag(cases, signs) <= cases["diag"])
 
 
 def test_the_cases_reach_every_regime(cases):
