@@ -309,6 +309,59 @@ def test_diagonal_self_term_never_above_the_oracle(cases):
         assert np.all(_diag(cases, signs) <= cases["diag"])
 
 
+def test_kappa_interval_rounded_outward(oracle_mod):
+    """The first phase's kappa interval in FP32 (double-float differences,
+    FP32 squares and sums, the end points multiplied by 1 -/+ 7u and rounded
+    down / up): never inside the oracle's [a, b]; and a cuboid the kernel
+    calls infeasible has no point at least zeta from the mean."""
+    rng = np.random.default_rng(19)
+    n = 20000
+    mu = rng.uniform(-3, 3, (n, 3))
+    t0 = rng.uniform(-1, 1, (n, 3))
+    thw = np.exp(rng.uniform(np.log(1e-5), np.log(1.0), (n, 3)))
+    near = rng.random(n) < 0.5
+    mu[near] = t0[near] + rng.uniform(-1.5, 1.5, (near.sum(), 3)) * thw[near]
+    sig = np.exp(rng.uniform(np.log(0.01), np.log(1.0), n))
+    zeta = np.where(rng.random(n) < 0.5, 0.0, np.exp(rng.uniform(np.log(1e-4), np.log(2.0), n)))
+    # the last quarter on the feasibility boundary: the farthest vertex at zeta (1 + delta), |delta| <= 30u
+    m = n // 4
+    zb = np.exp(rng.uniform(np.log(0.1), np.log(2.0), m))
+    o = rng.uniform(-1, 1, (m, 3)) * rng.uniform(0, 0.25, (m, 1)) * zb[:, None]  # |o| < zeta / 2
+    dirn = rng.uniform(0.2, 1.0, (m, 3))
+    tgt = zb * (1 + rng.uniform(-30, 30, m) * U)
+    # solve sum_k (|o_k| + lam d_k)^2 = tgt^2 for lam > 0
+    qa, qb, qc = (dirn ** 2).sum(1), 2 * (np.abs(o) * dirn).sum(1), (o ** 2).sum(1) - tgt ** 2
+    lam = (-qb + np.sqrt(qb * qb - 4 * qa * qc)) / (2 * qa)
+    t0[-m:] = rng.uniform(-1, 1, (m, 3))
+    mu[-m:] = t0[-m:] + o
+    thw[-m:] = lam[:, None] * dirn
+    zeta[-m:] = zb
+    muh, mul = split(mu)
+    th, tl = split(t0)
+    wh, wl = split(thw)
+    c = (muh.astype(np.float64) + mul) - (th.astype(np.float64) + tl)  # double-float difference, ~2^-44
+    ac = np.abs(c)
+    e = np.maximum(f32(ac - (wh.astype(np.float64) + wl)), F(0))
+    f = f32(ac) + wh
+    e2 = fma(e[:, 2], e[:, 2], fma(e[:, 1], e[:, 1], fma(e[:, 0], e[:, 0], np.zeros(n, np.float32))))
+    f2 = fma(f[:, 2], f[:, 2], fma(f[:, 1], f[:, 1], fma(f[:, 0], f[:, 0], np.zeros(n, np.float32))))
+    z2 = f32(zeta * zeta)
+    is2 = f32(1.0 / (sig * sig))
+    a = mul_rd(fma(np.maximum(e2, z2), is2, np.ones(n, np.float32)), np.full(n, c1m(7)))
+    b = mul_ru(fma(f2, is2, np.ones(n, np.float32)), np.full(n, c1(7)))
+    infeasible = f2 * c1(8) < z2
+    checked = edge = 0
+    for k in range(n):
+        ab = oracle_mod.kappa_interval(mu[k], sig[k], t0[k], thw[k], zeta[k])
+        if ab is None:
+            continue
+        assert not infeasible[k], k
+        assert a[k] <= ab[0] and b[k] >= ab[1], (k, a[k], ab[0], b[k], ab[1])
+        checked += 1
+        edge += k >= n - m
+    assert checked > n // 2 and edge > m // 4
+
+
 def test_the_cases_reach_every_regime(cases):
     """Near-aligned and near-antipodal pairs, tiny and pi-wide uncertainty
     angles, small and large concentrations."""
