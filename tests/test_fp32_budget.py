@@ -362,6 +362,90 @@ def test_kappa_interval_rounded_outward(oracle_mod):
     assert checked > n // 2 and edge > m // 4
 
 
+def _sin_half_psi_t(mu, t0, thw, sg):
+    """sin(psi_t / 2) as the first phase stores it (Lemma 3): FP32 angles to
+    the eight vertices pick the largest, the double-float chord to that
+    vertex gives it, the FP32 runner-up times (1 + 32u) covers a mis-chosen
+    vertex, pi when the mean is inside or a vertex angle may reach pi/2.
+    sg(shape) draws the signs of the approximate instructions.  The vertex
+    loop runs for every case here and its results are masked afterwards
+    where the mean is inside (the kernel skips it there)."""
+    with np.errstate(divide="ignore", invalid="ignore"):
+        return _sin_half_psi_t_all(mu, t0, thw, sg)
+
+
+def _sin_half_psi_t_all(mu, t0, thw, sg):
+    n = len(mu)
+    muh, mul = split(mu)
+    th, tl = split(t0)
+    wh, wl = split(thw)
+    c = (muh.astype(np.float64) + mul) - (th.astype(np.float64) + tl)
+    w = wh.astype(np.float64) + wl
+    inside = np.all(np.abs(c) - w <= 0, axis=1)
+    ch, d2 = f32(c), f32((c * c).sum(1))
+    m1 = np.full(n, F(-1))
+    m2 = np.full(n, F(-1))
+    best = np.zeros(n, int)
+    wide = np.zeros(n, bool)
+    for vtx in range(8):
+        o = [np.where((vtx >> k) & 1, wh[:, k], -wh[:, k]).astype(np.float32) for k in range(3)]
+        ax, ay, az = (ch[:, k] - o[k] for k in range(3))
+        cx, cy, cz = ch[:, 0], ch[:, 1], ch[:, 2]
+        crx, cry, crz = fma(o[1], cz, -(o[2] * cy)), fma(o[2], cx, -(o[0] * cz)), fma(o[0], cy, -(o[1] * cx))
+        cr2 = fma(crx, crx, fma(cry, cry, crz * crz))
+        ac = fma(ax, cx, fma(ay, cy, az * cz))
+        a2 = fma(ax, ax, fma(ay, ay, az * az))
+        nn = sqrta(a2 * d2, sg(n))
+        wide |= ac <= (F(64) * FU) * nn
+        s2 = cr2 * rcpa((F(2) * nn) * (nn + ac), sg(n))
+        up = s2 > m1
+        m2 = np.where(up, m1, np.maximum(m2, s2))
+        best = np.where(up, vtx, best)
+        m1 = np.where(up, s2, m1)
+    # chord between the unit directions of mu - t_vertex and mu - t0 (double-float)
+    sign = np.array([[1.0 if (b >> k) & 1 else -1.0 for k in range(3)] for b in range(8)])[best]
+    q = c - sign * w
+    qh, ql = split(q / np.linalg.norm(q, axis=1, keepdims=True))
+    vh, vl = split(c / np.linalg.norm(c, axis=1, keepdims=True))
+    dk = [(qh[:, k] - vh[:, k]) + (ql[:, k] - vl[:, k]) for k in range(3)]
+    ch2 = fma(dk[2], dk[2], fma(dk[1], dk[1], fma(dk[0], dk[0], np.zeros(n, np.float32))))
+    sp2 = np.minimum(np.maximum(F(0.25) * ch2 * c1(8), m2 * c1(32)), F(1))
+    sp2 = np.where(inside | wide, F(1), sp2).astype(np.float32)
+    return np.where(sp2 >= 1, F(1), np.minimum(sqrta(sp2, sg(n)) * c1(3), F(1)))
+
+
+def test_psi_t_rounded_outward(oracle_mod):
+    """The stored half-angle sine of psi_t is never below the oracle's (and
+    reaches 1 wherever the oracle's psi_t is pi), under random error signs
+    of the approximate instructions and under all-low and all-high ones."""
+    rng = np.random.default_rng(20)
+    n = 6000
+    t0 = rng.uniform(-1, 1, (n, 3))
+    thw = np.exp(rng.uniform(np.log(1e-5), np.log(1.0), (n, 3)))
+    scale = np.exp(rng.uniform(np.log(0.5), np.log(200.0), (n, 1)))
+    mu = t0 + rng.uniform(-1, 1, (n, 3)) * thw * scale
+    # a third almost on a symmetry axis of the cuboid: vertex angles that
+    # differ at FP32 precision, where the FP32 choice of vertex can be wrong
+    m = n // 3
+    ax = rng.integers(3, size=m)
+    off = rng.uniform(-1, 1, (m, 3)) * thw[-m:] * 10.0 ** rng.uniform(-9, -5, (m, 1))
+    off[np.arange(m), ax] = np.where(rng.random(m) < 0.5, -1, 1) * thw[-m:][np.arange(m), ax] * rng.uniform(1.5, 50, m)
+    mu[-m:] = t0[-m:] + off
+    psi = np.array([oracle_mod.psi_t(mu[k], t0[k], thw[k]) for k in range(n)])
+    want = np.where(psi >= np.pi, 1.0, np.sin(0.5 * psi))
+    for mode in ("low", "high", *range(30)):
+        if mode == "low":
+            sg = lambda m: -np.ones(m)  # noqa: E731
+        elif mode == "high":
+            sg = lambda m: np.ones(m)  # noqa: E731
+        else:
+            r = np.random.default_rng(100 + mode)
+            sg = lambda m: r.choice([-1.0, 1.0], m)  # noqa: E731
+        got = _sin_half_psi_t(mu, t0, thw, sg).astype(np.float64)
+        assert np.all(got >= want), (mode, np.min(got - want))
+    assert (psi >= np.pi).sum() > 300 and (psi < 1e-3).sum() > 300 and ((psi > 0.5) & (psi < np.pi)).sum() > 300
+
+
 def test_the_cases_reach_every_regime(cases):
     """Near-aligned and near-antipodal pairs, tiny and pi-wide uncertainty
     angles, small and large concentrations."""
