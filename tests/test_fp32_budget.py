@@ -160,6 +160,13 @@ def _cross(c, s):
     """Upper bound of the cross pair (row 0, the image component) as the
     kernel forms it, times its row factor; s: signs of the 10 approximate
     instructions on the path."""
+    e, wQ, Bw = _cross_parts(c, s)
+    return fma(e, wQ, np.zeros_like(wQ)).astype(np.float64) * Bw.astype(np.float64)
+
+
+def _cross_parts(c, s):
+    """The exponential, the factor it multiplies and the row factor of the
+    cross pair's upper bound."""
     a, b, sp, cp = _rows(c)
     a, b, sp, cp = a[:, 0], b[:, 0], sp[:, 0], cp[:, 0]
     vh, vl = split(c["v"][:, 0])
@@ -197,11 +204,11 @@ def _cross(c, s):
     r = rcpa(den * Kc, s[6])
     DL = ak4 * (slo * slo) * (Kc * r) * (-L2E)
     w = np.minimum(den * r, F(2))
-    term = fma(ex2a(fma(np.full_like(DL, F(12) * FU), np.abs(DL), DL + SLACK), s[7]), w * Q, np.zeros_like(w))
+    e = ex2a(fma(np.full_like(DL, F(12) * FU), np.abs(DL), DL + SLACK), s[7])
     ph = f32(c["phi1"][:, 0])
     Bw = np.where(b < F(9), ph * b * rcpa(gZ(b, s[8]), s[9]) * c1(12), ph * b).astype(np.float32)
     Bw = mul_ru(Bw, np.full_like(Bw, c1(8 + 6)))
-    return term.astype(np.float64) * Bw.astype(np.float64)
+    return e, (w * Q).astype(np.float32), Bw
 
 
 # ---------------------------------------------------------------- self pair
@@ -444,6 +451,70 @@ def test_psi_t_rounded_outward(oracle_mod):
         got = _sin_half_psi_t(mu, t0, thw, sg).astype(np.float64)
         assert np.all(got >= want), (mode, np.min(got - want))
     assert (psi >= np.pi).sum() > 300 and (psi < 1e-3).sum() > 300 and ((psi > 0.5) & (psi < np.pi)).sum() > 300
+
+
+def _row_cases(oracle_mod, rng, n2):
+    """One model component against n2 image components in one cube: the
+    pairs (0, j) of a row, with the oracle's pair bounds."""
+    while True:
+        mu1 = rng.uniform(-3, 3, (1, 3))
+        t0 = rng.uniform(-1, 1, 3)
+        thw = np.exp(rng.uniform(np.log(1e-3), np.log(0.3), 3))
+        r0 = Rotation.random(random_state=rng).as_rotvec() * rng.uniform(0, 1)
+        rhw = np.exp(rng.uniform(np.log(1e-3), np.log(0.3)))
+        R0 = Rotation.from_rotvec(r0).as_matrix()
+        v = (mu1[0] - t0) / np.linalg.norm(mu1[0] - t0)
+        m2 = rng.standard_normal((n2, 3)) * 0.3 + R0 @ v  # mostly near the model direction: large terms
+        m2 /= np.linalg.norm(m2, axis=1, keepdims=True)
+        k2 = np.exp(rng.uniform(0, np.log(2000.0), n2))
+        phi2 = rng.dirichlet(np.ones(n2))
+        prob = {"mu1": mu1, "sigma1": np.array([np.exp(rng.uniform(np.log(0.02), np.log(0.5)))]),
+                "phi1": np.array([1.0]), "mu2": m2, "kappa2": k2, "phi2": phi2}
+        mix = oracle_mod.Mixtures.from_problem(prob)
+        ab = oracle_mod.kappa_interval(mu1[0], prob["sigma1"][0], t0, thw, 0.01)
+        if ab is None:
+            continue
+        cube = np.concatenate([r0, [rhw], t0, thw])
+        ones = np.ones(n2)
+        c = dict(v=np.repeat(np.array([[v, v]]), n2, 0), u=m2 @ R0, k2=k2, phi1=np.outer(ones, [1.0, 1.0]),
+                 phi2=phi2, a=np.outer(ones, [ab[0], ab[0]]), b=np.outer(ones, [ab[1], ab[1]]),
+                 psit=np.outer(ones, [oracle_mod.psi_t(mu1[0], t0, thw)] * 2), psir=oracle_mod.psi_r(rhw) * ones)
+        ref = sum(oracle_mod.cross_ub_term(mix, 0, j, cube, 0.01) for j in range(n2))
+        return c, ref
+
+
+def _acc_add(s, c, x):
+    """Compensated FP32 accumulation (TwoSum), as the kernel's Acc."""
+    t = s + x
+    z = t - s
+    c = c + ((s - (t - z)) + (x - z))
+    return t, c
+
+
+def test_cross_row_sum_never_below_the_oracle(oracle_mod):
+    """A whole row of cross pairs: terms fused into FP32 chunk sums of 8,
+    chunks into a compensated sum, the row factor applied once (df_scale,
+    exact product plus one rounding) -- the (8 + 6)u of the row factor has to
+    cover the chunk and row sums."""
+    rng = np.random.default_rng(21)
+    for trial in range(40):
+        n2 = int(rng.integers(8, 300))
+        c, ref = _row_cases(oracle_mod, rng, n2)
+        for signs in [(-1.0,) * 10] + [tuple(rng.choice([-1.0, 1.0], 10)) for _ in range(3)]:
+            e, wQ, Bw = _cross_parts(c, signs)
+            order = rng.permutation(n2)  # any order of the pairs within a thread
+            s_, c_, pl, cnt = F(0), F(0), F(0), 0
+            for j in order:
+                pl = F(np.float64(e[j]) * np.float64(wQ[j]) + np.float64(pl))
+                cnt += 1
+                if cnt == 8:
+                    s_, c_ = _acc_add(s_, c_, pl)
+                    pl, cnt = F(0), 0
+            s_, c_ = _acc_add(s_, c_, pl)
+            h = F(np.float64(s_) * np.float64(Bw[0]))
+            lo = F(np.float64(c_) * np.float64(Bw[0]) + (np.float64(s_) * np.float64(Bw[0]) - np.float64(h)))
+            row = np.float64(h) + np.float64(lo)
+            assert row >= ref, (trial, n2, row / ref - 1)
 
 
 def test_the_cases_reach_every_regime(cases):
