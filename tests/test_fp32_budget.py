@@ -220,6 +220,13 @@ def _aw(a, ph, s0, s1):
 def _self(c, s):
     """Lower bound of the self pair (0, 1), both orders, as the kernel forms
     it with its row factors; s: signs of the 13 approximate instructions."""
+    e, wA, Awi = _self_parts(c, s)
+    return fma(e, wA, np.zeros_like(wA)).astype(np.float64) * Awi.astype(np.float64)
+
+
+def _self_parts(c, s):
+    """The exponential, the factor it multiplies and the row factor of the
+    self pair's lower bound."""
     a, b, sp, cp = _rows(c)
     vh, vl = split(c["v"][:, 0])
     mh, ml = split(c["v"][:, 1])
@@ -259,10 +266,9 @@ def _self(c, s):
     small = Kmax < F(0.25)
     w = np.where(Kmax < F(9), np.where(small, np.maximum(F(2) - F(2) * Kmax, F(0)), gZ(Kmax, s[7]) * w * c1m(64)), w)
     w = w.astype(np.float32)
-    term = fma(ex2a(DL - fma(np.full_like(DL, F(12) * FU), np.abs(DL), np.full_like(DL, SLACK)), s[8]), w * Am,
-               np.zeros_like(w))
+    e = ex2a(DL - fma(np.full_like(DL, F(12) * FU), np.abs(DL), np.full_like(DL, SLACK)), s[8])
     Awi = mul_rd(F(2) * Ai, np.full_like(Ai, c1m(8 + 3)))
-    return term.astype(np.float64) * Awi.astype(np.float64)
+    return e, (w * Am).astype(np.float32), Awi
 
 
 # Terms below this leave FP32's normal range after the exponential and flush
@@ -502,19 +508,56 @@ def test_cross_row_sum_never_below_the_oracle(oracle_mod):
         c, ref = _row_cases(oracle_mod, rng, n2)
         for signs in [(-1.0,) * 10] + [tuple(rng.choice([-1.0, 1.0], 10)) for _ in range(3)]:
             e, wQ, Bw = _cross_parts(c, signs)
-            order = rng.permutation(n2)  # any order of the pairs within a thread
-            s_, c_, pl, cnt = F(0), F(0), F(0), 0
-            for j in order:
-                pl = F(np.float64(e[j]) * np.float64(wQ[j]) + np.float64(pl))
-                cnt += 1
-                if cnt == 8:
-                    s_, c_ = _acc_add(s_, c_, pl)
-                    pl, cnt = F(0), 0
-            s_, c_ = _acc_add(s_, c_, pl)
-            h = F(np.float64(s_) * np.float64(Bw[0]))
-            lo = F(np.float64(c_) * np.float64(Bw[0]) + (np.float64(s_) * np.float64(Bw[0]) - np.float64(h)))
-            row = np.float64(h) + np.float64(lo)
+            row = _row_sum(e, wQ, Bw[0], rng.permutation(n2))  # any order of the pairs within a thread
             assert row >= ref, (trial, n2, row / ref - 1)
+
+
+def _row_sum(e, wX, factor, order):
+    """A thread's row: FP32 chunk sums of 8 fused terms, a compensated sum
+    of the chunks, and the row factor applied once (df_scale)."""
+    s_, c_, pl, cnt = F(0), F(0), F(0), 0
+    for j in order:
+        pl = F(np.float64(e[j]) * np.float64(wX[j]) + np.float64(pl))
+        cnt += 1
+        if cnt == 8:
+            s_, c_ = _acc_add(s_, c_, pl)
+            pl, cnt = F(0), 0
+    s_, c_ = _acc_add(s_, c_, pl)
+    h = F(np.float64(s_) * np.float64(factor))
+    lo = F(np.float64(c_) * np.float64(factor) + (np.float64(s_) * np.float64(factor) - np.float64(h)))
+    return np.float64(h) + np.float64(lo)
+
+
+def test_self_row_sum_never_above_the_oracle(oracle_mod):
+    """A row of self pairs (0, m), m = 1 .. n1 - 1, both orders, summed as
+    the kernel sums them; the (8 + 3)u of the row factor covers the sums."""
+    rng = np.random.default_rng(22)
+    for trial in range(30):
+        n1 = int(rng.integers(9, 120))
+        t0 = rng.uniform(-1, 1, 3)
+        thw = np.exp(rng.uniform(np.log(1e-3), np.log(0.3), 3))
+        mu1 = t0 + rng.standard_normal((n1, 3)) * rng.uniform(0.3, 3.0)
+        sig = np.exp(rng.uniform(np.log(0.05), np.log(1.0), n1))
+        phi = rng.dirichlet(np.ones(n1))
+        prob = {"mu1": mu1, "sigma1": sig, "phi1": phi, "mu2": np.array([[0.0, 0.0, 1.0]]),
+                "kappa2": np.array([5.0]), "phi2": np.array([1.0])}
+        ab = [oracle_mod.kappa_interval(mu1[i], sig[i], t0, thw, 0.01) for i in range(n1)]
+        if any(x is None for x in ab):
+            continue
+        mix = oracle_mod.Mixtures.from_problem(prob)
+        cube = np.concatenate([[0.0, 0.0, 0.0, 0.1], t0, thw])
+        v = (mu1 - t0) / np.linalg.norm(mu1 - t0, axis=1, keepdims=True)
+        psit = np.array([oracle_mod.psi_t(mu1[i], t0, thw) for i in range(n1)])
+        m = np.arange(1, n1)
+        c = dict(v=np.stack([np.repeat(v[:1], n1 - 1, 0), v[m]], 1), phi1=np.stack([np.full(n1 - 1, phi[0]), phi[m]], 1),
+                 a=np.array([[ab[0][0], ab[k][0]] for k in m]), b=np.array([[ab[0][1], ab[k][1]] for k in m]),
+                 psit=np.stack([np.full(n1 - 1, psit[0]), psit[m]], 1))
+        ref = sum(oracle_mod.self_lb_term(mix, 0, k, cube, 0.01) + oracle_mod.self_lb_term(mix, k, 0, cube, 0.01)
+                  for k in m)
+        for signs in [(-1.0,) * 13, (1.0,) * 13] + [tuple(rng.choice([-1.0, 1.0], 13)) for _ in range(3)]:
+            e, wA, Awi = _self_parts(c, signs)
+            row = _row_sum(e, wA, Awi[0], rng.permutation(n1 - 1))
+            assert row <= ref, (trial, n1, row / ref - 1)
 
 
 def test_the_cases_reach_every_regime(cases):
