@@ -317,34 +317,38 @@ def tree_cubes(seed: int, n: int, t_lo, t_hi, depth_lo: int = 2, depth_hi: int =
     Cubes whose rotation part lies wholly outside the pi-ball are redrawn.
     With ``near=(r, t)``, a fraction ``near_frac`` of the paths follow the
     children that contain that pose, so the batch also holds cubes around
-    the optimum."""
+    the optimum.  (Scalar arithmetic per level, in the order of the
+    vectorised statement c[a:b] + (2 bits - 1) h.)"""
     rng = np.random.default_rng(seed)
-    root = root_cube(t_lo, t_hi)
+    root = [float(v) for v in root_cube(t_lo, t_hi)]
+    nr = [float(v) for v in near[0]] if near is not None else None
+    nt = [float(v) for v in near[1]] if near is not None else None
     out = np.empty((n, CUBE_LEN))
-    depth = rng.integers(depth_lo, depth_hi + 1, n)
+    depth = rng.integers(depth_lo, depth_hi + 1, n).tolist()
     k = 0
     while k < n:
-        c = root.copy()
+        c = list(root)
         follow = near is not None and rng.random() < near_frac
         for _ in range(depth[k]):
-            rot = rng.random() < 0.5
-            if rot:
+            if rng.random() < 0.5:
                 h = c[3] * 0.5
                 if follow:
-                    bits = (np.asarray(near[0]) > c[0:3]).astype(float)
+                    bits = [1.0 if nr[a] > c[a] else 0.0 for a in range(3)]
                 else:
-                    bits = rng.integers(0, 2, 3).astype(float)
-                c[0:3] = c[0:3] + (2 * bits - 1) * h
+                    bits = rng.integers(0, 2, 3).tolist()
+                for a in range(3):
+                    c[a] = c[a] + (2.0 * bits[a] - 1.0) * h
                 c[3] = h
             else:
-                h = c[7:10] * 0.5
                 if follow:
-                    bits = (np.asarray(near[1]) > c[4:7]).astype(float)
+                    bits = [1.0 if nt[a] > c[4 + a] else 0.0 for a in range(3)]
                 else:
-                    bits = rng.integers(0, 2, 3).astype(float)
-                c[4:7] = c[4:7] + (2 * bits - 1) * h
-                c[7:10] = h
-        gap = np.maximum(np.abs(c[0:3]) - c[3], 0.0)
+                    bits = rng.integers(0, 2, 3).tolist()
+                for a in range(3):
+                    h = c[7 + a] * 0.5
+                    c[4 + a] = c[4 + a] + (2.0 * bits[a] - 1.0) * h
+                    c[7 + a] = h
+        gap = np.maximum(np.abs(np.array(c[0:3])) - c[3], 0.0)
         if np.linalg.norm(gap) > np.pi:
             continue
         out[k] = c
