@@ -1020,6 +1020,8 @@ extern "C" int gosma_bnb_load(gosma_ctx *ctx, const char *path) {
     for (int k = 0; k < 3; ++k) same = same && h.t_lo[k] == ctx->t_lo[k] && h.t_hi[k] == ctx->t_hi[k];
     if (!same) return fail(ctx, GOSMA_EINVAL, "bnb_load: the checkpoint belongs to other mixtures or another domain");
     if (h.tail > h.cap || c.tail != h.tail) return fail(ctx, GOSMA_EINVAL, "bnb_load: inconsistent checkpoint");
+    if (!file_holds(f, h.tail, sizeof(uint32_t) + sizeof(Node)))
+        return fail(ctx, GOSMA_EINVAL, "bnb_load: truncated checkpoint");
     std::vector<uint32_t> keys(h.tail);
     std::vector<Node> nodes(h.tail);
     if (h.tail && (fread(keys.data(), sizeof(uint32_t), h.tail, f) != h.tail ||

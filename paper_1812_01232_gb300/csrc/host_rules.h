@@ -1,8 +1,9 @@
-// Launch-shape rules of the host code, kept free of CUDA so that they can be
-// compiled and tested on their own.
+// Host-side rules of the library (launch shapes, checkpoint reading), kept
+// free of CUDA so that they can be compiled and tested on their own.
 #pragma once
 
 #include <algorithm>
+#include <cstdio>
 
 namespace gosma {
 
@@ -37,6 +38,19 @@ inline int sma_block_for(int count, int sm_count, bool f64, int n1, int n2) {
     int b = 128;
     while (b < (f64 ? 512 : 1024) && (long long)count * 2 * b <= 2048LL * sm_count && 32LL * b <= pairs) b *= 2;
     return b;
+}
+
+// Whether an open file holds at least `count` records of `bytes` bytes after
+// its current position (which is left where it was).  A reader checks this
+// before it sizes buffers from counts stored in the file, so that a damaged
+// or foreign file is refused instead of allocating whatever it claims.
+inline bool file_holds(FILE *f, unsigned long long count, unsigned long long bytes) {
+    if (bytes && count > 0x7fffffffffffffffULL / bytes) return false;
+    const long here = ftell(f);
+    if (here < 0 || fseek(f, 0, SEEK_END) != 0) return false;
+    const long end = ftell(f);
+    const bool ok = end >= here && (unsigned long long)(end - here) >= count * bytes;
+    return fseek(f, here, SEEK_SET) == 0 && ok;
 }
 
 }  // namespace gosma

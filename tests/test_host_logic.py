@@ -117,6 +117,14 @@ int main(int argc, char **argv) {
     if (what[0] == 'b') printf("%d\n", gosma::auto_pop_batch(atoll(argv[2]), atoi(argv[3]), strtoull(argv[4], 0, 10)));
     if (what[0] == 'm') printf("%d\n", gosma::sma_block_for(atoi(argv[2]), atoi(argv[3]), atoi(argv[4]) != 0,
                                                             atoi(argv[5]), atoi(argv[6])));
+    if (what[0] == 'f') {  // file skip count bytes: skip bytes, then ask for count records of bytes
+        FILE *f = fopen(argv[2], "rb");
+        if (!f) return 1;
+        fseek(f, atol(argv[3]), SEEK_SET);
+        bool ok = gosma::file_holds(f, strtoull(argv[4], 0, 10), strtoull(argv[5], 0, 10));
+        printf("%d\n", ok ? (int)ftell(f) : -1 - (int)ftell(f));  // the position is kept either way
+        fclose(f);
+    }
     return 0;
 }
 """
@@ -159,3 +167,16 @@ def test_sma_threads_per_seed(rules):
     assert rules("m", 1, 152, 0, 10, 8) == 128       # 135 pair terms: no wider than 128
     assert rules("m", 1216, 152, 0, 128, 64) == 256  # 2048 x 152 / 1216 = 256 threads per seed
     assert rules("m", 4864, 152, 0, 128, 64) == 128
+
+
+def test_checkpoint_reader_checks_the_file_size(rules, tmp_path):
+    """file_holds: the records a checkpoint's header announces must be in the
+    file before the reader sizes buffers from that count."""
+    p = tmp_path / "ck.bin"
+    p.write_bytes(bytes(1000))
+    assert rules("f", p, 100, 900, 1) == 100          # exactly the rest of the file
+    assert rules("f", p, 100, 13, 68) == 100          # 884 bytes of 900
+    assert rules("f", p, 100, 14, 68) == -1 - 100     # 952 > 900: refused, position kept
+    assert rules("f", p, 0, 0, 68) == 0
+    assert rules("f", p, 0, 2 ** 62, 68) == -1        # the product would overflow: refused
+    assert rules("f", p, 1000, 1, 1) == -1 - 1000     # nothing after the end
