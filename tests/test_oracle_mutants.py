@@ -103,6 +103,12 @@ MUTANTS = [
      "c[CUBE_T0 + a] = p->cube[CUBE_T0 + a] + (((k >> a) & 1) ? -h : -h);"),
     # SMA
     ("SMA: Armijo test reversed", G, "if (fn <= f + 1e-4 * step * gd) {", "if (fn >= f + 1e-4 * step * gd) {"),
+    ("SMA: two-loop correction with the wrong sign", G, "q[k] += S[6 * idx + k] * (alpha[h] - beta);",
+     "q[k] += S[6 * idx + k] * (beta - alpha[h]);"),
+    ("SMA: initial scaling inverted", G, "gamma = sy / yy;", "gamma = yy / sy;"),
+    ("SMA: rho without the reciprocal", G, "rho[head] = 1.0 / sy;", "rho[head] = sy;"),
+    ("SMA: gradient test on the smallest coordinate", G, "if (fabs(g[k]) > gmax) gmax = fabs(g[k]);",
+     "if (fabs(g[k]) < gmax) gmax = fabs(g[k]);"),
     # mixture generation (Sec. 6)
     ("GMM fit: sigma^2 without the factor 3", M, "double s = sqrt(ss[c] / (3.0 * (double)cnt[c]));",
      "double s = sqrt(ss[c] / ((double)cnt[c]));"),
