@@ -14,6 +14,13 @@ def _noise_free(seed, n1, sigma):
     return p
 
 
+def _assert_feasible(p, t):
+    """The reported camera centre lies in Omega_t: inside the box and at
+    least zeta from every model mean (Sec. 4.1)."""
+    assert np.all(t >= np.asarray(p["t_lo"]) - 1e-12) and np.all(t <= np.asarray(p["t_hi"]) + 1e-12)
+    assert np.min(np.linalg.norm(p["mu1"] - t, axis=1)) >= p["zeta"]
+
+
 def test_bnb_recovers_true_pose_noise_free(oracle_mod):
     """With the image mixture equal to the projected model, the L2 distance
     is zero at the true pose, so f* = -C22 (proof of Lemma 1) and the pose
@@ -26,7 +33,8 @@ def test_bnb_recovers_true_pose_noise_free(oracle_mod):
     assert res["status"] == 0
     assert res["gap_norm"] <= 1e-2
     assert res["f"] == pytest.approx(-c22, abs=1e-2 * c22)
-    assert res["lb"] <= -c22 + 1e-9
+    assert res["lb"] <= -c22 + 1e-9 and res["lb"] <= res["f"]
+    _assert_feasible(p, res["t"])
     ang = np.arccos(np.clip((np.trace(res["R"].T @ p["R_gt"]) - 1) / 2, -1, 1))
     assert ang < 0.1
     assert np.linalg.norm(res["t"] - p["t_gt"]) < 0.05 * np.linalg.norm(p["t_gt"]) + 1e-3
@@ -52,9 +60,20 @@ def test_bnb_certificate_against_brute_force(oracle_mod):
         if np.min(np.linalg.norm(p["mu1"] - t, axis=1)) < p["zeta"]:
             continue
         best = min(best, oracle_mod.objective_r(mix, r, t))
-    # local refinement from the best random samples cannot beat the certificate either
-    assert res["lb"] <= best + 1e-9
+    # the pose the image was generated from is feasible; its objective is far
+    # below what random poses reach on this peaked objective
+    _assert_feasible(p, p["t_gt"])
+    best = min(best, oracle_mod.objective_r(mix, p["r_gt"], p["t_gt"]))
+    assert res["lb"] <= best + 1e-9 and res["lb"] <= res["f"]
     assert res["f"] - eps * c22 <= best + 1e-9
+    _assert_feasible(p, res["t"])
+    # local minima from many seeds (SMA, Sec. 5) come much closer to the
+    # global minimum than random poses: the lower bound stays below them too
+    seeds = np.concatenate([Rotation.random(64, random_state=rng).as_rotvec(),
+                            rng.uniform(p["t_lo"], p["t_hi"], (64, 3))], 1)
+    local = [oracle_mod.sma(mix, x0, p["t_lo"], p["t_hi"], p["zeta"], max_iter=200)[1] for x0 in seeds]
+    local = min(f for f in local if np.isfinite(f))
+    assert res["lb"] <= local + 1e-9 and res["f"] - eps * c22 <= local + 1e-9
     assert oracle_mod.objective(mix, res["R"], res["t"]) == pytest.approx(res["f"], rel=1e-12)
     # a grid through the found optimum: nothing on it is below lb
     for d in np.linspace(-0.05, 0.05, 11):

@@ -146,3 +146,19 @@ def test_vmf_separated_directions_are_recovered(oracle_mod):
     r = oracle_mod.dp_cluster(x[perm], np.cos(np.radians(25)), vmf=True)
     assert r["k"] == 5
     assert _same_partition(r["labels"], lab[perm])
+
+
+def test_vmf_cluster_with_zero_direction_sum(oracle_mod):
+    """Reading M2: a cluster whose direction sum is exactly zero is centred
+    on its lowest-index point.  Antipodal unit vectors with a threshold
+    below -1 share one cluster whose sum is zero; its centre is the first
+    vector in either order, and a zero resultant length gives the smallest
+    concentration the fit returns."""
+    for x in (np.array([[0.0, 0.0, 1.0], [0.0, 0.0, -1.0]]),
+              np.array([[0.0, -1.0, 0.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [-1.0, 0.0, 0.0]])):
+        for order in (x, x[::-1].copy()):
+            r = oracle_mod.dp_cluster(order, -1.5, vmf=True, max_iter=10, kappa_max=1e4)
+            assert r["k"] == 1 and r["passes"] == 1
+            np.testing.assert_array_equal(r["labels"], np.zeros(len(order), int))
+            np.testing.assert_array_equal(r["mu"][0], order[0])
+            assert r["kappa"][0] < 1e-6 and r["phi"][0] == 1.0

@@ -9,7 +9,9 @@ gets the same treatment.  At least one pin must fail for every mutant; the
 oracle in the repository is not touched.  Mistakes that change only
 efficiency (which of rotation or translation is split, the L-BFGS
 direction's restart safeguard) or a documented reading (the scale of eps)
-are not listed: no correctness pin can see them.  Neither is phiZ of K at
+are not listed: no correctness pin can see them; nor is the global lower
+bound left uncapped at d*, which differs only when a run ends with every
+queued node stale.  Neither is phiZ of K at
 the (b_i, b_j) corner in place of the largest corner K in the self-pair
 bound: log Z(K) - k1 - k2 decreases in each concentration, so that form is a
 valid (slightly tighter) bound too.
@@ -90,9 +92,14 @@ MUTANTS = [
     ("cube upper bound: cross sum not doubled", G, "out[1] = cp.centre_feasible ? sc - 2.0 * cc : INFINITY;",
      "out[1] = cp.centre_feasible ? sc - cc : INFINITY;"),
     ("pi-ball test at radius 2 pi", G, "return sqrt(d2) > M_PI;", "return sqrt(d2) > 2.0 * M_PI;"),
+    ("kappa interval: a cuboid wholly within zeta kept", G, "if (dmax < zeta) return 0;", "if (dmax < 0.0) return 0;"),
+    ("a centre within zeta given an upper bound", G, "if (d < zeta) cp->centre_feasible = 0;",
+     "if (d < 0.0) cp->centre_feasible = 0;"),
     # Algorithm 1
     ("queue: highest lower bound first", G, "if (x->lb != y->lb) return x->lb < y->lb;",
      "if (x->lb != y->lb) return x->lb > y->lb;"),
+    ("Algorithm 1: global lower bound from the queue's last slot", G, "dlb = h.n > 0 ? h.a[0].lb : dstar;",
+     "dlb = h.n > 0 ? h.a[h.n - 1].lb : dstar;"),
     ("Algorithm 1: children kept when above d*", G, "if (lb < dstar) heap_push(&h, &ch[c]);",
      "if (lb > dstar) heap_push(&h, &ch[c]);"),
     ("branching: both rotation halves on the same side", G,
@@ -121,6 +128,8 @@ MUTANTS = [
      "if (vmf) return (x[0] * m[0] + x[1] * m[1]) + x[2] * m[1];"),
     ("DP-means: a new cluster below lambda", M, "return vmf ? best < lambda : best > lambda;",
      "return vmf ? best < lambda : best < lambda;"),
+    ("DP-vMF-means: a zero-sum cluster centred on its last point", M, "if (i < first[c]) first[c] = i;",
+     "if (i > first[c] || first[c] == n) first[c] = i;"),
     ("DP-means: empty clusters kept", M, "            if (cnt[c] == 0) {\n                remap[c] = -1;",
      "            if (0) {\n                remap[c] = -1;"),
     ("DP-means: start at the first point, not the mean", M,

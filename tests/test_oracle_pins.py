@@ -304,8 +304,12 @@ def _pose_pair_terms(oracle_mod, prob, R, t):
 
 
 def _sample_in_cube(rng, cube, prob, n):
+    """Up to n feasible poses of the cube (at most 200 n draws, so that a cube
+    with no feasible pose cannot stall the test)."""
     out = []
-    while len(out) < n:
+    for _ in range(200 * n):
+        if len(out) == n:
+            break
         r = cube[0:3] + rng.uniform(-1, 1, 3) * cube[3]
         t = cube[4:7] + rng.uniform(-1, 1, 3) * cube[7:10]
         if np.min(np.linalg.norm(prob["mu1"] - t, axis=1)) >= prob["zeta"]:
@@ -384,6 +388,11 @@ def test_infeasible_cubes(oracle_mod):
     outside_pi = np.concatenate([[3.0, 3.0, 3.0, 0.2], [0, 0, 0], [0.1, 0.1, 0.1]])
     B = oracle_mod.bounds(mix, np.stack([inside_ball, outside_pi]), prob["zeta"])
     assert np.all(np.isinf(B[:, 0])) and np.all(np.isinf(B[:, 1]))
+    # reading R5: a centre within zeta of a mean is no pose, but the cuboid
+    # around it still has feasible points: a finite lower bound, no upper bound
+    wide = np.concatenate([[0, 0, 0, 0.1], mu + 0.1 * prob["zeta"], [2 * prob["zeta"]] * 3])
+    b = oracle_mod.bounds(mix, wide[None], prob["zeta"])[0]
+    assert np.isfinite(b[0]) and np.isinf(b[1])
 
 
 # ------------------------------------------------- SMA gradient (Sec. 5)
