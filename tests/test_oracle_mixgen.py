@@ -162,3 +162,15 @@ def test_vmf_cluster_with_zero_direction_sum(oracle_mod):
             np.testing.assert_array_equal(r["labels"], np.zeros(len(order), int))
             np.testing.assert_array_equal(r["mu"][0], order[0])
             assert r["kappa"][0] < 1e-6 and r["phi"][0] == 1.0
+
+
+def test_vmf_fit_capped_at_kappa_max(oracle_mod):
+    """Reading M3: identical directions have mean resultant length 1, whose
+    maximum-likelihood concentration is unbounded; the fit returns the cap.
+    A spread-out cluster stays below it."""
+    x = np.tile([[0.6, 0.0, 0.8]], (5, 1))
+    r = oracle_mod.dp_cluster(x, 0.5, vmf=True, max_iter=10, kappa_max=1234.0)
+    assert r["k"] == 1 and r["kappa"][0] == 1234.0
+    y = np.array([[1.0, 0.0, 0.0], [0.0, 1.0, 0.0]])
+    r = oracle_mod.dp_cluster(y, -0.5, vmf=True, max_iter=10, kappa_max=1234.0)
+    assert r["k"] == 1 and 0.0 < r["kappa"][0] < 10.0

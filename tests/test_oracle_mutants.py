@@ -121,6 +121,7 @@ MUTANTS = [
      "double s = sqrt(ss[c] / ((double)cnt[c]));"),
     ("vMF fit: sign of 1/kappa in the mean resultant length", M, "return 1.0 / tanh(k) - 1.0 / k;",
      "return 1.0 / tanh(k) + 1.0 / k;"),
+    ("vMF fit: capped at 1, not at kappa_max", M, "                spread[c] = hi;\n", "                spread[c] = 1.0;\n"),
     ("vMF fit: mean length without the coordinate scale", M,
      "sqrt((s0 * s0 + s1 * s1) + s2 * s2) / (scale * (double)cnt[c]);",
      "sqrt((s0 * s0 + s1 * s1) + s2 * s2) / ((double)cnt[c]);"),
@@ -130,6 +131,14 @@ MUTANTS = [
      "return vmf ? best < lambda : best < lambda;"),
     ("DP-vMF-means: a zero-sum cluster centred on its last point", M, "if (i < first[c]) first[c] = i;",
      "if (i > first[c] || first[c] == n) first[c] = i;"),
+    ("GMM fit: the floor taken as a ceiling", M, "spread[c] = s > lo ? s : lo;", "spread[c] = s < lo ? s : lo;"),
+    ("vMF fit: the bisection moves the wrong end", M, "if (mg_A3(exp(m)) < rbar) a = m;",
+     "if (mg_A3(exp(m)) > rbar) a = m;"),
+    ("DP-means: points compared with the first centre only", M, "for (int c = 1; c < K; ++c) {",
+     "for (int c = 1; c < 1; ++c) {"),
+    ("DP-means: the last pass not counted", M, "            ++pass;\n            break;", "            break;"),
+    ("DP-means: points quantized at 2^-31", M, "#define MG_SCALE_PTS 4294967296.0       /* 2^32 */",
+     "#define MG_SCALE_PTS 2147483648.0       /* 2^31 */"),
     ("DP-means: empty clusters kept", M, "            if (cnt[c] == 0) {\n                remap[c] = -1;",
      "            if (0) {\n                remap[c] = -1;"),
     ("DP-means: start at the first point, not the mean", M,
