@@ -14,7 +14,10 @@ bound left uncapped at d*, which differs only when a run ends with every
 queued node stale.  Neither is phiZ of K at
 the (b_i, b_j) corner in place of the largest corner K in the self-pair
 bound: log Z(K) - k1 - k2 decreases in each concentration, so that form is a
-valid (slightly tighter) bound too.
+valid (slightly tighter) bound too.  Nor are changes that double precision
+cannot see: the second-order terms of the small-angle series of Rodrigues'
+formula (below 1e-8 rad they round away against 1), or of d log Z / dx
+below 1e-4 (no term of the objective reaches K < 1e-4 with any weight).
 """
 import concurrent.futures as cf
 import os
@@ -37,6 +40,7 @@ MUTANTS = [
     # Eq. (Z), the vMF inner product, Eq. (vMF_PN_map)
     ("log Z with e^-x for e^-2x", G, "return log(-expm1(-2.0 * x) / x);", "return log(-expm1(-x) / x);"),
     ("qPN concentration without the +1", G, "    return q * q + 1.0;", "    return q * q;"),
+    ("log Z near 0: +x in place of -x", G, "if (x < 1e-12) return M_LN2 - x;", "if (x < 1e-12) return M_LN2 + x;"),
     ("pair term: difference in place of the sum in K", G, "w[k] = ka * ua[k] + kb * ub[k];",
      "w[k] = ka * ua[k] - kb * ub[k];"),
     ("pair term: normaliser of the wrong component", G, "return om_logZ(K) - om_logZ(ka) - om_logZ(kb);",
@@ -60,6 +64,16 @@ MUTANTS = [
     ("gradient: right Jacobian of SO(3) in place of the left", G,
      "J[k] = (k % 4 == 0 ? 1.0 : 0.0) + a * S[k] + b * S2[k];",
      "J[k] = (k % 4 == 0 ? 1.0 : 0.0) - a * S[k] + b * S2[k];"),
+    ("gradient: the left Jacobian's series at small angles", G, "a = 0.5 - th * th / 24.0;", "a = -0.5;"),
+    ("gradient: d v / dt without the projection", G,
+     "dv[9 * i + 3 * p + q] = -((p == q ? 1.0 : 0.0) - v[3 * i + p] * v[3 * i + q]) / d[i];",
+     "dv[9 * i + 3 * p + q] = -((p == q ? 1.0 : 0.0)) / d[i];"),
+    ("gradient: a self pair's kappa term of j dropped", G,
+     "gt[q] += term * (gK * dK - gi * dk[3 * i + q] - gj * dk[3 * j + q]);",
+     "gt[q] += term * (gK * dK - gi * dk[3 * i + q]);"),
+    ("objective parts: a self pair with i twice", G,
+     "self += m->phi1[i] * m->phi1[j] * exp(om_pair_log(ki, vi, kj, vj));",
+     "self += m->phi1[i] * m->phi1[j] * exp(om_pair_log(ki, vi, ki, vi));"),
     ("gradient: sign of 1/x in d log Z / dx", G, "return 1.0 + 2.0 / expm1(2.0 * x) - 1.0 / x;",
      "return 1.0 + 2.0 / expm1(2.0 * x) + 1.0 / x;"),
     # Lemmas 2 and 3, the kappa interval

@@ -32,6 +32,10 @@ def test_logZ_limits(oracle_mod):
     x = 1e-3
     assert oracle_mod.logZ(x) == pytest.approx(np.log(2.0) + x * x / 6 - x ** 4 / 180, rel=1e-14)
     assert oracle_mod.phiZ(40.0) == pytest.approx(-np.log(40.0), rel=1e-14)
+    # near 0, phiZ(x) = log((1 - e^{-2x}) / x) = log 2 - x + x^2 / 6 + O(x^3):
+    # below and above any switch to a series the value follows it to rounding
+    for x in (1e-16, 3e-14, 9.9e-13, 1e-12, 1.01e-12, 1e-11, 1e-9):
+        assert abs(oracle_mod.phiZ(x) - (np.log(2.0) - x + x * x / 6)) <= 2e-16, x
 
 
 # ------------------------------------------------- vMF inner product (Lemma 1 proof)
@@ -412,6 +416,27 @@ def test_gradient_matches_central_differences(oracle_mod):
             gn[k] = (oracle_mod.objective_r(mix, (x + e)[:3], (x + e)[3:]) -
                      oracle_mod.objective_r(mix, (x - e)[:3], (x - e)[3:])) / (2 * h)
         assert np.allclose(g, gn, rtol=1e-6, atol=1e-6 * np.abs(gn).max())
+
+
+def test_gradient_near_the_identity_rotation(oracle_mod):
+    """At tiny rotation vectors the left Jacobian of SO(3) is I + [r]x / 2 +
+    O(|r|^2): its first-order term changes the rotation gradient by a
+    relative ~|r|, which central differences with one Richardson step
+    resolve at |r| = 1e-7 and 5e-7 (their own error there is about 1e-10
+    of the gradient)."""
+    prob = synth.tiny_problem(63)
+    mix = oracle_mod.Mixtures.from_problem(prob)
+
+    def central(r, t, k, h):
+        e = np.zeros(3)
+        e[k] = h
+        return (oracle_mod.objective_r(mix, r + e, t) - oracle_mod.objective_r(mix, r - e, t)) / (2 * h)
+
+    for r in (np.array([1e-7, -0.6e-7, 0.3e-7]), np.array([-4e-7, 2e-7, 2.5e-7])):
+        x = np.concatenate([r, prob["t_gt"]])
+        f, g = oracle_mod.objective_grad(mix, x)
+        gn = np.array([(4 * central(r, x[3:], k, 1e-4) - central(r, x[3:], k, 2e-4)) / 3 for k in range(3)])
+        assert np.allclose(g[:3], gn, rtol=0, atol=1e-9 * np.abs(gn).max()), (g[:3], gn)
 
 
 def test_sma_reaches_true_pose_from_nearby(oracle_mod):
