@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(128)
     __shared__ uint64_t mbar;
     __shared__ uint32_t tbase_s;
     unsigned char *sX = inf_smem, *sH = sX + INF_X, *sW1 = sH + INF_H, *sW2 = sW1 + INF_W1, *sW3 = sW2 + INF_W2;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
     if (warp == 0) tc_alloc(&tbase_s, INF_COLS);
     if (threadIdx.x == 0) {
         mbar_init(&mbar, 1);

@@ -83,8 +83,6 @@ struct ProbState {
 };
 
 constexpr int MP_BLOCK = 512;
-constexpr int MP_ITEMS = 8;
-constexpr int MP_TILE = MP_BLOCK * MP_ITEMS;
 // queue chunks: the unit of work of the select and compaction kernels
 constexpr int CH_KEYS = 8192;
 constexpr int CH_BLOCK = 256;

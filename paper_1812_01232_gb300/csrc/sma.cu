@@ -213,8 +213,8 @@ __device__ void sma_eval32(const MixDev &mx, const Sma32Tab &tb, const double *x
         int i = tid / n1, j = tid % n1;
         for (int q = tid; q < nn; q += B) {
             if (j >= i && !(mx.cls1 && mx.cls1[i] != mx.cls1[j])) {
-                const float4 A = tb.ma[i], Ab = tb.mb[i], B = tb.ma[j], Bb = tb.mb[j];
-                const float e0 = A.x - B.x, e1 = A.y - B.y, e2 = A.z - B.z;
+                const float4 A = tb.ma[i], Ab = tb.mb[i], Bm = tb.ma[j], Bb = tb.mb[j];
+                const float e0 = A.x - Bm.x, e1 = A.y - Bm.y, e2 = A.z - Bm.z;
                 const float s2 = e0 * e0 + e1 * e1 + e2 * e2;
                 const Pair32 p = pair32<true>(Ab.x, Ab.y, Ab.z, Bb.x, Bb.y, Bb.z, s2);
                 const float T = (i == j ? 1.f : 2.f) * tb.phi1[i] * tb.phi1[j] * __expf(p.E);
@@ -223,9 +223,9 @@ __device__ void sma_eval32(const MixDev &mx, const Sma32Tab &tb, const double *x
                 const float c = 1.f - 0.5f * s2;
                 const float ca = T * p.Ea * Ab.w, cb = T * p.Eb * Bb.w, ce = T * p.Ec;
                 // dc/dt = -[(v_j - c v_i)/d_i + (v_i - c v_j)/d_j]
-                gt0 += ca * A.x + cb * B.x - ce * ((B.x - c * A.x) * A.w + (A.x - c * B.x) * B.w);
-                gt1 += ca * A.y + cb * B.y - ce * ((B.y - c * A.y) * A.w + (A.y - c * B.y) * B.w);
-                gt2 += ca * A.z + cb * B.z - ce * ((B.z - c * A.z) * A.w + (A.z - c * B.z) * B.w);
+                gt0 += ca * A.x + cb * Bm.x - ce * ((Bm.x - c * A.x) * A.w + (A.x - c * Bm.x) * Bm.w);
+                gt1 += ca * A.y + cb * Bm.y - ce * ((Bm.y - c * A.y) * A.w + (A.y - c * Bm.y) * Bm.w);
+                gt2 += ca * A.z + cb * Bm.z - ce * ((Bm.z - c * A.z) * A.w + (A.z - c * Bm.z) * Bm.w);
             }
             j += sj;
             i += si;
