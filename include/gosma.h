@@ -183,7 +183,8 @@ int gosma_eval_bounds_detail(gosma_ctx *ctx, const gosma_cube *cubes, int n, gos
 int gosma_eval_objective(gosma_ctx *ctx, const double r[3], const double t[3], double *f);
 
 /* f and its gradient with respect to (r, t) in FP64 on the device, for
- * `count` poses x (count x 6: r then t, host pointers). */
+ * `count` poses x (count x 6: r then t, host pointers); any count >= 0
+ * (the poses are processed in launches of at most 65,535). */
 int gosma_eval_objective_grad(gosma_ctx *ctx, int count, const double *x, double *f, double *grad);
 
 /* Allocation-free variant of gosma_eval_objective_grad (the paper has no
@@ -201,7 +202,9 @@ int gosma_eval_objective_grad(gosma_ctx *ctx, int count, const double *x, double
  * exceeds it.  All calls on a device share that array, so calls whose kernels
  * overlap on the GPU (e.g. issued on different streams) race.  The first call
  * on each device looks up the array's device address (cudaGetSymbolAddress);
- * make that first call before any stream capture. */
+ * make that first call before any stream capture.  The address is kept for
+ * the life of the process, so do not cudaDeviceReset a device between calls.
+ * (The size limit also keeps count below 65,536, the kernels' grid limit.) */
 int gosma_eval_objective_grad_noalloc(gosma_ctx *ctx, int count, const double *d_x, double *d_out);
 
 /* SMA (Sec. 5) from `count` seed poses at once, on the device: each seed is
@@ -413,7 +416,10 @@ int gosma_bnb_save(gosma_ctx *ctx, const char *path);
 
 /* Resume a checkpoint on a context holding the same mixtures and domain
  * (GOSMA_EINVAL otherwise): later gosma_bnb_step calls continue the run
- * exactly as the saved one would have continued. */
+ * exactly as the saved one would have continued.  "Same mixtures" is
+ * checked on the sizes, C22 and a 64-bit fingerprint of every mixture array
+ * (means, scales, concentrations, class-weighted weights, classes), so a
+ * file from another problem of the same sizes is refused. */
 int gosma_bnb_load(gosma_ctx *ctx, const char *path);
 
 /* Number of kernels the context has launched since it was created. */

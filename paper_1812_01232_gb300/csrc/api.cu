@@ -10,6 +10,7 @@
 
 #include "classes.h"
 #include "gosma_internal.cuh"
+#include "host_rules.h"
 
 namespace gosma {
 
@@ -238,6 +239,16 @@ static int set_mixtures_impl(gosma_ctx *ctx, int nclass, const int *n1c, const i
     ctx->h_mu2 = mu2n;
     ctx->h_kappa2.assign(kappa2, kappa2 + n2);
     ctx->h_phi2 = phi2;
+    ProblemHash ph;
+    ph.array(ctx->h_mu1.data(), ctx->h_mu1.size());
+    ph.array(ctx->h_sigma1.data(), ctx->h_sigma1.size());
+    ph.array(ctx->h_phi1.data(), ctx->h_phi1.size());
+    ph.array(ctx->h_mu2.data(), ctx->h_mu2.size());
+    ph.array(ctx->h_kappa2.data(), ctx->h_kappa2.size());
+    ph.array(ctx->h_phi2.data(), ctx->h_phi2.size());
+    ph.array(cls1.data(), classes ? cls1.size() : 0);
+    ph.array(cls2.data(), classes ? cls2.size() : 0);
+    ctx->mix_hash = ph.h;
     ctx->have_mix = true;
     bnb_end_run(ctx);
     return GOSMA_OK;

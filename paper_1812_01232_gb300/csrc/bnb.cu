@@ -911,7 +911,7 @@ extern "C" int gosma_bnb_solve(gosma_ctx *ctx, const gosma_opts *opts, gosma_res
 // device status block, d* and the queue slots [0, tail) (keys and nodes,
 // dead slots included, so that compaction and selection replay exactly).
 namespace {
-constexpr char CK_MAGIC[8] = {'G', 'O', 'S', 'M', 'A', 'C', 'K', '1'};
+constexpr char CK_MAGIC[8] = {'G', 'O', 'S', 'M', 'A', 'C', 'K', '2'};
 struct CkHeader {
     char magic[8];
     int n1, n2;
@@ -919,6 +919,7 @@ struct CkHeader {
     unsigned long long cap;
     int pop, node_bytes, status_bytes, pad;
     unsigned long long tail;
+    unsigned long long mix_hash;  // fingerprint of the mixtures (ProblemHash)
 };
 struct CkSolve {  // the solver record without its events
     gosma_opts o;
@@ -961,6 +962,7 @@ extern "C" int gosma_bnb_save(gosma_ctx *ctx, const char *path) {
     h.node_bytes = (int)sizeof(Node);
     h.status_bytes = (int)sizeof(Status);
     h.tail = v.tail;
+    h.mix_hash = ctx->mix_hash;
     CkSolve c;
     memset(&c, 0, sizeof c);
     c.o = v.o;
@@ -1016,7 +1018,7 @@ extern "C" int gosma_bnb_load(gosma_ctx *ctx, const char *path) {
         h.status_bytes != (int)sizeof(Status) || fread(&c, sizeof c, 1, f) != 1 || fread(&hs, sizeof hs, 1, f) != 1)
         return fail(ctx, GOSMA_EINVAL, "bnb_load: not a checkpoint of this library");
     bool same = h.n1 == ctx->n1 && h.n2 == ctx->n2 && fabs(h.c22 - ctx->c22) <= 1e-12 * fabs(ctx->c22) &&
-                h.zeta == ctx->zeta;
+                h.zeta == ctx->zeta && h.mix_hash == ctx->mix_hash;
     for (int k = 0; k < 3; ++k) same = same && h.t_lo[k] == ctx->t_lo[k] && h.t_hi[k] == ctx->t_hi[k];
     if (!same) return fail(ctx, GOSMA_EINVAL, "bnb_load: the checkpoint belongs to other mixtures or another domain");
     if (h.tail > h.cap || c.tail != h.tail) return fail(ctx, GOSMA_EINVAL, "bnb_load: inconsistent checkpoint");

@@ -129,6 +129,7 @@ struct gosma_ctx {
     int n1 = 0, n2 = 0;
     std::vector<double> h_mu1, h_sigma1, h_phi1, h_mu2, h_kappa2, h_phi2;
     double c22 = 0.0;
+    unsigned long long mix_hash = 0;  // fingerprint of the staged mixtures (checkpoints)
     void *d_mix = nullptr;  // one allocation holding every mixture array
     gosma::MixDev mix{};
 

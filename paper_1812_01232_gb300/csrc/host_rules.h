@@ -3,7 +3,9 @@
 #pragma once
 
 #include <algorithm>
+#include <cstdint>
 #include <cstdio>
+#include <cstring>
 
 namespace gosma {
 
@@ -52,5 +54,28 @@ inline bool file_holds(FILE *f, unsigned long long count, unsigned long long byt
     const bool ok = end >= here && (unsigned long long)(end - here) >= count * bytes;
     return fseek(f, here, SEEK_SET) == 0 && ok;
 }
+
+// 64-bit FNV-1a fingerprint of a run's problem: the staged mixture arrays
+// (means, scales, concentrations and the class-weighted mixture weights) and
+// every component's class.  A checkpoint carries it, so that a queue of lower
+// bounds is never resumed against other mixtures of the same sizes.  Each
+// array is hashed with its length, so that moving values between arrays
+// changes the fingerprint.
+struct ProblemHash {
+    uint64_t h = 0xcbf29ce484222325ULL;
+    void bytes(const void *p, size_t n) {
+        const unsigned char *b = static_cast<const unsigned char *>(p);
+        for (size_t k = 0; k < n; ++k) {
+            h ^= b[k];
+            h *= 0x100000001b3ULL;
+        }
+    }
+    template <class T>
+    void array(const T *p, size_t n) {
+        const uint64_t len = n;
+        bytes(&len, sizeof len);
+        if (n) bytes(p, n * sizeof(T));
+    }
+};
 
 }  // namespace gosma

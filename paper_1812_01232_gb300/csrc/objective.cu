@@ -10,6 +10,9 @@
 
 namespace gosma {
 
+// Poses per launch of the objective kernels (they index poses by gridDim.y).
+constexpr int OBJ_MAX_POSES_PER_LAUNCH = 65535;
+
 int objective_grad_device(gosma_ctx *ctx, int count, const double *h_x, double *h_f, double *h_g) {
     if (count <= 0) return GOSMA_OK;
     const int n1 = ctx->n1, n2 = ctx->n2;
@@ -35,15 +38,21 @@ int objective_grad_device(gosma_ctx *ctx, int count, const double *h_x, double *
     memcpy(hp, h_x, bx);
     cudaError_t e = cudaMemcpyAsync(dx, hp, bx, cudaMemcpyHostToDevice, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "copy poses");
-    obj_prep<<<dim3((n1 + 127) / 128, count), 128, 0, ctx->stream>>>(OneMix{ctx->mix}, dx, di);
-    ++ctx->launches;
-    obj_pairs<<<dim3(nblk, count), OBJ_BLOCK, 0, ctx->stream>>>(OneMix{ctx->mix}, dx, di, dp, nblk);
-    ++ctx->launches;
-    obj_final<<<(count + OBJ_FINAL_WARPS - 1) / OBJ_FINAL_WARPS, 32 * OBJ_FINAL_WARPS, 0, ctx->stream>>>(count, dx, dp, nblk,
-                                                                                                   dout);
-    ++ctx->launches;
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "launch(objective)");
+    // poses index gridDim.y, so at most 65,535 of them go into one launch
+    for (int p0 = 0; p0 < count; p0 += OBJ_MAX_POSES_PER_LAUNCH) {
+        const int m = count - p0 < OBJ_MAX_POSES_PER_LAUNCH ? count - p0 : OBJ_MAX_POSES_PER_LAUNCH;
+        const double *xs = dx + 6 * (size_t)p0;
+        double *is = di + (size_t)OBJ_STRIDE * n1 * p0, *ps = dp + (size_t)7 * nblk * p0;
+        obj_prep<<<dim3((n1 + 127) / 128, m), 128, 0, ctx->stream>>>(OneMix{ctx->mix}, xs, is);
+        ++ctx->launches;
+        obj_pairs<<<dim3(nblk, m), OBJ_BLOCK, 0, ctx->stream>>>(OneMix{ctx->mix}, xs, is, ps, nblk);
+        ++ctx->launches;
+        obj_final<<<(m + OBJ_FINAL_WARPS - 1) / OBJ_FINAL_WARPS, 32 * OBJ_FINAL_WARPS, 0, ctx->stream>>>(
+            m, xs, ps, nblk, dout + 7 * (size_t)p0);
+        ++ctx->launches;
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "launch(objective)");
+    }
     double *ho = hp + 6 * count;
     e = cudaMemcpyAsync(ho, dout, bo, cudaMemcpyDeviceToHost, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "copy objective");
@@ -208,12 +217,19 @@ namespace gosma {
 // All calls on a device share it: two calls whose kernels overlap on the GPU
 // (for example on two streams) race on it.  The scratch needs no clearing:
 // every byte a call reads was written earlier in the same call.
-constexpr size_t NOALLOC_SCRATCH_BYTES = (size_t)8 << 20;  // 8 MiB
+//
+// A call is accepted when its scratch, count * (128 n1 + 56 ceil((n1^2 +
+// n1 n2) / 512)) bytes, is at most NOALLOC_LIMIT_BYTES; the array holds 256
+// bytes more, so that the partial sums can start on a 256-byte boundary
+// without shrinking that limit.
+constexpr size_t NOALLOC_LIMIT_BYTES = (size_t)8 << 20;  // 8 MiB
+constexpr size_t NOALLOC_SCRATCH_BYTES = NOALLOC_LIMIT_BYTES + 256;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
 // Device address of g_noalloc_scratch per device, looked up once per device
 // (in host code the array's name is only a host-side stand-in, not a device
-// address).
+// address) and kept for the life of the process: a cudaDeviceReset of that
+// device between calls would leave it stale.
 static std::mutex g_noalloc_mu;
 static void *g_noalloc_ptr[128];
 
@@ -243,10 +259,9 @@ extern "C" int gosma_eval_objective_grad_noalloc(gosma_ctx *ctx, int count, cons
     const int n1 = ctx->n1, n2 = ctx->n2;
     long long total = (long long)n1 * n1 + (long long)n1 * n2;
     int nblk = (int)((total + OBJ_CHUNK - 1) / OBJ_CHUNK);
-    size_t bi = sizeof(double) * OBJ_STRIDE * (size_t)n1 * count;
-    size_t bp = sizeof(double) * 7 * (size_t)nblk * count;
-    bi = (bi + 255) & ~(size_t)255;
-    if (bi + bp > NOALLOC_SCRATCH_BYTES)
+    const size_t bi = sizeof(double) * OBJ_STRIDE * (size_t)n1 * count;
+    const size_t bp = sizeof(double) * 7 * (size_t)nblk * count;
+    if (bi + bp > NOALLOC_LIMIT_BYTES)
         return fail(ctx, GOSMA_EINVAL,
                     "eval_objective_grad_noalloc: count * (128 n1 + 56 ceil((n1^2 + n1 n2) / 512)) bytes "
                     "exceeds the 8 MiB scratch; use fewer poses per call");
@@ -255,7 +270,8 @@ extern "C" int gosma_eval_objective_grad_noalloc(gosma_ctx *ctx, int count, cons
     void *scratch = nullptr;
     int rc = noalloc_scratch(ctx, &scratch);
     if (rc) return rc;
-    double *di = (double *)scratch, *dp = (double *)((char *)scratch + bi);
+    // partial sums on a 256-byte boundary: at most 255 bytes past the limit, inside the array
+    double *di = (double *)scratch, *dp = (double *)((char *)scratch + ((bi + 255) & ~(size_t)255));
     obj_prep<<<dim3((n1 + 127) / 128, count), 128, 0, ctx->stream>>>(OneMix{ctx->mix}, d_x, di);
     ++ctx->launches;
     obj_pairs<<<dim3(nblk, count), OBJ_BLOCK, 0, ctx->stream>>>(OneMix{ctx->mix}, d_x, di, dp, nblk);

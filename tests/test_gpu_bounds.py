@@ -142,6 +142,26 @@ def test_objective_and_gradient_fp64(ctx, oracle_mod):
         assert np.allclose(g[k], gr, rtol=1e-9, atol=1e-9 * np.abs(gr).max())
 
 
+def test_objective_more_poses_than_one_grid(ctx, oracle_mod):
+    """More than 65,535 poses in one call (the kernels take at most that many
+    per launch): the same bits as two smaller calls, and the oracle's f and
+    gradient on a sample."""
+    prob = synth.tiny_problem(31)
+    ctx.set_problem(prob)
+    rng = np.random.default_rng(32)
+    n = 70000
+    X = np.concatenate([rng.uniform(-np.pi / 2, np.pi / 2, (n, 3)), rng.uniform(-1, 1, (n, 3))], 1)
+    f, g = ctx.eval_objective_grad(X)
+    f1, g1 = ctx.eval_objective_grad(X[:40000])
+    f2, g2 = ctx.eval_objective_grad(X[40000:])
+    assert np.array_equal(f, np.concatenate([f1, f2])) and np.array_equal(g, np.concatenate([g1, g2]))
+    mix = oracle_mod.Mixtures.from_problem(prob)
+    for k in (0, 65534, 65535, 65536, n - 1):
+        fr, gr = oracle_mod.objective_grad(mix, X[k])
+        assert f[k] == pytest.approx(fr, rel=1e-11, abs=1e-12)
+        assert np.allclose(g[k], gr, rtol=1e-9, atol=1e-9 * np.abs(gr).max())
+
+
 def test_paper_scale_parity_full_batch(ctx, oracle_mod):
     """128 x 64 components, the full 65,536-cube batch in the benchmark's
     launch configuration; the oracle checks a sample of the cubes."""

@@ -53,6 +53,20 @@ def test_load_checks_the_problem(tmp_path):
     a.set_problem(synth.tiny_problem(1001))
     with pytest.raises(GosmaError):
         a.bnb_load(path)  # other mixtures
+    # the same image mixture (so the same C22) and sizes, the model means moved
+    # by 1 mm: only the mixture fingerprint tells the problems apart
+    q = dict(p)
+    q["mu1"] = p["mu1"] + 1e-3
+    a.set_problem(q)
+    with pytest.raises(GosmaError, match="other mixtures"):
+        a.bnb_load(path)
+    # one model scale changed
+    q = dict(p)
+    q["sigma1"] = p["sigma1"].copy()
+    q["sigma1"][3] *= 1.5
+    a.set_problem(q)
+    with pytest.raises(GosmaError, match="other mixtures"):
+        a.bnb_load(path)
     (tmp_path / "junk.gosma").write_bytes(b"not a checkpoint")
     a.set_problem(p)
     with pytest.raises(GosmaError):

@@ -110,6 +110,7 @@ def test_invalid_layouts_are_rejected(harness, n1c, n2c, w, phi1, phi2):
 RULES = r"""
 #include <cstdio>
 #include <cstdlib>
+#include <vector>
 #include "host_rules.h"
 int main(int argc, char **argv) {
     const char *what = argv[1];
@@ -117,6 +118,15 @@ int main(int argc, char **argv) {
     if (what[0] == 'b') printf("%d\n", gosma::auto_pop_batch(atoll(argv[2]), atoi(argv[3]), strtoull(argv[4], 0, 10)));
     if (what[0] == 'm') printf("%d\n", gosma::sma_block_for(atoi(argv[2]), atoi(argv[3]), atoi(argv[4]) != 0,
                                                             atoi(argv[5]), atoi(argv[6])));
+    if (what[0] == 'h') {  // hash: k, then values; the first k form one array, the rest another
+        const int k = atoi(argv[2]);
+        std::vector<double> v;
+        for (int a = 3; a < argc; ++a) v.push_back(strtod(argv[a], 0));
+        gosma::ProblemHash h;
+        h.array(v.data(), (size_t)k);
+        h.array(v.data() + k, v.size() - (size_t)k);
+        printf("%lld\n", (long long)(h.h >> 1));
+    }
     if (what[0] == 'f') {  // file skip count bytes: skip bytes, then ask for count records of bytes
         FILE *f = fopen(argv[2], "rb");
         if (!f) return 1;
@@ -180,3 +190,18 @@ def test_checkpoint_reader_checks_the_file_size(rules, tmp_path):
     assert rules("f", p, 0, 0, 68) == 0
     assert rules("f", p, 0, 2 ** 62, 68) == -1        # the product would overflow: refused
     assert rules("f", p, 1000, 1, 1) == -1 - 1000     # nothing after the end
+
+
+def test_checkpoint_problem_fingerprint(rules):
+    """The fingerprint a checkpoint carries changes when any one mixture value
+    changes, even by one unit in the last place, and when values move from one
+    array to the next; equal arrays give equal fingerprints."""
+    v = [0.25, -1.5, 3.0, 0.125, 2.0, 7.75]
+    base = rules("h", 3, *["%.17g" % x for x in v])
+    assert base == rules("h", 3, *["%.17g" % x for x in v])
+    for i in range(len(v)):
+        w = list(v)
+        w[i] = float(np.nextafter(w[i], np.inf))
+        assert rules("h", 3, *["%.17g" % x for x in w]) != base, i
+    assert rules("h", 2, *["%.17g" % x for x in v]) != base
+    assert rules("h", 4, *["%.17g" % x for x in v]) != base
