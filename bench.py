@@ -396,6 +396,7 @@ def run_ours(args):
         ctx.close()
         line["batched"] = run_batched(args.batch_budget)
         line["time_to_certified"] = run_time_to_certified(8)
+        line["psi_r_point"] = run_psi_r_point(8)
         line["sma"] = run_sma()
         line["mixgen"] = run_mixgen()
     print(json.dumps(line), flush=True)
@@ -519,6 +520,31 @@ def run_time_to_certified(n_prob):
                                                   for r, q in zip(res, single))),
                      "p50_s": float(np.median([r["seconds"] for r in res]))}
     ctx.close()
+    return out
+
+
+def run_psi_r_point(n_prob):
+    """The same tiny problems solved to the certified optimum with the
+    point-independent and the point-dependent rotation uncertainty angle
+    (Lemma 2; gosma_set_psi_r_mode), single-problem solver, automatic pop."""
+    from paper_1812_01232_gb300 import synth
+    from paper_1812_01232_gb300.gosma import Gosma
+    ctx = Gosma(0)
+    probs = [synth.tiny_problem(200000 + s) for s in range(n_prob)]
+    out = {"workload": "%d tiny problems (10 x 8 components), eps 1e-3, queue 2^26, automatic pop, single-problem "
+                       "solver" % n_prob}
+    for name, point in (("cube", False), ("point", True)):
+        ctx.set_psi_r_mode(point)
+        res = []
+        t0 = time.perf_counter()
+        for p in probs:
+            ctx.set_problem(p)
+            res.append(ctx.bnb_solve(eps=1e-3, max_seconds=60, queue_capacity=1 << 26))
+        out[name] = {"wall_s": time.perf_counter() - t0, "nodes": int(sum(r["nodes"] for r in res)),
+                     "certified": int(sum(r["status_name"] == "optimal" for r in res)),
+                     "f": [r["f"] for r in res]}
+    ctx.close()
+    out["node_ratio"] = out["point"]["nodes"] / max(1, out["cube"]["nodes"])
     return out
 
 

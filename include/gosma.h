@@ -156,6 +156,24 @@ int gosma_set_mixtures_classes(gosma_ctx *ctx, int nclass, const int *n1c, const
                                const double *mu1, const double *sigma1, const double *phi1, const double *mu2,
                                const double *kappa2, const double *phi2);
 
+/* Rotation uncertainty angle of Lemma 2 used in the cross pairs of every
+ * bound the context computes afterwards (gosma_eval_bounds, the
+ * branch-and-bound solvers).  The paper gives the angle as a maximum over
+ * the rotation cube's surface without a closed form; both modes bound it:
+ *   GOSMA_PSI_R_CUBE (default): sqrt(3) h (capped at pi), the same for
+ *     every direction, from angle(R_r p, R_r0 p) <= |r - r0|;
+ *   GOSMA_PSI_R_POINT: one angle per model direction p = v_i (at the
+ *     cuboid centre): sin(psi / 2) <= max over the cube's vertices d of
+ *     |J_r(r0) d / 2 x p| + 3 h^2 / 8 (J_r the right Jacobian of the
+ *     exponential map of SO(3)), never above the GOSMA_PSI_R_CUBE angle.
+ * It is 13% smaller on average for small cubes and costs O(n1) per cube,
+ * nothing per pair.  Branching (Sec. 4.1) keeps comparing the
+ * point-independent angle, and gosma_bound.psi_r reports it.  GOSMA_EINVAL
+ * for another mode. */
+#define GOSMA_PSI_R_CUBE 0
+#define GOSMA_PSI_R_POINT 1
+int gosma_set_psi_r_mode(gosma_ctx *ctx, int mode);
+
 /* Translation domain Omega_t: the cuboid [t_lo, t_hi] minus the points
  * within zeta of any model mean (Sec. 4.1).  zeta >= 0, t_lo < t_hi. */
 int gosma_set_domain(gosma_ctx *ctx, const double t_lo[3], const double t_hi[3], double zeta);
@@ -408,6 +426,21 @@ int gosma_bnb_history(gosma_ctx *ctx, long long max_points, gosma_trace_point *o
  * GOSMA_ENOTREADY without a run in progress, GOSMA_EINVAL for a NaN f or a
  * null x. */
 int gosma_bnb_set_incumbent(gosma_ctx *ctx, double f, const double x[6]);
+
+/* The children bounded by the last iteration of the run (Algorithm 1, "evaluate
+ * the bounds of the sub-cubes"), in child order (parent k gives children
+ * 8k .. 8k+7), as the bound kernel wrote them: cubes[c] the child's sub-cube
+ * (decoded from its cell), bounds[c] its record as in gosma_eval_bounds_detail,
+ * where lb, ub, self_lb, self_c and psi_t_max are the values the solver uses
+ * (self_lb and self_c of a child of a rotation split are its parent's cached
+ * sums), psi_r is Lemma 2's angle of the child's rotation cube, and cross_ub and
+ * cross_c are derived from them (lb = self_lb - 2 cross_ub - 1e-12 (self_lb + 2
+ * cross_ub), ub = self_c - 2 cross_c).  Infeasible children have every field
+ * +inf but the angles.  *count receives the number of children (0 before the
+ * first iteration); the first min(count, max_children) are copied (host
+ * arrays).  Read-only: the run continues unchanged.  GOSMA_ENOTREADY without a
+ * run. */
+int gosma_bnb_last_children(gosma_ctx *ctx, int max_children, gosma_cube *cubes, gosma_bound *bounds, int *count);
 
 /* Checkpoint of a run between two gosma_bnb_step calls: the solver record,
  * the incumbent and its pose, and every queue slot (keys and sub-cubes) go

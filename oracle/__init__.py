@@ -44,7 +44,7 @@ class SmaOpts(C.Structure):
 class BnbOpts(C.Structure):
     _fields_ = [("eps", C.c_double), ("pop", C.c_int), ("max_nodes", C.c_longlong),
                 ("max_seconds", C.c_double), ("use_sma", C.c_int), ("nthreads", C.c_int),
-                ("sma", SmaOpts)]
+                ("sma", SmaOpts), ("psi_mode", C.c_int)]
 
 
 class BnbResult(C.Structure):
@@ -106,6 +106,9 @@ def lib():
         L.om_cross_ub_term.argtypes = [C.POINTER(Mix), C.c_int, C.c_int, D, C.c_double]
         L.om_bounds.argtypes = [C.POINTER(Mix), D, C.c_double, D]
         L.om_bounds_batch.argtypes = [C.POINTER(Mix), C.c_int, D, C.c_double, D, C.c_int]
+        L.om_bounds_batch_mode.argtypes = [C.POINTER(Mix), C.c_int, D, C.c_double, C.c_int, D, C.c_int]
+        L.om_psi_r_point.restype = C.c_double
+        L.om_psi_r_point.argtypes = [D, C.c_double, D]
         L.om_max_threads.restype = C.c_int
         L.om_sma.restype = C.c_int
         L.om_sma.argtypes = [C.POINTER(Mix), C.POINTER(Domain), C.POINTER(SmaOpts), D, D, D]
@@ -219,6 +222,13 @@ def psi_r(r_hw):
     return lib().om_psi_r(float(r_hw))
 
 
+def psi_r_point(r0, r_hw, p):
+    """Lemma 2, point-dependent form (reading R16): bound of the angle
+    between R_r p and R_r0 p over the rotation cube (r0, r_hw)."""
+    r0, p = _f64(r0), _f64(p)
+    return lib().om_psi_r_point(_p(r0), float(r_hw), _p(p))
+
+
 def psi_t(p, t0, thw):
     p, t0, thw = _f64(p), _f64(t0), _f64(thw)
     return lib().om_psi_t(_p(p), _p(t0), _p(thw))
@@ -245,12 +255,15 @@ def cross_ub_term(mix, i, j, cube, zeta):
 BOUND_FIELDS = ("lb", "ub", "self_lb", "cross_ub", "self_c", "cross_c", "psi_r", "psi_t_max")
 
 
-def bounds(mix: Mixtures, cubes, zeta, nthreads: int = 0):
-    """Theorem 1 bounds of each cube; returns an (n, 8) array of BOUND_FIELDS."""
+def bounds(mix: Mixtures, cubes, zeta, nthreads: int = 0, psi_mode: int = 0):
+    """Theorem 1 bounds of each cube; returns an (n, 8) array of BOUND_FIELDS.
+    psi_mode 1 takes the point-dependent psi_r (reading R16) in the cross
+    pairs."""
     cubes = _f64(cubes, (-1, 10))
     out = np.zeros((cubes.shape[0], 8))
     if cubes.shape[0]:
-        lib().om_bounds_batch(mix.ref, cubes.shape[0], _p(cubes), float(zeta), _p(out), int(nthreads))
+        lib().om_bounds_batch_mode(mix.ref, cubes.shape[0], _p(cubes), float(zeta), int(psi_mode), _p(out),
+                                   int(nthreads))
     return out
 
 
@@ -278,11 +291,12 @@ def sma(mix: Mixtures, x0, t_lo, t_hi, zeta, max_iter=100, memory=10, gtol=1e-9)
 
 
 def bnb(mix: Mixtures, t_lo, t_hi, zeta, eps, pop=128, max_nodes=0, max_seconds=0.0, use_sma=True,
-        nthreads=0, sma_max_iter=100):
-    """Algorithm 1.  Returns a dict with the certificate and the pose."""
+        nthreads=0, sma_max_iter=100, psi_mode=0):
+    """Algorithm 1.  Returns a dict with the certificate and the pose.
+    psi_mode 1 bounds with the point-dependent psi_r (reading R16)."""
     dom = _domain(t_lo, t_hi, zeta)
     o = BnbOpts(float(eps), int(pop), int(max_nodes), float(max_seconds), int(bool(use_sma)), int(nthreads),
-                SmaOpts(sma_max_iter, 10, 1e-9))
+                SmaOpts(sma_max_iter, 10, 1e-9), int(psi_mode))
     res = BnbResult()
     lib().om_bnb(mix.ref, C.byref(dom), C.byref(o), C.byref(res))
     return {

@@ -45,6 +45,18 @@
  *   R7  epsilon is on the normalised L2 distance f / C22 + 1, where
  *       C22 = sum_jj' phi_2j phi_2j' Z(|k_j mu_j + k_j' mu_j'|)/(Z(k_j)Z(k_j')),
  *       so the raw-f tolerance is eps * C22.
+ *   R16 point-dependent psi_r (an option, mode 1 of om_bounds_mode): for
+ *       each model direction v_i (at the cuboid centre) a certified bound
+ *       of max over the rotation cube of angle(R_r v_i, R_r0 v_i), from the
+ *       relative quaternion w(r) = vec(q(r0)^* q(r)), whose norm across v
+ *       gives sin(angle / 2) = |w(r) x v| exactly.  Taylor's theorem at r0:
+ *       w(r0 + d) = J_r(r0) d / 2 + rho, |rho| <= |d|^2 / 8, since the
+ *       second derivative of the quaternion exponential along a line is at
+ *       most |d / 2|^2 in norm.  The first-order term is a norm of a linear
+ *       map, so its maximum over the cube is at a vertex.  Hence
+ *       sin(psi_r,i / 2) <= max_vertices |J_r d x v_i| / 2 + 3 h^2 / 8,
+ *       capped by the point-independent sqrt(3) h of R1.  The split rule
+ *       (R6) keeps comparing the R1 angle.
  */
 #include <math.h>
 #include <stdint.h>
@@ -362,6 +374,51 @@ double om_psi_r(double r_hw)
     return p < M_PI ? p : M_PI;
 }
 
+/* Right Jacobian of the exponential map of SO(3) at r:
+ * J_r(r) = I - (1 - cos|r|)/|r|^2 [r]x + (|r| - sin|r|)/|r|^3 [r]x^2,
+ * so that R_{r + d} = R_r R_{J_r(r) d} to first order in d. */
+static void right_jacobian(const double r[3], double J[9])
+{
+    double th = norm3(r), c1, c2;
+    if (th < 1e-6) {
+        c1 = 0.5 - th * th / 24.0;
+        c2 = 1.0 / 6.0 - th * th / 120.0;
+    } else {
+        c1 = (1.0 - cos(th)) / (th * th);
+        c2 = (th - sin(th)) / (th * th * th);
+    }
+    double x = r[0], y = r[1], z = r[2];
+    double S[9] = {0, -z, y, z, 0, -x, -y, x, 0};
+    for (int p = 0; p < 3; ++p)
+        for (int q = 0; q < 3; ++q) {
+            double s2 = 0;
+            for (int k = 0; k < 3; ++k) s2 += S[3 * p + k] * S[3 * k + q];
+            J[3 * p + q] = (p == q ? 1.0 : 0.0) - c1 * S[3 * p + q] + c2 * s2;
+        }
+}
+
+/* Lemma 2, point-dependent form (reading R16): an upper bound of the angle
+ * between R_r p and R_r0 p over the rotation cube of centre r0 and
+ * half-width r_hw, for a unit vector p. */
+double om_psi_r_point(const double r0[3], double r_hw, const double p[3])
+{
+    double J[9];
+    right_jacobian(r0, J);
+    double lin = 0.0;
+    for (int k = 0; k < 4; ++k) { /* the 8 vertices d come in pairs +-d with equal norms */
+        double d[3] = {r_hw, r_hw, r_hw}, c[3], x[3];
+        if (k > 0) d[k - 1] = -r_hw;
+        matvec(J, d, c);
+        cross3(c, p, x);
+        double nx = 0.5 * norm3(x);
+        if (nx > lin) lin = nx;
+    }
+    double s = lin + 3.0 * r_hw * r_hw / 8.0;
+    double psi = s >= 1.0 ? M_PI : 2.0 * asin(s);
+    double r1 = om_psi_r(r_hw);
+    return psi < r1 ? psi : r1;
+}
+
 /* Lemma 3 with reading R2. */
 double om_psi_t(const double p[3], const double t0[3], const double thw[3])
 {
@@ -447,6 +504,7 @@ static double self_lb_term_pre(const om_mix *m, int i, int j, const double *v, c
 static double cross_ub_term_pre(const om_mix *m, int i, int j, const double *v, const double *psi, const double *a,
                                 const double *b, const double R0[9], double psir)
 {
+    /* psir: the rotation uncertainty angle of model direction i (R1, or R16 in mode 1) */
     double w = m->phi1[i] * m->phi2[j];
     double u[3];
     matTvec(R0, m->mu2 + 3 * j, u); /* R_r0^{-1} mu_2j */
@@ -466,17 +524,20 @@ static double cross_ub_term_pre(const om_mix *m, int i, int j, const double *v, 
 /* Per-cube quantities shared by all pairs. */
 typedef struct {
     double *v, *psi, *a, *b;
+    double *psir_i; /* rotation uncertainty angle per model direction (R1, or R16 in mode 1) */
     double R0[9], psir, psit_max;
     int feasible, centre_feasible;
 } cube_pre;
 
-static void cube_prepare(const om_mix *m, const double cube[CUBE_LEN], double zeta, cube_pre *cp)
+/* mode 0: psi_r of reading R1 for every model direction; mode 1: reading R16. */
+static void cube_prepare(const om_mix *m, const double cube[CUBE_LEN], double zeta, int mode, cube_pre *cp)
 {
     int n1 = m->n1;
     cp->v = malloc(sizeof(double) * 3 * n1);
     cp->psi = malloc(sizeof(double) * n1);
     cp->a = malloc(sizeof(double) * n1);
     cp->b = malloc(sizeof(double) * n1);
+    cp->psir_i = malloc(sizeof(double) * n1);
     const double *t0 = cube + CUBE_T0, *thw = cube + CUBE_THW;
     om_rodrigues(cube + CUBE_R0, cp->R0);
     cp->psir = om_psi_r(cube[CUBE_RHW]);
@@ -489,6 +550,7 @@ static void cube_prepare(const om_mix *m, const double cube[CUBE_LEN], double ze
         double d = norm3(c);
         if (d < zeta) cp->centre_feasible = 0;
         for (int k = 0; k < 3; ++k) cp->v[3 * i + k] = d > 0 ? c[k] / d : 0.0;
+        cp->psir_i[i] = mode == 1 ? om_psi_r_point(cube + CUBE_R0, cube[CUBE_RHW], cp->v + 3 * i) : cp->psir;
         cp->psi[i] = om_psi_t(p, t0, thw);
         if (cp->psi[i] > cp->psit_max) cp->psit_max = cp->psi[i];
         if (!om_kappa_interval(p, m->sigma1[i], t0, thw, zeta, cp->a + i, cp->b + i)) cp->feasible = 0;
@@ -501,12 +563,13 @@ static void cube_release(cube_pre *cp)
     free(cp->psi);
     free(cp->a);
     free(cp->b);
+    free(cp->psir_i);
 }
 
 double om_self_lb_term(const om_mix *m, int i, int j, const double cube[CUBE_LEN], double zeta)
 {
     cube_pre cp;
-    cube_prepare(m, cube, zeta, &cp);
+    cube_prepare(m, cube, zeta, 0, &cp);
     double r = cp.feasible ? self_lb_term_pre(m, i, j, cp.v, cp.psi, cp.a, cp.b) : NAN;
     cube_release(&cp);
     return r;
@@ -515,7 +578,7 @@ double om_self_lb_term(const om_mix *m, int i, int j, const double cube[CUBE_LEN
 double om_cross_ub_term(const om_mix *m, int i, int j, const double cube[CUBE_LEN], double zeta)
 {
     cube_pre cp;
-    cube_prepare(m, cube, zeta, &cp);
+    cube_prepare(m, cube, zeta, 0, &cp);
     double r = cp.feasible ? cross_ub_term_pre(m, i, j, cp.v, cp.psi, cp.a, cp.b, cp.R0, cp.psir) : NAN;
     cube_release(&cp);
     return r;
@@ -525,11 +588,14 @@ double om_cross_ub_term(const om_mix *m, int i, int j, const double cube[CUBE_LE
  * f(R_r0, t0), out[2] = self lower-bound sum, out[3] = cross upper-bound
  * sum (lb = out[2] - 2 out[3]), out[4] = self sum at the centre,
  * out[5] = cross sum at the centre (ub = out[4] - 2 out[5]), out[6] = psi_r,
- * out[7] = max_i psi_t(mu_1i).  Infeasible cubes (R5) get +inf bounds. */
-void om_bounds(const om_mix *m, const double cube[CUBE_LEN], double zeta, double out[8])
+ * out[7] = max_i psi_t(mu_1i).  Infeasible cubes (R5) get +inf bounds.
+ * mode 0: psi_r of reading R1; mode 1: the point-dependent psi_r of
+ * reading R16 in the cross pairs (out[6] stays the R1 angle, the one the
+ * split rule compares). */
+void om_bounds_mode(const om_mix *m, const double cube[CUBE_LEN], double zeta, int mode, double out[8])
 {
     cube_pre cp;
-    cube_prepare(m, cube, zeta, &cp);
+    cube_prepare(m, cube, zeta, mode, &cp);
     out[6] = cp.psir;
     out[7] = cp.psit_max;
     if (!cp.feasible) {
@@ -541,7 +607,8 @@ void om_bounds(const om_mix *m, const double cube[CUBE_LEN], double zeta, double
     for (int i = 0; i < m->n1; ++i)
         for (int j = 0; j < m->n1; ++j) slb += self_lb_term_pre(m, i, j, cp.v, cp.psi, cp.a, cp.b);
     for (int i = 0; i < m->n1; ++i)
-        for (int j = 0; j < m->n2; ++j) cub += cross_ub_term_pre(m, i, j, cp.v, cp.psi, cp.a, cp.b, cp.R0, cp.psir);
+        for (int j = 0; j < m->n2; ++j)
+            cub += cross_ub_term_pre(m, i, j, cp.v, cp.psi, cp.a, cp.b, cp.R0, cp.psir_i[i]);
     out[0] = slb - 2.0 * cub;
     out[2] = slb;
     out[3] = cub;
@@ -558,15 +625,25 @@ void om_bounds(const om_mix *m, const double cube[CUBE_LEN], double zeta, double
     cube_release(&cp);
 }
 
+void om_bounds(const om_mix *m, const double cube[CUBE_LEN], double zeta, double out[8])
+{
+    om_bounds_mode(m, cube, zeta, 0, out);
+}
+
 /* Bounds of many cubes, cubes in parallel (nthreads <= 0: library default). */
-void om_bounds_batch(const om_mix *m, int n, const double *cubes, double zeta, double *out, int nthreads)
+void om_bounds_batch_mode(const om_mix *m, int n, const double *cubes, double zeta, int mode, double *out, int nthreads)
 {
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 1)
 #endif
-    for (int c = 0; c < n; ++c) om_bounds(m, cubes + (size_t)CUBE_LEN * c, zeta, out + 8 * (size_t)c);
+    for (int c = 0; c < n; ++c) om_bounds_mode(m, cubes + (size_t)CUBE_LEN * c, zeta, mode, out + 8 * (size_t)c);
     (void)nthreads;
+}
+
+void om_bounds_batch(const om_mix *m, int n, const double *cubes, double zeta, double *out, int nthreads)
+{
+    om_bounds_batch_mode(m, n, cubes, zeta, 0, out, nthreads);
 }
 
 int om_max_threads(void)
@@ -712,6 +789,7 @@ typedef struct {
     int use_sma;         /* run SMA when a sub-cube improves the incumbent */
     int nthreads;        /* OpenMP threads for bound evaluation (<= 0: default) */
     om_sma_opts sma;
+    int psi_mode;        /* 0: psi_r of reading R1; 1: point-dependent psi_r (R16) */
 } om_bnb_opts;
 
 typedef struct {
@@ -837,7 +915,7 @@ int om_bnb(const om_mix *m, const om_domain *dom, const om_bnb_opts *opt, om_bnb
     root.cube[CUBE_RHW] = M_PI;
     {
         double o[8];
-        om_bounds(m, root.cube, dom->zeta, o);
+        om_bounds_mode(m, root.cube, dom->zeta, opt->psi_mode, o);
         root.psir = o[6];
         root.psit_max = o[7];
     }
@@ -873,7 +951,7 @@ int om_bnb(const om_mix *m, const om_domain *dom, const om_bnb_opts *opt, om_bnb
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 1)
 #endif
-        for (int c = 0; c < nc; ++c) om_bounds(m, ch[c].cube, dom->zeta, out + 8 * c);
+        for (int c = 0; c < nc; ++c) om_bounds_mode(m, ch[c].cube, dom->zeta, opt->psi_mode, out + 8 * c);
         res->nodes += nc;
         res->iterations += 1;
         for (int c = 0; c < nc; ++c) {

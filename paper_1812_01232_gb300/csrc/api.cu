@@ -215,6 +215,7 @@ static int set_mixtures_impl(gosma_ctx *ctx, int nclass, const int *n1c, const i
     mx.rj0 = classes ? drj0 : nullptr;
     mx.rj1 = classes ? drj1 : nullptr;
     mx.rm1 = classes ? drm1 : nullptr;
+    mx.psi_point = ctx->psi_r_mode;
     void *old = ctx->d_mix;
     MixDev old_mix = ctx->mix;
     int old_n1 = ctx->n1, old_n2 = ctx->n2;
@@ -251,6 +252,16 @@ static int set_mixtures_impl(gosma_ctx *ctx, int nclass, const int *n1c, const i
     ctx->mix_hash = ph.h;
     ctx->have_mix = true;
     bnb_end_run(ctx);
+    return GOSMA_OK;
+}
+
+int gosma_set_psi_r_mode(gosma_ctx *ctx, int mode) {
+    if (!ctx) return GOSMA_EINVAL;
+    ctx->err.clear();
+    if (mode != GOSMA_PSI_R_CUBE && mode != GOSMA_PSI_R_POINT)
+        return fail(ctx, GOSMA_EINVAL, "set_psi_r_mode: mode must be GOSMA_PSI_R_CUBE or GOSMA_PSI_R_POINT");
+    ctx->psi_r_mode = mode;
+    ctx->mix.psi_point = mode;
     return GOSMA_OK;
 }
 

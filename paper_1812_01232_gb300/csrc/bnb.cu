@@ -673,6 +673,7 @@ struct Solve {
     double t_bound_ms = 0, t_iter_ms = 0, seconds = 0;
     int status = GOSMA_RUNNING;
     bool active = false;
+    int last_np = 0;  // parents popped by the last iteration (its children are in the kids buffer)
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     std::vector<gosma_trace_point> history;  // one point per iteration (Fig. 5)
 };
@@ -773,7 +774,7 @@ extern "C" int gosma_bnb_start(gosma_ctx *ctx, const gosma_opts *opts_in) {
     Node root;
     memset(&root, 0, sizeof root);
     root.lb = -INFINITY;
-    root.psit = (float)M_PI;
+    root.psit = PSI_PI_F;
     s->cur = 0;
     uint32_t rkey = order_key(-INFINITY);
     double dstar = INFINITY;
@@ -849,8 +850,10 @@ extern "C" int gosma_bnb_step(gosma_ctx *ctx, int max_iters, gosma_result *out) 
             }
         }
         long long self_children = 0;
+        v.last_np = 0;
         rc = iterate(ctx, v.dom, s, v.tail, np, v.ev, &self_children);
         if (rc) return rc;
+        v.last_np = np;
         float ms_b = 0, ms_i = 0;
         cudaEventElapsedTime(&ms_b, v.ev[1], v.ev[2]);
         cudaEventElapsedTime(&ms_i, v.ev[0], v.ev[3]);
@@ -1095,4 +1098,58 @@ extern "C" int gosma_bnb_set_incumbent(gosma_ctx *ctx, double f, const double x[
     cudaError_t e = cudaMemcpyAsync(s->dstar, &v.dstar, sizeof v.dstar, cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     return e == cudaSuccess ? GOSMA_OK : cuda_fail(ctx, e, "bnb_set_incumbent");
+}
+
+// The children of the last iteration, as the bound kernel left them in the
+// kids buffer: the sub-cube of each (decoded from its cell), its lower bound
+// and cached or fresh self sums (the queue node), its upper bound (kid_ub).
+// The cross sums are not stored; they follow from lb and the self sums.
+extern "C" int gosma_bnb_last_children(gosma_ctx *ctx, int max_children, gosma_cube *cubes, gosma_bound *bounds,
+                                       int *count) {
+    if (!ctx) return GOSMA_EINVAL;
+    ctx->err.clear();
+    Solve *vp = solve_of(ctx);
+    if (!vp) return fail(ctx, GOSMA_ENOTREADY, "bnb_last_children: no run");
+    if (!count || max_children < 0 || (max_children > 0 && (!cubes || !bounds)))
+        return fail(ctx, GOSMA_EINVAL, "bnb_last_children: bad arguments");
+    const Solve &v = *vp;
+    BnbState *s = (BnbState *)ctx->bnb;
+    const int nk = 8 * v.last_np;
+    *count = nk;
+    const int m = nk < max_children ? nk : max_children;
+    if (m == 0) return GOSMA_OK;
+    cudaSetDevice(ctx->device);
+    std::vector<Node> kids(m);
+    std::vector<double> ub(m);
+    cudaError_t e = cudaMemcpyAsync(kids.data(), s->kids, sizeof(Node) * m, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ub.data(), s->kid_ub, sizeof(double) * m, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "bnb_last_children: read children");
+    for (int c = 0; c < m; ++c) {
+        const Node &n = kids[c];
+        CubeGeom g;
+        decode(n, v.dom, g);
+        gosma_cube &q = cubes[c];
+        for (int k = 0; k < 3; ++k) {
+            q.r0[k] = g.r0[k];
+            q.t0[k] = g.t0[k];
+            q.t_hw[k] = g.thw[k];
+        }
+        q.r_hw = g.rhw;
+        gosma_bound &b = bounds[c];
+        b.lb = n.lb;
+        b.ub = ub[c];
+        if (std::isinf(n.lb)) {
+            b.self_lb = b.cross_ub = b.self_c = b.cross_c = n.lb;
+        } else {
+            // lb = self_lb - 2 cross_ub - 1e-12 (self_lb + 2 cross_ub), solved for cross_ub
+            b.self_lb = n.self_lb;
+            b.cross_ub = ((1.0 - 1e-12) * n.self_lb - n.lb) / (2.0 * (1.0 + 1e-12));
+            b.self_c = n.self_c;
+            b.cross_c = std::isinf(ub[c]) ? ub[c] : 0.5 * (n.self_c - ub[c]);
+        }
+        b.psi_r = psi_r_level(n.lr);
+        b.psi_t_max = n.psit;
+    }
+    return GOSMA_OK;
 }

@@ -28,11 +28,19 @@
 
 #include "dfloat.cuh"
 #include "gosma_internal.cuh"
+#include "packed.cuh"
 
 namespace gosma {
 
-// Per-cube data written by the pre-pass (144 bytes): the rotation and the
-// translation cuboid as double-floats.
+// psi_t = pi as a float: the largest float below pi (the nearest float,
+// (float)M_PI, lies above it), so that a rotation cube whose angle is capped
+// at pi still wins the split rule's tie with a mean inside the cuboid, as in
+// the FP64 comparison (ties split rotation).
+constexpr float PSI_PI_F = 3.14159250f;
+
+// Per-cube data written by the pre-pass (208 bytes): the rotation and the
+// translation cuboid as double-floats, and the terms of the point-dependent
+// rotation uncertainty angle.
 struct CubePrep {
     float Rh[9], Rl[9];  // R_r0 (row-major)
     float th[3], tl[3];  // t0
@@ -41,8 +49,13 @@ struct CubePrep {
     float psi_r;
     int infeasible;      // rotation cube wholly outside the pi-ball
     float pad[2];
+    // point-dependent psi_r (Lemma 2): pj[0..11] the images c_k = J_r(r0) d_k / 2
+    // of four vertices d_k = (+-h, +-h, h) of the rotation cube (the other four
+    // are their negatives), pj[12] their largest norm (rounded up), pj[13]
+    // 3 h^2 / 8 (rounded up), pj[14..15] padding
+    float pj[16];
 };
-static_assert(sizeof(CubePrep) == 144, "CubePrep layout");
+static_assert(sizeof(CubePrep) == 208, "CubePrep layout");
 constexpr int PREP_WORDS = sizeof(CubePrep) / 4;
 
 // shared-memory scalars of one cube
@@ -128,6 +141,62 @@ __device__ inline void cube_prepare(const double r0[3], double rhw, const double
         split_double(thw[k], o.wh[k], o.wl[k]);
     }
     o.pad[0] = o.pad[1] = 0.f;
+    // right Jacobian J_r(r0) = I - B [r0]x + C [r0]x^2, C = (|r0| - sin|r0|) / |r0|^3
+    // (R_{r0 + d} = R_r0 R_{J_r d} to first order), and the vertex images J_r d / 2
+    const double C = th < 1e-6 ? 1.0 / 6.0 - th2 / 120.0 : (th - A * th) / (th2 * th);
+    const double S[9] = {0.0, -z, y, z, 0.0, -x, -y, x, 0.0};
+    double J[9];
+    for (int p = 0; p < 3; ++p)
+        for (int q = 0; q < 3; ++q) {
+            double s2 = S[3 * p] * S[q] + S[3 * p + 1] * S[3 + q] + S[3 * p + 2] * S[6 + q];
+            J[3 * p + q] = (p == q ? 1.0 : 0.0) - B * S[3 * p + q] + C * s2;
+        }
+    double jmax = 0.0;
+    for (int k = 0; k < 4; ++k) {
+        double d[3] = {rhw, rhw, rhw};
+        if (k > 0) d[k - 1] = -rhw;
+        double n2 = 0.0;
+        for (int p = 0; p < 3; ++p) {
+            double c = 0.5 * (J[3 * p] * d[0] + J[3 * p + 1] * d[1] + J[3 * p + 2] * d[2]);
+            o.pj[3 * k + p] = (float)c;
+            n2 += c * c;
+        }
+        jmax = fmax(jmax, sqrt(n2));
+    }
+    o.pj[12] = __double2float_ru(jmax);
+    o.pj[13] = __double2float_ru(0.375 * rhw * rhw);
+    o.pj[14] = o.pj[15] = 0.f;
+}
+
+// Lemma 2, point-dependent form, for one model direction v (the hi part of
+// the unit vector v_i at t0): with w(r) the vector part of the relative
+// quaternion q(r0)^* q(r), sin(angle(R_r v, R_r0 v) / 2) = |w(r) x v|, and
+// w(r0 + d) = J_r(r0) d / 2 + rho with |rho| <= |d|^2 / 8 (the second
+// derivative of the quaternion exponential along a line is at most |d/2|^2),
+// so over the cube sin(psi_r / 2) <= max_k |c_k x v| + 3 h^2 / 8 (the
+// first-order term is a norm of a linear map: largest at a vertex).
+// Outward rounding: c_k and v carry u relative each (2u |c| on the cross
+// product), each FP32 cross-product component 2u (|c_a v_b| + |c_b v_a|)
+// (5u |c| on the vector), the squared norm 3u, sqrt 2u: the computed maximum
+// times (1 + 4u) plus 8u |c|max, rounded up, bounds the first-order term.
+// Cr, Sr (the point-independent pair) are replaced when the bound is smaller.
+__device__ __forceinline__ void point_psi_r(const CubePrep &P, float vx, float vy, float vz, float &Cr, float &Sr) {
+    const float U = GOSMA_U;
+    // read at every call: loads hoisted out of the row loop would hold 14
+    // registers across the pair loops
+    const volatile float *Jd = P.pj;
+    float best = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float cx = Jd[3 * k], cy = Jd[3 * k + 1], cz = Jd[3 * k + 2];
+        const float x = fmaf(cy, vz, -cz * vy), y = fmaf(cz, vx, -cx * vz), z = fmaf(cx, vy, -cy * vx);
+        best = fmaxf(best, fmaf(x, x, fmaf(y, y, z * z)));
+    }
+    const float s = __fadd_ru(__fmaf_ru(sqrta(best), 1.f + 4.f * U, 8.f * U * Jd[12]), Jd[13]);
+    if (s < Sr) {
+        Sr = s;
+        Cr = sqrta(fmaxf(fmaf(-s, s, 1.f), 0.f)) * (1.f - 3.f * U);
+    }
 }
 
 // g(x) = 1 - e^{-2x}, so that Z(x) = e^x g(x) / x (Eq. Z).  For x >= 9,
@@ -214,6 +283,78 @@ __device__ __forceinline__ void cross_pair(const RowCross &R, float4 J1, float4 
     pl = fmaf(ex2a(fmaf(12.f * U, fabsf(DL), DL + GOSMA_TERM_SLACK)), w * Q, pl);
 }
 
+// The row constants of RowCross in both lanes of packed pairs, for
+// cross_pair2.  nSs = -Ss (negation is exact).
+struct RowCross2 {
+    float2 vx, vy, vz, wx, wy, wz;
+    float2 a, b, k0, Cs, nSs, esS, A4;
+    __device__ __forceinline__ explicit RowCross2(const RowCross &R)
+        : vx(bc2(R.vx)), vy(bc2(R.vy)), vz(bc2(R.vz)), wx(bc2(R.wx)), wy(bc2(R.wy)), wz(bc2(R.wz)), a(bc2(R.a)),
+          b(bc2(R.b)), k0(bc2(R.k0)), Cs(bc2(R.Cs)), nSs(bc2(-R.Ss)), esS(bc2(R.esS)), A4(bc2(R.A4)) {}
+};
+
+__device__ __forceinline__ float2 sqrt2a(float2 x) { return make_float2(sqrta(x.x), sqrta(x.y)); }
+__device__ __forceinline__ float2 rcp2a(float2 x) { return make_float2(rcpa(x.x), rcpa(x.y)); }
+__device__ __forceinline__ float2 ex2_2a(float2 x) { return make_float2(ex2a(x.x), ex2a(x.y)); }
+
+// Two cross pairs (i, j) and (i, j') at once, lane x for column j (records
+// J1a, J2a) and lane y for j' (J1b, J2b): lane by lane the operations and
+// roundings of cross_pair, on packed pairs (the error budget above holds per
+// lane).  Rewritings that change no bit: 1 - s^2 is taken as -(s^2 - 1)
+// (round to nearest is symmetric), -k2 cos B as -(k2 cos B), 4 ks k2 as
+// ks (4 k2)... (scaling by 4 is exact), and 12u |DL| as -12u DL (DL <= 0: a
+// product of non-negative factors and -log2 e).
+__device__ __forceinline__ void cross_pair2(const RowCross2 &R, float4 J1a, float4 J2a, float4 J1b, float4 J2b,
+                                            float2 &pl, float2 &pc) {
+    const float U = GOSMA_U;
+    const float2 k2 = make_float2(J1a.w, J1b.w), Q = make_float2(J2a.w, J2b.w);
+    const float2 ux = make_float2(J1a.x, J1b.x), uy = make_float2(J1a.y, J1b.y), uz = make_float2(J1a.z, J1b.z);
+    const float2 lx = make_float2(J2a.x, J2b.x), ly = make_float2(J2a.y, J2b.y), lz = make_float2(J2a.z, J2b.z);
+    const float2 dx = add2(sub2(R.vx, ux), sub2(R.wx, lx)), dy = add2(sub2(R.vy, uy), sub2(R.wy, ly)),
+                 dz = add2(sub2(R.vz, uz), sub2(R.wz, lz));
+    const float2 px = add2(add2(R.vx, ux), add2(R.wx, lx)), py = add2(add2(R.vy, uy), add2(R.wy, ly)),
+                 pz = add2(add2(R.vz, uz), add2(R.wz, lz));
+    const float2 x2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));  // |v - u|^2 = 4 sin^2(theta/2)
+    const float2 y2 = fma2(px, px, fma2(py, py, mul2(pz, pz)));  // |v + u|^2 = 4 cos^2(theta/2)
+    // centre: kappa_1i(t0) = k0, angle theta
+    const float2 kk = mul2(R.k0, k2);
+    const float2 dk0 = sub2(R.k0, k2);
+    const float2 K0 = sqrt2a(fma2(dk0, dk0, mul2(kk, y2)));
+    const float2 den0 = add2(add2(R.k0, k2), K0);
+    const float2 K0c = max2(K0, 1e-20f);
+    const float2 r0 = rcp2a(mul2(den0, K0c));
+    float2 w0 = mul2(den0, r0);
+    if (K0.x < 9.f) w0.x = K0.x < 1e-3f ? 2.f - 2.f * K0.x : gZ(K0.x) * w0.x;
+    if (K0.y < 9.f) w0.y = K0.y < 1e-3f ? 2.f - 2.f * K0.y : gZ(K0.y) * w0.y;
+    pc = fma2(ex2_2a(mul2(mul2(mul2(kk, x2), mul2(K0c, r0)), bc2(-GOSMA_LOG2E))), mul2(w0, Q), pc);
+    // bound: B = max(0, theta - s)
+    const float2 sth = mul2(bc2(0.5f), sqrt2a(x2)), cth = mul2(bc2(0.5f), sqrt2a(y2));
+    const float2 sB = fma2(sth, R.Cs, mul2(cth, R.nSs));
+    const float2 es = fma2(bc2(7.5f * U), sth, R.esS);
+    const float2 slo = max2(sub2(sB, es), 0.f);
+    const float2 shi = min2(add2(max2(sB, 0.f), es), 1.f);
+    const float2 q1 = fma2(slo, slo, bc2(-1.f)), q2 = fma2(shi, shi, bc2(-1.f));
+    const float2 chi = min2(mul2(make_float2(sqrta(-q1.x), sqrta(-q1.y)), bc2(1.f + 3.f * U)), 1.f);
+    const float2 clo =
+        mul2(make_float2(sqrta(-fminf(q2.x, 0.f)), sqrta(-fminf(q2.y, 0.f))), bc2(1.f - 3.f * U));
+    const float2 ak4 = mul2(R.A4, k2);
+    const float2 dka = sub2(R.a, k2);
+    const float2 Khi = mul2(sqrt2a(fma2(dka, dka, mul2(ak4, mul2(chi, chi)))), bc2(1.f + 4.f * U));
+    const float2 cosBlo = fma2(mul2(bc2(2.f), clo), clo, bc2(-1.f));
+    const float2 kc = mul2(k2, cosBlo);
+    const float2 ks = make_float2(fminf(fmaxf(-kc.x, R.a.x), R.b.x), fminf(fmaxf(-kc.y, R.a.y), R.b.y));
+    const float2 dks = sub2(ks, k2);
+    const float2 Kmin =
+        mul2(sqrt2a(fma2(dks, dks, mul2(mul2(mul2(bc2(4.f), ks), k2), mul2(clo, clo)))), bc2(1.f - 4.f * U));
+    const float2 den = add2(add2(R.a, k2), Khi);
+    const float2 Kc = max2(Kmin, 1e-20f);
+    const float2 r = rcp2a(mul2(den, Kc));
+    const float2 DL = mul2(mul2(mul2(ak4, mul2(slo, slo)), mul2(Kc, r)), bc2(-GOSMA_LOG2E));
+    const float2 w = min2(mul2(den, r), 2.f);
+    const float2 arg = fma2(bc2(-12.f * U), DL, add2(DL, bc2(GOSMA_TERM_SLACK)));
+    pl = fma2(ex2_2a(arg), mul2(w, Q), pl);
+}
+
 struct RowSelf {
     float vx, vy, vz, wx, wy, wz;
     float a, b, k0, cp, sp;
@@ -274,6 +415,84 @@ __device__ __forceinline__ void self_pair(const RowSelf &R, float4 M1, float4 M2
     float w = den * r;
     if (Kmax < 9.f) w = Kmax < 0.25f ? fmaxf(2.f - 2.f * Kmax, 0.f) : gZ(Kmax) * w * (1.f - 64.f * U);
     pl = fmaf(ex2a(DL - fmaf(12.f * U, fabsf(DL), GOSMA_TERM_SLACK)), w * Am, pl);
+}
+
+// The row constants of RowSelf in both lanes of packed pairs, for self_pair2.
+struct RowSelf2 {
+    float2 vx, vy, vz, wx, wy, wz;
+    float2 a, b, k0, cp, sp, nsp;
+    __device__ __forceinline__ explicit RowSelf2(const RowSelf &R)
+        : vx(bc2(R.vx)), vy(bc2(R.vy)), vz(bc2(R.vz)), wx(bc2(R.wx)), wy(bc2(R.wy)), wz(bc2(R.wz)), a(bc2(R.a)),
+          b(bc2(R.b)), k0(bc2(R.k0)), cp(bc2(R.cp)), sp(bc2(R.sp)), nsp(bc2(-R.sp)) {}
+};
+
+// Two self pairs (i, m) and (i, m') at once (lane x: partner records M1a,
+// M2a, M3a, Uma; lane y: M1b, ...): lane by lane the operations and roundings
+// of self_pair.  Besides the rewritings of cross_pair2, -sin((psi_i+psi_m)/2)
+// is formed as 0 - S (exact; S >= 0, a sum of products of non-negative
+// half-angle sines and cosines, so |S| = S), and 12u |DL| + slack as
+// -12u DL + slack (DL <= 0).
+__device__ __forceinline__ void self_pair2(const RowSelf2 &R, float4 M1a, float4 M2a, float4 M3a, float Uma,
+                                           float4 M1b, float4 M2b, float4 M3b, float Umb, float2 &pl, float2 &pc) {
+    const float U = GOSMA_U;
+    const float2 am = make_float2(M1a.w, M1b.w), bm = make_float2(M2a.w, M2b.w), k0m = make_float2(M3a.x, M3b.x),
+                 cpm = make_float2(M3a.y, M3b.y), spm = make_float2(M3a.z, M3b.z), Am = make_float2(M3a.w, M3b.w),
+                 Um = make_float2(Uma, Umb);
+    const float2 ux = make_float2(M1a.x, M1b.x), uy = make_float2(M1a.y, M1b.y), uz = make_float2(M1a.z, M1b.z);
+    const float2 lx = make_float2(M2a.x, M2b.x), ly = make_float2(M2a.y, M2b.y), lz = make_float2(M2a.z, M2b.z);
+    const float2 dx = add2(sub2(R.vx, ux), sub2(R.wx, lx)), dy = add2(sub2(R.vy, uy), sub2(R.wy, ly)),
+                 dz = add2(sub2(R.vz, uz), sub2(R.wz, lz));
+    const float2 px = add2(add2(R.vx, ux), add2(R.wx, lx)), py = add2(add2(R.vy, uy), add2(R.wy, ly)),
+                 pz = add2(add2(R.vz, uz), add2(R.wz, lz));
+    const float2 x2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+    const float2 y2 = fma2(px, px, fma2(py, py, mul2(pz, pz)));
+    // centre
+    const float2 kk = mul2(R.k0, k0m);
+    const float2 dk0 = sub2(R.k0, k0m);
+    const float2 K0 = sqrt2a(fma2(dk0, dk0, mul2(kk, y2)));
+    const float2 den0 = add2(add2(R.k0, k0m), K0);
+    const float2 K0c = max2(K0, 1e-20f);
+    const float2 r0 = rcp2a(mul2(den0, K0c));
+    float2 w0 = mul2(den0, r0);
+    if (K0.x < 9.f) w0.x = K0.x < 1e-3f ? 2.f - 2.f * K0.x : gZ(K0.x) * w0.x;
+    if (K0.y < 9.f) w0.y = K0.y < 1e-3f ? 2.f - 2.f * K0.y : gZ(K0.y) * w0.y;
+    pc = fma2(ex2_2a(mul2(mul2(mul2(kk, x2), mul2(K0c, r0)), bc2(-GOSMA_LOG2E))), mul2(w0, Um), pc);
+    // bound: A = min(pi, theta + psi_i + psi_m)
+    const float2 sth = mul2(bc2(0.5f), sqrt2a(x2)), cth = mul2(bc2(0.5f), sqrt2a(y2));
+    const float2 C = fma2(R.cp, cpm, mul2(R.nsp, spm));  // cos((psi_i + psi_m)/2)
+    const float2 S = fma2(R.sp, cpm, mul2(R.cp, spm));   // sin((psi_i + psi_m)/2)
+    const float2 cA = fma2(cth, C, mul2(sth, sub2(bc2(0.f), S)));
+    const float2 sA = fma2(sth, C, mul2(cth, S));
+    const float2 es = mul2(bc2(10.f * U), add2(sth, S));
+    const float2 t1 = add2(sA, es);
+    const float2 shi = make_float2(cA.x <= 16.f * U ? 1.f : fminf(t1.x, 1.f), cA.y <= 16.f * U ? 1.f : fminf(t1.y, 1.f));
+    const float2 slo = max2(sub2(sA, es), 0.f);
+    const float2 q2 = fma2(shi, shi, bc2(-1.f)), q1 = fma2(slo, slo, bc2(-1.f));
+    const float2 clo =
+        mul2(make_float2(sqrta(-fminf(q2.x, 0.f)), sqrta(-fminf(q2.y, 0.f))), bc2(1.f - 3.f * U));
+    const float2 chi = min2(mul2(make_float2(sqrta(-q1.x), sqrta(-q1.y)), bc2(1.f + 3.f * U)), 1.f);
+    const float2 bb = mul2(R.b, bm);
+    const float2 dbb = sub2(R.b, bm);
+    const float2 Klo =
+        mul2(sqrt2a(fma2(dbb, dbb, mul2(mul2(bc2(4.f), bb), mul2(clo, clo)))), bc2(1.f - 4.f * U));
+    const float2 c4 = mul2(bc2(4.f), mul2(chi, chi));
+    const float2 q1a = sub2(R.a, am), q2a = sub2(R.a, bm), q3a = sub2(R.b, am);
+    const float2 ca = mul2(c4, R.a), cb = mul2(c4, R.b);
+    const float2 e1 = fma2(q1a, q1a, mul2(ca, am));
+    const float2 e2 = fma2(q2a, q2a, mul2(ca, bm));
+    const float2 e3 = fma2(q3a, q3a, mul2(cb, am));
+    const float2 e4 = fma2(dbb, dbb, mul2(c4, bb));
+    const float2 Kmax = mul2(make_float2(sqrta(fmaxf(fmaxf(e1.x, e2.x), fmaxf(e3.x, e4.x))),
+                                         sqrta(fmaxf(fmaxf(e1.y, e2.y), fmaxf(e3.y, e4.y)))),
+                             bc2(1.f + 5.f * U));
+    const float2 den = add2(add2(R.b, bm), Klo);
+    const float2 r = rcp2a(mul2(den, Kmax));
+    const float2 DL = mul2(mul2(mul2(bb, mul2(shi, shi)), mul2(Kmax, r)), bc2(-4.f * GOSMA_LOG2E));
+    float2 w = mul2(den, r);
+    if (Kmax.x < 9.f) w.x = Kmax.x < 0.25f ? fmaxf(2.f - 2.f * Kmax.x, 0.f) : gZ(Kmax.x) * w.x * (1.f - 64.f * U);
+    if (Kmax.y < 9.f) w.y = Kmax.y < 0.25f ? fmaxf(2.f - 2.f * Kmax.y, 0.f) : gZ(Kmax.y) * w.y * (1.f - 64.f * U);
+    const float2 arg = sub2(DL, fma2(bc2(-12.f * U), DL, bc2(GOSMA_TERM_SLACK)));
+    pl = fma2(ex2_2a(arg), mul2(w, Am), pl);
 }
 
 // k coth(k) / 2 = Z(2k) / Z(k)^2, the diagonal self term without phi^2
@@ -467,8 +686,10 @@ __device__ void cube_bounds(const MixDev &mx, const CubePrep &prep, df zeta2, bo
         const int Ti = n1 >= BLOCK ? BLOCK : pow2ceil(n1);
         const int Tj = BLOCK / Ti;
         const int ti = tid % Ti, tj = tid / Ti;
-        const float Cr = cs.rot.Cr, Sr = cs.rot.Sr;
         for (int i = ti; i < n1; i += Ti) {
+            // rotation uncertainty of this row: point-independent, or the
+            // point-dependent form of Lemma 2 when the mixtures ask for it
+            float Cr = cs.rot.Cr, Sr = cs.rot.Sr;
             RowCross R;
             const float4 m1 = sm.M1[i], m2 = sm.M2[i], m3 = sm.M3[i];
             R.vx = m1.x;
@@ -481,6 +702,7 @@ __device__ void cube_bounds(const MixDev &mx, const CubePrep &prep, df zeta2, bo
             R.b = m2.w;
             R.k0 = m3.x;
             R.A4 = 4.f * R.a;
+            if (mx.psi_point) point_psi_r(cs.rot, m1.x, m1.y, m1.z, Cr, Sr);
             float cps = m3.y, sps = m3.z;
             // s = psi_t,i + psi_r as half-angle cosine/sine (double-float, rounded once);
             // s >= pi means B = 0 everywhere
@@ -499,21 +721,30 @@ __device__ void cube_bounds(const MixDev &mx, const CubePrep &prep, df zeta2, bo
             Acc cl, cu;
             cl.zero();
             cu.zero();
-            float pl = 0.f, pc = 0.f;
+            // columns in packed pairs (j, j + 1), pair p of the row to thread p mod Tj;
+            // each lane keeps its own FP32 chunk sum of at most CHUNK terms
+            const RowCross2 R2(R);
+            float2 pl = make_float2(0.f, 0.f), pc = make_float2(0.f, 0.f);
             int cnt = 0;
             const int j1 = mx.rj1 ? mx.rj1[i] : n2;
+            int j = (mx.rj0 ? mx.rj0[i] : 0) + 2 * tj;
 #pragma unroll 1
-            for (int j = (mx.rj0 ? mx.rj0[i] : 0) + tj; j < j1; j += Tj) {
-                cross_pair(R, sm.J1[j], sm.J2[j], pl, pc);
+            for (; j + 1 < j1; j += 2 * Tj) {
+                cross_pair2(R2, sm.J1[j], sm.J2[j], sm.J1[j + 1], sm.J2[j + 1], pl, pc);
                 if (++cnt == CHUNK) {
-                    cl.add(pl);
-                    cu.add(pc);
-                    pl = pc = 0.f;
+                    cl.add(pl.x);
+                    cl.add(pl.y);
+                    cu.add(pc.x);
+                    cu.add(pc.y);
+                    pl = pc = make_float2(0.f, 0.f);
                     cnt = 0;
                 }
             }
-            cl.add(pl);
-            cu.add(pc);
+            if (j < j1) cross_pair(R, sm.J1[j], sm.J2[j], pl.x, pc.x);  // odd last column
+            cl.add(pl.x);
+            cl.add(pl.y);
+            cu.add(pc.x);
+            cu.add(pc.y);
             T[1] = df_add(T[1], df_scale(cl.s, cl.c, Bw));
             T[3] = df_add(T[3], df_scale(cu.s, cu.c, sm.Uw[i]));
         }
@@ -543,21 +774,30 @@ __device__ void cube_bounds(const MixDev &mx, const CubePrep &prep, df zeta2, bo
                     Acc sl, su;
                     sl.zero();
                     su.zero();
-                    float pl = 0.f, pc = 0.f;
+                    // partners in packed pairs (m, m + 1), as the columns above
+                    const RowSelf2 R2(R);
+                    float2 pl = make_float2(0.f, 0.f), pc = make_float2(0.f, 0.f);
                     int cnt = 0;
                     const int mend = mx.rm1 ? mx.rm1[i] : n1;
+                    int m = i + 1 + 2 * sj;
 #pragma unroll 1
-                    for (int m = i + 1 + sj; m < mend; m += Sj) {
-                        self_pair(R, sm.M1[m], sm.M2[m], sm.M3[m], sm.Uw[m], pl, pc);
+                    for (; m + 1 < mend; m += 2 * Sj) {
+                        self_pair2(R2, sm.M1[m], sm.M2[m], sm.M3[m], sm.Uw[m], sm.M1[m + 1], sm.M2[m + 1],
+                                   sm.M3[m + 1], sm.Uw[m + 1], pl, pc);
                         if (++cnt == CHUNK) {
-                            sl.add(pl);
-                            su.add(pc);
-                            pl = pc = 0.f;
+                            sl.add(pl.x);
+                            sl.add(pl.y);
+                            su.add(pc.x);
+                            su.add(pc.y);
+                            pl = pc = make_float2(0.f, 0.f);
                             cnt = 0;
                         }
                     }
-                    sl.add(pl);
-                    su.add(pc);
+                    if (m < mend) self_pair(R, sm.M1[m], sm.M2[m], sm.M3[m], sm.Uw[m], pl.x, pc.x);  // odd last partner
+                    sl.add(pl.x);
+                    sl.add(pl.y);
+                    su.add(pc.x);
+                    su.add(pc.y);
                     // both orders (i, m) and (m, i): factor 2, exact
                     float Awi = __fmul_rd(2.f * m3.w, 1.f - (float)(CHUNK + 3) * U);
                     T[0] = df_add(T[0], df_scale(sl.s, sl.c, Awi));
@@ -576,7 +816,7 @@ __device__ void cube_bounds(const MixDev &mx, const CubePrep &prep, df zeta2, bo
         out.cross_c = (double)T[3].h + (double)T[3].l;
         out.psi_r = cs.rot.psi_r;
         float smax = __uint_as_float(cs.spsi_max);
-        out.psi_t_max = smax >= 1.f ? (float)M_PI : 2.f * asinf(smax);
+        out.psi_t_max = smax >= 1.f ? PSI_PI_F : fminf(2.f * asinf(smax), PSI_PI_F);
         out.feasible = !cs.infeasible;
         out.centre_feasible = !cs.centre_infeasible;
     }

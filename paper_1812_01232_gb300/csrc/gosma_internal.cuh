@@ -38,6 +38,9 @@ struct MixDev {
     // each component's class.
     const int *cls1, *cls2;
     const int *rj0, *rj1, *rm1;
+    // Rotation uncertainty of the cross pairs (Lemma 2): 0 the point-independent
+    // angle sqrt(3) h, 1 the point-dependent angle of each model direction.
+    int psi_point;
 };
 
 // Feasible translations of a refinement (Sec. 4.1): inside [t_lo, t_hi] and
@@ -132,6 +135,9 @@ struct gosma_ctx {
     unsigned long long mix_hash = 0;  // fingerprint of the staged mixtures (checkpoints)
     void *d_mix = nullptr;  // one allocation holding every mixture array
     gosma::MixDev mix{};
+
+    // rotation uncertainty of the bounds (gosma_set_psi_r_mode): 0 point-independent, 1 point-dependent
+    int psi_r_mode = 0;
 
     // domain
     bool have_dom = false;

@@ -1510,6 +1510,7 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
         mx.mu2h = mx.mu1l + 3 * n1;
         mx.mu2l = mx.mu2h + 3 * n2;
         mx.zeta = p.zeta;
+        mx.psi_point = ctx->psi_r_mode;
         if (layouts[k].classes) {
             int *q = imix + i_off[k];
             mx.cls1 = q;
@@ -1592,7 +1593,7 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
     Node root;
     memset(&root, 0, sizeof root);
     root.lb = -INFINITY;
-    root.psit = (float)M_PI;
+    root.psit = PSI_PI_F;
     const uint32_t rkey = order_key(-INFINITY);
     if (e == cudaSuccess) e = cudaMemsetAsync(Qb.hist, 0, sizeof(unsigned int) * 2048 * nprob, st);
     root.ubf = INFINITY;

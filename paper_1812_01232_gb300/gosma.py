@@ -77,6 +77,7 @@ SIGNATURES = {
     "gosma_set_mixtures_classes": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), D, D, D, D,
                                              D, D, D]),
     "gosma_set_domain": (C.c_int, [C.c_void_p, D, D, C.c_double]),
+    "gosma_set_psi_r_mode": (C.c_int, [C.c_void_p, C.c_int]),
     "gosma_eval_bounds": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int]),
     "gosma_eval_bounds_detail": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_int]),
     "gosma_eval_objective": (C.c_int, [C.c_void_p, D, D, D]),
@@ -95,6 +96,7 @@ SIGNATURES = {
                                            C.c_void_p, C.c_void_p]),
     "gosma_bnb_step": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(Result)]),
     "gosma_bnb_history": (C.c_int, [C.c_void_p, C.c_longlong, C.c_void_p, C.POINTER(C.c_longlong)]),
+    "gosma_bnb_last_children": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]),
     "gosma_bnb_set_incumbent": (C.c_int, [C.c_void_p, C.c_double, D]),
     "gosma_bnb_save": (C.c_int, [C.c_void_p, C.c_char_p]),
     "gosma_bnb_load": (C.c_int, [C.c_void_p, C.c_char_p]),
@@ -277,6 +279,12 @@ class Gosma:
         else:
             self.set_mixtures(prob["mu1"], prob["sigma1"], prob["phi1"], prob["mu2"], prob["kappa2"], prob["phi2"])
         self.set_domain(prob["t_lo"], prob["t_hi"], prob["zeta"])
+
+    def set_psi_r_mode(self, point: bool):
+        """Rotation uncertainty of the bounds computed afterwards (Lemma 2):
+        point=False the point-independent sqrt(3) h, True one angle per model
+        direction (gosma_set_psi_r_mode)."""
+        self._check(self.L.gosma_set_psi_r_mode(self.h, 1 if point else 0), "set_psi_r_mode")
 
     # ---------------------------------------------------------------- bounds
     def eval_bounds(self, cubes, lb=None, ub=None):
@@ -525,6 +533,19 @@ class Gosma:
             self._check(self.L.gosma_bnb_history(self.h, n.value, out.ctypes.data_as(C.c_void_p), C.byref(n)),
                         "bnb_history")
         return out
+
+    def bnb_last_children(self):
+        """The children bounded by the last iteration: (cubes (n, 10), records
+        (n, 8) as in eval_bounds_detail)."""
+        n = C.c_int(0)
+        self._check(self.L.gosma_bnb_last_children(self.h, 0, None, None, C.byref(n)), "bnb_last_children")
+        cubes = np.zeros((n.value, 10))
+        rec = np.zeros((n.value, 8))
+        if n.value:
+            self._check(self.L.gosma_bnb_last_children(self.h, n.value, cubes.ctypes.data, rec.ctypes.data,
+                                                       C.byref(n)),
+                        "bnb_last_children")
+        return cubes, rec
 
     def bnb_save(self, path):
         self._check(self.L.gosma_bnb_save(self.h, os.fsencode(path)), "bnb_save")

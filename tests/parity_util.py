@@ -1,0 +1,75 @@
+"""Element-by-element comparison of device bound records with the FP64
+oracle's, shared by the GPU parity tests.
+
+Tolerances (derived from the FP32 error model of the bound kernel):
+* lower bound: never above the oracle's (up to 1e-13 of the term scale, the
+  oracle's own FP64 summation) and within 1e-5 of the term scale
+  S = self_lb + 2 cross_ub (lb itself can be near zero, so it is no scale);
+* upper bound (f at the centre): within 1e-5 of S_c = self_c + 2 cross_c;
+* feasibility decisions: identical; psi_r to 1e-6, psi_t to FP32 accuracy.
+
+Besides the relative errors, the lower-bound deficit lb_oracle - lb_gpu is
+reported in units of eps * C22, the quantity Algorithm 1's stopping test
+compares with: a deficit of x eps C22 delays the device's certificate until
+the oracle's gap would be (1 - x) eps C22.  It is split into its self part
+(the self lower-bound sum below the oracle's) and its cross part (twice the
+cross upper-bound sum above the oracle's).  Given the incumbent d*, the
+deficit is also reported over the sub-cubes whose oracle lower bound is at
+least d* - eps C22: only there can it change a pruning decision (lb >= d*)
+or Algorithm 1's stopping test (lb >= d* - eps C22).  With GOSMA_PARITY_LOG
+set, each comparison appends its statistics as one JSON line to that file;
+with GOSMA_PARITY_DUMP set to a folder, the records themselves are saved
+there (one .npz per comparison) for offline study.
+"""
+import json
+import os
+
+import numpy as np
+
+LB_TOL = 1e-5
+UB_TOL = 1e-5
+
+
+def compare(got, ref, tag="", eps_c22=None, dstar=None, cubes=None):
+    fin = np.isfinite(ref[:, 0])
+    assert np.array_equal(fin, np.isfinite(got[:, 0])), tag + " feasibility"
+    cf = np.isfinite(ref[:, 1])
+    assert np.array_equal(cf, np.isfinite(got[:, 1])), tag + " centre feasibility"
+    S = ref[fin, 2] + 2 * ref[fin, 3]
+    d = got[fin, 0] - ref[fin, 0]
+    assert np.all(d <= 1e-13 * S), tag + " lb above oracle by %g" % (d / S).max()
+    lb_err = np.abs(d) / S
+    assert lb_err.max(initial=0.0) <= LB_TOL, tag + " lb rel err %g" % lb_err.max()
+    Sc = ref[cf, 4] + 2 * ref[cf, 5]
+    ub_err = np.abs(got[cf, 1] - ref[cf, 1]) / Sc
+    assert ub_err.max(initial=0.0) <= UB_TOL, tag + " ub rel err %g" % ub_err.max()
+    assert np.allclose(got[:, 6], ref[:, 6], rtol=1e-6)
+    # psi_t as used (after the pi/2 reading) agrees to FP32 accuracy
+    assert np.allclose(got[:, 7], ref[:, 7], rtol=2e-3, atol=2e-5)
+    stats = {"tag": tag, "cubes": int(len(ref)), "feasible": int(fin.sum()),
+             "lb_rel_max": float(lb_err.max(initial=0.0)), "ub_rel_max": float(ub_err.max(initial=0.0)),
+             "lb_deficit_max": float((-d).max(initial=0.0)),
+             "self_deficit_max": float((ref[fin, 2] - got[fin, 2]).max(initial=0.0)),
+             "cross_excess_max": float((2 * (got[fin, 3] - ref[fin, 3])).max(initial=0.0))}
+    if eps_c22 is not None:
+        stats["eps_c22"] = float(eps_c22)
+        stats["lb_deficit_over_eps_c22"] = stats["lb_deficit_max"] / eps_c22
+        if dstar is not None and np.isfinite(dstar):
+            # the sub-cubes whose pruning (lb >= d*) or stopping-test (lb >= d* - eps C22)
+            # decision a deficit can change: oracle lb at least d* - eps C22
+            near = ref[fin, 0] >= dstar - eps_c22
+            stats["dstar"] = float(dstar)
+            stats["near_cubes"] = int(near.sum())
+            stats["near_deficit_over_eps_c22"] = float((-d[near]).max(initial=0.0)) / eps_c22
+            stats["near_lb_rel_max"] = float(lb_err[near].max(initial=0.0))
+    path = os.environ.get("GOSMA_PARITY_LOG")
+    if path:
+        with open(path, "a") as f:
+            f.write(json.dumps(stats) + "\n")
+    dump = os.environ.get("GOSMA_PARITY_DUMP")
+    if dump:
+        os.makedirs(dump, exist_ok=True)
+        name = "".join(ch if ch.isalnum() else "_" for ch in tag)
+        np.savez_compressed(os.path.join(dump, name + ".npz"), got=got, ref=ref,
+                            cubes=cubes if cubes is not None else np.zeros(0))
+    return stats

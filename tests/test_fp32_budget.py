@@ -459,6 +459,70 @@ def test_psi_t_rounded_outward(oracle_mod):
     assert (psi >= np.pi).sum() > 300 and (psi < 1e-3).sum() > 300 and ((psi > 0.5) & (psi < np.pi)).sum() > 300
 
 
+def _point_psi_r_device(r0, h, v, sq, allow=True):
+    """sin(psi_r / 2) of one model direction as the kernel forms it
+    (point_psi_r in csrc/bounds_core.cuh): the pre-pass's FP64 vertex images
+    J_r(r0) d / 2 rounded to float, their largest norm and 3 h^2 / 8 rounded
+    up; FP32 cross products (the fused multiply-adds rounded once), the
+    square root off by sq * 2u, the allowances, and the result rounded up."""
+    th2 = float(r0 @ r0)
+    th = np.sqrt(th2)
+    A = 1 - th2 / 6 if th < 1e-8 else np.sin(th) / th
+    B = 0.5 - th2 / 24 if th < 1e-8 else (1 - np.cos(th)) / th2
+    Cc = 1 / 6 - th2 / 120 if th < 1e-6 else (th - A * th) / (th2 * th)
+    x, y, z = r0
+    S = np.array([[0, -z, y], [z, 0, -x], [-y, x, 0]])
+    J = np.eye(3) - B * S + Cc * (S @ S)
+    cs, jmax = [], 0.0
+    for k in range(4):
+        d = np.full(3, h)
+        if k:
+            d[k - 1] = -h
+        c = 0.5 * (J @ d)
+        cs.append(c.astype(np.float32))
+        jmax = max(jmax, np.linalg.norm(c))
+    jm = toward(np.array([jmax]), np.ones(1))[0]
+    s2 = toward(np.array([0.375 * h * h]), np.ones(1))[0]
+    vh = v.astype(np.float32)
+    best = F(0)
+    for c in cs:
+        def fm(a, b, cc):
+            return fma(np.array([a]), np.array([b]), np.array([cc]))[0]
+        cx = fm(c[1], vh[2], -(c[2] * vh[1]))
+        cy = fm(c[2], vh[0], -(c[0] * vh[2]))
+        cz = fm(c[0], vh[1], -(c[1] * vh[0]))
+        best = max(best, fm(cx, cx, fm(cy, cy, cz * cz)))
+    r = sqrta(np.array([best]), sq)[0]
+    if not allow:
+        return float(r) + float(s2)
+    lin = toward(np.array([float(r) * (1 + 4 * U) + 8 * U * float(jm)]), np.ones(1))
+    return float(toward(np.array([float(lin[0]) + float(s2)]), np.ones(1))[0])
+
+
+def test_point_psi_r_rounded_outward(oracle_mod):
+    """The per-direction rotation uncertainty of Lemma 2 (reading R16) as the
+    kernel computes it: its half-angle sine is never below the oracle's, with
+    the square root at either end of its error bound, over cubes all over the
+    pi-ball (a third near its surface) from h = 1e-6 to 1; without the
+    allowances, cases fall below."""
+    rng = np.random.default_rng(31)
+    short = 0
+    for k in range(3000):
+        h = float(np.exp(rng.uniform(np.log(1e-6), 0)))
+        d = rng.standard_normal(3)
+        d /= np.linalg.norm(d)
+        r0 = d * (rng.uniform(2.6, 3.1) if k % 3 == 0 else rng.uniform(0, 2.6))
+        v = rng.standard_normal(3)
+        v /= np.linalg.norm(v)
+        ref = np.sin(0.5 * oracle_mod.psi_r_point(r0, h, v))
+        hk = float(toward(np.array([np.sin(0.5 * min(np.sqrt(3) * h, np.pi))]), np.ones(1))[0])
+        for sq in (-1.0, 1.0):
+            dev = min(_point_psi_r_device(r0, h, v, sq), hk)
+            assert dev >= ref * (1 - 1e-15), (k, r0, h, v, dev / ref - 1)
+        short += _point_psi_r_device(r0, h, v, -1.0, allow=False) < ref
+    assert short > 0
+
+
 def _row_cases(oracle_mod, rng, n2):
     """One model component against n2 image components in one cube: the
     pairs (0, j) of a row, with the oracle's pair bounds."""
@@ -498,31 +562,56 @@ def _acc_add(s, c, x):
 
 
 def test_cross_row_sum_never_below_the_oracle(oracle_mod):
-    """A whole row of cross pairs: terms fused into FP32 chunk sums of 8,
-    chunks into a compensated sum, the row factor applied once (df_scale,
-    exact product plus one rounding) -- the (8 + 6)u of the row factor has to
-    cover the chunk and row sums."""
+    """A whole row of cross pairs: terms fused into FP32 chunk sums of 8
+    (one lane, or the packed loop's two lanes), chunks into a compensated
+    sum, the row factor applied once (df_scale, exact product plus one
+    rounding) -- the (8 + 6)u of the row factor has to cover the chunk and
+    row sums."""
     rng = np.random.default_rng(21)
     for trial in range(40):
         n2 = int(rng.integers(8, 300))
         c, ref = _row_cases(oracle_mod, rng, n2)
         for signs in [(-1.0,) * 10] + [tuple(rng.choice([-1.0, 1.0], 10)) for _ in range(3)]:
             e, wQ, Bw = _cross_parts(c, signs)
-            row = _row_sum(e, wQ, Bw[0], rng.permutation(n2))  # any order of the pairs within a thread
-            assert row >= ref, (trial, n2, row / ref - 1)
+            for paired in (False, True):  # any order of the pairs within a thread
+                row = _row_sum(e, wQ, Bw[0], rng.permutation(n2), paired)
+                assert row >= ref, (trial, n2, paired, row / ref - 1)
 
 
-def _row_sum(e, wX, factor, order):
+def _row_sum(e, wX, factor, order, paired=False):
     """A thread's row: FP32 chunk sums of 8 fused terms, a compensated sum
-    of the chunks, and the row factor applied once (df_scale)."""
-    s_, c_, pl, cnt = F(0), F(0), F(0), 0
-    for j in order:
-        pl = F(np.float64(e[j]) * np.float64(wX[j]) + np.float64(pl))
-        cnt += 1
-        if cnt == 8:
-            s_, c_ = _acc_add(s_, c_, pl)
-            pl, cnt = F(0), 0
-    s_, c_ = _acc_add(s_, c_, pl)
+    of the chunks, and the row factor applied once (df_scale).  paired: the
+    kernel's packed loop, which takes the terms two at a time into two lanes,
+    each with its own chunk sum; after 8 steps both lanes go into the
+    compensated sum (lane x first), and an odd last term joins lane x."""
+    s_, c_ = F(0), F(0)
+
+    def fused(j, acc):
+        return F(np.float64(e[j]) * np.float64(wX[j]) + np.float64(acc))
+
+    if not paired:
+        pl, cnt = F(0), 0
+        for j in order:
+            pl = fused(j, pl)
+            cnt += 1
+            if cnt == 8:
+                s_, c_ = _acc_add(s_, c_, pl)
+                pl, cnt = F(0), 0
+        s_, c_ = _acc_add(s_, c_, pl)
+    else:
+        px, py, cnt = F(0), F(0), 0
+        n = len(order)
+        for k in range(0, n - 1, 2):
+            px, py = fused(order[k], px), fused(order[k + 1], py)
+            cnt += 1
+            if cnt == 8:
+                s_, c_ = _acc_add(s_, c_, px)
+                s_, c_ = _acc_add(s_, c_, py)
+                px, py, cnt = F(0), F(0), 0
+        if n % 2:
+            px = fused(order[n - 1], px)
+        s_, c_ = _acc_add(s_, c_, px)
+        s_, c_ = _acc_add(s_, c_, py)
     h = F(np.float64(s_) * np.float64(factor))
     lo = F(np.float64(c_) * np.float64(factor) + (np.float64(s_) * np.float64(factor) - np.float64(h)))
     return np.float64(h) + np.float64(lo)
@@ -556,8 +645,9 @@ def test_self_row_sum_never_above_the_oracle(oracle_mod):
                   for k in m)
         for signs in [(-1.0,) * 13, (1.0,) * 13] + [tuple(rng.choice([-1.0, 1.0], 13)) for _ in range(3)]:
             e, wA, Awi = _self_parts(c, signs)
-            row = _row_sum(e, wA, Awi[0], rng.permutation(n1 - 1))
-            assert row <= ref, (trial, n1, row / ref - 1)
+            for paired in (False, True):
+                row = _row_sum(e, wA, Awi[0], rng.permutation(n1 - 1), paired)
+                assert row <= ref, (trial, n1, paired, row / ref - 1)
 
 
 def test_the_cases_reach_every_regime(cases):

@@ -16,7 +16,8 @@ the (b_i, b_j) corner in place of the largest corner K in the self-pair
 bound: log Z(K) - k1 - k2 decreases in each concentration, so that form is a
 valid (slightly tighter) bound too.  Nor are changes that double precision
 cannot see: the second-order terms of the small-angle series of Rodrigues'
-formula (below 1e-8 rad they round away against 1), or of d log Z / dx
+formula (below 1e-8 rad they round away against 1), of the right Jacobian
+below 1e-6 rad (they multiply [r0]x, itself below 1e-6), or of d log Z / dx
 below 1e-4 (no term of the objective reaches K < 1e-4 with any weight).
 """
 import concurrent.futures as cf
@@ -78,6 +79,18 @@ MUTANTS = [
      "return 1.0 + 2.0 / expm1(2.0 * x) + 1.0 / x;"),
     # Lemmas 2 and 3, the kappa interval
     ("Lemma 2: sqrt(2) in place of sqrt(3)", G, "double p = sqrt(3.0) * r_hw;", "double p = sqrt(2.0) * r_hw;"),
+    ("Lemma 2 per direction: the left Jacobian in place of the right", G,
+     "J[3 * p + q] = (p == q ? 1.0 : 0.0) - c1 * S[3 * p + q] + c2 * s2;",
+     "J[3 * p + q] = (p == q ? 1.0 : 0.0) + c1 * S[3 * p + q] + c2 * s2;"),
+    ("Lemma 2 per direction: the second-order allowance dropped", G, "double s = lin + 3.0 * r_hw * r_hw / 8.0;",
+     "double s = lin;"),
+    ("Lemma 2 per direction: one vertex only", G, "for (int k = 0; k < 4; ++k) { /* the 8 vertices",
+     "for (int k = 0; k < 1; ++k) { /* the 8 vertices"),
+    ("Lemma 2 per direction: the vertex images without the half", G, "double nx = 0.5 * norm3(x);",
+     "double nx = norm3(x);"),
+    ("Lemma 2 per direction: its bound unused by the cross pairs", G,
+     "cp->psir_i[i] = mode == 1 ? om_psi_r_point(cube + CUBE_R0, cube[CUBE_RHW], cp->v + 3 * i) : cp->psir;",
+     "cp->psir_i[i] = cp->psir;"),
     ("Lemma 3: half of the vertices", G, "for (int vtx = 0; vtx < 8; ++vtx) {", "for (int vtx = 0; vtx < 4; ++vtx) {"),
     ("Lemma 3: a point inside the cuboid gets 0", G, "if (inside) return M_PI;", "if (inside) return 0.0;"),
     ("kappa interval: nearest face in place of the farthest", G, "double f = f1 > f2 ? f1 : f2;",

@@ -166,6 +166,84 @@ def test_psi_r_dominates_sampled_rotations(oracle_mod):
         assert ang.max() <= oracle_mod.psi_r(hw) + 1e-12
 
 
+def _largest_rotation_angle(r0, hw, p, rng, n_inner=2000):
+    """Largest angle between R_r p and R_r0 p (scipy rotations) over samples of
+    the rotation cube: its 8 vertices, 20 points on each of its 12 edges,
+    100 on each of its 6 faces and n_inner inside."""
+    corners = np.array([[(k >> a & 1) * 2 - 1 for a in range(3)] for k in range(8)], float)
+    pts = [corners]
+    for a in range(3):  # edges along axis a
+        for k in range(4):
+            e = np.zeros((20, 3))
+            e[:, a] = np.linspace(-1, 1, 20)
+            o = [b for b in range(3) if b != a]
+            e[:, o[0]] = 1.0 if k & 1 else -1.0
+            e[:, o[1]] = 1.0 if k & 2 else -1.0
+            pts.append(e)
+    for a in range(3):  # faces normal to axis a
+        for sgn in (-1.0, 1.0):
+            f = rng.uniform(-1, 1, (100, 3))
+            f[:, a] = sgn
+            pts.append(f)
+    pts.append(rng.uniform(-1, 1, (n_inner, 3)))
+    rs = r0 + hw * np.concatenate(pts)
+    a = Rotation.from_rotvec(rs).apply(p)
+    b = Rotation.from_rotvec(r0).apply(p)
+    return float(np.arctan2(np.linalg.norm(np.cross(a, b), axis=1), a @ b).max())
+
+
+def _random_rotation_cube(rng, k):
+    """Cube centres over the whole pi-ball, a third of them near its surface,
+    where the exponential map's Jacobian contracts most."""
+    d = rng.standard_normal(3)
+    d /= np.linalg.norm(d)
+    rad = rng.uniform(2.6, 3.1) if k % 3 == 0 else rng.uniform(0, 2.6)
+    return rad * d
+
+
+def test_point_psi_r_dominates_sampled_rotations(oracle_mod):
+    """Lemma 2, point-dependent form (reading R16): the bound is never below
+    the largest angle found by dense sampling of the rotation cube, and never
+    above the point-independent sqrt(3) h."""
+    rng = np.random.default_rng(13)
+    for k in range(90):
+        hw = [1e-3, 1e-2, 0.05, 0.2, 0.5, 1.0][k % 6]
+        r0 = _random_rotation_cube(rng, k)
+        p = rng.standard_normal(3)
+        p /= np.linalg.norm(p)
+        bound = oracle_mod.psi_r_point(r0, hw, p)
+        assert _largest_rotation_angle(r0, hw, p, rng) <= bound + 1e-12, (k, r0, hw, p)
+        assert bound <= oracle_mod.psi_r(hw) + 1e-15
+
+
+def test_point_psi_r_is_tight_for_small_cubes(oracle_mod):
+    """The bound's first-order term is attained at a vertex, so for small cubes
+    it exceeds the sampled maximum by second-order terms only (at most 3 h^2 / 4
+    of allowance and 3 h^2 / 4 of linearisation at the vertex)."""
+    rng = np.random.default_rng(14)
+    for k in range(60):
+        hw = [1e-3, 3e-3][k % 2]
+        r0 = _random_rotation_cube(rng, k)
+        p = rng.standard_normal(3)
+        p /= np.linalg.norm(p)
+        bound = oracle_mod.psi_r_point(r0, hw, p)
+        assert bound - _largest_rotation_angle(r0, hw, p, rng, 200) <= 2 * hw * hw, (k, r0, p)
+
+
+@pytest.mark.parametrize("hw", [1e-3, 1e-2, 0.1])
+def test_point_psi_r_closed_form_at_the_identity(oracle_mod, hw):
+    """At r0 = 0 a unit vector p on a coordinate axis turns by at most sqrt(2) h
+    over the cube (attained at r = (0, h, h) for p = e_x: the angle is
+    2 asin(sin(|r|/2) |r x p| / |r|), largest where r is orthogonal to p), and
+    the bound is that plus its second-order allowance."""
+    for p in np.eye(3):
+        b = oracle_mod.psi_r_point(np.zeros(3), hw, p)
+        assert np.sqrt(2) * hw <= b <= np.sqrt(2) * hw + 0.8 * hw * hw
+    # along the diagonal the largest turn is smaller: sqrt(8/3) h to first order
+    d = np.ones(3) / np.sqrt(3)
+    assert oracle_mod.psi_r_point(np.zeros(3), hw, d) <= np.sqrt(8 / 3) * hw + 0.8 * hw * hw
+
+
 def test_psi_t_dominates_sampled_translations(oracle_mod):
     rng = np.random.default_rng(12)
     tight = 0
@@ -360,6 +438,33 @@ def test_bounds_sandwich_objective(oracle_mod):
         if np.isfinite(b[1]):
             R0 = Rotation.from_rotvec(cube[0:3]).as_matrix()
             assert b[1] == pytest.approx(oracle_mod.objective(mix, R0, cube[4:7]), rel=1e-9)
+        for r, t in _sample_in_cube(rng, cube, prob, 30):
+            assert b[0] <= oracle_mod.objective_r(mix, r, t) + 1e-9
+            n += 1
+    assert n > 500
+
+
+def test_point_psi_r_bounds_sandwich_objective(oracle_mod):
+    """Theorem 1 with the point-dependent psi_r (reading R16): the lower bound
+    stays below f at sampled poses of the cube, is at least the lower bound
+    with the point-independent psi_r (never looser), and is strictly above it
+    on most cubes; the upper bound is unchanged."""
+    prob = synth.tiny_problem(34)
+    mix = oracle_mod.Mixtures.from_problem(prob)
+    cubes = synth.tree_cubes(35, 60, prob["t_lo"], prob["t_hi"], 3, 12, near=(prob["r_gt"], prob["t_gt"]),
+                             near_frac=0.7)
+    B0 = oracle_mod.bounds(mix, cubes, prob["zeta"])
+    B1 = oracle_mod.bounds(mix, cubes, prob["zeta"], psi_mode=1)
+    fin = np.isfinite(B0[:, 0])
+    assert np.array_equal(fin, np.isfinite(B1[:, 0]))
+    assert np.array_equal(B0[:, 1], B1[:, 1]) and np.array_equal(B0[:, 2], B1[:, 2])
+    assert np.all(B1[fin, 0] >= B0[fin, 0] - 1e-12 * (B0[fin, 2] + 2 * B0[fin, 3]))
+    assert np.mean(B1[fin, 0] > B0[fin, 0]) > 0.5
+    rng = np.random.default_rng(36)
+    n = 0
+    for cube, b in zip(cubes, B1):
+        if not np.isfinite(b[0]):
+            continue
         for r, t in _sample_in_cube(rng, cube, prob, 30):
             assert b[0] <= oracle_mod.objective_r(mix, r, t) + 1e-9
             n += 1
