@@ -70,12 +70,18 @@ METRIC = "pair-bound evals/s (cube*i*j/s)"
 UNIT = "pairs/s"
 POP = 8192
 SEED = 2000
-# FP32-pipe operations per pair of the bound kernel, counted from its
-# source (half-angle, centre term, bound term, compensated accumulation);
-# MUFU operations (9 per pair) run on a separate pipe with 32 lanes per SM.
+# FP32-pipe lane operations per pair the bound kernel executes, counted from
+# its source (half-angle, centre term, bound term, outward roundings,
+# compensated accumulation); packed FP32x2 instructions do two of them.
 OPS_CROSS = 112
 OPS_SELF = 120
 FP32_LANES_PER_SM = 128
+# Algorithmic work per pair bound, cross or self: the closed forms of
+# Theorem 1 for the bound and the centre term without the kernel's
+# outward-rounding allowances and compensated sums, about 40 FP32 operations
+# and 11 multi-function-unit operations (7 sqrt, 2 rcp, 2 ex2).
+ALG_FP32_PER_PAIR = 40
+ALG_MUFU_MIX = {"sqrt": 7, "rcp": 2, "ex2": 2}
 
 
 def log(*a):
@@ -289,6 +295,7 @@ def run_ours(args):
     from paper_1812_01232_gb300.gosma import Gosma
     prob = make_problem(rank)
     ctx = Gosma(local)
+    rates = ctx.selftest_pipe_rates()  # measured pipe throughputs (lanes per SM per clock)
     ctx.set_problem(prob)
     n1, n2 = ctx.n1, ctx.n2
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
@@ -352,12 +359,24 @@ def run_ours(args):
         e2e_t.append(time.perf_counter() - t0)
     e2e_value = 8 * POP * n1 * n2 / float(np.mean(e2e_t))
 
-    # ---------------- roofline of the bound kernel (FP32 pipe)
+    # ---------------- roofline of the bound kernel (FP32 pipe; algorithmic count against FP32 and MUFU)
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
-    max_mhz = ck["sm_max_mhz"] or 2070.0
+    max_mhz = ck["sm_max_mhz"] or rates["clock_mhz"]
     peak = sm_count * FP32_LANES_PER_SM * max_mhz * 1e6 / 1e9  # Gop/s
     achieved = (OPS_CROSS * pairs + OPS_SELF * self_pairs) / (bound_ms / 1e3) / 1e9
     traffic = kernel_traffic()
+    # effective MUFU rate of the kernel's mix (harmonic: cycles add up per pair)
+    mufu_n = sum(ALG_MUFU_MIX.values())
+    mufu_rate = mufu_n / sum(k / rates[op] for op, k in ALG_MUFU_MIX.items())
+    mufu_peak = sm_count * mufu_rate * max_mhz * 1e6 / 1e9  # Gop/s
+    alg_pairs = pairs + self_pairs
+    alg_fp32 = ALG_FP32_PER_PAIR * alg_pairs / (bound_ms / 1e3) / 1e9
+    alg_mufu = mufu_n * alg_pairs / (bound_ms / 1e3) / 1e9
+    alg = {"fp32_ops_per_pair": ALG_FP32_PER_PAIR, "mufu_ops_per_pair": mufu_n, "mufu_mix": ALG_MUFU_MIX,
+           "pairs_per_step": alg_pairs / args.steps, "fp32_achieved": alg_fp32, "fp32_frac": alg_fp32 / peak,
+           "mufu_achieved": alg_mufu, "mufu_peak": mufu_peak, "mufu_frac": alg_mufu / mufu_peak,
+           "unit": "Gop/s"}
+    alg["binding"] = "mufu" if alg["mufu_frac"] >= alg["fp32_frac"] else "fp32"
 
     if rank != 0:
         if dist:
@@ -386,8 +405,16 @@ def run_ours(args):
                         "distinct translation cuboid; %d distinct)" % (len(cubes), n_cuboids)},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s (FP32 pipe)",
                      "frac": achieved / peak, "traffic": traffic,
+                     "frac_algorithmic": max(alg["fp32_frac"], alg["mufu_frac"]), "algorithmic": alg,
                      "kernel": "bound_children", "kernel_ms_per_step": bound_ms / args.steps,
-                     "peak_basis": "%d SMs x %d FP32 lanes x %.0f MHz" % (sm_count, FP32_LANES_PER_SM, max_mhz)},
+                     "peak_basis": "%d SMs x %d FP32 lanes x %.0f MHz (unit count); frac counts the %d/%d FP32 "
+                                   "lane operations the kernel executes per cross/self pair"
+                                   % (sm_count, FP32_LANES_PER_SM, max_mhz, OPS_CROSS, OPS_SELF),
+                     "mufu_peak_basis": "%d SMs x %.1f MUFU lanes per SM per clock x %.0f MHz: the sqrt/rcp/ex2 "
+                                        "rates measured by gosma_selftest_pipe_rates (8 independent chains per "
+                                        "thread, 2048 threads per SM, CUDA events), weighted by the mix %s"
+                                        % (sm_count, mufu_rate, max_mhz, ALG_MUFU_MIX),
+                     "measured_pipe_rates": rates},
         "cpu_baseline": cpu,
         "clocks": ck,
         "gpu_launches": launches,

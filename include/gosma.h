@@ -474,6 +474,16 @@ int gosma_debug_fail_allocations(gosma_ctx *ctx, int n);
  * in that order), and the error bounds the bound kernel's slack assumes. */
 int gosma_selftest_approx(gosma_ctx *ctx, double measured[5], double assumed[5]);
 
+/* Diagnostics (no counterpart in the paper): measured throughput of the
+ * pipes the bound kernel runs on, in lane operations per SM per clock cycle
+ * at the device's maximum SM clock (*clock_mhz receives it): rates[0] scalar
+ * FP32 fused multiply-add, rates[1] packed FP32x2 fused multiply-add (lanes,
+ * two per instruction), rates[2] ex2.approx, rates[3] sqrt.approx, rates[4]
+ * rcp.approx.  Each is timed with CUDA events over one launch of 8 x 256
+ * threads per SM running eight independent chains of that instruction (best
+ * of three launches after a warm-up).  A few milliseconds of device time. */
+int gosma_selftest_pipe_rates(gosma_ctx *ctx, double rates[5], double *clock_mhz);
+
 #ifdef __cplusplus
 }
 #endif

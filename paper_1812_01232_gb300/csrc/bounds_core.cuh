@@ -49,13 +49,14 @@ struct CubePrep {
     float psi_r;
     int infeasible;      // rotation cube wholly outside the pi-ball
     float pad[2];
-    // point-dependent psi_r (Lemma 2): pj[0..11] the images c_k = J_r(r0) d_k / 2
-    // of four vertices d_k = (+-h, +-h, h) of the rotation cube (the other four
-    // are their negatives), pj[12] their largest norm (rounded up), pj[13]
-    // 3 h^2 / 8 (rounded up), pj[14..15] padding
-    float pj[16];
+    // point-dependent psi_r (Lemma 2), from the images c_k = J_r(r0) d_k / 2 of
+    // four vertices d_k = (+-h, +-h, h) of the rotation cube (the other four are
+    // their negatives): pj[8k .. 8k+2] c_k (hi), pj[8k+3 .. 8k+5] c_k (lo),
+    // pj[8k+6], pj[8k+7] |c_k|^2 (hi, lo); pj[32] 3 h^2 / 8 and pj[33]
+    // 64 u^2 max_k |c_k| (both rounded up); pj[34..35] padding
+    float pj[36];
 };
-static_assert(sizeof(CubePrep) == 208, "CubePrep layout");
+static_assert(sizeof(CubePrep) == 288, "CubePrep layout");
 constexpr int PREP_WORDS = sizeof(CubePrep) / 4;
 
 // shared-memory scalars of one cube
@@ -69,32 +70,54 @@ struct CubeShared {
 
 // Directions are double-floats (hi + lo equals the unit vector to ~2^-44),
 // so differences of nearly parallel directions keep full FP32 relative
-// accuracy.  Shared-memory records are float4 so that a pair reads its
-// partner with two or three 16-byte loads.
+// accuracy.  The pair loops take partners two at a time into the two lanes
+// of packed FP32x2 registers, so the records are stored in pairs, lanes
+// interleaved: one 16-byte load gives two aligned lane pairs.  A missing
+// partner of an odd count is a copy of the last one with zero weight.
+//   JP (image columns 2p, 2p+1; lanes a, b), 4 float4 per pair:
+//     (ux_a, ux_b, uy_a, uy_b) (uz_a, uz_b, k2_a, k2_b) (lx_a, lx_b, ly_a, ly_b) (lz_a, lz_b, Q_a, Q_b)
+//     u = R_r0^T mu_2j (hi, then lo), k2 = kappa_2j, Q the column factor
+//   MP (model rows 2q, 2q+1), 6 float4 per pair:
+//     (vx_a, vx_b, vy_a, vy_b) (vz_a, vz_b, a_a, a_b) (lx_a, lx_b, ly_a, ly_b) (lz_a, lz_b, b_a, b_b)
+//     (k0_a, k0_b, cp_a, cp_b) (sp_a, sp_b, Aw_a, Aw_b)
+//     v = v_i (hi, then lo), [a, b] the kappa interval, k0 = kappa_1i(t0),
+//     cp, sp = cos, sin of psi_t,i / 2, Aw the row factor of the self bound
+//   UP (model rows 2q, 2q+1): (Uw_a, Uw_b), the row factor of the centre term
 struct SmemArrays {
-    float4 *M1;  // model rows (n1): v_hi (xyz), a
-    float4 *M2;  //                   v_lo (xyz), b
-    float4 *M3;  //                   k0, cos(psi_t/2), sin(psi_t/2), A_w
-    float *Uw;   //                   U_w
-    float4 *J1;  // image columns (n2): u_hi (xyz), kappa_2
-    float4 *J2;  //                     u_lo (xyz), Q
+    float4 *JP;
+    float4 *MP;
+    float2 *UP;
 };
 
 __host__ __device__ inline size_t bounds_smem_arrays_bytes(int n1, int n2) {
-    return (size_t)n1 * (3 * sizeof(float4) + sizeof(float)) + (size_t)n2 * 2 * sizeof(float4) + 16;
+    const size_t p1 = (size_t)(n1 + 1) / 2, p2 = (size_t)(n2 + 1) / 2;
+    return p2 * 4 * sizeof(float4) + p1 * (6 * sizeof(float4) + sizeof(float2)) + 16;
 }
 
 __device__ inline SmemArrays carve(float *base, int n1, int n2) {
     SmemArrays s;
     float4 *p = reinterpret_cast<float4 *>(base);
-    s.M1 = p;
-    s.M2 = p + n1;
-    s.M3 = p + 2 * n1;
-    s.J1 = p + 3 * n1;
-    s.J2 = p + 3 * n1 + n2;
-    s.Uw = reinterpret_cast<float *>(p + 3 * n1 + 2 * n2);
+    const int p1 = (n1 + 1) / 2, p2 = (n2 + 1) / 2;
+    s.JP = p;
+    s.MP = p + 4 * p2;
+    s.UP = reinterpret_cast<float2 *>(p + 4 * p2 + 6 * p1);
     return s;
 }
+
+// Field f (0..11, in the order of MP above: vx vy vz a lx ly lz b k0 cp sp Aw)
+// of model row i.
+__device__ __forceinline__ float &mp_at(const SmemArrays &sm, int i, int f) {
+    return reinterpret_cast<float *>(sm.MP)[24 * (i >> 1) + 2 * f + (i & 1)];
+}
+__device__ __forceinline__ float &up_at(const SmemArrays &sm, int i) {
+    return reinterpret_cast<float *>(sm.UP)[i];
+}
+// Field f (0..7: ux uy uz k2 lx ly lz Q) of image column j.
+__device__ __forceinline__ float &jp_at(const SmemArrays &sm, int j, int f) {
+    return reinterpret_cast<float *>(sm.JP)[16 * (j >> 1) + 2 * f + (j & 1)];
+}
+enum { MP_VX = 0, MP_VY, MP_VZ, MP_A, MP_LX, MP_LY, MP_LZ, MP_B, MP_K0, MP_CP, MP_SP, MP_AW };
+enum { JP_UX = 0, JP_UY, JP_UZ, JP_K2, JP_LX, JP_LY, JP_LZ, JP_Q };
 
 __device__ inline int pow2ceil(int x) {
     int p = 1;
@@ -151,51 +174,80 @@ __device__ inline void cube_prepare(const double r0[3], double rhw, const double
             double s2 = S[3 * p] * S[q] + S[3 * p + 1] * S[3 + q] + S[3 * p + 2] * S[6 + q];
             J[3 * p + q] = (p == q ? 1.0 : 0.0) - B * S[3 * p + q] + C * s2;
         }
-    double jmax = 0.0;
+    double cmax = 0.0;
     for (int k = 0; k < 4; ++k) {
         double d[3] = {rhw, rhw, rhw};
         if (k > 0) d[k - 1] = -rhw;
         double n2 = 0.0;
         for (int p = 0; p < 3; ++p) {
             double c = 0.5 * (J[3 * p] * d[0] + J[3 * p + 1] * d[1] + J[3 * p + 2] * d[2]);
-            o.pj[3 * k + p] = (float)c;
+            split_double(c, o.pj[8 * k + p], o.pj[8 * k + 3 + p]);
             n2 += c * c;
         }
-        jmax = fmax(jmax, sqrt(n2));
+        split_double(n2, o.pj[8 * k + 6], o.pj[8 * k + 7]);
+        cmax = fmax(cmax, sqrt(n2));
     }
-    o.pj[12] = __double2float_ru(jmax);
-    o.pj[13] = __double2float_ru(0.375 * rhw * rhw);
-    o.pj[14] = o.pj[15] = 0.f;
+    o.pj[32] = __double2float_ru(0.375 * rhw * rhw);
+    o.pj[33] = __double2float_ru(64.0 * 0x1p-48 * cmax);
+    o.pj[34] = o.pj[35] = 0.f;
 }
 
-// Lemma 2, point-dependent form, for one model direction v (the hi part of
-// the unit vector v_i at t0): with w(r) the vector part of the relative
+// Lemma 2, point-dependent form, for one model direction v (the unit vector
+// v_i at t0, as a double-float): with w(r) the vector part of the relative
 // quaternion q(r0)^* q(r), sin(angle(R_r v, R_r0 v) / 2) = |w(r) x v|, and
 // w(r0 + d) = J_r(r0) d / 2 + rho with |rho| <= |d|^2 / 8 (the second
 // derivative of the quaternion exponential along a line is at most |d/2|^2),
 // so over the cube sin(psi_r / 2) <= max_k |c_k x v| + 3 h^2 / 8 (the
 // first-order term is a norm of a linear map: largest at a vertex).
-// Outward rounding: c_k and v carry u relative each (2u |c| on the cross
-// product), each FP32 cross-product component 2u (|c_a v_b| + |c_b v_a|)
-// (5u |c| on the vector), the squared norm 3u, sqrt 2u: the computed maximum
-// times (1 + 4u) plus 8u |c|max, rounded up, bounds the first-order term.
-// Cr, Sr (the point-independent pair) are replaced when the bound is smaller.
-__device__ __forceinline__ void point_psi_r(const CubePrep &P, float vx, float vy, float vz, float &Cr, float &Sr) {
-    const float U = GOSMA_U;
-    // read at every call: loads hoisted out of the row loop would hold 14
-    // registers across the pair loops
-    const volatile float *Jd = P.pj;
-    float best = 0.f;
+// |c_k x v|^2 = |c_k|^2 - (c_k . v)^2 is formed in double-float (error at most
+// 8 u^2 |c|^2: no cancellation beyond a factor 4, since the largest of the
+// four is at least |c|^2 / 4 for any v), its square root by one double-float
+// Newton step from the FP32 estimate (relative error below 8 u^2), and the
+// sum with 3 h^2 / 8 and the 64 u^2 |c|max allowance is rounded up once: the
+// sine is at most one unit in the last place above the exact bound, as the
+// point-independent sine.
+// The cosine sqrt(1 - s^2) is formed the same way and rounded down (0 where
+// it is below 1/16, i.e. psi_r above 172 degrees).  Cr, Sr (the
+// point-independent pair) are replaced when the bound is smaller.
+__device__ __forceinline__ void point_psi_r(const CubePrep &P, df vx, df vy, df vz, float &Cr, float &Sr) {
+    const float U2 = GOSMA_U * GOSMA_U;
+    // read at every call: loads hoisted out of the row loop would hold the
+    // 36 words in registers across the pair loops
+    const volatile float *pj = P.pj;
+    df best = {0.f, 0.f};
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const float cx = Jd[3 * k], cy = Jd[3 * k + 1], cz = Jd[3 * k + 2];
-        const float x = fmaf(cy, vz, -cz * vy), y = fmaf(cz, vx, -cx * vz), z = fmaf(cx, vy, -cy * vx);
-        best = fmaxf(best, fmaf(x, x, fmaf(y, y, z * z)));
+        const df c0 = {pj[8 * k], pj[8 * k + 3]}, c1 = {pj[8 * k + 1], pj[8 * k + 4]},
+                 c2 = {pj[8 * k + 2], pj[8 * k + 5]};
+        const df dot = df_dot3(c0, vx, c1, vy, c2, vz);
+        const df n2 = df_sub(df{pj[8 * k + 6], pj[8 * k + 7]}, df_mul(dot, dot));
+        if (n2.h > best.h || (n2.h == best.h && n2.l > best.l)) best = n2;
     }
-    const float s = __fadd_ru(__fmaf_ru(sqrta(best), 1.f + 4.f * U, 8.f * U * Jd[12]), Jd[13]);
+    float lh = 0.f, ll = 0.f;
+    if (best.h > 0.f) {
+        const float r = sqrta(best.h);
+        const df rr = two_prod(r, r);
+        const float e = (((best.h - rr.h) - rr.l) + best.l) * (0.5f * rcpa(r));  // best.h - rr.h is exact
+        const df lin = fast_two_sum(r, e);
+        lh = lin.h;
+        ll = lin.l;
+    }
+    const float s = __fadd_ru(lh, __fadd_ru(ll, __fadd_ru(pj[32], pj[33])));
     if (s < Sr) {
         Sr = s;
-        Cr = sqrta(fmaxf(fmaf(-s, s, 1.f), 0.f)) * (1.f - 3.f * U);
+        // cos(psi_r / 2) = sqrt(1 - s^2): 1 - s^2 as an exact double-float but
+        // for one rounding of its tail (below u^2 / 2)
+        const df p = two_prod(s, s);
+        const df t = two_sum(1.f, -p.h);
+        const df w = two_sum(t.h, t.l - p.l);
+        float c = 0.f;
+        if (w.h > 0.00390625f) {  // 1/256: cos(psi_r / 2) above 1/16
+            const float r = sqrta(w.h);
+            const df rr = two_prod(r, r);
+            const float e = (((w.h - rr.h) - rr.l) + w.l) * (0.5f * rcpa(r));
+            c = __fadd_rd(r, __fmaf_rd(-64.f * U2, r, e));
+        }
+        Cr = c;
     }
 }
 
@@ -236,53 +288,6 @@ struct RowCross {
     float a, b, k0, Cs, Ss, esS, A4;
 };
 
-// One cross pair (i, j): adds to pl the upper bound of the pair's term over
-// the cube (Theorem 1, Eq. K1i2j_ub with B of Eq. K1i2j_ub_B) and to pc the
-// term at the centre (Lemma 1), both without the row multipliers.
-__device__ __forceinline__ void cross_pair(const RowCross &R, float4 J1, float4 J2, float &pl, float &pc) {
-    const float U = GOSMA_U;
-    const float k2 = J1.w, Q = J2.w;
-    float dx = (R.vx - J1.x) + (R.wx - J2.x), dy = (R.vy - J1.y) + (R.wy - J2.y), dz = (R.vz - J1.z) + (R.wz - J2.z);
-    float px = (R.vx + J1.x) + (R.wx + J2.x), py = (R.vy + J1.y) + (R.wy + J2.y), pz = (R.vz + J1.z) + (R.wz + J2.z);
-    float x2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));  // |v - u|^2 = 4 sin^2(theta/2)
-    float y2 = fmaf(px, px, fmaf(py, py, pz * pz));  // |v + u|^2 = 4 cos^2(theta/2)
-    // centre: kappa_1i(t0) = k0, angle theta
-    float kk = R.k0 * k2;
-    float dk0 = R.k0 - k2;
-    float K0 = sqrta(fmaf(dk0, dk0, kk * y2));
-    float den0 = (R.k0 + k2) + K0;
-    float K0c = fmaxf(K0, 1e-20f);
-    float r0 = rcpa(den0 * K0c);
-    float w0 = den0 * r0;  // 1/K0, times g(K0) below (g(K)/K -> 2 as K -> 0)
-    if (K0 < 9.f) w0 = K0 < 1e-3f ? 2.f - 2.f * K0 : gZ(K0) * w0;
-    pc = fmaf(ex2a(kk * x2 * (K0c * r0) * (-GOSMA_LOG2E)), w0 * Q, pc);
-    // bound: B = max(0, theta - s), s = psi_t,i + psi_r (Cs, Ss = cos, sin of s/2)
-    float sth = 0.5f * sqrta(x2), cth = 0.5f * sqrta(y2);
-    float sB = fmaf(sth, R.Cs, -cth * R.Ss);
-    float es = fmaf(7.5f * U, sth, R.esS);
-    float slo = fmaxf(sB - es, 0.f);
-    float shi = fminf(fmaxf(sB, 0.f) + es, 1.f);
-    // cos(B/2) from the sine bounds: sqrt(1 - s^2), one rounding of 1 - s^2, sqrt 2u
-    float chi = fminf(sqrta(fmaf(-slo, slo, 1.f)) * (1.f + 3.f * U), 1.f);
-    float clo = sqrta(fmaxf(fmaf(-shi, shi, 1.f), 0.f)) * (1.f - 3.f * U);
-    // K(a) - a - k2: an upper bound uses the smallest sin and the largest K
-    float ak4 = R.A4 * k2;
-    float dka = R.a - k2;
-    float Khi = sqrta(fmaf(dka, dka, ak4 * (chi * chi))) * (1.f + 4.f * U);
-    // smallest K over kappa_1 in [a, b] (minimiser -k2 cos B, clamped), from below
-    float cosBlo = fmaf(2.f * clo, clo, -1.f);
-    float ks = fminf(fmaxf(-k2 * cosBlo, R.a), R.b);
-    float dks = ks - k2;
-    float Kmin = sqrta(fmaf(dks, dks, 4.f * ks * k2 * (clo * clo))) * (1.f - 4.f * U);
-    float den = (R.a + k2) + Khi;
-    float Kc = fmaxf(Kmin, 1e-20f);
-    float r = rcpa(den * Kc);
-    float DL = ak4 * (slo * slo) * (Kc * r) * (-GOSMA_LOG2E);
-    // g(K)/K <= min(1/K, 2): an upper bound without evaluating g
-    float w = fminf(den * r, 2.f);
-    pl = fmaf(ex2a(fmaf(12.f * U, fabsf(DL), DL + GOSMA_TERM_SLACK)), w * Q, pl);
-}
-
 // The row constants of RowCross in both lanes of packed pairs, for
 // cross_pair2.  nSs = -Ss (negation is exact).
 struct RowCross2 {
@@ -297,19 +302,28 @@ __device__ __forceinline__ float2 sqrt2a(float2 x) { return make_float2(sqrta(x.
 __device__ __forceinline__ float2 rcp2a(float2 x) { return make_float2(rcpa(x.x), rcpa(x.y)); }
 __device__ __forceinline__ float2 ex2_2a(float2 x) { return make_float2(ex2a(x.x), ex2a(x.y)); }
 
-// Two cross pairs (i, j) and (i, j') at once, lane x for column j (records
-// J1a, J2a) and lane y for j' (J1b, J2b): lane by lane the operations and
-// roundings of cross_pair, on packed pairs (the error budget above holds per
-// lane).  Rewritings that change no bit: 1 - s^2 is taken as -(s^2 - 1)
-// (round to nearest is symmetric), -k2 cos B as -(k2 cos B), 4 ks k2 as
-// ks (4 k2)... (scaling by 4 is exact), and 12u |DL| as -12u DL (DL <= 0: a
-// product of non-negative factors and -log2 e).
-__device__ __forceinline__ void cross_pair2(const RowCross2 &R, float4 J1a, float4 J2a, float4 J1b, float4 J2b,
+// Two cross pairs (i, j) and (i, j') at once, lane x for column j and lane y
+// for j' (their JP records P0 .. P3): adds to pl the upper bound of each
+// pair's term over the cube (Theorem 1, Eq. K1i2j_ub with B of Eq.
+// K1i2j_ub_B) and to pc the term at the centre (Lemma 1), both without the
+// row multipliers.  Every operation is per lane, rounded to nearest as a
+// scalar FP32 operation would be (the error budget above holds per lane).
+//   |v -+ u|^2 from double-float directions, the centre term in the linear
+//   form above, then the bound: B = max(0, theta - s), s = psi_t,i + psi_r
+//   (Cs, Ss = cos, sin of s/2); cos(B/2) from the sine bounds as
+//   sqrt(1 - s^2) (one rounding of 1 - s^2, sqrt 2u); K(a) - a - k2 with the
+//   smallest sine and the largest K; the smallest K over kappa_1 in [a, b]
+//   (minimiser -k2 cos B, clamped), from below; g(K)/K <= min(1/K, 2).
+// Forms chosen for the packed instructions, exact rewritings: 1 - s^2 is
+// taken as -(s^2 - 1) (rounding to nearest is symmetric), -k2 cos B as
+// -(k2 cos B), and 12u |DL| as -12u DL (DL <= 0: a product of non-negative
+// factors and -log2 e).
+__device__ __forceinline__ void cross_pair2(const RowCross2 &R, float4 P0, float4 P1, float4 P2, float4 P3,
                                             float2 &pl, float2 &pc) {
     const float U = GOSMA_U;
-    const float2 k2 = make_float2(J1a.w, J1b.w), Q = make_float2(J2a.w, J2b.w);
-    const float2 ux = make_float2(J1a.x, J1b.x), uy = make_float2(J1a.y, J1b.y), uz = make_float2(J1a.z, J1b.z);
-    const float2 lx = make_float2(J2a.x, J2b.x), ly = make_float2(J2a.y, J2b.y), lz = make_float2(J2a.z, J2b.z);
+    const float2 k2 = make_float2(P1.z, P1.w), Q = make_float2(P3.z, P3.w);
+    const float2 ux = make_float2(P0.x, P0.y), uy = make_float2(P0.z, P0.w), uz = make_float2(P1.x, P1.y);
+    const float2 lx = make_float2(P2.x, P2.y), ly = make_float2(P2.z, P2.w), lz = make_float2(P3.x, P3.y);
     const float2 dx = add2(sub2(R.vx, ux), sub2(R.wx, lx)), dy = add2(sub2(R.vy, uy), sub2(R.wy, ly)),
                  dz = add2(sub2(R.vz, uz), sub2(R.wz, lz));
     const float2 px = add2(add2(R.vx, ux), add2(R.wx, lx)), py = add2(add2(R.vy, uy), add2(R.wy, ly)),
@@ -360,63 +374,6 @@ struct RowSelf {
     float a, b, k0, cp, sp;
 };
 
-// One self pair (i, m), i != m: adds to pl the lower bound of the pair's term
-// over the cuboid (Theorem 1, Eq. K1i1j_lb with A of Eq. K1i1j_lb_A) and to pc
-// the centre term, both without the row multipliers.
-__device__ __forceinline__ void self_pair(const RowSelf &R, float4 M1, float4 M2, float4 M3, float Um, float &pl,
-                                          float &pc) {
-    const float U = GOSMA_U;
-    const float am = M1.w, bm = M2.w, k0m = M3.x, cpm = M3.y, spm = M3.z, Am = M3.w;
-    float dx = (R.vx - M1.x) + (R.wx - M2.x), dy = (R.vy - M1.y) + (R.wy - M2.y), dz = (R.vz - M1.z) + (R.wz - M2.z);
-    float px = (R.vx + M1.x) + (R.wx + M2.x), py = (R.vy + M1.y) + (R.wy + M2.y), pz = (R.vz + M1.z) + (R.wz + M2.z);
-    float x2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    float y2 = fmaf(px, px, fmaf(py, py, pz * pz));
-    // centre
-    float kk = R.k0 * k0m;
-    float dk0 = R.k0 - k0m;
-    float K0 = sqrta(fmaf(dk0, dk0, kk * y2));
-    float den0 = (R.k0 + k0m) + K0;
-    float K0c = fmaxf(K0, 1e-20f);
-    float r0 = rcpa(den0 * K0c);
-    float w0 = den0 * r0;
-    if (K0 < 9.f) w0 = K0 < 1e-3f ? 2.f - 2.f * K0 : gZ(K0) * w0;
-    pc = fmaf(ex2a(kk * x2 * (K0c * r0) * (-GOSMA_LOG2E)), w0 * Um, pc);
-    // bound: A = min(pi, theta + psi_i + psi_m); the half-angle pair of
-    // (psi_i + psi_m)/2 is formed here in FP32 (2u each): sin(A/2) carries
-    // <= 9.5u (sin(theta/2) + sin(psi/2)), cos(A/2) <= 14u
-    float sth = 0.5f * sqrta(x2), cth = 0.5f * sqrta(y2);
-    float C = fmaf(R.cp, cpm, -R.sp * spm);  // cos((psi_i + psi_m)/2)
-    float S = fmaf(R.sp, cpm, R.cp * spm);   // sin((psi_i + psi_m)/2)
-    float cA = fmaf(cth, C, -sth * S);       // cos(A/2) before the clamp at pi
-    float sA = fmaf(sth, C, cth * S);
-    float es = 10.f * U * (sth + fabsf(S));
-    bool api = cA <= 16.f * U;               // A may reach pi
-    float shi = api ? 1.f : fminf(sA + es, 1.f);
-    float slo = fmaxf(sA - es, 0.f);
-    // cos(A/2) from the sine bounds (A/2 <= pi/2), as in the cross pair
-    float clo = sqrta(fmaxf(fmaf(-shi, shi, 1.f), 0.f)) * (1.f - 3.f * U);
-    float chi = fminf(sqrta(fmaf(-slo, slo, 1.f)) * (1.f + 3.f * U), 1.f);
-    // K(b_i, b_m) - b_i - b_m: a lower bound uses the largest sin and the smallest K
-    float bb = R.b * bm;
-    float dbb = R.b - bm;
-    float Klo = sqrta(fmaf(dbb, dbb, 4.f * bb * (clo * clo))) * (1.f - 4.f * U);
-    // largest K over the four corners of [a_i, b_i] x [a_m, b_m], from above
-    float c4 = 4.f * (chi * chi);
-    float q1 = R.a - am, q2 = R.a - bm, q3 = R.b - am;
-    float e1 = fmaf(q1, q1, c4 * R.a * am);
-    float e2 = fmaf(q2, q2, c4 * R.a * bm);
-    float e3 = fmaf(q3, q3, c4 * R.b * am);
-    float e4 = fmaf(dbb, dbb, c4 * bb);
-    float Kmax = sqrta(fmaxf(fmaxf(e1, e2), fmaxf(e3, e4))) * (1.f + 5.f * U);
-    float den = (R.b + bm) + Klo;
-    float r = rcpa(den * Kmax);
-    float DL = bb * (shi * shi) * (Kmax * r) * (-4.f * GOSMA_LOG2E);
-    // g(K)/K from below: g(K)/K >= 2 - 2K for small K; g rounded with <= 64u error otherwise
-    float w = den * r;
-    if (Kmax < 9.f) w = Kmax < 0.25f ? fmaxf(2.f - 2.f * Kmax, 0.f) : gZ(Kmax) * w * (1.f - 64.f * U);
-    pl = fmaf(ex2a(DL - fmaf(12.f * U, fabsf(DL), GOSMA_TERM_SLACK)), w * Am, pl);
-}
-
 // The row constants of RowSelf in both lanes of packed pairs, for self_pair2.
 struct RowSelf2 {
     float2 vx, vy, vz, wx, wy, wz;
@@ -426,20 +383,28 @@ struct RowSelf2 {
           b(bc2(R.b)), k0(bc2(R.k0)), cp(bc2(R.cp)), sp(bc2(R.sp)), nsp(bc2(-R.sp)) {}
 };
 
-// Two self pairs (i, m) and (i, m') at once (lane x: partner records M1a,
-// M2a, M3a, Uma; lane y: M1b, ...): lane by lane the operations and roundings
-// of self_pair.  Besides the rewritings of cross_pair2, -sin((psi_i+psi_m)/2)
-// is formed as 0 - S (exact; S >= 0, a sum of products of non-negative
-// half-angle sines and cosines, so |S| = S), and 12u |DL| + slack as
-// -12u DL + slack (DL <= 0).
-__device__ __forceinline__ void self_pair2(const RowSelf2 &R, float4 M1a, float4 M2a, float4 M3a, float Uma,
-                                           float4 M1b, float4 M2b, float4 M3b, float Umb, float2 &pl, float2 &pc) {
+// Two self pairs (i, m) and (i, m') at once, lane x for partner m and lane y
+// for m' (their MP records P0 .. P5 and UP record Um): adds to pl the lower
+// bound of each pair's term over the cuboid (Theorem 1, Eq. K1i1j_lb with A
+// of Eq. K1i1j_lb_A) and to pc the centre term, both without the row
+// multipliers; per lane as a scalar FP32 evaluation would round.
+//   The bound: A = min(pi, theta + psi_i + psi_m), the half-angle pair of
+//   (psi_i + psi_m)/2 formed here in FP32 (2u each): sin(A/2) carries
+//   <= 9.5u (sin(theta/2) + sin(psi/2)), cos(A/2) <= 14u; cos(A/2) from the
+//   sine bounds (A/2 <= pi/2); K(b_i, b_m) - b_i - b_m with the largest sine
+//   and the smallest K; the largest K over the four corners of
+//   [a_i, b_i] x [a_m, b_m], from above; g(K)/K from below: >= 2 - 2K for
+//   small K, g rounded with <= 64u error otherwise.
+// Besides the rewritings of cross_pair2, -sin((psi_i+psi_m)/2) is formed as
+// 0 - S (exact; S >= 0, a sum of products of non-negative half-angle sines
+// and cosines, so |S| = S).
+__device__ __forceinline__ void self_pair2(const RowSelf2 &R, float4 P0, float4 P1, float4 P2, float4 P3, float4 P4,
+                                           float4 P5, float2 Um, float2 &pl, float2 &pc) {
     const float U = GOSMA_U;
-    const float2 am = make_float2(M1a.w, M1b.w), bm = make_float2(M2a.w, M2b.w), k0m = make_float2(M3a.x, M3b.x),
-                 cpm = make_float2(M3a.y, M3b.y), spm = make_float2(M3a.z, M3b.z), Am = make_float2(M3a.w, M3b.w),
-                 Um = make_float2(Uma, Umb);
-    const float2 ux = make_float2(M1a.x, M1b.x), uy = make_float2(M1a.y, M1b.y), uz = make_float2(M1a.z, M1b.z);
-    const float2 lx = make_float2(M2a.x, M2b.x), ly = make_float2(M2a.y, M2b.y), lz = make_float2(M2a.z, M2b.z);
+    const float2 am = make_float2(P1.z, P1.w), bm = make_float2(P3.z, P3.w), k0m = make_float2(P4.x, P4.y),
+                 cpm = make_float2(P4.z, P4.w), spm = make_float2(P5.x, P5.y), Am = make_float2(P5.z, P5.w);
+    const float2 ux = make_float2(P0.x, P0.y), uy = make_float2(P0.z, P0.w), uz = make_float2(P1.x, P1.y);
+    const float2 lx = make_float2(P2.x, P2.y), ly = make_float2(P2.z, P2.w), lz = make_float2(P3.x, P3.y);
     const float2 dx = add2(sub2(R.vx, ux), sub2(R.wx, lx)), dy = add2(sub2(R.vy, uy), sub2(R.wy, ly)),
                  dz = add2(sub2(R.vz, uz), sub2(R.wz, lz));
     const float2 px = add2(add2(R.vx, ux), add2(R.wx, lx)), py = add2(add2(R.vy, uy), add2(R.wy, ly)),
@@ -557,16 +522,25 @@ __device__ void cube_bounds(const MixDev &mx, const CubePrep &prep, df zeta2, bo
     __syncthreads();
 
     // ---------------- phase 1a: image columns u_j = R_r0^T mu_2j (double-float)
-    for (int j = tid; j < n2; j += BLOCK) {
-        df m0 = {mx.mu2h[3 * j], mx.mu2l[3 * j]}, m1 = {mx.mu2h[3 * j + 1], mx.mu2l[3 * j + 1]},
-           m2 = {mx.mu2h[3 * j + 2], mx.mu2l[3 * j + 2]};
+    // (an odd count gets a copy of the last column with zero weight as the
+    // partner of the last pair)
+    for (int j = tid; j < n2 + (n2 & 1); j += BLOCK) {
+        const int jj = j < n2 ? j : n2 - 1;
+        df m0 = {mx.mu2h[3 * jj], mx.mu2l[3 * jj]}, m1 = {mx.mu2h[3 * jj + 1], mx.mu2l[3 * jj + 1]},
+           m2 = {mx.mu2h[3 * jj + 2], mx.mu2l[3 * jj + 2]};
         df u[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c)
             u[c] = df_dot3({cs.rot.Rh[c], cs.rot.Rl[c]}, m0, {cs.rot.Rh[3 + c], cs.rot.Rl[3 + c]}, m1,
                            {cs.rot.Rh[6 + c], cs.rot.Rl[6 + c]}, m2);
-        sm.J1[j] = make_float4(u[0].h, u[1].h, u[2].h, mx.kappa2[j]);
-        sm.J2[j] = make_float4(u[0].l, u[1].l, u[2].l, mx.Q2[j]);
+        jp_at(sm, j, JP_UX) = u[0].h;
+        jp_at(sm, j, JP_UY) = u[1].h;
+        jp_at(sm, j, JP_UZ) = u[2].h;
+        jp_at(sm, j, JP_K2) = mx.kappa2[jj];
+        jp_at(sm, j, JP_LX) = u[0].l;
+        jp_at(sm, j, JP_LY) = u[1].l;
+        jp_at(sm, j, JP_LZ) = u[2].l;
+        jp_at(sm, j, JP_Q) = j < n2 ? mx.Q2[jj] : 0.f;
     }
 
     // ---------------- phase 1b: model rows (double-float geometry)
@@ -667,10 +641,23 @@ __device__ void cube_bounds(const MixDev &mx, const CubePrep &prep, df zeta2, bo
         // phi_i a_i / g(a_i) from below, phi_i k0_i / g(k0_i)
         float Aw = a < 9.f ? ph * a * rcpa(gZ(a)) * (1.f - 12.f * U) : __fmul_rd(ph * a, 1.f - 3.f * U);
         float Uw = k0 < 9.f ? ph * k0 * rcpa(gZ(k0)) : ph * k0;
-        sm.M1[i] = make_float4(v[0].h, v[1].h, v[2].h, a);
-        sm.M2[i] = make_float4(v[0].l, v[1].l, v[2].l, b);
-        sm.M3[i] = make_float4(k0, cps, sps, Aw);
-        sm.Uw[i] = Uw;
+        // the row's record, and for the last row of an odd count also its copy with
+        // zero weights (the partner of the last pair)
+        for (int r = i; r <= (i == n1 - 1 && (n1 & 1) ? n1 : i); ++r) {
+            mp_at(sm, r, MP_VX) = v[0].h;
+            mp_at(sm, r, MP_VY) = v[1].h;
+            mp_at(sm, r, MP_VZ) = v[2].h;
+            mp_at(sm, r, MP_A) = a;
+            mp_at(sm, r, MP_LX) = v[0].l;
+            mp_at(sm, r, MP_LY) = v[1].l;
+            mp_at(sm, r, MP_LZ) = v[2].l;
+            mp_at(sm, r, MP_B) = b;
+            mp_at(sm, r, MP_K0) = k0;
+            mp_at(sm, r, MP_CP) = cps;
+            mp_at(sm, r, MP_SP) = sps;
+            mp_at(sm, r, MP_AW) = r == i ? Aw : 0.f;
+            up_at(sm, r) = r == i ? Uw : 0.f;
+        }
         // diagonal self term phi_i^2 k coth(k) / 2, smallest over [a_i, b_i] at a_i
         dsl.add(ph * ph * half_kcothk(a) * (1.f - 16.f * U));
         dsu.add(ph * ph * half_kcothk(k0));
@@ -691,19 +678,18 @@ __device__ void cube_bounds(const MixDev &mx, const CubePrep &prep, df zeta2, bo
             // point-dependent form of Lemma 2 when the mixtures ask for it
             float Cr = cs.rot.Cr, Sr = cs.rot.Sr;
             RowCross R;
-            const float4 m1 = sm.M1[i], m2 = sm.M2[i], m3 = sm.M3[i];
-            R.vx = m1.x;
-            R.vy = m1.y;
-            R.vz = m1.z;
-            R.wx = m2.x;
-            R.wy = m2.y;
-            R.wz = m2.z;
-            R.a = m1.w;
-            R.b = m2.w;
-            R.k0 = m3.x;
+            R.vx = mp_at(sm, i, MP_VX);
+            R.vy = mp_at(sm, i, MP_VY);
+            R.vz = mp_at(sm, i, MP_VZ);
+            R.wx = mp_at(sm, i, MP_LX);
+            R.wy = mp_at(sm, i, MP_LY);
+            R.wz = mp_at(sm, i, MP_LZ);
+            R.a = mp_at(sm, i, MP_A);
+            R.b = mp_at(sm, i, MP_B);
+            R.k0 = mp_at(sm, i, MP_K0);
             R.A4 = 4.f * R.a;
-            if (mx.psi_point) point_psi_r(cs.rot, m1.x, m1.y, m1.z, Cr, Sr);
-            float cps = m3.y, sps = m3.z;
+            if (mx.psi_point) point_psi_r(cs.rot, df{R.vx, R.wx}, df{R.vy, R.wy}, df{R.vz, R.wz}, Cr, Sr);
+            const float cps = mp_at(sm, i, MP_CP), sps = mp_at(sm, i, MP_SP);
             // s = psi_t,i + psi_r as half-angle cosine/sine (double-float, rounded once);
             // s >= pi means B = 0 everywhere
             df cc = two_prod(cps, Cr), ssp = two_prod(sps, Sr), sc = two_prod(sps, Cr), cs2 = two_prod(cps, Sr);
@@ -721,16 +707,22 @@ __device__ void cube_bounds(const MixDev &mx, const CubePrep &prep, df zeta2, bo
             Acc cl, cu;
             cl.zero();
             cu.zero();
-            // columns in packed pairs (j, j + 1), pair p of the row to thread p mod Tj;
-            // each lane keeps its own FP32 chunk sum of at most CHUNK terms
+            // the row's columns [j0, j1) in stored pairs p0 .. p1 - 1, pair p to thread
+            // p mod Tj; each lane keeps its own FP32 chunk sum of at most CHUNK terms.
+            // A pair with a column outside the range (before j0 when j0 is odd, at j1
+            // when j1 is odd) runs with that column's weight Q set to zero.
             const RowCross2 R2(R);
             float2 pl = make_float2(0.f, 0.f), pc = make_float2(0.f, 0.f);
             int cnt = 0;
-            const int j1 = mx.rj1 ? mx.rj1[i] : n2;
-            int j = (mx.rj0 ? mx.rj0[i] : 0) + 2 * tj;
-#pragma unroll 1
-            for (; j + 1 < j1; j += 2 * Tj) {
-                cross_pair2(R2, sm.J1[j], sm.J2[j], sm.J1[j + 1], sm.J2[j + 1], pl, pc);
+            const int j0 = mx.rj0 ? mx.rj0[i] : 0, j1 = mx.rj1 ? mx.rj1[i] : n2;
+            const int p0 = j0 >> 1, p1 = (j1 + 1) >> 1;
+            const int pa = (j0 & 1) ? p0 : -1, pb = (j1 & 1) ? p1 - 1 : -1;
+            auto step = [&](int q, bool ma, bool mb) {
+                const float4 A = sm.JP[4 * q], B = sm.JP[4 * q + 1], C = sm.JP[4 * q + 2];
+                float4 D = sm.JP[4 * q + 3];
+                if (ma) D.z = 0.f;
+                if (mb) D.w = 0.f;
+                cross_pair2(R2, A, B, C, D, pl, pc);
                 if (++cnt == CHUNK) {
                     cl.add(pl.x);
                     cl.add(pl.y);
@@ -739,14 +731,22 @@ __device__ void cube_bounds(const MixDev &mx, const CubePrep &prep, df zeta2, bo
                     pl = pc = make_float2(0.f, 0.f);
                     cnt = 0;
                 }
+            };
+            int q = p0 + tj;
+            if (q == pa) {
+                step(q, true, q == pb);
+                q += Tj;
             }
-            if (j < j1) cross_pair(R, sm.J1[j], sm.J2[j], pl.x, pc.x);  // odd last column
+            const int qend = pb >= 0 ? pb : p1;
+#pragma unroll 1
+            for (; q < qend; q += Tj) step(q, false, false);
+            if (q == pb) step(q, false, true);
             cl.add(pl.x);
             cl.add(pl.y);
             cu.add(pc.x);
             cu.add(pc.y);
             T[1] = df_add(T[1], df_scale(cl.s, cl.c, Bw));
-            T[3] = df_add(T[3], df_scale(cu.s, cu.c, sm.Uw[i]));
+            T[3] = df_add(T[3], df_scale(cu.s, cu.c, up_at(sm, i)));
         }
         // ---------------- phase 2b: self pairs i < m, rows paired (p, n1-2-p) for balance
         if (need_self && n1 > 1) {
@@ -759,31 +759,37 @@ __device__ void cube_bounds(const MixDev &mx, const CubePrep &prep, df zeta2, bo
                     int i = h == 0 ? pp : n1 - 2 - pp;
                     if (h == 1 && i == pp) break;
                     RowSelf R;
-                    const float4 m1 = sm.M1[i], m2 = sm.M2[i], m3 = sm.M3[i];
-                    R.vx = m1.x;
-                    R.vy = m1.y;
-                    R.vz = m1.z;
-                    R.wx = m2.x;
-                    R.wy = m2.y;
-                    R.wz = m2.z;
-                    R.a = m1.w;
-                    R.b = m2.w;
-                    R.k0 = m3.x;
-                    R.cp = m3.y;
-                    R.sp = m3.z;
+                    R.vx = mp_at(sm, i, MP_VX);
+                    R.vy = mp_at(sm, i, MP_VY);
+                    R.vz = mp_at(sm, i, MP_VZ);
+                    R.wx = mp_at(sm, i, MP_LX);
+                    R.wy = mp_at(sm, i, MP_LY);
+                    R.wz = mp_at(sm, i, MP_LZ);
+                    R.a = mp_at(sm, i, MP_A);
+                    R.b = mp_at(sm, i, MP_B);
+                    R.k0 = mp_at(sm, i, MP_K0);
+                    R.cp = mp_at(sm, i, MP_CP);
+                    R.sp = mp_at(sm, i, MP_SP);
                     Acc sl, su;
                     sl.zero();
                     su.zero();
-                    // partners in packed pairs (m, m + 1), as the columns above
+                    // partners m in [i + 1, mend) in stored pairs, as the columns above; a
+                    // pair holding row i itself (i even) or a row at mend (mend odd) runs
+                    // with that row's weights Aw and Uw set to zero
                     const RowSelf2 R2(R);
                     float2 pl = make_float2(0.f, 0.f), pc = make_float2(0.f, 0.f);
                     int cnt = 0;
                     const int mend = mx.rm1 ? mx.rm1[i] : n1;
-                    int m = i + 1 + 2 * sj;
-#pragma unroll 1
-                    for (; m + 1 < mend; m += 2 * Sj) {
-                        self_pair2(R2, sm.M1[m], sm.M2[m], sm.M3[m], sm.Uw[m], sm.M1[m + 1], sm.M2[m + 1],
-                                   sm.M3[m + 1], sm.Uw[m + 1], pl, pc);
+                    const int q0 = (i + 1) >> 1, q1 = (mend + 1) >> 1;
+                    const int qa = ((i + 1) & 1) ? q0 : -1, qb = (mend & 1) ? q1 - 1 : -1;
+                    auto step = [&](int q, bool ma, bool mb) {
+                        const float4 *P = sm.MP + 6 * q;
+                        const float4 A = P[0], B = P[1], C = P[2], D = P[3], E = P[4];
+                        float4 F = P[5];
+                        float2 Um = sm.UP[q];
+                        if (ma) F.z = Um.x = 0.f;
+                        if (mb) F.w = Um.y = 0.f;
+                        self_pair2(R2, A, B, C, D, E, F, Um, pl, pc);
                         if (++cnt == CHUNK) {
                             sl.add(pl.x);
                             sl.add(pl.y);
@@ -792,16 +798,24 @@ __device__ void cube_bounds(const MixDev &mx, const CubePrep &prep, df zeta2, bo
                             pl = pc = make_float2(0.f, 0.f);
                             cnt = 0;
                         }
+                    };
+                    int q = q0 + sj;
+                    if (q == qa) {
+                        step(q, true, q == qb);
+                        q += Sj;
                     }
-                    if (m < mend) self_pair(R, sm.M1[m], sm.M2[m], sm.M3[m], sm.Uw[m], pl.x, pc.x);  // odd last partner
+                    const int qend = qb >= 0 ? qb : q1;
+#pragma unroll 1
+                    for (; q < qend; q += Sj) step(q, false, false);
+                    if (q == qb) step(q, false, true);
                     sl.add(pl.x);
                     sl.add(pl.y);
                     su.add(pc.x);
                     su.add(pc.y);
                     // both orders (i, m) and (m, i): factor 2, exact
-                    float Awi = __fmul_rd(2.f * m3.w, 1.f - (float)(CHUNK + 3) * U);
+                    float Awi = __fmul_rd(2.f * mp_at(sm, i, MP_AW), 1.f - (float)(CHUNK + 3) * U);
                     T[0] = df_add(T[0], df_scale(sl.s, sl.c, Awi));
-                    T[2] = df_add(T[2], df_scale(su.s, su.c, 2.f * sm.Uw[i]));
+                    T[2] = df_add(T[2], df_scale(su.s, su.c, 2.f * up_at(sm, i)));
                 }
             }
         }

@@ -102,6 +102,7 @@ SIGNATURES = {
     "gosma_bnb_load": (C.c_int, [C.c_void_p, C.c_char_p]),
     "gosma_selftest_approx": (C.c_int, [C.c_void_p, D, D]),
     "gosma_selftest_wait_timeout": (C.c_int, [C.c_void_p, C.c_double]),
+    "gosma_selftest_pipe_rates": (C.c_int, [C.c_void_p, D, D]),
     "gosma_debug_fail_allocations": (C.c_int, [C.c_void_p, C.c_int]),
     "gosma_kernel_launches": (C.c_longlong, [C.c_void_p]),
     "gosma_mlp_set_params": (C.c_int, [C.c_void_p, FP]),
@@ -555,6 +556,13 @@ class Gosma:
 
     def kernel_launches(self):
         return int(self.L.gosma_kernel_launches(self.h))
+
+    def selftest_pipe_rates(self):
+        """Measured lane operations per SM per clock: dict(ffma, ffma2, ex2, sqrt, rcp, clock_mhz)."""
+        r = np.zeros(5)
+        mhz = C.c_double()
+        self._check(self.L.gosma_selftest_pipe_rates(self.h, _p(r), C.byref(mhz)), "selftest_pipe_rates")
+        return dict(zip(("ffma", "ffma2", "ex2", "sqrt", "rcp"), r.tolist()), clock_mhz=mhz.value)
 
     def selftest_wait_timeout(self, limit_seconds=0.05):
         """Returns the library's return code (GOSMA_ETIMEOUT when the bounded wait gave up)."""

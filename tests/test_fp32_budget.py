@@ -3,7 +3,7 @@
 On the device the pair terms of Theorem 1 run in FP32 with the approximate
 ex2 / rcp / sqrt instructions, and a slack is meant to keep every cross
 upper bound at or above, and every self lower bound at or below, the exact
-value (cross_pair and self_pair in csrc/bounds_core.cuh, whose header states
+value (cross_pair2 and self_pair2 in csrc/bounds_core.cuh, per lane; the header states
 the budget).  This test replays the bound part of those two functions in
 numpy float32, operation by operation: plain operations rounded to nearest,
 the fused multiply-adds the source writes rounded once, and every
@@ -459,12 +459,85 @@ def test_psi_t_rounded_outward(oracle_mod):
     assert (psi >= np.pi).sum() > 300 and (psi < 1e-3).sum() > 300 and ((psi > 0.5) & (psi < np.pi)).sum() > 300
 
 
-def _point_psi_r_device(r0, h, v, sq, allow=True):
-    """sin(psi_r / 2) of one model direction as the kernel forms it
+def _f(x):
+    return np.float32(x)
+
+
+def _fma1(a, b, c):
+    """Scalar fmaf: the exact product plus c, rounded once (through FP64)."""
+    return np.float32(np.float64(a) * np.float64(b) + np.float64(c))
+
+
+def _two_sum(a, b):
+    s_ = _f(a + b)
+    bb = _f(s_ - a)
+    return s_, _f(_f(a - _f(s_ - bb)) + _f(b - bb))
+
+
+def _fast_two_sum(a, b):
+    s_ = _f(a + b)
+    return s_, _f(b - _f(s_ - a))
+
+
+def _two_prod(a, b):
+    p = _f(a * b)
+    return p, _fma1(a, b, -p)
+
+
+def _split(x):
+    h = np.float32(x)
+    return h, np.float32(x - np.float64(h))
+
+
+def _df_dot3(a, b):
+    """dfloat.cuh df_dot3 of double-float 3-vectors a, b (lists of (h, l))."""
+    p = [_two_prod(a[k][0], b[k][0]) for k in range(3)]
+    e = [_fma1(a[k][0], b[k][1], _fma1(a[k][1], b[k][0], p[k][1])) for k in range(3)]
+    s1 = _two_sum(p[0][0], p[1][0])
+    t = _two_sum(s1[0], p[2][0])
+    return _fast_two_sum(t[0], _f(_f(s1[1] + t[1]) + _f(_f(e[0] + e[1]) + e[2])))
+
+
+def _df_mul(a, b):
+    p = _two_prod(a[0], b[0])
+    return _fast_two_sum(p[0], _f(p[1] + _fma1(a[0], b[1], _f(a[1] * b[0]))))
+
+
+def _df_sub(a, b):
+    s_ = _two_sum(a[0], -b[0])
+    return _fast_two_sum(s_[0], _f(s_[1] + _f(a[1] - b[1])))
+
+
+def _up(x):
+    return float(toward(np.array([x]), np.ones(1))[0])
+
+
+def _down(x):
+    return float(toward(np.array([x]), -np.ones(1))[0])
+
+
+def _approx1(exact, sgn, rel):
+    return float(approx(np.array([exact]), sgn, rel)[0])
+
+
+def _newton_sqrt(w, sq, rc):
+    """sqrt of a double-float w by one Newton step from the approximate FP32
+    square root (sq, rc: the ends of the sqrt and rcp error bounds)."""
+    r = _f(_approx1(np.sqrt(np.float64(w[0])), sq, 2 * U))
+    rr = _two_prod(r, r)
+    inv = _f(_approx1(1.0 / np.float64(r), rc, 2 * U))
+    e = _f(_f(_f(_f(w[0] - rr[0]) - rr[1]) + w[1]) * _f(_f(0.5) * inv))
+    return r, e
+
+
+def _point_psi_r_device(r0, h, v, sq, rc):
+    """The per-direction rotation uncertainty as the kernel forms it
     (point_psi_r in csrc/bounds_core.cuh): the pre-pass's FP64 vertex images
-    J_r(r0) d / 2 rounded to float, their largest norm and 3 h^2 / 8 rounded
-    up; FP32 cross products (the fused multiply-adds rounded once), the
-    square root off by sq * 2u, the allowances, and the result rounded up."""
+    J_r(r0) d / 2 and their squared norms split to double-floats, the
+    double-float dot products, squared cross norms and Newton square roots,
+    the approximate sqrt and rcp at the sq and rc ends of their error bounds,
+    and the directed roundings.  Returns (sine, cosine, largest squared cross
+    norm / largest squared image norm)."""
     th2 = float(r0 @ r0)
     th = np.sqrt(th2)
     A = 1 - th2 / 6 if th < 1e-8 else np.sin(th) / th
@@ -473,54 +546,71 @@ def _point_psi_r_device(r0, h, v, sq, allow=True):
     x, y, z = r0
     S = np.array([[0, -z, y], [z, 0, -x], [-y, x, 0]])
     J = np.eye(3) - B * S + Cc * (S @ S)
-    cs, jmax = [], 0.0
+    vd = [_split(c) for c in v]
+    best, cmax, n2max = (_f(0), _f(0)), 0.0, 0.0
     for k in range(4):
         d = np.full(3, h)
         if k:
             d[k - 1] = -h
         c = 0.5 * (J @ d)
-        cs.append(c.astype(np.float32))
-        jmax = max(jmax, np.linalg.norm(c))
-    jm = toward(np.array([jmax]), np.ones(1))[0]
-    s2 = toward(np.array([0.375 * h * h]), np.ones(1))[0]
-    vh = v.astype(np.float32)
-    best = F(0)
-    for c in cs:
-        def fm(a, b, cc):
-            return fma(np.array([a]), np.array([b]), np.array([cc]))[0]
-        cx = fm(c[1], vh[2], -(c[2] * vh[1]))
-        cy = fm(c[2], vh[0], -(c[0] * vh[2]))
-        cz = fm(c[0], vh[1], -(c[1] * vh[0]))
-        best = max(best, fm(cx, cx, fm(cy, cy, cz * cz)))
-    r = sqrta(np.array([best]), sq)[0]
-    if not allow:
-        return float(r) + float(s2)
-    lin = toward(np.array([float(r) * (1 + 4 * U) + 8 * U * float(jm)]), np.ones(1))
-    return float(toward(np.array([float(lin[0]) + float(s2)]), np.ones(1))[0])
+        n2 = float(c @ c)
+        cmax = max(cmax, np.sqrt(n2))
+        dot = _df_dot3([_split(ci) for ci in c], vd)
+        n = _df_sub(_split(n2), _df_mul(dot, dot))
+        n2max = max(n2max, float(n[0]) + float(n[1]))
+        if n[0] > best[0] or (n[0] == best[0] and n[1] > best[1]):
+            best = n
+    ratio = n2max / cmax ** 2
+    lh, ll = _f(0), _f(0)
+    if best[0] > 0:
+        r, e = _newton_sqrt(best, sq, rc)
+        lh, ll = _fast_two_sum(r, e)
+    s2 = _up(0.375 * h * h)
+    al = _up(64.0 * 2.0 ** -48 * cmax)
+    sn = _up(np.float64(lh) + np.float64(_up(np.float64(ll) + np.float64(_up(np.float64(s2) + np.float64(al))))))
+    sf = _f(sn)
+    p = _two_prod(sf, sf)
+    t = _two_sum(_f(1), -p[0])
+    w = _two_sum(t[0], _f(t[1] - p[1]))
+    cs = 0.0
+    if w[0] > 1 / 256:
+        r, e = _newton_sqrt(w, sq, rc)
+        lo = _down(-64.0 * U * U * np.float64(r) + np.float64(e))
+        cs = _down(np.float64(r) + lo)
+    return sn, cs, ratio
 
 
 def test_point_psi_r_rounded_outward(oracle_mod):
     """The per-direction rotation uncertainty of Lemma 2 (reading R16) as the
-    kernel computes it: its half-angle sine is never below the oracle's, with
-    the square root at either end of its error bound, over cubes all over the
-    pi-ball (a third near its surface) from h = 1e-6 to 1; without the
-    allowances, cases fall below."""
+    kernel computes it: its half-angle sine is never below and its cosine
+    never above the oracle's, with the approximate sqrt and rcp at either
+    end of their error bounds, over cubes all over the pi-ball (a third near
+    its surface) from h = 1e-6 to 1; the sine is within 3u of the oracle's
+    (one rounding up is up to 2u just above a power of two: the
+    point-independent sine, rounded up once from FP64, is within 2u), and the
+    largest squared cross
+    norm is at least a quarter of the largest squared image norm (the
+    cancellation the error budget allows)."""
     rng = np.random.default_rng(31)
-    short = 0
-    for k in range(3000):
+    worst = 0.0
+    for k in range(1500):
         h = float(np.exp(rng.uniform(np.log(1e-6), 0)))
         d = rng.standard_normal(3)
         d /= np.linalg.norm(d)
         r0 = d * (rng.uniform(2.6, 3.1) if k % 3 == 0 else rng.uniform(0, 2.6))
         v = rng.standard_normal(3)
         v /= np.linalg.norm(v)
-        ref = np.sin(0.5 * oracle_mod.psi_r_point(r0, h, v))
-        hk = float(toward(np.array([np.sin(0.5 * min(np.sqrt(3) * h, np.pi))]), np.ones(1))[0])
+        psi = oracle_mod.psi_r_point(r0, h, v)
+        hk = min(np.sqrt(3) * h, np.pi)
         for sq in (-1.0, 1.0):
-            dev = min(_point_psi_r_device(r0, h, v, sq), hk)
-            assert dev >= ref * (1 - 1e-15), (k, r0, h, v, dev / ref - 1)
-        short += _point_psi_r_device(r0, h, v, -1.0, allow=False) < ref
-    assert short > 0
+            for rc in (-1.0, 1.0):
+                sn, cs, ratio = _point_psi_r_device(r0, h, v, sq, rc)
+                assert ratio >= 0.25, (k, r0, h, v, ratio)
+                if psi < hk:  # the kernel uses the point-dependent pair only where it is smaller
+                    assert sn >= np.sin(0.5 * psi), (k, r0, h, v, sn / np.sin(0.5 * psi) - 1)
+                    assert cs <= np.cos(0.5 * psi), (k, r0, h, v, cs / np.cos(0.5 * psi) - 1)
+                    worst = max(worst, sn / np.sin(0.5 * psi) - 1)
+    assert worst <= 3 * U, worst / U
 
 
 def _row_cases(oracle_mod, rng, n2):

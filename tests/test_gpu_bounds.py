@@ -27,6 +27,17 @@ def test_approx_instruction_accuracy(ctx):
     assert np.all(measured <= assumed), (measured, assumed)
 
 
+def test_pipe_rates_are_plausible(ctx):
+    """The measured pipe throughputs that the roofline divides by: FP32 FMA at
+    most the 128 lanes per SM per clock of the hardware (within clock
+    measurement noise), packed FMA at least as fast in lanes, MUFU slower."""
+    r = ctx.selftest_pipe_rates()
+    assert 32 <= r["ffma"] <= 140 and r["ffma2"] <= 140 and r["ffma2"] >= 0.9 * r["ffma"], r
+    for k in ("ex2", "sqrt", "rcp"):
+        assert 4 <= r[k] <= r["ffma"], r
+    assert r["clock_mhz"] > 500
+
+
 @pytest.mark.parametrize("seed", [1000, 1001, 1002])
 def test_tiny_parity(ctx, oracle_mod, seed):
     prob = synth.tiny_problem(seed)

@@ -79,3 +79,21 @@ def test_bnb_certificate_against_brute_force(oracle_mod):
     for d in np.linspace(-0.05, 0.05, 11):
         f = oracle_mod.objective_r(mix, res["r"] + d, res["t"])
         assert f >= res["lb"] - 1e-9
+
+
+def test_paper_scale_gap_at_the_true_pose_is_linear_in_the_cell(oracle_mod):
+    """Why the paper-scale workload (128 x 64, eps = 1e-4) does not certify
+    (reading R11): Theorem 1 bounds every pair term separately over the
+    cell, so even a cube centred on the true pose has an upper-lower gap that
+    falls only linearly with its size, about 150 w for half-widths w (in
+    radians and metres): 40 eps C22 at w = 1e-4 and still 4 eps C22 at
+    w = 1e-5, so cells of about 2 micrometres are needed near the optimum."""
+    p = synth.paper_scale_problem(2000)
+    mix = oracle_mod.Mixtures.from_problem(p)
+    epsf = p["eps"] * oracle_mod.c22(mix)
+    gaps = []
+    for w in (1e-4, 1e-5, 1e-6):
+        b = oracle_mod.bounds(mix, np.concatenate([p["r_gt"], [w], p["t_gt"], [w] * 3])[None], p["zeta"])[0]
+        gaps.append(b[1] - b[0])
+    assert gaps[0] > 30 * epsf and gaps[1] > 3 * epsf and gaps[2] < epsf
+    assert gaps[0] / gaps[1] == pytest.approx(10, rel=0.05) and gaps[1] / gaps[2] == pytest.approx(10, rel=0.05)
