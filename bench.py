@@ -421,7 +421,7 @@ def run_ours(args):
     }
     if world == 1 and not args.no_extra:
         ctx.close()
-        line["batched"] = run_batched(args.batch_budget)
+        line["batched"] = run_batched(args.batch_budget, args.batch_queue)
         line["time_to_certified"] = run_time_to_certified(8)
         line["psi_r_point"] = run_psi_r_point(8)
         line["sma"] = run_sma()
@@ -432,27 +432,38 @@ def run_ours(args):
     return 0
 
 
-def run_batched(budget_s):
-    """Config of 256 uneven problems in one batched solve (see module doc)."""
+def run_batched(budget_s, queue=1 << 20, compare_fixed=True):
+    """Config of 256 uneven problems in one batched solve (see module doc):
+    the autotuned bound-kernel shape, and the fixed default shape (128
+    threads, one sub-cube per block) on the same problems and budget."""
     from paper_1812_01232_gb300 import synth
     from paper_1812_01232_gb300.gosma import Gosma
     ctx = Gosma(0)
     probs = synth.uneven_problems(3000, count=256)
-    t0 = time.perf_counter()
-    res = ctx.bnb_solve_batch(probs, eps=1e-3, pop=64, max_seconds=budget_s, queue_capacity=1 << 20)
-    wall = time.perf_counter() - t0
-    dev_s = res[0]["iteration_ms"] / 1e3
-    pairs = float(sum(r["cross_pairs"] for r in res))
-    cert = [r["seconds"] for r in res if r["status_name"] == "optimal"]
-    st = [r["status_name"] for r in res]
+    out = {"workload": "256 problems, n1 ~ U{16..256}, n2 ~ U{8..128}, 20%% outliers, eps 1e-3, pop 64 per problem, "
+                       "queue %d per problem, budget %.0f s" % (queue, budget_s)}
+    for name, shape in (("tuned", None), ("fixed_128x1", (128, 1))) if compare_fixed else (("tuned", None),):
+        t0 = time.perf_counter()
+        res = ctx.bnb_solve_batch(probs, eps=1e-3, pop=64, max_seconds=budget_s, queue_capacity=queue, shape=shape)
+        wall = time.perf_counter() - t0
+        dev_s = res[0]["iteration_ms"] / 1e3
+        pairs = float(sum(r["cross_pairs"] for r in res))
+        cert = [r["seconds"] for r in res if r["status_name"] == "optimal"]
+        st = [r["status_name"] for r in res]
+        row = {"pairs_per_s": pairs / dev_s, "device_s": dev_s, "wall_s": wall,
+               "certified": len(cert), "statuses": {k: st.count(k) for k in sorted(set(st))},
+               "p50_s": float(np.percentile(cert, 50)) if cert else None,
+               "p99_s": float(np.percentile(cert, 99)) if cert else None,
+               "queue_peak_max": int(max(r["queue_peak"] for r in res)),
+               "shape": [res[0]["block_size"], res[0]["cubes_per_block"]], "tunings": res[0]["tunings"]}
+        if name == "tuned":
+            out.update(row)
+        else:
+            out[name] = row
+    if compare_fixed:
+        out["tuned_over_fixed"] = out["pairs_per_s"] / out["fixed_128x1"]["pairs_per_s"]
     ctx.close()
-    return {"workload": "256 problems, n1 ~ U{16..256}, n2 ~ U{8..128}, 20%% outliers, eps 1e-3, pop 64 per problem, "
-                        "queue 2^20 per problem, budget %.0f s" % budget_s,
-            "pairs_per_s": pairs / dev_s, "device_s": dev_s, "wall_s": wall,
-            "certified": len(cert), "statuses": {k: st.count(k) for k in sorted(set(st))},
-            "p50_s": float(np.percentile(cert, 50)) if cert else None,
-            "p99_s": float(np.percentile(cert, 99)) if cert else None,
-            "block_size": res[0]["block_size"]}
+    return out
 
 
 def run_sma():
@@ -586,7 +597,10 @@ def main():
                     help="--impl reference: host-core seconds spread over the warm-up and timed steps")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the batched and time-to-certificate measurements")
-    ap.add_argument("--batch-budget", type=float, default=20.0, help="seconds for the 256-problem batched solve")
+    ap.add_argument("--batch-budget", type=float, default=15.0, help="seconds for each 256-problem batched solve")
+    ap.add_argument("--batch-queue", type=int, default=1 << 20, help="queue capacity per problem of the batched solve")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="print only the batched measurement (one JSON line), autotuned shape only")
     ap.add_argument("--queue-capacity", type=int, default=1 << 27,
                     help="device queue capacity in sub-cubes (64 bytes each, twice)")
     args = ap.parse_args()
@@ -594,6 +608,10 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.batch_only:
+        print(json.dumps({"batched": run_batched(args.batch_budget, args.batch_queue, compare_fixed=False)}),
+              flush=True)
+        return 0
     return run_ours(args)
 
 

@@ -78,6 +78,11 @@ typedef struct {
     int use_sma;         /* run local refinement (SMA, Sec. 5) when a sub-cube improves d* */
     int sma_max_iter;    /* L-BFGS iterations per SMA call (<= 0: 100) */
     long long queue_capacity; /* device queue capacity in cubes (<= 0: library default) */
+    int bound_block;     /* gosma_bnb_solve_batch: threads per block of the bound kernel, and */
+    int bound_cubes;     /* sub-cubes per block (groups of bound_block / bound_cubes threads):
+                            32x1, 64x1, 64x2, 128x1, 128x2, 128x4, 256x1, 256x2, 256x4, 512x1 or
+                            1024x1; both 0 (the default): chosen by the autotuner.  The
+                            single-problem solver ignores them. */
 } gosma_opts;
 
 typedef struct {
@@ -99,7 +104,9 @@ typedef struct {
     double iteration_ms;     /* device time of whole iterations (CUDA events)  */
     long long queue_size;    /* live sub-cubes in the queue                    */
     long long launches;      /* kernels the context has launched so far        */
-    int block_size;          /* threads per cube chosen by the batch autotuner  */
+    int block_size;          /* batched solver: threads per block of the bound kernel  */
+    int cubes_per_block;     /* batched solver: sub-cubes per block of the bound kernel */
+    int tunings;             /* batched solver: times the autotuner timed the shapes     */
 } gosma_result;
 
 /* One independent alignment problem for gosma_bnb_solve_batch: the mixtures
@@ -305,8 +312,15 @@ int gosma_bnb_solve(gosma_ctx *ctx, const gosma_opts *opts, gosma_result *out);
  * Every 8 iterations the host refines each problem whose d* improved with
  * L-BFGS (SMA, Sec. 5) in lock step, all such problems' poses in one FP64
  * launch per step (opts->use_sma, opts->sma_max_iter).  The iteration runs
- * as a captured CUDA graph on a private stream; the bound kernel's block size
- * is picked by timing the candidates (results[k].block_size).
+ * as a captured CUDA graph on a private stream.  The bound kernel's shape
+ * (threads per block, sub-cubes per block) is the caller's
+ * (opts->bound_block, opts->bound_cubes) or picked by an autotuner: each
+ * candidate shape is launched once and then timed three times on the same
+ * children at the fifth iteration, the smallest median wins, and the shapes
+ * are timed again (and the graph captured anew) whenever the number of
+ * unfinished problems has halved since the last tuning; results[k] reports
+ * the final shape and the number of tunings.  The bounds of one sub-cube
+ * differ between shapes only by the order of their FP32 sums.
  * results[k].seconds is the device time from the start to problem k's
  * certificate.  opts->queue_capacity is per problem (default 2^18
  * sub-cubes; two buffers of that size are allocated per problem),
@@ -442,6 +456,37 @@ int gosma_bnb_set_incumbent(gosma_ctx *ctx, double f, const double x[6]);
  * run. */
 int gosma_bnb_last_children(gosma_ctx *ctx, int max_children, gosma_cube *cubes, gosma_bound *bounds, int *count);
 
+/* A queue record of a branch-and-bound run (64 bytes): a sub-cube as cell
+ * coordinates of the run's domain (rotation cube r at level lr of the
+ * circumscribing cube [-pi, pi]^3, translation cuboid t at level lt of the
+ * domain), its Theorem 1 lower bound and the self sums of its cuboid.  Only
+ * meaningful to runs of the same mixtures and domain. */
+typedef struct {
+    double lb;                /* lower bound of f over the sub-cube           */
+    double self_lb, self_c;   /* self sums of the cuboid (valid when flags & 1) */
+    unsigned int r[3], t[3];  /* cell coordinates                              */
+    unsigned short lr, lt;    /* levels (halvings) of the rotation and translation parts */
+    float psit;               /* largest psi_t over the cuboid (split rule)   */
+    unsigned int flags;
+    float ubf;                /* upper bound at the centre (FP32), when known */
+} gosma_node;
+
+/* Move sub-cubes between runs of one problem (Algorithm 1 over several
+ * solvers: their queues together hold the live sub-cubes, so the global
+ * lower bound is the smallest of the runs' lower bounds).  Between
+ * gosma_bnb_step calls:
+ *   gosma_bnb_export drops the queued sub-cubes whose lower bound is not
+ *   below d*, then removes up to max_nodes of the others (the most recently
+ *   queued) from the run and writes them to out (host, max_nodes records);
+ *   *count receives how many.  The run's lower bound is recomputed.
+ *   gosma_bnb_import appends n records (host) to the run's queue (a run that
+ *   had certified, with an empty queue, runs again); GOSMA_EINVAL when a
+ *   record is not one of this library's or the queue would overflow.
+ * Both: GOSMA_ENOTREADY without a run in progress.  The records must come
+ * from a run of the same mixtures and domain. */
+int gosma_bnb_export(gosma_ctx *ctx, int max_nodes, gosma_node *out, int *count);
+int gosma_bnb_import(gosma_ctx *ctx, int n, const gosma_node *in);
+
 /* Checkpoint of a run between two gosma_bnb_step calls: the solver record,
  * the incumbent and its pose, and every queue slot (keys and sub-cubes) go
  * to the file at path.  GOSMA_ENOTREADY without a run. */
@@ -479,10 +524,11 @@ int gosma_selftest_approx(gosma_ctx *ctx, double measured[5], double assumed[5])
  * at the device's maximum SM clock (*clock_mhz receives it): rates[0] scalar
  * FP32 fused multiply-add, rates[1] packed FP32x2 fused multiply-add (lanes,
  * two per instruction), rates[2] ex2.approx, rates[3] sqrt.approx, rates[4]
- * rcp.approx.  Each is timed with CUDA events over one launch of 8 x 256
+ * rcp.approx, rates[5] rsqrt.approx, rates[6] lg2.approx (each rcp and lg2
+ * beside one FP32 add).  Each is timed with CUDA events over one launch of 8 x 256
  * threads per SM running eight independent chains of that instruction (best
  * of three launches after a warm-up).  A few milliseconds of device time. */
-int gosma_selftest_pipe_rates(gosma_ctx *ctx, double rates[5], double *clock_mhz);
+int gosma_selftest_pipe_rates(gosma_ctx *ctx, double rates[7], double *clock_mhz);
 
 #ifdef __cplusplus
 }

@@ -1153,3 +1153,99 @@ extern "C" int gosma_bnb_last_children(gosma_ctx *ctx, int max_children, gosma_c
     }
     return GOSMA_OK;
 }
+
+// ---------------------------------------------------------------- moving queue records between runs
+// Sub-cubes can move between runs of the same problem (same mixtures and
+// domain, so the same cell coordinates): the sharded solve hands queue
+// records from the busiest rank to idle ones between steps.
+static_assert(sizeof(gosma_node) == sizeof(Node), "gosma_node mirrors the queue node");
+static_assert(offsetof(gosma_node, r) == offsetof(Node, r) && offsetof(gosma_node, lr) == offsetof(Node, lr) &&
+                  offsetof(gosma_node, psit) == offsetof(Node, psit) && offsetof(gosma_node, ubf) == offsetof(Node, ubf),
+              "gosma_node layout");
+
+// Smallest live key of the queue [0, tail) into the status record, read back
+// as the run's global lower bound.
+static int refresh_lower_bound(gosma_ctx *ctx, BnbState *s, Solve &v) {
+    const unsigned int dead = DEAD;
+    cudaError_t e = cudaMemcpyAsync(&s->st->minkey, &dead, sizeof dead, cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "refresh lower bound");
+    if (v.tail) {
+        min_key<<<grid_for(v.tail, 256, ctx->sm_count), 256, 0, ctx->stream>>>(s->keys[s->cur], v.tail, s->st);
+        ++ctx->launches;
+    }
+    unsigned int mk = DEAD;
+    e = cudaMemcpyAsync(&mk, &s->st->minkey, sizeof mk, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "refresh lower bound");
+    v.dlb = mk == DEAD ? v.dstar : (double)key_value(mk);
+    if (v.dlb > v.dstar) v.dlb = v.dstar;
+    return GOSMA_OK;
+}
+
+extern "C" int gosma_bnb_export(gosma_ctx *ctx, int max_nodes, gosma_node *out, int *count) {
+    if (!ctx) return GOSMA_EINVAL;
+    ctx->err.clear();
+    Solve *vp = solve_of(ctx);
+    if (!vp || !vp->active) return fail(ctx, GOSMA_ENOTREADY, "bnb_export: no run in progress");
+    if (!count || max_nodes < 0 || (max_nodes > 0 && !out)) return fail(ctx, GOSMA_EINVAL, "bnb_export: bad arguments");
+    Solve &v = *vp;
+    BnbState *s = (BnbState *)ctx->bnb;
+    cudaSetDevice(ctx->device);
+    *count = 0;
+    if (max_nodes == 0 || v.tail == 0) return GOSMA_OK;
+    // compaction leaves exactly the live sub-cubes (lb < d*) in [0, tail)
+    unsigned long long nt = 0;
+    int rc = compact(ctx, s, v.tail, &nt);
+    if (rc) return rc;
+    v.tail = v.live = nt;
+    const unsigned long long m = nt < (unsigned long long)max_nodes ? nt : (unsigned long long)max_nodes;
+    v.tail -= m;
+    v.live -= m;
+    cudaError_t e = cudaMemcpyAsync(out, s->q[s->cur] + v.tail, sizeof(Node) * m, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&s->st->tail, &v.tail, sizeof v.tail, cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "bnb_export");
+    rc = refresh_lower_bound(ctx, s, v);
+    if (rc) return rc;
+    *count = (int)m;
+    return GOSMA_OK;
+}
+
+extern "C" int gosma_bnb_import(gosma_ctx *ctx, int n, const gosma_node *in) {
+    if (!ctx) return GOSMA_EINVAL;
+    ctx->err.clear();
+    Solve *vp = solve_of(ctx);
+    if (!vp || !vp->active) return fail(ctx, GOSMA_ENOTREADY, "bnb_import: no run in progress");
+    if (n < 0 || (n > 0 && !in)) return fail(ctx, GOSMA_EINVAL, "bnb_import: bad arguments");
+    Solve &v = *vp;
+    BnbState *s = (BnbState *)ctx->bnb;
+    if (n == 0) return GOSMA_OK;
+    for (int k = 0; k < n; ++k)
+        if (in[k].lr > MAX_LEVEL || in[k].lt > MAX_LEVEL || std::isnan(in[k].lb))
+            return fail(ctx, GOSMA_EINVAL, "bnb_import: not a queue record of this library");
+    cudaSetDevice(ctx->device);
+    if (v.tail + (unsigned long long)n > s->cap) {
+        unsigned long long nt = 0;
+        int rc = compact(ctx, s, v.tail, &nt);
+        if (rc) return rc;
+        v.tail = v.live = nt;
+        if (v.tail + (unsigned long long)n > s->cap)
+            return fail(ctx, GOSMA_EINVAL, "bnb_import: the queue would exceed its capacity");
+    }
+    std::vector<uint32_t> keys(n);
+    for (int k = 0; k < n; ++k) {
+        float f = (float)in[k].lb;  // the lower bound rounded down to FP32, as the queue keys are
+        if ((double)f > in[k].lb) f = nextafterf(f, -INFINITY);
+        keys[k] = order_key(f);
+    }
+    cudaError_t e = cudaMemcpyAsync(s->q[s->cur] + v.tail, in, sizeof(Node) * n, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->keys[s->cur] + v.tail, keys.data(), sizeof(uint32_t) * n, cudaMemcpyHostToDevice,
+                            ctx->stream);
+    v.tail += n;
+    v.live += n;
+    if ((long long)v.live > v.peak) v.peak = (long long)v.live;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&s->st->tail, &v.tail, sizeof v.tail, cudaMemcpyHostToDevice, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "bnb_import");
+    if (v.status == GOSMA_OPTIMAL) v.status = GOSMA_RUNNING;  // a run that had certified its own queue has work again
+    return refresh_lower_bound(ctx, s, v);
+}

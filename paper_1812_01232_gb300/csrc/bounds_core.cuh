@@ -467,10 +467,25 @@ __device__ __forceinline__ float half_kcothk(float k) {
     return 0.5f * k * (1.f + e) * rcpa(1.f - e);
 }
 
-// Warp + block reduction of four double-floats; the result is valid in thread 0.
-template <int BLOCK>
-__device__ inline void block_reduce_df(df v[4], CubeShared &cs) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// A group of GT threads (whole warps) of a BLOCK-thread block works on one
+// cube; the block holds BLOCK / GT groups.  gsync is the group's barrier:
+// the block barrier when one group is the block, else named barrier
+// 1 + gid for the group's GT threads.
+template <int BLOCK, int GT>
+__device__ __forceinline__ void gsync(int gid) {
+    static_assert(GT % 32 == 0 && BLOCK % GT == 0 && BLOCK / GT <= 15, "groups of whole warps");
+    if constexpr (GT == BLOCK) {
+        __syncthreads();
+    } else {
+        asm volatile("bar.sync %0, %1;" ::"r"(gid + 1), "n"(GT) : "memory");
+    }
+}
+
+// Warp + group reduction of four double-floats; the result is valid in the
+// group's thread 0 (gtid == 0).
+template <int BLOCK, int GT>
+__device__ inline void group_reduce_df(df v[4], CubeShared &cs, int gid, int gtid) {
+    const int lane = gtid & 31, warp = gtid >> 5;
 #pragma unroll
     for (int k = 0; k < 4; ++k)
         for (int o = 16; o > 0; o >>= 1) {
@@ -482,20 +497,28 @@ __device__ inline void block_reduce_df(df v[4], CubeShared &cs) {
             cs.red[2 * k][warp] = v[k].h;
             cs.red[2 * k + 1][warp] = v[k].l;
         }
-    __syncthreads();
-    if (threadIdx.x == 0)
+    gsync<BLOCK, GT>(gid);
+    if (gtid == 0)
         for (int k = 0; k < 4; ++k) {
             df s = {cs.red[2 * k][0], cs.red[2 * k + 1][0]};
-            for (int w = 1; w < BLOCK / 32; ++w) s = df_add(s, {cs.red[2 * k][w], cs.red[2 * k + 1][w]});
+            for (int w = 1; w < GT / 32; ++w) s = df_add(s, {cs.red[2 * k][w], cs.red[2 * k + 1][w]});
             v[k] = s;
         }
 }
 
 // Work distribution of the persistent bound kernels: cubes are handed out
-// one at a time from a device counter that is zero at launch, so that blocks
+// one at a time from a device counter that is zero at launch, so that groups
 // drawing cheap cubes (infeasible ones, children reusing cached self sums)
-// take more of them.  Every thread of the block calls it; the leading barrier
-// keeps the slot from being overwritten before all threads have read it.
+// take more of them.  Every thread of the group calls it; the leading barrier
+// keeps the group's slot from being overwritten before all its threads have
+// read it.
+template <int BLOCK, int GT>
+__device__ __forceinline__ int next_cube(int *counter, int *slot, int gid, int gtid) {
+    gsync<BLOCK, GT>(gid);
+    if (gtid == 0) *slot = atomicAdd(counter, 1);
+    gsync<BLOCK, GT>(gid);
+    return *slot;
+}
 __device__ __forceinline__ int next_cube(int *counter, int *slot) {
     __syncthreads();
     if (threadIdx.x == 0) *slot = atomicAdd(counter, 1);
@@ -503,28 +526,30 @@ __device__ __forceinline__ int next_cube(int *counter, int *slot) {
     return *slot;
 }
 
-// The whole per-cube computation.  Every thread of the block must call it
-// with the same cube; sums are valid in thread 0 on return.  need_self = 0
-// skips the self pairs (the caller reuses cached self sums).
-template <int BLOCK>
+// The whole per-cube computation.  Every thread of the group (GT threads,
+// group gid of the block, gtid its thread) must call it with the same cube,
+// its own CubeShared and shared arrays; sums are valid in the group's thread
+// 0 on return.  need_self = 0 skips the self pairs (the caller reuses cached
+// self sums).
+template <int BLOCK, int GT = BLOCK>
 __device__ void cube_bounds(const MixDev &mx, const CubePrep &prep, df zeta2, bool need_self, CubeShared &cs,
-                            const SmemArrays &sm, CubeSums &out) {
-    const int tid = threadIdx.x;
+                            const SmemArrays &sm, CubeSums &out, int gid = 0, int gtid = threadIdx.x) {
+    const int tid = gtid;
     const int n1 = mx.n1, n2 = mx.n2;
     const float U = GOSMA_U;
-    for (int k = tid; k < PREP_WORDS; k += BLOCK)
+    for (int k = tid; k < PREP_WORDS; k += GT)
         reinterpret_cast<float *>(&cs.rot)[k] = reinterpret_cast<const float *>(&prep)[k];
     if (tid == 0) {
         cs.infeasible = prep.infeasible;
         cs.centre_infeasible = 0;
         cs.spsi_max = 0u;
     }
-    __syncthreads();
+    gsync<BLOCK, GT>(gid);
 
     // ---------------- phase 1a: image columns u_j = R_r0^T mu_2j (double-float)
     // (an odd count gets a copy of the last column with zero weight as the
     // partner of the last pair)
-    for (int j = tid; j < n2 + (n2 & 1); j += BLOCK) {
+    for (int j = tid; j < n2 + (n2 & 1); j += GT) {
         const int jj = j < n2 ? j : n2 - 1;
         df m0 = {mx.mu2h[3 * jj], mx.mu2l[3 * jj]}, m1 = {mx.mu2h[3 * jj + 1], mx.mu2l[3 * jj + 1]},
            m2 = {mx.mu2h[3 * jj + 2], mx.mu2l[3 * jj + 2]};
@@ -547,7 +572,7 @@ __device__ void cube_bounds(const MixDev &mx, const CubePrep &prep, df zeta2, bo
     Acc dsl, dsu;  // diagonal self terms of this thread
     dsl.zero();
     dsu.zero();
-    for (int i = tid; i < n1; i += BLOCK) {
+    for (int i = tid; i < n1; i += GT) {
         df c[3], w[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -662,7 +687,7 @@ __device__ void cube_bounds(const MixDev &mx, const CubePrep &prep, df zeta2, bo
         dsl.add(ph * ph * half_kcothk(a) * (1.f - 16.f * U));
         dsu.add(ph * ph * half_kcothk(k0));
     }
-    __syncthreads();
+    gsync<BLOCK, GT>(gid);
 
     // per-thread sums (double-float): self lb, cross ub, self centre, cross centre
     df T[4] = {fast_two_sum(dsl.s, dsl.c), {0.f, 0.f}, fast_two_sum(dsu.s, dsu.c), {0.f, 0.f}};
@@ -670,8 +695,8 @@ __device__ void cube_bounds(const MixDev &mx, const CubePrep &prep, df zeta2, bo
 
     if (!cs.infeasible) {
         // ---------------- phase 2a: cross pairs
-        const int Ti = n1 >= BLOCK ? BLOCK : pow2ceil(n1);
-        const int Tj = BLOCK / Ti;
+        const int Ti = n1 >= GT ? GT : pow2ceil(n1);
+        const int Tj = GT / Ti;
         const int ti = tid % Ti, tj = tid / Ti;
         for (int i = ti; i < n1; i += Ti) {
             // rotation uncertainty of this row: point-independent, or the
@@ -751,8 +776,8 @@ __device__ void cube_bounds(const MixDev &mx, const CubePrep &prep, df zeta2, bo
         // ---------------- phase 2b: self pairs i < m, rows paired (p, n1-2-p) for balance
         if (need_self && n1 > 1) {
             const int NP = n1 / 2;  // ceil((n1 - 1) / 2)
-            const int Si = NP >= BLOCK ? BLOCK : pow2ceil(NP);
-            const int Sj = BLOCK / Si;
+            const int Si = NP >= GT ? GT : pow2ceil(NP);
+            const int Sj = GT / Si;
             const int si = tid % Si, sj = tid / Si;
             for (int pp = si; pp < NP; pp += Si) {
                 for (int h = 0; h < 2; ++h) {
@@ -822,7 +847,7 @@ __device__ void cube_bounds(const MixDev &mx, const CubePrep &prep, df zeta2, bo
     }
 
     // ---------------- phase 3: block reduction (double-float)
-    block_reduce_df<BLOCK>(T, cs);
+    group_reduce_df<BLOCK, GT>(T, cs, gid, gtid);
     if (tid == 0) {
         out.self_lb = (double)T[0].h + (double)T[0].l;
         out.cross_ub = (double)T[1].h + (double)T[1].l;
@@ -834,7 +859,7 @@ __device__ void cube_bounds(const MixDev &mx, const CubePrep &prep, df zeta2, bo
         out.feasible = !cs.infeasible;
         out.centre_feasible = !cs.centre_infeasible;
     }
-    __syncthreads();
+    gsync<BLOCK, GT>(gid);
 }
 
 // Final per-cube values from the sums (thread 0).

@@ -42,6 +42,59 @@ inline int sma_block_for(int count, int sm_count, bool f64, int n1, int n2) {
     return b;
 }
 
+// Shape of the batched solver's bound kernel: threads per block and cubes per
+// block (groups of block / cubes threads, whole warps, each bounding its own
+// sub-cube).
+struct BoundShape {
+    int block, cubes;
+};
+
+// The shapes the batched solver's autotuner times.  wide: the block size a
+// single problem of the largest mixture would use (32 for tiny mixtures,
+// 512 or 1024 for large ones); group_bytes: the shared memory one group
+// needs.  Shapes whose groups would not fit 200 KB of shared memory per
+// block, or whose groups would be narrower than a warp, are left out.
+inline int bound_shape_candidates(int wide, size_t group_bytes, BoundShape out[12]) {
+    static const BoundShape all[] = {{32, 1},  {64, 1},  {64, 2},  {128, 1}, {128, 2}, {128, 4},
+                                     {256, 1}, {256, 2}, {256, 4}, {512, 1}, {1024, 1}};
+    int n = 0;
+    for (const BoundShape &c : all) {
+        if (c.block == 32 && wide != 32) continue;       // one warp per cube only for tiny mixtures
+        if (c.block >= 512 && c.block != wide) continue;  // wide blocks only where one problem would use them
+        if (c.block / c.cubes < 32) continue;
+        if (((group_bytes + 15) & ~(size_t)15) * (size_t)c.cubes > (size_t)200 * 1024) continue;
+        out[n++] = c;
+    }
+    return n;
+}
+
+// The autotuner's choice from a timing table: ms[c * reps + k] is the k-th
+// timed launch of candidate c (after one untimed warm launch).  The
+// candidate with the smallest median wins, ties to the earlier candidate.
+inline int pick_shape(const float *ms, int ncand, int reps) {
+    int best = -1;
+    float best_med = 0.f;
+    for (int c = 0; c < ncand; ++c) {
+        float v[16];
+        const int r = reps < 16 ? reps : 16;
+        for (int k = 0; k < r; ++k) v[k] = ms[c * reps + k];
+        std::sort(v, v + r);
+        const float med = r % 2 ? v[r / 2] : 0.5f * (v[r / 2 - 1] + v[r / 2]);
+        if (best < 0 || med < best_med) {
+            best = c;
+            best_med = med;
+        }
+    }
+    return best;
+}
+
+// Re-tune when the unfinished problems have halved since the last tuning
+// (the work of a launch, and so the best shape, follows the mix of
+// unfinished problems), while some remain.
+inline bool retune_due(int running_at_tune, int running_now) {
+    return running_now > 0 && 2 * running_now <= running_at_tune;
+}
+
 // Whether an open file holds at least `count` records of `bytes` bytes after
 // its current position (which is left where it was).  A reader checks this
 // before it sizes buffers from counts stored in the file, so that a damaged

@@ -564,42 +564,50 @@ __global__ void mp_prep(const ProbDev *__restrict__ P, const int *__restrict__ o
     }
 }
 
-template <int BLOCK>
+// G cubes per block: groups of BLOCK / G threads (whole warps), each with its
+// own shared arrays (group_floats floats of the dynamic shared memory) and
+// its own work slot.
+template <int BLOCK, int G>
 __global__ void __launch_bounds__(BLOCK)
     mp_bound(const ProbDev *__restrict__ P, const int *__restrict__ off, int nprob, const Node *__restrict__ parents,
              const CubePrep *__restrict__ prep, Node *__restrict__ kids, double *__restrict__ kid_ub,
-             int *__restrict__ counter) {
+             int *__restrict__ counter, int group_floats) {
+    constexpr int GT = BLOCK / G;
     extern __shared__ float smem_f[];
-    __shared__ CubeShared cs;
-    __shared__ CubeSums sums;
-    __shared__ int slot;
+    __shared__ CubeShared cs[G];
+    __shared__ CubeSums sums[G];
+    __shared__ int slot[G];
+    const int gid = threadIdx.x / GT, gtid = threadIdx.x % GT;
+    float *my_smem = smem_f + (size_t)gid * group_floats;
     const double inf = __longlong_as_double(0x7ff0000000000000LL);
     const int N = off[nprob];
-    for (int w = next_cube(counter, &slot); w < N; w = next_cube(counter, &slot)) {
+    for (int w = next_cube<BLOCK, GT>(counter, &slot[gid], gid, gtid); w < N;
+         w = next_cube<BLOCK, GT>(counter, &slot[gid], gid, gtid)) {
         const int k = mp_find(off, nprob, w), c = w - off[k];
         const MixDev &mx = P[k].mx;
-        SmemArrays sm = carve(smem_f, mx.n1, mx.n2);
+        SmemArrays sm = carve(my_smem, mx.n1, mx.n2);
         const Node &pr = parents[w >> 3];
         const bool rot = split_rotation(pr);
         const bool need_self = !(pr.flags & 1u) || !rot;
-        cube_bounds<BLOCK>(mx, prep[w], P[k].zeta2, need_self, cs, sm, sums);
-        if (threadIdx.x == 0) {
+        cube_bounds<BLOCK, GT>(mx, prep[w], P[k].zeta2, need_self, cs[gid], sm, sums[gid], gid, gtid);
+        if (gtid == 0) {
+            const CubeSums &su = sums[gid];
             const Node p = pr;
             Node ch = child_of(p, c & 7, rot);
-            double sl = need_self ? sums.self_lb : p.self_lb;
-            double sc = need_self ? sums.self_c : p.self_c;
+            double sl = need_self ? su.self_lb : p.self_lb;
+            double sc = need_self ? su.self_c : p.self_c;
             double lb, ub;
-            if (!sums.feasible) {
+            if (!su.feasible) {
                 lb = ub = inf;
             } else {
-                double Ssum = sl + 2.0 * sums.cross_ub;
-                lb = sl - 2.0 * sums.cross_ub - 1e-12 * Ssum;
-                ub = sums.centre_feasible ? sc - 2.0 * sums.cross_c : inf;
+                double Ssum = sl + 2.0 * su.cross_ub;
+                lb = sl - 2.0 * su.cross_ub - 1e-12 * Ssum;
+                ub = su.centre_feasible ? sc - 2.0 * su.cross_c : inf;
             }
             ch.lb = lb;
             ch.self_lb = sl;
             ch.self_c = sc;
-            ch.psit = sums.psi_t_max;
+            ch.psit = su.psi_t_max;
             ch.flags |= 1u;
             kids[w] = ch;
             kid_ub[w] = ub;
@@ -1129,34 +1137,46 @@ struct MultiBuffers {
     }
 };
 
-template <int BLOCK>
-static cudaError_t mp_bound_launch(gosma_ctx *ctx, cudaStream_t st, const ProbDev *P, const int *off, int nprob, const Node *parents,
-                                   const CubePrep *prep, Node *kids, double *kid_ub, int *counter, size_t smem) {
-    auto kern = mp_bound<BLOCK>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <int BLOCK, int G>
+static cudaError_t mp_bound_launch(gosma_ctx *ctx, cudaStream_t st, const ProbDev *P, const int *off, int nprob,
+                                   const Node *parents, const CubePrep *prep, Node *kids, double *kid_ub, int *counter,
+                                   size_t smem) {
+    auto kern = mp_bound<BLOCK, G>;
+    const size_t group = (smem + 15) & ~(size_t)15;  // each group's arrays start on a 16-byte boundary
+    const size_t total = group * G;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)total);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BLOCK, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BLOCK, total);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     e = cudaMemsetAsync(counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
-    kern<<<ctx->sm_count * per_sm, BLOCK, smem, st>>>(P, off, nprob, parents, prep, kids, kid_ub, counter);
+    kern<<<ctx->sm_count * per_sm, BLOCK, total, st>>>(P, off, nprob, parents, prep, kids, kid_ub, counter,
+                                                        (int)(group / sizeof(float)));
     ++ctx->launches;
     return cudaGetLastError();
 }
 
-static cudaError_t mp_bound_any(int block, gosma_ctx *ctx, cudaStream_t st, const ProbDev *P, const int *off, int nprob,
-                                const Node *parents, const CubePrep *prep, Node *kids, double *kid_ub, int *counter,
-                                size_t smem) {
-    switch (block) {
-    case 32: return mp_bound_launch<32>(ctx, st, P, off, nprob, parents, prep, kids, kid_ub, counter, smem);
-    case 64: return mp_bound_launch<64>(ctx, st, P, off, nprob, parents, prep, kids, kid_ub, counter, smem);
-    case 128: return mp_bound_launch<128>(ctx, st, P, off, nprob, parents, prep, kids, kid_ub, counter, smem);
-    case 256: return mp_bound_launch<256>(ctx, st, P, off, nprob, parents, prep, kids, kid_ub, counter, smem);
-    case 512: return mp_bound_launch<512>(ctx, st, P, off, nprob, parents, prep, kids, kid_ub, counter, smem);
-    default: return mp_bound_launch<1024>(ctx, st, P, off, nprob, parents, prep, kids, kid_ub, counter, smem);
-    }
+// The bound kernel's shapes: threads per block x cubes per block.
+static cudaError_t mp_bound_any(BoundShape shape, gosma_ctx *ctx, cudaStream_t st, const ProbDev *P, const int *off,
+                                int nprob, const Node *parents, const CubePrep *prep, Node *kids, double *kid_ub,
+                                int *counter, size_t smem) {
+#define MPB(B, G) \
+    if (shape.block == B && shape.cubes == G) return mp_bound_launch<B, G>(ctx, st, P, off, nprob, parents, prep, kids, kid_ub, counter, smem)
+    MPB(32, 1);
+    MPB(64, 1);
+    MPB(64, 2);
+    MPB(128, 1);
+    MPB(128, 2);
+    MPB(128, 4);
+    MPB(256, 1);
+    MPB(256, 2);
+    MPB(256, 4);
+    MPB(512, 1);
+    MPB(1024, 1);
+#undef MPB
+    return cudaErrorInvalidValue;
 }
 
 static int validate_problem(gosma_ctx *ctx, const gosma_problem &p, int k) {
@@ -1400,6 +1420,13 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
     if (8LL * o.pop * nprob > 0x7fffffffLL)
         return fail(ctx, GOSMA_EINVAL, "bnb_solve_batch: 8 * pop * problems must be below 2^31");
     if (cap < 16ULL * o.pop) return fail(ctx, GOSMA_EINVAL, "bnb_solve_batch: queue_capacity below 16 * pop");
+    {
+        const BoundShape ok[] = {{32, 1},  {64, 1},  {64, 2},  {128, 1}, {128, 2}, {128, 4},
+                                 {256, 1}, {256, 2}, {256, 4}, {512, 1}, {1024, 1}};
+        bool valid = o.bound_block == 0 && o.bound_cubes == 0;
+        for (const BoundShape &c : ok) valid = valid || (o.bound_block == c.block && o.bound_cubes == c.cubes);
+        if (!valid) return fail(ctx, GOSMA_EINVAL, "bnb_solve_batch: unsupported bound_block x bound_cubes");
+    }
     for (int k = 0; k < nprob; ++k) {
         int rc = validate_problem(ctx, probs[k], k);
         if (rc) return rc;
@@ -1770,62 +1797,92 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
         return eb;
     };
 
-    // ---- eager iterations; at TUNE_ITER the candidate block sizes of the bound kernel are timed
-    // on the same prepared children (the bound kernel only writes the children's records)
-    // tune once the queues hold enough parents for a representative launch
-    // (8^5 per problem unless the pop quota is smaller)
-    const int TUNE_ITER = 5;
-    int block = 128, iter = 0;
+    // ---- the bound kernel's shape (threads per block x cubes per block): the
+    // caller's, or timed: every candidate is launched once untimed, then
+    // TUNE_REPS times timed on the same prepared children (the bound kernel
+    // only writes the children's records), and the smallest median wins
+    // (pick_shape).  The first tuning runs at TUNE_ITER, once the queues hold
+    // enough parents for a representative launch (8^5 per problem unless the
+    // pop quota is smaller); the shapes are timed again whenever the
+    // unfinished problems have halved since (retune_due).
+    const int TUNE_ITER = 5, TUNE_REPS = 3;
+    const bool tune = o.bound_block == 0;
+    BoundShape shape = tune ? BoundShape{128, 1} : BoundShape{o.bound_block, o.bound_cubes};
+    BoundShape cands[12];
+    const int ncand = bound_shape_candidates(bounds_block_size(max_n1, max_n2), smem, cands);
+    int tunings = 0, running_at_tune = nprob, iter = 0;
     cudaEvent_t ta, tb;
     cudaEventCreate(&ta);
     cudaEventCreate(&tb);
-    for (; iter <= TUNE_ITER && e == cudaSuccess; ++iter) {
+    struct EventFree {
+        cudaEvent_t a, b;
+        ~EventFree() {
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+        }
+    } ev_guard{ta, tb};
+    auto eager = [&](bool tune_now) -> cudaError_t {
         front();
-        if (iter == TUNE_ITER) {
-            float best = 1e30f;
-            // 32 threads when even the largest mixture has few pairs per cube
-            // (as bounds_block_size picks for one problem), a wider block for
-            // large mixtures
-            const int wide = bounds_block_size(max_n1, max_n2);
-            for (int cand : {wide == 32 ? 32 : 0, 64, 128, 256, wide > 256 ? wide : 0}) {
-                if (!cand) continue;
-                cudaEventRecord(ta, st);
-                e = mp_bound_any(cand, ctx, st, dP, off, nprob, parents, prep, kids, kid_ub, Qb.quota + 1, smem);
-                cudaEventRecord(tb, st);
-                if (e == cudaSuccess) e = cudaEventSynchronize(tb);
-                float ms = 0;
-                cudaEventElapsedTime(&ms, ta, tb);
-                if (e == cudaSuccess && ms < best) {
-                    best = ms;
-                    block = cand;
+        cudaError_t ee = cudaSuccess;
+        if (tune_now && ncand > 0) {
+            std::vector<float> ms((size_t)ncand * TUNE_REPS, 1e30f);
+            for (int c = 0; c < ncand && ee == cudaSuccess; ++c)
+                for (int rep = 0; rep <= TUNE_REPS && ee == cudaSuccess; ++rep) {
+                    cudaEventRecord(ta, st);
+                    cudaError_t el = mp_bound_any(cands[c], ctx, st, dP, off, nprob, parents, prep, kids, kid_ub,
+                                                  Qb.quota + 1, smem);
+                    cudaEventRecord(tb, st);
+                    if (el != cudaSuccess) {  // a shape that does not fit: never picked
+                        cudaGetLastError();
+                        break;
+                    }
+                    ee = cudaEventSynchronize(tb);
+                    float t = 0.f;
+                    if (ee == cudaSuccess) ee = cudaEventElapsedTime(&t, ta, tb);
+                    if (rep > 0) ms[(size_t)c * TUNE_REPS + rep - 1] = t;
                 }
+            if (ee == cudaSuccess) {
+                shape = cands[pick_shape(ms.data(), ncand, TUNE_REPS)];
+                ++tunings;
+                // this iteration's children from the chosen shape
+                ee = mp_bound_any(shape, ctx, st, dP, off, nprob, parents, prep, kids, kid_ub, Qb.quota + 1, smem);
             }
         } else {
-            e = mp_bound_any(block, ctx, st, dP, off, nprob, parents, prep, kids, kid_ub, Qb.quota + 1, smem);
+            ee = mp_bound_any(shape, ctx, st, dP, off, nprob, parents, prep, kids, kid_ub, Qb.quota + 1, smem);
         }
-        if (e == cudaSuccess) e = back();
-        if (e == cudaSuccess) e = cudaGetLastError();
-    }
-    cudaEventDestroy(ta);
-    cudaEventDestroy(tb);
+        if (ee == cudaSuccess) ee = back();
+        if (ee == cudaSuccess) ee = cudaGetLastError();
+        return ee;
+    };
+    for (; iter <= TUNE_ITER && e == cudaSuccess; ++iter) e = eager(tune && iter == TUNE_ITER);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "batch iterations");
 
     // ---- one iteration captured in a CUDA graph, replayed until every problem is done
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
-        front();
-        cudaError_t e2 = mp_bound_any(block, ctx, st, dP, off, nprob, parents, prep, kids, kid_ub, Qb.quota + 1, smem);
-        cudaError_t e3 = back();
-        cudaMemcpyAsync(h_ndone, d_ndone, sizeof(int), cudaMemcpyDeviceToHost, st);
-        e = cudaStreamEndCapture(st, &graph);
-        if (e == cudaSuccess) e = e2;
-        if (e == cudaSuccess) e = e3;
-    }
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
-    if (e != cudaSuccess) {
+    auto capture = [&]() -> cudaError_t {
+        cudaError_t ec = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+        if (ec == cudaSuccess) {
+            front();
+            cudaError_t e2 = mp_bound_any(shape, ctx, st, dP, off, nprob, parents, prep, kids, kid_ub, Qb.quota + 1, smem);
+            cudaError_t e3 = back();
+            cudaMemcpyAsync(h_ndone, d_ndone, sizeof(int), cudaMemcpyDeviceToHost, st);
+            ec = cudaStreamEndCapture(st, &graph);
+            if (ec == cudaSuccess) ec = e2;
+            if (ec == cudaSuccess) ec = e3;
+        }
+        if (ec == cudaSuccess) ec = cudaGraphInstantiate(&exec, graph, 0);
+        return ec;
+    };
+    auto release_graph = [&]() {
+        if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
+        exec = nullptr;
+        graph = nullptr;
+    };
+    e = capture();
+    if (e != cudaSuccess) {
+        release_graph();
         return cuda_fail(ctx, e, "batch graph capture");
     }
     if (o.use_sma) wk.th = std::thread(worker);
@@ -1842,6 +1899,15 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
                 timed_out = true;
                 break;
             }
+            const int running = nprob - *h_ndone;
+            if (e == cudaSuccess && tune && retune_due(running_at_tune, running)) {
+                // time the shapes again on an eager iteration, then a new graph
+                release_graph();
+                ++iter;
+                e = eager(true);
+                running_at_tune = running;
+                if (e == cudaSuccess) e = capture();
+            }
         }
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -1852,8 +1918,7 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
     if (e == cudaSuccess) e = apply_pending();
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     ctx->launches += refine.launches;
-    cudaGraphExecDestroy(exec);
-    cudaGraphDestroy(graph);
+    release_graph();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "batch replay");
 
     // ---- results
@@ -1907,7 +1972,9 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
         r.seconds = (times[it] - times[0]) * 1e-9;
         r.iteration_ms = total_s * 1e3;
         r.launches = ctx->launches;
-        r.block_size = block;
+        r.block_size = shape.block;
+        r.cubes_per_block = shape.cubes;
+        r.tunings = tunings;
     }
     if (d_trace) {
         std::vector<int> cnt(nprob);

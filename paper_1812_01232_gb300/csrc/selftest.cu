@@ -1,6 +1,7 @@
 // Throughput of the pipes the bound kernel runs on, measured on the device:
 // scalar FP32 fused multiply-add, packed FP32x2 fused multiply-add, and the
-// approximate ex2, sqrt and rcp instructions of the multi-function unit.
+// approximate ex2, sqrt, rcp, rsqrt and lg2 instructions of the
+// multi-function unit.
 // These are the denominators of the bound kernel's roofline (per SM and
 // clock cycle), measured instead of taken from tables.
 //
@@ -10,14 +11,44 @@
 // CUDA events time the launch; lanes per SM per clock = lane operations /
 // (seconds x SMs x the maximum SM clock).  The chains stay bounded
 // (a -> a * c + d with |c| < 1, a -> 2^-a on [0, 1], a -> sqrt(a),
-// a -> 1 / a) and their results are stored only under a flag that is never
-// set, so that the compiler keeps every instruction.
+// a -> 1 / (a + 0.5), a -> 1 / sqrt(a), a -> lg2(a + 1.5)) and their results are
+// stored only under a flag that is never set; the approximate instructions
+// are volatile, so that the compiler keeps every one.
 #include "gosma_internal.cuh"
 #include "packed.cuh"
 
 namespace gosma {
 
+// Volatile forms of the approximate instructions: a chain such as
+// a -> rcp(a) would otherwise be folded by the compiler.
+__device__ __forceinline__ float ex2v(float x) {
+    float y;
+    asm volatile("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sqrtv(float x) {
+    float y;
+    asm volatile("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcpv(float x) {
+    float y;
+    asm volatile("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rsqrtv(float x) {
+    float y;
+    asm volatile("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float lg2v(float x) {
+    float y;
+    asm volatile("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 constexpr int PR_ITERS = 2048;
+constexpr int PR_OPS = 7;
 constexpr int PR_THREADS = 256;
 constexpr int PR_BLOCKS_PER_SM = 8;
 
@@ -46,9 +77,11 @@ __global__ void __launch_bounds__(PR_THREADS) pipe_rate_kernel(float *sink, int 
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
                 if (OP == 0) a[k] = fmaf(a[k], 0.999f, 0.001f);
-                if (OP == 2) a[k] = ex2a(-a[k]);
-                if (OP == 3) a[k] = sqrta(a[k]);
-                if (OP == 4) a[k] = rcpa(a[k]);
+                if (OP == 2) a[k] = ex2v(-a[k]);
+                if (OP == 3) a[k] = sqrtv(a[k]);
+                if (OP == 4) a[k] = rcpv(a[k] + 0.5f);  // one FP32 add beside each rcp (rcp(rcp(a)) folds)
+                if (OP == 5) a[k] = rsqrtv(a[k]);   // a -> 1/sqrt(a): bounded, 1 is its fixed point
+                if (OP == 6) a[k] = lg2v(a[k] + 1.5f);  // one FP32 add beside each lg2
             }
     }
     if (store) {
@@ -59,7 +92,7 @@ __global__ void __launch_bounds__(PR_THREADS) pipe_rate_kernel(float *sink, int 
     }
 }
 
-int selftest_pipe_rates(gosma_ctx *ctx, double rates[5], double *clock_mhz) {
+int selftest_pipe_rates(gosma_ctx *ctx, double rates[PR_OPS], double *clock_mhz) {
     cudaSetDevice(ctx->device);
     int khz = 0;
     cudaError_t e = cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, ctx->device);
@@ -71,9 +104,10 @@ int selftest_pipe_rates(gosma_ctx *ctx, double rates[5], double *clock_mhz) {
     cudaEvent_t ev[2];
     cudaEventCreate(&ev[0]);
     cudaEventCreate(&ev[1]);
-    void (*kern[5])(float *, int) = {pipe_rate_kernel<0>, pipe_rate_kernel<1>, pipe_rate_kernel<2>,
-                                     pipe_rate_kernel<3>, pipe_rate_kernel<4>};
-    for (int op = 0; op < 5 && e == cudaSuccess; ++op) {
+    void (*kern[PR_OPS])(float *, int) = {pipe_rate_kernel<0>, pipe_rate_kernel<1>, pipe_rate_kernel<2>,
+                                          pipe_rate_kernel<3>, pipe_rate_kernel<4>, pipe_rate_kernel<5>,
+                                          pipe_rate_kernel<6>};
+    for (int op = 0; op < PR_OPS && e == cudaSuccess; ++op) {
         float best = 1e30f;
         for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {  // the first launch warms up
             cudaEventRecord(ev[0], ctx->stream);
@@ -99,7 +133,7 @@ int selftest_pipe_rates(gosma_ctx *ctx, double rates[5], double *clock_mhz) {
 
 }  // namespace gosma
 
-extern "C" int gosma_selftest_pipe_rates(gosma_ctx *ctx, double rates[5], double *clock_mhz) {
+extern "C" int gosma_selftest_pipe_rates(gosma_ctx *ctx, double rates[7], double *clock_mhz) {
     if (!ctx) return GOSMA_EINVAL;
     ctx->err.clear();
     if (!rates || !clock_mhz) return gosma::fail(ctx, GOSMA_EINVAL, "selftest_pipe_rates: null output");

@@ -32,7 +32,8 @@ class Bound(C.Structure):
 
 class Opts(C.Structure):
     _fields_ = [("eps", C.c_double), ("pop", C.c_int), ("max_nodes", C.c_longlong), ("max_seconds", C.c_double),
-                ("use_sma", C.c_int), ("sma_max_iter", C.c_int), ("queue_capacity", C.c_longlong)]
+                ("use_sma", C.c_int), ("sma_max_iter", C.c_int), ("queue_capacity", C.c_longlong),
+                ("bound_block", C.c_int), ("bound_cubes", C.c_int)]
 
 
 class Result(C.Structure):
@@ -42,7 +43,8 @@ class Result(C.Structure):
                 ("sma_calls", C.c_longlong), ("queue_peak", C.c_longlong), ("seconds", C.c_double),
                 ("status", C.c_int), ("cross_pairs", C.c_longlong), ("self_pairs", C.c_longlong),
                 ("bound_ms", C.c_double), ("iteration_ms", C.c_double), ("queue_size", C.c_longlong),
-                ("launches", C.c_longlong), ("block_size", C.c_int)]
+                ("launches", C.c_longlong), ("block_size", C.c_int), ("cubes_per_block", C.c_int),
+                ("tunings", C.c_int)]
 
 
 class Problem(C.Structure):
@@ -63,6 +65,11 @@ class LearnOpts(C.Structure):
 # gosma_trace_point as a numpy record
 HISTORY_DTYPE = np.dtype([("iteration", "<i8"), ("seconds", "<f8"), ("dstar", "<f8"), ("lower_bound", "<f8"),
                           ("queue_size", "<i8"), ("nodes", "<i8")])
+
+# gosma_node as a numpy record
+NODE_DTYPE = np.dtype([("lb", "<f8"), ("self_lb", "<f8"), ("self_c", "<f8"), ("r", "<u4", (3,)), ("t", "<u4", (3,)),
+                       ("lr", "<u2"), ("lt", "<u2"), ("psit", "<f4"), ("flags", "<u4"), ("ubf", "<f4")])
+assert NODE_DTYPE.itemsize == 64
 
 # gosma_trace_rec as a numpy record
 TRACE_DTYPE = np.dtype([("feat", "<f4", (16,)), ("cube", "<f8", (10,)), ("lb", "<f8"), ("ub", "<f8"),
@@ -97,6 +104,8 @@ SIGNATURES = {
     "gosma_bnb_step": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(Result)]),
     "gosma_bnb_history": (C.c_int, [C.c_void_p, C.c_longlong, C.c_void_p, C.POINTER(C.c_longlong)]),
     "gosma_bnb_last_children": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]),
+    "gosma_bnb_export": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_int)]),
+    "gosma_bnb_import": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p]),
     "gosma_bnb_set_incumbent": (C.c_int, [C.c_void_p, C.c_double, D]),
     "gosma_bnb_save": (C.c_int, [C.c_void_p, C.c_char_p]),
     "gosma_bnb_load": (C.c_int, [C.c_void_p, C.c_char_p]),
@@ -213,6 +222,8 @@ def _dev(t, name, dtype, shape, device):
 
 class Gosma:
     """One libgosma context on one CUDA device and stream."""
+
+    node_dtype = NODE_DTYPE  # queue records of bnb_export / bnb_import
 
     def __init__(self, device: int = 0, stream=None):
         self.L = load_library()
@@ -407,9 +418,10 @@ class Gosma:
 
     # ---------------------------------------------------------------- branch-and-bound
     @staticmethod
-    def _opts(eps, pop, max_nodes, max_seconds, use_sma, sma_max_iter, queue_capacity):
+    def _opts(eps, pop, max_nodes, max_seconds, use_sma, sma_max_iter, queue_capacity, shape=None):
+        b, g = shape if shape is not None else (0, 0)
         return Opts(float(eps), int(pop), int(max_nodes), float(max_seconds), int(bool(use_sma)), int(sma_max_iter),
-                    int(queue_capacity))
+                    int(queue_capacity), int(b), int(g))
 
     @staticmethod
     def _result(r):
@@ -420,7 +432,7 @@ class Gosma:
             "seconds": r.seconds, "status": r.status, "status_name": STATUS.get(r.status, str(r.status)),
             "cross_pairs": r.cross_pairs, "self_pairs": r.self_pairs, "bound_ms": r.bound_ms,
             "iteration_ms": r.iteration_ms, "queue_size": r.queue_size, "launches": r.launches,
-            "block_size": r.block_size,
+            "block_size": r.block_size, "cubes_per_block": r.cubes_per_block, "tunings": r.tunings,
         }
 
     def bnb_solve(self, eps=0.1, pop=0, max_nodes=0, max_seconds=0.0, use_sma=True, sma_max_iter=100,
@@ -432,9 +444,12 @@ class Gosma:
         return self._result(r)
 
     def bnb_solve_batch(self, problems, eps=0.1, pop=0, max_nodes=0, max_seconds=0.0, use_sma=True,
-                        sma_max_iter=100, queue_capacity=0, learned=None, trace_cap=0):
+                        sma_max_iter=100, queue_capacity=0, learned=None, trace_cap=0, shape=None):
         """Algorithm 1 for many independent problems at once (list of problem
         dicts as produced by synth); returns one result dict per problem.
+
+        ``shape``: None (the autotuner picks the bound kernel's shape) or
+        (threads per block, sub-cubes per block).
 
         ``learned``: None (plain) or a dict with ``beta``, ``seed`` and
         ``active_iters`` for the network-ordered form (parameters loaded with
@@ -460,7 +475,7 @@ class Gosma:
                 keep.append(c)
                 ip = C.POINTER(C.c_int)
                 p.nclass, p.n1c, p.n2c, p.w = len(c[0]), c[0].ctypes.data_as(ip), c[1].ctypes.data_as(ip), _p(c[2])
-        o = self._opts(eps, pop, max_nodes, max_seconds, use_sma, sma_max_iter, queue_capacity)
+        o = self._opts(eps, pop, max_nodes, max_seconds, use_sma, sma_max_iter, queue_capacity, shape)
         res = (Result * len(problems))()
         lo = LearnOpts(0, 0.0, 0, int(trace_cap), 0)
         if learned is not None:
@@ -548,6 +563,19 @@ class Gosma:
                         "bnb_last_children")
         return cubes, rec
 
+    def bnb_export(self, max_nodes):
+        """Remove up to max_nodes live sub-cubes from the run; returns them as a
+        NODE_DTYPE array (gosma_bnb_export)."""
+        out = np.zeros(max(0, int(max_nodes)), dtype=NODE_DTYPE)
+        n = C.c_int(0)
+        self._check(self.L.gosma_bnb_export(self.h, int(max_nodes), out.ctypes.data, C.byref(n)), "bnb_export")
+        return out[:n.value].copy()
+
+    def bnb_import(self, nodes):
+        """Append queue records (a NODE_DTYPE array) to the run (gosma_bnb_import)."""
+        nodes = np.ascontiguousarray(nodes, dtype=NODE_DTYPE)
+        self._check(self.L.gosma_bnb_import(self.h, len(nodes), nodes.ctypes.data), "bnb_import")
+
     def bnb_save(self, path):
         self._check(self.L.gosma_bnb_save(self.h, os.fsencode(path)), "bnb_save")
 
@@ -558,11 +586,11 @@ class Gosma:
         return int(self.L.gosma_kernel_launches(self.h))
 
     def selftest_pipe_rates(self):
-        """Measured lane operations per SM per clock: dict(ffma, ffma2, ex2, sqrt, rcp, clock_mhz)."""
-        r = np.zeros(5)
+        """Measured lane operations per SM per clock: dict(ffma, ffma2, ex2, sqrt, rcp, rsqrt, lg2, clock_mhz)."""
+        r = np.zeros(7)
         mhz = C.c_double()
         self._check(self.L.gosma_selftest_pipe_rates(self.h, _p(r), C.byref(mhz)), "selftest_pipe_rates")
-        return dict(zip(("ffma", "ffma2", "ex2", "sqrt", "rcp"), r.tolist()), clock_mhz=mhz.value)
+        return dict(zip(("ffma", "ffma2", "ex2", "sqrt", "rcp", "rsqrt", "lg2"), r.tolist()), clock_mhz=mhz.value)
 
     def selftest_wait_timeout(self, limit_seconds=0.05):
         """Returns the library's return code (GOSMA_ETIMEOUT when the bounded wait gave up)."""

@@ -3,8 +3,18 @@ oracle's, shared by the GPU parity tests.
 
 Tolerances (derived from the FP32 error model of the bound kernel):
 * lower bound: never above the oracle's (up to 1e-13 of the term scale, the
-  oracle's own FP64 summation) and within 1e-5 of the term scale
-  S = self_lb + 2 cross_ub (lb itself can be near zero, so it is no scale);
+  oracle's own FP64 summation) and within LB_TOL x max(1, sqrt(k2max / 200))
+  of the term scale S = self_lb + 2 cross_ub (lb itself can be near zero, so
+  it is no scale), k2max the largest image concentration.  The kernel's
+  allowance on the half-angle sine of B (at most 7.5u per unit of
+  sin(theta/2) + sin(s/2), from FP32 directions) moves a term's exponent
+  -c sin^2(B/2), c about 2 k_eff for k_eff = a k2 / (a + k2), by up to
+  2 c sin(B/2) times the allowance; the largest error of a term relative to
+  its own peak is about 0.6 sqrt(2c) times the allowance, so the bound's
+  relative error grows as sqrt(kappa).  The bar is 1e-5 up to k2max = 200,
+  the paper-scale workload's range (where the benchmark runs), and grows as
+  sqrt(k2max) above it (the tiny workload's qPN concentrations reach a few
+  thousand);
 * upper bound (f at the centre): within 1e-5 of S_c = self_c + 2 cross_c;
 * feasibility decisions: identical; psi_r to 1e-6, psi_t to FP32 accuracy.
 
@@ -30,23 +40,21 @@ LB_TOL = 1e-5
 UB_TOL = 1e-5
 
 
-def compare(got, ref, tag="", eps_c22=None, dstar=None, cubes=None):
+def lb_tol(kappa2_max=None):
+    """The lower-bound bar in units of S for image concentrations up to kappa2_max."""
+    return LB_TOL * max(1.0, float(np.sqrt(kappa2_max / 200.0))) if kappa2_max is not None else LB_TOL
+
+
+def compare(got, ref, tag="", eps_c22=None, dstar=None, cubes=None, kappa2_max=None):
     fin = np.isfinite(ref[:, 0])
-    assert np.array_equal(fin, np.isfinite(got[:, 0])), tag + " feasibility"
     cf = np.isfinite(ref[:, 1])
-    assert np.array_equal(cf, np.isfinite(got[:, 1])), tag + " centre feasibility"
     S = ref[fin, 2] + 2 * ref[fin, 3]
     d = got[fin, 0] - ref[fin, 0]
-    assert np.all(d <= 1e-13 * S), tag + " lb above oracle by %g" % (d / S).max()
     lb_err = np.abs(d) / S
-    assert lb_err.max(initial=0.0) <= LB_TOL, tag + " lb rel err %g" % lb_err.max()
     Sc = ref[cf, 4] + 2 * ref[cf, 5]
     ub_err = np.abs(got[cf, 1] - ref[cf, 1]) / Sc
-    assert ub_err.max(initial=0.0) <= UB_TOL, tag + " ub rel err %g" % ub_err.max()
-    assert np.allclose(got[:, 6], ref[:, 6], rtol=1e-6)
-    # psi_t as used (after the pi/2 reading) agrees to FP32 accuracy
-    assert np.allclose(got[:, 7], ref[:, 7], rtol=2e-3, atol=2e-5)
-    stats = {"tag": tag, "cubes": int(len(ref)), "feasible": int(fin.sum()),
+    tol = lb_tol(kappa2_max)
+    stats = {"tag": tag, "cubes": int(len(ref)), "feasible": int(fin.sum()), "lb_tol": tol,
              "lb_rel_max": float(lb_err.max(initial=0.0)), "ub_rel_max": float(ub_err.max(initial=0.0)),
              "lb_deficit_max": float((-d).max(initial=0.0)),
              "self_deficit_max": float((ref[fin, 2] - got[fin, 2]).max(initial=0.0)),
@@ -62,6 +70,7 @@ def compare(got, ref, tag="", eps_c22=None, dstar=None, cubes=None):
             stats["near_cubes"] = int(near.sum())
             stats["near_deficit_over_eps_c22"] = float((-d[near]).max(initial=0.0)) / eps_c22
             stats["near_lb_rel_max"] = float(lb_err[near].max(initial=0.0))
+    # statistics and records first, so that a failing comparison leaves them too
     path = os.environ.get("GOSMA_PARITY_LOG")
     if path:
         with open(path, "a") as f:
@@ -72,4 +81,12 @@ def compare(got, ref, tag="", eps_c22=None, dstar=None, cubes=None):
         name = "".join(ch if ch.isalnum() else "_" for ch in tag)
         np.savez_compressed(os.path.join(dump, name + ".npz"), got=got, ref=ref,
                             cubes=cubes if cubes is not None else np.zeros(0))
+    assert np.array_equal(fin, np.isfinite(got[:, 0])), tag + " feasibility"
+    assert np.array_equal(cf, np.isfinite(got[:, 1])), tag + " centre feasibility"
+    assert np.all(d <= 1e-13 * S), tag + " lb above oracle by %g" % (d / S).max()
+    assert lb_err.max(initial=0.0) <= tol, tag + " lb rel err %g (bar %g)" % (lb_err.max(), tol)
+    assert ub_err.max(initial=0.0) <= UB_TOL, tag + " ub rel err %g" % ub_err.max()
+    assert np.allclose(got[:, 6], ref[:, 6], rtol=1e-6)
+    # psi_t as used (after the pi/2 reading) agrees to FP32 accuracy
+    assert np.allclose(got[:, 7], ref[:, 7], rtol=2e-3, atol=2e-5)
     return stats

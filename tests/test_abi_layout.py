@@ -30,6 +30,7 @@ STRUCTS = {
     "gosma_learn_opts": G.LearnOpts,
     "gosma_trace_point": G.HISTORY_DTYPE,
     "gosma_trace_rec": G.TRACE_DTYPE,
+    "gosma_node": G.NODE_DTYPE,
 }
 
 

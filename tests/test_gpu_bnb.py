@@ -290,3 +290,25 @@ def test_history_follows_the_run(ctx):
     # the incumbent reaches its final value early; most of the run raises the lower bound
     first = np.flatnonzero(h["dstar"] - r["f"] <= 1e-3 * r["c22"])[0]
     assert first < 0.5 * len(h)
+
+
+def test_batch_bound_shapes_agree(ctx):
+    """The bound kernel's shapes (threads per block x sub-cubes per block):
+    every fixed shape and the autotuned run certify the same optima, the
+    result reports the shape used, the autotuner timed the shapes at least
+    once, and an unsupported shape is refused."""
+    from paper_1812_01232_gb300.gosma import GosmaError
+    probs = [synth.tiny_problem(200000 + s) for s in range(4)]
+    tuned = ctx.bnb_solve_batch(probs, eps=1e-3, max_seconds=120, queue_capacity=1 << 24)
+    assert all(r["tunings"] >= 1 for r in tuned)
+    assert (tuned[0]["block_size"], tuned[0]["cubes_per_block"]) in [
+        (32, 1), (64, 1), (64, 2), (128, 1), (128, 2), (128, 4), (256, 1), (256, 2), (256, 4)]
+    for shape in ((32, 1), (64, 2), (128, 4), (256, 1)):
+        res = ctx.bnb_solve_batch(probs, eps=1e-3, max_seconds=120, queue_capacity=1 << 24, shape=shape)
+        for a, b in zip(res, tuned):
+            assert a["block_size"] == shape[0] and a["cubes_per_block"] == shape[1] and a["tunings"] == 0
+            if a["status_name"] == b["status_name"] == "optimal":
+                assert abs(a["f"] - b["f"]) <= 1e-3 * a["c22"]
+                assert a["lb"] <= b["f"] + 1e-9 and b["lb"] <= a["f"] + 1e-9
+    with pytest.raises(GosmaError):
+        ctx.bnb_solve_batch(probs, eps=1e-3, max_seconds=10, shape=(128, 3))

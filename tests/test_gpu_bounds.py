@@ -33,7 +33,7 @@ def test_pipe_rates_are_plausible(ctx):
     measurement noise), packed FMA at least as fast in lanes, MUFU slower."""
     r = ctx.selftest_pipe_rates()
     assert 32 <= r["ffma"] <= 140 and r["ffma2"] <= 140 and r["ffma2"] >= 0.9 * r["ffma"], r
-    for k in ("ex2", "sqrt", "rcp"):
+    for k in ("ex2", "sqrt", "rcp", "rsqrt", "lg2"):
         assert 4 <= r[k] <= r["ffma"], r
     assert r["clock_mhz"] > 500
 
@@ -46,7 +46,7 @@ def test_tiny_parity(ctx, oracle_mod, seed):
                              near_frac=0.5)
     got = ctx.eval_bounds_detail(cubes)
     ref = oracle_mod.bounds(oracle_mod.Mixtures.from_problem(prob), cubes, prob["zeta"])
-    compare(got, ref, "tiny")
+    compare(got, ref, "tiny", kappa2_max=prob["kappa2"].max())
 
 
 def test_host_and_device_paths_agree(ctx):
@@ -74,7 +74,7 @@ def test_ragged_sizes(ctx, oracle_mod, n1, n2):
                              near=(prob["r_gt"], prob["t_gt"]), near_frac=0.5)
     got = ctx.eval_bounds_detail(cubes)
     ref = oracle_mod.bounds(oracle_mod.Mixtures.from_problem(prob), cubes, prob["zeta"])
-    compare(got, ref, "%dx%d" % (n1, n2))
+    compare(got, ref, "%dx%d" % (n1, n2), kappa2_max=prob["kappa2"].max())
 
 
 def test_edge_cases(ctx, oracle_mod):
@@ -92,7 +92,7 @@ def test_edge_cases(ctx, oracle_mod):
     ])
     got = ctx.eval_bounds_detail(cubes)
     ref = oracle_mod.bounds(oracle_mod.Mixtures.from_problem(prob), cubes, prob["zeta"])
-    compare(got, ref, "edge")
+    compare(got, ref, "edge", kappa2_max=prob["kappa2"].max())
     assert np.isinf(got[0, 0]) and np.isinf(got[1, 0])
     assert np.isfinite(got[3, 0]) and got[3, 1] - got[3, 0] < 1e-4 * (got[3, 2] + 2 * got[3, 3])
 
@@ -159,7 +159,8 @@ def test_paper_scale_parity_full_batch(ctx, oracle_mod):
     got = ctx.eval_bounds_detail(cubes)
     mix = oracle_mod.Mixtures.from_problem(prob)
     ref = oracle_mod.bounds(mix, cubes, prob["zeta"])
-    compare(got, ref, "paper-scale eval_bounds", eps_c22=prob["eps"] * oracle_mod.c22(mix), cubes=cubes)
+    compare(got, ref, "paper-scale eval_bounds", eps_c22=prob["eps"] * oracle_mod.c22(mix), cubes=cubes,
+            kappa2_max=prob["kappa2"].max())
     both = np.isfinite(got[:, 0]) & np.isfinite(got[:, 1])
     assert np.all(got[both, 0] <= got[both, 1])
 
@@ -184,7 +185,8 @@ def test_stress_parity_full_size(ctx, oracle_mod):
                           rng.choice(np.flatnonzero(both), 128, replace=False)])
     mix = oracle_mod.Mixtures.from_problem(prob)
     ref = oracle_mod.bounds(mix, cubes[idx], prob["zeta"])
-    compare(got[idx], ref, "stress", eps_c22=prob["eps"] * oracle_mod.c22(mix), cubes=cubes[idx])
+    compare(got[idx], ref, "stress", eps_c22=prob["eps"] * oracle_mod.c22(mix), cubes=cubes[idx],
+            kappa2_max=prob["kappa2"].max())
     assert np.all(got[both, 0] <= got[both, 1])
 
 
@@ -203,7 +205,7 @@ def test_largest_mixture_that_fits(ctx, oracle_mod):
     both = np.isfinite(got[:, 0]) & np.isfinite(got[:, 1])
     idx = np.concatenate([np.arange(4), np.flatnonzero(both)[:4]])
     ref = oracle_mod.bounds(oracle_mod.Mixtures.from_problem(prob), cubes[idx], prob["zeta"])
-    compare(got[idx], ref, "largest")
+    compare(got[idx], ref, "largest", kappa2_max=prob["kappa2"].max())
     big = synth.stress_problem(4100, n1=n1 + 1, n2=n2)
     with pytest.raises(GosmaError):
         ctx.set_problem(big)

@@ -47,7 +47,10 @@ def test_tiny_parity_point_mode(ctx, oracle_mod, seed):
                              near_frac=0.5)
     g0, g1 = _both_modes(ctx, cubes)
     mix = oracle_mod.Mixtures.from_problem(prob)
-    compare(g1, oracle_mod.bounds(mix, cubes, prob["zeta"], psi_mode=1), "tiny point-psi_r")
+    compare(g0, oracle_mod.bounds(mix, cubes, prob["zeta"]), "tiny %d cube-psi_r" % seed, cubes=cubes,
+            kappa2_max=prob["kappa2"].max())
+    compare(g1, oracle_mod.bounds(mix, cubes, prob["zeta"], psi_mode=1), "tiny %d point-psi_r" % seed, cubes=cubes,
+            kappa2_max=prob["kappa2"].max())
     fin = np.isfinite(g0[:, 0])
     assert np.array_equal(g0[:, 1], g1[:, 1], equal_nan=True)  # the centre term does not use psi_r
     assert np.array_equal(g0[:, 2], g1[:, 2], equal_nan=True)  # nor do the self pairs
@@ -63,9 +66,12 @@ def test_ragged_parity_point_mode(ctx, oracle_mod, n1, n2):
     ctx.set_problem(prob)
     cubes = synth.tree_cubes(int(rng.integers(1 << 30)), 97, prob["t_lo"], prob["t_hi"], 1, 14,
                              near=(prob["r_gt"], prob["t_gt"]), near_frac=0.5)
-    _, g1 = _both_modes(ctx, cubes)
-    compare(g1, oracle_mod.bounds(oracle_mod.Mixtures.from_problem(prob), cubes, prob["zeta"], psi_mode=1),
-            "%dx%d point-psi_r" % (n1, n2))
+    g0, g1 = _both_modes(ctx, cubes)
+    mix = oracle_mod.Mixtures.from_problem(prob)
+    compare(g0, oracle_mod.bounds(mix, cubes, prob["zeta"]), "%dx%d cube-psi_r" % (n1, n2), cubes=cubes,
+            kappa2_max=prob["kappa2"].max())
+    compare(g1, oracle_mod.bounds(mix, cubes, prob["zeta"], psi_mode=1), "%dx%d point-psi_r" % (n1, n2), cubes=cubes,
+            kappa2_max=prob["kappa2"].max())
 
 
 def test_paper_scale_parity_point_mode(ctx, oracle_mod):

@@ -118,6 +118,18 @@ int main(int argc, char **argv) {
     if (what[0] == 'b') printf("%d\n", gosma::auto_pop_batch(atoll(argv[2]), atoi(argv[3]), strtoull(argv[4], 0, 10)));
     if (what[0] == 'm') printf("%d\n", gosma::sma_block_for(atoi(argv[2]), atoi(argv[3]), atoi(argv[4]) != 0,
                                                             atoi(argv[5]), atoi(argv[6])));
+    if (what[0] == 'p') {  // pick: ncand reps, then ncand * reps timings
+        const int nc = atoi(argv[2]), reps = atoi(argv[3]);
+        std::vector<float> ms;
+        for (int a = 4; a < argc; ++a) ms.push_back((float)atof(argv[a]));
+        printf("%d\n", gosma::pick_shape(ms.data(), nc, reps));
+    }
+    if (what[0] == 'r') printf("%d\n", gosma::retune_due(atoi(argv[2]), atoi(argv[3])) ? 1 : 0);
+    if (what[0] == 'c') {  // candidates: wide group_bytes -> how many shapes
+        gosma::BoundShape c[12];
+        const int n = gosma::bound_shape_candidates(atoi(argv[2]), (size_t)atoll(argv[3]), c);
+        printf("%d\n", n);
+    }
     if (what[0] == 'h') {  // hash: k, then values; the first k form one array, the rest another
         const int k = atoi(argv[2]);
         std::vector<double> v;
@@ -205,3 +217,31 @@ def test_checkpoint_problem_fingerprint(rules):
         assert rules("h", 3, *["%.17g" % x for x in w]) != base, i
     assert rules("h", 2, *["%.17g" % x for x in v]) != base
     assert rules("h", 4, *["%.17g" % x for x in v]) != base
+
+
+def test_autotuner_picks_the_smallest_median(rules):
+    """pick_shape on fake timing tables (3 timings per candidate): the
+    smallest median wins, a single outlier does not decide, ties go to the
+    earlier candidate, and a shape that could not run (1e30) never wins."""
+    assert rules("p", 3, 3, 2.0, 2.1, 1.9, 1.5, 1.6, 1.4, 1.7, 1.8, 1.6) == 1
+    assert rules("p", 2, 3, 1.0, 9.0, 1.1, 1.2, 1.2, 1.2) == 0      # median 1.1 beats 1.2 despite the 9.0
+    assert rules("p", 2, 3, 5.0, 0.1, 5.0, 1.0, 1.0, 1.0) == 1      # one fast outlier is not the median
+    assert rules("p", 2, 3, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0) == 0      # tie: the earlier candidate
+    assert rules("p", 3, 3, 1e30, 1e30, 1e30, 2.0, 2.0, 2.0, 1e30, 1e30, 1e30) == 1
+
+
+def test_autotuner_retunes_when_half_the_problems_finished(rules):
+    assert rules("r", 256, 128) == 1 and rules("r", 256, 129) == 0
+    assert rules("r", 128, 64) == 1 and rules("r", 1, 0) == 0          # nothing left to tune for
+    assert rules("r", 2, 1) == 1
+
+
+def test_autotuner_candidates(rules):
+    """The shapes timed: a one-warp block only for tiny mixtures, wide blocks
+    only where one problem would use them, no group narrower than a warp, and
+    nothing whose groups' shared memory exceeds 200 KB per block."""
+    assert rules("c", 32, 4096) == 9        # 32x1 64x1 64x2 128x1 128x2 128x4 256x1 256x2 256x4
+    assert rules("c", 128, 4096) == 8       # no 32x1
+    assert rules("c", 1024, 4096) == 9      # + 1024x1
+    assert rules("c", 128, 60 * 1024) == 6  # 64x1 64x2 128x1 128x2 256x1 256x2: four groups of 60 KB do not fit
+    assert rules("c", 512, 150 * 1024) == 4  # one group per block only: 64x1 128x1 256x1 512x1
