@@ -19,6 +19,10 @@ e2e: the same metric through gosma_eval_bounds with host buffers: every step
 copies a batch of 65,536 sub-cubes of the same tree depths from host memory
 and reads back their lower and upper bounds.
 
+--batch-only (with --batch-budget and --batch-queue): just the batched
+measurement, autotuned shape only (a long documented run of the 256 uneven
+problems with large queues).
+
 --impl reference: the FP64 CPU oracle, as it stands, on the host cores, on a
 bounded sample of the same workload per step (sub-cubes of the same problem
 at tree depths 2-12, Theorem 1 bounds; --ref-seconds of host time spread over
@@ -34,7 +38,9 @@ Two more measurements ride on the same line (rank 0, N = 1, unless
   eps 1e-3) in one batched solve (one captured CUDA graph per iteration)
   under a time budget: aggregate pair-bound evals/s and per-problem time to
   the certified optimum (p50/p99 over the problems certified in the budget,
-  with the count);
+  with the count), with the bound kernel's shape picked by the autotuner and,
+  on the same problems and budget, with the fixed default shape (128
+  threads, one sub-cube per block);
 * "time_to_certified": tiny problems (10 x 8 components, eps 1e-3) solved
   to the certified optimum by the plain single-problem solver (one after the
   other), the plain batched solver and the learned batched solver (network
@@ -42,6 +48,9 @@ Two more measurements ride on the same line (rank 0, N = 1, unless
   iterations, about the first 10% of the nodes, where the incumbent is
   found), on the same problems, each with
   its automatic pop;
+* "psi_r_point": the same tiny problems solved by the single-problem solver
+  with the point-independent and the point-dependent rotation uncertainty
+  angle (Lemma 2): nodes and wall time to the certified optima;
 * "sma": the batched device refinement (SMA, Sec. 5) of many seed poses of
   the 128 x 64 paper-scale problem (half near the true pose, half uniform),
   seeds refined per second with the FP32 and the FP64 search (CUDA events
@@ -556,7 +565,8 @@ def run_time_to_certified(n_prob):
                      "certified": int(sum(r["status_name"] == "optimal" for r in res)),
                      "agree_with_single": int(sum(abs(r["f"] - q["f"]) <= eps * q["c22"]
                                                   for r, q in zip(res, single))),
-                     "p50_s": float(np.median([r["seconds"] for r in res]))}
+                     "p50_s": float(np.median([r["seconds"] for r in res])),
+                     "shape": [res[0]["block_size"], res[0]["cubes_per_block"]], "tunings": res[0]["tunings"]}
     ctx.close()
     return out
 

@@ -107,6 +107,7 @@ typedef struct {
     int block_size;          /* batched solver: threads per block of the bound kernel  */
     int cubes_per_block;     /* batched solver: sub-cubes per block of the bound kernel */
     int tunings;             /* batched solver: times the autotuner timed the shapes     */
+    long long dstar_iteration; /* the iteration that last lowered d* (the final incumbent's) */
 } gosma_result;
 
 /* One independent alignment problem for gosma_bnb_solve_batch: the mixtures
@@ -316,9 +317,10 @@ int gosma_bnb_solve(gosma_ctx *ctx, const gosma_opts *opts, gosma_result *out);
  * (threads per block, sub-cubes per block) is the caller's
  * (opts->bound_block, opts->bound_cubes) or picked by an autotuner: each
  * candidate shape is launched once and then timed three times on the same
- * children at the fifth iteration, the smallest median wins, and the shapes
- * are timed again (and the graph captured anew) whenever the number of
- * unfinished problems has halved since the last tuning; results[k] reports
+ * children (a sixteenth of the iteration's, at least 64 per SM) at the fifth
+ * iteration, the smallest median wins, and the shapes are timed again (and
+ * the graph captured anew) whenever the number of unfinished problems has
+ * halved since the last tuning, at least 32 iterations after it; results[k] reports
  * the final shape and the number of tunings.  The bounds of one sub-cube
  * differ between shapes only by the order of their FP32 sums.
  * results[k].seconds is the device time from the start to problem k's

@@ -220,14 +220,15 @@ __global__ void ext_scatter(uint32_t *__restrict__ keys, const Node *__restrict_
 
 // ---------------------------------------------------------------- 3. bound
 // Pre-pass for the children: one thread per child.
-__global__ void cube_prep_children(Domain dom, const Node *__restrict__ parents, int np, CubePrep *__restrict__ prep) {
+__global__ void cube_prep_children(Domain dom, const Node *__restrict__ parents, int np, CubePrep *__restrict__ prep,
+                                   int point) {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= 8 * np) return;
     const Node p = parents[c >> 3];
     Node ch = child_of(p, c & 7, split_rotation(p));
     CubeGeom g;
     decode(ch, dom, g);
-    cube_prepare(g.r0, g.rhw, g.t0, g.thw, prep[c]);
+    cube_prepare(g.r0, g.rhw, g.t0, g.thw, prep[c], point != 0);
 }
 
 template <int BLOCK>
@@ -541,7 +542,7 @@ static int launch_children(gosma_ctx *ctx, const Domain &dom, BnbState *s, int n
     if (grid > 8LL * np) grid = 8LL * np;
     e = cudaMemsetAsync(s->kid_rot, 0, 2 * sizeof(unsigned int), ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "memset(children)");
-    cube_prep_children<<<(8 * np + 127) / 128, 128, 0, ctx->stream>>>(dom, s->parents, np, s->rot);
+    cube_prep_children<<<(8 * np + 127) / 128, 128, 0, ctx->stream>>>(dom, s->parents, np, s->rot, ctx->mix.psi_point);
     ++ctx->launches;
     df z2;
     split_double(ctx->zeta * ctx->zeta, z2.h, z2.l);
@@ -674,6 +675,7 @@ struct Solve {
     int status = GOSMA_RUNNING;
     bool active = false;
     int last_np = 0;  // parents popped by the last iteration (its children are in the kids buffer)
+    long long dstar_iter = 0;  // iteration that last lowered d*
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     std::vector<gosma_trace_point> history;  // one point per iteration (Fig. 5)
 };
@@ -727,6 +729,7 @@ static void fill_result(gosma_ctx *ctx, const Solve &v, gosma_result *out) {
     out->iteration_ms = v.t_iter_ms;
     out->queue_size = (long long)v.live;
     out->launches = ctx->launches;
+    out->dstar_iteration = v.dstar_iter;
 }
 
 }  // namespace gosma
@@ -881,6 +884,7 @@ extern "C" int gosma_bnb_step(gosma_ctx *ctx, int max_iters, gosma_result *out) 
             if (v.o.use_sma) ++v.sma_calls;
             if (f1 < v.dstar) {
                 v.dstar = f1;
+                v.dstar_iter = v.iters;
                 memcpy(v.best, x1, sizeof x1);
                 e = cudaMemcpyAsync(s->dstar, &v.dstar, sizeof v.dstar, cudaMemcpyHostToDevice, ctx->stream);
                 if (e != cudaSuccess) return cuda_fail(ctx, e, "set d*");
@@ -914,7 +918,7 @@ extern "C" int gosma_bnb_solve(gosma_ctx *ctx, const gosma_opts *opts, gosma_res
 // device status block, d* and the queue slots [0, tail) (keys and nodes,
 // dead slots included, so that compaction and selection replay exactly).
 namespace {
-constexpr char CK_MAGIC[8] = {'G', 'O', 'S', 'M', 'A', 'C', 'K', '2'};
+constexpr char CK_MAGIC[8] = {'G', 'O', 'S', 'M', 'A', 'C', 'K', '3'};
 struct CkHeader {
     char magic[8];
     int n1, n2;
@@ -931,6 +935,7 @@ struct CkSolve {  // the solver record without its events
     long long nodes, iters, sma_calls, peak, cross_pairs, self_pairs;
     double t_bound_ms, t_iter_ms, seconds;
     int status, cur;
+    long long dstar_iter;
 };
 struct FileCloser {
     FILE *f;
@@ -986,6 +991,7 @@ extern "C" int gosma_bnb_save(gosma_ctx *ctx, const char *path) {
     c.seconds = v.seconds;
     c.status = v.status;
     c.cur = s->cur;
+    c.dstar_iter = v.dstar_iter;
     Status hs;
     std::vector<uint32_t> keys(v.tail);
     std::vector<Node> nodes(v.tail);
@@ -1063,6 +1069,7 @@ extern "C" int gosma_bnb_load(gosma_ctx *ctx, const char *path) {
     v.t_iter_ms = c.t_iter_ms;
     v.seconds = c.seconds;
     v.status = c.status;
+    v.dstar_iter = c.dstar_iter;
     v.active = true;
     return GOSMA_OK;
 }
@@ -1093,6 +1100,7 @@ extern "C" int gosma_bnb_set_incumbent(gosma_ctx *ctx, double f, const double x[
     BnbState *s = (BnbState *)ctx->bnb;
     cudaSetDevice(ctx->device);
     v.dstar = f;
+    v.dstar_iter = v.iters;
     memcpy(v.best, x, sizeof v.best);
     if (v.dlb > v.dstar) v.dlb = v.dstar;
     cudaError_t e = cudaMemcpyAsync(s->dstar, &v.dstar, sizeof v.dstar, cudaMemcpyHostToDevice, ctx->stream);

@@ -8,9 +8,9 @@
 namespace gosma {
 
 // Pre-pass: one thread per cube.
-__global__ void cube_prep_cubes(const gosma_cube *__restrict__ cubes, int n, CubePrep *__restrict__ prep) {
+__global__ void cube_prep_cubes(const gosma_cube *__restrict__ cubes, int n, CubePrep *__restrict__ prep, int point) {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < n) cube_prepare(cubes[c].r0, cubes[c].r_hw, cubes[c].t0, cubes[c].t_hw, prep[c]);
+    if (c < n) cube_prepare(cubes[c].r0, cubes[c].r_hw, cubes[c].t0, cubes[c].t_hw, prep[c], point != 0);
 }
 
 // The self terms of Theorem 1 depend only on the translation cuboid, so
@@ -169,7 +169,7 @@ int launch_bounds(gosma_ctx *ctx, const gosma_cube *d_cubes, int n, gosma_bound 
         ctx->rot_bytes = need;
     }
     CubePrep *rot = (CubePrep *)ctx->d_rot;
-    cube_prep_cubes<<<(n + 127) / 128, 128, 0, ctx->stream>>>(d_cubes, n, rot);
+    cube_prep_cubes<<<(n + 127) / 128, 128, 0, ctx->stream>>>(d_cubes, n, rot, ctx->mix.psi_point);
     ++ctx->launches;
     char *base = (char *)ctx->d_rot;
     unsigned long long *keys = (unsigned long long *)(base + o_keys);

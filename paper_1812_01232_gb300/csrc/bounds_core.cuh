@@ -58,6 +58,7 @@ struct CubePrep {
 };
 static_assert(sizeof(CubePrep) == 288, "CubePrep layout");
 constexpr int PREP_WORDS = sizeof(CubePrep) / 4;
+constexpr int PREP_WORDS_CUBE = offsetof(CubePrep, pj) / 4;  // without the point-dependent terms
 
 // shared-memory scalars of one cube
 struct CubeShared {
@@ -129,7 +130,7 @@ __device__ inline int pow2ceil(int x) {
 // angle(R_r p, R_r0 p) <= |r - r0| <= sqrt(3) r_hw capped at pi, and the
 // translation cuboid split into double-floats.
 __device__ inline void cube_prepare(const double r0[3], double rhw, const double t0[3], const double thw[3],
-                                    CubePrep &o) {
+                                    CubePrep &o, bool point) {
     double th2 = r0[0] * r0[0] + r0[1] * r0[1] + r0[2] * r0[2];
     double th = sqrt(th2), A, B;
     if (th < 1e-8) {
@@ -164,6 +165,7 @@ __device__ inline void cube_prepare(const double r0[3], double rhw, const double
         split_double(thw[k], o.wh[k], o.wl[k]);
     }
     o.pad[0] = o.pad[1] = 0.f;
+    if (!point) return;  // the point-dependent terms below are read only in that mode
     // right Jacobian J_r(r0) = I - B [r0]x + C [r0]x^2, C = (|r0| - sin|r0|) / |r0|^3
     // (R_{r0 + d} = R_r0 R_{J_r d} to first order), and the vertex images J_r d / 2
     const double C = th < 1e-6 ? 1.0 / 6.0 - th2 / 120.0 : (th - A * th) / (th2 * th);
@@ -537,7 +539,7 @@ __device__ void cube_bounds(const MixDev &mx, const CubePrep &prep, df zeta2, bo
     const int tid = gtid;
     const int n1 = mx.n1, n2 = mx.n2;
     const float U = GOSMA_U;
-    for (int k = tid; k < PREP_WORDS; k += GT)
+    for (int k = tid; k < (mx.psi_point ? PREP_WORDS : PREP_WORDS_CUBE); k += GT)
         reinterpret_cast<float *>(&cs.rot)[k] = reinterpret_cast<const float *>(&prep)[k];
     if (tid == 0) {
         cs.infeasible = prep.infeasible;

@@ -90,9 +90,12 @@ inline int pick_shape(const float *ms, int ncand, int reps) {
 
 // Re-tune when the unfinished problems have halved since the last tuning
 // (the work of a launch, and so the best shape, follows the mix of
-// unfinished problems), while some remain.
-inline bool retune_due(int running_at_tune, int running_now) {
-    return running_now > 0 && 2 * running_now <= running_at_tune;
+// unfinished problems), while some remain, and at least RETUNE_GAP
+// iterations after the last tuning (a short run does not earn back the
+// timings).
+constexpr int RETUNE_GAP = 32;
+inline bool retune_due(int running_at_tune, int running_now, int iters_since_tune) {
+    return running_now > 0 && 2 * running_now <= running_at_tune && iters_since_tune >= RETUNE_GAP;
 }
 
 // Whether an open file holds at least `count` records of `bytes` bytes after

@@ -68,6 +68,7 @@ struct ProbState {
     long long nodes, cross_pairs;
     int done;  // 0 running, else 1 + GOSMA_* status
     int done_iter;
+    int dstar_iter;  // iteration whose end last lowered d*
     int np;
     // incumbent candidates of this iteration: 0 = centre of the child with the
     // smallest upper bound, 1 = the network's seed pose (learned form)
@@ -560,7 +561,7 @@ __global__ void mp_prep(const ProbDev *__restrict__ P, const int *__restrict__ o
         Node ch = child_of(p, c & 7, split_rotation(p));
         CubeGeom g;
         decode(ch, P[k].dom, g);
-        cube_prepare(g.r0, g.rhw, g.t0, g.thw, prep[w]);
+        cube_prepare(g.r0, g.rhw, g.t0, g.thw, prep[w], P[k].mx.psi_point != 0);
     }
 }
 
@@ -571,7 +572,7 @@ template <int BLOCK, int G>
 __global__ void __launch_bounds__(BLOCK)
     mp_bound(const ProbDev *__restrict__ P, const int *__restrict__ off, int nprob, const Node *__restrict__ parents,
              const CubePrep *__restrict__ prep, Node *__restrict__ kids, double *__restrict__ kid_ub,
-             int *__restrict__ counter, int group_floats) {
+             int *__restrict__ counter, int group_floats, int limit) {
     constexpr int GT = BLOCK / G;
     extern __shared__ float smem_f[];
     __shared__ CubeShared cs[G];
@@ -580,7 +581,7 @@ __global__ void __launch_bounds__(BLOCK)
     const int gid = threadIdx.x / GT, gtid = threadIdx.x % GT;
     float *my_smem = smem_f + (size_t)gid * group_floats;
     const double inf = __longlong_as_double(0x7ff0000000000000LL);
-    const int N = off[nprob];
+    const int N = min(off[nprob], limit);  // limit: the autotuner times a prefix of the children
     for (int w = next_cube<BLOCK, GT>(counter, &slot[gid], gid, gtid); w < N;
          w = next_cube<BLOCK, GT>(counter, &slot[gid], gid, gtid)) {
         const int k = mp_find(off, nprob, w), c = w - off[k];
@@ -972,7 +973,8 @@ __global__ void __launch_bounds__(MPO_BLOCK)
 
 // Sum the partials in a fixed order; the best feasible candidate replaces d*
 // when smaller.
-__global__ void mp_obj_final(ProbState *__restrict__ S, int nprob, const double *__restrict__ part, int nblk) {
+__global__ void mp_obj_final(ProbState *__restrict__ S, int nprob, const double *__restrict__ part, int nblk,
+                             const int *__restrict__ d_iter) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nprob) return;
     ProbState &st = S[k];
@@ -982,6 +984,7 @@ __global__ void mp_obj_final(ProbState *__restrict__ S, int nprob, const double 
         for (int b = 0; b < nblk; ++b) f += part[(size_t)(2 * k + c) * nblk + b];
         if (f < st.dstar) {
             st.dstar = f;
+            st.dstar_iter = *d_iter;
             for (int a = 0; a < 6; ++a) st.best_x[a] = st.cand_x[c][a];
         }
     }
@@ -1110,12 +1113,14 @@ struct Incumbent {
 };
 
 // Refined incumbents replace d* and the best pose where they are better.
-__global__ void mp_apply(ProbState *__restrict__ S, const Incumbent *__restrict__ u, int n) {
+__global__ void mp_apply(ProbState *__restrict__ S, const Incumbent *__restrict__ u, int n,
+                         const int *__restrict__ d_iter) {
     int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n) return;
     ProbState &st = S[u[q].k];
     if (u[q].f < st.dstar) {
         st.dstar = u[q].f;
+        st.dstar_iter = *d_iter;
         for (int a = 0; a < 6; ++a) st.best_x[a] = u[q].x[a];
     }
 }
@@ -1140,7 +1145,7 @@ struct MultiBuffers {
 template <int BLOCK, int G>
 static cudaError_t mp_bound_launch(gosma_ctx *ctx, cudaStream_t st, const ProbDev *P, const int *off, int nprob,
                                    const Node *parents, const CubePrep *prep, Node *kids, double *kid_ub, int *counter,
-                                   size_t smem) {
+                                   size_t smem, int limit) {
     auto kern = mp_bound<BLOCK, G>;
     const size_t group = (smem + 15) & ~(size_t)15;  // each group's arrays start on a 16-byte boundary
     const size_t total = group * G;
@@ -1153,7 +1158,7 @@ static cudaError_t mp_bound_launch(gosma_ctx *ctx, cudaStream_t st, const ProbDe
     e = cudaMemsetAsync(counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
     kern<<<ctx->sm_count * per_sm, BLOCK, total, st>>>(P, off, nprob, parents, prep, kids, kid_ub, counter,
-                                                        (int)(group / sizeof(float)));
+                                                        (int)(group / sizeof(float)), limit);
     ++ctx->launches;
     return cudaGetLastError();
 }
@@ -1161,9 +1166,10 @@ static cudaError_t mp_bound_launch(gosma_ctx *ctx, cudaStream_t st, const ProbDe
 // The bound kernel's shapes: threads per block x cubes per block.
 static cudaError_t mp_bound_any(BoundShape shape, gosma_ctx *ctx, cudaStream_t st, const ProbDev *P, const int *off,
                                 int nprob, const Node *parents, const CubePrep *prep, Node *kids, double *kid_ub,
-                                int *counter, size_t smem) {
-#define MPB(B, G) \
-    if (shape.block == B && shape.cubes == G) return mp_bound_launch<B, G>(ctx, st, P, off, nprob, parents, prep, kids, kid_ub, counter, smem)
+                                int *counter, size_t smem, int limit = 0x7fffffff) {
+#define MPB(B, G)                                                                                                     \
+    if (shape.block == B && shape.cubes == G)                                                                          \
+    return mp_bound_launch<B, G>(ctx, st, P, off, nprob, parents, prep, kids, kid_ub, counter, smem, limit)
     MPB(32, 1);
     MPB(64, 1);
     MPB(64, 2);
@@ -1359,13 +1365,13 @@ struct BatchRefiner {
 
     // Improvements go to the device through mp_apply on the iteration's stream
     // (ordered between graph replays); mp_apply keeps the smaller of the two.
-    cudaError_t apply(cudaStream_t sm, ProbState *S_dev, const std::vector<Incumbent> &u) {
+    cudaError_t apply(cudaStream_t sm, ProbState *S_dev, const std::vector<Incumbent> &u, const int *d_iter) {
         if (u.empty()) return cudaSuccess;
         const int nu = (int)std::min<size_t>(u.size(), (size_t)nprob);
         memcpy(hupd, u.data(), sizeof(Incumbent) * nu);
         cudaError_t e = cudaMemcpyAsync(d_upd, hupd, sizeof(Incumbent) * nu, cudaMemcpyHostToDevice, sm);
         if (e != cudaSuccess) return e;
-        mp_apply<<<(nu + 127) / 128, 128, 0, sm>>>(S_dev, d_upd, nu);
+        mp_apply<<<(nu + 127) / 128, 128, 0, sm>>>(S_dev, d_upd, nu, d_iter);
         ++launches;
         e = cudaGetLastError();
         // the staging buffer is reused by the next apply: wait for the copy
@@ -1739,7 +1745,7 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
         for (size_t i = 0; i < u.size(); ++i)
             if (w == 0 || u[w - 1].k != u[i].k) u[w++] = u[i];
         u.resize(w);
-        return refine.apply(st, dS, u);
+        return refine.apply(st, dS, u, d_iter);
     };
     mp_start<<<1, 1, 0, st>>>(d_time);
     ++ctx->launches;
@@ -1791,7 +1797,7 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
         }
         mp_obj_prep<<<dim3((max_n1 + 127) / 128, 2 * nprob), 128, 0, st>>>(dP, dS, ioff, idata);
         mp_obj_pairs<<<dim3(nblk, 2 * nprob), MPO_BLOCK, 0, st>>>(dP, dS, ioff, idata, part, nblk);
-        mp_obj_final<<<(nprob + 127) / 128, 128, 0, st>>>(dS, nprob, part, nblk);
+        mp_obj_final<<<(nprob + 127) / 128, 128, 0, st>>>(dS, nprob, part, nblk, d_iter);
         mp_tick<<<1, 32, 0, st>>>(dS, nprob, d_iter, d_time, d_ndone);
         ctx->launches += 5;
         return eb;
@@ -1801,16 +1807,18 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
     // caller's, or timed: every candidate is launched once untimed, then
     // TUNE_REPS times timed on the same prepared children (the bound kernel
     // only writes the children's records), and the smallest median wins
-    // (pick_shape).  The first tuning runs at TUNE_ITER, once the queues hold
+    // (pick_shape); the timings take a prefix of the children, the chosen shape
+    // then bounds all of them.  The first tuning runs at TUNE_ITER, once the queues hold
     // enough parents for a representative launch (8^5 per problem unless the
     // pop quota is smaller); the shapes are timed again whenever the
-    // unfinished problems have halved since (retune_due).
+    // unfinished problems have halved since, at least RETUNE_GAP iterations
+    // later (retune_due).
     const int TUNE_ITER = 5, TUNE_REPS = 3;
     const bool tune = o.bound_block == 0;
     BoundShape shape = tune ? BoundShape{128, 1} : BoundShape{o.bound_block, o.bound_cubes};
     BoundShape cands[12];
     const int ncand = bound_shape_candidates(bounds_block_size(max_n1, max_n2), smem, cands);
-    int tunings = 0, running_at_tune = nprob, iter = 0;
+    int tunings = 0, running_at_tune = nprob, iter = 0, tuned_at = 0;
     cudaEvent_t ta, tb;
     cudaEventCreate(&ta);
     cudaEventCreate(&tb);
@@ -1825,12 +1833,19 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
         front();
         cudaError_t ee = cudaSuccess;
         if (tune_now && ncand > 0) {
+            // the timings run on a prefix of the iteration's children (a
+            // sixteenth, at least 64 per SM), so that tuning costs about as much
+            // as two or three launches
+            int nkid = 0;
+            ee = cudaMemcpyAsync(&nkid, off + nprob, sizeof(int), cudaMemcpyDeviceToHost, st);
+            if (ee == cudaSuccess) ee = cudaStreamSynchronize(st);
+            const int limit = std::max(nkid / 16, 64 * ctx->sm_count);
             std::vector<float> ms((size_t)ncand * TUNE_REPS, 1e30f);
             for (int c = 0; c < ncand && ee == cudaSuccess; ++c)
                 for (int rep = 0; rep <= TUNE_REPS && ee == cudaSuccess; ++rep) {
                     cudaEventRecord(ta, st);
                     cudaError_t el = mp_bound_any(cands[c], ctx, st, dP, off, nprob, parents, prep, kids, kid_ub,
-                                                  Qb.quota + 1, smem);
+                                                  Qb.quota + 1, smem, limit);
                     cudaEventRecord(tb, st);
                     if (el != cudaSuccess) {  // a shape that does not fit: never picked
                         cudaGetLastError();
@@ -1855,6 +1870,7 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
         return ee;
     };
     for (; iter <= TUNE_ITER && e == cudaSuccess; ++iter) e = eager(tune && iter == TUNE_ITER);
+    tuned_at = TUNE_ITER;
     if (e != cudaSuccess) return cuda_fail(ctx, e, "batch iterations");
 
     // ---- one iteration captured in a CUDA graph, replayed until every problem is done
@@ -1900,12 +1916,13 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
                 break;
             }
             const int running = nprob - *h_ndone;
-            if (e == cudaSuccess && tune && retune_due(running_at_tune, running)) {
+            if (e == cudaSuccess && tune && retune_due(running_at_tune, running, iter - tuned_at)) {
                 // time the shapes again on an eager iteration, then a new graph
                 release_graph();
                 ++iter;
                 e = eager(true);
                 running_at_tune = running;
+                tuned_at = iter;
                 if (e == cudaSuccess) e = capture();
             }
         }
@@ -1974,6 +1991,7 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
         r.launches = ctx->launches;
         r.block_size = shape.block;
         r.cubes_per_block = shape.cubes;
+        r.dstar_iteration = s.dstar_iter;
         r.tunings = tunings;
     }
     if (d_trace) {

@@ -44,7 +44,7 @@ class Result(C.Structure):
                 ("status", C.c_int), ("cross_pairs", C.c_longlong), ("self_pairs", C.c_longlong),
                 ("bound_ms", C.c_double), ("iteration_ms", C.c_double), ("queue_size", C.c_longlong),
                 ("launches", C.c_longlong), ("block_size", C.c_int), ("cubes_per_block", C.c_int),
-                ("tunings", C.c_int)]
+                ("tunings", C.c_int), ("dstar_iteration", C.c_longlong)]
 
 
 class Problem(C.Structure):
@@ -433,6 +433,7 @@ class Gosma:
             "cross_pairs": r.cross_pairs, "self_pairs": r.self_pairs, "bound_ms": r.bound_ms,
             "iteration_ms": r.iteration_ms, "queue_size": r.queue_size, "launches": r.launches,
             "block_size": r.block_size, "cubes_per_block": r.cubes_per_block, "tunings": r.tunings,
+            "dstar_iteration": r.dstar_iteration,
         }
 
     def bnb_solve(self, eps=0.1, pop=0, max_nodes=0, max_seconds=0.0, use_sma=True, sma_max_iter=100,

@@ -34,7 +34,8 @@ def test_resume_replays_the_run(tmp_path, seed, steps):
     res = b.bnb_step(0)
     b.close()
     assert full["status_name"] == res["status_name"] == "optimal"
-    for k in ("f", "lb", "nodes", "iterations", "sma_calls", "queue_peak", "cross_pairs", "self_pairs"):
+    for k in ("f", "lb", "nodes", "iterations", "sma_calls", "queue_peak", "cross_pairs", "self_pairs",
+              "dstar_iteration"):
         assert res[k] == full[k], k
     assert np.array_equal(res["r"], full["r"]) and np.array_equal(res["t"], full["t"])
 

@@ -124,7 +124,7 @@ int main(int argc, char **argv) {
         for (int a = 4; a < argc; ++a) ms.push_back((float)atof(argv[a]));
         printf("%d\n", gosma::pick_shape(ms.data(), nc, reps));
     }
-    if (what[0] == 'r') printf("%d\n", gosma::retune_due(atoi(argv[2]), atoi(argv[3])) ? 1 : 0);
+    if (what[0] == 'r') printf("%d\n", gosma::retune_due(atoi(argv[2]), atoi(argv[3]), atoi(argv[4])) ? 1 : 0);
     if (what[0] == 'c') {  // candidates: wide group_bytes -> how many shapes
         gosma::BoundShape c[12];
         const int n = gosma::bound_shape_candidates(atoi(argv[2]), (size_t)atoll(argv[3]), c);
@@ -231,9 +231,13 @@ def test_autotuner_picks_the_smallest_median(rules):
 
 
 def test_autotuner_retunes_when_half_the_problems_finished(rules):
-    assert rules("r", 256, 128) == 1 and rules("r", 256, 129) == 0
-    assert rules("r", 128, 64) == 1 and rules("r", 1, 0) == 0          # nothing left to tune for
-    assert rules("r", 2, 1) == 1
+    """retune_due(running at the last tuning, running now, iterations since):
+    half the problems finished, some left, and at least 32 iterations since
+    the last tuning (a short run would not earn the timings back)."""
+    assert rules("r", 256, 128, 32) == 1 and rules("r", 256, 129, 32) == 0
+    assert rules("r", 128, 64, 100) == 1 and rules("r", 1, 0, 100) == 0    # nothing left to tune for
+    assert rules("r", 2, 1, 32) == 1
+    assert rules("r", 256, 128, 31) == 0 and rules("r", 2, 1, 5) == 0      # too soon after the last tuning
 
 
 def test_autotuner_candidates(rules):
