@@ -46,11 +46,13 @@ Two more measurements ride on the same line (rank 0, N = 1, unless
   other), the plain batched solver and the learned batched solver (network
   weights from paper_1812_01232_gb300/weights, scoring during the first 8
   iterations, about the first 10% of the nodes, where the incumbent is
-  found), on the same problems, each with
-  its automatic pop;
+  found), on the same problems, each with its automatic pop, three times
+  each (median wall time; the iteration of the final incumbent shows what
+  the network's seeds change);
 * "psi_r_point": the same tiny problems solved by the single-problem solver
   with the point-independent and the point-dependent rotation uncertainty
-  angle (Lemma 2): nodes and wall time to the certified optima;
+  angle (Lemma 2): nodes and wall time (median of three) to the certified
+  optima;
 * "sma": the batched device refinement (SMA, Sec. 5) of many seed poses of
   the 128 x 64 paper-scale problem (half near the true pose, half uniform),
   seeds refined per second with the FP32 and the FP64 search (CUDA events
@@ -80,17 +82,21 @@ UNIT = "pairs/s"
 POP = 8192
 SEED = 2000
 # FP32-pipe lane operations per pair the bound kernel executes, counted from
-# its source (half-angle, centre term, bound term, outward roundings,
-# compensated accumulation); packed FP32x2 instructions do two of them.
-OPS_CROSS = 112
-OPS_SELF = 120
+# the source of cross_pair2 / self_pair2 (packed FP32x2 instructions count
+# as two): double-float geometry 24, centre term 16, bound term 40 (cross)
+# or 61 (self), and 1.5 per pair for the chunked compensated accumulation.
+OPS_CROSS = 82
+OPS_SELF = 103
 FP32_LANES_PER_SM = 128
-# Algorithmic work per pair bound, cross or self: the closed forms of
-# Theorem 1 for the bound and the centre term without the kernel's
-# outward-rounding allowances and compensated sums, about 40 FP32 operations
-# and 11 multi-function-unit operations (7 sqrt, 2 rcp, 2 ex2).
-ALG_FP32_PER_PAIR = 40
-ALG_MUFU_MIX = {"sqrt": 7, "rcp": 2, "ex2": 2}
+# Algorithmic work per pair bound, counted from the kernel's closed forms of
+# Theorem 1 (the bound) and Lemma 1 (the centre term) without its
+# outward-rounding allowances, double-float low parts and compensated sums:
+# |v -+ u|^2 12, centre term 14, bound term 31 FP32 operations; 5 sqrt
+# (sin and cos of theta/2, K at the centre, the largest and the smallest K),
+# 2 rcp and 2 ex2 on the multi-function unit.  The self pairs are counted
+# alike (their four-corner K maximum makes them dearer, so this undercounts).
+ALG_FP32_PER_PAIR = 57
+ALG_MUFU_MIX = {"sqrt": 5, "rcp": 2, "ex2": 2}
 
 
 def log(*a):
@@ -368,24 +374,46 @@ def run_ours(args):
         e2e_t.append(time.perf_counter() - t0)
     e2e_value = 8 * POP * n1 * n2 / float(np.mean(e2e_t))
 
-    # ---------------- roofline of the bound kernel (FP32 pipe; algorithmic count against FP32 and MUFU)
+    # ---------------- roofline of the bound kernel: algorithmic operations against the measured
+    # rates of the FP32 pipe (packed FMA) and the multi-function unit; the binding pipe is the roofline
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
     max_mhz = ck["sm_max_mhz"] or rates["clock_mhz"]
-    peak = sm_count * FP32_LANES_PER_SM * max_mhz * 1e6 / 1e9  # Gop/s
-    achieved = (OPS_CROSS * pairs + OPS_SELF * self_pairs) / (bound_ms / 1e3) / 1e9
-    traffic = kernel_traffic()
-    # effective MUFU rate of the kernel's mix (harmonic: cycles add up per pair)
+    sec = bound_ms / 1e3
+    alg_pairs = pairs + self_pairs
+    fp32_peak = sm_count * rates["ffma2"] * max_mhz * 1e6 / 1e9  # Gop/s
+    # effective MUFU rate of the mix (harmonic: the cycles of a pair's operations add up)
     mufu_n = sum(ALG_MUFU_MIX.values())
     mufu_rate = mufu_n / sum(k / rates[op] for op, k in ALG_MUFU_MIX.items())
     mufu_peak = sm_count * mufu_rate * max_mhz * 1e6 / 1e9  # Gop/s
-    alg_pairs = pairs + self_pairs
-    alg_fp32 = ALG_FP32_PER_PAIR * alg_pairs / (bound_ms / 1e3) / 1e9
-    alg_mufu = mufu_n * alg_pairs / (bound_ms / 1e3) / 1e9
-    alg = {"fp32_ops_per_pair": ALG_FP32_PER_PAIR, "mufu_ops_per_pair": mufu_n, "mufu_mix": ALG_MUFU_MIX,
-           "pairs_per_step": alg_pairs / args.steps, "fp32_achieved": alg_fp32, "fp32_frac": alg_fp32 / peak,
-           "mufu_achieved": alg_mufu, "mufu_peak": mufu_peak, "mufu_frac": alg_mufu / mufu_peak,
-           "unit": "Gop/s"}
-    alg["binding"] = "mufu" if alg["mufu_frac"] >= alg["fp32_frac"] else "fp32"
+    alg_fp32 = ALG_FP32_PER_PAIR * alg_pairs / sec / 1e9
+    alg_mufu = mufu_n * alg_pairs / sec / 1e9
+    binding = "mufu" if alg_mufu / mufu_peak >= alg_fp32 / fp32_peak else "fp32"
+    unit_peak = sm_count * FP32_LANES_PER_SM * max_mhz * 1e6 / 1e9
+    executed = (OPS_CROSS * pairs + OPS_SELF * self_pairs) / sec / 1e9
+    traffic = kernel_traffic()
+    roof = {
+        "bound": "alu", "binding_pipe": binding,
+        "achieved": alg_mufu if binding == "mufu" else alg_fp32,
+        "peak": mufu_peak if binding == "mufu" else fp32_peak,
+        "unit": "Gop/s (%s, algorithmic)" % ("MUFU" if binding == "mufu" else "FP32"),
+        "traffic": traffic, "kernel": "bound_children", "kernel_ms_per_step": bound_ms / args.steps,
+        "pairs_per_step": alg_pairs / args.steps,
+        "algorithmic": {"fp32_ops_per_pair": ALG_FP32_PER_PAIR, "mufu_ops_per_pair": mufu_n,
+                        "mufu_mix": ALG_MUFU_MIX, "fp32_achieved": alg_fp32, "fp32_peak": fp32_peak,
+                        "fp32_frac": alg_fp32 / fp32_peak, "mufu_achieved": alg_mufu, "mufu_peak": mufu_peak,
+                        "mufu_frac": alg_mufu / mufu_peak, "unit": "Gop/s"},
+        "peak_basis": "%d SMs x the measured lanes per SM per clock x %.0f MHz: FP32 %.1f (packed FMA), MUFU "
+                      "%.1f (the sqrt/rcp/ex2 rates weighted by the mix %s); gosma_selftest_pipe_rates, 8 "
+                      "independent chains per thread, 2048 threads per SM, CUDA events"
+                      % (sm_count, max_mhz, rates["ffma2"], mufu_rate, ALG_MUFU_MIX),
+        "fp32_executed": {"ops_per_cross_pair": OPS_CROSS, "ops_per_self_pair": OPS_SELF, "achieved": executed,
+                          "peak": unit_peak, "frac": executed / unit_peak, "unit": "Gop/s",
+                          "peak_basis": "%d SMs x %d FP32 lanes x %.0f MHz (unit count)"
+                                        % (sm_count, FP32_LANES_PER_SM, max_mhz)},
+        "measured_pipe_rates": rates,
+    }
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["frac_algorithmic"] = roof["frac"]
 
     if rank != 0:
         if dist:
@@ -412,18 +440,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": int(2 * 8 * len(cubes)),
                 "call": "gosma_eval_bounds on host buffers, %d sub-cubes per step (self sums computed once per "
                         "distinct translation cuboid; %d distinct)" % (len(cubes), n_cuboids)},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gop/s (FP32 pipe)",
-                     "frac": achieved / peak, "traffic": traffic,
-                     "frac_algorithmic": max(alg["fp32_frac"], alg["mufu_frac"]), "algorithmic": alg,
-                     "kernel": "bound_children", "kernel_ms_per_step": bound_ms / args.steps,
-                     "peak_basis": "%d SMs x %d FP32 lanes x %.0f MHz (unit count); frac counts the %d/%d FP32 "
-                                   "lane operations the kernel executes per cross/self pair"
-                                   % (sm_count, FP32_LANES_PER_SM, max_mhz, OPS_CROSS, OPS_SELF),
-                     "mufu_peak_basis": "%d SMs x %.1f MUFU lanes per SM per clock x %.0f MHz: the sqrt/rcp/ex2 "
-                                        "rates measured by gosma_selftest_pipe_rates (8 independent chains per "
-                                        "thread, 2048 threads per SM, CUDA events), weighted by the mix %s"
-                                        % (sm_count, mufu_rate, max_mhz, ALG_MUFU_MIX),
-                     "measured_pipe_rates": rates},
+        "roofline": roof,
         "cpu_baseline": cpu,
         "clocks": ck,
         "gpu_launches": launches,
@@ -539,58 +556,78 @@ def run_mixgen():
     return out
 
 
-def run_time_to_certified(n_prob):
-    """Plain single, plain batched and learned batched solves of the same tiny problems."""
+def run_time_to_certified(n_prob, repeats=3):
+    """Plain single, plain batched and learned batched solves of the same tiny
+    problems, `repeats` times each (the arms interleaved); wall_s is the
+    median over the repeats."""
     from paper_1812_01232_gb300 import learn, synth
     from paper_1812_01232_gb300.gosma import Gosma
     ctx = Gosma(0)
     eps = 1e-3
     probs = [synth.tiny_problem(200000 + s) for s in range(n_prob)]
     out = {"workload": "%d tiny problems (10 x 8 components), eps 1e-3, queue 2^26 per problem; every solver "
-                       "with its automatic pop (65536 sub-cubes per iteration and problem for 10 x 8 mixtures)"
-                       % n_prob}
-    single = []
-    t0 = time.perf_counter()
-    for p in probs:
-        ctx.set_problem(p)
-        single.append(ctx.bnb_solve(eps=eps, max_seconds=60, queue_capacity=1 << 26))
-    out["plain_single"] = {"wall_s": time.perf_counter() - t0, "nodes": int(sum(r["nodes"] for r in single)),
-                           "certified": int(sum(r["status_name"] == "optimal" for r in single))}
+                       "with its automatic pop (65536 sub-cubes per iteration and problem for 10 x 8 mixtures); "
+                       "%d repeats, wall_s the median" % (n_prob, repeats)}
     ctx.mlp_set_params(learn.load(os.path.join(ROOT, "paper_1812_01232_gb300", "weights", "gosma_mlp.npz")))
-    for name, learned in (("plain_batched", None),
-                          ("learned_batched", {"beta": 1e-4, "seed": True, "active_iters": 8})):
+    walls = {"plain_single": [], "plain_batched": [], "learned_batched": []}
+    last = {}
+    for _ in range(repeats):
+        single = []
         t0 = time.perf_counter()
-        res = ctx.bnb_solve_batch(probs, eps=eps, max_seconds=120, queue_capacity=1 << 26, learned=learned)
-        out[name] = {"wall_s": time.perf_counter() - t0, "nodes": int(sum(r["nodes"] for r in res)),
+        for p in probs:
+            ctx.set_problem(p)
+            single.append(ctx.bnb_solve(eps=eps, max_seconds=60, queue_capacity=1 << 26))
+        walls["plain_single"].append(time.perf_counter() - t0)
+        last["plain_single"] = single
+        for name, learned in (("plain_batched", None),
+                              ("learned_batched", {"beta": 1e-4, "seed": True, "active_iters": 8})):
+            t0 = time.perf_counter()
+            last[name] = ctx.bnb_solve_batch(probs, eps=eps, max_seconds=120, queue_capacity=1 << 26,
+                                             learned=learned)
+            walls[name].append(time.perf_counter() - t0)
+    single = last["plain_single"]
+    for name, res in last.items():
+        out[name] = {"wall_s": float(np.median(walls[name])), "wall_s_runs": [round(w, 4) for w in walls[name]],
+                     "nodes": int(sum(r["nodes"] for r in res)),
                      "certified": int(sum(r["status_name"] == "optimal" for r in res)),
-                     "agree_with_single": int(sum(abs(r["f"] - q["f"]) <= eps * q["c22"]
-                                                  for r, q in zip(res, single))),
-                     "p50_s": float(np.median([r["seconds"] for r in res])),
-                     "shape": [res[0]["block_size"], res[0]["cubes_per_block"]], "tunings": res[0]["tunings"]}
+                     "median_dstar_iteration": float(np.median([r["dstar_iteration"] for r in res]))}
+        if name != "plain_single":
+            out[name].update({
+                "agree_with_single": int(sum(abs(r["f"] - q["f"]) <= eps * q["c22"] for r, q in zip(res, single))),
+                "p50_s": float(np.median([r["seconds"] for r in res])),
+                "shape": [res[0]["block_size"], res[0]["cubes_per_block"]], "tunings": res[0]["tunings"]})
     ctx.close()
     return out
 
 
-def run_psi_r_point(n_prob):
+def run_psi_r_point(n_prob, repeats=3):
     """The same tiny problems solved to the certified optimum with the
     point-independent and the point-dependent rotation uncertainty angle
-    (Lemma 2; gosma_set_psi_r_mode), single-problem solver, automatic pop."""
+    (Lemma 2; gosma_set_psi_r_mode), single-problem solver, automatic pop,
+    `repeats` times each (wall_s the median)."""
     from paper_1812_01232_gb300 import synth
     from paper_1812_01232_gb300.gosma import Gosma
     ctx = Gosma(0)
     probs = [synth.tiny_problem(200000 + s) for s in range(n_prob)]
     out = {"workload": "%d tiny problems (10 x 8 components), eps 1e-3, queue 2^26, automatic pop, single-problem "
-                       "solver" % n_prob}
-    for name, point in (("cube", False), ("point", True)):
-        ctx.set_psi_r_mode(point)
-        res = []
-        t0 = time.perf_counter()
-        for p in probs:
-            ctx.set_problem(p)
-            res.append(ctx.bnb_solve(eps=1e-3, max_seconds=60, queue_capacity=1 << 26))
-        out[name] = {"wall_s": time.perf_counter() - t0, "nodes": int(sum(r["nodes"] for r in res)),
-                     "certified": int(sum(r["status_name"] == "optimal" for r in res)),
-                     "f": [r["f"] for r in res]}
+                       "solver; %d repeats, wall_s the median" % (n_prob, repeats)}
+    walls = {"cube": [], "point": []}
+    for _ in range(repeats):
+        for name, point in (("cube", False), ("point", True)):
+            ctx.set_psi_r_mode(point)
+            res = []
+            t0 = time.perf_counter()
+            for p in probs:
+                ctx.set_problem(p)
+                res.append(ctx.bnb_solve(eps=1e-3, max_seconds=60, queue_capacity=1 << 26))
+            walls[name].append(time.perf_counter() - t0)
+            out[name] = {"nodes": int(sum(r["nodes"] for r in res)),
+                         "certified": int(sum(r["status_name"] == "optimal" for r in res)),
+                         "f": [r["f"] for r in res]}
+    ctx.set_psi_r_mode(False)
+    for name in walls:
+        out[name]["wall_s"] = float(np.median(walls[name]))
+        out[name]["wall_s_runs"] = [round(w, 4) for w in walls[name]]
     ctx.close()
     out["node_ratio"] = out["point"]["nodes"] / max(1, out["cube"]["nodes"])
     return out
@@ -599,8 +636,8 @@ def run_psi_r_point(n_prob):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=150.0,

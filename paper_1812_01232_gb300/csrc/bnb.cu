@@ -228,8 +228,10 @@ __global__ void cube_prep_children(Domain dom, const Node *__restrict__ parents,
     Node ch = child_of(p, c & 7, split_rotation(p));
     CubeGeom g;
     decode(ch, dom, g);
-    cube_prepare(g.r0, g.rhw, g.t0, g.thw, prep[c], point != 0);
+    cube_prepare(g.r0, g.rhw, g.t0, g.thw, prep[c], point ? prep_point(prep, 8 * np, c) : nullptr);
 }
+
+constexpr int CHILD_RUN = 4;  // children per work item (a divisor of 8)
 
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK)
@@ -242,10 +244,18 @@ __global__ void __launch_bounds__(BLOCK)
     __shared__ int slot;
     SmemArrays sm = carve(smem_f, mx.n1, mx.n2);
     const double inf = __longlong_as_double(0x7ff0000000000000LL);
-    for (int c = next_cube(counter, &slot); c < 8 * np; c = next_cube(counter, &slot)) {
+    // work in quarters of a parent's children (CHILD_RUN siblings): after a
+    // rotation split the siblings share the parent's cuboid, so the rows of
+    // the first serve the others
+    for (int g = next_cube(counter, &slot); g < 8 * np / CHILD_RUN; g = next_cube(counter, &slot))
+#pragma unroll 1
+    for (int k = 0; k < CHILD_RUN; ++k) {
+        const int c = CHILD_RUN * g + k;
         // a child keeps its parent's cuboid, and so its self sums, after a rotation split
-        const bool need_self = !(parents[c >> 3].flags & 1u) || !split_rotation(parents[c >> 3]);
-        cube_bounds<BLOCK>(mx, prep[c], zeta2, need_self, cs, sm, sums);
+        const bool rot = split_rotation(parents[c >> 3]);
+        const bool need_self = !(parents[c >> 3].flags & 1u) || !rot;
+        cube_bounds<BLOCK>(mx, prep[c], prep_point(prep, 8 * np, c), zeta2, need_self, cs, sm, sums, 0, threadIdx.x,
+                           k > 0 && !need_self);
         if (threadIdx.x == 0) {
             const Node p = parents[c >> 3];
             Node ch = child_of(p, c & 7, split_rotation(p));
@@ -515,7 +525,7 @@ static int alloc_state(gosma_ctx *ctx, unsigned long long cap, int pop, BnbState
     ALLOC(s->total, sizeof(unsigned long long));
     ALLOC(s->st, sizeof(Status));
     ALLOC(s->kid_rot, 2 * sizeof(unsigned int));
-    ALLOC(s->rot, sizeof(CubePrep) * 8 * pop);
+    ALLOC(s->rot, 2 * sizeof(CubePrep) * 8 * pop);  // cube records, then the point-dependent ones
 #undef ALLOC
     if (e == cudaSuccess) e = cudaMallocHost((void **)&s->h_st, sizeof(Status));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&s->h_flags, sizeof(unsigned int));
@@ -539,7 +549,7 @@ static int launch_children(gosma_ctx *ctx, const Domain &dom, BnbState *s, int n
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BLOCK, smem);
     if (e != cudaSuccess || per_sm < 1) return fail(ctx, GOSMA_ECUDA, "children kernel does not fit");
     long long grid = (long long)ctx->sm_count * per_sm;
-    if (grid > 8LL * np) grid = 8LL * np;
+    if (grid > 8LL * np / CHILD_RUN) grid = 8LL * np / CHILD_RUN;
     e = cudaMemsetAsync(s->kid_rot, 0, 2 * sizeof(unsigned int), ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "memset(children)");
     cube_prep_children<<<(8 * np + 127) / 128, 128, 0, ctx->stream>>>(dom, s->parents, np, s->rot, ctx->mix.psi_point);

@@ -10,7 +10,9 @@ namespace gosma {
 // Pre-pass: one thread per cube.
 __global__ void cube_prep_cubes(const gosma_cube *__restrict__ cubes, int n, CubePrep *__restrict__ prep, int point) {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < n) cube_prepare(cubes[c].r0, cubes[c].r_hw, cubes[c].t0, cubes[c].t_hw, prep[c], point != 0);
+    if (c < n)
+        cube_prepare(cubes[c].r0, cubes[c].r_hw, cubes[c].t0, cubes[c].t_hw, prep[c],
+                     point ? prep_point(prep, n, c) : nullptr);
 }
 
 // The self terms of Theorem 1 depend only on the translation cuboid, so
@@ -89,7 +91,7 @@ __global__ void __launch_bounds__(BLOCK) eval_bounds_kernel(MixDev mx, const gos
     for (int c = next_cube(counter, &slot); c < n; c = next_cube(counter, &slot)) {
         const int o = owner ? owner[c] : c;
         if ((o != c) != (pass == 1)) continue;  // block-uniform
-        cube_bounds<BLOCK>(mx, prep[c], zeta2, o == c, cs, sm, sums);
+        cube_bounds<BLOCK>(mx, prep[c], prep_point(prep, n, c), zeta2, o == c, cs, sm, sums);
         if (threadIdx.x == 0) {
             if (o != c) {  // written by the owner in pass 0
                 sums.self_lb = out[o].self_lb;
@@ -120,8 +122,9 @@ int bounds_block_size(int n1, int n2) {
     return b;
 }
 
-// The per-cube pre-pass records are followed by the work counter.
-static size_t rot_counter_offset(int n) { return sizeof(CubePrep) * (size_t)n; }
+// The per-cube pre-pass records (cube records, then the point-dependent
+// ones) are followed by the work counter.
+static size_t rot_counter_offset(int n) { return 2 * sizeof(CubePrep) * (size_t)n; }
 
 template <int BLOCK>
 static int launch_t(gosma_ctx *ctx, const gosma_cube *d_cubes, int n, gosma_bound *d_out, const CubePrep *d_rot,

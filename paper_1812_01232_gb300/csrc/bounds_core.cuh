@@ -38,9 +38,11 @@ namespace gosma {
 // the FP64 comparison (ties split rotation).
 constexpr float PSI_PI_F = 3.14159250f;
 
-// Per-cube data written by the pre-pass (208 bytes): the rotation and the
-// translation cuboid as double-floats, and the terms of the point-dependent
-// rotation uncertainty angle.
+// Per-cube data written by the pre-pass (144 bytes): the rotation and the
+// translation cuboid as double-floats.  The terms of the point-dependent
+// rotation uncertainty angle are a record of the same size in a second
+// array, n records after the first (n = the records of the call), written
+// and read only in that mode.
 struct CubePrep {
     float Rh[9], Rl[9];  // R_r0 (row-major)
     float th[3], tl[3];  // t0
@@ -49,21 +51,32 @@ struct CubePrep {
     float psi_r;
     int infeasible;      // rotation cube wholly outside the pi-ball
     float pad[2];
-    // point-dependent psi_r (Lemma 2), from the images c_k = J_r(r0) d_k / 2 of
-    // four vertices d_k = (+-h, +-h, h) of the rotation cube (the other four are
-    // their negatives): pj[8k .. 8k+2] c_k (hi), pj[8k+3 .. 8k+5] c_k (lo),
-    // pj[8k+6], pj[8k+7] |c_k|^2 (hi, lo); pj[32] 3 h^2 / 8 and pj[33]
-    // 64 u^2 max_k |c_k| (both rounded up); pj[34..35] padding
+};
+// point-dependent psi_r (Lemma 2), from the images c_k = J_r(r0) d_k / 2 of
+// four vertices d_k = (+-h, +-h, h) of the rotation cube (the other four are
+// their negatives): pj[8k .. 8k+2] c_k (hi), pj[8k+3 .. 8k+5] c_k (lo),
+// pj[8k+6], pj[8k+7] |c_k|^2 (hi, lo); pj[32] 3 h^2 / 8 and pj[33]
+// 64 u^2 max_k |c_k| (both rounded up); pj[34..35] padding
+struct CubePrepPoint {
     float pj[36];
 };
-static_assert(sizeof(CubePrep) == 288, "CubePrep layout");
+static_assert(sizeof(CubePrep) == 144 && sizeof(CubePrepPoint) == sizeof(CubePrep), "CubePrep layout");
 constexpr int PREP_WORDS = sizeof(CubePrep) / 4;
-constexpr int PREP_WORDS_CUBE = offsetof(CubePrep, pj) / 4;  // without the point-dependent terms
+constexpr int PREP_POINT_WORDS = sizeof(CubePrepPoint) / 4;
+// the point-dependent record of cube c of n: the second array
+__device__ __forceinline__ CubePrepPoint *prep_point(CubePrep *prep, int n, int c) {
+    return reinterpret_cast<CubePrepPoint *>(prep + n) + c;
+}
+__device__ __forceinline__ const CubePrepPoint *prep_point(const CubePrep *prep, int n, int c) {
+    return reinterpret_cast<const CubePrepPoint *>(prep + n) + c;
+}
 
 // shared-memory scalars of one cube
 struct CubeShared {
     CubePrep rot;
-    int infeasible;         // no feasible pose in the cube
+    CubePrepPoint rotp;
+    int infeasible;         // no feasible pose in the cube: the rotation cube ...
+    int cub_infeasible;     // ... or the translation cuboid (every point within zeta of a mean)
     int centre_infeasible;  // t0 within zeta of a mean
     unsigned spsi_max;      // max over i of sin(psi_t,i / 2), as float bits
     float red[8][32];       // block reduction: 4 double-float sums x warps
@@ -130,7 +143,7 @@ __device__ inline int pow2ceil(int x) {
 // angle(R_r p, R_r0 p) <= |r - r0| <= sqrt(3) r_hw capped at pi, and the
 // translation cuboid split into double-floats.
 __device__ inline void cube_prepare(const double r0[3], double rhw, const double t0[3], const double thw[3],
-                                    CubePrep &o, bool point) {
+                                    CubePrep &o, CubePrepPoint *pt) {
     double th2 = r0[0] * r0[0] + r0[1] * r0[1] + r0[2] * r0[2];
     double th = sqrt(th2), A, B;
     if (th < 1e-8) {
@@ -165,7 +178,7 @@ __device__ inline void cube_prepare(const double r0[3], double rhw, const double
         split_double(thw[k], o.wh[k], o.wl[k]);
     }
     o.pad[0] = o.pad[1] = 0.f;
-    if (!point) return;  // the point-dependent terms below are read only in that mode
+    if (!pt) return;  // the point-dependent terms below are read only in that mode
     // right Jacobian J_r(r0) = I - B [r0]x + C [r0]x^2, C = (|r0| - sin|r0|) / |r0|^3
     // (R_{r0 + d} = R_r0 R_{J_r d} to first order), and the vertex images J_r d / 2
     const double C = th < 1e-6 ? 1.0 / 6.0 - th2 / 120.0 : (th - A * th) / (th2 * th);
@@ -183,15 +196,15 @@ __device__ inline void cube_prepare(const double r0[3], double rhw, const double
         double n2 = 0.0;
         for (int p = 0; p < 3; ++p) {
             double c = 0.5 * (J[3 * p] * d[0] + J[3 * p + 1] * d[1] + J[3 * p + 2] * d[2]);
-            split_double(c, o.pj[8 * k + p], o.pj[8 * k + 3 + p]);
+            split_double(c, pt->pj[8 * k + p], pt->pj[8 * k + 3 + p]);
             n2 += c * c;
         }
-        split_double(n2, o.pj[8 * k + 6], o.pj[8 * k + 7]);
+        split_double(n2, pt->pj[8 * k + 6], pt->pj[8 * k + 7]);
         cmax = fmax(cmax, sqrt(n2));
     }
-    o.pj[32] = __double2float_ru(0.375 * rhw * rhw);
-    o.pj[33] = __double2float_ru(64.0 * 0x1p-48 * cmax);
-    o.pj[34] = o.pj[35] = 0.f;
+    pt->pj[32] = __double2float_ru(0.375 * rhw * rhw);
+    pt->pj[33] = __double2float_ru(64.0 * 0x1p-48 * cmax);
+    pt->pj[34] = pt->pj[35] = 0.f;
 }
 
 // Lemma 2, point-dependent form, for one model direction v (the unit vector
@@ -211,7 +224,7 @@ __device__ inline void cube_prepare(const double r0[3], double rhw, const double
 // The cosine sqrt(1 - s^2) is formed the same way and rounded down (0 where
 // it is below 1/16, i.e. psi_r above 172 degrees).  Cr, Sr (the
 // point-independent pair) are replaced when the bound is smaller.
-__device__ __forceinline__ void point_psi_r(const CubePrep &P, df vx, df vy, df vz, float &Cr, float &Sr) {
+__device__ __forceinline__ void point_psi_r(const CubePrepPoint &P, df vx, df vy, df vz, float &Cr, float &Sr) {
     const float U2 = GOSMA_U * GOSMA_U;
     // read at every call: loads hoisted out of the row loop would hold the
     // 36 words in registers across the pair loops
@@ -272,17 +285,25 @@ __device__ __forceinline__ float gZ(float x) { return 1.f - ex2a(-2.f * GOSMA_LO
 //  * the half-angle sine/cosine of s = psi_t + psi_r (row constants, evaluated
 //    in double-float, rounded once) carry <= u relative;
 //  * hence sin(B/2) = sin(theta/2) cos(s/2) - cos(theta/2) sin(s/2) is off by
-//    at most 7.5u (sin(theta/2) + sin(s/2)) =: es; cos(B/2) is bounded from
-//    the sine bounds as sqrt(1 - sin^2) (one rounding, sqrt 2u: 3u);
-//  * K from above/below: 4u (sqrt 2u, K^2 2u);
-//  * the exponent K - k1 - k2 (log2 units) carries <= 11u relative, and
+//    at most 7.5u (sin(theta/2) + sin(s/2)) =: es; cos(B/2) enters only
+//    squared (in K and in cos B = 2 cos^2(B/2) - 1), bounded from the sine
+//    bounds as 1 - sin^2 (one rounding of the fused s^2 - 1: no square
+//    root);
+//  * K: 3.5u (sqrt 2u, K^2 2.5u); the self pair rounds its K bounds outward
+//    by 4u and 5u, the cross pair leaves them to the slacks below;
+//  * the exponent K - k1 - k2 (log2 units) carries <= 11u relative (15u in
+//    the cross pair, whose K and cos^2 are not rounded outward), and
 //    rounding the ex2 argument adds 0.5u of it: the argument moves by
-//    12u |exponent| in the safe direction;
+//    12u |exponent| (cross pair 16u) in the safe direction;
 //  * the factor outside the exponential: ex2 3u, rcp 2u, four products 4u,
 //    one sum 1u: 10u relative = 14.4u in log2 units (TERM_SLACK);
 //  * row weights, chunk sums (CHUNK-1 terms, plain FP32) and compensated row
 //    sums: applied once per row with directed rounding.
 #define GOSMA_TERM_SLACK (15.f * GOSMA_U)
+// The cross pair's term slack: GOSMA_TERM_SLACK and the smallest K's
+// rounding without an outward factor (3.5u relative in g(K)/K: 5u in log2
+// units).
+#define GOSMA_CROSS_SLACK (20.f * GOSMA_U)
 constexpr int CHUNK = 8;
 
 struct RowCross {
@@ -291,13 +312,13 @@ struct RowCross {
 };
 
 // The row constants of RowCross in both lanes of packed pairs, for
-// cross_pair2.  nSs = -Ss (negation is exact).
+// cross_pair2.  nSs = -Ss, nA4 = -A4 (negation is exact).
 struct RowCross2 {
     float2 vx, vy, vz, wx, wy, wz;
-    float2 a, b, k0, Cs, nSs, esS, A4;
+    float2 a, b, k0, Cs, nSs, esS, nA4;
     __device__ __forceinline__ explicit RowCross2(const RowCross &R)
         : vx(bc2(R.vx)), vy(bc2(R.vy)), vz(bc2(R.vz)), wx(bc2(R.wx)), wy(bc2(R.wy)), wz(bc2(R.wz)), a(bc2(R.a)),
-          b(bc2(R.b)), k0(bc2(R.k0)), Cs(bc2(R.Cs)), nSs(bc2(-R.Ss)), esS(bc2(R.esS)), A4(bc2(R.A4)) {}
+          b(bc2(R.b)), k0(bc2(R.k0)), Cs(bc2(R.Cs)), nSs(bc2(-R.Ss)), esS(bc2(R.esS)), nA4(bc2(-R.A4)) {}
 };
 
 __device__ __forceinline__ float2 sqrt2a(float2 x) { return make_float2(sqrta(x.x), sqrta(x.y)); }
@@ -312,8 +333,8 @@ __device__ __forceinline__ float2 ex2_2a(float2 x) { return make_float2(ex2a(x.x
 // scalar FP32 operation would be (the error budget above holds per lane).
 //   |v -+ u|^2 from double-float directions, the centre term in the linear
 //   form above, then the bound: B = max(0, theta - s), s = psi_t,i + psi_r
-//   (Cs, Ss = cos, sin of s/2); cos(B/2) from the sine bounds as
-//   sqrt(1 - s^2) (one rounding of 1 - s^2, sqrt 2u); K(a) - a - k2 with the
+//   (Cs, Ss = cos, sin of s/2); cos^2(B/2) from the sine bounds as
+//   1 - s^2 (one rounding of 1 - s^2, 2u outward); K(a) - a - k2 with the
 //   smallest sine and the largest K; the smallest K over kappa_1 in [a, b]
 //   (minimiser -k2 cos B, clamped), from below; g(K)/K <= min(1/K, 2).
 // Forms chosen for the packed instructions, exact rewritings: 1 - s^2 is
@@ -349,25 +370,24 @@ __device__ __forceinline__ void cross_pair2(const RowCross2 &R, float4 P0, float
     const float2 es = fma2(bc2(7.5f * U), sth, R.esS);
     const float2 slo = max2(sub2(sB, es), 0.f);
     const float2 shi = min2(add2(max2(sB, 0.f), es), 1.f);
+    // cos^2(B/2) = 1 - sin^2(B/2) from the sine bounds, as -q with q = s^2 - 1
+    // rounded once (q < 0: both sines stay below 1).  No outward factor on
+    // the cosines or on K: their roundings (K within 3.5u) are covered by the
+    // exponent's relative slack (16u) and the term slack (20u).
     const float2 q1 = fma2(slo, slo, bc2(-1.f)), q2 = fma2(shi, shi, bc2(-1.f));
-    const float2 chi = min2(mul2(make_float2(sqrta(-q1.x), sqrta(-q1.y)), bc2(1.f + 3.f * U)), 1.f);
-    const float2 clo =
-        mul2(make_float2(sqrta(-fminf(q2.x, 0.f)), sqrta(-fminf(q2.y, 0.f))), bc2(1.f - 3.f * U));
-    const float2 ak4 = mul2(R.A4, k2);
+    const float2 nak4 = mul2(R.nA4, k2);  // -4 a k2
     const float2 dka = sub2(R.a, k2);
-    const float2 Khi = mul2(sqrt2a(fma2(dka, dka, mul2(ak4, mul2(chi, chi)))), bc2(1.f + 4.f * U));
-    const float2 cosBlo = fma2(mul2(bc2(2.f), clo), clo, bc2(-1.f));
-    const float2 kc = mul2(k2, cosBlo);
-    const float2 ks = make_float2(fminf(fmaxf(-kc.x, R.a.x), R.b.x), fminf(fmaxf(-kc.y, R.a.y), R.b.y));
+    const float2 Khi = sqrt2a(fma2(nak4, q1, mul2(dka, dka)));
+    const float2 nkc = mul2(k2, fma2(bc2(2.f), q2, bc2(1.f)));  // -k2 cos B
+    const float2 ks = make_float2(fminf(fmaxf(nkc.x, R.a.x), R.b.x), fminf(fmaxf(nkc.y, R.a.y), R.b.y));
     const float2 dks = sub2(ks, k2);
-    const float2 Kmin =
-        mul2(sqrt2a(fma2(dks, dks, mul2(mul2(mul2(bc2(4.f), ks), k2), mul2(clo, clo)))), bc2(1.f - 4.f * U));
+    const float2 Kmin = sqrt2a(fma2(mul2(mul2(bc2(-4.f), ks), k2), q2, mul2(dks, dks)));
     const float2 den = add2(add2(R.a, k2), Khi);
     const float2 Kc = max2(Kmin, 1e-20f);
     const float2 r = rcp2a(mul2(den, Kc));
-    const float2 DL = mul2(mul2(mul2(ak4, mul2(slo, slo)), mul2(Kc, r)), bc2(-GOSMA_LOG2E));
+    const float2 DL = mul2(mul2(mul2(nak4, mul2(slo, slo)), mul2(Kc, r)), bc2(GOSMA_LOG2E));
     const float2 w = min2(mul2(den, r), 2.f);
-    const float2 arg = fma2(bc2(-12.f * U), DL, add2(DL, bc2(GOSMA_TERM_SLACK)));
+    const float2 arg = fma2(bc2(-16.f * U), DL, add2(DL, bc2(GOSMA_CROSS_SLACK)));
     pl = fma2(ex2_2a(arg), mul2(w, Q), pl);
 }
 
@@ -392,8 +412,9 @@ struct RowSelf2 {
 // multipliers; per lane as a scalar FP32 evaluation would round.
 //   The bound: A = min(pi, theta + psi_i + psi_m), the half-angle pair of
 //   (psi_i + psi_m)/2 formed here in FP32 (2u each): sin(A/2) carries
-//   <= 9.5u (sin(theta/2) + sin(psi/2)), cos(A/2) <= 14u; cos(A/2) from the
-//   sine bounds (A/2 <= pi/2); K(b_i, b_m) - b_i - b_m with the largest sine
+//   <= 9.5u (sin(theta/2) + sin(psi/2)), cos(A/2) <= 14u; cos^2(A/2) from
+//   the sine bounds as 1 - sin^2 (A/2 <= pi/2; one rounding, 2u outward);
+//   K(b_i, b_m) - b_i - b_m with the largest sine
 //   and the smallest K; the largest K over the four corners of
 //   [a_i, b_i] x [a_m, b_m], from above; g(K)/K from below: >= 2 - 2K for
 //   small K, g rounded with <= 64u error otherwise.
@@ -434,15 +455,13 @@ __device__ __forceinline__ void self_pair2(const RowSelf2 &R, float4 P0, float4 
     const float2 t1 = add2(sA, es);
     const float2 shi = make_float2(cA.x <= 16.f * U ? 1.f : fminf(t1.x, 1.f), cA.y <= 16.f * U ? 1.f : fminf(t1.y, 1.f));
     const float2 slo = max2(sub2(sA, es), 0.f);
+    // cos^2(A/2) bounds as in cross_pair2
     const float2 q2 = fma2(shi, shi, bc2(-1.f)), q1 = fma2(slo, slo, bc2(-1.f));
-    const float2 clo =
-        mul2(make_float2(sqrta(-fminf(q2.x, 0.f)), sqrta(-fminf(q2.y, 0.f))), bc2(1.f - 3.f * U));
-    const float2 chi = min2(mul2(make_float2(sqrta(-q1.x), sqrta(-q1.y)), bc2(1.f + 3.f * U)), 1.f);
+    const float2 clo2 = mul2(q2, bc2(-(1.f - 2.f * U))), chi2 = mul2(q1, bc2(-(1.f + 2.f * U)));
     const float2 bb = mul2(R.b, bm);
     const float2 dbb = sub2(R.b, bm);
-    const float2 Klo =
-        mul2(sqrt2a(fma2(dbb, dbb, mul2(mul2(bc2(4.f), bb), mul2(clo, clo)))), bc2(1.f - 4.f * U));
-    const float2 c4 = mul2(bc2(4.f), mul2(chi, chi));
+    const float2 Klo = mul2(sqrt2a(fma2(dbb, dbb, mul2(mul2(bc2(4.f), bb), clo2))), bc2(1.f - 4.f * U));
+    const float2 c4 = mul2(bc2(4.f), chi2);
     const float2 q1a = sub2(R.a, am), q2a = sub2(R.a, bm), q3a = sub2(R.b, am);
     const float2 ca = mul2(c4, R.a), cb = mul2(c4, R.b);
     const float2 e1 = fma2(q1a, q1a, mul2(ca, am));
@@ -532,19 +551,30 @@ __device__ __forceinline__ int next_cube(int *counter, int *slot) {
 // group gid of the block, gtid its thread) must call it with the same cube,
 // its own CubeShared and shared arrays; sums are valid in the group's thread
 // 0 on return.  need_self = 0 skips the self pairs (the caller reuses cached
-// self sums).
+// self sums).  reuse_rows = 1 skips the model rows (phase 1b): the group's
+// previous call was for a cube of the same mixtures and the same translation
+// cuboid (a sibling after a rotation split), and neither call needs its self
+// sums; the rows, the cuboid's feasibility flags and psi_t max depend on the
+// cuboid alone.
 template <int BLOCK, int GT = BLOCK>
-__device__ void cube_bounds(const MixDev &mx, const CubePrep &prep, df zeta2, bool need_self, CubeShared &cs,
-                            const SmemArrays &sm, CubeSums &out, int gid = 0, int gtid = threadIdx.x) {
+__device__ void cube_bounds(const MixDev &mx, const CubePrep &prep, const CubePrepPoint *pt, df zeta2, bool need_self,
+                            CubeShared &cs, const SmemArrays &sm, CubeSums &out, int gid = 0,
+                            int gtid = threadIdx.x, bool reuse_rows = false) {
     const int tid = gtid;
     const int n1 = mx.n1, n2 = mx.n2;
     const float U = GOSMA_U;
-    for (int k = tid; k < (mx.psi_point ? PREP_WORDS : PREP_WORDS_CUBE); k += GT)
+    for (int k = tid; k < PREP_WORDS; k += GT)
         reinterpret_cast<float *>(&cs.rot)[k] = reinterpret_cast<const float *>(&prep)[k];
+    if (mx.psi_point)
+        for (int k = tid; k < PREP_POINT_WORDS; k += GT)
+            reinterpret_cast<float *>(&cs.rotp)[k] = reinterpret_cast<const float *>(pt)[k];
     if (tid == 0) {
         cs.infeasible = prep.infeasible;
-        cs.centre_infeasible = 0;
-        cs.spsi_max = 0u;
+        if (!reuse_rows) {
+            cs.cub_infeasible = 0;
+            cs.centre_infeasible = 0;
+            cs.spsi_max = 0u;
+        }
     }
     gsync<BLOCK, GT>(gid);
 
@@ -574,7 +604,7 @@ __device__ void cube_bounds(const MixDev &mx, const CubePrep &prep, df zeta2, bo
     Acc dsl, dsu;  // diagonal self terms of this thread
     dsl.zero();
     dsu.zero();
-    for (int i = tid; i < n1; i += GT) {
+    for (int i = reuse_rows ? n1 : tid; i < n1; i += GT) {
         df c[3], w[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -595,7 +625,7 @@ __device__ void cube_bounds(const MixDev &mx, const CubePrep &prep, df zeta2, bo
             e2 = fmaf(e, e, e2);
             f2 = fmaf(f, f, f2);
         }
-        if (f2 * (1.f + 8.f * U) < zeta2.h) atomicOr(&cs.infeasible, 1);
+        if (f2 * (1.f + 8.f * U) < zeta2.h) atomicOr(&cs.cub_infeasible, 1);
         float is2 = mx.inv_sig2[i];
         // kappa range over the feasible part of the cuboid (nearest point clamped to
         // zeta); each end carries <= 6u (distance 1u, squares and sums 4u, fma 1u)
@@ -695,7 +725,8 @@ __device__ void cube_bounds(const MixDev &mx, const CubePrep &prep, df zeta2, bo
     df T[4] = {fast_two_sum(dsl.s, dsl.c), {0.f, 0.f}, fast_two_sum(dsu.s, dsu.c), {0.f, 0.f}};
     T[0] = df_scale(T[0].h, T[0].l, 1.f - 3.f * U);
 
-    if (!cs.infeasible) {
+    const bool infeasible = cs.infeasible || cs.cub_infeasible;
+    if (!infeasible) {
         // ---------------- phase 2a: cross pairs
         const int Ti = n1 >= GT ? GT : pow2ceil(n1);
         const int Tj = GT / Ti;
@@ -715,7 +746,7 @@ __device__ void cube_bounds(const MixDev &mx, const CubePrep &prep, df zeta2, bo
             R.b = mp_at(sm, i, MP_B);
             R.k0 = mp_at(sm, i, MP_K0);
             R.A4 = 4.f * R.a;
-            if (mx.psi_point) point_psi_r(cs.rot, df{R.vx, R.wx}, df{R.vy, R.wy}, df{R.vz, R.wz}, Cr, Sr);
+            if (mx.psi_point) point_psi_r(cs.rotp, df{R.vx, R.wx}, df{R.vy, R.wy}, df{R.vz, R.wz}, Cr, Sr);
             const float cps = mp_at(sm, i, MP_CP), sps = mp_at(sm, i, MP_SP);
             // s = psi_t,i + psi_r as half-angle cosine/sine (double-float, rounded once);
             // s >= pi means B = 0 everywhere
@@ -858,7 +889,7 @@ __device__ void cube_bounds(const MixDev &mx, const CubePrep &prep, df zeta2, bo
         out.psi_r = cs.rot.psi_r;
         float smax = __uint_as_float(cs.spsi_max);
         out.psi_t_max = smax >= 1.f ? PSI_PI_F : fminf(2.f * asinf(smax), PSI_PI_F);
-        out.feasible = !cs.infeasible;
+        out.feasible = !infeasible;
         out.centre_feasible = !cs.centre_infeasible;
     }
     gsync<BLOCK, GT>(gid);

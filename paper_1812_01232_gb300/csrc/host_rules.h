@@ -70,22 +70,35 @@ inline int bound_shape_candidates(int wide, size_t group_bytes, BoundShape out[1
 
 // The autotuner's choice from a timing table: ms[c * reps + k] is the k-th
 // timed launch of candidate c (after one untimed warm launch).  The
-// candidate with the smallest median wins, ties to the earlier candidate.
-inline int pick_shape(const float *ms, int ncand, int reps) {
+// candidate with the smallest median wins, ties to the earlier candidate;
+// but the preferred candidate pref (the default shape; -1: none) stays
+// unless the winner's median is more than PICK_MARGIN below its own (the
+// timings sample a sixteenth of the work, so small differences are noise).
+constexpr float PICK_MARGIN = 0.03f;
+inline int pick_shape(const float *ms, int ncand, int reps, int pref = -1) {
     int best = -1;
-    float best_med = 0.f;
+    float best_med = 0.f, pref_med = 0.f;
     for (int c = 0; c < ncand; ++c) {
         float v[16];
         const int r = reps < 16 ? reps : 16;
         for (int k = 0; k < r; ++k) v[k] = ms[c * reps + k];
         std::sort(v, v + r);
         const float med = r % 2 ? v[r / 2] : 0.5f * (v[r / 2 - 1] + v[r / 2]);
+        if (c == pref) pref_med = med;
         if (best < 0 || med < best_med) {
             best = c;
             best_med = med;
         }
     }
+    if (pref >= 0 && pref < ncand && best != pref && best_med > (1.f - PICK_MARGIN) * pref_med) return pref;
     return best;
+}
+
+// The stride of the autotuner's sample: every stride-th run of four sibling
+// children (a sixteenth of the work), but at least 16 runs per SM.
+inline int tune_stride(long long nkid, int sm_count) {
+    long long s = nkid / (64LL * sm_count);
+    return (int)(s < 1 ? 1 : s > 16 ? 16 : s);
 }
 
 // Re-tune when the unfinished problems have halved since the last tuning

@@ -561,9 +561,11 @@ __global__ void mp_prep(const ProbDev *__restrict__ P, const int *__restrict__ o
         Node ch = child_of(p, c & 7, split_rotation(p));
         CubeGeom g;
         decode(ch, P[k].dom, g);
-        cube_prepare(g.r0, g.rhw, g.t0, g.thw, prep[w], P[k].mx.psi_point != 0);
+        cube_prepare(g.r0, g.rhw, g.t0, g.thw, prep[w], P[k].mx.psi_point ? prep_point(prep, N, w) : nullptr);
     }
 }
+
+constexpr int MP_CHILD_RUN = 4;  // children per work item (a divisor of 8)
 
 // G cubes per block: groups of BLOCK / G threads (whole warps), each with its
 // own shared arrays (group_floats floats of the dynamic shared memory) and
@@ -572,7 +574,7 @@ template <int BLOCK, int G>
 __global__ void __launch_bounds__(BLOCK)
     mp_bound(const ProbDev *__restrict__ P, const int *__restrict__ off, int nprob, const Node *__restrict__ parents,
              const CubePrep *__restrict__ prep, Node *__restrict__ kids, double *__restrict__ kid_ub,
-             int *__restrict__ counter, int group_floats, int limit) {
+             int *__restrict__ counter, int group_floats, int stride) {
     constexpr int GT = BLOCK / G;
     extern __shared__ float smem_f[];
     __shared__ CubeShared cs[G];
@@ -581,16 +583,24 @@ __global__ void __launch_bounds__(BLOCK)
     const int gid = threadIdx.x / GT, gtid = threadIdx.x % GT;
     float *my_smem = smem_f + (size_t)gid * group_floats;
     const double inf = __longlong_as_double(0x7ff0000000000000LL);
-    const int N = min(off[nprob], limit);  // limit: the autotuner times a prefix of the children
-    for (int w = next_cube<BLOCK, GT>(counter, &slot[gid], gid, gtid); w < N;
-         w = next_cube<BLOCK, GT>(counter, &slot[gid], gid, gtid)) {
+    const int N = off[nprob];
+    // work in runs of MP_CHILD_RUN siblings (offsets are multiples of 8, so a
+    // run never crosses a parent): after a rotation split the siblings share
+    // the parent's cuboid, so the rows of the first serve the others.  stride
+    // > 1 (the autotuner's timings) takes every stride-th run only.
+    for (int g = stride * next_cube<BLOCK, GT>(counter, &slot[gid], gid, gtid); MP_CHILD_RUN * g < N;
+         g = stride * next_cube<BLOCK, GT>(counter, &slot[gid], gid, gtid))
+#pragma unroll 1
+    for (int r = 0; r < MP_CHILD_RUN && MP_CHILD_RUN * g + r < N; ++r) {
+        const int w = MP_CHILD_RUN * g + r;
         const int k = mp_find(off, nprob, w), c = w - off[k];
         const MixDev &mx = P[k].mx;
         SmemArrays sm = carve(my_smem, mx.n1, mx.n2);
         const Node &pr = parents[w >> 3];
         const bool rot = split_rotation(pr);
         const bool need_self = !(pr.flags & 1u) || !rot;
-        cube_bounds<BLOCK, GT>(mx, prep[w], P[k].zeta2, need_self, cs[gid], sm, sums[gid], gid, gtid);
+        cube_bounds<BLOCK, GT>(mx, prep[w], prep_point(prep, off[nprob], w), P[k].zeta2, need_self, cs[gid], sm,
+                               sums[gid], gid, gtid, r > 0 && !need_self);
         if (gtid == 0) {
             const CubeSums &su = sums[gid];
             const Node p = pr;
@@ -1145,7 +1155,7 @@ struct MultiBuffers {
 template <int BLOCK, int G>
 static cudaError_t mp_bound_launch(gosma_ctx *ctx, cudaStream_t st, const ProbDev *P, const int *off, int nprob,
                                    const Node *parents, const CubePrep *prep, Node *kids, double *kid_ub, int *counter,
-                                   size_t smem, int limit) {
+                                   size_t smem, int stride) {
     auto kern = mp_bound<BLOCK, G>;
     const size_t group = (smem + 15) & ~(size_t)15;  // each group's arrays start on a 16-byte boundary
     const size_t total = group * G;
@@ -1158,7 +1168,7 @@ static cudaError_t mp_bound_launch(gosma_ctx *ctx, cudaStream_t st, const ProbDe
     e = cudaMemsetAsync(counter, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
     kern<<<ctx->sm_count * per_sm, BLOCK, total, st>>>(P, off, nprob, parents, prep, kids, kid_ub, counter,
-                                                        (int)(group / sizeof(float)), limit);
+                                                        (int)(group / sizeof(float)), stride);
     ++ctx->launches;
     return cudaGetLastError();
 }
@@ -1166,10 +1176,10 @@ static cudaError_t mp_bound_launch(gosma_ctx *ctx, cudaStream_t st, const ProbDe
 // The bound kernel's shapes: threads per block x cubes per block.
 static cudaError_t mp_bound_any(BoundShape shape, gosma_ctx *ctx, cudaStream_t st, const ProbDev *P, const int *off,
                                 int nprob, const Node *parents, const CubePrep *prep, Node *kids, double *kid_ub,
-                                int *counter, size_t smem, int limit = 0x7fffffff) {
+                                int *counter, size_t smem, int stride = 1) {
 #define MPB(B, G)                                                                                                     \
     if (shape.block == B && shape.cubes == G)                                                                          \
-    return mp_bound_launch<B, G>(ctx, st, P, off, nprob, parents, prep, kids, kid_ub, counter, smem, limit)
+    return mp_bound_launch<B, G>(ctx, st, P, off, nprob, parents, prep, kids, kid_ub, counter, smem, stride)
     MPB(32, 1);
     MPB(64, 1);
     MPB(64, 2);
@@ -1602,7 +1612,7 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
         (e = B.get(&Qb.c_live, max_chunks)) == cudaSuccess && (e = B.get(&Qb.c_base, max_chunks)) == cudaSuccess &&
         (e = B.get(&Qb.quota, 3)) == cudaSuccess &&  // [1]: the bound kernel's work counter, [2]: rows to score
         (e = B.get(&parents, (size_t)pop * nprob)) == cudaSuccess && (e = B.get(&kids, nkids)) == cudaSuccess &&
-        (e = B.get(&kid_ub, nkids)) == cudaSuccess && (e = B.get(&prep, nkids)) == cudaSuccess &&
+        (e = B.get(&kid_ub, nkids)) == cudaSuccess && (e = B.get(&prep, 2 * (size_t)nkids)) == cudaSuccess &&
         (e = B.get(&off, nprob + 1)) == cudaSuccess && (e = B.get(&ioff, nprob)) == cudaSuccess &&
         (e = B.get(&idata, 16 * (size_t)sum_n1)) == cudaSuccess &&
         (e = B.get(&part, 2 * (size_t)nblk * nprob)) == cudaSuccess) {
@@ -1807,8 +1817,10 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
     // caller's, or timed: every candidate is launched once untimed, then
     // TUNE_REPS times timed on the same prepared children (the bound kernel
     // only writes the children's records), and the smallest median wins
-    // (pick_shape); the timings take a prefix of the children, the chosen shape
-    // then bounds all of them.  The first tuning runs at TUNE_ITER, once the queues hold
+    // (pick_shape, which keeps the default 128 x 1 unless another shape is 3%
+    // faster); the timings take every 16th run of sibling children (all
+    // problems alike), the chosen shape then bounds all of them.  The first
+    // tuning runs at TUNE_ITER, once the queues hold
     // enough parents for a representative launch (8^5 per problem unless the
     // pop quota is smaller); the shapes are timed again whenever the
     // unfinished problems have halved since, at least RETUNE_GAP iterations
@@ -1833,19 +1845,19 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
         front();
         cudaError_t ee = cudaSuccess;
         if (tune_now && ncand > 0) {
-            // the timings run on a prefix of the iteration's children (a
-            // sixteenth, at least 64 per SM), so that tuning costs about as much
-            // as two or three launches
+            // the timings run on a sample of the iteration's children (every
+            // stride-th run of siblings: a sixteenth, at least 16 runs per SM),
+            // so that tuning costs about as much as two or three launches
             int nkid = 0;
             ee = cudaMemcpyAsync(&nkid, off + nprob, sizeof(int), cudaMemcpyDeviceToHost, st);
             if (ee == cudaSuccess) ee = cudaStreamSynchronize(st);
-            const int limit = std::max(nkid / 16, 64 * ctx->sm_count);
+            const int stride = tune_stride(nkid, ctx->sm_count);
             std::vector<float> ms((size_t)ncand * TUNE_REPS, 1e30f);
             for (int c = 0; c < ncand && ee == cudaSuccess; ++c)
                 for (int rep = 0; rep <= TUNE_REPS && ee == cudaSuccess; ++rep) {
                     cudaEventRecord(ta, st);
                     cudaError_t el = mp_bound_any(cands[c], ctx, st, dP, off, nprob, parents, prep, kids, kid_ub,
-                                                  Qb.quota + 1, smem, limit);
+                                                  Qb.quota + 1, smem, stride);
                     cudaEventRecord(tb, st);
                     if (el != cudaSuccess) {  // a shape that does not fit: never picked
                         cudaGetLastError();
@@ -1857,7 +1869,10 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
                     if (rep > 0) ms[(size_t)c * TUNE_REPS + rep - 1] = t;
                 }
             if (ee == cudaSuccess) {
-                shape = cands[pick_shape(ms.data(), ncand, TUNE_REPS)];
+                int pref = -1;
+                for (int c = 0; c < ncand; ++c)
+                    if (cands[c].block == 128 && cands[c].cubes == 1) pref = c;
+                shape = cands[pick_shape(ms.data(), ncand, TUNE_REPS, pref)];
                 ++tunings;
                 // this iteration's children from the chosen shape
                 ee = mp_bound_any(shape, ctx, st, dP, off, nprob, parents, prep, kids, kid_ub, Qb.quota + 1, smem);

@@ -88,18 +88,22 @@ def collect_certified(ctx, seeds, eps, trace_cap, cap, chunk=64):
     return np.concatenate(F), np.concatenate(L), np.concatenate(T), kept
 
 
-def evaluate_certified(ctx, params, seeds, eps, beta, active_iters, repeats, cap, rng):
+def evaluate_certified(ctx, params, seeds, eps, beta, active_iters, repeats, cap, rng, chunk=32):
     """Plain and learned batched solves of the same held-out tiny problems,
-    `repeats` times each: per problem and repeat the device time to its
-    certificate, its nodes and the iteration of its final incumbent; paired
-    learned / plain ratios with bootstrap intervals of their medians."""
+    `repeats` times each, in batches of `chunk` problems (the queues of a
+    batch are allocated together): per problem and repeat the device time to
+    its certificate, its nodes and the iteration of its final incumbent;
+    paired learned / plain ratios with bootstrap intervals of their medians."""
     probs = [synth.tiny_problem(int(s)) for s in seeds]
     ctx.mlp_set_params(params)
     runs = {"plain": [], "learned": []}
     for _ in range(repeats):
         for name, learned in (("plain", None), ("learned", dict(beta=beta, seed=True, active_iters=active_iters))):
             t0 = time.time()
-            res = ctx.bnb_solve_batch(probs, eps=eps, max_seconds=600, queue_capacity=cap, learned=learned)
+            res = []
+            for i in range(0, len(probs), chunk):
+                res += ctx.bnb_solve_batch(probs[i:i + chunk], eps=eps, max_seconds=600, queue_capacity=cap,
+                                           learned=learned)
             runs[name].append(dict(wall=time.time() - t0, res=res))
     out = {"problems": len(probs), "repeats": repeats, "beta": beta, "active_iters": active_iters}
     both = [k for k in range(len(probs))

@@ -76,6 +76,7 @@ def ex2a(x, s):
 L2E = F(1.4426950408889634)
 FU = F(U)
 SLACK = F(15) * FU
+CROSS_SLACK = F(20) * FU
 
 
 def c1(k):
@@ -158,7 +159,7 @@ def _rows(c):
 # ---------------------------------------------------------------- cross pair
 def _cross(c, s):
     """Upper bound of the cross pair (row 0, the image component) as the
-    kernel forms it, times its row factor; s: signs of the 10 approximate
+    kernel forms it, times its row factor; s: signs of the 8 approximate
     instructions on the path."""
     e, wQ, Bw = _cross_parts(c, s)
     return fma(e, wQ, np.zeros_like(wQ)).astype(np.float64) * Bw.astype(np.float64)
@@ -189,24 +190,25 @@ def _cross_parts(c, s):
     es = fma(np.full_like(sth, F(7.5) * FU), sth, esS)
     slo = np.maximum(sB - es, F(0))
     shi = np.minimum(np.maximum(sB, F(0)) + es, F(1))
-    chi = np.minimum(sqrta(fma(-slo, slo, np.ones_like(slo)), s[2]) * c1(3), F(1))
-    clo = sqrta(np.maximum(fma(-shi, shi, np.ones_like(shi)), F(0)), s[3]) * c1m(3)
-    A4 = F(4) * a
-    ak4 = A4 * k2
+    # cos^2(B/2) = -(s^2 - 1), the fused s^2 - 1 rounded once; no outward factors
+    q1 = fma(slo, slo, -np.ones_like(slo))
+    q2 = fma(shi, shi, -np.ones_like(shi))
+    assert np.all(q1 < 0) and np.all(q2 <= 0)
+    nak4 = (-(F(4) * a)) * k2
     dka = a - k2
-    Khi = sqrta(fma(dka, dka, ak4 * (chi * chi)), s[4]) * c1(4)
-    cosBlo = fma(F(2) * clo, clo, -np.ones_like(clo))
-    ks = np.minimum(np.maximum(-k2 * cosBlo, a), b)
+    Khi = sqrta(fma(nak4, q1, dka * dka), s[2])
+    nkc = k2 * fma(np.full_like(q2, F(2)), q2, np.ones_like(q2))
+    ks = np.minimum(np.maximum(nkc, a), b)
     dks = ks - k2
-    Kmin = sqrta(fma(dks, dks, F(4) * ks * k2 * (clo * clo)), s[5]) * c1m(4)
+    Kmin = sqrta(fma(F(-4) * ks * k2, q2, dks * dks), s[3])
     den = (a + k2) + Khi
     Kc = np.maximum(Kmin, F(1e-20))
-    r = rcpa(den * Kc, s[6])
-    DL = ak4 * (slo * slo) * (Kc * r) * (-L2E)
+    r = rcpa(den * Kc, s[4])
+    DL = nak4 * (slo * slo) * (Kc * r) * L2E
     w = np.minimum(den * r, F(2))
-    e = ex2a(fma(np.full_like(DL, F(12) * FU), np.abs(DL), DL + SLACK), s[7])
+    e = ex2a(fma(np.full_like(DL, F(-16) * FU), DL, DL + CROSS_SLACK), s[5])
     ph = f32(c["phi1"][:, 0])
-    Bw = np.where(b < F(9), ph * b * rcpa(gZ(b, s[8]), s[9]) * c1(12), ph * b).astype(np.float32)
+    Bw = np.where(b < F(9), ph * b * rcpa(gZ(b, s[6]), s[7]) * c1(12), ph * b).astype(np.float32)
     Bw = mul_ru(Bw, np.full_like(Bw, c1(8 + 6)))
     return e, (w * Q).astype(np.float32), Bw
 
@@ -219,7 +221,7 @@ def _aw(a, ph, s0, s1):
 
 def _self(c, s):
     """Lower bound of the self pair (0, 1), both orders, as the kernel forms
-    it with its row factors; s: signs of the 13 approximate instructions."""
+    it with its row factors; s: signs of the 11 approximate instructions."""
     e, wA, Awi = _self_parts(c, s)
     return fma(e, wA, np.zeros_like(wA)).astype(np.float64) * Awi.astype(np.float64)
 
@@ -231,8 +233,8 @@ def _self_parts(c, s):
     vh, vl = split(c["v"][:, 0])
     mh, ml = split(c["v"][:, 1])
     ph = f32(c["phi1"])
-    Am = _aw(a[:, 1], ph[:, 1], s[9], s[10]).astype(np.float32)
-    Ai = _aw(a[:, 0], ph[:, 0], s[11], s[12]).astype(np.float32)
+    Am = _aw(a[:, 1], ph[:, 1], s[7], s[8]).astype(np.float32)
+    Ai = _aw(a[:, 0], ph[:, 0], s[9], s[10]).astype(np.float32)
     d = [(vh[:, k] - mh[:, k]) + (vl[:, k] - ml[:, k]) for k in range(3)]
     p = [(vh[:, k] + mh[:, k]) + (vl[:, k] + ml[:, k]) for k in range(3)]
     x2 = fma(d[0], d[0], fma(d[1], d[1], d[2] * d[2]))
@@ -246,27 +248,27 @@ def _self_parts(c, s):
     api = cA <= F(16) * FU
     shi = np.where(api, F(1), np.minimum(sA + es, F(1))).astype(np.float32)
     slo = np.maximum(sA - es, F(0))
-    clo = sqrta(np.maximum(fma(-shi, shi, np.ones_like(shi)), F(0)), s[2]) * c1m(3)
-    chi = np.minimum(sqrta(fma(-slo, slo, np.ones_like(slo)), s[3]) * c1(3), F(1))
+    clo2 = fma(shi, shi, -np.ones_like(shi)) * (-c1m(2))
+    chi2 = fma(slo, slo, -np.ones_like(slo)) * (-c1(2))
     ai, bi, am, bm = a[:, 0], b[:, 0], a[:, 1], b[:, 1]
     bb = bi * bm
     dbb = bi - bm
-    Klo = sqrta(fma(dbb, dbb, F(4) * bb * (clo * clo)), s[4]) * c1m(4)
-    c4 = F(4) * (chi * chi)
+    Klo = sqrta(fma(dbb, dbb, F(4) * bb * clo2), s[2]) * c1m(4)
+    c4 = F(4) * chi2
     q1, q2, q3 = ai - am, ai - bm, bi - am
     e1 = fma(q1, q1, c4 * ai * am)
     e2 = fma(q2, q2, c4 * ai * bm)
     e3 = fma(q3, q3, c4 * bi * am)
     e4 = fma(dbb, dbb, c4 * bb)
-    Kmax = sqrta(np.maximum(np.maximum(e1, e2), np.maximum(e3, e4)), s[5]) * c1(5)
+    Kmax = sqrta(np.maximum(np.maximum(e1, e2), np.maximum(e3, e4)), s[3]) * c1(5)
     den = (bi + bm) + Klo
-    r = rcpa(den * Kmax, s[6])
+    r = rcpa(den * Kmax, s[4])
     DL = bb * (shi * shi) * (Kmax * r) * (F(-4) * L2E)
     w = den * r
     small = Kmax < F(0.25)
-    w = np.where(Kmax < F(9), np.where(small, np.maximum(F(2) - F(2) * Kmax, F(0)), gZ(Kmax, s[7]) * w * c1m(64)), w)
+    w = np.where(Kmax < F(9), np.where(small, np.maximum(F(2) - F(2) * Kmax, F(0)), gZ(Kmax, s[5]) * w * c1m(64)), w)
     w = w.astype(np.float32)
-    e = ex2a(DL - fma(np.full_like(DL, F(12) * FU), np.abs(DL), np.full_like(DL, SLACK)), s[8])
+    e = ex2a(DL - fma(np.full_like(DL, F(12) * FU), np.abs(DL), np.full_like(DL, SLACK)), s[6])
     Awi = mul_rd(F(2) * Ai, np.full_like(Ai, c1m(8 + 3)))
     return e, (w * Am).astype(np.float32), Awi
 
@@ -295,7 +297,7 @@ def cases(oracle_mod):
 
 def test_cross_upper_bound_never_below_the_oracle(cases):
     worst = np.inf
-    for signs in itertools.product((-1.0, 1.0), repeat=10):
+    for signs in itertools.product((-1.0, 1.0), repeat=8):
         ub = _cross(cases, signs)
         ref = cases["cross"]
         ok = ref > FLOOR
@@ -307,7 +309,7 @@ def test_cross_upper_bound_never_below_the_oracle(cases):
 
 def test_self_lower_bound_never_above_the_oracle(cases):
     rng = np.random.default_rng(18)
-    combos = [(-1.0,) * 13, (1.0,) * 13] + [tuple(rng.choice([-1.0, 1.0], 13)) for _ in range(400)]
+    combos = [(-1.0,) * 11, (1.0,) * 11] + [tuple(rng.choice([-1.0, 1.0], 11)) for _ in range(400)]
     for signs in combos:
         lb = _self(cases, signs)
         ref = cases["self2"]
@@ -661,7 +663,7 @@ def test_cross_row_sum_never_below_the_oracle(oracle_mod):
     for trial in range(40):
         n2 = int(rng.integers(8, 300))
         c, ref = _row_cases(oracle_mod, rng, n2)
-        for signs in [(-1.0,) * 10] + [tuple(rng.choice([-1.0, 1.0], 10)) for _ in range(3)]:
+        for signs in [(-1.0,) * 8] + [tuple(rng.choice([-1.0, 1.0], 8)) for _ in range(3)]:
             e, wQ, Bw = _cross_parts(c, signs)
             for paired in (False, True):  # any order of the pairs within a thread
                 row = _row_sum(e, wQ, Bw[0], rng.permutation(n2), paired)
@@ -733,7 +735,7 @@ def test_self_row_sum_never_above_the_oracle(oracle_mod):
                  psit=np.stack([np.full(n1 - 1, psit[0]), psit[m]], 1))
         ref = sum(oracle_mod.self_lb_term(mix, 0, k, cube, 0.01) + oracle_mod.self_lb_term(mix, k, 0, cube, 0.01)
                   for k in m)
-        for signs in [(-1.0,) * 13, (1.0,) * 13] + [tuple(rng.choice([-1.0, 1.0], 13)) for _ in range(3)]:
+        for signs in [(-1.0,) * 11, (1.0,) * 11] + [tuple(rng.choice([-1.0, 1.0], 11)) for _ in range(3)]:
             e, wA, Awi = _self_parts(c, signs)
             for paired in (False, True):
                 row = _row_sum(e, wA, Awi[0], rng.permutation(n1 - 1), paired)

@@ -118,12 +118,13 @@ int main(int argc, char **argv) {
     if (what[0] == 'b') printf("%d\n", gosma::auto_pop_batch(atoll(argv[2]), atoi(argv[3]), strtoull(argv[4], 0, 10)));
     if (what[0] == 'm') printf("%d\n", gosma::sma_block_for(atoi(argv[2]), atoi(argv[3]), atoi(argv[4]) != 0,
                                                             atoi(argv[5]), atoi(argv[6])));
-    if (what[0] == 'p') {  // pick: ncand reps, then ncand * reps timings
-        const int nc = atoi(argv[2]), reps = atoi(argv[3]);
+    if (what[0] == 'p') {  // pick: ncand reps pref, then ncand * reps timings
+        const int nc = atoi(argv[2]), reps = atoi(argv[3]), pref = atoi(argv[4]);
         std::vector<float> ms;
-        for (int a = 4; a < argc; ++a) ms.push_back((float)atof(argv[a]));
-        printf("%d\n", gosma::pick_shape(ms.data(), nc, reps));
+        for (int a = 5; a < argc; ++a) ms.push_back((float)atof(argv[a]));
+        printf("%d\n", gosma::pick_shape(ms.data(), nc, reps, pref));
     }
+    if (what[0] == 't') printf("%d\n", gosma::tune_stride(atoll(argv[2]), atoi(argv[3])));
     if (what[0] == 'r') printf("%d\n", gosma::retune_due(atoi(argv[2]), atoi(argv[3]), atoi(argv[4])) ? 1 : 0);
     if (what[0] == 'c') {  // candidates: wide group_bytes -> how many shapes
         gosma::BoundShape c[12];
@@ -223,11 +224,28 @@ def test_autotuner_picks_the_smallest_median(rules):
     """pick_shape on fake timing tables (3 timings per candidate): the
     smallest median wins, a single outlier does not decide, ties go to the
     earlier candidate, and a shape that could not run (1e30) never wins."""
-    assert rules("p", 3, 3, 2.0, 2.1, 1.9, 1.5, 1.6, 1.4, 1.7, 1.8, 1.6) == 1
-    assert rules("p", 2, 3, 1.0, 9.0, 1.1, 1.2, 1.2, 1.2) == 0      # median 1.1 beats 1.2 despite the 9.0
-    assert rules("p", 2, 3, 5.0, 0.1, 5.0, 1.0, 1.0, 1.0) == 1      # one fast outlier is not the median
-    assert rules("p", 2, 3, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0) == 0      # tie: the earlier candidate
-    assert rules("p", 3, 3, 1e30, 1e30, 1e30, 2.0, 2.0, 2.0, 1e30, 1e30, 1e30) == 1
+    assert rules("p", 3, 3, -1, 2.0, 2.1, 1.9, 1.5, 1.6, 1.4, 1.7, 1.8, 1.6) == 1
+    assert rules("p", 2, 3, -1, 1.0, 9.0, 1.1, 1.2, 1.2, 1.2) == 0      # median 1.1 beats 1.2 despite the 9.0
+    assert rules("p", 2, 3, -1, 5.0, 0.1, 5.0, 1.0, 1.0, 1.0) == 1      # one fast outlier is not the median
+    assert rules("p", 2, 3, -1, 1.0, 1.0, 1.0, 1.0, 1.0, 1.0) == 0      # tie: the earlier candidate
+    assert rules("p", 3, 3, -1, 1e30, 1e30, 1e30, 2.0, 2.0, 2.0, 1e30, 1e30, 1e30) == 1
+
+
+def test_autotuner_keeps_the_default_within_the_margin(rules):
+    """The default shape (pref) stays unless the winner's median is more
+    than 3% below its own; a default that could not run never stays."""
+    assert rules("p", 3, 3, 1, 0.98, 0.98, 0.98, 1.0, 1.0, 1.0, 1.2, 1.2, 1.2) == 1   # 2% faster: noise
+    assert rules("p", 3, 3, 1, 0.96, 0.96, 0.96, 1.0, 1.0, 1.0, 1.2, 1.2, 1.2) == 0   # 4% faster: taken
+    assert rules("p", 3, 3, 1, 1.1, 1.1, 1.1, 1.0, 1.0, 1.0, 1.2, 1.2, 1.2) == 1      # the default is best
+    assert rules("p", 2, 3, 0, 1e30, 1e30, 1e30, 5.0, 5.0, 5.0) == 1
+
+
+def test_autotuner_samples_a_sixteenth(rules):
+    """Every stride-th run of four siblings: 16 for large iterations, fewer
+    so that at least 16 runs per SM remain, never below 1."""
+    assert rules("t", 1 << 22, 152) == 16
+    assert rules("t", 64 * 152 * 5, 152) == 5
+    assert rules("t", 100, 152) == 1
 
 
 def test_autotuner_retunes_when_half_the_problems_finished(rules):
