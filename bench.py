@@ -111,7 +111,9 @@ def dist_env():
 
 
 class Clocks:
-    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    """nvidia-smi sampling of SM clocks and throttle reasons (every 50 ms)
+    from the pipe-rate probes through the warm-up to the end of the timed
+    region."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -129,10 +131,21 @@ class Clocks:
             os.close(fd)
             self.f = open(self.path, "w")
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.Q,
-                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                       "--format=csv,noheader,nounits", "-lms", "50"], stdout=self.f,
                                       stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
+
+    def lines(self):
+        """Samples written so far."""
+        if self.p is None:
+            return 1 << 30
+        self.f.flush()
+        try:
+            with open(self.path) as f:
+                return sum(1 for _ in f)
+        except OSError:
+            return 0
 
     def stop(self):
         out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
@@ -161,7 +174,8 @@ class Clocks:
         os.unlink(self.path)
         if sm:
             out = {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
-                   "samples": len(sm)}
+                   "samples": len(sm), "window": "every 50 ms from the pipe-rate probes through the warm-up "
+                                                 "to the end of the timed steps"}
         return out
 
 
@@ -310,6 +324,10 @@ def run_ours(args):
     from paper_1812_01232_gb300.gosma import Gosma
     prob = make_problem(rank)
     ctx = Gosma(local)
+    # clock sampling from here to the end of the timed steps: the pipe-rate
+    # probes, the warm-up and the timed steps all keep the GPU busy
+    clocks = Clocks(local)
+    clocks.start()
     rates = ctx.selftest_pipe_rates()  # measured pipe throughputs (lanes per SM per clock)
     ctx.set_problem(prob)
     n1, n2 = ctx.n1, ctx.n2
@@ -326,12 +344,17 @@ def run_ours(args):
     if r["status_name"] != "running":
         raise RuntimeError("branch-and-bound stopped during warm-up: %s" % r["status_name"])
 
+    # the sampler's first samples before the timed steps: L2-flush writes keep
+    # the GPU busy meanwhile (at most 3 s), without stepping the solver
+    t_wait = time.perf_counter()
+    while clocks.lines() < 2 and time.perf_counter() - t_wait < 3.0:
+        flush.zero_()
+        torch.cuda.synchronize()
+
     # ---------------- timed steps
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks = Clocks(local)
-    clocks.start()
     times = []
     pairs = 0
     self_pairs = 0

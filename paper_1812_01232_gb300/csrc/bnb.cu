@@ -234,7 +234,7 @@ __global__ void cube_prep_children(Domain dom, const Node *__restrict__ parents,
 constexpr int CHILD_RUN = 4;  // children per work item (a divisor of 8)
 
 template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK)
+__global__ void __launch_bounds__(BLOCK, bound_min_blocks<BLOCK>())
     bound_children(MixDev mx, Domain dom, df zeta2, const Node *__restrict__ parents, int np,
                    const CubePrep *__restrict__ prep, Node *__restrict__ kids, double *__restrict__ kid_ub,
                    unsigned int *__restrict__ n_self, int *__restrict__ counter) {
@@ -247,36 +247,38 @@ __global__ void __launch_bounds__(BLOCK)
     // work in quarters of a parent's children (CHILD_RUN siblings): after a
     // rotation split the siblings share the parent's cuboid, so the rows of
     // the first serve the others
-    for (int g = next_cube(counter, &slot); g < 8 * np / CHILD_RUN; g = next_cube(counter, &slot))
+    for (int g = next_cube(counter, &slot); g < 8 * np / CHILD_RUN; g = next_cube(counter, &slot)) {
+        // the run's parent; a child keeps its cuboid, and so its self sums, after a rotation split
+        const Node &par = parents[(CHILD_RUN * g) >> 3];
+        const bool rot = split_rotation(par);
+        const bool need_self = !(par.flags & 1u) || !rot;
 #pragma unroll 1
-    for (int k = 0; k < CHILD_RUN; ++k) {
-        const int c = CHILD_RUN * g + k;
-        // a child keeps its parent's cuboid, and so its self sums, after a rotation split
-        const bool rot = split_rotation(parents[c >> 3]);
-        const bool need_self = !(parents[c >> 3].flags & 1u) || !rot;
-        cube_bounds<BLOCK>(mx, prep[c], prep_point(prep, 8 * np, c), zeta2, need_self, cs, sm, sums, 0, threadIdx.x,
-                           k > 0 && !need_self);
-        if (threadIdx.x == 0) {
-            const Node p = parents[c >> 3];
-            Node ch = child_of(p, c & 7, split_rotation(p));
-            if (need_self) atomicAdd(n_self, 1u);
-            double sl = need_self ? sums.self_lb : p.self_lb;
-            double sc = need_self ? sums.self_c : p.self_c;
-            double lb, ub;
-            if (!sums.feasible) {
-                lb = ub = inf;
-            } else {
-                double S = sl + 2.0 * sums.cross_ub;
-                lb = sl - 2.0 * sums.cross_ub - 1e-12 * S;
-                ub = sums.centre_feasible ? sc - 2.0 * sums.cross_c : inf;
+        for (int k = 0; k < CHILD_RUN; ++k) {
+            const int c = CHILD_RUN * g + k;
+            cube_bounds<BLOCK>(mx, prep[c], prep_point(prep, 8 * np, c), zeta2, need_self, cs, sm, sums, 0,
+                               threadIdx.x, k > 0 && !need_self);
+            if (threadIdx.x == 0) {
+                const Node p = par;
+                Node ch = child_of(p, c & 7, rot);
+                if (need_self) atomicAdd(n_self, 1u);
+                double sl = need_self ? sums.self_lb : p.self_lb;
+                double sc = need_self ? sums.self_c : p.self_c;
+                double lb, ub;
+                if (!sums.feasible) {
+                    lb = ub = inf;
+                } else {
+                    double S = sl + 2.0 * sums.cross_ub;
+                    lb = sl - 2.0 * sums.cross_ub - 1e-12 * S;
+                    ub = sums.centre_feasible ? sc - 2.0 * sums.cross_c : inf;
+                }
+                ch.lb = lb;
+                ch.self_lb = sl;
+                ch.self_c = sc;
+                ch.psit = sums.psi_t_max;
+                ch.flags |= 1u;
+                kids[c] = ch;
+                kid_ub[c] = ub;
             }
-            ch.lb = lb;
-            ch.self_lb = sl;
-            ch.self_c = sc;
-            ch.psit = sums.psi_t_max;
-            ch.flags |= 1u;
-            kids[c] = ch;
-            kid_ub[c] = ub;
         }
     }
 }

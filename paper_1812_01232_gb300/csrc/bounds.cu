@@ -79,7 +79,7 @@ __global__ void cuboid_owner(const CubePrep *__restrict__ prep, int n, const uns
 // pass 0: the cubes that own their self sums (or all cubes when owner is
 // null); pass 1: the others, with the owner's self sums.
 template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK) eval_bounds_kernel(MixDev mx, const gosma_cube *__restrict__ cubes, int n,
+__global__ void __launch_bounds__(BLOCK, bound_min_blocks<BLOCK>()) eval_bounds_kernel(MixDev mx, const gosma_cube *__restrict__ cubes, int n,
                                                             const CubePrep *__restrict__ prep, df zeta2,
                                                             gosma_bound *__restrict__ out, int *__restrict__ counter,
                                                             const int *__restrict__ owner, int pass) {

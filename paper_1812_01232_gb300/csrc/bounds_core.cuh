@@ -527,6 +527,16 @@ __device__ inline void group_reduce_df(df v[4], CubeShared &cs, int gid, int gti
         }
 }
 
+// Blocks per SM the bound kernels ask the compiler to fit.  32- and 64-thread
+// blocks work on small mixtures, whose cubes are short and latency-bound, so
+// they need every resident warp (32 blocks of one warp, 16 of two: 64
+// registers per thread); 128- and 256-thread blocks keep 7 and 3 blocks
+// (73 and 85 registers), which is what the pair loops need without spills.
+template <int BLOCK>
+constexpr int bound_min_blocks() {
+    return BLOCK <= 64 ? 1024 / BLOCK : BLOCK == 128 ? 7 : BLOCK == 256 ? 3 : 1;
+}
+
 // Work distribution of the persistent bound kernels: cubes are handed out
 // one at a time from a device counter that is zero at launch, so that groups
 // drawing cheap cubes (infeasible ones, children reusing cached self sums)
@@ -563,6 +573,11 @@ __device__ void cube_bounds(const MixDev &mx, const CubePrep &prep, const CubePr
     const int tid = gtid;
     const int n1 = mx.n1, n2 = mx.n2;
     const float U = GOSMA_U;
+    // Small groups serve small mixtures, whose rows hold few pairs: there one
+    // copy of each pair loop, with the edge pairs masked at run time, runs
+    // fewer instructions per cube than peeled edge pairs; larger groups peel
+    // the masked edge pairs off their long loops.
+    constexpr bool COMPACT_LOOPS = GT <= 64;
     for (int k = tid; k < PREP_WORDS; k += GT)
         reinterpret_cast<float *>(&cs.rot)[k] = reinterpret_cast<const float *>(&prep)[k];
     if (mx.psi_point)
@@ -791,14 +806,19 @@ __device__ void cube_bounds(const MixDev &mx, const CubePrep &prep, const CubePr
                 }
             };
             int q = p0 + tj;
-            if (q == pa) {
-                step(q, true, q == pb);
-                q += Tj;
-            }
-            const int qend = pb >= 0 ? pb : p1;
+            if constexpr (COMPACT_LOOPS) {
 #pragma unroll 1
-            for (; q < qend; q += Tj) step(q, false, false);
-            if (q == pb) step(q, false, true);
+                for (; q < p1; q += Tj) step(q, q == pa, q == pb);
+            } else {
+                if (q == pa) {
+                    step(q, true, q == pb);
+                    q += Tj;
+                }
+                const int qend = pb >= 0 ? pb : p1;
+#pragma unroll 1
+                for (; q < qend; q += Tj) step(q, false, false);
+                if (q == pb) step(q, false, true);
+            }
             cl.add(pl.x);
             cl.add(pl.y);
             cu.add(pc.x);
@@ -858,14 +878,19 @@ __device__ void cube_bounds(const MixDev &mx, const CubePrep &prep, const CubePr
                         }
                     };
                     int q = q0 + sj;
-                    if (q == qa) {
-                        step(q, true, q == qb);
-                        q += Sj;
-                    }
-                    const int qend = qb >= 0 ? qb : q1;
+                    if constexpr (COMPACT_LOOPS) {
 #pragma unroll 1
-                    for (; q < qend; q += Sj) step(q, false, false);
-                    if (q == qb) step(q, false, true);
+                        for (; q < q1; q += Sj) step(q, q == qa, q == qb);
+                    } else {
+                        if (q == qa) {
+                            step(q, true, q == qb);
+                            q += Sj;
+                        }
+                        const int qend = qb >= 0 ? qb : q1;
+#pragma unroll 1
+                        for (; q < qend; q += Sj) step(q, false, false);
+                        if (q == qb) step(q, false, true);
+                    }
                     sl.add(pl.x);
                     sl.add(pl.y);
                     su.add(pc.x);
@@ -882,9 +907,10 @@ __device__ void cube_bounds(const MixDev &mx, const CubePrep &prep, const CubePr
     // ---------------- phase 3: block reduction (double-float)
     group_reduce_df<BLOCK, GT>(T, cs, gid, gtid);
     if (tid == 0) {
-        out.self_lb = (double)T[0].h + (double)T[0].l;
+        // (the self sums only when computed: callers that skip them use cached ones)
+        out.self_lb = need_self ? (double)T[0].h + (double)T[0].l : 0.0;
         out.cross_ub = (double)T[1].h + (double)T[1].l;
-        out.self_c = (double)T[2].h + (double)T[2].l;
+        out.self_c = need_self ? (double)T[2].h + (double)T[2].l : 0.0;
         out.cross_c = (double)T[3].h + (double)T[3].l;
         out.psi_r = cs.rot.psi_r;
         float smax = __uint_as_float(cs.spsi_max);

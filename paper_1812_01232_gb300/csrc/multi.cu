@@ -567,11 +567,13 @@ __global__ void mp_prep(const ProbDev *__restrict__ P, const int *__restrict__ o
 
 constexpr int MP_CHILD_RUN = 4;  // children per work item (a divisor of 8)
 
-// G cubes per block: groups of BLOCK / G threads (whole warps), each with its
+// G cubes per block: groups of BLOCK / G threads (whole warps; several cubes
+// per block keep about 100 registers per thread, as their group barriers and
+// slots need them), each with its
 // own shared arrays (group_floats floats of the dynamic shared memory) and
 // its own work slot.
 template <int BLOCK, int G>
-__global__ void __launch_bounds__(BLOCK)
+__global__ void __launch_bounds__(BLOCK, G == 1 ? bound_min_blocks<BLOCK>() : 65536 / (BLOCK * 100))
     mp_bound(const ProbDev *__restrict__ P, const int *__restrict__ off, int nprob, const Node *__restrict__ parents,
              const CubePrep *__restrict__ prep, Node *__restrict__ kids, double *__restrict__ kid_ub,
              int *__restrict__ counter, int group_floats, int stride) {
@@ -589,39 +591,42 @@ __global__ void __launch_bounds__(BLOCK)
     // the parent's cuboid, so the rows of the first serve the others.  stride
     // > 1 (the autotuner's timings) takes every stride-th run only.
     for (int g = stride * next_cube<BLOCK, GT>(counter, &slot[gid], gid, gtid); MP_CHILD_RUN * g < N;
-         g = stride * next_cube<BLOCK, GT>(counter, &slot[gid], gid, gtid))
-#pragma unroll 1
-    for (int r = 0; r < MP_CHILD_RUN && MP_CHILD_RUN * g + r < N; ++r) {
-        const int w = MP_CHILD_RUN * g + r;
-        const int k = mp_find(off, nprob, w), c = w - off[k];
+         g = stride * next_cube<BLOCK, GT>(counter, &slot[gid], gid, gtid)) {
+        // the run's parent and problem (a run never crosses a parent)
+        const int w0 = MP_CHILD_RUN * g;
+        const int k = mp_find(off, nprob, w0);
         const MixDev &mx = P[k].mx;
         SmemArrays sm = carve(my_smem, mx.n1, mx.n2);
-        const Node &pr = parents[w >> 3];
+        const Node &pr = parents[w0 >> 3];
         const bool rot = split_rotation(pr);
         const bool need_self = !(pr.flags & 1u) || !rot;
-        cube_bounds<BLOCK, GT>(mx, prep[w], prep_point(prep, off[nprob], w), P[k].zeta2, need_self, cs[gid], sm,
-                               sums[gid], gid, gtid, r > 0 && !need_self);
-        if (gtid == 0) {
-            const CubeSums &su = sums[gid];
-            const Node p = pr;
-            Node ch = child_of(p, c & 7, rot);
-            double sl = need_self ? su.self_lb : p.self_lb;
-            double sc = need_self ? su.self_c : p.self_c;
-            double lb, ub;
-            if (!su.feasible) {
-                lb = ub = inf;
-            } else {
-                double Ssum = sl + 2.0 * su.cross_ub;
-                lb = sl - 2.0 * su.cross_ub - 1e-12 * Ssum;
-                ub = su.centre_feasible ? sc - 2.0 * su.cross_c : inf;
+#pragma unroll 1
+        for (int r = 0; r < MP_CHILD_RUN && w0 + r < N; ++r) {
+            const int w = w0 + r, c = w - off[k];
+            cube_bounds<BLOCK, GT>(mx, prep[w], prep_point(prep, N, w), P[k].zeta2, need_self, cs[gid], sm,
+                                   sums[gid], gid, gtid, r > 0 && !need_self);
+            if (gtid == 0) {
+                const CubeSums &su = sums[gid];
+                const Node p = pr;
+                Node ch = child_of(p, c & 7, rot);
+                double sl = need_self ? su.self_lb : p.self_lb;
+                double sc = need_self ? su.self_c : p.self_c;
+                double lb, ub;
+                if (!su.feasible) {
+                    lb = ub = inf;
+                } else {
+                    double Ssum = sl + 2.0 * su.cross_ub;
+                    lb = sl - 2.0 * su.cross_ub - 1e-12 * Ssum;
+                    ub = su.centre_feasible ? sc - 2.0 * su.cross_c : inf;
+                }
+                ch.lb = lb;
+                ch.self_lb = sl;
+                ch.self_c = sc;
+                ch.psit = su.psi_t_max;
+                ch.flags |= 1u;
+                kids[w] = ch;
+                kid_ub[w] = ub;
             }
-            ch.lb = lb;
-            ch.self_lb = sl;
-            ch.self_c = sc;
-            ch.psit = su.psi_t_max;
-            ch.flags |= 1u;
-            kids[w] = ch;
-            kid_ub[w] = ub;
         }
     }
 }

@@ -5,6 +5,7 @@
     python -m paper_1812_01232_gb300.profile_cases batch --problems 64 --max-nodes 100000
     python -m paper_1812_01232_gb300.profile_cases sma --seeds 1216 --precision 32
     python -m paper_1812_01232_gb300.profile_cases mixgen --points 100000 --passes 30
+    python -m paper_1812_01232_gb300.profile_cases tiny --problems 8 --reps 1
 
 stress  Theorem 1 bounds of `cubes` sub-cubes of the 2048 x 512 stress problem
         (device buffers), `reps` launches of the bound kernel.
@@ -18,6 +19,9 @@ sma     SMA from `seeds` seed poses of the 128 x 64 paper-scale problem
 mixgen  DP-means of `points` points of the synthetic indoor scene
         (lambda 2 m^2) with at most `passes` passes, then DP-vMF-means of as
         many bearing vectors (12-degree threshold).
+tiny    the tiny problems 200000.. (10 x 8 components) solved one after the
+        other to the certificate by the single-problem solver (eps 1e-3,
+        automatic pop, 2^26-node queue), `reps` times.
 Each prints one line of timing so that the plain run can be compared.
 """
 from __future__ import annotations
@@ -50,8 +54,11 @@ def stress(a):
     torch.cuda.synchronize()
     dt = (time.perf_counter() - t0) / a.reps
     n1, n2 = len(prob["sigma1"]), len(prob["kappa2"])
-    print("stress: %d cubes, %.3f ms per launch, %.3e cross pairs/s, %.3e self pairs/s" % (
-        len(cubes), 1e3 * dt, len(cubes) * n1 * n2 / dt, len(cubes) * n1 * (n1 - 1) / 2 / dt))
+    # self sums are computed once per distinct translation cuboid of the call
+    cuboids = len(np.unique(np.ascontiguousarray(cubes[:, 4:10]), axis=0))
+    print("stress: %d cubes (%d distinct translation cuboids), %.3f ms per call, %.3e cross pairs/s, "
+          "%.3e self pairs computed/s" % (len(cubes), cuboids, 1e3 * dt, len(cubes) * n1 * n2 / dt,
+                                         cuboids * n1 * (n1 - 1) / 2 / dt))
 
 
 def mlp(a):
@@ -113,6 +120,18 @@ def mixgen(a):
         a.points, r["k"], r["passes"], t1 - t0, a.points, v["k"], v["passes"], t2 - t1))
 
 
+def tiny(a):
+    probs = [synth.tiny_problem(200000 + s) for s in range(a.problems)]
+    ctx = Gosma(0)
+    for _ in range(a.reps):
+        t0 = time.perf_counter()
+        nodes = 0
+        for p in probs:
+            ctx.set_problem(p)
+            nodes += ctx.bnb_solve(eps=1e-3, max_seconds=60, queue_capacity=1 << 26)["nodes"]
+        print("tiny: %d problems, %d nodes, %.3f s" % (a.problems, nodes, time.perf_counter() - t0))
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     sub = ap.add_subparsers(dest="case", required=True)
@@ -131,8 +150,11 @@ def main(argv=None):
     g = sub.add_parser("mixgen")
     g.add_argument("--points", type=int, default=100000)
     g.add_argument("--passes", type=int, default=30)
+    t = sub.add_parser("tiny")
+    t.add_argument("--problems", type=int, default=8)
+    t.add_argument("--reps", type=int, default=1)
     a = ap.parse_args(argv)
-    {"stress": stress, "mlp": mlp, "batch": batch, "sma": sma, "mixgen": mixgen}[a.case](a)
+    {"stress": stress, "mlp": mlp, "batch": batch, "sma": sma, "mixgen": mixgen, "tiny": tiny}[a.case](a)
     return 0
 
 

@@ -68,6 +68,24 @@ def test_dp_vmf_means_matches_oracle(ctx, oracle_mod, n, deg, seed):
     _compare(g, o, "kappa", 1e-12)
 
 
+def test_vmf_degenerate_clusters_match_oracle(ctx, oracle_mod):
+    """The oracle's pinned degenerate cases on the device: a cluster whose
+    direction sum is exactly zero (antipodal vectors under a threshold below
+    -1) is centred on its lowest-index vector with the smallest
+    concentration; identical directions get the concentration cap."""
+    cases = [(np.array([[0.0, 0.0, 1.0], [0.0, 0.0, -1.0]]), -1.5, 1e4),
+             (np.array([[0.0, -1.0, 0.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [-1.0, 0.0, 0.0]]), -1.5, 1e4),
+             (np.tile([[0.6, 0.0, 0.8]], (5, 1)), 0.5, 1234.0),
+             (np.array([[1.0, 0.0, 0.0], [0.0, 1.0, 0.0]]), -0.5, 1234.0)]
+    for x, lam, kmax in cases:
+        for order in (x, x[::-1].copy()):
+            g = ctx.dp_vmf_means(order, lam, max_iter=10, kappa_max=kmax)
+            o = oracle_mod.dp_cluster(order, lam, vmf=True, max_iter=10, kappa_max=kmax)
+            _compare(g, o, "kappa", 1e-12)
+    g = ctx.dp_vmf_means(cases[2][0], 0.5, max_iter=10, kappa_max=1234.0)
+    assert g["kappa"][0] == 1234.0
+
+
 def test_scene_at_paper_size(ctx, oracle_mod):
     """100k scene points and 100k bearing vectors (the size the paper
     downsamples to), about 100 and 70 clusters, 30 passes."""
