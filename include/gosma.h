@@ -317,12 +317,15 @@ int gosma_bnb_solve(gosma_ctx *ctx, const gosma_opts *opts, gosma_result *out);
  * (threads per block, sub-cubes per block) is the caller's
  * (opts->bound_block, opts->bound_cubes) or picked by an autotuner: each
  * candidate shape is launched once and then timed three times on the same
- * sample of children (every 16th run of four siblings, across all problems;
- * at least 16 runs per SM) at the fifth iteration; the smallest median wins
- * if it is at least 3% below the default shape's (128 threads, one sub-cube),
- * else the default stays; the shapes are timed again (and the graph
- * captured anew) whenever the number of unfinished problems has halved
- * since the last tuning, at least 32 iterations after it; results[k] reports
+ * sample of children (every few runs of four siblings, across all problems:
+ * a sixteenth of the iteration, at least 64 children per SM) at
+ * the fifth iteration; the smallest median wins if it is at least 3% below
+ * the default shape's (128 threads, one sub-cube), and a winner by less
+ * than 15% must also beat it in a full launch on the same children, else
+ * the default stays; the shapes
+ * are timed again (and the graph captured anew) whenever the number of
+ * unfinished problems has halved since the last tuning, at least 32
+ * iterations after it; results[k] reports
  * the final shape and the number of tunings.  The bounds of one sub-cube
  * differ between shapes only by the order of their FP32 sums.
  * results[k].seconds is the device time from the start to problem k's

@@ -312,13 +312,14 @@ struct RowCross {
 };
 
 // The row constants of RowCross in both lanes of packed pairs, for
-// cross_pair2.  nSs = -Ss, nA4 = -A4 (negation is exact).
+// cross_pair2.  hCs = Cs / 2, nhSs = -Ss / 2, nA4 = -A4 (exact: the halves
+// multiply |v - u| and |v + u|, which are 2 sin and 2 cos of theta/2).
 struct RowCross2 {
     float2 vx, vy, vz, wx, wy, wz;
-    float2 a, b, k0, Cs, nSs, esS, nA4;
+    float2 a, b, k0, hCs, nhSs, esS, nA4;
     __device__ __forceinline__ explicit RowCross2(const RowCross &R)
         : vx(bc2(R.vx)), vy(bc2(R.vy)), vz(bc2(R.vz)), wx(bc2(R.wx)), wy(bc2(R.wy)), wz(bc2(R.wz)), a(bc2(R.a)),
-          b(bc2(R.b)), k0(bc2(R.k0)), Cs(bc2(R.Cs)), nSs(bc2(-R.Ss)), esS(bc2(R.esS)), nA4(bc2(-R.A4)) {}
+          b(bc2(R.b)), k0(bc2(R.k0)), hCs(bc2(0.5f * R.Cs)), nhSs(bc2(-0.5f * R.Ss)), esS(bc2(R.esS)), nA4(bc2(-R.A4)) {}
 };
 
 __device__ __forceinline__ float2 sqrt2a(float2 x) { return make_float2(sqrta(x.x), sqrta(x.y)); }
@@ -365,9 +366,11 @@ __device__ __forceinline__ void cross_pair2(const RowCross2 &R, float4 P0, float
     if (K0.y < 9.f) w0.y = K0.y < 1e-3f ? 2.f - 2.f * K0.y : gZ(K0.y) * w0.y;
     pc = fma2(ex2_2a(mul2(mul2(mul2(kk, x2), mul2(K0c, r0)), bc2(-GOSMA_LOG2E))), mul2(w0, Q), pc);
     // bound: B = max(0, theta - s)
-    const float2 sth = mul2(bc2(0.5f), sqrt2a(x2)), cth = mul2(bc2(0.5f), sqrt2a(y2));
-    const float2 sB = fma2(sth, R.Cs, mul2(cth, R.nSs));
-    const float2 es = fma2(bc2(7.5f * U), sth, R.esS);
+    // sx, sy = 2 sin, 2 cos of theta/2; the halves sit in the row constants,
+    // so sB and es round exactly as from sin(theta/2) and cos(theta/2)
+    const float2 sx = sqrt2a(x2), sy = sqrt2a(y2);
+    const float2 sB = fma2(sx, R.hCs, mul2(sy, R.nhSs));
+    const float2 es = fma2(bc2(3.75f * U), sx, R.esS);
     const float2 slo = max2(sub2(sB, es), 0.f);
     const float2 shi = min2(add2(max2(sB, 0.f), es), 1.f);
     // cos^2(B/2) = 1 - sin^2(B/2) from the sine bounds, as -q with q = s^2 - 1
@@ -397,12 +400,15 @@ struct RowSelf {
 };
 
 // The row constants of RowSelf in both lanes of packed pairs, for self_pair2.
+// (the half-angle pair of psi_i/2 halved, hcp = cp / 2, hsp = sp / 2,
+// nhsp = -sp / 2, exact: see RowCross2)
 struct RowSelf2 {
     float2 vx, vy, vz, wx, wy, wz;
-    float2 a, b, k0, cp, sp, nsp;
+    float2 a, b, k0, hcp, hsp, nhsp;
     __device__ __forceinline__ explicit RowSelf2(const RowSelf &R)
         : vx(bc2(R.vx)), vy(bc2(R.vy)), vz(bc2(R.vz)), wx(bc2(R.wx)), wy(bc2(R.wy)), wz(bc2(R.wz)), a(bc2(R.a)),
-          b(bc2(R.b)), k0(bc2(R.k0)), cp(bc2(R.cp)), sp(bc2(R.sp)), nsp(bc2(-R.sp)) {}
+          b(bc2(R.b)), k0(bc2(R.k0)), hcp(bc2(0.5f * R.cp)), hsp(bc2(0.5f * R.sp)),
+          nhsp(bc2(-0.5f * R.sp)) {}
 };
 
 // Two self pairs (i, m) and (i, m') at once, lane x for partner m and lane y
@@ -418,9 +424,9 @@ struct RowSelf2 {
 //   and the smallest K; the largest K over the four corners of
 //   [a_i, b_i] x [a_m, b_m], from above; g(K)/K from below: >= 2 - 2K for
 //   small K, g rounded with <= 64u error otherwise.
-// Besides the rewritings of cross_pair2, -sin((psi_i+psi_m)/2) is formed as
-// 0 - S (exact; S >= 0, a sum of products of non-negative half-angle sines
-// and cosines, so |S| = S).
+// Besides the rewritings of cross_pair2, -sin((psi_i+psi_m)/2) / 2 is formed as
+// 0 - hS (exact; hS >= 0, a sum of products of non-negative half-angle
+// sines and cosines).
 __device__ __forceinline__ void self_pair2(const RowSelf2 &R, float4 P0, float4 P1, float4 P2, float4 P3, float4 P4,
                                            float4 P5, float2 Um, float2 &pl, float2 &pc) {
     const float U = GOSMA_U;
@@ -446,12 +452,14 @@ __device__ __forceinline__ void self_pair2(const RowSelf2 &R, float4 P0, float4 
     if (K0.y < 9.f) w0.y = K0.y < 1e-3f ? 2.f - 2.f * K0.y : gZ(K0.y) * w0.y;
     pc = fma2(ex2_2a(mul2(mul2(mul2(kk, x2), mul2(K0c, r0)), bc2(-GOSMA_LOG2E))), mul2(w0, Um), pc);
     // bound: A = min(pi, theta + psi_i + psi_m)
-    const float2 sth = mul2(bc2(0.5f), sqrt2a(x2)), cth = mul2(bc2(0.5f), sqrt2a(y2));
-    const float2 C = fma2(R.cp, cpm, mul2(R.nsp, spm));  // cos((psi_i + psi_m)/2)
-    const float2 S = fma2(R.sp, cpm, mul2(R.cp, spm));   // sin((psi_i + psi_m)/2)
-    const float2 cA = fma2(cth, C, mul2(sth, sub2(bc2(0.f), S)));
-    const float2 sA = fma2(sth, C, mul2(cth, S));
-    const float2 es = mul2(bc2(10.f * U), add2(sth, S));
+    const float2 sx = sqrt2a(x2), sy = sqrt2a(y2);          // 2 sin, 2 cos of theta/2
+    const float2 hC = fma2(R.hcp, cpm, mul2(R.nhsp, spm));  // cos((psi_i + psi_m)/2) / 2
+    const float2 hS = fma2(R.hsp, cpm, mul2(R.hcp, spm));   // sin((psi_i + psi_m)/2) / 2
+    const float2 cA = fma2(sy, hC, mul2(sx, sub2(bc2(0.f), hS)));
+    const float2 sA = fma2(sx, hC, mul2(sy, hS));
+    // 10u (sin(theta/2) + sin(psi/2)) as 5u sx + 20u hS (two roundings, at
+    // most 2u of it: still above the 9.5u the sine carries)
+    const float2 es = fma2(bc2(5.f * U), sx, mul2(bc2(20.f * U), hS));
     const float2 t1 = add2(sA, es);
     const float2 shi = make_float2(cA.x <= 16.f * U ? 1.f : fminf(t1.x, 1.f), cA.y <= 16.f * U ? 1.f : fminf(t1.y, 1.f));
     const float2 slo = max2(sub2(sA, es), 0.f);

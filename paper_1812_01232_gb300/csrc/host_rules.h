@@ -75,6 +75,17 @@ inline int bound_shape_candidates(int wide, size_t group_bytes, BoundShape out[1
 // unless the winner's median is more than PICK_MARGIN below its own (the
 // timings sample a sixteenth of the work, so small differences are noise).
 constexpr float PICK_MARGIN = 0.03f;
+// A pick whose median is below CLEAR_WIN of the default's is taken as it is;
+// a narrower win is checked again in full launches (sample_median gives the
+// medians).
+constexpr float CLEAR_WIN = 0.85f;
+inline float sample_median(const float *ms, int c, int reps) {
+    float v[16];
+    const int r = reps < 16 ? reps : 16;
+    for (int k = 0; k < r; ++k) v[k] = ms[c * reps + k];
+    std::sort(v, v + r);
+    return r % 2 ? v[r / 2] : 0.5f * (v[r / 2 - 1] + v[r / 2]);
+}
 inline int pick_shape(const float *ms, int ncand, int reps, int pref = -1) {
     int best = -1;
     float best_med = 0.f, pref_med = 0.f;
@@ -95,7 +106,9 @@ inline int pick_shape(const float *ms, int ncand, int reps, int pref = -1) {
 }
 
 // The stride of the autotuner's sample: every stride-th run of four sibling
-// children (a sixteenth of the work), but at least 16 runs per SM.
+// children, a sixteenth of the work but at least 64 children per SM (a
+// sample this small can mislead by a few per cent, which the full-launch
+// check of narrow wins catches).
 inline int tune_stride(long long nkid, int sm_count) {
     long long s = nkid / (64LL * sm_count);
     return (int)(s < 1 ? 1 : s > 16 ? 16 : s);

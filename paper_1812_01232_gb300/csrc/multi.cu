@@ -1823,13 +1823,15 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
     // TUNE_REPS times timed on the same prepared children (the bound kernel
     // only writes the children's records), and the smallest median wins
     // (pick_shape, which keeps the default 128 x 1 unless another shape is 3%
-    // faster); the timings take every 16th run of sibling children (all
-    // problems alike), the chosen shape then bounds all of them.  The first
-    // tuning runs at TUNE_ITER, once the queues hold
-    // enough parents for a representative launch (8^5 per problem unless the
-    // pop quota is smaller); the shapes are timed again whenever the
-    // unfinished problems have halved since, at least RETUNE_GAP iterations
-    // later (retune_due).
+    // faster); the timings take a sample of sibling runs (all problems alike,
+    // tune_stride).  A pick other than the default by less than 15% on the
+    // sample must then win against it in full launches on the same children
+    // (the default's launch first, the pick's last, whose records stay; both
+    // give the same bounds up to the order of FP32 sums), else the default
+    // stays.  The first tuning runs at TUNE_ITER, once the
+    // queues hold enough parents for a representative launch; the shapes are
+    // timed again whenever the unfinished problems have halved since, at
+    // least RETUNE_GAP iterations later (retune_due).
     const int TUNE_ITER = 5, TUNE_REPS = 3;
     const bool tune = o.bound_block == 0;
     BoundShape shape = tune ? BoundShape{128, 1} : BoundShape{o.bound_block, o.bound_cubes};
@@ -1846,13 +1848,24 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
             cudaEventDestroy(b);
         }
     } ev_guard{ta, tb};
+    // a full bound launch of the iteration with shape sh, timed
+    auto timed_full = [&](BoundShape sh, float &ms) -> cudaError_t {
+        cudaError_t ee = cudaEventRecord(ta, st);
+        if (ee == cudaSuccess)
+            ee = mp_bound_any(sh, ctx, st, dP, off, nprob, parents, prep, kids, kid_ub, Qb.quota + 1, smem);
+        if (ee == cudaSuccess) ee = cudaEventRecord(tb, st);
+        if (ee == cudaSuccess) ee = cudaEventSynchronize(tb);
+        if (ee == cudaSuccess) ee = cudaEventElapsedTime(&ms, ta, tb);
+        return ee;
+    };
+    // one iteration on the eager path; tune_now times the candidates first
     auto eager = [&](bool tune_now) -> cudaError_t {
         front();
         cudaError_t ee = cudaSuccess;
         if (tune_now && ncand > 0) {
             // the timings run on a sample of the iteration's children (every
-            // stride-th run of siblings: a sixteenth, at least 16 runs per SM),
-            // so that tuning costs about as much as two or three launches
+            // stride-th run of siblings: a sixteenth, at least 64 children per
+            // SM), so that tuning costs about two launches
             int nkid = 0;
             ee = cudaMemcpyAsync(&nkid, off + nprob, sizeof(int), cudaMemcpyDeviceToHost, st);
             if (ee == cudaSuccess) ee = cudaStreamSynchronize(st);
@@ -1877,10 +1890,22 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
                 int pref = -1;
                 for (int c = 0; c < ncand; ++c)
                     if (cands[c].block == 128 && cands[c].cubes == 1) pref = c;
-                shape = cands[pick_shape(ms.data(), ncand, TUNE_REPS, pref)];
+                const int ip = pick_shape(ms.data(), ncand, TUNE_REPS, pref);
+                const BoundShape pick = cands[ip];
                 ++tunings;
-                // this iteration's children from the chosen shape
-                ee = mp_bound_any(shape, ctx, st, dP, off, nprob, parents, prep, kids, kid_ub, Qb.quota + 1, smem);
+                if (pref >= 0 && ip != pref &&
+                    sample_median(ms.data(), ip, TUNE_REPS) > CLEAR_WIN * sample_median(ms.data(), pref, TUNE_REPS)) {
+                    // the pick against the default in full launches on this iteration's
+                    // children; the pick's launch runs last, and its records stay
+                    float t_def = 0.f, t_pick = 0.f;
+                    ee = timed_full(cands[pref], t_def);
+                    if (ee == cudaSuccess) ee = timed_full(pick, t_pick);
+                    shape = t_pick < t_def ? pick : cands[pref];
+                } else {
+                    shape = pick;
+                    // this iteration's children from the chosen shape
+                    ee = mp_bound_any(shape, ctx, st, dP, off, nprob, parents, prep, kids, kid_ub, Qb.quota + 1, smem);
+                }
             }
         } else {
             ee = mp_bound_any(shape, ctx, st, dP, off, nprob, parents, prep, kids, kid_ub, Qb.quota + 1, smem);

@@ -185,9 +185,9 @@ def _cross_parts(c, s):
     p = [(vh[:, k] + uh[:, k]) + (vl[:, k] + ul[:, k]) for k in range(3)]
     x2 = fma(d[0], d[0], fma(d[1], d[1], d[2] * d[2]))
     y2 = fma(p[0], p[0], fma(p[1], p[1], p[2] * p[2]))
-    sth, cth = F(0.5) * sqrta(x2, s[0]), F(0.5) * sqrta(y2, s[1])
-    sB = fma(sth, Cs, -(cth * Ss))
-    es = fma(np.full_like(sth, F(7.5) * FU), sth, esS)
+    sx, sy = sqrta(x2, s[0]), sqrta(y2, s[1])  # 2 sin, 2 cos of theta/2; the halves in the row constants
+    sB = fma(sx, F(0.5) * Cs, -(sy * (F(0.5) * Ss)))
+    es = fma(np.full_like(sx, F(3.75) * FU), sx, esS)
     slo = np.maximum(sB - es, F(0))
     shi = np.minimum(np.maximum(sB, F(0)) + es, F(1))
     # cos^2(B/2) = -(s^2 - 1), the fused s^2 - 1 rounded once; no outward factors
@@ -239,12 +239,13 @@ def _self_parts(c, s):
     p = [(vh[:, k] + mh[:, k]) + (vl[:, k] + ml[:, k]) for k in range(3)]
     x2 = fma(d[0], d[0], fma(d[1], d[1], d[2] * d[2]))
     y2 = fma(p[0], p[0], fma(p[1], p[1], p[2] * p[2]))
-    sth, cth = F(0.5) * sqrta(x2, s[0]), F(0.5) * sqrta(y2, s[1])
-    C = fma(cp[:, 0], cp[:, 1], -(sp[:, 0] * sp[:, 1]))
-    S = fma(sp[:, 0], cp[:, 1], cp[:, 0] * sp[:, 1])
-    cA = fma(cth, C, -(sth * S))
-    sA = fma(sth, C, cth * S)
-    es = (F(10) * FU) * (sth + np.abs(S))
+    sx, sy = sqrta(x2, s[0]), sqrta(y2, s[1])  # 2 sin, 2 cos of theta/2
+    hcp, hsp = F(0.5) * cp, F(0.5) * sp       # the row's halved half-angle pair
+    hC = fma(hcp[:, 0], cp[:, 1], -(hsp[:, 0] * sp[:, 1]))
+    hS = fma(hsp[:, 0], cp[:, 1], hcp[:, 0] * sp[:, 1])
+    cA = fma(sy, hC, -(sx * hS))
+    sA = fma(sx, hC, sy * hS)
+    es = fma(np.full_like(sx, F(5) * FU), sx, (F(20) * FU) * hS)
     api = cA <= F(16) * FU
     shi = np.where(api, F(1), np.minimum(sA + es, F(1))).astype(np.float32)
     slo = np.maximum(sA - es, F(0))

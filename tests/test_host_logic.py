@@ -124,6 +124,12 @@ int main(int argc, char **argv) {
         for (int a = 5; a < argc; ++a) ms.push_back((float)atof(argv[a]));
         printf("%d\n", gosma::pick_shape(ms.data(), nc, reps, pref));
     }
+    if (what[0] == 'q') {  // median: reps c, then the timings of the candidates
+        const int reps = atoi(argv[2]), c = atoi(argv[3]);
+        std::vector<float> ms;
+        for (int a = 4; a < argc; ++a) ms.push_back((float)atof(argv[a]));
+        printf("%d\n", (int)(1000.f * gosma::sample_median(ms.data(), c, reps) + 0.5f));
+    }
     if (what[0] == 't') printf("%d\n", gosma::tune_stride(atoll(argv[2]), atoi(argv[3])));
     if (what[0] == 'r') printf("%d\n", gosma::retune_due(atoi(argv[2]), atoi(argv[3]), atoi(argv[4])) ? 1 : 0);
     if (what[0] == 'c') {  // candidates: wide group_bytes -> how many shapes
@@ -240,9 +246,16 @@ def test_autotuner_keeps_the_default_within_the_margin(rules):
     assert rules("p", 2, 3, 0, 1e30, 1e30, 1e30, 5.0, 5.0, 5.0) == 1
 
 
+def test_sample_median(rules):
+    """The median of one candidate's timings (in thousandths): odd and even
+    counts, the other candidates' timings ignored."""
+    assert rules("q", 3, 1, 9.0, 9.0, 9.0, 2.0, 1.0, 3.0) == 2000
+    assert rules("q", 4, 0, 1.0, 4.0, 2.0, 3.0, 9.0, 9.0, 9.0, 9.0) == 2500
+
+
 def test_autotuner_samples_a_sixteenth(rules):
-    """Every stride-th run of four siblings: 16 for large iterations, fewer
-    so that at least 16 runs per SM remain, never below 1."""
+    """Every stride-th run of four siblings: a sixteenth of the work, at
+    least 64 children per SM, all of it for small iterations."""
     assert rules("t", 1 << 22, 152) == 16
     assert rules("t", 64 * 152 * 5, 152) == 5
     assert rules("t", 100, 152) == 1
@@ -256,6 +269,7 @@ def test_autotuner_retunes_when_half_the_problems_finished(rules):
     assert rules("r", 128, 64, 100) == 1 and rules("r", 1, 0, 100) == 0    # nothing left to tune for
     assert rules("r", 2, 1, 32) == 1
     assert rules("r", 256, 128, 31) == 0 and rules("r", 2, 1, 5) == 0      # too soon after the last tuning
+    assert rules("r", 256, 256, 1000) == 0                                # nothing finished: no re-tuning
 
 
 def test_autotuner_candidates(rules):
