@@ -82,9 +82,11 @@ struct CubeShared {
     float red[8][32];       // block reduction: 4 double-float sums x warps
 };
 
-// Directions are double-floats (hi + lo equals the unit vector to ~2^-44),
-// so differences of nearly parallel directions keep full FP32 relative
-// accuracy.  The pair loops take partners two at a time into the two lanes
+// Directions are formed as double-floats (hi + lo equals the unit vector to
+// ~2^-44) and stored with both parts; the pair loops read the FP32 parts only
+// and carry the low parts' effect as an absolute allowance (GOSMA_HI_ALLOW),
+// the model rows' low parts serve the point-dependent rotation angle, and the
+// image columns' are kept in the layout unread.  The pair loops take partners two at a time into the two lanes
 // of packed FP32x2 registers, so the records are stored in pairs, lanes
 // interleaved: one 16-byte load gives two aligned lane pairs.  A missing
 // partner of an odd count is a copy of the last one with zero weight.
@@ -280,12 +282,14 @@ __device__ __forceinline__ float gZ(float x) { return 1.f - ex2a(-2.f * GOSMA_LO
 // Error budget (u = 2^-24; approximate instructions as documented for PTX:
 // ex2 2^-22.5, rcp and sqrt 2^-23, rsqrt 2^-22.9 relative, i.e. <= 3u, 2u,
 // 2u, 2.2u; gosma_selftest_approx measures them on the device):
-//  * |v - u| and |v + u| from double-float directions: 2u per component, so
-//    sin(theta/2), cos(theta/2) carry <= 5.5u relative (squares 3.5u, sqrt 2u);
+//  * |v - u| and |v + u| from the directions' FP32 parts: the differences
+//    and sums rounded (u/2 per component), so sin(theta/2), cos(theta/2)
+//    carry <= 5.5u relative (squares 3.5u, sqrt 2u), and the missing low
+//    parts 0.87u absolute (GOSMA_HI_ALLOW);
 //  * the half-angle sine/cosine of s = psi_t + psi_r (row constants, evaluated
 //    in double-float, rounded once) carry <= u relative;
 //  * hence sin(B/2) = sin(theta/2) cos(s/2) - cos(theta/2) sin(s/2) is off by
-//    at most 7.5u (sin(theta/2) + sin(s/2)) =: es; cos(B/2) enters only
+//    at most 7.5u (sin(theta/2) + sin(s/2)) + 1.3u =: es; cos(B/2) enters only
 //    squared (in K and in cos B = 2 cos^2(B/2) - 1), bounded from the sine
 //    bounds as 1 - sin^2 (one rounding of the fused s^2 - 1: no square
 //    root);
@@ -300,6 +304,12 @@ __device__ __forceinline__ float gZ(float x) { return 1.f - ex2a(-2.f * GOSMA_LO
 //  * row weights, chunk sums (CHUNK-1 terms, plain FP32) and compensated row
 //    sums: applied once per row with directed rounding.
 #define GOSMA_TERM_SLACK (15.f * GOSMA_U)
+// The pair terms take the unit directions' FP32 parts only: |v -+ u| is then
+// within sqrt(3) u of its exact value (each low part is at most u/2), so the
+// sine and cosine of theta/2 within 0.87u, and a sine built from both
+// (sin(theta/2) cos(s/2) -+ cos(theta/2) sin(s/2)) within 0.87u (cos + sin)
+// <= 1.23u: an absolute allowance of 1.3u on every half-angle sine.
+#define GOSMA_HI_ALLOW (1.3f * GOSMA_U)
 // The cross pair's term slack: GOSMA_TERM_SLACK and the smallest K's
 // rounding without an outward factor (3.5u relative in g(K)/K: 5u in log2
 // units).
@@ -315,11 +325,11 @@ struct RowCross {
 // cross_pair2.  hCs = Cs / 2, nhSs = -Ss / 2, nA4 = -A4 (exact: the halves
 // multiply |v - u| and |v + u|, which are 2 sin and 2 cos of theta/2).
 struct RowCross2 {
-    float2 vx, vy, vz, wx, wy, wz;
+    float2 vx, vy, vz;
     float2 a, b, k0, hCs, nhSs, esS, nA4;
     __device__ __forceinline__ explicit RowCross2(const RowCross &R)
-        : vx(bc2(R.vx)), vy(bc2(R.vy)), vz(bc2(R.vz)), wx(bc2(R.wx)), wy(bc2(R.wy)), wz(bc2(R.wz)), a(bc2(R.a)),
-          b(bc2(R.b)), k0(bc2(R.k0)), hCs(bc2(0.5f * R.Cs)), nhSs(bc2(-0.5f * R.Ss)), esS(bc2(R.esS)), nA4(bc2(-R.A4)) {}
+        : vx(bc2(R.vx)), vy(bc2(R.vy)), vz(bc2(R.vz)), a(bc2(R.a)), b(bc2(R.b)), k0(bc2(R.k0)),
+          hCs(bc2(0.5f * R.Cs)), nhSs(bc2(-0.5f * R.Ss)), esS(bc2(R.esS)), nA4(bc2(-R.A4)) {}
 };
 
 __device__ __forceinline__ float2 sqrt2a(float2 x) { return make_float2(sqrta(x.x), sqrta(x.y)); }
@@ -332,7 +342,7 @@ __device__ __forceinline__ float2 ex2_2a(float2 x) { return make_float2(ex2a(x.x
 // K1i2j_ub_B) and to pc the term at the centre (Lemma 1), both without the
 // row multipliers.  Every operation is per lane, rounded to nearest as a
 // scalar FP32 operation would be (the error budget above holds per lane).
-//   |v -+ u|^2 from double-float directions, the centre term in the linear
+//   |v -+ u|^2 from the directions' FP32 parts, the centre term in the linear
 //   form above, then the bound: B = max(0, theta - s), s = psi_t,i + psi_r
 //   (Cs, Ss = cos, sin of s/2); cos^2(B/2) from the sine bounds as
 //   1 - s^2 (one rounding of 1 - s^2, 2u outward); K(a) - a - k2 with the
@@ -347,11 +357,10 @@ __device__ __forceinline__ void cross_pair2(const RowCross2 &R, float4 P0, float
     const float U = GOSMA_U;
     const float2 k2 = make_float2(P1.z, P1.w), Q = make_float2(P3.z, P3.w);
     const float2 ux = make_float2(P0.x, P0.y), uy = make_float2(P0.z, P0.w), uz = make_float2(P1.x, P1.y);
-    const float2 lx = make_float2(P2.x, P2.y), ly = make_float2(P2.z, P2.w), lz = make_float2(P3.x, P3.y);
-    const float2 dx = add2(sub2(R.vx, ux), sub2(R.wx, lx)), dy = add2(sub2(R.vy, uy), sub2(R.wy, ly)),
-                 dz = add2(sub2(R.vz, uz), sub2(R.wz, lz));
-    const float2 px = add2(add2(R.vx, ux), add2(R.wx, lx)), py = add2(add2(R.vy, uy), add2(R.wy, ly)),
-                 pz = add2(add2(R.vz, uz), add2(R.wz, lz));
+    // the directions' FP32 parts only (their low parts move sin and cos of
+    // theta/2 by at most 0.87u, which the row's allowance esS carries)
+    const float2 dx = sub2(R.vx, ux), dy = sub2(R.vy, uy), dz = sub2(R.vz, uz);
+    const float2 px = add2(R.vx, ux), py = add2(R.vy, uy), pz = add2(R.vz, uz);
     const float2 x2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));  // |v - u|^2 = 4 sin^2(theta/2)
     const float2 y2 = fma2(px, px, fma2(py, py, mul2(pz, pz)));  // |v + u|^2 = 4 cos^2(theta/2)
     // centre: kappa_1i(t0) = k0, angle theta
@@ -403,12 +412,11 @@ struct RowSelf {
 // (the half-angle pair of psi_i/2 halved, hcp = cp / 2, hsp = sp / 2,
 // nhsp = -sp / 2, exact: see RowCross2)
 struct RowSelf2 {
-    float2 vx, vy, vz, wx, wy, wz;
+    float2 vx, vy, vz;
     float2 a, b, k0, hcp, hsp, nhsp;
     __device__ __forceinline__ explicit RowSelf2(const RowSelf &R)
-        : vx(bc2(R.vx)), vy(bc2(R.vy)), vz(bc2(R.vz)), wx(bc2(R.wx)), wy(bc2(R.wy)), wz(bc2(R.wz)), a(bc2(R.a)),
-          b(bc2(R.b)), k0(bc2(R.k0)), hcp(bc2(0.5f * R.cp)), hsp(bc2(0.5f * R.sp)),
-          nhsp(bc2(-0.5f * R.sp)) {}
+        : vx(bc2(R.vx)), vy(bc2(R.vy)), vz(bc2(R.vz)), a(bc2(R.a)), b(bc2(R.b)), k0(bc2(R.k0)),
+          hcp(bc2(0.5f * R.cp)), hsp(bc2(0.5f * R.sp)), nhsp(bc2(-0.5f * R.sp)) {}
 };
 
 // Two self pairs (i, m) and (i, m') at once, lane x for partner m and lane y
@@ -433,11 +441,8 @@ __device__ __forceinline__ void self_pair2(const RowSelf2 &R, float4 P0, float4 
     const float2 am = make_float2(P1.z, P1.w), bm = make_float2(P3.z, P3.w), k0m = make_float2(P4.x, P4.y),
                  cpm = make_float2(P4.z, P4.w), spm = make_float2(P5.x, P5.y), Am = make_float2(P5.z, P5.w);
     const float2 ux = make_float2(P0.x, P0.y), uy = make_float2(P0.z, P0.w), uz = make_float2(P1.x, P1.y);
-    const float2 lx = make_float2(P2.x, P2.y), ly = make_float2(P2.z, P2.w), lz = make_float2(P3.x, P3.y);
-    const float2 dx = add2(sub2(R.vx, ux), sub2(R.wx, lx)), dy = add2(sub2(R.vy, uy), sub2(R.wy, ly)),
-                 dz = add2(sub2(R.vz, uz), sub2(R.wz, lz));
-    const float2 px = add2(add2(R.vx, ux), add2(R.wx, lx)), py = add2(add2(R.vy, uy), add2(R.wy, ly)),
-                 pz = add2(add2(R.vz, uz), add2(R.wz, lz));
+    const float2 dx = sub2(R.vx, ux), dy = sub2(R.vy, uy), dz = sub2(R.vz, uz);  // FP32 parts, as cross_pair2
+    const float2 px = add2(R.vx, ux), py = add2(R.vy, uy), pz = add2(R.vz, uz);
     const float2 x2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
     const float2 y2 = fma2(px, px, fma2(py, py, mul2(pz, pz)));
     // centre
@@ -459,7 +464,7 @@ __device__ __forceinline__ void self_pair2(const RowSelf2 &R, float4 P0, float4 
     const float2 sA = fma2(sx, hC, mul2(sy, hS));
     // 10u (sin(theta/2) + sin(psi/2)) as 5u sx + 20u hS (two roundings, at
     // most 2u of it: still above the 9.5u the sine carries)
-    const float2 es = fma2(bc2(5.f * U), sx, mul2(bc2(20.f * U), hS));
+    const float2 es = fma2(bc2(5.f * U), sx, fma2(bc2(20.f * U), hS, bc2(GOSMA_HI_ALLOW)));
     const float2 t1 = add2(sA, es);
     const float2 shi = make_float2(cA.x <= 16.f * U ? 1.f : fminf(t1.x, 1.f), cA.y <= 16.f * U ? 1.f : fminf(t1.y, 1.f));
     const float2 slo = max2(sub2(sA, es), 0.f);
@@ -538,11 +543,11 @@ __device__ inline void group_reduce_df(df v[4], CubeShared &cs, int gid, int gti
 // Blocks per SM the bound kernels ask the compiler to fit.  32- and 64-thread
 // blocks work on small mixtures, whose cubes are short and latency-bound, so
 // they need every resident warp (32 blocks of one warp, 16 of two: 64
-// registers per thread); 128- and 256-thread blocks keep 7 and 3 blocks
-// (73 and 85 registers), which is what the pair loops need without spills.
+// registers per thread); 128- and 256-thread blocks keep 8 and 3 blocks
+// (64 and 85 registers), which is what the pair loops need without spills.
 template <int BLOCK>
 constexpr int bound_min_blocks() {
-    return BLOCK <= 64 ? 1024 / BLOCK : BLOCK == 128 ? 7 : BLOCK == 256 ? 3 : 1;
+    return BLOCK <= 64 ? 1024 / BLOCK : BLOCK == 128 ? 8 : BLOCK == 256 ? 3 : 1;
 }
 
 // Work distribution of the persistent bound kernels: cubes are handed out
@@ -780,7 +785,7 @@ __device__ void cube_bounds(const MixDev &mx, const CubePrep &prep, const CubePr
                 R.Cs = 0.f;
                 R.Ss = 1.f;
             }
-            R.esS = 7.5f * U * R.Ss;
+            R.esS = fmaf(7.5f * U, R.Ss, GOSMA_HI_ALLOW);
             // phi_i b_i / g(b_i) from above (for b >= 9 g rounds to 1, at most 2^-25 high),
             // times the chunk and row-sum allowances
             float Bw = R.b < 9.f ? mx.phi1f[i] * R.b * rcpa(gZ(R.b)) * (1.f + 12.f * U) : mx.phi1f[i] * R.b;

@@ -77,6 +77,9 @@ L2E = F(1.4426950408889634)
 FU = F(U)
 SLACK = F(15) * FU
 CROSS_SLACK = F(20) * FU
+# the absolute allowance on the half-angle sines for directions taken in
+# their FP32 parts only (|v -+ u| within sqrt(3) u: sB within 1.23u)
+HI_ALLOW = F(1.3) * FU
 
 
 def c1(k):
@@ -146,6 +149,51 @@ def _cases(oracle_mod, rng, n):
     return {k: np.array([c[k] for c in out]) for k in out[0]}
 
 
+def _hi_part_cases(oracle_mod, rng, n, pool=40):
+    """Cross pairs where dropping the directions' low parts hurts most: fine
+    cubes, concentrated components (kappa_1 and kappa_2 in the thousands),
+    the image direction at an angle of s + 1/sqrt(kappa) or so from R0 v_0
+    (where the term is most sensitive to sin(B/2)), and, of `pool` random
+    directions each, the one whose FP32 parts lengthen |v - u| the most."""
+    out = []
+    while len(out) < n:
+        t0 = rng.uniform(-1, 1, 3)
+        thw = np.full(3, 10.0 ** rng.uniform(-5, -4))
+        rhw = 10.0 ** rng.uniform(-5, -4)
+        r0 = Rotation.random(random_state=rng).as_rotvec() * rng.uniform(0, 1)
+        R0 = Rotation.from_rotvec(r0).as_matrix()
+        sig = np.array([10.0 ** rng.uniform(-2, -1.3), 0.3])
+        k2 = 10.0 ** rng.uniform(3, 4)
+        best = None
+        for _ in range(pool):
+            mu1 = np.stack([t0 + rng.standard_normal(3) * rng.uniform(1, 3), rng.uniform(-3, 3, 3)])
+            v = (mu1 - t0) / np.linalg.norm(mu1 - t0, axis=1, keepdims=True)
+            ang = 2.2 * rhw + 2e-4 + rng.uniform(0.3, 3.0) / np.sqrt(k2)
+            axis = np.cross(v[0], rng.standard_normal(3))
+            u = Rotation.from_rotvec(axis / np.linalg.norm(axis) * ang).apply(v[0])
+            d_hi = np.linalg.norm(f32(v[0]).astype(np.float64) - f32(u).astype(np.float64))
+            gain = d_hi - np.linalg.norm(v[0] - u)
+            if best is None or gain > best[0]:
+                best = (gain, mu1, u)
+        _, mu1, u = best
+        m2 = R0 @ u
+        prob = {"mu1": mu1, "sigma1": sig, "phi1": np.array([0.4, 0.6]), "mu2": m2[None], "kappa2": np.array([k2]),
+                "phi2": np.array([1.0])}
+        mix = oracle_mod.Mixtures.from_problem(prob)
+        zeta = 0.01
+        ab = [oracle_mod.kappa_interval(mu1[i], sig[i], t0, thw, zeta) for i in range(2)]
+        if ab[0] is None or ab[1] is None:
+            continue
+        cube = np.concatenate([r0, [rhw], t0, thw])
+        v = (mu1 - t0) / np.linalg.norm(mu1 - t0, axis=1, keepdims=True)
+        out.append(dict(
+            v=v, u=R0.T @ m2, k2=k2, phi1=prob["phi1"], phi2=1.0, a=np.array([ab[0][0], ab[1][0]]),
+            b=np.array([ab[0][1], ab[1][1]]),
+            psit=np.array([oracle_mod.psi_t(mu1[i], t0, thw) for i in range(2)]), psir=oracle_mod.psi_r(rhw),
+            cross=oracle_mod.cross_ub_term(mix, 0, 0, cube, zeta)))
+    return {k: np.array([c[k] for c in out]) for k in out[0]}
+
+
 def _rows(c):
     """What the first phase stores for each model row (at the edge of its allowances)."""
     a = toward(c["a"] * (1 - U), -np.ones_like(c["a"]))
@@ -180,9 +228,12 @@ def _cross_parts(c, s):
     Ss = f32(sp.astype(np.float64) * Cr + cp.astype(np.float64) * Sr)
     Ss = np.where(Cs <= 0, F(1), Ss).astype(np.float32)
     Cs = np.where(Cs <= 0, F(0), Cs).astype(np.float32)
-    esS = (F(7.5) * FU) * Ss
-    d = [(vh[:, k] - uh[:, k]) + (vl[:, k] - ul[:, k]) for k in range(3)]
-    p = [(vh[:, k] + uh[:, k]) + (vl[:, k] + ul[:, k]) for k in range(3)]
+    # the directions' FP32 parts only: |v -+ u| within sqrt(3) u of the exact
+    # value, so sin and cos of theta/2 within 0.87u and sB within 1.23u
+    # absolute, which the row's allowance carries (1.3u)
+    esS = fma(np.full_like(Ss, F(7.5) * FU), Ss, np.full_like(Ss, HI_ALLOW))
+    d = [vh[:, k] - uh[:, k] for k in range(3)]
+    p = [vh[:, k] + uh[:, k] for k in range(3)]
     x2 = fma(d[0], d[0], fma(d[1], d[1], d[2] * d[2]))
     y2 = fma(p[0], p[0], fma(p[1], p[1], p[2] * p[2]))
     sx, sy = sqrta(x2, s[0]), sqrta(y2, s[1])  # 2 sin, 2 cos of theta/2; the halves in the row constants
@@ -235,8 +286,8 @@ def _self_parts(c, s):
     ph = f32(c["phi1"])
     Am = _aw(a[:, 1], ph[:, 1], s[7], s[8]).astype(np.float32)
     Ai = _aw(a[:, 0], ph[:, 0], s[9], s[10]).astype(np.float32)
-    d = [(vh[:, k] - mh[:, k]) + (vl[:, k] - ml[:, k]) for k in range(3)]
-    p = [(vh[:, k] + mh[:, k]) + (vl[:, k] + ml[:, k]) for k in range(3)]
+    d = [vh[:, k] - mh[:, k] for k in range(3)]
+    p = [vh[:, k] + mh[:, k] for k in range(3)]
     x2 = fma(d[0], d[0], fma(d[1], d[1], d[2] * d[2]))
     y2 = fma(p[0], p[0], fma(p[1], p[1], p[2] * p[2]))
     sx, sy = sqrta(x2, s[0]), sqrta(y2, s[1])  # 2 sin, 2 cos of theta/2
@@ -245,7 +296,7 @@ def _self_parts(c, s):
     hS = fma(hsp[:, 0], cp[:, 1], hcp[:, 0] * sp[:, 1])
     cA = fma(sy, hC, -(sx * hS))
     sA = fma(sx, hC, sy * hS)
-    es = fma(np.full_like(sx, F(5) * FU), sx, (F(20) * FU) * hS)
+    es = fma(np.full_like(sx, F(5) * FU), sx, fma(np.full_like(hS, F(20) * FU), hS, np.full_like(hS, HI_ALLOW)))
     api = cA <= F(16) * FU
     shi = np.where(api, F(1), np.minimum(sA + es, F(1))).astype(np.float32)
     slo = np.maximum(sA - es, F(0))
@@ -306,6 +357,26 @@ def test_cross_upper_bound_never_below_the_oracle(cases):
         worst = min(worst, ratio.min())
         assert np.all(ub[ok] >= ref[ok]), (signs, ratio.min())
     assert worst >= 1.0
+
+
+def test_cross_bound_covers_the_dropped_low_parts(oracle_mod):
+    """The pair code takes the unit directions' FP32 parts only; the row's
+    absolute allowance of 1.3u on sin(B/2) covers what the low parts would
+    have changed.  On the pairs where that matters most the bound stays
+    above the oracle's under every sign of the instruction errors, and
+    without the allowance it does not."""
+    global HI_ALLOW
+    c = _hi_part_cases(oracle_mod, np.random.default_rng(23), 300)
+    ok = c["cross"] > FLOOR
+    assert ok.sum() > 200
+    for signs in itertools.product((-1.0, 1.0), repeat=8):
+        assert np.all(_cross(c, signs)[ok] >= c["cross"][ok]), signs
+    keep, HI_ALLOW = HI_ALLOW, F(0)
+    try:
+        low = [np.any(_cross(c, signs)[ok] < c["cross"][ok]) for signs in ((-1.0,) * 8, (1.0,) * 8)]
+    finally:
+        HI_ALLOW = keep
+    assert any(low)
 
 
 def test_self_lower_bound_never_above_the_oracle(cases):
