@@ -101,6 +101,24 @@ def test_scene_at_paper_size(ctx, oracle_mod):
     assert 50 <= g["k"] <= 100
 
 
+def test_scene_at_paper_default_scales(ctx, oracle_mod):
+    """The same scene at the paper's default scale parameters (Sec. 7's
+    set-up: lambda_p = 0.25 m, a squared-distance penalty of 0.0625 m^2, and
+    lambda_f = 2 degrees): thousands of clusters (about 3,500 and 1,600), so
+    each pass runs thousands of grid-wide rounds; two passes keep the oracle
+    to a few seconds."""
+    sc = synth.scene_points(11)
+    g = ctx.dp_means(sc["points"], 0.0625, max_iter=2, kmax=8192)
+    o = oracle_mod.dp_cluster(sc["points"], 0.0625, max_iter=2, kmax=8192)
+    _compare(g, o, "sigma", 1e-13)
+    assert g["k"] > 2000
+    lam = np.cos(np.radians(2.0))
+    g = ctx.dp_vmf_means(sc["bearings"], lam, max_iter=2, kmax=8192)
+    o = oracle_mod.dp_cluster(sc["bearings"], lam, vmf=True, max_iter=2, kmax=8192)
+    _compare(g, o, "kappa", 1e-12)
+    assert g["k"] > 1000
+
+
 def test_generated_mixtures_feed_the_objective(ctx, oracle_mod):
     """The generated GMM and vMFMM are valid gosma_set_mixtures inputs and the
     device objective on them equals the oracle objective on the oracle's."""
