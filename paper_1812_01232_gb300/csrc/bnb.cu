@@ -219,16 +219,16 @@ __global__ void ext_scatter(uint32_t *__restrict__ keys, const Node *__restrict_
 }
 
 // ---------------------------------------------------------------- 3. bound
-// Pre-pass for the children: one thread per child.
-__global__ void cube_prep_children(Domain dom, const Node *__restrict__ parents, int np, CubePrep *__restrict__ prep,
-                                   int point) {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= 8 * np) return;
-    const Node p = parents[c >> 3];
-    Node ch = child_of(p, c & 7, split_rotation(p));
-    CubeGeom g;
-    decode(ch, dom, g);
-    cube_prepare(g.r0, g.rhw, g.t0, g.thw, prep[c], point ? prep_point(prep, 8 * np, c) : nullptr);
+// Pre-pass for the children: a block per PREP_TILE children, the work shared
+// between siblings (prep_children_tile).
+__global__ void __launch_bounds__(PREP_TILE)
+    cube_prep_children(Domain dom, const Node *__restrict__ parents, int np, CubePrep *__restrict__ prep, int point) {
+    const int n = 8 * np;
+    prep_children_tile(blockIdx.x * PREP_TILE, n, prep, n, [&](int w, Node &p, Domain &d, bool &pt) {
+        p = parents[w >> 3];
+        d = dom;
+        pt = point != 0;
+    });
 }
 
 constexpr int CHILD_RUN = 4;  // children per work item (a divisor of 8)
@@ -554,7 +554,8 @@ static int launch_children(gosma_ctx *ctx, const Domain &dom, BnbState *s, int n
     if (grid > 8LL * np / CHILD_RUN) grid = 8LL * np / CHILD_RUN;
     e = cudaMemsetAsync(s->kid_rot, 0, 2 * sizeof(unsigned int), ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "memset(children)");
-    cube_prep_children<<<(8 * np + 127) / 128, 128, 0, ctx->stream>>>(dom, s->parents, np, s->rot, ctx->mix.psi_point);
+    cube_prep_children<<<(8 * np + PREP_TILE - 1) / PREP_TILE, PREP_TILE, 0, ctx->stream>>>(dom, s->parents, np, s->rot,
+                                                                                          ctx->mix.psi_point);
     ++ctx->launches;
     df z2;
     split_double(ctx->zeta * ctx->zeta, z2.h, z2.l);

@@ -59,12 +59,29 @@ __host__ __device__ inline void decode(const Node &n, const Domain &d, CubeGeom 
     }
 }
 
+// The split rule's comparison psi_r(lr) >= psit, taken in FP32: psit is a
+// float, so the FP64 comparison holds exactly when psit is at most the
+// largest float at or below psi_r(lr).  psi_r(lr) = fl(sqrt(3) pi) 2^-lr for
+// lr >= 1 (scaling by 2^-lr is exact) and pi at lr = 0, so that float is
+// PSI_R_F 2^-lr, PSI_R_F = fl(sqrt(3) pi) = 5.441398092702653 rounded down to
+// a float, and PSI_PI_F at lr = 0.  (FP64 instructions cost the FP64 unit a
+// whole warp's time, and every thread of a bound kernel tests its run's
+// parent.)
+constexpr float PSI_R_F = 0x1.5c3fdcp+2f;
+__host__ __device__ inline float psi_r_level_floor(int lr) {
+    if (lr == 0) return PSI_PI_F;
+    const uint32_t e = (uint32_t)(127 - lr) << 23;  // 2^-lr, 1 <= lr < 127
+    float s;
+    memcpy(&s, &e, 4);
+    return PSI_R_F * s;
+}
+
 // Child k of a parent (Sec. 4.1: the split halves the rotation cube or the
 // translation cuboid, whichever has the greater angular uncertainty).
 __host__ __device__ inline bool split_rotation(const Node &p) {
     if (p.lr >= MAX_LEVEL) return false;
     if (p.lt >= MAX_LEVEL) return true;
-    return psi_r_level(p.lr) >= (double)p.psit;
+    return p.psit <= psi_r_level_floor(p.lr);
 }
 
 __host__ __device__ inline Node child_of(const Node &p, int k, bool rot) {
@@ -78,6 +95,91 @@ __host__ __device__ inline Node child_of(const Node &p, int k, bool rot) {
         c.flags &= ~1u;  // the cuboid changed: self sums must be recomputed
     }
     return c;
+}
+
+// Pre-pass of the children w in [base, base + PREP_TILE) of n (base and n
+// multiples of 8, so that a tile holds whole families of eight siblings), by
+// a block of PREP_TILE threads.  An FP64 instruction costs the FP64 unit a
+// whole warp's time however few of its lanes are active, so the pre-pass's
+// FP64 bulk is shared between siblings and packed into the block's first
+// threads:
+//   * Rodrigues' formula and the rotation-cube terms run once per family for
+//     a translation split (the children keep their parent's rotation cube)
+//     and once per child for a rotation split;
+//   * the rotation uncertainty angle runs once per family (siblings share a
+//     level);
+//   * every child splits its own cuboid.
+// The shared parts are computed for the family's first child and copied to
+// its siblings: every record equals cube_prepare's for that child.
+// fam(w, parent, domain, point) gives child w's parent node, its problem's
+// translation domain and whether the point-dependent terms are wanted; nrec
+// is the record count of prep (the point-dependent records follow it).
+constexpr int PREP_TILE = 256;
+
+template <class Family>
+__device__ void prep_children_tile(int base, int n, CubePrep *__restrict__ prep, int nrec, const Family &fam) {
+    __shared__ double s_geo[PREP_TILE][4];  // r0, rotation half-width of each child
+    __shared__ int s_job[PREP_TILE];        // children that need Rodrigues' formula, packed
+    __shared__ int s_wsum[PREP_TILE / 32 + 1];
+    __shared__ unsigned char s_pt[PREP_TILE];
+    const int t = threadIdx.x, w = base + t, lane = t & 31, warp = t >> 5;
+    const bool valid = w < n;
+    bool rot = false, point = false;
+    CubeGeom g;
+    if (valid) {
+        Node p;
+        Domain d;
+        fam(w, p, d, point);
+        rot = split_rotation(p);
+        decode(child_of(p, w & 7, rot), d, g);
+        for (int k = 0; k < 3; ++k) s_geo[t][k] = g.r0[k];
+        s_geo[t][3] = g.rhw;
+        s_pt[t] = point ? 1 : 0;
+    }
+    const bool need = valid && (rot || (w & 7) == 0);
+    const unsigned bal = __ballot_sync(0xffffffffu, need);
+    if (lane == 0) s_wsum[warp] = __popc(bal);
+    __syncthreads();
+    if (t == 0) {
+        int sum = 0;
+        for (int k = 0; k < PREP_TILE / 32; ++k) {
+            const int x = s_wsum[k];
+            s_wsum[k] = sum;
+            sum += x;
+        }
+        s_wsum[PREP_TILE / 32] = sum;
+    }
+    __syncthreads();
+    if (need) s_job[s_wsum[warp] + __popc(bal & ((1u << lane) - 1u))] = t;
+    __syncthreads();
+    if (t < PREP_TILE / 8 && base + 8 * t < n) cube_prepare_psi_r(s_geo[8 * t][3], prep[base + 8 * t]);
+    if (t < s_wsum[PREP_TILE / 32]) {
+        const int j = s_job[t];
+        cube_prepare_rotation(s_geo[j], s_geo[j][3], prep[base + j],
+                              s_pt[j] ? prep_point(prep, nrec, base + j) : nullptr);
+    }
+    __syncthreads();  // the shared parts above are visible to the block
+    if (!valid) return;
+    CubePrep &o = prep[w];
+    if (w & 7) {
+        const CubePrep &f = prep[w & ~7];
+        o.Cr = f.Cr;
+        o.Sr = f.Sr;
+        o.psi_r = f.psi_r;
+        if (!rot) {
+            for (int k = 0; k < 9; ++k) {
+                o.Rh[k] = f.Rh[k];
+                o.Rl[k] = f.Rl[k];
+            }
+            o.infeasible = f.infeasible;
+            if (point) {
+                const CubePrepPoint &fp = *prep_point(prep, nrec, w & ~7);
+                CubePrepPoint &op = *prep_point(prep, nrec, w);
+                for (int k = 0; k < PREP_POINT_WORDS; ++k) op.pj[k] = fp.pj[k];
+            }
+        }
+    }
+    cube_prepare_translation(g.t0, g.thw, o);
 }
 
 }  // namespace gosma

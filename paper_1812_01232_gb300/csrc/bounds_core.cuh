@@ -141,11 +141,14 @@ __device__ inline int pow2ceil(int x) {
     return p;
 }
 
-// Pre-pass for one cube: Rodrigues' formula (Sec. 4.1), Lemma 2 read as
-// angle(R_r p, R_r0 p) <= |r - r0| <= sqrt(3) r_hw capped at pi, and the
-// translation cuboid split into double-floats.
-__device__ inline void cube_prepare(const double r0[3], double rhw, const double t0[3], const double thw[3],
-                                    CubePrep &o, CubePrepPoint *pt) {
+// Pre-pass for one cube, in three parts that depend on different parts of
+// the cube, so that a caller can share them between cubes (the eight children
+// of a translation split share their parent's rotation cube, the children of
+// any split share a level): Rodrigues' formula (Sec. 4.1) and the
+// rotation-cube terms, Lemma 2 read as angle(R_r p, R_r0 p) <= |r - r0| <=
+// sqrt(3) r_hw capped at pi, and the translation cuboid split into
+// double-floats.
+__device__ inline void cube_prepare_rotation(const double r0[3], double rhw, CubePrep &o, CubePrepPoint *pt) {
     double th2 = r0[0] * r0[0] + r0[1] * r0[1] + r0[2] * r0[2];
     double th = sqrt(th2), A, B;
     if (th < 1e-8) {
@@ -162,24 +165,12 @@ __device__ inline void cube_prepare(const double r0[3], double rhw, const double
                    A * z + B * x * y,         1.0 - B * (x * x + z * z), -A * x + B * y * z,
                    -A * y + B * x * z,        A * x + B * y * z,         1.0 - B * (x * x + y * y)};
     for (int k = 0; k < 9; ++k) split_double(R[k], o.Rh[k], o.Rl[k]);
-    double pr = sqrt(3.0) * rhw;
-    if (pr > M_PI) pr = M_PI;
-    double sh, ch;
-    sincos(0.5 * pr, &sh, &ch);
-    o.Sr = __double2float_ru(sh);
-    o.Cr = __double2float_rd(ch);
-    o.psi_r = (float)pr;
     double d2 = 0.0;
     for (int k = 0; k < 3; ++k) {
         double e = fabs(r0[k]) - rhw;
         if (e > 0) d2 += e * e;
     }
     o.infeasible = d2 > M_PI * M_PI ? 1 : 0;
-    for (int k = 0; k < 3; ++k) {
-        split_double(t0[k], o.th[k], o.tl[k]);
-        split_double(thw[k], o.wh[k], o.wl[k]);
-    }
-    o.pad[0] = o.pad[1] = 0.f;
     if (!pt) return;  // the point-dependent terms below are read only in that mode
     // right Jacobian J_r(r0) = I - B [r0]x + C [r0]x^2, C = (|r0| - sin|r0|) / |r0|^3
     // (R_{r0 + d} = R_r0 R_{J_r d} to first order), and the vertex images J_r d / 2
@@ -207,6 +198,31 @@ __device__ inline void cube_prepare(const double r0[3], double rhw, const double
     pt->pj[32] = __double2float_ru(0.375 * rhw * rhw);
     pt->pj[33] = __double2float_ru(64.0 * 0x1p-48 * cmax);
     pt->pj[34] = pt->pj[35] = 0.f;
+}
+
+__device__ inline void cube_prepare_psi_r(double rhw, CubePrep &o) {
+    double pr = sqrt(3.0) * rhw;
+    if (pr > M_PI) pr = M_PI;
+    double sh, ch;
+    sincos(0.5 * pr, &sh, &ch);
+    o.Sr = __double2float_ru(sh);
+    o.Cr = __double2float_rd(ch);
+    o.psi_r = (float)pr;
+}
+
+__device__ inline void cube_prepare_translation(const double t0[3], const double thw[3], CubePrep &o) {
+    for (int k = 0; k < 3; ++k) {
+        split_double(t0[k], o.th[k], o.tl[k]);
+        split_double(thw[k], o.wh[k], o.wl[k]);
+    }
+    o.pad[0] = o.pad[1] = 0.f;
+}
+
+__device__ inline void cube_prepare(const double r0[3], double rhw, const double t0[3], const double thw[3],
+                                    CubePrep &o, CubePrepPoint *pt) {
+    cube_prepare_rotation(r0, rhw, o, pt);
+    cube_prepare_psi_r(rhw, o);
+    cube_prepare_translation(t0, thw, o);
 }
 
 // Lemma 2, point-dependent form, for one model direction v (the unit vector
@@ -515,29 +531,39 @@ __device__ __forceinline__ void gsync(int gid) {
     }
 }
 
-// Warp + group reduction of four double-floats; the result is valid in the
-// group's thread 0 (gtid == 0).
+// Warp + group reduction of four double-floats, scattered: on return, lane
+// 8k of the group's first warp (gtid == 8k, k = 0..3) holds the group's
+// total of v[k].  Within a warp the first two levels halve the sums between
+// the lanes (after xor 16, lanes 0-15 carry sums 0 and 1 and lanes 16-31
+// sums 2 and 3; after xor 8, lanes 8k .. 8k + 7 carry sum k), and the last
+// three reduce within eight lanes: 7 double-float additions per lane instead
+// of 20 for four full reductions, and no barrier for a one-warp group.
 template <int BLOCK, int GT>
-__device__ inline void group_reduce_df(df v[4], CubeShared &cs, int gid, int gtid) {
+__device__ inline df group_reduce_df(const df v[4], CubeShared &cs, int gid, int gtid) {
     const int lane = gtid & 31, warp = gtid >> 5;
+    const bool h16 = lane & 16, h8 = lane & 8;
+    auto xshfl = [](df x, int o) {
+        return df{__shfl_xor_sync(0xffffffffu, x.h, o), __shfl_xor_sync(0xffffffffu, x.l, o)};
+    };
+    const df g0 = df_add(h16 ? v[2] : v[0], xshfl(h16 ? v[0] : v[2], 16));
+    const df g1 = df_add(h16 ? v[3] : v[1], xshfl(h16 ? v[1] : v[3], 16));
+    df b = df_add(h8 ? g1 : g0, xshfl(h8 ? g0 : g1, 8));
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
-        for (int o = 16; o > 0; o >>= 1) {
-            df t = {__shfl_down_sync(0xffffffffu, v[k].h, o), __shfl_down_sync(0xffffffffu, v[k].l, o)};
-            v[k] = df_add(v[k], t);
+    for (int o = 4; o > 0; o >>= 1) b = df_add(b, xshfl(b, o));
+    if constexpr (GT > 32) {
+        if ((lane & 7) == 0) {
+            cs.red[2 * (lane >> 3)][warp] = b.h;
+            cs.red[2 * (lane >> 3) + 1][warp] = b.l;
         }
-    if (lane == 0)
-        for (int k = 0; k < 4; ++k) {
-            cs.red[2 * k][warp] = v[k].h;
-            cs.red[2 * k + 1][warp] = v[k].l;
-        }
-    gsync<BLOCK, GT>(gid);
-    if (gtid == 0)
-        for (int k = 0; k < 4; ++k) {
+        gsync<BLOCK, GT>(gid);
+        if (gtid < 32 && (lane & 7) == 0) {
+            const int k = lane >> 3;
             df s = {cs.red[2 * k][0], cs.red[2 * k + 1][0]};
             for (int w = 1; w < GT / 32; ++w) s = df_add(s, {cs.red[2 * k][w], cs.red[2 * k + 1][w]});
-            v[k] = s;
+            b = s;
         }
+    }
+    return b;
 }
 
 // Blocks per SM the bound kernels ask the compiler to fit.  32- and 64-thread
@@ -918,13 +944,24 @@ __device__ void cube_bounds(const MixDev &mx, const CubePrep &prep, const CubePr
     }
 
     // ---------------- phase 3: block reduction (double-float)
-    group_reduce_df<BLOCK, GT>(T, cs, gid, gtid);
+    const df tot = group_reduce_df<BLOCK, GT>(T, cs, gid, gtid);
+    // Lanes 0, 8, 16, 24 of the group's first warp hold the four sums and
+    // convert them to FP64 together: an FP64 instruction costs the FP64 unit
+    // a whole warp's time however few lanes run it.
+    // (the self sums only when computed: callers that skip them use cached ones)
+    if (tid < 32 && (tid & 7) == 0) {
+        const int k = tid >> 3;
+        const double d = (need_self || (k & 1)) ? (double)tot.h + (double)tot.l : 0.0;
+        if (k == 0)
+            out.self_lb = d;
+        else if (k == 1)
+            out.cross_ub = d;
+        else if (k == 2)
+            out.self_c = d;
+        else
+            out.cross_c = d;
+    }
     if (tid == 0) {
-        // (the self sums only when computed: callers that skip them use cached ones)
-        out.self_lb = need_self ? (double)T[0].h + (double)T[0].l : 0.0;
-        out.cross_ub = (double)T[1].h + (double)T[1].l;
-        out.self_c = need_self ? (double)T[2].h + (double)T[2].l : 0.0;
-        out.cross_c = (double)T[3].h + (double)T[3].l;
         out.psi_r = cs.rot.psi_r;
         float smax = __uint_as_float(cs.spsi_max);
         out.psi_t_max = smax >= 1.f ? PSI_PI_F : fminf(2.f * asinf(smax), PSI_PI_F);

@@ -552,17 +552,18 @@ __global__ void mp_flip(ProbState *__restrict__ S, int nprob, int *__restrict__ 
     }
 }
 
-__global__ void mp_prep(const ProbDev *__restrict__ P, const int *__restrict__ off, int nprob,
-                        const Node *__restrict__ parents, CubePrep *__restrict__ prep) {
+__global__ void __launch_bounds__(PREP_TILE) mp_prep(const ProbDev *__restrict__ P, const int *__restrict__ off,
+                                                     int nprob, const Node *__restrict__ parents,
+                                                     CubePrep *__restrict__ prep) {
     const int N = off[nprob];
-    for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < N; w += gridDim.x * blockDim.x) {
-        int k = mp_find(off, nprob, w), c = w - off[k];
-        const Node p = parents[w >> 3];
-        Node ch = child_of(p, c & 7, split_rotation(p));
-        CubeGeom g;
-        decode(ch, P[k].dom, g);
-        cube_prepare(g.r0, g.rhw, g.t0, g.thw, prep[w], P[k].mx.psi_point ? prep_point(prep, N, w) : nullptr);
-    }
+    // tiles of whole families: the problems' offsets are multiples of 8
+    for (int base = blockIdx.x * PREP_TILE; base < N; base += gridDim.x * PREP_TILE)
+        prep_children_tile(base, N, prep, N, [&](int w, Node &p, Domain &d, bool &pt) {
+            const int k = mp_find(off, nprob, w);
+            p = parents[w >> 3];
+            d = P[k].dom;
+            pt = P[k].mx.psi_point != 0;
+        });
 }
 
 constexpr int MP_CHILD_RUN = 4;  // children per work item (a divisor of 8)
@@ -1788,7 +1789,7 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
         mp_cscan_any<true><<<nprob, MP_BLOCK, 0, st>>>(dS, Qb, nprob);
         mp_scatter<true><<<chunk_grid, CH_BLOCK, 0, st>>>(dP, dS, Qb, nprob, parents, off);
         mp_flip<<<(nprob + 255) / 256, 256, 0, st>>>(dS, nprob, d_tcount, lo.trace_cap);
-        mp_prep<<<prep_grid, 128, 0, st>>>(dP, off, nprob, parents, prep);
+        mp_prep<<<2 * ctx->sm_count, PREP_TILE, 0, st>>>(dP, off, nprob, parents, prep);
         ctx->launches += 16;
     };
     auto back = [&]() -> cudaError_t {

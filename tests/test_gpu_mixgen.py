@@ -4,7 +4,8 @@ oracle.  Labels, cluster counts, passes and centres are integer or exact
 results (cluster sums are exact integers on both sides and every distance is
 formed with the same rounded operations), so they must agree bit for bit;
 the fitted sigma and kappa sum per-point terms in different orders and agree
-to 1e-13 and 1e-12 relative."""
+to 1e-13 and 1e-12 relative (kappa above 100, whose fit amplifies the
+summation's rounding by kappa: 1e-14 kappa relative)."""
 import json
 import os
 
@@ -33,7 +34,10 @@ def _compare(g, o, key, tol):
     np.testing.assert_array_equal(g["labels"], o["labels"])
     np.testing.assert_array_equal(g["mu"], o["mu"])
     np.testing.assert_array_equal(g["phi"], o["phi"])
-    np.testing.assert_allclose(g[key], o[key], rtol=tol)
+    err = np.abs(g[key] - o[key])
+    bad = err > tol * np.abs(o[key])
+    assert not bad.any(), "%s differs at %d of %d clusters (largest relative difference %.3g)" % (
+        key, bad.sum(), len(bad), (err / np.abs(o[key])).max())
 
 
 def test_worked_examples(ctx):
@@ -115,7 +119,12 @@ def test_scene_at_paper_default_scales(ctx, oracle_mod):
     lam = np.cos(np.radians(2.0))
     g = ctx.dp_vmf_means(sc["bearings"], lam, max_iter=2, kmax=8192)
     o = oracle_mod.dp_cluster(sc["bearings"], lam, vmf=True, max_iter=2, kmax=8192)
-    _compare(g, o, "kappa", 1e-12)
+    # kappa solves A(kappa) = Rbar with A(kappa) ~ 1 - 1/kappa, so a change of
+    # Rbar (the two sides sum the same unit vectors in different orders, a
+    # few u apart) moves kappa by kappa^2 dRbar: relative 1e-14 kappa allows
+    # dRbar up to ~90u (the 12-degree clusters, kappa < 1,000, stay within
+    # 1e-12; these reach 11,000)
+    _compare(g, o, "kappa", 1e-12 * np.maximum(1.0, 1e-2 * o["kappa"]))
     assert g["k"] > 1000
 
 
