@@ -80,9 +80,10 @@ typedef struct {
     long long queue_capacity; /* device queue capacity in cubes (<= 0: library default) */
     int bound_block;     /* gosma_bnb_solve_batch: threads per block of the bound kernel, and */
     int bound_cubes;     /* sub-cubes per block (groups of bound_block / bound_cubes threads):
-                            32x1, 64x1, 64x2, 128x1, 128x2, 128x4, 256x1, 256x2, 256x4, 512x1 or
-                            1024x1; both 0 (the default): chosen by the autotuner.  The
-                            single-problem solver ignores them. */
+                            32x1, 32x2 (half-warp groups, for mixtures of at most 16 model
+                            components), 64x1, 64x2, 128x1, 128x2, 128x4, 256x1, 256x2, 256x4,
+                            512x1 or 1024x1; both 0 (the default): chosen by the autotuner.
+                            The single-problem solver ignores them. */
 } gosma_opts;
 
 typedef struct {

@@ -155,7 +155,9 @@ __global__ void ext_count(const uint32_t *__restrict__ keys, unsigned long long 
 }
 
 // One block: per tile, how many of its ties are popped and where its popped
-// nodes start in the parent buffer.
+// nodes start in the parent buffer.  Each thread takes SEL_ITEMS consecutive
+// tiles, so that a queue of tens of millions of keys (thousands of tiles)
+// needs few block-wide scans.
 __global__ void ext_scan(const int2 *__restrict__ cnt, int ntile, const Status *st, int2 *__restrict__ off) {
     __shared__ int sh[32];
     __shared__ int carry_eq, carry_pop;
@@ -165,19 +167,33 @@ __global__ void ext_scan(const int2 *__restrict__ cnt, int ntile, const Status *
     }
     __syncthreads();
     const int ties = (int)st->sel_need[2];
-    for (int b0 = 0; b0 < ntile; b0 += SEL_BLOCK) {
-        int b = b0 + threadIdx.x;
-        int2 c = b < ntile ? cnt[b] : make_int2(0, 0);
-        int tot;
-        int eq_before = carry_eq + block_excl_scan(c.y, sh, tot);
-        int take = min(max(ties - eq_before, 0), c.y);
-        int pop = c.x + take;
-        int tot_pop;
+    for (int b0 = 0; b0 < ntile; b0 += SEL_TILE) {
+        const int b = b0 + threadIdx.x * SEL_ITEMS;
+        int2 c[SEL_ITEMS];
+        int eq = 0;
+#pragma unroll
+        for (int k = 0; k < SEL_ITEMS; ++k) {
+            c[k] = b + k < ntile ? cnt[b + k] : make_int2(0, 0);
+            eq += c[k].y;
+        }
+        int tot_eq, tot_pop;
+        int eq_before = carry_eq + block_excl_scan(eq, sh, tot_eq);
+        int take[SEL_ITEMS], pop = 0;
+#pragma unroll
+        for (int k = 0; k < SEL_ITEMS; ++k) {
+            take[k] = min(max(ties - eq_before, 0), c[k].y);
+            eq_before += c[k].y;
+            pop += c[k].x + take[k];
+        }
         int pop_before = carry_pop + block_excl_scan(pop, sh, tot_pop);
-        if (b < ntile) off[b] = make_int2(pop_before, take);
+#pragma unroll
+        for (int k = 0; k < SEL_ITEMS; ++k) {
+            if (b + k < ntile) off[b + k] = make_int2(pop_before, take[k]);
+            pop_before += c[k].x + take[k];
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
-            carry_eq += tot;
+            carry_eq += tot_eq;
             carry_pop += tot_pop;
         }
         __syncthreads();
@@ -233,21 +249,28 @@ __global__ void __launch_bounds__(PREP_TILE)
 
 constexpr int CHILD_RUN = 4;  // children per work item (a divisor of 8)
 
-template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK, bound_min_blocks<BLOCK>())
+// G cubes per block: groups of GT = BLOCK / G threads (one group: the
+// block; two half-warp groups in a one-warp block for the smallest
+// mixtures), each with its own shared arrays (group_floats floats of the
+// dynamic shared memory), its own per-cube scalars and its own work slot.
+template <int BLOCK, int G>
+__global__ void __launch_bounds__(BLOCK, G == 1 ? bound_min_blocks<BLOCK>() : 24)
     bound_children(MixDev mx, Domain dom, df zeta2, const Node *__restrict__ parents, int np,
                    const CubePrep *__restrict__ prep, Node *__restrict__ kids, double *__restrict__ kid_ub,
-                   unsigned int *__restrict__ n_self, int *__restrict__ counter) {
+                   unsigned int *__restrict__ n_self, int *__restrict__ counter, int group_floats) {
+    constexpr int GT = BLOCK / G;
     extern __shared__ float smem_f[];
-    __shared__ CubeShared cs;
-    __shared__ CubeSums sums;
-    __shared__ int slot;
-    SmemArrays sm = carve(smem_f, mx.n1, mx.n2);
+    __shared__ CubeShared cs[G];
+    __shared__ CubeSums sums[G];
+    __shared__ int slot[G];
+    const int gid = threadIdx.x / GT, gtid = threadIdx.x % GT;
+    SmemArrays sm = carve(smem_f + (size_t)gid * group_floats, mx.n1, mx.n2);
     const double inf = __longlong_as_double(0x7ff0000000000000LL);
     // work in quarters of a parent's children (CHILD_RUN siblings): after a
     // rotation split the siblings share the parent's cuboid, so the rows of
     // the first serve the others
-    for (int g = next_cube(counter, &slot); g < 8 * np / CHILD_RUN; g = next_cube(counter, &slot)) {
+    for (int g = next_cube<BLOCK, GT>(counter, &slot[gid], gid, gtid); g < 8 * np / CHILD_RUN;
+         g = next_cube<BLOCK, GT>(counter, &slot[gid], gid, gtid)) {
         // the run's parent; a child keeps its cuboid, and so its self sums, after a rotation split
         const Node &par = parents[(CHILD_RUN * g) >> 3];
         const bool rot = split_rotation(par);
@@ -255,26 +278,27 @@ __global__ void __launch_bounds__(BLOCK, bound_min_blocks<BLOCK>())
 #pragma unroll 1
         for (int k = 0; k < CHILD_RUN; ++k) {
             const int c = CHILD_RUN * g + k;
-            cube_bounds<BLOCK>(mx, prep[c], prep_point(prep, 8 * np, c), zeta2, need_self, cs, sm, sums, 0,
-                               threadIdx.x, k > 0 && !need_self);
-            if (threadIdx.x == 0) {
+            cube_bounds<BLOCK, GT>(mx, prep[c], prep_point(prep, 8 * np, c), zeta2, need_self, cs[gid], sm,
+                                   sums[gid], gid, gtid, k > 0 && !need_self);
+            if (gtid < 2) {
+                const CubeSums &su = sums[gid];
+                const double sl = need_self ? su.self_lb : par.self_lb;
+                const double sc = need_self ? su.self_c : par.self_c;
+                double lb, ub;
+                cube_lb_ub(sl, su.cross_ub, sc, su.cross_c, gtid == 0, lb, ub);
+                if (gtid == 1) continue;
                 const Node p = par;
                 Node ch = child_of(p, c & 7, rot);
                 if (need_self) atomicAdd(n_self, 1u);
-                double sl = need_self ? sums.self_lb : p.self_lb;
-                double sc = need_self ? sums.self_c : p.self_c;
-                double lb, ub;
-                if (!sums.feasible) {
+                if (!su.feasible) {
                     lb = ub = inf;
-                } else {
-                    double S = sl + 2.0 * sums.cross_ub;
-                    lb = sl - 2.0 * sums.cross_ub - 1e-12 * S;
-                    ub = sums.centre_feasible ? sc - 2.0 * sums.cross_c : inf;
+                } else if (!su.centre_feasible) {
+                    ub = inf;
                 }
                 ch.lb = lb;
                 ch.self_lb = sl;
                 ch.self_c = sc;
-                ch.psit = sums.psi_t_max;
+                ch.psit = su.psi_t_max;
                 ch.flags |= 1u;
                 kids[c] = ch;
                 kid_ub[c] = ub;
@@ -541,17 +565,19 @@ static int alloc_state(gosma_ctx *ctx, unsigned long long cap, int pop, BnbState
     return GOSMA_OK;
 }
 
-template <int BLOCK>
+template <int BLOCK, int G = 1>
 static int launch_children(gosma_ctx *ctx, const Domain &dom, BnbState *s, int np) {
-    size_t smem = bounds_smem_bytes(ctx->n1, ctx->n2);
-    auto kern = bound_children<BLOCK>;
+    const size_t group = (bounds_smem_bytes(ctx->n1, ctx->n2) + 15) & ~(size_t)15;
+    const size_t smem = group * G;
+    auto kern = bound_children<BLOCK, G>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFuncSetAttribute(children)");
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BLOCK, smem);
     if (e != cudaSuccess || per_sm < 1) return fail(ctx, GOSMA_ECUDA, "children kernel does not fit");
     long long grid = (long long)ctx->sm_count * per_sm;
-    if (grid > 8LL * np / CHILD_RUN) grid = 8LL * np / CHILD_RUN;
+    const long long runs = 8LL * np / CHILD_RUN;
+    if (grid > (runs + G - 1) / G) grid = (runs + G - 1) / G;
     e = cudaMemsetAsync(s->kid_rot, 0, 2 * sizeof(unsigned int), ctx->stream);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "memset(children)");
     cube_prep_children<<<(8 * np + PREP_TILE - 1) / PREP_TILE, PREP_TILE, 0, ctx->stream>>>(dom, s->parents, np, s->rot,
@@ -560,7 +586,7 @@ static int launch_children(gosma_ctx *ctx, const Domain &dom, BnbState *s, int n
     df z2;
     split_double(ctx->zeta * ctx->zeta, z2.h, z2.l);
     kern<<<(int)grid, BLOCK, smem, ctx->stream>>>(ctx->mix, dom, z2, s->parents, np, s->rot, s->kids, s->kid_ub,
-                                                   s->kid_rot, (int *)(s->kid_rot + 1));
+                                                   s->kid_rot, (int *)(s->kid_rot + 1), (int)(group / sizeof(float)));
     ++ctx->launches;
     e = cudaGetLastError();
     return e == cudaSuccess ? GOSMA_OK : cuda_fail(ctx, e, "launch(children)");
@@ -568,7 +594,8 @@ static int launch_children(gosma_ctx *ctx, const Domain &dom, BnbState *s, int n
 
 static int launch_children_any(gosma_ctx *ctx, const Domain &dom, BnbState *s, int np) {
     switch (bounds_block_size(ctx->n1, ctx->n2)) {
-    case 32: return launch_children<32>(ctx, dom, s, np);
+    case 32:  // mixtures of at most 16 model rows: two cubes to a warp
+        return ctx->n1 <= 16 ? launch_children<32, 2>(ctx, dom, s, np) : launch_children<32>(ctx, dom, s, np);
     case 64: return launch_children<64>(ctx, dom, s, np);
     case 128: return launch_children<128>(ctx, dom, s, np);
     case 256: return launch_children<256>(ctx, dom, s, np);

@@ -48,15 +48,23 @@ __host__ __device__ inline double psi_r_level(int lr) {
     return p < M_PI ? p : M_PI;
 }
 
-__host__ __device__ inline void decode(const Node &n, const Domain &d, CubeGeom &g) {
-    double rh = ldexp(M_PI, -(int)n.lr);
-    g.rhw = rh;
+// A node's cell as FP64 geometry: the rotation cube (centre, half-width) and
+// the translation cuboid (centre, half-widths), each from its own level.
+__host__ __device__ inline void decode_rotation(const Node &n, double r0[3], double &rhw) {
+    const double rh = ldexp(M_PI, -(int)n.lr);
+    rhw = rh;
+    for (int k = 0; k < 3; ++k) r0[k] = -M_PI + (2.0 * n.r[k] + 1.0) * rh;
+}
+__host__ __device__ inline void decode_translation(const Node &n, const Domain &d, double t0[3], double thw[3]) {
     for (int k = 0; k < 3; ++k) {
-        g.r0[k] = -M_PI + (2.0 * n.r[k] + 1.0) * rh;
-        double th = ldexp(d.t_hi[k] - d.t_lo[k], -(int)n.lt - 1);
-        g.thw[k] = th;
-        g.t0[k] = d.t_lo[k] + (2.0 * n.t[k] + 1.0) * th;
+        const double th = ldexp(d.t_hi[k] - d.t_lo[k], -(int)n.lt - 1);
+        thw[k] = th;
+        t0[k] = d.t_lo[k] + (2.0 * n.t[k] + 1.0) * th;
     }
+}
+__host__ __device__ inline void decode(const Node &n, const Domain &d, CubeGeom &g) {
+    decode_rotation(n, g.r0, g.rhw);
+    decode_translation(n, d, g.t0, g.thw);
 }
 
 // The split rule's comparison psi_r(lr) >= psit, taken in FP32: psit is a
@@ -101,16 +109,17 @@ __host__ __device__ inline Node child_of(const Node &p, int k, bool rot) {
 // multiples of 8, so that a tile holds whole families of eight siblings), by
 // a block of PREP_TILE threads.  An FP64 instruction costs the FP64 unit a
 // whole warp's time however few of its lanes are active, so the pre-pass's
-// FP64 bulk is shared between siblings and packed into the block's first
+// FP64 work is shared between siblings and packed into the block's first
 // threads:
 //   * Rodrigues' formula and the rotation-cube terms run once per family for
 //     a translation split (the children keep their parent's rotation cube)
 //     and once per child for a rotation split;
+//   * the cuboid's split into double-floats runs once per family for a
+//     rotation split and once per child for a translation split;
 //   * the rotation uncertainty angle runs once per family (siblings share a
-//     level);
-//   * every child splits its own cuboid.
-// The shared parts are computed for the family's first child and copied to
-// its siblings: every record equals cube_prepare's for that child.
+//     level).
+// A part shared by a family is computed for its first child and copied to
+// the siblings: every record equals cube_prepare's for that child.
 // fam(w, parent, domain, point) gives child w's parent node, its problem's
 // translation domain and whether the point-dependent terms are wanted; nrec
 // is the record count of prep (the point-dependent records follow it).
@@ -118,68 +127,88 @@ constexpr int PREP_TILE = 256;
 
 template <class Family>
 __device__ void prep_children_tile(int base, int n, CubePrep *__restrict__ prep, int nrec, const Family &fam) {
-    __shared__ double s_geo[PREP_TILE][4];  // r0, rotation half-width of each child
-    __shared__ int s_job[PREP_TILE];        // children that need Rodrigues' formula, packed
-    __shared__ int s_wsum[PREP_TILE / 32 + 1];
+    __shared__ Node s_child[PREP_TILE];
+    __shared__ Domain s_dom[PREP_TILE / 8];
+    __shared__ int s_job[2][PREP_TILE];  // children that run the rotation / translation part, packed
+    __shared__ int s_wsum[2][PREP_TILE / 32 + 1];
     __shared__ unsigned char s_pt[PREP_TILE];
     const int t = threadIdx.x, w = base + t, lane = t & 31, warp = t >> 5;
     const bool valid = w < n;
     bool rot = false, point = false;
-    CubeGeom g;
     if (valid) {
         Node p;
         Domain d;
         fam(w, p, d, point);
         rot = split_rotation(p);
-        decode(child_of(p, w & 7, rot), d, g);
-        for (int k = 0; k < 3; ++k) s_geo[t][k] = g.r0[k];
-        s_geo[t][3] = g.rhw;
+        s_child[t] = child_of(p, w & 7, rot);
+        if ((w & 7) == 0) s_dom[t >> 3] = d;
         s_pt[t] = point ? 1 : 0;
     }
-    const bool need = valid && (rot || (w & 7) == 0);
-    const unsigned bal = __ballot_sync(0xffffffffu, need);
-    if (lane == 0) s_wsum[warp] = __popc(bal);
+    const bool first = (w & 7) == 0;
+    const unsigned bal[2] = {__ballot_sync(0xffffffffu, valid && (rot || first)),
+                             __ballot_sync(0xffffffffu, valid && (!rot || first))};
+    if (lane == 0) {
+        s_wsum[0][warp] = __popc(bal[0]);
+        s_wsum[1][warp] = __popc(bal[1]);
+    }
     __syncthreads();
-    if (t == 0) {
+    if (t < 2) {
         int sum = 0;
         for (int k = 0; k < PREP_TILE / 32; ++k) {
-            const int x = s_wsum[k];
-            s_wsum[k] = sum;
+            const int x = s_wsum[t][k];
+            s_wsum[t][k] = sum;
             sum += x;
         }
-        s_wsum[PREP_TILE / 32] = sum;
+        s_wsum[t][PREP_TILE / 32] = sum;
     }
     __syncthreads();
-    if (need) s_job[s_wsum[warp] + __popc(bal & ((1u << lane) - 1u))] = t;
+    for (int a = 0; a < 2; ++a)
+        if ((bal[a] >> lane) & 1u) s_job[a][s_wsum[a][warp] + __popc(bal[a] & ((1u << lane) - 1u))] = t;
     __syncthreads();
-    if (t < PREP_TILE / 8 && base + 8 * t < n) cube_prepare_psi_r(s_geo[8 * t][3], prep[base + 8 * t]);
-    if (t < s_wsum[PREP_TILE / 32]) {
-        const int j = s_job[t];
-        cube_prepare_rotation(s_geo[j], s_geo[j][3], prep[base + j],
-                              s_pt[j] ? prep_point(prep, nrec, base + j) : nullptr);
+    if (t < PREP_TILE / 8 && base + 8 * t < n) {
+        double r0[3], rhw;
+        decode_rotation(s_child[8 * t], r0, rhw);
+        cube_prepare_psi_r(rhw, prep[base + 8 * t]);
     }
-    __syncthreads();  // the shared parts above are visible to the block
-    if (!valid) return;
+    if (t < s_wsum[0][PREP_TILE / 32]) {
+        const int j = s_job[0][t];
+        double r0[3], rhw;
+        decode_rotation(s_child[j], r0, rhw);
+        cube_prepare_rotation(r0, rhw, prep[base + j], s_pt[j] ? prep_point(prep, nrec, base + j) : nullptr);
+    }
+    if (t < s_wsum[1][PREP_TILE / 32]) {
+        const int j = s_job[1][t];
+        double t0[3], thw[3];
+        decode_translation(s_child[j], s_dom[j >> 3], t0, thw);
+        cube_prepare_translation(t0, thw, prep[base + j]);
+    }
+    __syncthreads();  // the parts above are visible to the block
+    if (!valid || first) return;
     CubePrep &o = prep[w];
-    if (w & 7) {
-        const CubePrep &f = prep[w & ~7];
-        o.Cr = f.Cr;
-        o.Sr = f.Sr;
-        o.psi_r = f.psi_r;
-        if (!rot) {
-            for (int k = 0; k < 9; ++k) {
-                o.Rh[k] = f.Rh[k];
-                o.Rl[k] = f.Rl[k];
-            }
-            o.infeasible = f.infeasible;
-            if (point) {
-                const CubePrepPoint &fp = *prep_point(prep, nrec, w & ~7);
-                CubePrepPoint &op = *prep_point(prep, nrec, w);
-                for (int k = 0; k < PREP_POINT_WORDS; ++k) op.pj[k] = fp.pj[k];
-            }
+    const CubePrep &f = prep[w & ~7];
+    o.Cr = f.Cr;
+    o.Sr = f.Sr;
+    o.psi_r = f.psi_r;
+    if (rot) {
+        for (int k = 0; k < 3; ++k) {
+            o.th[k] = f.th[k];
+            o.tl[k] = f.tl[k];
+            o.wh[k] = f.wh[k];
+            o.wl[k] = f.wl[k];
+        }
+        o.pad[0] = o.pad[1] = 0.f;
+    } else {
+        for (int k = 0; k < 9; ++k) {
+            o.Rh[k] = f.Rh[k];
+            o.Rl[k] = f.Rl[k];
+        }
+        o.infeasible = f.infeasible;
+        if (point) {
+            const CubePrepPoint &fp = *prep_point(prep, nrec, w & ~7);
+            CubePrepPoint &op = *prep_point(prep, nrec, w);
+            for (int k = 0; k < PREP_POINT_WORDS; ++k) op.pj[k] = fp.pj[k];
         }
     }
-    cube_prepare_translation(g.t0, g.thw, o);
 }
 
 }  // namespace gosma

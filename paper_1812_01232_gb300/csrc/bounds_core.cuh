@@ -366,8 +366,9 @@ __device__ __forceinline__ float2 ex2_2a(float2 x) { return make_float2(ex2a(x.x
 //   (minimiser -k2 cos B, clamped), from below; g(K)/K <= min(1/K, 2).
 // Forms chosen for the packed instructions, exact rewritings: 1 - s^2 is
 // taken as -(s^2 - 1) (rounding to nearest is symmetric), -k2 cos B as
-// -(k2 cos B), and 12u |DL| as -12u DL (DL <= 0: a product of non-negative
-// factors and -log2 e).
+// -(k2 cos B), and the exponent's relative slack as one fused
+// DL (1 - 16u) + slack (DL <= 0: a product of non-negative factors and
+// -log2 e; 1 - 16u is a float, and one rounding replaces two).
 __device__ __forceinline__ void cross_pair2(const RowCross2 &R, float4 P0, float4 P1, float4 P2, float4 P3,
                                             float2 &pl, float2 &pc) {
     const float U = GOSMA_U;
@@ -415,7 +416,7 @@ __device__ __forceinline__ void cross_pair2(const RowCross2 &R, float4 P0, float
     const float2 r = rcp2a(mul2(den, Kc));
     const float2 DL = mul2(mul2(mul2(nak4, mul2(slo, slo)), mul2(Kc, r)), bc2(GOSMA_LOG2E));
     const float2 w = min2(mul2(den, r), 2.f);
-    const float2 arg = fma2(bc2(-16.f * U), DL, add2(DL, bc2(GOSMA_CROSS_SLACK)));
+    const float2 arg = fma2(DL, bc2(1.f - 16.f * U), bc2(GOSMA_CROSS_SLACK));
     pl = fma2(ex2_2a(arg), mul2(w, Q), pl);
 }
 
@@ -450,7 +451,8 @@ struct RowSelf2 {
 //   small K, g rounded with <= 64u error otherwise.
 // Besides the rewritings of cross_pair2, -sin((psi_i+psi_m)/2) / 2 is formed as
 // 0 - hS (exact; hS >= 0, a sum of products of non-negative half-angle
-// sines and cosines).
+// sines and cosines), and the exponent's slack as DL (1 + 12u) - slack in
+// one fused operation (DL <= 0).
 __device__ __forceinline__ void self_pair2(const RowSelf2 &R, float4 P0, float4 P1, float4 P2, float4 P3, float4 P4,
                                            float4 P5, float2 Um, float2 &pl, float2 &pc) {
     const float U = GOSMA_U;
@@ -506,7 +508,7 @@ __device__ __forceinline__ void self_pair2(const RowSelf2 &R, float4 P0, float4 
     float2 w = mul2(den, r);
     if (Kmax.x < 9.f) w.x = Kmax.x < 0.25f ? fmaxf(2.f - 2.f * Kmax.x, 0.f) : gZ(Kmax.x) * w.x * (1.f - 64.f * U);
     if (Kmax.y < 9.f) w.y = Kmax.y < 0.25f ? fmaxf(2.f - 2.f * Kmax.y, 0.f) : gZ(Kmax.y) * w.y * (1.f - 64.f * U);
-    const float2 arg = sub2(DL, fma2(bc2(-12.f * U), DL, bc2(GOSMA_TERM_SLACK)));
+    const float2 arg = fma2(DL, bc2(1.f + 12.f * U), bc2(-GOSMA_TERM_SLACK));
     pl = fma2(ex2_2a(arg), mul2(w, Am), pl);
 }
 
@@ -517,53 +519,85 @@ __device__ __forceinline__ float half_kcothk(float k) {
     return 0.5f * k * (1.f + e) * rcpa(1.f - e);
 }
 
-// A group of GT threads (whole warps) of a BLOCK-thread block works on one
-// cube; the block holds BLOCK / GT groups.  gsync is the group's barrier:
-// the block barrier when one group is the block, else named barrier
-// 1 + gid for the group's GT threads.
+// A group of GT threads (half a warp, or whole warps) of a BLOCK-thread
+// block works on one cube; the block holds BLOCK / GT groups.  gsync is the
+// group's barrier: the block barrier when one group is the block, a warp
+// barrier over the group's lanes for a half-warp group, else named barrier
+// 1 + gid for the group's GT threads.  Half-warp groups serve the smallest
+// mixtures (at most 16 model rows), two cubes to a warp.
+template <int GT>
+__device__ __forceinline__ unsigned group_lanes() {
+    if constexpr (GT >= 32) {
+        return 0xffffffffu;
+    } else {
+        return ((1u << GT) - 1u) << ((threadIdx.x & 31) & ~(unsigned)(GT - 1));
+    }
+}
+
 template <int BLOCK, int GT>
 __device__ __forceinline__ void gsync(int gid) {
-    static_assert(GT % 32 == 0 && BLOCK % GT == 0 && BLOCK / GT <= 15, "groups of whole warps");
+    static_assert((GT == 16 || GT % 32 == 0) && BLOCK % GT == 0 && BLOCK / GT <= 15, "groups of half or whole warps");
     if constexpr (GT == BLOCK) {
         __syncthreads();
+    } else if constexpr (GT < 32) {
+        __syncwarp(group_lanes<GT>());
     } else {
         asm volatile("bar.sync %0, %1;" ::"r"(gid + 1), "n"(GT) : "memory");
     }
 }
 
-// Warp + group reduction of four double-floats, scattered: on return, lane
-// 8k of the group's first warp (gtid == 8k, k = 0..3) holds the group's
+// Lanes of the group that hold the four sums after group_reduce_df: sum k
+// in gtid k * sum_lane_stride<GT>().
+template <int GT>
+__host__ __device__ constexpr int sum_lane_stride() {
+    return GT >= 32 ? 8 : GT / 4;
+}
+
+// Warp + group reduction of four double-floats, scattered: on return, the
+// group's thread gtid = k sum_lane_stride (k = 0..3; lanes 0, 8, 16, 24 of
+// its first warp, or 0, 4, 8, 12 of a half-warp group) holds the group's
 // total of v[k].  Within a warp the first two levels halve the sums between
 // the lanes (after xor 16, lanes 0-15 carry sums 0 and 1 and lanes 16-31
 // sums 2 and 3; after xor 8, lanes 8k .. 8k + 7 carry sum k), and the last
 // three reduce within eight lanes: 7 double-float additions per lane instead
-// of 20 for four full reductions, and no barrier for a one-warp group.
+// of 20 for four full reductions, and no barrier for a one-warp group.  A
+// half-warp group does the same within its 16 lanes (xor 8, 4, then 2, 1).
 template <int BLOCK, int GT>
 __device__ inline df group_reduce_df(const df v[4], CubeShared &cs, int gid, int gtid) {
-    const int lane = gtid & 31, warp = gtid >> 5;
-    const bool h16 = lane & 16, h8 = lane & 8;
-    auto xshfl = [](df x, int o) {
-        return df{__shfl_xor_sync(0xffffffffu, x.h, o), __shfl_xor_sync(0xffffffffu, x.l, o)};
+    const unsigned mask = group_lanes<GT>();
+    auto xshfl = [mask](df x, int o) {
+        return df{__shfl_xor_sync(mask, x.h, o), __shfl_xor_sync(mask, x.l, o)};
     };
-    const df g0 = df_add(h16 ? v[2] : v[0], xshfl(h16 ? v[0] : v[2], 16));
-    const df g1 = df_add(h16 ? v[3] : v[1], xshfl(h16 ? v[1] : v[3], 16));
-    df b = df_add(h8 ? g1 : g0, xshfl(h8 ? g0 : g1, 8));
+    if constexpr (GT == 16) {
+        const bool h8 = gtid & 8, h4 = gtid & 4;
+        const df g0 = df_add(h8 ? v[2] : v[0], xshfl(h8 ? v[0] : v[2], 8));
+        const df g1 = df_add(h8 ? v[3] : v[1], xshfl(h8 ? v[1] : v[3], 8));
+        df b = df_add(h4 ? g1 : g0, xshfl(h4 ? g0 : g1, 4));
+        b = df_add(b, xshfl(b, 2));
+        return df_add(b, xshfl(b, 1));
+    } else {
+        const int lane = gtid & 31, warp = gtid >> 5;
+        const bool h16 = lane & 16, h8 = lane & 8;
+        const df g0 = df_add(h16 ? v[2] : v[0], xshfl(h16 ? v[0] : v[2], 16));
+        const df g1 = df_add(h16 ? v[3] : v[1], xshfl(h16 ? v[1] : v[3], 16));
+        df b = df_add(h8 ? g1 : g0, xshfl(h8 ? g0 : g1, 8));
 #pragma unroll
-    for (int o = 4; o > 0; o >>= 1) b = df_add(b, xshfl(b, o));
-    if constexpr (GT > 32) {
-        if ((lane & 7) == 0) {
-            cs.red[2 * (lane >> 3)][warp] = b.h;
-            cs.red[2 * (lane >> 3) + 1][warp] = b.l;
+        for (int o = 4; o > 0; o >>= 1) b = df_add(b, xshfl(b, o));
+        if constexpr (GT > 32) {
+            if ((lane & 7) == 0) {
+                cs.red[2 * (lane >> 3)][warp] = b.h;
+                cs.red[2 * (lane >> 3) + 1][warp] = b.l;
+            }
+            gsync<BLOCK, GT>(gid);
+            if (gtid < 32 && (lane & 7) == 0) {
+                const int k = lane >> 3;
+                df s = {cs.red[2 * k][0], cs.red[2 * k + 1][0]};
+                for (int w = 1; w < GT / 32; ++w) s = df_add(s, {cs.red[2 * k][w], cs.red[2 * k + 1][w]});
+                b = s;
+            }
         }
-        gsync<BLOCK, GT>(gid);
-        if (gtid < 32 && (lane & 7) == 0) {
-            const int k = lane >> 3;
-            df s = {cs.red[2 * k][0], cs.red[2 * k + 1][0]};
-            for (int w = 1; w < GT / 32; ++w) s = df_add(s, {cs.red[2 * k][w], cs.red[2 * k + 1][w]});
-            b = s;
-        }
+        return b;
     }
-    return b;
 }
 
 // Blocks per SM the bound kernels ask the compiler to fit.  32- and 64-thread
@@ -945,12 +979,14 @@ __device__ void cube_bounds(const MixDev &mx, const CubePrep &prep, const CubePr
 
     // ---------------- phase 3: block reduction (double-float)
     const df tot = group_reduce_df<BLOCK, GT>(T, cs, gid, gtid);
-    // Lanes 0, 8, 16, 24 of the group's first warp hold the four sums and
-    // convert them to FP64 together: an FP64 instruction costs the FP64 unit
-    // a whole warp's time however few lanes run it.
+    // The four lanes that hold the sums (lanes 0, 8, 16, 24 of the group's
+    // first warp; 0, 4, 8, 12 of a half-warp group) convert them to FP64
+    // together: an FP64 instruction costs the FP64 unit a whole warp's time
+    // however few lanes run it (and the two groups of a warp share it).
     // (the self sums only when computed: callers that skip them use cached ones)
-    if (tid < 32 && (tid & 7) == 0) {
-        const int k = tid >> 3;
+    constexpr int SL = sum_lane_stride<GT>();
+    if (tid < 4 * SL && tid % SL == 0) {
+        const int k = tid / SL;
         const double d = (need_self || (k & 1)) ? (double)tot.h + (double)tot.l : 0.0;
         if (k == 0)
             out.self_lb = d;
@@ -969,6 +1005,24 @@ __device__ void cube_bounds(const MixDev &mx, const CubePrep &prep, const CubePr
         out.centre_feasible = !cs.centre_infeasible;
     }
     gsync<BLOCK, GT>(gid);
+}
+
+// Theorem 1's bounds of a cube from its FP64 sums: lb = self_lb - 2 cross_ub
+// less 1e-12 (self_lb + 2 cross_ub), the allowance for the double-float
+// partial sums (~2^-44), and ub = self_c - 2 cross_c.  Called by lanes 0
+// and 1 of a group together (first = lane 0): lane 1 forms ub in the same
+// FP64 instructions as lane 0 forms lb (an FP64 instruction costs the FP64
+// unit a whole warp's time however few lanes run it); both lanes return
+// both.  The sums are finite.
+__device__ __forceinline__ void cube_lb_ub(double self_lb, double cross_ub, double self_c, double cross_c, bool first,
+                                           double &lb, double &ub) {
+    const double x = first ? self_lb : self_c, y = first ? cross_ub : cross_c;
+    const double S = x + 2.0 * y;
+    const double v = x - 2.0 * y;
+    const double w = v - (first ? 1e-12 : 0.0) * S;
+    const double o = __shfl_xor_sync(0x3u << ((threadIdx.x & 31) & ~1u), w, 1);
+    lb = first ? w : o;
+    ub = first ? o : w;
 }
 
 // Final per-cube values from the sums (thread 0).

@@ -43,8 +43,8 @@ inline int sma_block_for(int count, int sm_count, bool f64, int n1, int n2) {
 }
 
 // Shape of the batched solver's bound kernel: threads per block and cubes per
-// block (groups of block / cubes threads, whole warps, each bounding its own
-// sub-cube).
+// block (groups of block / cubes threads, each bounding its own sub-cube:
+// whole warps, or half a warp for 32 x 2).
 struct BoundShape {
     int block, cubes;
 };
@@ -52,16 +52,18 @@ struct BoundShape {
 // The shapes the batched solver's autotuner times.  wide: the block size a
 // single problem of the largest mixture would use (32 for tiny mixtures,
 // 512 or 1024 for large ones); group_bytes: the shared memory one group
-// needs.  Shapes whose groups would not fit 200 KB of shared memory per
-// block, or whose groups would be narrower than a warp, are left out.
-inline int bound_shape_candidates(int wide, size_t group_bytes, BoundShape out[12]) {
-    static const BoundShape all[] = {{32, 1},  {64, 1},  {64, 2},  {128, 1}, {128, 2}, {128, 4},
-                                     {256, 1}, {256, 2}, {256, 4}, {512, 1}, {1024, 1}};
+// needs; max_n1: the largest model mixture.  Shapes whose groups would not
+// fit 200 KB of shared memory per block are left out, and so are groups
+// narrower than a warp, except the half-warp groups of 32 x 2 for tiny
+// mixtures of at most 16 model rows.
+inline int bound_shape_candidates(int wide, size_t group_bytes, BoundShape out[12], int max_n1 = 1 << 30) {
+    static const BoundShape all[] = {{32, 1},  {32, 2},  {64, 1},  {64, 2},  {128, 1}, {128, 2},
+                                     {128, 4}, {256, 1}, {256, 2}, {256, 4}, {512, 1}, {1024, 1}};
     int n = 0;
     for (const BoundShape &c : all) {
-        if (c.block == 32 && wide != 32) continue;       // one warp per cube only for tiny mixtures
+        if (c.block == 32 && wide != 32) continue;       // one warp per block only for tiny mixtures
         if (c.block >= 512 && c.block != wide) continue;  // wide blocks only where one problem would use them
-        if (c.block / c.cubes < 32) continue;
+        if (c.block / c.cubes < 32 && !(c.block / c.cubes == 16 && max_n1 <= 16)) continue;
         if (((group_bytes + 15) & ~(size_t)15) * (size_t)c.cubes > (size_t)200 * 1024) continue;
         out[n++] = c;
     }

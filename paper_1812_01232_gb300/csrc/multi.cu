@@ -607,19 +607,19 @@ __global__ void __launch_bounds__(BLOCK, G == 1 ? (BLOCK == 128 ? 7 : bound_min_
             const int w = w0 + r, c = w - off[k];
             cube_bounds<BLOCK, GT>(mx, prep[w], prep_point(prep, N, w), P[k].zeta2, need_self, cs[gid], sm,
                                    sums[gid], gid, gtid, r > 0 && !need_self);
-            if (gtid == 0) {
+            if (gtid < 2) {
                 const CubeSums &su = sums[gid];
+                const double sl = need_self ? su.self_lb : pr.self_lb;
+                const double sc = need_self ? su.self_c : pr.self_c;
+                double lb, ub;
+                cube_lb_ub(sl, su.cross_ub, sc, su.cross_c, gtid == 0, lb, ub);
+                if (gtid == 1) continue;
                 const Node p = pr;
                 Node ch = child_of(p, c & 7, rot);
-                double sl = need_self ? su.self_lb : p.self_lb;
-                double sc = need_self ? su.self_c : p.self_c;
-                double lb, ub;
                 if (!su.feasible) {
                     lb = ub = inf;
-                } else {
-                    double Ssum = sl + 2.0 * su.cross_ub;
-                    lb = sl - 2.0 * su.cross_ub - 1e-12 * Ssum;
-                    ub = su.centre_feasible ? sc - 2.0 * su.cross_c : inf;
+                } else if (!su.centre_feasible) {
+                    ub = inf;
                 }
                 ch.lb = lb;
                 ch.self_lb = sl;
@@ -1188,6 +1188,7 @@ static cudaError_t mp_bound_any(BoundShape shape, gosma_ctx *ctx, cudaStream_t s
     if (shape.block == B && shape.cubes == G)                                                                          \
     return mp_bound_launch<B, G>(ctx, st, P, off, nprob, parents, prep, kids, kid_ub, counter, smem, stride)
     MPB(32, 1);
+    MPB(32, 2);
     MPB(64, 1);
     MPB(64, 2);
     MPB(128, 1);
@@ -1444,8 +1445,8 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
         return fail(ctx, GOSMA_EINVAL, "bnb_solve_batch: 8 * pop * problems must be below 2^31");
     if (cap < 16ULL * o.pop) return fail(ctx, GOSMA_EINVAL, "bnb_solve_batch: queue_capacity below 16 * pop");
     {
-        const BoundShape ok[] = {{32, 1},  {64, 1},  {64, 2},  {128, 1}, {128, 2}, {128, 4},
-                                 {256, 1}, {256, 2}, {256, 4}, {512, 1}, {1024, 1}};
+        const BoundShape ok[] = {{32, 1},  {32, 2},  {64, 1},  {64, 2},  {128, 1}, {128, 2},
+                                 {128, 4}, {256, 1}, {256, 2}, {256, 4}, {512, 1}, {1024, 1}};
         bool valid = o.bound_block == 0 && o.bound_cubes == 0;
         for (const BoundShape &c : ok) valid = valid || (o.bound_block == c.block && o.bound_cubes == c.cubes);
         if (!valid) return fail(ctx, GOSMA_EINVAL, "bnb_solve_batch: unsupported bound_block x bound_cubes");
@@ -1838,7 +1839,7 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
     const bool tune = o.bound_block == 0;
     BoundShape shape = tune ? BoundShape{128, 1} : BoundShape{o.bound_block, o.bound_cubes};
     BoundShape cands[12];
-    const int ncand = bound_shape_candidates(bounds_block_size(max_n1, max_n2), smem, cands);
+    const int ncand = bound_shape_candidates(bounds_block_size(max_n1, max_n2), smem, cands, max_n1);
     int tunings = 0, running_at_tune = nprob, iter = 0, tuned_at = 0;
     cudaEvent_t ta, tb;
     cudaEventCreate(&ta);

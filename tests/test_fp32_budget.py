@@ -257,7 +257,7 @@ def _cross_parts(c, s):
     r = rcpa(den * Kc, s[4])
     DL = nak4 * (slo * slo) * (Kc * r) * L2E
     w = np.minimum(den * r, F(2))
-    e = ex2a(fma(np.full_like(DL, F(-16) * FU), DL, DL + CROSS_SLACK), s[5])
+    e = ex2a(fma(DL, np.full_like(DL, F(1) - F(16) * FU), np.full_like(DL, CROSS_SLACK)), s[5])
     ph = f32(c["phi1"][:, 0])
     Bw = np.where(b < F(9), ph * b * rcpa(gZ(b, s[6]), s[7]) * c1(12), ph * b).astype(np.float32)
     Bw = mul_ru(Bw, np.full_like(Bw, c1(8 + 6)))
@@ -320,7 +320,7 @@ def _self_parts(c, s):
     small = Kmax < F(0.25)
     w = np.where(Kmax < F(9), np.where(small, np.maximum(F(2) - F(2) * Kmax, F(0)), gZ(Kmax, s[5]) * w * c1m(64)), w)
     w = w.astype(np.float32)
-    e = ex2a(DL - fma(np.full_like(DL, F(12) * FU), np.abs(DL), np.full_like(DL, SLACK)), s[6])
+    e = ex2a(fma(DL, np.full_like(DL, F(1) + F(12) * FU), np.full_like(DL, -SLACK)), s[6])
     Awi = mul_rd(F(2) * Ai, np.full_like(Ai, c1m(8 + 3)))
     return e, (w * Am).astype(np.float32), Awi
 

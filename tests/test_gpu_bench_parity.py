@@ -86,3 +86,35 @@ def test_last_children_before_and_between_runs():
     c2, _ = ctx.bnb_last_children()
     assert 0 < len(c2) <= 8 * 64 and len(c2) % 8 == 0
     ctx.close()
+
+
+@pytest.mark.parametrize("seed,steps", [(1000, 4), (1003, 9)])
+def test_small_mixture_step_children_match_the_oracle(oracle_mod, seed, steps):
+    """The same element-by-element comparison for a 10 x 8 tiny problem, whose
+    children kernel runs two sub-cubes per warp (half-warp groups: model rows
+    on 16 lanes, the sums reduced within the half), at the solver's automatic
+    pop (65,536 parents, 524,288 children per step)."""
+    from paper_1812_01232_gb300 import build
+    build.build()
+    from paper_1812_01232_gb300.gosma import Gosma
+    prob = synth.tiny_problem(seed)
+    ctx = Gosma(0)
+    ctx.set_problem(prob)
+    ctx.bnb_start(eps=1e-3, queue_capacity=1 << 24)
+    n1 = ctx.n1
+    prev = ctx.bnb_step(steps)
+    for _ in range(16):  # the first later step with children of both split types
+        r = ctx.bnb_step(1)
+        cubes, got = ctx.bnb_last_children()
+        fresh = (r["self_pairs"] - prev["self_pairs"]) // (n1 * (n1 - 1) // 2)
+        if r["status_name"] != "running" or 0 < fresh < len(cubes):
+            break
+        prev = r
+    ctx.close()
+    assert r["status_name"] == "running" and len(cubes) >= 8 * 512, (r["status_name"], len(cubes))
+    assert 0 < fresh < len(cubes), fresh
+    mix = oracle_mod.Mixtures.from_problem(prob)
+    ref = oracle_mod.bounds(mix, cubes, prob["zeta"])
+    st = compare(got, ref, "tiny step children (seed %d, +%d)" % (seed, steps),
+                 eps_c22=1e-3 * oracle_mod.c22(mix), dstar=r["f"], cubes=cubes, kappa2_max=prob["kappa2"].max())
+    assert st["near_deficit_over_eps_c22"] < CERT_BAR, st

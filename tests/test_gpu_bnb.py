@@ -293,8 +293,9 @@ def test_history_follows_the_run(ctx):
 
 
 def test_batch_bound_shapes_agree(ctx):
-    """The bound kernel's shapes (threads per block x sub-cubes per block):
-    every fixed shape and the autotuned run certify the same optima, the
+    """The bound kernel's shapes (threads per block x sub-cubes per block,
+    32 x 2 in half-warp groups): every fixed shape and the autotuned run
+    certify the same optima, the
     result reports the shape used, the autotuner timed the shapes at least
     once, and an unsupported shape is refused."""
     from paper_1812_01232_gb300.gosma import GosmaError
@@ -302,8 +303,8 @@ def test_batch_bound_shapes_agree(ctx):
     tuned = ctx.bnb_solve_batch(probs, eps=1e-3, max_seconds=120, queue_capacity=1 << 24)
     assert all(r["tunings"] >= 1 for r in tuned)
     assert (tuned[0]["block_size"], tuned[0]["cubes_per_block"]) in [
-        (32, 1), (64, 1), (64, 2), (128, 1), (128, 2), (128, 4), (256, 1), (256, 2), (256, 4)]
-    for shape in ((32, 1), (64, 2), (128, 4), (256, 1)):
+        (32, 1), (32, 2), (64, 1), (64, 2), (128, 1), (128, 2), (128, 4), (256, 1), (256, 2), (256, 4)]
+    for shape in ((32, 1), (32, 2), (64, 2), (128, 4), (256, 1)):
         res = ctx.bnb_solve_batch(probs, eps=1e-3, max_seconds=120, queue_capacity=1 << 24, shape=shape)
         for a, b in zip(res, tuned):
             assert a["block_size"] == shape[0] and a["cubes_per_block"] == shape[1] and a["tunings"] == 0

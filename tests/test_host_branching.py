@@ -181,6 +181,16 @@ def test_split_rule(harness):
     if below > psi3:
         below = np.nextafter(below, np.float32(0))
     assert rule(3, 2, float(below))[0] == 1  # the largest FP32 key at or below psi_r still splits the rotation
+    # at every level the rule agrees with the FP64 comparison at the float
+    # keys nearest psi_r (the kernels take it in FP32)
+    for lr in range(0, 30):
+        psi = min(np.sqrt(3) * np.pi * 2.0 ** -lr, np.pi)
+        at = np.float32(psi)
+        if float(at) > psi:
+            at = np.nextafter(at, np.float32(0))
+        for key in (at, np.nextafter(at, np.float32(np.inf)), np.nextafter(at, np.float32(0)), np.float32(0.0),
+                    np.float32(4.0)):
+            assert rule(lr, 0, float(key))[0] == int(psi >= float(key)), (lr, float(key))
     # level limits: a cell at the deepest level is never split further along that part
     assert rule(30, 5, 0.0)[0] == 0
     assert rule(5, 30, 10.0)[0] == 1

@@ -134,7 +134,8 @@ int main(int argc, char **argv) {
     if (what[0] == 'r') printf("%d\n", gosma::retune_due(atoi(argv[2]), atoi(argv[3]), atoi(argv[4])) ? 1 : 0);
     if (what[0] == 'c') {  // candidates: wide group_bytes -> how many shapes
         gosma::BoundShape c[12];
-        const int n = gosma::bound_shape_candidates(atoi(argv[2]), (size_t)atoll(argv[3]), c);
+        const int n = argc > 4 ? gosma::bound_shape_candidates(atoi(argv[2]), (size_t)atoll(argv[3]), c, atoi(argv[4]))
+                               : gosma::bound_shape_candidates(atoi(argv[2]), (size_t)atoll(argv[3]), c);
         printf("%d\n", n);
     }
     if (what[0] == 'h') {  // hash: k, then values; the first k form one array, the rest another
@@ -274,9 +275,13 @@ def test_autotuner_retunes_when_half_the_problems_finished(rules):
 
 def test_autotuner_candidates(rules):
     """The shapes timed: a one-warp block only for tiny mixtures, wide blocks
-    only where one problem would use them, no group narrower than a warp, and
+    only where one problem would use them, no group narrower than a warp but
+    the half-warp groups of 32x2 for mixtures of at most 16 model rows, and
     nothing whose groups' shared memory exceeds 200 KB per block."""
     assert rules("c", 32, 4096) == 9        # 32x1 64x1 64x2 128x1 128x2 128x4 256x1 256x2 256x4
+    assert rules("c", 32, 4096, 16) == 10   # + 32x2
+    assert rules("c", 32, 4096, 17) == 9
+    assert rules("c", 128, 4096, 10) == 8   # no one-warp block for wider mixtures
     assert rules("c", 128, 4096) == 8       # no 32x1
     assert rules("c", 1024, 4096) == 9      # + 1024x1
     assert rules("c", 128, 60 * 1024) == 6  # 64x1 64x2 128x1 128x2 256x1 256x2: four groups of 60 KB do not fit
