@@ -86,10 +86,10 @@ POP = 8192
 SEED = 2000
 # FP32-pipe lane operations per pair the bound kernel executes, counted from
 # the source of cross_pair2 / self_pair2 (packed FP32x2 instructions count
-# as two): geometry 12, centre term 16, bound term 38 (cross) or 59 (self),
+# as two): geometry 12, centre term 16, bound term 37 (cross) or 58 (self),
 # and 1.5 per pair for the chunked compensated accumulation.
-OPS_CROSS = 68
-OPS_SELF = 89
+OPS_CROSS = 67
+OPS_SELF = 88
 FP32_LANES_PER_SM = 128
 # Algorithmic work per pair bound, counted from the kernel's closed forms of
 # Theorem 1 (the bound) and Lemma 1 (the centre term) without its
