@@ -86,9 +86,10 @@ POP = 8192
 SEED = 2000
 # FP32-pipe lane operations per pair the bound kernel executes, counted from
 # the source of cross_pair2 / self_pair2 (packed FP32x2 instructions count
-# as two): geometry 12, centre term 16, bound term 37 (cross) or 58 (self),
-# and 1.5 per pair for the chunked compensated accumulation.
-OPS_CROSS = 67
+# as two): geometry 12, centre term 15 (cross) or 16 (self), bound term 36
+# (cross) or 58 (self), and 1.5 per pair for the chunked compensated
+# accumulation.
+OPS_CROSS = 65
 OPS_SELF = 88
 FP32_LANES_PER_SM = 128
 # Algorithmic work per pair bound, counted from the kernel's closed forms of

@@ -151,7 +151,7 @@ static int set_mixtures_impl(gosma_ctx *ctx, int nclass, const int *n1c, const i
     const bool classes = CL.classes;
     cudaSetDevice(ctx->device);
     size_t nd = 3 * (size_t)n1 + 2 * n1 + 3 * (size_t)n2 + 2 * n2;
-    size_t nf = 8 * (size_t)n1 + 8 * (size_t)n2;
+    size_t nf = 8 * (size_t)n1 + 10 * (size_t)n2;
     const size_t ni = classes ? 5 * (size_t)n1 + (size_t)n2 : 0;  // class ids and pair ranges
     size_t bytes = nd * sizeof(double) + nf * sizeof(float) + ni * sizeof(int) + 256;
     void *d = nullptr;
@@ -163,7 +163,8 @@ static int set_mixtures_impl(gosma_ctx *ctx, int nclass, const int *n1c, const i
     float *pf = (float *)(dphi2 + n2);
     float *inv_sig2 = pf, *phi1f = pf + n1, *k2f = phi1f + n1, *Q2 = k2f + n2;
     float *mu1h = Q2 + n2, *mu1l = mu1h + 3 * n1, *mu2h = mu1l + 3 * n1, *mu2l = mu2h + 3 * n2;
-    int *pi = (int *)(mu2l + 3 * n2);
+    float *lQ2c = mu2l + 3 * n2, *lQ2b = lQ2c + n2;
+    int *pi = (int *)(lQ2b + n2);
     int *dcls1 = pi, *drj0 = pi + n1, *drj1 = pi + 2 * n1, *drm1 = pi + 3 * n1, *dcls2 = pi + 4 * n1;
     std::vector<float> hk2(n2);
     for (int j = 0; j < n2; ++j) hk2[j] = (float)kappa2[j];
@@ -209,6 +210,8 @@ static int set_mixtures_impl(gosma_ctx *ctx, int nclass, const int *n1c, const i
     mx.mu1l = mu1l;
     mx.mu2h = mu2h;
     mx.mu2l = mu2l;
+    mx.lQ2c = lQ2c;
+    mx.lQ2b = lQ2b;
     mx.zeta = ctx->zeta;
     mx.cls1 = classes ? dcls1 : nullptr;
     mx.cls2 = classes ? dcls2 : nullptr;

@@ -83,16 +83,17 @@ struct CubeShared {
 };
 
 // Directions are formed as double-floats (hi + lo equals the unit vector to
-// ~2^-44) and stored with both parts; the pair loops read the FP32 parts only
-// and carry the low parts' effect as an absolute allowance (GOSMA_HI_ALLOW),
-// the model rows' low parts serve the point-dependent rotation angle, and the
-// image columns' are kept in the layout unread.  The pair loops take partners two at a time into the two lanes
+// ~2^-44); the pair loops read the FP32 parts only and carry the low parts'
+// effect as an absolute allowance (GOSMA_HI_ALLOW), and the model rows' low
+// parts serve the point-dependent rotation angle.  The pair loops take partners two at a time into the two lanes
 // of packed FP32x2 registers, so the records are stored in pairs, lanes
 // interleaved: one 16-byte load gives two aligned lane pairs.  A missing
 // partner of an odd count is a copy of the last one with zero weight.
 //   JP (image columns 2p, 2p+1; lanes a, b), 4 float4 per pair:
-//     (ux_a, ux_b, uy_a, uy_b) (uz_a, uz_b, k2_a, k2_b) (lx_a, lx_b, ly_a, ly_b) (lz_a, lz_b, Q_a, Q_b)
-//     u = R_r0^T mu_2j (hi, then lo), k2 = kappa_2j, Q the column factor
+//     (ux_a, ux_b, uy_a, uy_b) (uz_a, uz_b, k2_a, k2_b) (lqc_a, lqc_b, lqb_a, lqb_b) (lz_a, lz_b, Q_a, Q_b)
+//     u = R_r0^T mu_2j (FP32 part), k2 = kappa_2j, lqc and lqb the column
+//     factor's log2 for the centre term and for the bound (MixDev::lQ2c,
+//     lQ2b); lz, the last low part of u, and Q, the factor itself, unread
 //   MP (model rows 2q, 2q+1), 6 float4 per pair:
 //     (vx_a, vx_b, vy_a, vy_b) (vz_a, vz_b, a_a, a_b) (lx_a, lx_b, ly_a, ly_b) (lz_a, lz_b, b_a, b_b)
 //     (k0_a, k0_b, cp_a, cp_b) (sp_a, sp_b, Aw_a, Aw_b)
@@ -128,12 +129,12 @@ __device__ __forceinline__ float &mp_at(const SmemArrays &sm, int i, int f) {
 __device__ __forceinline__ float &up_at(const SmemArrays &sm, int i) {
     return reinterpret_cast<float *>(sm.UP)[i];
 }
-// Field f (0..7: ux uy uz k2 lx ly lz Q) of image column j.
+// Field f (0..7: ux uy uz k2 lqc lqb lz Q) of image column j.
 __device__ __forceinline__ float &jp_at(const SmemArrays &sm, int j, int f) {
     return reinterpret_cast<float *>(sm.JP)[16 * (j >> 1) + 2 * f + (j & 1)];
 }
 enum { MP_VX = 0, MP_VY, MP_VZ, MP_A, MP_LX, MP_LY, MP_LZ, MP_B, MP_K0, MP_CP, MP_SP, MP_AW };
-enum { JP_UX = 0, JP_UY, JP_UZ, JP_K2, JP_LX, JP_LY, JP_LZ, JP_Q };
+enum { JP_UX = 0, JP_UY, JP_UZ, JP_K2, JP_LQC, JP_LQB, JP_LZ, JP_Q };
 
 __device__ inline int pow2ceil(int x) {
     int p = 1;
@@ -326,10 +327,14 @@ __device__ __forceinline__ float gZ(float x) { return 1.f - ex2a(-2.f * GOSMA_LO
 // (sin(theta/2) cos(s/2) -+ cos(theta/2) sin(s/2)) within 0.87u (cos + sin)
 // <= 1.23u: an absolute allowance of 1.3u on every half-angle sine.
 #define GOSMA_HI_ALLOW (1.3f * GOSMA_U)
-// The cross pair's term slack: GOSMA_TERM_SLACK and the smallest K's
-// rounding without an outward factor (3.5u relative in g(K)/K: 5u in log2
-// units).
-#define GOSMA_CROSS_SLACK (20.f * GOSMA_U)
+// The cross pair's term slack (GOSMA_CROSS_SLACK, 20u): GOSMA_TERM_SLACK and
+// the smallest K's rounding without an outward factor (3.5u relative in
+// g(K)/K: 5u in log2 units).  It rides on the log2 of the image column's
+// factor (MixDev::lQ2b), which enters the exponent instead of multiplying
+// the term: lQ2b = log2 Q_j + 20u + u (|log2 Q_j| + 1), rounded up, so that
+// the exponent's one rounding (0.5u of |DL| + |lQ2b|) stays covered: its
+// |DL| part by the exponent's relative slack, its |lQ2b| part by the last
+// term (and the product by Q, one of the four above, is gone).
 constexpr int CHUNK = 8;
 
 struct RowCross {
@@ -353,10 +358,10 @@ __device__ __forceinline__ float2 rcp2a(float2 x) { return make_float2(rcpa(x.x)
 __device__ __forceinline__ float2 ex2_2a(float2 x) { return make_float2(ex2a(x.x), ex2a(x.y)); }
 
 // Two cross pairs (i, j) and (i, j') at once, lane x for column j and lane y
-// for j' (their JP records P0 .. P3): adds to pl the upper bound of each
+// for j' (their JP records P0 .. P2): adds to pl the upper bound of each
 // pair's term over the cube (Theorem 1, Eq. K1i2j_ub with B of Eq.
 // K1i2j_ub_B) and to pc the term at the centre (Lemma 1), both without the
-// row multipliers.  Every operation is per lane, rounded to nearest as a
+// row multipliers; the column factor enters each exponent as its log2.  Every operation is per lane, rounded to nearest as a
 // scalar FP32 operation would be (the error budget above holds per lane).
 //   |v -+ u|^2 from the directions' FP32 parts, the centre term in the linear
 //   form above, then the bound: B = max(0, theta - s), s = psi_t,i + psi_r
@@ -369,10 +374,10 @@ __device__ __forceinline__ float2 ex2_2a(float2 x) { return make_float2(ex2a(x.x
 // -(k2 cos B), and the exponent's relative slack as one fused
 // DL (1 - 16u) + slack (DL <= 0: a product of non-negative factors and
 // -log2 e; 1 - 16u is a float, and one rounding replaces two).
-__device__ __forceinline__ void cross_pair2(const RowCross2 &R, float4 P0, float4 P1, float4 P2, float4 P3,
-                                            float2 &pl, float2 &pc) {
+__device__ __forceinline__ void cross_pair2(const RowCross2 &R, float4 P0, float4 P1, float4 P2, float2 &pl,
+                                            float2 &pc) {
     const float U = GOSMA_U;
-    const float2 k2 = make_float2(P1.z, P1.w), Q = make_float2(P3.z, P3.w);
+    const float2 k2 = make_float2(P1.z, P1.w), lqc = make_float2(P2.x, P2.y), lqb = make_float2(P2.z, P2.w);
     const float2 ux = make_float2(P0.x, P0.y), uy = make_float2(P0.z, P0.w), uz = make_float2(P1.x, P1.y);
     // the directions' FP32 parts only (their low parts move sin and cos of
     // theta/2 by at most 0.87u, which the row's allowance esS carries)
@@ -390,7 +395,7 @@ __device__ __forceinline__ void cross_pair2(const RowCross2 &R, float4 P0, float
     float2 w0 = mul2(den0, r0);
     if (K0.x < 9.f) w0.x = K0.x < 1e-3f ? 2.f - 2.f * K0.x : gZ(K0.x) * w0.x;
     if (K0.y < 9.f) w0.y = K0.y < 1e-3f ? 2.f - 2.f * K0.y : gZ(K0.y) * w0.y;
-    pc = fma2(ex2_2a(mul2(mul2(mul2(kk, x2), mul2(K0c, r0)), bc2(-GOSMA_LOG2E))), mul2(w0, Q), pc);
+    pc = fma2(ex2_2a(fma2(mul2(mul2(kk, x2), mul2(K0c, r0)), bc2(-GOSMA_LOG2E), lqc)), w0, pc);
     // bound: B = max(0, theta - s)
     // sx, sy = 2 sin, 2 cos of theta/2; the halves sit in the row constants,
     // so sB and es round exactly as from sin(theta/2) and cos(theta/2)
@@ -416,8 +421,8 @@ __device__ __forceinline__ void cross_pair2(const RowCross2 &R, float4 P0, float
     const float2 r = rcp2a(mul2(den, Kc));
     const float2 DL = mul2(mul2(mul2(nak4, mul2(slo, slo)), mul2(Kc, r)), bc2(GOSMA_LOG2E));
     const float2 w = min2(mul2(den, r), 2.f);
-    const float2 arg = fma2(DL, bc2(1.f - 16.f * U), bc2(GOSMA_CROSS_SLACK));
-    pl = fma2(ex2_2a(arg), mul2(w, Q), pl);
+    const float2 arg = fma2(DL, bc2(1.f - 16.f * U), lqb);
+    pl = fma2(ex2_2a(arg), w, pl);
 }
 
 struct RowSelf {
@@ -682,8 +687,8 @@ __device__ void cube_bounds(const MixDev &mx, const CubePrep &prep, const CubePr
         jp_at(sm, j, JP_UY) = u[1].h;
         jp_at(sm, j, JP_UZ) = u[2].h;
         jp_at(sm, j, JP_K2) = mx.kappa2[jj];
-        jp_at(sm, j, JP_LX) = u[0].l;
-        jp_at(sm, j, JP_LY) = u[1].l;
+        jp_at(sm, j, JP_LQC) = j < n2 ? mx.lQ2c[jj] : __int_as_float(0xff800000);  // -inf: no term
+        jp_at(sm, j, JP_LQB) = j < n2 ? mx.lQ2b[jj] : __int_as_float(0xff800000);
         jp_at(sm, j, JP_LZ) = u[2].l;
         jp_at(sm, j, JP_Q) = j < n2 ? mx.Q2[jj] : 0.f;
     }
@@ -856,7 +861,7 @@ __device__ void cube_bounds(const MixDev &mx, const CubePrep &prep, const CubePr
             // the row's columns [j0, j1) in stored pairs p0 .. p1 - 1, pair p to thread
             // p mod Tj; each lane keeps its own FP32 chunk sum of at most CHUNK terms.
             // A pair with a column outside the range (before j0 when j0 is odd, at j1
-            // when j1 is odd) runs with that column's weight Q set to zero.
+            // when j1 is odd) runs with that column's weight set to zero (its log2 to -inf).
             const RowCross2 R2(R);
             float2 pl = make_float2(0.f, 0.f), pc = make_float2(0.f, 0.f);
             int cnt = 0;
@@ -864,11 +869,11 @@ __device__ void cube_bounds(const MixDev &mx, const CubePrep &prep, const CubePr
             const int p0 = j0 >> 1, p1 = (j1 + 1) >> 1;
             const int pa = (j0 & 1) ? p0 : -1, pb = (j1 & 1) ? p1 - 1 : -1;
             auto step = [&](int q, bool ma, bool mb) {
-                const float4 A = sm.JP[4 * q], B = sm.JP[4 * q + 1], C = sm.JP[4 * q + 2];
-                float4 D = sm.JP[4 * q + 3];
-                if (ma) D.z = 0.f;
-                if (mb) D.w = 0.f;
-                cross_pair2(R2, A, B, C, D, pl, pc);
+                const float4 A = sm.JP[4 * q], B = sm.JP[4 * q + 1];
+                float4 C = sm.JP[4 * q + 2];
+                if (ma) C.x = C.z = __int_as_float(0xff800000);  // log2 of a zero weight
+                if (mb) C.y = C.w = __int_as_float(0xff800000);
+                cross_pair2(R2, A, B, C, pl, pc);
                 if (++cnt == CHUNK) {
                     cl.add(pl.x);
                     cl.add(pl.y);

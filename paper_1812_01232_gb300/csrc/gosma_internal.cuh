@@ -31,6 +31,11 @@ struct MixDev {
     const double *phi2d;   // n2
     const float *mu1h, *mu1l;  // n1 x 3: mu1 as double-floats (hi, lo)
     const float *mu2h, *mu2l;  // n2 x 3: unit mu2 as double-floats
+    // n2: log2 Q2 from FP64: lQ2c rounded to nearest (the centre terms);
+    // lQ2b raised by GOSMA_CROSS_SLACK and by u (|log2 Q2| + 1) (the final
+    // rounding of a cross bound's exponent, which adds it) and rounded up;
+    // -inf for a zero weight
+    const float *lQ2c, *lQ2b;
     double zeta;           // point-to-camera limit (Sec. 4.1)
     // Semantic classes (Sec. 4.2); all null for one class.  Pairs interact
     // only within a class: model row i pairs with image columns
@@ -66,6 +71,9 @@ struct CubeSums {
 // knows exactly what is computed.  Their accuracy is measured against FP64
 // by gosma_selftest_approx; the kernel's slack assumes the bounds below.
 #define GOSMA_U 5.9604644775390625e-8f   // 2^-24, unit roundoff of FP32
+// The cross pair's term slack in log2 units (the error budget in
+// bounds_core.cuh): it rides on the log2 of each image column's factor.
+#define GOSMA_CROSS_SLACK (20.f * GOSMA_U)
 #define GOSMA_LOG2E 1.4426950408889634f
 
 // Relative error assumed for ex2/rcp/rsqrt/sqrt (2^-22) and the absolute +

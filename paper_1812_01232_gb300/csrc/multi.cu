@@ -1482,7 +1482,7 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
     for (int k = 0; k < nprob; ++k) {
         const int n1 = probs[k].n1, n2 = probs[k].n2;
         d_off[k + 1] = d_off[k] + 5 * (size_t)n1 + 5 * (size_t)n2;
-        f_off[k + 1] = f_off[k] + 8 * (size_t)n1 + 8 * (size_t)n2;
+        f_off[k + 1] = f_off[k] + 8 * (size_t)n1 + 10 * (size_t)n2;
         max_n1 = std::max(max_n1, n1);
         max_n2 = std::max(max_n2, n2);
         sum_n1 += n1;
@@ -1560,6 +1560,8 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
         mx.mu1l = mx.mu1h + 3 * n1;
         mx.mu2h = mx.mu1l + 3 * n1;
         mx.mu2l = mx.mu2h + 3 * n2;
+        mx.lQ2c = mx.mu2l + 3 * n2;
+        mx.lQ2b = mx.lQ2c + n2;
         mx.zeta = p.zeta;
         mx.psi_point = ctx->psi_r_mode;
         if (layouts[k].classes) {

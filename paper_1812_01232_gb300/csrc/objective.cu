@@ -87,9 +87,18 @@ __global__ void setup_image(MixDev mx, double *c22part) {
         double K = sqrt(w0 * w0 + w1 * w1 + w2 * w2);
         acc += mx.phi2d[a] * mx.phi2d[b] * exp(logZ_d(K) - logZ_d(ka) - logZ_d(kb));
     }
+    float *lQc = const_cast<float *>(mx.lQ2c), *lQb = const_cast<float *>(mx.lQ2b);
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n2; j += gridDim.x * blockDim.x) {
         double k = mx.kappa2d[j];
-        Q2[j] = (float)(mx.phi2d[j] * k / -expm1(-2.0 * k));
+        const double q = mx.phi2d[j] * k / -expm1(-2.0 * k);
+        Q2[j] = (float)q;
+        // log2 Q for the pair terms' exponents; the bound's copy carries the
+        // cross pair's slack (20 u) and the rounding of its own size in the
+        // exponent's final rounding (u (|log2 Q| + 1)), rounded up
+        const float ninf = __int_as_float(0xff800000);
+        const double lq = log2(q);
+        lQc[j] = q > 0.0 ? (float)lq : ninf;
+        lQb[j] = q > 0.0 ? __double2float_ru(lq + (double)GOSMA_CROSS_SLACK + 0x1p-24 * (fabs(lq) + 1.0)) : ninf;
         for (int c = 0; c < 3; ++c) {
             double m = mx.mu2[3 * j + c];
             float h = (float)m;

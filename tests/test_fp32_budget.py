@@ -16,7 +16,7 @@ ends at a(1 - u) and b(1 + u), half-angle sines rounded up and cosines down,
 kappa_2 and the column factor rounded to nearest.  The geometry (kappa
 intervals, psi_t, psi_r, directions) comes from the FP64 oracle, and the
 replayed bound must never cross the oracle's pair bound for the same cube.
-On these 3,000 cubes the smallest margins are 22.5u (cross) and 36u (self):
+On these 3,000 cubes the smallest margins are 25.4u (cross) and 39.9u (self):
 a dropped angle allowance, the wrong end of a sine interval or clamp, or a
 slack of the wrong sign crosses the oracle, while each few-u rounding
 direction on its own stays inside the margin.
@@ -214,14 +214,17 @@ def _cross(c, s):
 
 
 def _cross_parts(c, s):
-    """The exponential, the factor it multiplies and the row factor of the
-    cross pair's upper bound."""
+    """The exponential (the column factor inside, as its log2), the factor
+    it multiplies and the row factor of the cross pair's upper bound."""
     a, b, sp, cp = _rows(c)
     a, b, sp, cp = a[:, 0], b[:, 0], sp[:, 0], cp[:, 0]
     vh, vl = split(c["v"][:, 0])
     uh, ul = split(c["u"])
     k2 = f32(c["k2"])
-    Q = f32(c["phi2"] * c["k2"] / -np.expm1(-2 * c["k2"]))
+    # the column factor enters the exponent as its log2, from FP64, raised by
+    # the cross slack and by the exponent's rounding of its own size, rounded up
+    lq = np.log2(c["phi2"] * c["k2"] / -np.expm1(-2 * c["k2"]))
+    lqb = toward(lq + np.float64(CROSS_SLACK) + U * (np.abs(lq) + 1.0), np.ones_like(lq))
     Sr = toward(np.sin(0.5 * c["psir"]), np.ones_like(c["psir"]))
     Cr = toward(np.cos(0.5 * c["psir"]), -np.ones_like(c["psir"]))
     Cs = f32(cp.astype(np.float64) * Cr - sp.astype(np.float64) * Sr)
@@ -257,11 +260,11 @@ def _cross_parts(c, s):
     r = rcpa(den * Kc, s[4])
     DL = nak4 * (slo * slo) * (Kc * r) * L2E
     w = np.minimum(den * r, F(2))
-    e = ex2a(fma(DL, np.full_like(DL, F(1) - F(16) * FU), np.full_like(DL, CROSS_SLACK)), s[5])
+    e = ex2a(fma(DL, np.full_like(DL, F(1) - F(16) * FU), lqb), s[5])
     ph = f32(c["phi1"][:, 0])
     Bw = np.where(b < F(9), ph * b * rcpa(gZ(b, s[6]), s[7]) * c1(12), ph * b).astype(np.float32)
     Bw = mul_ru(Bw, np.full_like(Bw, c1(8 + 6)))
-    return e, (w * Q).astype(np.float32), Bw
+    return e, w.astype(np.float32), Bw
 
 
 # ---------------------------------------------------------------- self pair
