@@ -538,6 +538,14 @@ int gosma_selftest_approx(gosma_ctx *ctx, double measured[5], double assumed[5])
  * of three launches after a warm-up).  A few milliseconds of device time. */
 int gosma_selftest_pipe_rates(gosma_ctx *ctx, double rates[7], double *clock_mhz);
 
+/* Diagnostics: the rotation matrices R_r of Rodrigues' formula (Sec. 4.1)
+ * as the bound kernels' pre-pass forms them (double-float arithmetic, each
+ * entry an unevaluated sum of two floats, returned as their FP64 sum), for
+ * n >= 0 rotation vectors r (host, n x 3); R (host, n x 9, row-major per
+ * vector) receives them.  For checking their accuracy against an FP64
+ * rotation; n = 0 is a no-op. */
+int gosma_selftest_rodrigues(gosma_ctx *ctx, int n, const double *r, double *R);
+
 #ifdef __cplusplus
 }
 #endif

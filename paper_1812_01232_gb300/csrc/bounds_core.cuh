@@ -149,7 +149,58 @@ __device__ inline int pow2ceil(int x) {
 // rotation-cube terms, Lemma 2 read as angle(R_r p, R_r0 p) <= |r - r0| <=
 // sqrt(3) r_hw capped at pi, and the translation cuboid split into
 // double-floats.
+// Rodrigues' formula R = I + A [r]x + B [r]x^2 (A = sin|r| / |r|, B = (1 -
+// cos|r|) / |r|^2) in double-float arithmetic, R to ~2^-44 absolute: the
+// FP64 form's sincos and divisions cost the FP64 unit (about 1/64 of the
+// FP32 rate here) more than all the rest of the pre-pass.  Below |r| = 1e-3
+// A and B come from their series (the next terms are below 2^-60).
+__device__ inline void rodrigues_df(const double r0[3], float Rh[9], float Rl[9]) {
+    df x, y, z;
+    split_double(r0[0], x.h, x.l);
+    split_double(r0[1], y.h, y.l);
+    split_double(r0[2], z.h, z.l);
+    const df xx = df_mul(x, x), yy = df_mul(y, y), zz = df_mul(z, z);
+    const df th2 = df_add(df_add(xx, yy), zz);
+    const df one = {1.f, 0.f};
+    df A, B;
+    if (th2.h < 1e-6f) {
+        A = df_add(one, df_mul(th2, df{fmaf(th2.h, 1.f / 120.f, -1.f / 6.f), 0.f}));
+        B = df_add(df{0.5f, 0.f}, df_mul(th2, df{fmaf(th2.h, 1.f / 720.f, -1.f / 24.f), 0.f}));
+    } else {
+        const df th = df_mul(th2, df_rsqrt(th2, rsqrta(th2.h)));
+        df sn, cs;
+        df_sincos(th, sn, cs);
+        A = df_div(sn, th);
+        B = df_div(df_sub(one, cs), th2);
+    }
+    const df xy = df_mul(x, y), xz = df_mul(x, z), yz = df_mul(y, z);
+    const df Ax = df_mul(A, x), Ay = df_mul(A, y), Az = df_mul(A, z);
+    const df Bxy = df_mul(B, xy), Bxz = df_mul(B, xz), Byz = df_mul(B, yz);
+    const df R[9] = {df_sub(one, df_mul(B, df_add(yy, zz))), df_sub(Bxy, Az), df_add(Bxz, Ay),
+                     df_add(Bxy, Az), df_sub(one, df_mul(B, df_add(xx, zz))), df_sub(Byz, Ax),
+                     df_sub(Bxz, Ay), df_add(Byz, Ax), df_sub(one, df_mul(B, df_add(xx, yy)))};
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        Rh[k] = R[k].h;
+        Rl[k] = R[k].l;
+    }
+}
+
+// The rotation-cube part of the pre-pass: R_r0 (FP64 Rodrigues' formula in
+// the point-dependent mode, whose vertex terms reuse its FP64 quantities;
+// else the double-float form), whether the cube lies wholly outside the
+// pi-ball, and the point-dependent terms when pt is given.
 __device__ inline void cube_prepare_rotation(const double r0[3], double rhw, CubePrep &o, CubePrepPoint *pt) {
+    double d2 = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        double e = fabs(r0[k]) - rhw;
+        if (e > 0) d2 += e * e;
+    }
+    o.infeasible = d2 > M_PI * M_PI ? 1 : 0;
+    if (!pt) {
+        rodrigues_df(r0, o.Rh, o.Rl);
+        return;
+    }
     double th2 = r0[0] * r0[0] + r0[1] * r0[1] + r0[2] * r0[2];
     double th = sqrt(th2), A, B;
     if (th < 1e-8) {
@@ -166,13 +217,6 @@ __device__ inline void cube_prepare_rotation(const double r0[3], double rhw, Cub
                    A * z + B * x * y,         1.0 - B * (x * x + z * z), -A * x + B * y * z,
                    -A * y + B * x * z,        A * x + B * y * z,         1.0 - B * (x * x + y * y)};
     for (int k = 0; k < 9; ++k) split_double(R[k], o.Rh[k], o.Rl[k]);
-    double d2 = 0.0;
-    for (int k = 0; k < 3; ++k) {
-        double e = fabs(r0[k]) - rhw;
-        if (e > 0) d2 += e * e;
-    }
-    o.infeasible = d2 > M_PI * M_PI ? 1 : 0;
-    if (!pt) return;  // the point-dependent terms below are read only in that mode
     // right Jacobian J_r(r0) = I - B [r0]x + C [r0]x^2, C = (|r0| - sin|r0|) / |r0|^3
     // (R_{r0 + d} = R_r0 R_{J_r d} to first order), and the vertex images J_r d / 2
     const double C = th < 1e-6 ? 1.0 / 6.0 - th2 / 120.0 : (th - A * th) / (th2 * th);

@@ -93,6 +93,63 @@ __device__ __forceinline__ df df_scale(float s, float c, float w) {
     return fast_two_sum(p.h, p.l);
 }
 
+// a / b for double-floats (b != 0): an FP32 quotient and one correction
+// from the exact remainder, relative error ~2^-44.
+__device__ __forceinline__ df df_div(df a, df b) {
+    const float q0 = a.h / b.h;
+    const df p = two_prod(q0, b.h);
+    const float r = ((a.h - p.h) - p.l + a.l) - q0 * b.l;  // a - q0 b; a.h - p.h is exact
+    return fast_two_sum(q0, r / b.h);
+}
+
+// sin and cos of a double-float 0 <= t <= 8, to ~2^-46 absolute (Cody and
+// Waite's reduction by k pi/2 with pi/2 in three floats, the first two of
+// 20 bits so that k times them is exact; then the Taylor series of sin and
+// cos on |x| <= pi/4, the terms from x^11 and x^10 on in FP32, the leading
+// five in double-float).
+__device__ inline void df_sincos(df t, df &s, df &c) {
+    const float P1 = 0x1.921fcp+0f, P2 = -0x1.5777ap-21f, P3 = -0x1.73dcb4p-43f;
+    const float k = rintf(t.h * 0x1.45f306p-1f);  // nearest multiple of pi/2
+    const df a = two_sum(t.h - k * P1, t.l);       // t.h - k P1 is exact
+    const df b = two_sum(a.h, -k * P2);
+    const df x = fast_two_sum(b.h, (a.l + b.l) - k * P3);
+    const df z = df_mul(x, x);
+    // sin x / x = sum (-1)^n z^n / (2n + 1)!, cos x = sum (-1)^n z^n / (2n)!
+    float ts = 0x1.71b8fp-66f, tc = -0x1.0ce396p-70f;
+    ts = fmaf(ts, z.h, -0x1.2f49b4p-57f);
+    ts = fmaf(ts, z.h, 0x1.952c78p-49f);
+    ts = fmaf(ts, z.h, -0x1.ae7f3ep-41f);
+    ts = fmaf(ts, z.h, 0x1.612462p-33f);
+    ts = fmaf(ts, z.h, -0x1.ae6456p-26f);
+    tc = fmaf(tc, z.h, 0x1.e542bap-62f);
+    tc = fmaf(tc, z.h, -0x1.682786p-53f);
+    tc = fmaf(tc, z.h, 0x1.ae7f3ep-45f);
+    tc = fmaf(tc, z.h, -0x1.93974ap-37f);
+    tc = fmaf(tc, z.h, 0x1.1eed8ep-29f);
+    tc = fmaf(tc, z.h, -0x1.27e4fcp-22f);
+    const df cs[5] = {{1.f, 0.f},
+                      {-0x1.555556p-3f, 0x1.555556p-28f},
+                      {0x1.111112p-7f, -0x1.dddddep-32f},
+                      {-0x1.a01a02p-13f, 0x1.7f97fap-39f},
+                      {0x1.71de3ap-19f, 0x1.55b1ccp-45f}};
+    const df cc[5] = {{1.f, 0.f},
+                      {-0.5f, 0.f},
+                      {0x1.555556p-5f, -0x1.555556p-30f},
+                      {-0x1.6c16c2p-10f, 0x1.27d27ep-35f},
+                      {0x1.a01a02p-16f, -0x1.7f97fap-42f}};
+    df ps = {ts, 0.f}, pc = {tc, 0.f};
+#pragma unroll
+    for (int n = 4; n >= 0; --n) {
+        ps = df_add(df_mul(ps, z), cs[n]);
+        pc = df_add(df_mul(pc, z), cc[n]);
+    }
+    const df sx = df_mul(x, ps);
+    const int q = (int)k & 3;
+    const df nsx = {-sx.h, -sx.l}, npc = {-pc.h, -pc.l};
+    s = q == 0 ? sx : q == 1 ? pc : q == 2 ? nsx : npc;
+    c = q == 0 ? pc : q == 1 ? nsx : q == 2 ? npc : sx;
+}
+
 __host__ __device__ inline void split_double(double x, float &h, float &l) {
     h = (float)x;
     l = (float)(x - (double)h);

@@ -14,6 +14,7 @@
 // a -> 1 / (a + 0.5), a -> 1 / sqrt(a), a -> lg2(a + 1.5)) and their results are
 // stored only under a flag that is never set; the approximate instructions
 // are volatile, so that the compiler keeps every one.
+#include "bounds_core.cuh"
 #include "gosma_internal.cuh"
 #include "packed.cuh"
 
@@ -131,7 +132,44 @@ int selftest_pipe_rates(gosma_ctx *ctx, double rates[PR_OPS], double *clock_mhz)
     return GOSMA_OK;
 }
 
+// The pre-pass's rotation matrices (hi + lo of each entry, in FP64) for n
+// rotation vectors, one thread each.
+__global__ void rodrigues_probe(int n, const double *__restrict__ r, double *__restrict__ R) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double r0[3] = {r[3 * i], r[3 * i + 1], r[3 * i + 2]};
+    float h[9], l[9];
+    rodrigues_df(r0, h, l);
+    for (int k = 0; k < 9; ++k) R[9 * (size_t)i + k] = (double)h[k] + (double)l[k];
+}
+
+int selftest_rodrigues(gosma_ctx *ctx, int n, const double *h_r, double *h_R) {
+    cudaSetDevice(ctx->device);
+    double *d = nullptr;
+    cudaError_t e = dev_malloc(ctx, (void **)&d, sizeof(double) * 12 * (size_t)n);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc(rodrigues)");
+    double *dR = d + 3 * (size_t)n;
+    e = cudaMemcpyAsync(d, h_r, sizeof(double) * 3 * (size_t)n, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) {
+        rodrigues_probe<<<(n + 127) / 128, 128, 0, ctx->stream>>>(n, d, dR);
+        ++ctx->launches;
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_R, dR, sizeof(double) * 9 * (size_t)n, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(d);
+    return e == cudaSuccess ? GOSMA_OK : cuda_fail(ctx, e, "rodrigues");
+}
+
 }  // namespace gosma
+
+extern "C" int gosma_selftest_rodrigues(gosma_ctx *ctx, int n, const double *r, double *R) {
+    if (!ctx) return GOSMA_EINVAL;
+    ctx->err.clear();
+    if (n < 0 || (n > 0 && (!r || !R))) return gosma::fail(ctx, GOSMA_EINVAL, "selftest_rodrigues: bad arguments");
+    if (n == 0) return GOSMA_OK;
+    return gosma::selftest_rodrigues(ctx, n, r, R);
+}
 
 extern "C" int gosma_selftest_pipe_rates(gosma_ctx *ctx, double rates[7], double *clock_mhz) {
     if (!ctx) return GOSMA_EINVAL;

@@ -112,6 +112,7 @@ SIGNATURES = {
     "gosma_selftest_approx": (C.c_int, [C.c_void_p, D, D]),
     "gosma_selftest_wait_timeout": (C.c_int, [C.c_void_p, C.c_double]),
     "gosma_selftest_pipe_rates": (C.c_int, [C.c_void_p, D, D]),
+    "gosma_selftest_rodrigues": (C.c_int, [C.c_void_p, C.c_int, D, D]),
     "gosma_debug_fail_allocations": (C.c_int, [C.c_void_p, C.c_int]),
     "gosma_kernel_launches": (C.c_longlong, [C.c_void_p]),
     "gosma_mlp_set_params": (C.c_int, [C.c_void_p, FP]),
@@ -592,6 +593,13 @@ class Gosma:
         mhz = C.c_double()
         self._check(self.L.gosma_selftest_pipe_rates(self.h, _p(r), C.byref(mhz)), "selftest_pipe_rates")
         return dict(zip(("ffma", "ffma2", "ex2", "sqrt", "rcp", "rsqrt", "lg2"), r.tolist()), clock_mhz=mhz.value)
+
+    def selftest_rodrigues(self, r):
+        """The pre-pass's rotation matrices (double-float, summed in FP64) for rotation vectors r (n x 3)."""
+        r = _f64(r, (-1, 3))
+        R = np.zeros((len(r), 3, 3))
+        self._check(self.L.gosma_selftest_rodrigues(self.h, len(r), _p(r), _p(R)), "selftest_rodrigues")
+        return R
 
     def selftest_wait_timeout(self, limit_seconds=0.05):
         """Returns the library's return code (GOSMA_ETIMEOUT when the bounded wait gave up)."""

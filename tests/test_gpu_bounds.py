@@ -27,6 +27,36 @@ def test_approx_instruction_accuracy(ctx):
     assert np.all(measured <= assumed), (measured, assumed)
 
 
+def test_prepass_rotation_matrices_match_fp64(ctx, oracle_mod):
+    """The pre-pass forms R_r (Rodrigues' formula, Sec. 4.1) in double-float
+    arithmetic: every entry within 2^-42 of the oracle's FP64 rotation (about
+    ten double-float operations of relative error ~2^-47 on entries up to 2;
+    the directions it rotates may be off by u/2 in their FP32 parts, so
+    2^-42 is far inside what the pair terms' allowance carries), on
+    the cube centres the solvers use (levels 1-30 of the pi-cube), random
+    vectors up to |r| = pi sqrt(3), vectors near the range reduction's
+    boundaries (|r| near multiples of pi/4), the small-angle series
+    (|r| < 1e-3) and its edge, and the zero vector."""
+    rng = np.random.default_rng(5)
+    vecs = [np.zeros(3)]
+    for lr in range(1, 31):  # cell centres at each level
+        h = np.pi * 2.0 ** -lr
+        cells = rng.integers(0, 2 ** lr, (8, 3))
+        vecs += list(-np.pi + (2 * cells + 1) * h)
+    d = rng.standard_normal((4000, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    vecs += list(d[:1000] * rng.uniform(0, np.pi * np.sqrt(3), 1000)[:, None])
+    near = np.concatenate([k * np.pi / 4 + rng.uniform(-1e-6, 1e-6, 100) for k in range(1, 7)])
+    vecs += list(d[1000:1600] * near[:, None])
+    small = np.concatenate([10.0 ** rng.uniform(-12, -3, 300), 1e-3 * (1 + rng.uniform(-1e-4, 1e-4, 100))])
+    vecs += list(d[1600:2000] * small[:, None])
+    r = np.array(vecs)
+    got = ctx.selftest_rodrigues(r)
+    ref = np.array([oracle_mod.rodrigues(v) for v in r])
+    err = np.abs(got - ref).max(axis=(1, 2))
+    assert err.max() <= 2.0 ** -42, (err.max(), r[err.argmax()])
+
+
 def test_pipe_rates_are_plausible(ctx):
     """The measured pipe throughputs that the roofline divides by: FP32 FMA at
     most the 128 lanes per SM per clock of the hardware (within clock
