@@ -34,6 +34,7 @@
 #include <vector>
 
 #include "bnb_common.cuh"
+#include "prep_tile.cuh"
 #include "host_rules.h"
 
 namespace gosma {

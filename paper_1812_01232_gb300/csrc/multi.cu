@@ -46,6 +46,7 @@
 #include <vector>
 
 #include "bnb_common.cuh"
+#include "prep_tile.cuh"
 #include "classes.h"
 #include "host_rules.h"
 #include "mlp.cuh"
@@ -1792,7 +1793,7 @@ extern "C" int gosma_bnb_solve_batch_ex(gosma_ctx *ctx, int nprob, const gosma_p
         mp_cscan_any<true><<<nprob, MP_BLOCK, 0, st>>>(dS, Qb, nprob);
         mp_scatter<true><<<chunk_grid, CH_BLOCK, 0, st>>>(dP, dS, Qb, nprob, parents, off);
         mp_flip<<<(nprob + 255) / 256, 256, 0, st>>>(dS, nprob, d_tcount, lo.trace_cap);
-        mp_prep<<<2 * ctx->sm_count, PREP_TILE, 0, st>>>(dP, off, nprob, parents, prep);
+        mp_prep<<<4 * ctx->sm_count, PREP_TILE, 0, st>>>(dP, off, nprob, parents, prep);
         ctx->launches += 16;
     };
     auto back = [&]() -> cudaError_t {
