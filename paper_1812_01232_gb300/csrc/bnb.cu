@@ -47,7 +47,7 @@ struct Status {
     unsigned int best_child_u;    // smallest child index attaining it
     unsigned int minkey;          // smallest live key (orderable)
     int best_child;               // child with the smallest upper bound (-1: none)
-    int pad;
+    unsigned int rest_min;        // smallest live key the iteration's pop leaves in the queue
     double best_ub;
     Node best_node;
     // selection results
@@ -92,6 +92,7 @@ __global__ void sel_find(unsigned int *__restrict__ hist, int pass, Status *st, 
         __syncthreads();
     }
     unsigned int before = t ? part[t - 1] : 0u;
+    if (pass == 2 && t == 0) st->rest_min = DEAD;  // ext_count and ext_scan fill it
     if (before < need && need <= before + a) {
         st->sel_bin[pass] = 2 * t;
         st->sel_need[pass] = need - before;
@@ -134,21 +135,27 @@ __device__ inline int block_excl_scan(int v, int *sh, int &total) {
     return base + x - v;
 }
 
-// Per tile: number of keys below T and equal to T.
-__global__ void ext_count(const uint32_t *__restrict__ keys, unsigned long long n, const Status *st,
+// Per tile: number of keys below T and equal to T; and the smallest live
+// key above T (the pop leaves it), so that the global lower bound needs no
+// further pass over the queue.
+__global__ void ext_count(const uint32_t *__restrict__ keys, unsigned long long n, Status *st,
                           int2 *__restrict__ cnt) {
     __shared__ int sh[32];
     uint32_t T = sel_threshold(st);
     unsigned long long base = (unsigned long long)blockIdx.x * SEL_TILE + threadIdx.x * SEL_ITEMS;
     int lt = 0, eq = 0;
+    uint32_t above = DEAD;
     for (int k = 0; k < SEL_ITEMS; ++k) {
         unsigned long long q = base + k;
         if (q < n) {
             uint32_t key = keys[q];
             lt += key != DEAD && key < T;
             eq += key != DEAD && key == T;
+            if (key > T) above = min(above, key);  // DEAD is the largest key
         }
     }
+    for (int o = 16; o > 0; o >>= 1) above = min(above, __shfl_down_sync(0xffffffffu, above, o));
+    if ((threadIdx.x & 31) == 0 && above != DEAD) atomicMin(&st->rest_min, above);
     int tot_lt, tot_eq;
     block_excl_scan(lt, sh, tot_lt);
     block_excl_scan(eq, sh, tot_eq);
@@ -158,8 +165,9 @@ __global__ void ext_count(const uint32_t *__restrict__ keys, unsigned long long 
 // One block: per tile, how many of its ties are popped and where its popped
 // nodes start in the parent buffer.  Each thread takes SEL_ITEMS consecutive
 // tiles, so that a queue of tens of millions of keys (thousands of tiles)
-// needs few block-wide scans.
-__global__ void ext_scan(const int2 *__restrict__ cnt, int ntile, const Status *st, int2 *__restrict__ off) {
+// needs few block-wide scans.  Keys equal to T that are not popped stay in
+// the queue: then T is the smallest live key left.
+__global__ void ext_scan(const int2 *__restrict__ cnt, int ntile, Status *st, int2 *__restrict__ off) {
     __shared__ int sh[32];
     __shared__ int carry_eq, carry_pop;
     if (threadIdx.x == 0) {
@@ -199,6 +207,7 @@ __global__ void ext_scan(const int2 *__restrict__ cnt, int ntile, const Status *
         }
         __syncthreads();
     }
+    if (threadIdx.x == 0 && carry_eq > ties) atomicMin(&st->rest_min, sel_threshold(st));
 }
 
 __global__ void ext_scatter(uint32_t *__restrict__ keys, const Node *__restrict__ q, unsigned long long n,
@@ -380,19 +389,27 @@ __global__ void app_scatter(const Node *__restrict__ kids, const double *__restr
     }
     int tot;
     unsigned long long pos = tail + off[blockIdx.x].x + block_excl_scan(cnt, sh, tot);
+    uint32_t kmin = DEAD;
     for (int k = 0; k < SEL_ITEMS; ++k)
         if (alive[k]) {
             if (pos < cap) {
                 q[pos] = kids[base + k];
-                keys[pos] = order_key(__double2float_rd(kids[base + k].lb));
+                const uint32_t key = order_key(__double2float_rd(kids[base + k].lb));
+                keys[pos] = key;
+                kmin = min(kmin, key);
             }
             ++pos;
         }
+    for (int o = 16; o > 0; o >>= 1) kmin = min(kmin, __shfl_down_sync(0xffffffffu, kmin, o));
+    if ((threadIdx.x & 31) == 0 && kmin != DEAD) atomicMin(&st->minkey, kmin);
 }
 
-// Publish the iteration's results (one thread).
+// Publish the iteration's results (one thread): the smallest live key (the
+// global lower bound of Algorithm 1) is the smaller of the appended
+// children's and what the pop left in the queue.
 __global__ void app_finish(const Node *__restrict__ kids, const double *__restrict__ kid_ub, Status *st) {
     st->tail = st->new_tail;
+    st->minkey = min(st->minkey, st->rest_min);
     if (st->best_key != ~0ULL) {
         int c = (int)st->best_child_u;
         st->best_child = c;
@@ -612,7 +629,8 @@ static int grid_for(unsigned long long n, int block, int sm) {
     return g < 1 ? 1 : (int)g;
 }
 
-// One iteration on the device: select, extract, bound, append, min.
+// One iteration on the device: select, extract, bound, append (the smallest
+// live key, the global lower bound, from the extraction and the append).
 static int iterate(gosma_ctx *ctx, const Domain &dom, BnbState *s, unsigned long long tail, int np, cudaEvent_t *ev,
                    long long *self_children) {
     cudaStream_t st = ctx->stream;
@@ -650,10 +668,6 @@ static int iterate(gosma_ctx *ctx, const Domain &dom, BnbState *s, unsigned long
     app_scatter<<<ktile, SEL_BLOCK, 0, st>>>(s->kids, s->kid_ub, nk, s->dstar, s->off, q, keys, s->cap, s->st);
     ++ctx->launches;
     app_finish<<<1, 1, 0, st>>>(s->kids, s->kid_ub, s->st);
-    ++ctx->launches;
-    unsigned long long ntail = tail + 8ULL * np;  // upper bound of the new tail
-    if (ntail > s->cap) ntail = s->cap;
-    min_key<<<grid_for(ntail, 256, ctx->sm_count), 256, 0, st>>>(keys, ntail, s->st);
     ++ctx->launches;
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "launch(append/min)");
