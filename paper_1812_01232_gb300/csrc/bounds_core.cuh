@@ -85,9 +85,10 @@ struct CubeShared {
 // Directions are formed as double-floats (hi + lo equals the unit vector to
 // ~2^-44); the pair loops read the FP32 parts only and carry the low parts'
 // effect as an absolute allowance (GOSMA_HI_ALLOW), and the model rows' low
-// parts serve the point-dependent rotation angle.  The pair loops take partners two at a time into the two lanes
-// of packed FP32x2 registers, so the records are stored in pairs, lanes
-// interleaved: one 16-byte load gives two aligned lane pairs.  A missing
+// parts serve the point-dependent rotation angle.  The pair loops take
+// partners two at a time into the two lanes of packed FP32x2 registers, so
+// the records are stored in pairs, lanes interleaved: one 16-byte load gives
+// two aligned lane pairs.  A missing
 // partner of an odd count is a copy of the last one with zero weight.
 //   JP (image columns 2p, 2p+1; lanes a, b), 4 float4 per pair:
 //     (ux_a, ux_b, uy_a, uy_b) (uz_a, uz_b, k2_a, k2_b) (lqc_a, lqc_b, lqb_a, lqb_b) (lz_a, lz_b, Q_a, Q_b)
@@ -142,13 +143,6 @@ __device__ inline int pow2ceil(int x) {
     return p;
 }
 
-// Pre-pass for one cube, in three parts that depend on different parts of
-// the cube, so that a caller can share them between cubes (the eight children
-// of a translation split share their parent's rotation cube, the children of
-// any split share a level): Rodrigues' formula (Sec. 4.1) and the
-// rotation-cube terms, Lemma 2 read as angle(R_r p, R_r0 p) <= |r - r0| <=
-// sqrt(3) r_hw capped at pi, and the translation cuboid split into
-// double-floats.
 // Rodrigues' formula R = I + A [r]x + B [r]x^2 (A = sin|r| / |r|, B = (1 -
 // cos|r|) / |r|^2) in double-float arithmetic, R to ~2^-44 absolute: the
 // FP64 form's sincos and divisions cost the FP64 unit (about 1/64 of the
@@ -186,10 +180,18 @@ __device__ inline void rodrigues_df(const double r0[3], float Rh[9], float Rl[9]
     }
 }
 
-// The rotation-cube part of the pre-pass: R_r0 (FP64 Rodrigues' formula in
-// the point-dependent mode, whose vertex terms reuse its FP64 quantities;
-// else the double-float form), whether the cube lies wholly outside the
-// pi-ball, and the point-dependent terms when pt is given.
+// Pre-pass for one cube, in three parts that depend on different parts of
+// the cube, so that a caller can share them between cubes (the eight children
+// of a translation split share their parent's rotation cube, the children of
+// any split share a level): Rodrigues' formula (Sec. 4.1) and the
+// rotation-cube terms, Lemma 2 read as angle(R_r p, R_r0 p) <= |r - r0| <=
+// sqrt(3) r_hw capped at pi, and the translation cuboid split into
+// double-floats.
+//
+// The rotation-cube part: R_r0 (FP64 Rodrigues' formula in the
+// point-dependent mode, whose vertex terms reuse its FP64 quantities; else
+// the double-float form), whether the cube lies wholly outside the pi-ball,
+// and the point-dependent terms when pt is given.
 __device__ inline void cube_prepare_rotation(const double r0[3], double rhw, CubePrep &o, CubePrepPoint *pt) {
     double d2 = 0.0;
     for (int k = 0; k < 3; ++k) {
@@ -405,8 +407,9 @@ __device__ __forceinline__ float2 ex2_2a(float2 x) { return make_float2(ex2a(x.x
 // for j' (their JP records P0 .. P2): adds to pl the upper bound of each
 // pair's term over the cube (Theorem 1, Eq. K1i2j_ub with B of Eq.
 // K1i2j_ub_B) and to pc the term at the centre (Lemma 1), both without the
-// row multipliers; the column factor enters each exponent as its log2.  Every operation is per lane, rounded to nearest as a
-// scalar FP32 operation would be (the error budget above holds per lane).
+// row multipliers; the column factor enters each exponent as its log2.
+// Every operation is per lane, rounded to nearest as a scalar FP32
+// operation would be (the error budget above holds per lane).
 //   |v -+ u|^2 from the directions' FP32 parts, the centre term in the linear
 //   form above, then the bound: B = max(0, theta - s), s = psi_t,i + psi_r
 //   (Cs, Ss = cos, sin of s/2); cos^2(B/2) from the sine bounds as
@@ -1031,7 +1034,7 @@ __device__ void cube_bounds(const MixDev &mx, const CubePrep &prep, const CubePr
     // The four lanes that hold the sums (lanes 0, 8, 16, 24 of the group's
     // first warp; 0, 4, 8, 12 of a half-warp group) convert them to FP64
     // together: an FP64 instruction costs the FP64 unit a whole warp's time
-    // however few lanes run it (and the two groups of a warp share it).
+    // however few lanes run it.
     // (the self sums only when computed: callers that skip them use cached ones)
     constexpr int SL = sum_lane_stride<GT>();
     if (tid < 4 * SL && tid % SL == 0) {
