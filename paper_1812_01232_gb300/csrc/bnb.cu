@@ -154,12 +154,20 @@ __global__ void ext_count(const uint32_t *__restrict__ keys, unsigned long long 
             if (key > T) above = min(above, key);  // DEAD is the largest key
         }
     }
+    // one atomic per block, and only when the block beats the running minimum
+    // (atomics on one address from every warp would serialise)
+    __shared__ uint32_t wmin[SEL_BLOCK / 32];
     for (int o = 16; o > 0; o >>= 1) above = min(above, __shfl_down_sync(0xffffffffu, above, o));
-    if ((threadIdx.x & 31) == 0 && above != DEAD) atomicMin(&st->rest_min, above);
+    if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = above;
     int tot_lt, tot_eq;
-    block_excl_scan(lt, sh, tot_lt);
+    block_excl_scan(lt, sh, tot_lt);  // its barriers also publish wmin
     block_excl_scan(eq, sh, tot_eq);
-    if (threadIdx.x == 0) cnt[blockIdx.x] = make_int2(tot_lt, tot_eq);
+    if (threadIdx.x == 0) {
+        cnt[blockIdx.x] = make_int2(tot_lt, tot_eq);
+        uint32_t m = wmin[0];
+        for (int w = 1; w < SEL_BLOCK / 32; ++w) m = min(m, wmin[w]);
+        if (m < *(volatile const uint32_t *)&st->rest_min) atomicMin(&st->rest_min, m);
+    }
 }
 
 // One block: per tile, how many of its ties are popped and where its popped
