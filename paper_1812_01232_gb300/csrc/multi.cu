@@ -569,12 +569,12 @@ __global__ void __launch_bounds__(PREP_TILE) mp_prep(const ProbDev *__restrict__
 
 constexpr int MP_CHILD_RUN = 4;  // children per work item (a divisor of 8)
 
-// G cubes per block: groups of BLOCK / G threads (whole warps; several cubes
-// per block keep about 100 registers per thread, as their group barriers and
-// slots need them, and 128 x 1 keeps 7 blocks per SM: at 8 its per-problem
-// lookups spill), each with its
-// own shared arrays (group_floats floats of the dynamic shared memory) and
-// its own work slot.
+// G cubes per block: groups of BLOCK / G threads (whole warps, or half a
+// warp in 32 x 2; several cubes per block keep about 100 registers per
+// thread, as their group barriers and slots need them, and 128 x 1 keeps 7
+// blocks per SM: at 8 its per-problem lookups spill), each with its own
+// shared arrays (group_floats floats of the dynamic shared memory) and its
+// own work slot.
 template <int BLOCK, int G>
 __global__ void __launch_bounds__(BLOCK, G == 1 ? (BLOCK == 128 ? 7 : bound_min_blocks<BLOCK>()) : 65536 / (BLOCK * 100))
     mp_bound(const ProbDev *__restrict__ P, const int *__restrict__ off, int nprob, const Node *__restrict__ parents,
