@@ -183,18 +183,28 @@ class Clocks:
         return out
 
 
+def _code_only(text):
+    """Source text without comments and blank lines (the fingerprint follows
+    the code, not its commentary)."""
+    import re
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(line.rstrip() for line in text.split("\n") if line.strip())
+
+
 def kernel_source_sha256():
     """Fingerprint of the bound kernel's device code: the bound core, the
-    double-float helpers, the queue-node helpers and the kernel function."""
+    double-float helpers, the queue-node helpers and the kernel function,
+    comments left out."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_1812_01232_gb300", "csrc")
     h = hashlib.sha256()
     for f in ("bounds_core.cuh", "dfloat.cuh", "bnb_common.cuh"):
-        h.update(open(os.path.join(csrc, f), "rb").read())
+        h.update(_code_only(open(os.path.join(csrc, f)).read()).encode())
     src = open(os.path.join(csrc, "bnb.cu")).read()
     i = src.index("bound_children(MixDev mx")
     j = src.index("\n}\n", i)
-    h.update(src[i:j].encode())
+    h.update(_code_only(src[i:j]).encode())
     return h.hexdigest()
 
 

@@ -1,11 +1,13 @@
 // Per-cube Theorem 1 bounds: the hot loop of GOSMA (Algorithm 1, "evaluate
 // the bounds of the sub-cubes in parallel").
 //
-// One thread block evaluates one sub-cube C_r x C_t at a time:
-//   pre-pass (cube_prepare): R_r0 by Rodrigues' formula in FP64, split into
-//            FP32 hi/lo pairs, the rotation uncertainty psi_r (Lemma 2) as an
-//            outward-rounded half-angle cosine/sine, and the cuboid as
-//            double-floats, one thread per cube;
+// One thread group (a block, part of a block, or half a warp for the
+// smallest mixtures) evaluates one sub-cube C_r x C_t at a time:
+//   pre-pass (cube_prepare): R_r0 by Rodrigues' formula in double-float
+//            arithmetic (hi/lo FP32 pairs), the rotation uncertainty psi_r
+//            (Lemma 2) as an outward-rounded half-angle cosine/sine, and the
+//            cuboid as double-floats, per cube (the solvers share the parts
+//            that siblings have in common);
 //   phase 1  per image component j: u_j = R_r0^T mu_2j; per model component
 //            i: v_i, kappa_1i(t0), the kappa interval [a_i, b_i] over the
 //            cuboid, psi_t(mu_1i) (Lemma 3) -- all in double-float FP32, into
@@ -13,7 +15,7 @@
 //   phase 2  diagonal self terms, all cross pairs (i, j) and all self pairs
 //            i < m; threads own model rows and stream the partner arrays
 //            from shared memory (broadcast reads within a warp);
-//   phase 3  block reduction of the four sums in double-float.
+//   phase 3  group reduction of the four sums in double-float.
 // No FP64 arithmetic runs per component or per pair: FP64 is ~1/64 of the
 // FP32 rate on this GPU.
 //
