@@ -686,8 +686,8 @@ __device__ __forceinline__ int next_cube(int *counter, int *slot) {
 
 // The whole per-cube computation.  Every thread of the group (GT threads,
 // group gid of the block, gtid its thread) must call it with the same cube,
-// its own CubeShared and shared arrays; sums are valid in the group's thread
-// 0 on return.  need_self = 0 skips the self pairs (the caller reuses cached
+// its own CubeShared and shared arrays; the sums in out (shared memory) are
+// valid for the whole group on return.  need_self = 0 skips the self pairs (the caller reuses cached
 // self sums).  reuse_rows = 1 skips the model rows (phase 1b): the group's
 // previous call was for a cube of the same mixtures and the same translation
 // cuboid (a sibling after a rotation split), and neither call needs its self
